@@ -1,0 +1,432 @@
+"""FP64 CPU oracle of the implicit FE time step (TEST INFRASTRUCTURE ONLY).
+
+Only tests, the package's smoke check and the benchmark's CPU-baseline leg may
+import this module.  The product path (the CUDA library and its binding) never
+calls it, and it shares no code with that path: the only common input is the
+seeded workload generator ``fe_inputs``.
+
+What it computes, in the paper's order (arXiv 2306.05893, Section 3):
+  * element internal force f_e = dW_e/dx and exact tangent K_e = df_e/dx for
+    P1 tets (one point) and trilinear hexes (2x2x2 Gauss), for St Venant-
+    Kirchhoff, compressible neo-Hookean and decoupled Mooney-Rivlin energies
+    written with the invariants I1 = tr C, I2 = ((tr C)^2 - tr C^2)/2 and
+    J = det F of Section 3.1;
+  * consistent mass M;
+  * triplet assembly by plain summation, then the projective constraints of
+    Section 5.1 (fixed rows and columns cleared, 1 on the diagonal);
+  * A = (1 + h alpha) M + h (beta + h) K (Eq. "dynamic equation2") and
+    b = p - f - (alpha M + (beta + h) K) v (Eq. "dynamic equation1" with the
+    Rayleigh damping B = alpha M + beta K);
+  * a direct sparse solve of A a = b, then backward Euler
+    v+ = v + h a, q+ = q + h v+ (Eq. "implicit integration");
+  * the CSR pattern and the triplet -> slot map C (Section 4.2), built here by
+    sorting unique (row, col) keys, i.e. independently of the double transpose.
+
+Everything is numpy float64 (complex128 where a complex-step derivative is
+taken), vectorised over elements only: no blocking, fusion or reordering.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+SVK, NEOHOOKE, MOONEY_RIVLIN = 0, 1, 2
+TET4, HEX8 = 0, 1
+
+_I3 = np.eye(3)
+
+
+# ============================================================ material laws
+# Each law gives the energy density psi(F), the first Piola-Kirchhoff stress
+# P = dpsi/dF and the tangent CC[i,J,k,L] = dP_iJ / dF_kL.  Arrays broadcast
+# over leading axes; p0, p1, p2 are the law's three parameters:
+#   SVK, neo-Hookean: (mu, lambda, unused); Mooney-Rivlin: (C10, C01, kappa).
+
+def _ex(p, F):
+    return np.asarray(p)[..., None, None]
+
+
+def _ex4(p):
+    return np.asarray(p)[..., None, None, None, None]
+
+
+def _tr(A):
+    return np.einsum("...ii->...", A)
+
+
+def svk_psi(F, mu, lam, _=None):
+    E = 0.5 * (np.swapaxes(F, -1, -2) @ F - _I3)
+    trE = _tr(E)
+    return mu * _tr(E @ E) + 0.5 * lam * trE * trE
+
+
+def svk_pk1(F, mu, lam, _=None):
+    E = 0.5 * (np.swapaxes(F, -1, -2) @ F - _I3)
+    S = 2.0 * _ex(mu, F) * E + _ex(lam, F) * _tr(E)[..., None, None] * _I3
+    return F @ S
+
+
+def svk_tangent(F, mu, lam, _=None):
+    E = 0.5 * (np.swapaxes(F, -1, -2) @ F - _I3)
+    S = 2.0 * _ex(mu, F) * E + _ex(lam, F) * _tr(E)[..., None, None] * _I3
+    B = F @ np.swapaxes(F, -1, -2)
+    CC = np.einsum("ik,...LJ->...iJkL", _I3, S)
+    CC = CC + _ex4(mu) * (np.einsum("...iL,...kJ->...iJkL", F, F)
+                          + np.einsum("...ik,JL->...iJkL", B, _I3))
+    CC = CC + _ex4(lam) * np.einsum("...iJ,...kL->...iJkL", F, F)
+    return CC
+
+
+def nh_psi(F, mu, lam, _=None):
+    J = np.linalg.det(F)
+    lnJ = np.log(J)
+    I1 = _tr(np.swapaxes(F, -1, -2) @ F)
+    return 0.5 * mu * (I1 - 3.0) - mu * lnJ + 0.5 * lam * lnJ * lnJ
+
+
+def nh_pk1(F, mu, lam, _=None):
+    G = np.swapaxes(np.linalg.inv(F), -1, -2)
+    lnJ = np.log(np.linalg.det(F))
+    return _ex(mu, F) * (F - G) + (_ex(lam, F) * lnJ[..., None, None]) * G
+
+
+def nh_tangent(F, mu, lam, _=None):
+    G = np.swapaxes(np.linalg.inv(F), -1, -2)
+    lnJ = np.log(np.linalg.det(F))
+    CC = _ex4(mu) * np.einsum("ik,JL->iJkL", _I3, _I3)
+    CC = CC + (_ex4(mu) - _ex4(lam) * lnJ[..., None, None, None, None]) * np.einsum(
+        "...iL,...kJ->...iJkL", G, G)
+    CC = CC + _ex4(lam) * np.einsum("...iJ,...kL->...iJkL", G, G)
+    return CC
+
+
+def _mr_parts(F):
+    C = np.swapaxes(F, -1, -2) @ F
+    I1 = _tr(C)
+    I2 = 0.5 * (I1 * I1 - _tr(C @ C))
+    J = np.linalg.det(F)
+    G = np.swapaxes(np.linalg.inv(F), -1, -2)
+    return C, I1, I2, J, G
+
+
+def mr_psi(F, c10, c01, kappa):
+    _, I1, I2, J, _ = _mr_parts(F)
+    return (c10 * (J ** (-2.0 / 3.0) * I1 - 3.0) + c01 * (J ** (-4.0 / 3.0) * I2 - 3.0)
+            + 0.5 * kappa * (J - 1.0) ** 2)
+
+
+def mr_pk1(F, c10, c01, kappa):
+    C, I1, I2, J, G = _mr_parts(F)
+    x = lambda s: s[..., None, None]  # noqa: E731
+    J23, J43 = J ** (-2.0 / 3.0), J ** (-4.0 / 3.0)
+    H = x(I1) * F - F @ C
+    P = _ex(c10, F) * x(J23) * (2.0 * F - (2.0 / 3.0) * x(I1) * G)
+    P = P + _ex(c01, F) * x(J43) * (2.0 * H - (4.0 / 3.0) * x(I2) * G)
+    P = P + _ex(kappa, F) * x((J - 1.0) * J) * G
+    return P
+
+
+def mr_tangent(F, c10, c01, kappa):
+    C, I1, I2, J, G = _mr_parts(F)
+    B = F @ np.swapaxes(F, -1, -2)
+    x2 = lambda s: s[..., None, None]  # noqa: E731
+    x4 = lambda s: s[..., None, None, None, None]  # noqa: E731
+    J23, J43 = J ** (-2.0 / 3.0), J ** (-4.0 / 3.0)
+    H = x2(I1) * F - F @ C
+    dd = np.einsum("ik,JL->iJkL", _I3, _I3)
+    o = lambda a, b: np.einsum("...iJ,...kL->...iJkL", a, b)  # noqa: E731  a_iJ b_kL
+    x_ = lambda a, b: np.einsum("...iL,...kJ->...iJkL", a, b)  # noqa: E731  a_iL b_kJ
+    t1 = (-(2.0 / 3.0) * o(2.0 * F - (2.0 / 3.0) * x2(I1) * G, G) + 2.0 * dd
+          - (4.0 / 3.0) * o(G, F) + (2.0 / 3.0) * x4(I1) * x_(G, G))
+    d_fc = (np.einsum("ik,...LJ->...iJkL", _I3, C) + x_(F, F)
+            + np.einsum("...ik,JL->...iJkL", B, _I3))
+    t2 = (-(4.0 / 3.0) * o(2.0 * H - (4.0 / 3.0) * x2(I2) * G, G)
+          + 2.0 * (2.0 * o(F, F) + x4(I1) * dd - d_fc)
+          - (8.0 / 3.0) * o(G, H) + (4.0 / 3.0) * x4(I2) * x_(G, G))
+    t3 = x4((2.0 * J - 1.0) * J) * o(G, G) - x4(J * J - J) * x_(G, G)
+    return _ex4(c10) * x4(J23) * t1 + _ex4(c01) * x4(J43) * t2 + _ex4(kappa) * t3
+
+
+LAWS = {
+    SVK: (svk_psi, svk_pk1, svk_tangent),
+    NEOHOOKE: (nh_psi, nh_pk1, nh_tangent),
+    MOONEY_RIVLIN: (mr_psi, mr_pk1, mr_tangent),
+}
+
+
+# ======================================================== element geometry
+
+def _hex_corners():
+    return np.array([[2 * (a & 1) - 1, 2 * ((a >> 1) & 1) - 1, 2 * ((a >> 2) & 1) - 1]
+                     for a in range(8)], dtype=np.float64)
+
+
+def hex_shape(xi):
+    """Trilinear shape functions N[8] and derivatives dN[8, 3] at xi on [-1,1]^3,
+    local node a at corner (2dx-1, 2dy-1, 2dz-1) with a = dx + 2dy + 4dz."""
+    c = _hex_corners()
+    f = 1.0 + c * np.asarray(xi)[None, :]
+    N = np.prod(f, axis=1) / 8.0
+    dN = np.empty((8, 3))
+    for r in range(3):
+        o = [s for s in range(3) if s != r]
+        dN[:, r] = c[:, r] * f[:, o[0]] * f[:, o[1]] / 8.0
+    return N, dN
+
+
+def hex_gauss_points():
+    """2x2x2 Gauss points +-1/sqrt(3) (weight 1) in the local corner order."""
+    return _hex_corners() / math.sqrt(3.0)
+
+
+class Quadrature:
+    """Rest-state data: gradN [E, Q, npe, 3] (w.r.t. rest coordinates X) and
+    weights w [E, Q] (volume for a tet; detJ0 for a hex Gauss point)."""
+
+    def __init__(self, elem_type, X, conn):
+        self.elem_type = elem_type
+        self.conn = np.asarray(conn)
+        Xe = np.asarray(X)[self.conn]                       # [E, npe, 3]
+        if elem_type == TET4:
+            Dm = np.swapaxes(Xe[:, 1:] - Xe[:, [0]], 1, 2)  # columns X_a - X_0
+            Gm = np.linalg.inv(Dm)                           # row a-1 = grad N_a
+            g = np.concatenate([-Gm.sum(axis=1, keepdims=True), Gm], axis=1)
+            self.gradN = g[:, None]                          # [E, 1, 4, 3]
+            self.w = (np.linalg.det(Dm) / 6.0)[:, None]
+        else:
+            gps = hex_gauss_points()
+            grads, ws = [], []
+            for q in range(8):
+                _, dN = hex_shape(gps[q])
+                J0 = np.einsum("eai,ar->eir", Xe, dN)         # dX_i / dxi_r
+                J0inv = np.linalg.inv(J0)
+                grads.append(np.einsum("ar,erJ->eaJ", dN, J0inv))
+                ws.append(np.linalg.det(J0))
+            self.gradN = np.stack(grads, axis=1)             # [E, 8, 8, 3]
+            self.w = np.stack(ws, axis=1)                    # [E, 8]
+
+    @property
+    def npe(self):
+        return self.conn.shape[1]
+
+    def deformation_gradient(self, x):
+        """F[e, q] = sum_a x_a (outer) gradN_a."""
+        xe = np.asarray(x)[self.conn]                        # [E, npe, 3]
+        return np.einsum("eai,eqaJ->eqiJ", xe, self.gradN)
+
+
+def _params(params, E):
+    p = np.asarray(params, dtype=np.float64)
+    if p.ndim == 1:
+        p = np.broadcast_to(p, (E, 3))
+    return p[:, 0][:, None], p[:, 1][:, None], p[:, 2][:, None]   # [E, 1] each
+
+
+def element_energy(quad, x, model, params):
+    """W_e = sum_q w_q psi(F_q)  -> [E]."""
+    psi = LAWS[model][0]
+    F = quad.deformation_gradient(x)
+    a, b, c = _params(params, F.shape[0])
+    return np.einsum("eq,eq->e", quad.w, psi(F, a, b, c))
+
+
+def element_force(quad, x, model, params):
+    """f_e[3a+i] = sum_q w_q sum_J P_iJ gradN_aJ  (internal force dW_e/dx)."""
+    P = LAWS[model][1](quad.deformation_gradient(x), *_params(params, quad.conn.shape[0]))
+    f = np.einsum("eq,eqiJ,eqaJ->eai", quad.w, P, quad.gradN)
+    return f.reshape(f.shape[0], -1)
+
+
+def element_tangent(quad, x, model, params):
+    """K_e[3a+i, 3b+k] = sum_q w_q sum_JL CC_iJkL gradN_aJ gradN_bL."""
+    CC = LAWS[model][2](quad.deformation_gradient(x), *_params(params, quad.conn.shape[0]))
+    K = np.einsum("eq,eqiJkL,eqaJ,eqbL->eaibk", quad.w, CC, quad.gradN, quad.gradN,
+                  optimize=True)
+    E, n = K.shape[0], K.shape[1] * 3
+    return K.reshape(E, n, n)
+
+
+def element_mass(elem_type, X, conn, rho):
+    """Consistent mass scalars m_e[a, b] = rho int N_a N_b dV (times I3 per block)."""
+    X = np.asarray(X)
+    if elem_type == TET4:
+        Xe = X[conn]
+        Dm = np.swapaxes(Xe[:, 1:] - Xe[:, [0]], 1, 2)
+        V = np.linalg.det(Dm) / 6.0
+        base = (np.ones((4, 4)) + np.eye(4)) / 20.0
+        return rho * V[:, None, None] * base[None]
+    Xe = X[conn]
+    m = np.zeros((conn.shape[0], 8, 8))
+    for xi in hex_gauss_points():
+        N, dN = hex_shape(xi)
+        detJ = np.linalg.det(np.einsum("eai,ar->eir", Xe, dN))
+        m += rho * detJ[:, None, None] * np.outer(N, N)[None]
+    return m
+
+
+# ================================================= triplets, pattern and C
+
+def triplet_dofs(conn):
+    """(row, col) DOF of every triplet in the fill order
+    t = ((e*npe + a)*npe + b)*9 + 3i + k, value K_e[3a+i, 3b+k]."""
+    conn = np.asarray(conn, dtype=np.int64)
+    E, npe = conn.shape
+    a = np.arange(npe)
+    i = np.arange(3)
+    # shapes [E, a, b, i, k]
+    row = 3 * conn[:, :, None, None, None] + i[None, None, None, :, None]
+    col = 3 * conn[:, None, :, None, None] + i[None, None, None, None, :]
+    row = np.broadcast_to(row, (E, npe, npe, 3, 3)).reshape(-1)
+    col = np.broadcast_to(col, (E, npe, npe, 3, 3)).reshape(-1)
+    del a
+    return row, col
+
+
+def element_values_fill_order(Ke):
+    """K_e [E, 3npe, 3npe] with index (3a+i, 3b+k) -> fill-order values [E*npe*npe*9]."""
+    E, n, _ = Ke.shape
+    npe = n // 3
+    return Ke.reshape(E, npe, 3, npe, 3).transpose(0, 1, 3, 2, 4).reshape(-1)
+
+
+def csr_pattern(n_dof, conn, fixed_dofs):
+    """CSR pattern of the projected matrix and the map C (triplet -> slot, or -1).
+
+    Rows and columns ascending, duplicates merged, fixed rows hold only their
+    diagonal, fixed columns are removed (Section 5.1); C[t] = -1 whenever the
+    triplet's row or column DOF is fixed.  Built by sorting unique keys."""
+    row, col = triplet_dofs(conn)
+    fixed = np.zeros(n_dof, dtype=bool)
+    fixed[np.asarray(fixed_dofs, dtype=np.int64)] = True
+    keep = ~(fixed[row] | fixed[col])
+    keys = row[keep] * n_dof + col[keep]
+    fd = np.nonzero(fixed)[0].astype(np.int64)
+    uniq = np.unique(np.concatenate([keys, fd * n_dof + fd]))
+    r = uniq // n_dof
+    colind = (uniq % n_dof).astype(np.int32)
+    rowptr = np.zeros(n_dof + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    rowptr = np.cumsum(rowptr).astype(np.int32)
+    C = np.full(row.shape[0], -1, dtype=np.int64)
+    C[keep] = np.searchsorted(uniq, keys)
+    return rowptr, colind, C.astype(np.int32)
+
+
+def assemble(n_dof, conn, values_fill_order):
+    """Unconstrained global matrix: plain sum of every triplet (COO -> CSR)."""
+    row, col = triplet_dofs(conn)
+    return sp.coo_matrix((values_fill_order, (row, col)), shape=(n_dof, n_dof)).tocsr()
+
+
+def mass_fill_order(m_scalar):
+    """Mass scalars m[e, a, b] -> fill-order triplet values (block m_ab * I3)."""
+    E, npe, _ = m_scalar.shape
+    blk = m_scalar[:, :, :, None, None] * _I3[None, None, None]
+    return blk.reshape(-1)
+
+
+def project(Afull, fixed_dofs):
+    """Projective constraints: clear fixed rows and columns, 1 on the diagonal."""
+    n = Afull.shape[0]
+    keep = np.ones(n)
+    keep[np.asarray(fixed_dofs, dtype=np.int64)] = 0.0
+    D = sp.diags(keep)
+    fixd = sp.diags(1.0 - keep)
+    return (D @ Afull @ D + fixd).tocsr()
+
+
+def values_in_pattern(Aproj, rowptr, colind):
+    """Values of a sparse matrix read at every slot of a CSR pattern."""
+    n = rowptr.shape[0] - 1
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    return np.asarray(Aproj[rows, colind]).reshape(-1)
+
+
+# ================================================================ the model
+
+class Model:
+    """A mesh + material + time-integration parameters; state-independent data."""
+
+    def __init__(self, elem_type, X, conn, fixed_nodes, model, params, rho, h, alpha, beta):
+        self.elem_type = elem_type
+        self.X = np.asarray(X, dtype=np.float64)
+        self.conn = np.asarray(conn, dtype=np.int64)
+        self.n_dof = 3 * self.X.shape[0]
+        fn = np.asarray(fixed_nodes, dtype=np.int64)
+        self.fixed_dofs = (3 * fn[:, None] + np.arange(3)[None, :]).reshape(-1)
+        self.model = model
+        self.params = np.asarray(params, dtype=np.float64)
+        self.rho, self.h, self.alpha, self.beta = rho, h, alpha, beta
+        self.quad = Quadrature(elem_type, self.X, self.conn)
+        self.m_e = element_mass(elem_type, self.X, self.conn, rho)
+        self.M = assemble(self.n_dof, self.conn, mass_fill_order(self.m_e))
+
+    @classmethod
+    def from_workload(cls, wl, params=None):
+        m = wl.mesh
+        return cls(m.elem_type, m.X, m.conn, m.fixed_nodes, wl.model,
+                   wl.params if params is None else params, wl.rho, wl.h, wl.alpha, wl.beta)
+
+    # -- per element
+    def energy(self, q):
+        return element_energy(self.quad, q.reshape(-1, 3), self.model, self.params).sum()
+
+    def element_force(self, q):
+        return element_force(self.quad, q.reshape(-1, 3), self.model, self.params)
+
+    def element_tangent(self, q):
+        return element_tangent(self.quad, q.reshape(-1, 3), self.model, self.params)
+
+    # -- assembled
+    def internal_force(self, q):
+        fe = self.element_force(q)
+        f = np.zeros(self.n_dof, dtype=fe.dtype)
+        dofs = (3 * self.conn[:, :, None] + np.arange(3)[None, None, :]).reshape(fe.shape[0], -1)
+        np.add.at(f, dofs.reshape(-1), fe.reshape(-1))
+        return f
+
+    def stiffness(self, q):
+        return assemble(self.n_dof, self.conn, element_values_fill_order(self.element_tangent(q)))
+
+    def system(self, q, v, p):
+        """Projected A and b of one step (Eq. "dynamic equation2"; C-1 reading of b)."""
+        h, al, be = self.h, self.alpha, self.beta
+        f = self.internal_force(q)
+        K = self.stiffness(q)
+        A = (1.0 + h * al) * self.M + h * (be + h) * K
+        b = p - f - (al * (self.M @ v) + (be + h) * (K @ v))
+        b[self.fixed_dofs] = 0.0
+        return project(A, self.fixed_dofs), b
+
+    def step(self, q, v, p):
+        """One backward-Euler step with one Newton iteration; direct solve."""
+        A, b = self.system(q, v, p)
+        a = direct_solve(A, b)
+        v1 = v + self.h * a
+        q1 = q + self.h * v1
+        return q1, v1, a
+
+    def pattern(self):
+        return csr_pattern(self.n_dof, self.conn, self.fixed_dofs)
+
+
+def direct_solve(A, b):
+    """Sparse direct solve (SuperLU with a symmetric fill-reducing order)."""
+    if A.shape[0] <= 3000:
+        return np.linalg.solve(A.toarray(), b)
+    lu = spla.splu(A.tocsc(), permc_spec="MMD_AT_PLUS_A")
+    return lu.solve(b)
+
+
+def rollout(model, q0, v0, loads, n_steps):
+    """q_t, v_t for t = 0..n_steps (loads(t) -> p_t as a [n_dof] vector)."""
+    qs, vs = [q0.copy()], [v0.copy()]
+    q, v = q0.copy(), v0.copy()
+    for t in range(n_steps):
+        q, v, _ = model.step(q, v, loads(t))
+        qs.append(q)
+        vs.append(v)
+    return np.array(qs), np.array(vs)
