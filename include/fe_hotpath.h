@@ -1,0 +1,190 @@
+/*
+ * fe_hotpath.h -- C ABI of the GB300 implicit finite-element time step.
+ *
+ * The library implements the hot path of Zeng & Courtecuisse, "Efficient
+ * parallelization strategy for real-time FE simulations" (arXiv 2306.05893):
+ *
+ *   per-element hyperelastic force and tangent (Section 3.1)
+ *   -> fast assembly of A and b through a triplet->CSR map C computed once
+ *      per topology (Section 4, Algorithm 1, Table "build pattern")
+ *   -> preconditioned CG on A a = b with
+ *        A = (1 + h alpha) M + h (beta + h) K          (Eq. "dynamic equation2")
+ *        b = p - f - (alpha M + (beta + h) K) v        (Eq. "dynamic equation1",
+ *                                                       Rayleigh B = alpha M + beta K)
+ *      and a lagged LDL^T preconditioner P = A_t = L D L^T
+ *      (Eq. "asynchronous preconditioner", Section 3.3) applied level by level
+ *      over nested-dissection sub-domains (Section 6.1, Eq. "regional problem")
+ *   -> backward Euler v+ = v + h a, q+ = q + h v+     (Eq. "implicit integration").
+ *
+ * Conventions shared by every call:
+ *   - every call returns an fe_status; none throws or aborts;
+ *   - a message for the last failure of a context is in fe_last_error();
+ *   - after a non-zero status other than FE_ERR_CUDA the context stays usable;
+ *   - DOF numbering: DOF = 3 * node + component, node-major;
+ *   - the caller owns every buffer it passes; fe_create copies all inputs;
+ *   - "host or device" buffers: when fe_options.device_ptrs is 1 the state
+ *     and force pointers of fe_set_state / fe_get_state / fe_step /
+ *     fe_element_eval / fe_assemble are device pointers used on
+ *     fe_options.stream; otherwise they are host pointers and the call copies
+ *     through the library's own pinned staging buffers.
+ */
+#ifndef FE_HOTPATH_H
+#define FE_HOTPATH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fe_ctx fe_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  FE_OK = 0,
+  FE_ERR_ARG = 1,             /* invalid argument (sizes, pointers, ids)       */
+  FE_ERR_CUDA = 2,            /* CUDA runtime error; context must be destroyed */
+  FE_ERR_OOM = 3,             /* device or host allocation failed              */
+  FE_ERR_PATTERN_CHANGED = 4, /* topology differs from the one the map C holds */
+  FE_ERR_NOT_CONVERGED = 5,   /* PCG hit max_iters                             */
+  FE_ERR_BREAKDOWN = 6,       /* p^T A p <= 0 in CG or an LDL^T pivot <= 0     */
+  FE_ERR_INVERTED = 7,        /* an element has det F <= 0                     */
+  FE_ERR_TIMEOUT = 8,         /* the lagged factor was not ready in time       */
+  FE_ERR_STATE = 9            /* calls out of order (e.g. step before pattern) */
+} fe_status;
+
+enum { FE_TET4 = 0, FE_HEX8 = 1 };
+enum { FE_SVK = 0, FE_NEOHOOKE = 1, FE_MOONEY_RIVLIN = 2 };
+enum { FE_FP64 = 0, FE_MIXED = 1 };
+
+/* Mesh (Section 3.1).  Local node order of a hex: a = dx + 2 dy + 4 dz.
+ * rest_xyz [n_nodes * 3] (host), conn [n_elems * npe] (host, npe = 4 or 8),
+ * fixed_nodes [n_fixed] (host): nodes held by projective constraints
+ * (Section 5.1): their rows and columns are cleared with 1 on the diagonal. */
+typedef struct {
+  int32_t elem_type;
+  int64_t n_nodes;
+  int64_t n_elems;
+  const double *rest_xyz;
+  const int32_t *conn;
+  int64_t n_fixed;
+  const int32_t *fixed_nodes;
+} fe_mesh;
+
+/* Material (Section 3.1): params are (mu, lambda, unused) for St Venant-
+ * Kirchhoff and neo-Hookean, (C10, C01, kappa) for Mooney-Rivlin; one triple
+ * for the whole mesh, or one per element when per_element = 1
+ * ([n_elems * 3], element-major).  rho is the mass density. */
+typedef struct {
+  int32_t model;
+  double rho;
+  const double *params;
+  int32_t per_element;
+} fe_material;
+
+typedef struct {
+  int32_t precision;      /* FE_FP64: all FP64.  FE_MIXED: FP32 tangent,
+                             SpMV and triangular solves, FP64 force, residual,
+                             dot products and pivots, iterative refinement. */
+  double tol;             /* stop when ||b - A a||_2 <= tol ||b||_2           */
+  int32_t max_iters;      /* PCG iterations per step (all refinement sweeps)  */
+  int32_t refactor_every; /* R: factor A_s at steps s = 0 mod R; that factor
+                             preconditions steps s+1 .. s+R (step 0 uses A_0)  */
+  int32_t device_ptrs;    /* 1: state/force buffers are device pointers       */
+  void *stream;           /* cudaStream_t for device_ptrs = 1 (NULL: legacy)  */
+  int32_t keep_checkpoints; /* store (q_t, v_t) of every step for fe_adjoint  */
+  int32_t nd_leaf_nodes;  /* nested-dissection leaf size in nodes (0: 64)     */
+  double inner_tol;       /* FE_MIXED inner PCG tolerance per sweep (0: 1e-4) */
+  double factor_timeout_s;/* host deadline for a lagged factor (0: 30 s)      */
+  int32_t use_graph;      /* 1: replay the PCG iteration as a CUDA graph      */
+} fe_options;
+
+typedef struct {
+  int32_t iters;          /* PCG iterations of the step (all sweeps)          */
+  int32_t refinements;    /* outer FP64 residual sweeps (FE_MIXED), else 1    */
+  int32_t factor_age;     /* steps since the preconditioner's matrix          */
+  double rel_residual;    /* final ||b - A a|| / ||b|| (FP64)                 */
+} fe_step_info;
+
+/* Fills *opt with defaults: FP64, tol 1e-8, max_iters 1000, R = 1, host
+ * pointers, no checkpoints. */
+int fe_options_default(fe_options *opt);
+
+/* Copies mesh, material, h, Rayleigh (alpha, beta) and options into a new
+ * context (Section 3.2).  Touches no GPU.  *out is NULL on failure. */
+int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alpha,
+              double beta, const fe_options *opt, fe_ctx **out);
+
+/* Setup once per topology (Section 4.2, Table "build pattern"; Section 5.1;
+ * Section 6.1): the triplet (row, col) stream in fill order
+ *   t = ((e * npe + a) * npe + b) * 9 + 3 i + k   (value K_e[3a+i][3b+k]),
+ * the CSR pattern by two transposes with fixed rows/columns skipped, the map C
+ * (triplet -> CSR slot, -1 when dropped) and its inverse (per slot, its
+ * triplets ascending), the consistent mass on that pattern, a nested-
+ * dissection ordering of the free nodes, the multifrontal symbolic analysis
+ * and the level schedule.  Host work only; device buffers are created at the
+ * first call that needs the GPU.  Must precede every call below. */
+int fe_build_pattern(fe_ctx *ctx);
+
+/* Borrowed host views of the setup products, valid until fe_destroy:
+ * rowptr [n+1], colind [nnz], scatter = C [ntrip]. */
+int fe_get_pattern(fe_ctx *ctx, int64_t *n, int64_t *nnz, const int32_t **rowptr,
+                   const int32_t **colind, int64_t *ntrip, const int32_t **scatter);
+
+/* Inverse of C: slot s gathers triplets slot_src[slot_ptr[s] .. slot_ptr[s+1])
+ * (ascending).  Borrowed host views. */
+int fe_get_inverse_map(fe_ctx *ctx, const int64_t **slot_ptr, const int32_t **slot_src);
+
+/* Consistent-mass values on the CSR pattern (host, [nnz], fixed rows 0). */
+int fe_get_mass(fe_ctx *ctx, const double **mass_vals);
+
+/* Nested-dissection result (Section 6.1): perm [n_free_dofs] lists the
+ * original DOF of each new position; fronts: n_fronts, and per front its
+ * first pivot (new numbering), pivot count, update-row count, parent (-1 for
+ * a root) and level (0 = leaves).  Borrowed host views. */
+int fe_get_ordering(fe_ctx *ctx, int64_t *n_free, const int32_t **perm, int64_t *n_fronts,
+                    const int32_t **front_first, const int32_t **front_npiv,
+                    const int32_t **front_nupd, const int32_t **front_parent,
+                    const int32_t **front_level);
+
+/* Update rows (original DOF numbers, ascending in the new order) of a front. */
+int fe_get_front_rows(fe_ctx *ctx, int64_t front, int64_t *n_upd, const int32_t **rows);
+
+/* Sets the state (positions q and velocities v, [n] each; NULL keeps the
+ * current value).  Default state: q = rest positions, v = 0.  v must vanish
+ * on fixed DOFs (FE_ERR_ARG otherwise). */
+int fe_set_state(fe_ctx *ctx, const double *q, const double *v);
+int fe_get_state(fe_ctx *ctx, double *q, double *v);
+
+/* Element kernel alone at positions q ([n], NULL: current state):
+ * f_e [n_elems * 3npe] and K_e [n_elems * (3npe)^2] in fill order (FP64
+ * outputs; FP32 tangents are widened).  Either output may be NULL. */
+int fe_element_eval(fe_ctx *ctx, const double *q, double *f_e, double *K_e);
+
+/* Element kernel + fast assembly at the current state with external force
+ * p_ext [n] (NULL = 0): A_vals [nnz] on the CSR pattern and b [n]
+ * (Eq. "dynamic equation2"; fixed rows: A_ii = 1, b_i = 0).  Either output
+ * may be NULL. */
+int fe_assemble(fe_ctx *ctx, const double *p_ext, double *A_vals, double *b);
+
+/* Numeric LDL^T of the current A (Eq. "asynchronous preconditioner") on the
+ * factor stream, and one application z = P^{-1} r ([n] each, FP64 in/out).
+ * For tests of the factor and of the level-scheduled solves. */
+int fe_factor_now(fe_ctx *ctx);
+int fe_apply_preconditioner(fe_ctx *ctx, const double *r, double *z);
+
+/* One implicit step with external nodal forces p_ext [n] (NULL = 0), one
+ * Newton iteration (Eq. "taylor expansion").  Writes the new q, v when the
+ * pointers are non-NULL; info may be NULL. */
+int fe_step(fe_ctx *ctx, const double *p_ext, double *q_out, double *v_out,
+            fe_step_info *info);
+
+/* Message of the last failure on ctx ("" if none). */
+const char *fe_last_error(const fe_ctx *ctx);
+
+/* Frees every host and device resource of ctx (NULL is a no-op). */
+void fe_destroy(fe_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_HOTPATH_H */

@@ -1,0 +1,262 @@
+"""Python binding of the GB300 implicit-FE library (argument marshalling only).
+
+Every numerical step runs in the CUDA library ``_build/libfe_hotpath.so``
+(built by ``build.build()``); this module only converts numpy arrays / torch
+tensors to pointers and status codes to exceptions.  There is no CPU path:
+calls fail with ``FEError`` when the library or a GPU is missing.
+
+The functions keep the C names (``fe_create``, ``fe_build_pattern``,
+``fe_step`` ...); ``FEContext`` bundles them with the handle's lifetime.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import _abi
+from ._abi import (FE_FP64, FE_HEX8, FE_MIXED, FE_MOONEY_RIVLIN, FE_NEOHOOKE,  # noqa: F401
+                   FE_SVK, FE_TET4, FeOptions, FeStepInfo)
+
+_LIB = None
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+class FEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_abi.STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib_path():
+    return os.environ.get("FE_HOTPATH_LIB") or os.path.join(_HERE, "_build", "libfe_hotpath.so")
+
+
+def load(path=None):
+    """Load (once) and return the CUDA library; raises if it is not built."""
+    global _LIB
+    if _LIB is None:
+        p = path or lib_path()
+        if not os.path.exists(p):
+            raise FEError(-1, f"CUDA library not built ({p}); call paper_2306_05893_gb300.build.build()")
+        _LIB = _abi.bind(ct.CDLL(p))
+    return _LIB
+
+
+def _check(ctx, status):
+    if status != 0:
+        msg = _LIB.fe_last_error(ctx) if ctx else b""
+        raise FEError(status, (msg or b"").decode())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    """Pointer of a numpy array (host) or a torch tensor (device or host)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ct.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ct.c_void_p)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def options(**kw) -> FeOptions:
+    load()
+    o = FeOptions()
+    _LIB.fe_options_default(ct.byref(o))
+    for k, v in kw.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = v.cuda_stream if hasattr(v, "cuda_stream") else int(v)
+        setattr(o, k, v)
+    return o
+
+
+# ------------------------------------------------------------ C-named calls
+
+def fe_create(elem_type, X, conn, fixed_nodes, model, rho, params, h, alpha, beta, opts=None):
+    lib = load()
+    X = _f64(X).reshape(-1, 3)
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    fixed = np.ascontiguousarray(fixed_nodes, dtype=np.int32).reshape(-1)
+    params = _f64(params)
+    per_elem = 1 if params.ndim == 2 else 0
+    mesh = _abi.FeMesh(elem_type, X.shape[0], conn.shape[0], _dptr(X),
+                       conn.ctypes.data_as(ct.POINTER(ct.c_int32)), fixed.size,
+                       fixed.ctypes.data_as(ct.POINTER(ct.c_int32)))
+    mat = _abi.FeMaterial(model, float(rho), _dptr(params), per_elem)
+    opts = opts if opts is not None else options()
+    h_ctx = ct.c_void_p()
+    st = lib.fe_create(ct.byref(mesh), ct.byref(mat), float(h), float(alpha), float(beta),
+                       ct.byref(opts), ct.byref(h_ctx))
+    if st != 0:
+        raise FEError(st, "fe_create rejected its arguments")
+    return h_ctx
+
+
+def fe_build_pattern(ctx):
+    _check(ctx, load().fe_build_pattern(ctx))
+
+
+def fe_get_pattern(ctx):
+    n, nnz, nt = ct.c_int64(), ct.c_int64(), ct.c_int64()
+    rp, ci, sc = (ct.POINTER(ct.c_int32)() for _ in range(3))
+    _check(ctx, load().fe_get_pattern(ctx, ct.byref(n), ct.byref(nnz), ct.byref(rp), ct.byref(ci),
+                                      ct.byref(nt), ct.byref(sc)))
+    return (np.ctypeslib.as_array(rp, (n.value + 1,)).copy(),
+            np.ctypeslib.as_array(ci, (nnz.value,)).copy(),
+            np.ctypeslib.as_array(sc, (nt.value,)).copy())
+
+
+def fe_get_inverse_map(ctx, nnz):
+    sp_, ss = ct.POINTER(ct.c_int64)(), ct.POINTER(ct.c_int32)()
+    _check(ctx, load().fe_get_inverse_map(ctx, ct.byref(sp_), ct.byref(ss)))
+    slot_ptr = np.ctypeslib.as_array(sp_, (nnz + 1,)).copy()
+    return slot_ptr, np.ctypeslib.as_array(ss, (int(slot_ptr[-1]),)).copy()
+
+
+def fe_get_mass(ctx, nnz):
+    mp = ct.POINTER(ct.c_double)()
+    _check(ctx, load().fe_get_mass(ctx, ct.byref(mp)))
+    return np.ctypeslib.as_array(mp, (nnz,)).copy()
+
+
+def fe_get_ordering(ctx):
+    nf, nfr = ct.c_int64(), ct.c_int64()
+    ptrs = [ct.POINTER(ct.c_int32)() for _ in range(6)]
+    _check(ctx, load().fe_get_ordering(ctx, ct.byref(nf), ct.byref(ptrs[0]), ct.byref(nfr),
+                                       *[ct.byref(p) for p in ptrs[1:]]))
+    perm = np.ctypeslib.as_array(ptrs[0], (nf.value,)).copy() if nf.value else np.zeros(0, np.int32)
+    fr = [np.ctypeslib.as_array(p, (nfr.value,)).copy() for p in ptrs[1:]]
+    return dict(perm=perm, first=fr[0], npiv=fr[1], nupd=fr[2], parent=fr[3], level=fr[4])
+
+
+def fe_get_front_rows(ctx, f):
+    nu = ct.c_int64()
+    rp = ct.POINTER(ct.c_int32)()
+    _check(ctx, load().fe_get_front_rows(ctx, int(f), ct.byref(nu), ct.byref(rp)))
+    return np.ctypeslib.as_array(rp, (nu.value,)).copy() if nu.value else np.zeros(0, np.int32)
+
+
+def fe_set_state(ctx, q=None, v=None):
+    _check(ctx, load().fe_set_state(ctx, _ptr(q), _ptr(v)))
+
+
+def fe_get_state(ctx, q=None, v=None):
+    _check(ctx, load().fe_get_state(ctx, _ptr(q), _ptr(v)))
+
+
+def fe_element_eval(ctx, q=None, f_e=None, K_e=None):
+    _check(ctx, load().fe_element_eval(ctx, _ptr(q), _ptr(f_e), _ptr(K_e)))
+
+
+def fe_assemble(ctx, p_ext=None, A_vals=None, b=None):
+    _check(ctx, load().fe_assemble(ctx, _ptr(p_ext), _ptr(A_vals), _ptr(b)))
+
+
+def fe_factor_now(ctx):
+    _check(ctx, load().fe_factor_now(ctx))
+
+
+def fe_apply_preconditioner(ctx, r, z):
+    _check(ctx, load().fe_apply_preconditioner(ctx, _ptr(r), _ptr(z)))
+
+
+def fe_step(ctx, p_ext=None, q_out=None, v_out=None):
+    info = FeStepInfo()
+    st = load().fe_step(ctx, _ptr(p_ext), _ptr(q_out), _ptr(v_out), ct.byref(info))
+    _check(ctx, st)
+    return info
+
+
+def fe_destroy(ctx):
+    if ctx:
+        load().fe_destroy(ctx)
+
+
+# ---------------------------------------------------------------- wrapper
+
+class FEContext:
+    """Owns one fe_ctx.  Host numpy arrays or (device_ptrs=1) CUDA tensors."""
+
+    def __init__(self, elem_type, X, conn, fixed_nodes, model, rho, params, h, alpha, beta,
+                 build=True, **opts):
+        self.n = 3 * np.asarray(X).reshape(-1, 3).shape[0]
+        self.n_elems = np.asarray(conn).shape[0]
+        self.npe = np.asarray(conn).shape[1]
+        self.opts = options(**opts)
+        self.ctx = fe_create(elem_type, X, conn, fixed_nodes, model, rho, params, h, alpha, beta,
+                             self.opts)
+        if build:
+            fe_build_pattern(self.ctx)
+            self.rowptr, self.colind, self.C = fe_get_pattern(self.ctx)
+            self.nnz = self.colind.size
+
+    @classmethod
+    def from_workload(cls, wl, params=None, **opts):
+        m = wl.mesh
+        kw = dict(precision=wl.precision, tol=wl.tol, refactor_every=wl.refactor_every)
+        kw.update(opts)
+        return cls(m.elem_type, m.X, m.conn, m.fixed_nodes, wl.model, wl.rho,
+                   wl.params if params is None else params, wl.h, wl.alpha, wl.beta, **kw)
+
+    def close(self):
+        if self.ctx:
+            fe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # convenience host-side helpers (copies)
+    def inverse_map(self):
+        return fe_get_inverse_map(self.ctx, self.nnz)
+
+    def mass(self):
+        return fe_get_mass(self.ctx, self.nnz)
+
+    def ordering(self):
+        return fe_get_ordering(self.ctx)
+
+    def set_state(self, q=None, v=None):
+        fe_set_state(self.ctx, q, v)
+
+    def get_state(self):
+        q = np.empty(self.n)
+        v = np.empty(self.n)
+        fe_get_state(self.ctx, q, v)
+        return q, v
+
+    def element_eval(self, q=None):
+        m = 3 * self.npe
+        f = np.empty(self.n_elems * m)
+        K = np.empty(self.n_elems * m * m)
+        fe_element_eval(self.ctx, None if q is None else _f64(q), f, K)
+        return f.reshape(self.n_elems, m), K
+
+    def assemble(self, p=None):
+        A = np.empty(self.nnz)
+        b = np.empty(self.n)
+        fe_assemble(self.ctx, None if p is None else _f64(p), A, b)
+        return A, b
+
+    def factor_now(self):
+        fe_factor_now(self.ctx)
+
+    def apply_preconditioner(self, r):
+        z = np.empty(self.n)
+        fe_apply_preconditioner(self.ctx, _f64(r), z)
+        return z
+
+    def step(self, p=None, q_out=None, v_out=None):
+        p_arg = p if (p is None or hasattr(p, "data_ptr")) else _f64(p)
+        return fe_step(self.ctx, p_arg, q_out, v_out)

@@ -1,0 +1,514 @@
+// C-ABI entry points that use the GPU: device state, one implicit step
+// (element kernel -> gather assembly -> [lagged factor on the side stream]
+// -> PCG with the level-scheduled LDL^T preconditioner -> backward Euler),
+// and the stage-level calls used by the parity tests.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <thread>
+
+#include "fe_device.cuh"
+
+namespace fe {
+
+namespace {
+
+bool mixed(const fe_ctx *c) { return c->opt.precision == FE_MIXED; }
+size_t vsz(const fe_ctx *c) { return mixed(c) ? sizeof(float) : sizeof(double); }
+
+template <typename T>
+int dalloc(fe_ctx *c, DeviceState *d, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(c, FE_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  d->allocs.push_back(*p);
+  d->bytes_total += count * sizeof(T);
+  return FE_OK;
+}
+
+int dallocv(fe_ctx *c, DeviceState *d, void **p, size_t bytes) {
+  return dalloc(c, d, reinterpret_cast<unsigned char **>(p), bytes);
+}
+
+template <typename T>
+int upload(fe_ctx *c, DeviceState *d, T **p, const std::vector<T> &h) {
+  int st = dalloc(c, d, p, h.size());
+  if (st) return st;
+  if (!h.empty()) FE_CUDA_TRY(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FE_OK;
+}
+
+#define FE_TRY(x)      \
+  do {                 \
+    int s_ = (x);      \
+    if (s_) return s_; \
+  } while (0)
+
+int ensure_device(fe_ctx *c) {
+  if (!c->built) return set_error(c, FE_ERR_STATE, "fe_build_pattern has not run");
+  if (c->dev) return FE_OK;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return set_error(c, FE_ERR_CUDA, "no CUDA device available");
+  }
+  DeviceState *d = new DeviceState();
+  c->dev = d;
+  FE_CUDA_TRY(cudaGetDevice(&d->device));
+  if (c->opt.device_ptrs && c->opt.stream) {
+    d->stream = reinterpret_cast<cudaStream_t>(c->opt.stream);
+  } else {
+    FE_CUDA_TRY(cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking));
+    d->own_stream = true;
+  }
+  FE_CUDA_TRY(cudaStreamCreateWithFlags(&d->fstream, cudaStreamNonBlocking));
+  FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_assembled, cudaEventDisableTiming));
+  FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_factored, cudaEventDisableTiming));
+  FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_apply_done, cudaEventDisableTiming));
+
+  const int64_t n = c->n, E = c->n_elems, nf = int64_t(c->fronts.size());
+  const int npe = c->npe, ke = 9 * npe * npe;
+  const bool fp32 = mixed(c);
+  const size_t ts = fp32 ? 4 : 8;
+  // mesh / setup products
+  FE_TRY(upload(c, d, &d->conn, c->conn));
+  FE_TRY(upload(c, d, &d->rest, c->rest));
+  {
+    std::vector<double> pt(3 * E);
+    for (int64_t e = 0; e < E; ++e)
+      for (int k = 0; k < 3; ++k) pt[k * E + e] = c->params[3 * e + k];
+    FE_TRY(upload(c, d, &d->params, pt));
+  }
+  FE_TRY(upload(c, d, &d->X, c->X));
+  FE_TRY(upload(c, d, &d->rowptr, c->rowptr));
+  FE_TRY(upload(c, d, &d->colind, c->colind));
+  {
+    std::vector<int32_t> sp(c->slot_ptr.size());
+    for (size_t i = 0; i < sp.size(); ++i) sp[i] = int32_t(c->slot_ptr[i]);
+    FE_TRY(upload(c, d, &d->slot_ptr, sp));
+  }
+  FE_TRY(upload(c, d, &d->slot_src, c->slot_src));
+  FE_TRY(upload(c, d, &d->mass, c->mass));
+  FE_TRY(upload(c, d, &d->fixed_row, c->fixed_dof));
+  FE_TRY(upload(c, d, &d->node_ptr, c->node_ptr));
+  FE_TRY(upload(c, d, &d->node_src, c->node_src));
+  // state
+  FE_TRY(upload(c, d, &d->q, c->X));
+  FE_TRY(dalloc(c, d, &d->v, n));
+  FE_CUDA_TRY(cudaMemset(d->v, 0, n * sizeof(double)));
+  FE_TRY(dalloc(c, d, &d->pext, n));
+  FE_TRY(dalloc(c, d, &d->acc, n));
+  FE_TRY(dalloc(c, d, &d->x, n));
+  FE_TRY(dalloc(c, d, &d->r, n));
+  FE_TRY(dalloc(c, d, &d->b, n));
+  FE_TRY(dallocv(c, d, &d->fe, size_t(E) * 3 * npe * ts));
+  FE_TRY(dallocv(c, d, &d->Ke, size_t(E) * ke * ts));
+  FE_TRY(dallocv(c, d, &d->A, size_t(c->nnz) * ts));
+  FE_TRY(dallocv(c, d, &d->Afac, size_t(c->nnz) * ts));
+  FE_TRY(dallocv(c, d, &d->vz, n * ts));
+  FE_TRY(dallocv(c, d, &d->vp, n * ts));
+  FE_TRY(dallocv(c, d, &d->vq, n * ts));
+  FE_TRY(dallocv(c, d, &d->vr, n * ts));
+  FE_TRY(dallocv(c, d, &d->vd, n * ts));
+  FE_CUDA_TRY(cudaMemset(d->vz, 0, n * ts));  // fixed DOFs of z stay 0 forever
+  FE_TRY(dallocv(c, d, reinterpret_cast<void **>(&d->scal), S_COUNT * sizeof(double) + 4 * sizeof(int)));
+  d->flags = reinterpret_cast<int *>(d->scal + S_COUNT);
+  FE_CUDA_TRY(cudaMemset(d->scal, 0, S_COUNT * sizeof(double) + 4 * sizeof(int)));
+  FE_TRY(dalloc(c, d, &d->partials, kMaxBlocks));
+  FE_TRY(dalloc(c, d, &d->ticket, 4));
+  FE_CUDA_TRY(cudaMemset(d->ticket, 0, 4 * sizeof(unsigned int)));
+  FE_CUDA_TRY(cudaMallocHost(&d->h_scal, S_COUNT * sizeof(double) + 4 * sizeof(int)));
+  d->h_flags = reinterpret_cast<int *>(d->h_scal + S_COUNT);
+  FE_CUDA_TRY(cudaMallocHost(&d->stage_in, n * sizeof(double)));
+  FE_CUDA_TRY(cudaMallocHost(&d->stage_out, 2 * n * sizeof(double)));
+
+  // multifrontal factor
+  std::vector<DFront> df(nf);
+  int64_t fac = 0;
+  for (int64_t f = 0; f < nf; ++f) {
+    const Front &F = c->fronts[f];
+    DFront &o = df[f];
+    o.first = F.first; o.npiv = F.npiv; o.nupd = F.nupd; o.m = F.m();
+    o.child_begin = c->child_ptr[f]; o.child_end = c->child_ptr[f + 1];
+    o.f_off = F.f_off; o.y_off = F.y_off; o.w_off = F.w_off; o.u_off = F.u_off;
+    o.rows_off = F.rows_off; o.fac_off = fac;
+    fac += F.npiv + 1;
+  }
+  FE_TRY(upload(c, d, &d->fronts, df));
+  FE_TRY(upload(c, d, &d->perm, c->perm));
+  FE_TRY(upload(c, d, &d->upd_rows_old, c->upd_rows_old));
+  FE_TRY(upload(c, d, &d->rmap, c->rmap));
+  FE_TRY(upload(c, d, &d->child_list, c->child_list));
+  FE_TRY(upload(c, d, &d->fa_slot, c->fa_slot));
+  FE_TRY(upload(c, d, &d->fa_off, c->fa_off));
+  FE_TRY(upload(c, d, &d->fa_colptr, c->fa_colptr));
+  // task lists, int4-aligned
+  std::vector<int32_t> all;
+  std::vector<int32_t> lf;
+  auto pad4 = [&]() { while (all.size() % 4) all.push_back(0); };
+  d->lt.assign(c->levels.size(), DeviceState::LevelTasks());
+  for (size_t lv = 0; lv < c->levels.size(); ++lv) {
+    const Level &L = c->levels[lv];
+    auto &T = d->lt[lv];
+    T.nfronts = int64_t(L.fronts.size());
+    T.fronts_off = int64_t(lf.size());
+    lf.insert(lf.end(), L.fronts.begin(), L.fronts.end());
+    pad4();
+    T.asm_off = int64_t(all.size()); T.asm_n = int64_t(L.asm_tasks.size() / 3);
+    all.insert(all.end(), L.asm_tasks.begin(), L.asm_tasks.end());
+    for (int s = 0; s < L.steps; ++s) {
+      pad4();
+      T.diag_off.push_back(int64_t(all.size())); T.diag_n.push_back(int64_t(L.diag[s].size() / 4));
+      all.insert(all.end(), L.diag[s].begin(), L.diag[s].end());
+      T.panel_off.push_back(int64_t(all.size())); T.panel_n.push_back(int64_t(L.panel[s].size() / 4));
+      all.insert(all.end(), L.panel[s].begin(), L.panel[s].end());
+      T.trail_off.push_back(int64_t(all.size())); T.trail_n.push_back(int64_t(L.trail[s].size() / 4));
+      all.insert(all.end(), L.trail[s].begin(), L.trail[s].end());
+    }
+    pad4();
+    T.fwd_off = int64_t(all.size()); T.fwd_n = int64_t(L.fwd_tasks.size() / 2);
+    all.insert(all.end(), L.fwd_tasks.begin(), L.fwd_tasks.end());
+    T.bwd_off = int64_t(all.size()); T.bwd_n = int64_t(L.bwd_tasks.size() / 2);
+    all.insert(all.end(), L.bwd_tasks.begin(), L.bwd_tasks.end());
+  }
+  FE_TRY(upload(c, d, &d->tasks, all));
+  FE_TRY(upload(c, d, &d->level_fronts, lf));
+  FE_TRY(dallocv(c, d, &d->F, size_t(c->f_total) * ts));
+  for (int k = 0; k < 2; ++k) {
+    FE_TRY(dallocv(c, d, &d->Y[k], size_t(c->y_total) * ts));
+    FE_TRY(dalloc(c, d, &d->D[k], size_t(2 * std::max<int64_t>(c->n_free, 1))));
+  }
+  FE_TRY(dallocv(c, d, &d->wbuf, size_t(c->w_total) * ts));
+  FE_TRY(dallocv(c, d, &d->ubuf, size_t(std::max<int64_t>(c->u_total, 1)) * ts));
+  FE_TRY(dallocv(c, d, &d->yperm, size_t(std::max<int64_t>(c->n_free, 1)) * ts));
+  FE_CUDA_TRY(cudaDeviceSynchronize());
+  return FE_OK;
+}
+
+// host or device pointer in -> device buffer (stream-ordered)
+int stage_in(fe_ctx *c, double *dst, const double *src, int64_t n) {
+  DeviceState *d = c->dev;
+  if (c->opt.device_ptrs) {
+    FE_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, d->stream));
+  } else {
+    std::memcpy(d->stage_in, src, n * sizeof(double));
+    FE_CUDA_TRY(cudaMemcpyAsync(dst, d->stage_in, n * sizeof(double), cudaMemcpyHostToDevice, d->stream));
+    FE_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  }
+  return FE_OK;
+}
+
+int stage_out(fe_ctx *c, double *dst, const double *src, int64_t n, int slot) {
+  DeviceState *d = c->dev;
+  if (c->opt.device_ptrs) {
+    FE_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, d->stream));
+  } else {
+    double *h = d->stage_out + slot * c->n;
+    FE_CUDA_TRY(cudaMemcpyAsync(h, src, n * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+    FE_CUDA_TRY(cudaStreamSynchronize(d->stream));
+    std::memcpy(dst, h, n * sizeof(double));
+  }
+  return FE_OK;
+}
+
+int read_scalars(fe_ctx *c) {
+  DeviceState *d = c->dev;
+  FE_CUDA_TRY(cudaMemcpyAsync(d->h_scal, d->scal, S_COUNT * sizeof(double) + 4 * sizeof(int),
+                              cudaMemcpyDeviceToHost, d->stream));
+  FE_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return FE_OK;
+}
+
+int flag_status(fe_ctx *c) {
+  const int f = c->dev->h_flags[0];
+  if (f & FLAG_INVERTED) return set_error(c, FE_ERR_INVERTED, "an element has det F <= 0");
+  if (f & FLAG_PIVOT) return set_error(c, FE_ERR_BREAKDOWN, "LDL^T pivot <= 0");
+  if (f & FLAG_BREAKDOWN) return set_error(c, FE_ERR_BREAKDOWN, "CG breakdown (p^T A p <= 0 or r^T z <= 0)");
+  return FE_OK;
+}
+
+int clear_flags(fe_ctx *c) {
+  FE_CUDA_TRY(cudaMemsetAsync(c->dev->flags, 0, 4 * sizeof(int), c->dev->stream));
+  return FE_OK;
+}
+
+// Wait (host deadline) until the factor launched on the side stream is done.
+int wait_factor(fe_ctx *c) {
+  DeviceState *d = c->dev;
+  if (d->factor_pending < 0) return FE_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(d->ev_factored);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return set_error(c, FE_ERR_CUDA, std::string("factor: ") + cudaGetErrorString(e));
+    double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > c->opt.factor_timeout_s) return set_error(c, FE_ERR_TIMEOUT, "lagged factor not ready before the deadline");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  FE_CUDA_TRY(cudaStreamWaitEvent(d->stream, d->ev_factored, 0));
+  d->cur = d->factor_pending;
+  d->cur_step = d->pending_step;
+  d->factor_pending = -1;
+  d->have_factor = true;
+  return FE_OK;
+}
+
+// Snapshot A (main stream) and factor it on the side stream into the free buffer.
+int launch_factor(fe_ctx *c, int64_t step_tag) {
+  DeviceState *d = c->dev;
+  const bool fp32 = mixed(c);
+  const int buf = d->have_factor ? 1 - d->cur : d->cur;
+  FE_CUDA_TRY(cudaMemcpyAsync(d->Afac, d->A, size_t(c->nnz) * vsz(c), cudaMemcpyDeviceToDevice, d->stream));
+  FE_CUDA_TRY(cudaEventRecord(d->ev_assembled, d->stream));
+  FE_CUDA_TRY(cudaStreamWaitEvent(d->fstream, d->ev_assembled, 0));
+  factor_enqueue(c, d, buf, fp32, d->Afac, d->fstream);
+  FE_CUDA_TRY(cudaGetLastError());
+  FE_CUDA_TRY(cudaEventRecord(d->ev_factored, d->fstream));
+  d->factor_pending = buf;
+  d->pending_step = step_tag;
+  return FE_OK;
+}
+
+// PCG on (X, R) with the current factor; X = 0 and R = rhs were set by
+// init_solve.  Iterations accumulate in S_ITERS.
+int pcg(fe_ctx *c, bool fp32, void *X, void *R) {
+  DeviceState *d = c->dev;
+  cudaStream_t s = d->stream;
+  apply_enqueue(c, d, d->cur, fp32, R, d->vz, s);
+  launch_dot_rz(c, d, fp32, R, d->vz, true, s);
+  launch_update_p(c, d, fp32, d->vz, d->vp, true, s);
+  for (;;) {
+    launch_spmv_dot(c, d, fp32, d->vp, d->vq, s);
+    launch_axpy_norm(c, d, fp32, X, R, d->vp, d->vq, s);
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_TRY(read_scalars(c));
+    FE_TRY(flag_status(c));
+    if (d->h_scal[S_DONE] != 0.0) break;
+    if (d->h_scal[S_ITERS] >= c->opt.max_iters)
+      return set_error(c, FE_ERR_NOT_CONVERGED, "PCG reached max_iters");
+    apply_enqueue(c, d, d->cur, fp32, R, d->vz, s);
+    launch_dot_rz(c, d, fp32, R, d->vz, false, s);
+    launch_update_p(c, d, fp32, d->vz, d->vp, false, s);
+  }
+  return FE_OK;
+}
+
+// Solve A a = b into d->x (FP64): plain PCG, or FP64 residual refinement
+// around an FP32 inner PCG.
+int solve(fe_ctx *c, fe_step_info *info) {
+  DeviceState *d = c->dev;
+  cudaStream_t s = d->stream;
+  const bool fp32 = mixed(c);
+  int sweeps = 0;
+  if (!fp32) {
+    launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s);
+    FE_TRY(read_scalars(c));
+    if (d->h_scal[S_DONE] == 0.0) FE_TRY(pcg(c, false, d->x, d->r));
+    sweeps = 1;
+    if (info) info->rel_residual = d->h_scal[S_BB] > 0 ? std::sqrt(d->h_scal[S_RR] / d->h_scal[S_BB]) : 0.0;
+  } else {
+    launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s);  // x = 0, r = b (FP64)
+    for (;;) {
+      if (sweeps > 0) launch_residual(c, d, true, s);
+      FE_TRY(read_scalars(c));
+      FE_TRY(flag_status(c));
+      if (d->h_scal[S_ODONE] != 0.0) break;
+      if (d->h_scal[S_ITERS] >= c->opt.max_iters)
+        return set_error(c, FE_ERR_NOT_CONVERGED, "refinement reached max_iters");
+      launch_init_solve(c, d, true, d->vd, d->vr, d->r, c->opt.inner_tol, false, s);
+      FE_TRY(pcg(c, true, d->vd, d->vr));
+      launch_refine_update(c, d, s);
+      ++sweeps;
+    }
+    if (info) info->rel_residual = d->h_scal[S_BB] > 0 ? std::sqrt(d->h_scal[S_ORR] / d->h_scal[S_BB]) : 0.0;
+  }
+  if (info) {
+    info->iters = int32_t(d->h_scal[S_ITERS]);
+    info->refinements = sweeps;
+  }
+  return FE_OK;
+}
+
+}  // namespace
+
+void destroy_device(fe_ctx *c) {
+  DeviceState *d = c->dev;
+  if (!d) return;
+  cudaDeviceSynchronize();
+  for (void *p : d->allocs) cudaFree(p);
+  if (d->h_scal) cudaFreeHost(d->h_scal);
+  if (d->stage_in) cudaFreeHost(d->stage_in);
+  if (d->stage_out) cudaFreeHost(d->stage_out);
+  if (d->stage_big) cudaFreeHost(d->stage_big);
+  if (d->ev_assembled) cudaEventDestroy(d->ev_assembled);
+  if (d->ev_factored) cudaEventDestroy(d->ev_factored);
+  if (d->ev_apply_done) cudaEventDestroy(d->ev_apply_done);
+  if (d->fstream) cudaStreamDestroy(d->fstream);
+  if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
+  cudaGetLastError();
+  delete d;
+  c->dev = nullptr;
+}
+
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" {
+
+int fe_set_state(fe_ctx *c, const double *q, const double *v) {
+  if (!c) return FE_ERR_ARG;
+  FE_TRY(ensure_device(c));
+  if (v && !c->opt.device_ptrs)
+    for (int64_t i = 0; i < c->n; ++i)
+      if (c->fixed_dof[i] && v[i] != 0.0) return set_error(c, FE_ERR_ARG, "v must vanish on fixed DOFs");
+  if (q) FE_TRY(stage_in(c, c->dev->q, q, c->n));
+  if (v) FE_TRY(stage_in(c, c->dev->v, v, c->n));
+  FE_CUDA_TRY(cudaStreamSynchronize(c->dev->stream));
+  return FE_OK;
+}
+
+int fe_get_state(fe_ctx *c, double *q, double *v) {
+  if (!c) return FE_ERR_ARG;
+  FE_TRY(ensure_device(c));
+  if (q) FE_TRY(stage_out(c, q, c->dev->q, c->n, 0));
+  if (v) FE_TRY(stage_out(c, v, c->dev->v, c->n, 1));
+  FE_CUDA_TRY(cudaStreamSynchronize(c->dev->stream));
+  return FE_OK;
+}
+
+int fe_element_eval(fe_ctx *c, const double *q, double *f_e, double *K_e) {
+  if (!c) return FE_ERR_ARG;
+  FE_TRY(ensure_device(c));
+  DeviceState *d = c->dev;
+  const double *qd = d->q;
+  if (q) {
+    FE_TRY(stage_in(c, d->x, q, c->n));
+    qd = d->x;
+  }
+  FE_TRY(clear_flags(c));
+  launch_element(c, d, qd, mixed(c), d->stream);
+  FE_CUDA_TRY(cudaGetLastError());
+  const int64_t nf = c->n_elems * 3 * c->npe, nk = c->n_elems * 9 * c->npe * c->npe;
+  double *tmp = nullptr;
+  FE_CUDA_TRY(cudaMalloc(&tmp, std::max(nf, nk) * sizeof(double)));
+  auto out = [&](double *dst, const void *src, int64_t cnt) -> int {
+    launch_convert(src, mixed(c), tmp, false, cnt, d->stream);
+    FE_CUDA_TRY(cudaMemcpyAsync(dst, tmp, cnt * sizeof(double),
+                                c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d->stream));
+    FE_CUDA_TRY(cudaStreamSynchronize(d->stream));
+    return FE_OK;
+  };
+  int st = FE_OK;
+  if (f_e) st = out(f_e, d->fe, nf);
+  if (!st && K_e) st = out(K_e, d->Ke, nk);
+  cudaFree(tmp);
+  if (st) return st;
+  FE_TRY(read_scalars(c));
+  return flag_status(c);
+}
+
+int fe_assemble(fe_ctx *c, const double *p_ext, double *A_vals, double *b) {
+  if (!c) return FE_ERR_ARG;
+  FE_TRY(ensure_device(c));
+  DeviceState *d = c->dev;
+  const double *pd = nullptr;
+  if (p_ext) {
+    FE_TRY(stage_in(c, d->pext, p_ext, c->n));
+    pd = d->pext;
+  }
+  FE_TRY(clear_flags(c));
+  launch_element(c, d, d->q, mixed(c), d->stream);
+  launch_assemble(c, d, mixed(c), pd, d->stream);
+  FE_CUDA_TRY(cudaGetLastError());
+  if (A_vals) {
+    double *tmp = nullptr;
+    FE_CUDA_TRY(cudaMalloc(&tmp, c->nnz * sizeof(double)));
+    launch_convert(d->A, mixed(c), tmp, false, c->nnz, d->stream);
+    cudaError_t e = cudaMemcpyAsync(A_vals, tmp, c->nnz * sizeof(double),
+                                    c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    d->stream);
+    cudaStreamSynchronize(d->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (b) FE_TRY(stage_out(c, b, d->b, c->n, 0));
+  FE_TRY(read_scalars(c));
+  return flag_status(c);
+}
+
+int fe_factor_now(fe_ctx *c) {
+  if (!c) return FE_ERR_ARG;
+  FE_TRY(ensure_device(c));
+  DeviceState *d = c->dev;
+  FE_TRY(clear_flags(c));
+  FE_TRY(launch_factor(c, d->step_index));
+  FE_TRY(wait_factor(c));
+  FE_TRY(read_scalars(c));
+  return flag_status(c);
+}
+
+int fe_apply_preconditioner(fe_ctx *c, const double *r, double *z) {
+  if (!c || !r || !z) return FE_ERR_ARG;
+  FE_TRY(ensure_device(c));
+  DeviceState *d = c->dev;
+  if (!d->have_factor) return set_error(c, FE_ERR_STATE, "no factor: call fe_factor_now or fe_step first");
+  FE_TRY(stage_in(c, d->r, r, c->n));
+  const bool fp32 = mixed(c);
+  launch_convert(d->r, false, d->vr, fp32, c->n, d->stream);
+  apply_enqueue(c, d, d->cur, fp32, d->vr, d->vz, d->stream);
+  launch_convert(d->vz, fp32, d->x, false, c->n, d->stream);
+  FE_CUDA_TRY(cudaGetLastError());
+  FE_TRY(stage_out(c, z, d->x, c->n, 0));
+  return FE_OK;
+}
+
+int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_step_info *info) {
+  if (!c) return FE_ERR_ARG;
+  FE_TRY(ensure_device(c));
+  DeviceState *d = c->dev;
+  cudaStream_t s = d->stream;
+  const bool fp32 = mixed(c);
+  const int64_t step = d->step_index;
+  const int R = c->opt.refactor_every;
+  const double *pd = nullptr;
+  if (p_ext) {
+    FE_TRY(stage_in(c, d->pext, p_ext, c->n));
+    pd = d->pext;
+  }
+  FE_TRY(clear_flags(c));
+  // S1 element kernel, S3 gather assembly of A and b
+  launch_element(c, d, d->q, fp32, s);
+  launch_assemble(c, d, fp32, pd, s);
+  FE_CUDA_TRY(cudaGetLastError());
+  // S4 lagged refactorisation: A_s is factored at s = 0 mod R on the side
+  // stream and preconditions steps s+1 .. s+R; step 0 (and R = 1) waits.
+  if (d->factor_pending >= 0) FE_TRY(wait_factor(c));
+  if (step % R == 0) {
+    FE_TRY(launch_factor(c, step));
+    if (step == 0 || R == 1 || !d->have_factor) FE_TRY(wait_factor(c));
+  }
+  const int age = int(step - d->cur_step);
+  // S5-S7 PCG, S9 refinement
+  int st = solve(c, info);
+  if (st) {
+    // leave the state untouched; a pending factor still completes on its stream
+    return st;
+  }
+  // S8 backward Euler
+  launch_integrate(c, d, s);
+  FE_CUDA_TRY(cudaGetLastError());
+  if (q_out) FE_TRY(stage_out(c, q_out, d->q, c->n, 0));
+  if (v_out) FE_TRY(stage_out(c, v_out, d->v, c->n, 1));
+  if (info) info->factor_age = age;
+  d->step_index = step + 1;
+  return FE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Internal definition of the fe_ctx handle shared by the host setup (C++)
+// and the CUDA translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fe_hotpath.h"
+
+namespace fe {
+
+constexpr int kNB = 64;        // panel width of the front factorisation
+constexpr int kTile = 64;      // tile edge of the front update kernels
+constexpr int kApplyRows = 64; // rows per task of the forward apply
+
+// Task kinds of the multifrontal factorisation (packed in int4.y >> 24).
+enum TaskKind { T_DIAG = 0, T_PANEL = 1, T_XK = 2, T_TRAIL = 3, T_RUPD = 4 };
+
+struct Front {
+  int32_t first = 0;      // first pivot, new DOF numbering
+  int32_t npiv = 0;       // p: pivots (DOFs) of the front
+  int32_t nupd = 0;       // number of update rows (DOFs)
+  int32_t parent = -1;
+  int32_t level = 0;      // 0 = leaf; children are on lower levels
+  int64_t f_off = 0;      // offset of the dense m x m front (column-major)
+  int64_t y_off = 0;      // offset of the m x p apply operator Y
+  int64_t w_off = 0;      // offset of the m-vector work buffer
+  int64_t u_off = 0;      // offset of the update vector (nupd)
+  int64_t rows_off = 0;   // offset into upd_rows_new / upd_rows_old
+  int64_t rmap_off = 0;   // offset of this front's map into its parent's front
+  int32_t m() const { return npiv + nupd; }
+};
+
+struct Level {
+  std::vector<int32_t> fronts;        // fronts of this level
+  int32_t steps = 0;                  // panel steps (max over fronts)
+  // factorisation task lists: assembly, then per step {diag, panel+xk, trail+rupd}
+  std::vector<int32_t> asm_tasks;     // (front, c0, c1) triples
+  std::vector<std::vector<int32_t>> diag, panel, trail;  // int4 per task
+  // apply task lists
+  std::vector<int32_t> fwd_tasks;     // (front, r0) pairs
+  std::vector<int32_t> bwd_tasks;     // (front, c0) pairs
+};
+
+struct DeviceState;  // defined in the CUDA translation unit
+
+}  // namespace fe
+
+struct fe_ctx {
+  // ---------------------------------------------------------------- inputs
+  int32_t elem_type = 0, npe = 4;
+  int64_t n_nodes = 0, n_elems = 0;
+  std::vector<double> X;              // [n_nodes * 3]
+  std::vector<int32_t> conn;          // [n_elems * npe]
+  std::vector<int32_t> fixed_nodes;
+  int32_t model = 0;
+  double rho = 0;
+  std::vector<double> params;         // [n_elems * 3] (expanded)
+  double h = 0, alpha = 0, beta = 0;
+  fe_options opt{};
+
+  // ---------------------------------------------------------- setup products
+  bool built = false;
+  int64_t n = 0, nnz = 0, ntrip = 0;
+  std::vector<int8_t> fixed_dof;      // [n]
+  std::vector<int32_t> rowptr, colind, C;
+  std::vector<int64_t> slot_ptr;      // [nnz + 1]
+  std::vector<int32_t> slot_src;      // [slot_ptr[nnz]]
+  std::vector<double> mass;           // [nnz]
+  std::vector<int32_t> node_ptr, node_src;   // node -> (e * npe + a), ascending
+  std::vector<double> rest;           // element rest data, SoA [ncoef][n_elems]
+  int32_t rest_ncoef = 0;
+
+  // nested dissection + multifrontal symbolic analysis
+  int64_t n_free = 0;
+  std::vector<int32_t> perm;          // new DOF -> original DOF   [n_free]
+  std::vector<int32_t> iperm;         // original DOF -> new DOF or -1 [n]
+  std::vector<fe::Front> fronts;
+  std::vector<int32_t> front_first, front_npiv, front_nupd, front_parent, front_level;
+  std::vector<int32_t> upd_rows_new, upd_rows_old;  // per front, update rows
+  std::vector<int32_t> rmap;          // per child: positions in its parent's front
+  std::vector<int32_t> child_ptr, child_list;       // children of each front, ascending
+  std::vector<int64_t> fa_ptr;        // per front, A entries: [fa_ptr[f], fa_ptr[f+1])
+  std::vector<int32_t> fa_slot, fa_off;             // CSR slot, offset in the front
+  std::vector<int64_t> fa_colptr;     // per front: per local column start into fa_*
+  std::vector<fe::Level> levels;
+  int64_t f_total = 0, y_total = 0, w_total = 0, u_total = 0;
+  double factor_flops = 0;
+
+  fe::DeviceState *dev = nullptr;
+  std::string err;
+};
+
+namespace fe {
+// host setup (fe_setup.cpp)
+int build_pattern_host(fe_ctx *c);
+int set_error(const fe_ctx *c, int code, const std::string &msg);
+// device side (fe_api.cu)
+void destroy_device(fe_ctx *c);
+}  // namespace fe

@@ -1,0 +1,142 @@
+// Device-side declarations shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "fe_ctx.h"
+
+namespace fe {
+
+#define FE_CUDA_TRY(call)                                                         \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return set_error(c, FE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Front descriptor as the kernels see it.
+struct DFront {
+  int32_t first, npiv, nupd, m;
+  int32_t child_begin, child_end;    // into child_list
+  int64_t f_off, y_off, w_off, u_off, rows_off, fac_off;
+};
+
+// Error flags raised by kernels (bit mask in DeviceState::flags[0]).
+enum { FLAG_INVERTED = 1, FLAG_PIVOT = 2, FLAG_BREAKDOWN = 4 };
+
+// Scalars of the PCG kept on the device (double).
+enum {
+  S_RZ = 0, S_RZ_NEW, S_PQ, S_ALPHA, S_BETA, S_RR, S_BB, S_TOL2, S_DONE, S_ITERS,
+  S_ORR, S_OTOL2, S_ODONE,
+  S_COUNT = 16
+};
+
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+struct DeviceState {
+  int device = 0;
+  cudaStream_t stream = nullptr;   // main stream (caller's or own)
+  cudaStream_t fstream = nullptr;  // factor side stream
+  bool own_stream = false;
+  cudaEvent_t ev_assembled = nullptr, ev_factored = nullptr, ev_apply_done = nullptr;
+  std::vector<void *> allocs;
+
+  // mesh / setup
+  int32_t *conn = nullptr;
+  double *rest = nullptr, *params = nullptr, *X = nullptr;
+  int32_t *rowptr = nullptr, *colind = nullptr, *slot_ptr = nullptr, *slot_src = nullptr;
+  double *mass = nullptr;
+  int8_t *fixed_row = nullptr;
+  int32_t *node_ptr = nullptr, *node_src = nullptr;
+
+  // state
+  double *q = nullptr, *v = nullptr, *pext = nullptr, *acc = nullptr;
+  double *stage_in = nullptr, *stage_out = nullptr;  // pinned host staging [n]
+  double *stage_big = nullptr; size_t stage_big_bytes = 0;
+
+  // element outputs f_e, K_e in the element type (FP64, or FP32 when mixed)
+  void *fe = nullptr;
+  void *Ke = nullptr;
+  // system: A in the matrix type (+ the snapshot the factor reads), b in FP64
+  void *A = nullptr;
+  void *Afac = nullptr;
+  double *b = nullptr;
+
+  // PCG vectors (FP64 outer) and inner vectors (matrix type)
+  double *x = nullptr, *r = nullptr;
+  void *vz = nullptr, *vp = nullptr, *vq = nullptr, *vr = nullptr, *vd = nullptr;
+  double *scal = nullptr;          // [S_COUNT] device scalars
+  double *partials = nullptr;      // [kMaxBlocks]
+  unsigned int *ticket = nullptr;  // last-block counters [4]
+  int *flags = nullptr;            // device error flags
+  int *h_flags = nullptr;          // pinned mirror
+  double *h_scal = nullptr;        // pinned mirror of scal
+
+  // multifrontal factor
+  DFront *fronts = nullptr;
+  int32_t *perm = nullptr, *upd_rows_old = nullptr, *rmap = nullptr, *child_list = nullptr;
+  int32_t *fa_slot = nullptr, *fa_off = nullptr;
+  int64_t *fa_colptr = nullptr;
+  int32_t *tasks = nullptr;        // all task lists, concatenated
+  void *F = nullptr;               // front scratch (factor type)
+  void *Y[2] = {nullptr, nullptr}; // apply operators (double-buffered for the lag)
+  double *D[2] = {nullptr, nullptr};
+  void *wbuf = nullptr, *ubuf = nullptr, *yperm = nullptr;  // apply work vectors
+  int cur = 0;                     // buffer the solver reads
+  int factor_pending = -1;         // buffer being written on fstream, or -1
+  int64_t pending_step = -1;       // step whose A the pending factor holds
+  int64_t cur_step = -1;           // step whose A the current factor holds
+  bool have_factor = false;
+
+  // task list offsets: per level {asm, per step: diag, panel, trail}, fwd, bwd
+  struct LevelTasks {
+    int64_t asm_off = 0, asm_n = 0;
+    std::vector<int64_t> diag_off, diag_n, panel_off, panel_n, trail_off, trail_n;
+    int64_t fwd_off = 0, fwd_n = 0, bwd_off = 0, bwd_n = 0;
+    int64_t nfronts = 0, fronts_off = 0;
+  };
+  std::vector<LevelTasks> lt;
+  int32_t *level_fronts = nullptr;
+
+  int64_t step_index = 0;
+  size_t bytes_total = 0;
+};
+
+constexpr int kMaxBlocks = 4096;
+
+// ------------------------------------------------------------ kernel launchers
+// (fe_kernels.cu)
+void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool fp32, cudaStream_t s);
+void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const double *pext, cudaStream_t s);
+// y = A x; S_PQ = x.y; S_ALPHA = S_RZ / S_PQ
+void launch_spmv_dot(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y, cudaStream_t s);
+// r = b - A x (FP64 accumulation); S_ORR, S_ODONE
+void launch_residual(const fe_ctx *c, const DeviceState *d, bool fp32, cudaStream_t s);
+// x += alpha p; r -= alpha q; S_RR, S_DONE, S_ITERS
+void launch_axpy_norm(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const void *p,
+                      const void *q, cudaStream_t s);
+// S_BETA = r.z / S_RZ; S_RZ = r.z
+void launch_dot_rz(const fe_ctx *c, const DeviceState *d, bool fp32, const void *r, const void *z, bool first,
+                   cudaStream_t s);
+// p = z + beta p
+void launch_update_p(const fe_ctx *c, const DeviceState *d, bool fp32, const void *z, void *p, bool first,
+                     cudaStream_t s);
+// x = 0, r = rhs; tolerances (outer: S_BB, S_OTOL2, S_ORR, S_ODONE, S_ITERS = 0)
+void launch_init_solve(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const double *rhs,
+                       double tol, bool outer, cudaStream_t s);
+void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s);  // x += (double) vd
+void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s);
+void launch_convert(const void *src, bool src32, void *dst, bool dst32, int64_t n, cudaStream_t s);
+
+// (fe_factor.cu)
+int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Afac, cudaStream_t s);
+void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
+                   cudaStream_t s);
+
+}  // namespace fe

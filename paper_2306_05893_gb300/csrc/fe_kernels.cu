@@ -1,0 +1,634 @@
+// Hot-path kernels of one implicit step: element force/tangent (Section 3.1),
+// gather assembly of A and b through the inverse of the map C (Section 4.2,
+// Eq. "dynamic equation2"), CSR SpMV and the fused CG vector operations
+// (Section 6.2, Fig. "DataTransfer"), backward-Euler integration
+// (Eq. "implicit integration").  Every reduction is deterministic: per-block
+// partials in a fixed order, summed in a fixed order by the last block.
+#include <cuda_runtime.h>
+
+#include "fe_device.cuh"
+#include "fe_material.cuh"
+
+namespace fe {
+
+// ------------------------------------------------------------- reductions
+
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = (threadIdx.x < BLOCK / 32) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+// Grid-wide deterministic sum; returns true in the last block to finish, whose
+// thread 0 then holds the total in *out.
+template <int BLOCK>
+__device__ __forceinline__ bool grid_sum(double v, double *partials, unsigned int *ticket,
+                                         double *out) {
+  __shared__ double sh[BLOCK / 32];
+  __shared__ bool last;
+  double s = block_sum<BLOCK>(v, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s;
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += BLOCK) acc += ((volatile double *)partials)[i];
+  double tot = block_sum<BLOCK>(acc, sh);
+  if (threadIdx.x == 0) {
+    *out = tot;
+    *ticket = 0u;
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool solve_done(const double *scal) { return scal[S_DONE] != 0.0; }
+
+// ---------------------------------------------------------- element kernels
+
+template <typename T>
+__device__ __forceinline__ T ld_cast(const double *p) { return T(__ldg(p)); }
+
+// One thread per tet.  Rest data SoA [10][E]: rows of Dm^{-1} (= grad N_1..3),
+// volume.  Outputs f_e [E][4][3] and K_e [E][144] in fill order
+// ((a*4 + b)*9 + 3i + k), staged through shared memory for coalesced stores.
+template <int MODEL, typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, const int32_t *__restrict__ conn,
+                                                    const double *__restrict__ rest,
+                                                    const double *__restrict__ params,
+                                                    const double *__restrict__ X,
+                                                    const double *__restrict__ q, T *__restrict__ f_out,
+                                                    T *__restrict__ K_out, int *flags) {
+  extern __shared__ unsigned char smem_raw[];
+  T *sk = reinterpret_cast<T *>(smem_raw);
+  constexpr int LD = 145;
+  const int64_t e0 = int64_t(blockIdx.x) * BLOCK;
+  const int64_t e = e0 + threadIdx.x;
+  if (e < E) {
+    const int4 cn = reinterpret_cast<const int4 *>(conn)[e];
+    const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
+    T g[4][3];
+#pragma unroll
+    for (int a = 1; a < 4; ++a)
+#pragma unroll
+      for (int J = 0; J < 3; ++J) g[a][J] = ld_cast<T>(rest + (3 * (a - 1) + J) * E + e);
+#pragma unroll
+    for (int J = 0; J < 3; ++J) g[0][J] = -(g[1][J] + g[2][J] + g[3][J]);
+    const T V = ld_cast<T>(rest + 9 * E + e);
+    const T p0 = ld_cast<T>(params + e), p1 = ld_cast<T>(params + E + e),
+            p2 = ld_cast<T>(params + 2 * E + e);
+    T H[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int J = 0; J < 3; ++J) H[i][J] = T(0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        // displacement in FP64, then the working type
+        const T u = T(__ldg(q + 3 * nd[a] + i) - __ldg(X + 3 * nd[a] + i));
+#pragma unroll
+        for (int J = 0; J < 3; ++J) H[i][J] += u * g[a][J];
+      }
+    Kin<T> kin;
+    kin.init(H);
+    if (!(kin.J > T(0))) atomicOr(flags, FLAG_INVERTED);
+    Law<MODEL, T> law;
+    T P[3][3];
+    law.init(kin, H, p0, p1, p2, P);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        T s = T(0);
+#pragma unroll
+        for (int J = 0; J < 3; ++J) s += P[i][J] * g[a][J];
+        f_out[e * 12 + 3 * a + i] = V * s;
+      }
+    T *row = sk + threadIdx.x * LD;
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll 1
+      for (int k = i; k < 3; ++k) {
+        T C[3][3];
+        law.block(i, k, C);
+        T hb[4][3];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int J = 0; J < 3; ++J) hb[b][J] = C[J][0] * g[b][0] + C[J][1] * g[b][1] + C[J][2] * g[b][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const T val = V * (g[a][0] * hb[b][0] + g[a][1] * hb[b][1] + g[a][2] * hb[b][2]);
+            row[(a * 4 + b) * 9 + 3 * i + k] = val;
+            if (i != k) row[(b * 4 + a) * 9 + 3 * k + i] = val;  // major symmetry of CC
+          }
+      }
+    }
+  }
+  __syncthreads();
+  const int64_t nvalid = (E - e0) < BLOCK ? (E - e0) : BLOCK;
+  T *dst = K_out + e0 * 144;
+  for (int64_t idx = threadIdx.x; idx < nvalid * 144; idx += BLOCK)
+    dst[idx] = sk[(idx / 144) * LD + idx % 144];
+}
+
+// One thread per (hex, local node a); 8 Gauss points.  Rest data SoA
+// [8 * 25][E]: per Gauss point grad N (8 x 3) and w det J0.  Thread a owns
+// the block row a of K_e (72 values) and f_a.
+template <int MODEL, typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, const int32_t *__restrict__ conn,
+                                                    const double *__restrict__ rest,
+                                                    const double *__restrict__ params,
+                                                    const double *__restrict__ X,
+                                                    const double *__restrict__ q, T *__restrict__ f_out,
+                                                    T *__restrict__ K_out, int *flags) {
+  extern __shared__ unsigned char smem_raw[];
+  T *sk = reinterpret_cast<T *>(smem_raw);
+  constexpr int EPB = BLOCK / 8;  // elements per block
+  constexpr int LD = 577;
+  const int64_t e0 = int64_t(blockIdx.x) * EPB;
+  const int el = threadIdx.x >> 3, a = threadIdx.x & 7;
+  const int64_t e = e0 + el;
+  if (e < E) {
+    T u[8][3];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int nb = __ldg(conn + e * 8 + b);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[b][i] = T(__ldg(q + 3 * nb + i) - __ldg(X + 3 * nb + i));
+    }
+    const T p0 = ld_cast<T>(params + e), p1 = ld_cast<T>(params + E + e),
+            p2 = ld_cast<T>(params + 2 * E + e);
+    T acc[8][9];
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+#pragma unroll
+      for (int c = 0; c < 9; ++c) acc[b][c] = T(0);
+    T fa[3] = {T(0), T(0), T(0)};
+#pragma unroll 1
+    for (int gp = 0; gp < 8; ++gp) {
+      T g[8][3];
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) g[b][J] = ld_cast<T>(rest + (gp * 25 + 3 * b + J) * E + e);
+      const T w = ld_cast<T>(rest + (gp * 25 + 24) * E + e);
+      T H[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) {
+          T s = T(0);
+#pragma unroll
+          for (int b = 0; b < 8; ++b) s += u[b][i] * g[b][J];
+          H[i][J] = s;
+        }
+      Kin<T> kin;
+      kin.init(H);
+      if (!(kin.J > T(0)) && a == 0) atomicOr(flags, FLAG_INVERTED);
+      Law<MODEL, T> law;
+      T P[3][3];
+      law.init(kin, H, p0, p1, p2, P);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) fa[i] += w * (P[i][0] * g[a][0] + P[i][1] * g[a][1] + P[i][2] * g[a][2]);
+#pragma unroll 1
+      for (int i = 0; i < 3; ++i)
+#pragma unroll 1
+        for (int k = 0; k < 3; ++k) {
+          T C[3][3];
+          law.block(i, k, C);
+          T vL[3];
+#pragma unroll
+          for (int L = 0; L < 3; ++L) vL[L] = w * (g[a][0] * C[0][L] + g[a][1] * C[1][L] + g[a][2] * C[2][L]);
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[b][3 * i + k] += vL[0] * g[b][0] + vL[1] * g[b][1] + vL[2] * g[b][2];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) f_out[e * 24 + 3 * a + i] = fa[i];
+    T *row = sk + el * LD + a * 72;
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+#pragma unroll
+      for (int c = 0; c < 9; ++c) row[b * 9 + c] = acc[b][c];
+  }
+  __syncthreads();
+  const int64_t nvalid = (E - e0) < EPB ? (E - e0) : EPB;
+  T *dst = K_out + e0 * 576;
+  for (int64_t idx = threadIdx.x; idx < nvalid * 576; idx += BLOCK)
+    dst[idx] = sk[(idx / 576) * LD + idx % 576];
+}
+
+template <int MODEL, typename T>
+static void launch_element_t(const fe_ctx *c, const DeviceState *d, const double *q, cudaStream_t s) {
+  const int64_t E = c->n_elems;
+  T *fo = reinterpret_cast<T *>(d->fe);
+  T *Ko = reinterpret_cast<T *>(d->Ke);
+  if (c->elem_type == FE_TET4) {
+    constexpr int B = sizeof(T) == 8 ? 64 : 128;
+    const size_t sm = size_t(B) * 145 * sizeof(T);
+    cudaFuncSetAttribute(tet_kernel<MODEL, T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    tet_kernel<MODEL, T, B><<<unsigned((E + B - 1) / B), B, sm, s>>>(E, d->conn, d->rest, d->params,
+                                                                     d->X, q, fo, Ko, d->flags);
+  } else {
+    constexpr int B = 128, EPB = B / 8;
+    const size_t sm = size_t(EPB) * 577 * sizeof(T);
+    cudaFuncSetAttribute(hex_kernel<MODEL, T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    hex_kernel<MODEL, T, B><<<unsigned((E + EPB - 1) / EPB), B, sm, s>>>(E, d->conn, d->rest, d->params,
+                                                                        d->X, q, fo, Ko, d->flags);
+  }
+}
+
+void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool fp32, cudaStream_t s) {
+  switch (c->model) {
+    case FE_SVK:
+      fp32 ? launch_element_t<FE_SVK, float>(c, d, q, s) : launch_element_t<FE_SVK, double>(c, d, q, s);
+      break;
+    case FE_NEOHOOKE:
+      fp32 ? launch_element_t<FE_NEOHOOKE, float>(c, d, q, s)
+           : launch_element_t<FE_NEOHOOKE, double>(c, d, q, s);
+      break;
+    default:
+      fp32 ? launch_element_t<FE_MOONEY_RIVLIN, float>(c, d, q, s)
+           : launch_element_t<FE_MOONEY_RIVLIN, double>(c, d, q, s);
+  }
+}
+
+// ------------------------------------------------------ gather assembly
+// One warp per CSR row.  Slot s: K_s = sum of its triplets (ascending ids, as
+// the inverse of C lists them), A_s = cM M_s + cK K_s; the row of b gathers
+// the element forces of its node and subtracts (alpha M + (beta+h) K) v.
+template <typename TK, typename TA>
+__global__ void __launch_bounds__(256) assemble_kernel(
+    int64_t n, int npe, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
+    const int32_t *__restrict__ slot_ptr, const int32_t *__restrict__ slot_src,
+    const TK *__restrict__ Ke, const double *__restrict__ mass, const TK *__restrict__ fe,
+    const int32_t *__restrict__ node_ptr, const int32_t *__restrict__ node_src,
+    const int8_t *__restrict__ fixed_row, const double *__restrict__ v, const double *__restrict__ p,
+    double cM, double cK, double al, double bh, TA *__restrict__ A, double *__restrict__ b) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t row = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n; row += warps) {
+    const int32_t s0 = rowptr[row], s1 = rowptr[row + 1];
+    if (fixed_row[row]) {
+      if (lane == 0) {
+        A[s0] = TA(1);
+        b[row] = 0.0;
+      }
+      continue;
+    }
+    double acc = 0.0;
+    for (int32_t s = s0 + lane; s < s1; s += 32) {
+      double Ks = 0.0;
+      const int32_t j1 = slot_ptr[s + 1];
+      for (int32_t j = slot_ptr[s]; j < j1; ++j) Ks += double(Ke[slot_src[j]]);
+      const double Ms = mass[s];
+      A[s] = TA(cM * Ms + cK * Ks);
+      acc += (al * Ms + bh * Ks) * v[colind[s]];
+    }
+    const int64_t node = row / 3;
+    const int comp = int(row - 3 * node);
+    double fs = 0.0;
+    for (int32_t j = node_ptr[node] + lane; j < node_ptr[node + 1]; j += 32)
+      fs += double(fe[int64_t(node_src[j]) * 3 + comp]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      fs += __shfl_xor_sync(0xffffffffu, fs, o);
+    }
+    if (lane == 0) b[row] = (p ? p[row] : 0.0) - fs - acc;
+  }
+}
+
+void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const double *pext,
+                     cudaStream_t s) {
+  const double h = c->h, al = c->alpha, be = c->beta;
+  const double cM = 1.0 + h * al, cK = h * (be + h), bh = be + h;
+  const int64_t n = c->n;
+  const unsigned grid = unsigned(std::min<int64_t>((n + 7) / 8, 152 * 64));
+  if (fp32)
+    assemble_kernel<float, float><<<grid, 256, 0, s>>>(
+        n, c->npe, d->rowptr, d->colind, d->slot_ptr, d->slot_src, (const float *)d->Ke, d->mass,
+        (const float *)d->fe, d->node_ptr, d->node_src, d->fixed_row, d->v, pext, cM, cK, al, bh,
+        (float *)d->A, d->b);
+  else
+    assemble_kernel<double, double><<<grid, 256, 0, s>>>(
+        n, c->npe, d->rowptr, d->colind, d->slot_ptr, d->slot_src, (const double *)d->Ke, d->mass,
+        (const double *)d->fe, d->node_ptr, d->node_src, d->fixed_row, d->v, pext, cM, cK, al, bh,
+        (double *)d->A, d->b);
+}
+
+// ------------------------------------------------------------------ SpMV
+constexpr int kRedBlock = 256;
+
+static unsigned red_grid(int64_t n) {
+  int64_t g = (n + kRedBlock - 1) / kRedBlock;
+  return unsigned(std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8)));
+}
+
+// y = A x (TPR threads per row) fused with x.y; the last block sets
+// alpha = rz / (x.y) and flags a breakdown when x.y <= 0.
+template <typename TA, typename TV, int TPR>
+__global__ void __launch_bounds__(kRedBlock) spmv_dot_kernel(
+    int64_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
+    const TA *__restrict__ A, const TV *__restrict__ x, TV *__restrict__ y, double *scal,
+    double *partials, unsigned int *ticket, int *flags) {
+  if (solve_done(scal)) return;
+  const int sub = threadIdx.x % TPR;
+  const int64_t groups = int64_t(gridDim.x) * (kRedBlock / TPR);
+  double dot = 0.0;
+  for (int64_t row = int64_t(blockIdx.x) * (kRedBlock / TPR) + threadIdx.x / TPR; row < n; row += groups) {
+    TV acc = TV(0);
+    const int32_t k1 = rowptr[row + 1];
+    for (int32_t k = rowptr[row] + sub; k < k1; k += TPR) acc += TV(A[k]) * x[colind[k]];
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
+    if (sub == 0) {
+      y[row] = acc;
+      dot += double(x[row]) * double(acc);
+    }
+  }
+  double tot;
+  if (grid_sum<kRedBlock>(dot, partials, ticket, &tot) && threadIdx.x == 0) {
+    scal[S_PQ] = tot;
+    if (!(tot > 0.0)) {
+      atomicOr(flags, FLAG_BREAKDOWN);
+      scal[S_DONE] = 1.0;
+      scal[S_ALPHA] = 0.0;
+    } else {
+      scal[S_ALPHA] = scal[S_RZ] / tot;
+    }
+  }
+}
+
+// r = b - A x in FP64 (A in its storage type); ||r||^2 -> S_ORR, S_ODONE.
+template <typename TA, int TPR>
+__global__ void __launch_bounds__(kRedBlock) residual_kernel(
+    int64_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
+    const TA *__restrict__ A, const double *__restrict__ x, const double *__restrict__ b,
+    double *__restrict__ r, double *scal, double *partials, unsigned int *ticket) {
+  const int sub = threadIdx.x % TPR;
+  const int64_t groups = int64_t(gridDim.x) * (kRedBlock / TPR);
+  double rr = 0.0;
+  for (int64_t row = int64_t(blockIdx.x) * (kRedBlock / TPR) + threadIdx.x / TPR; row < n; row += groups) {
+    double acc = 0.0;
+    const int32_t k1 = rowptr[row + 1];
+    for (int32_t k = rowptr[row] + sub; k < k1; k += TPR) acc += double(A[k]) * x[colind[k]];
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
+    if (sub == 0) {
+      const double ri = b[row] - acc;
+      r[row] = ri;
+      rr += ri * ri;
+    }
+  }
+  double tot;
+  if (grid_sum<kRedBlock>(rr, partials, ticket, &tot) && threadIdx.x == 0) {
+    scal[S_ORR] = tot;
+    scal[S_ODONE] = (tot <= scal[S_OTOL2]) ? 1.0 : 0.0;
+  }
+}
+
+// x += alpha p; r -= alpha q; ||r||^2 -> S_RR; S_DONE when below S_TOL2.
+template <typename TV>
+__global__ void __launch_bounds__(kRedBlock) axpy_norm_kernel(int64_t n, TV *__restrict__ x,
+                                                              TV *__restrict__ r,
+                                                              const TV *__restrict__ p,
+                                                              const TV *__restrict__ q, double *scal,
+                                                              double *partials, unsigned int *ticket) {
+  if (solve_done(scal)) return;
+  const TV al = TV(scal[S_ALPHA]);
+  double rr = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * kRedBlock + threadIdx.x; i < n; i += int64_t(gridDim.x) * kRedBlock) {
+    x[i] += al * p[i];
+    const TV ri = r[i] - al * q[i];
+    r[i] = ri;
+    rr += double(ri) * double(ri);
+  }
+  double tot;
+  if (grid_sum<kRedBlock>(rr, partials, ticket, &tot) && threadIdx.x == 0) {
+    scal[S_RR] = tot;
+    scal[S_ITERS] += 1.0;
+    if (tot <= scal[S_TOL2]) scal[S_DONE] = 1.0;
+  }
+}
+
+// rz_new = r.z; first: S_RZ = rz_new; else beta = rz_new / S_RZ, S_RZ = rz_new.
+template <typename TV>
+__global__ void __launch_bounds__(kRedBlock) dot_rz_kernel(int64_t n, const TV *__restrict__ r,
+                                                           const TV *__restrict__ z, int first,
+                                                           double *scal, double *partials,
+                                                           unsigned int *ticket, int *flags) {
+  if (solve_done(scal)) return;
+  double s = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * kRedBlock + threadIdx.x; i < n; i += int64_t(gridDim.x) * kRedBlock)
+    s += double(r[i]) * double(z[i]);
+  double tot;
+  if (grid_sum<kRedBlock>(s, partials, ticket, &tot) && threadIdx.x == 0) {
+    if (!(tot > 0.0) && scal[S_RR] > 0.0) {  // P^{-1} lost definiteness
+      atomicOr(flags, FLAG_BREAKDOWN);
+      scal[S_DONE] = 1.0;
+    }
+    if (first) {
+      scal[S_BETA] = 0.0;
+    } else {
+      scal[S_BETA] = tot / scal[S_RZ];
+    }
+    scal[S_RZ] = tot;
+  }
+}
+
+template <typename TV>
+__global__ void update_p_kernel(int64_t n, const TV *__restrict__ z, TV *__restrict__ p, int first,
+                                const double *scal) {
+  if (solve_done(scal)) return;
+  const TV be = first ? TV(0) : TV(scal[S_BETA]);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = z[i] + be * p[i];
+}
+
+// Start of a (sub)solve: x = 0, r = rhs (cast), ||rhs||^2 -> tolerance.
+// outer = 1: S_BB, S_OTOL2 = tol^2 * bb, S_ORR, S_ODONE.  outer = 0: inner
+// solve with S_TOL2 = tol^2 * ||rhs||^2, S_DONE.
+template <typename TV>
+__global__ void __launch_bounds__(kRedBlock) init_solve_kernel(int64_t n, TV *__restrict__ x,
+                                                               TV *__restrict__ r,
+                                                               const double *__restrict__ rhs,
+                                                               double tol, int outer, double *scal,
+                                                               double *partials, unsigned int *ticket) {
+  double s = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * kRedBlock + threadIdx.x; i < n; i += int64_t(gridDim.x) * kRedBlock) {
+    const double v = rhs[i];
+    x[i] = TV(0);
+    r[i] = TV(v);
+    s += v * v;
+  }
+  double tot;
+  if (grid_sum<kRedBlock>(s, partials, ticket, &tot) && threadIdx.x == 0) {
+    if (outer) {
+      scal[S_BB] = tot;
+      scal[S_OTOL2] = tol * tol * tot;
+      scal[S_ORR] = tot;
+      scal[S_ODONE] = (tot == 0.0) ? 1.0 : 0.0;
+      scal[S_ITERS] = 0.0;
+    }
+    scal[S_TOL2] = tol * tol * tot;
+    scal[S_RR] = tot;
+    scal[S_DONE] = (tot == 0.0) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void refine_update_kernel(int64_t n, double *__restrict__ x, const float *__restrict__ d) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] += double(d[i]);
+}
+
+__global__ void integrate_kernel(int64_t n, double h, const double *__restrict__ a, double *__restrict__ v,
+                                 double *__restrict__ q) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double vn = v[i] + h * a[i];
+    v[i] = vn;
+    q[i] += h * vn;
+  }
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(const S *__restrict__ src, D *__restrict__ dst, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    dst[i] = D(src[i]);
+}
+
+static unsigned ew_grid(int64_t n) {
+  return unsigned(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
+}
+
+static int tpr_for(const fe_ctx *c) { return c->elem_type == FE_TET4 ? 8 : 16; }
+
+void launch_spmv_dot(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y,
+                     cudaStream_t s) {
+  const int64_t n = c->n;
+  const unsigned g = red_grid(n * tpr_for(c) / 4);
+  if (fp32) {
+    if (tpr_for(c) == 8)
+      spmv_dot_kernel<float, float, 8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const float *)d->A,
+                                                               (const float *)x, (float *)y, d->scal,
+                                                               d->partials, d->ticket, d->flags);
+    else
+      spmv_dot_kernel<float, float, 16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const float *)d->A,
+                                                                (const float *)x, (float *)y, d->scal,
+                                                                d->partials, d->ticket, d->flags);
+  } else {
+    if (tpr_for(c) == 8)
+      spmv_dot_kernel<double, double, 8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind,
+                                                                 (const double *)d->A, (const double *)x,
+                                                                 (double *)y, d->scal, d->partials,
+                                                                 d->ticket, d->flags);
+    else
+      spmv_dot_kernel<double, double, 16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind,
+                                                                  (const double *)d->A, (const double *)x,
+                                                                  (double *)y, d->scal, d->partials,
+                                                                  d->ticket, d->flags);
+  }
+}
+
+void launch_residual(const fe_ctx *c, const DeviceState *d, bool fp32, cudaStream_t s) {
+  const int64_t n = c->n;
+  const unsigned g = red_grid(n * tpr_for(c) / 4);
+  if (fp32) {
+    if (tpr_for(c) == 8)
+      residual_kernel<float, 8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const float *)d->A, d->x,
+                                                        d->b, d->r, d->scal, d->partials, d->ticket);
+    else
+      residual_kernel<float, 16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const float *)d->A, d->x,
+                                                         d->b, d->r, d->scal, d->partials, d->ticket);
+  } else {
+    if (tpr_for(c) == 8)
+      residual_kernel<double, 8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const double *)d->A,
+                                                         d->x, d->b, d->r, d->scal, d->partials, d->ticket);
+    else
+      residual_kernel<double, 16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const double *)d->A,
+                                                          d->x, d->b, d->r, d->scal, d->partials, d->ticket);
+  }
+}
+
+void launch_axpy_norm(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const void *p,
+                      const void *q, cudaStream_t s) {
+  const int64_t n = c->n;
+  if (fp32)
+    axpy_norm_kernel<float><<<red_grid(n), kRedBlock, 0, s>>>(n, (float *)x, (float *)r, (const float *)p,
+                                                              (const float *)q, d->scal, d->partials, d->ticket);
+  else
+    axpy_norm_kernel<double><<<red_grid(n), kRedBlock, 0, s>>>(n, (double *)x, (double *)r,
+                                                               (const double *)p, (const double *)q, d->scal,
+                                                               d->partials, d->ticket);
+}
+
+void launch_dot_rz(const fe_ctx *c, const DeviceState *d, bool fp32, const void *r, const void *z, bool first,
+                   cudaStream_t s) {
+  const int64_t n = c->n;
+  if (fp32)
+    dot_rz_kernel<float><<<red_grid(n), kRedBlock, 0, s>>>(n, (const float *)r, (const float *)z, first,
+                                                           d->scal, d->partials, d->ticket, d->flags);
+  else
+    dot_rz_kernel<double><<<red_grid(n), kRedBlock, 0, s>>>(n, (const double *)r, (const double *)z, first,
+                                                            d->scal, d->partials, d->ticket, d->flags);
+}
+
+void launch_update_p(const fe_ctx *c, const DeviceState *d, bool fp32, const void *z, void *p, bool first,
+                     cudaStream_t s) {
+  const int64_t n = c->n;
+  if (fp32)
+    update_p_kernel<float><<<ew_grid(n), 256, 0, s>>>(n, (const float *)z, (float *)p, first, d->scal);
+  else
+    update_p_kernel<double><<<ew_grid(n), 256, 0, s>>>(n, (const double *)z, (double *)p, first, d->scal);
+}
+
+void launch_init_solve(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const double *rhs,
+                       double tol, bool outer, cudaStream_t s) {
+  const int64_t n = c->n;
+  if (fp32)
+    init_solve_kernel<float><<<red_grid(n), kRedBlock, 0, s>>>(n, (float *)x, (float *)r, rhs, tol, outer,
+                                                               d->scal, d->partials, d->ticket);
+  else
+    init_solve_kernel<double><<<red_grid(n), kRedBlock, 0, s>>>(n, (double *)x, (double *)r, rhs, tol, outer,
+                                                                d->scal, d->partials, d->ticket);
+}
+
+void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
+  refine_update_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, d->x, (const float *)d->vd);
+}
+
+void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
+  integrate_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, c->h, d->x, d->v, d->q);
+}
+
+void launch_convert(const void *src, bool src32, void *dst, bool dst32, int64_t n, cudaStream_t s) {
+  const unsigned g = ew_grid(n);
+  if (src32 && dst32)
+    convert_kernel<float, float><<<g, 256, 0, s>>>((const float *)src, (float *)dst, n);
+  else if (src32)
+    convert_kernel<float, double><<<g, 256, 0, s>>>((const float *)src, (double *)dst, n);
+  else if (dst32)
+    convert_kernel<double, float><<<g, 256, 0, s>>>((const double *)src, (float *)dst, n);
+  else
+    convert_kernel<double, double><<<g, 256, 0, s>>>((const double *)src, (double *)dst, n);
+}
+
+}  // namespace fe

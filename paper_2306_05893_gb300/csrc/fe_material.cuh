@@ -1,0 +1,246 @@
+// Hyperelastic laws of Section 3.1 on the device, written in terms of the
+// displacement gradient H = F - I so that FP32 arithmetic keeps the stress
+// accurate relative to its own size (no cancellation of F against I):
+//   E = (H + H^T + H^T H)/2, J - 1 = tr H + ((tr H)^2 - tr H^2)/2 + det H,
+//   F - F^{-T} = H + F^{-T} H^T, 2F - (2/3) I1 F^{-T} = 4 F^{-T} dev E, ...
+// The tangent CC_iJkL = dP_iJ/dF_kL is evaluated one 3x3 block
+// C_ik[J][L] = CC_iJkL at a time.
+#pragma once
+
+#include "../../include/fe_hotpath.h"
+
+namespace fe {
+
+template <typename T>
+struct M3 {
+  T a[3][3];
+};
+
+template <typename T>
+__device__ __forceinline__ T tr3(const T m[3][3]) { return m[0][0] + m[1][1] + m[2][2]; }
+
+template <typename T>
+__device__ __forceinline__ T det3d(const T m[3][3]) {
+  return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+         m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+         m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+template <typename T>
+__device__ __forceinline__ T mlog1p(T x);
+template <>
+__device__ __forceinline__ double mlog1p<double>(double x) { return log1p(x); }
+template <>
+__device__ __forceinline__ float mlog1p<float>(float x) { return log1pf(x); }
+template <typename T>
+__device__ __forceinline__ T mexp(T x);
+template <>
+__device__ __forceinline__ double mexp<double>(double x) { return exp(x); }
+template <>
+__device__ __forceinline__ float mexp<float>(float x) { return expf(x); }
+
+// Kinematics common to every law.
+template <typename T>
+struct Kin {
+  T F[3][3], E[3][3], G[3][3];  // F, Green strain, F^{-T}
+  T trE, Jm1, J;
+  __device__ void init(const T H[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T s = H[i][j] + H[j][i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s += H[k][i] * H[k][j];
+        E[i][j] = T(0.5) * s;
+        F[i][j] = H[i][j] + (i == j ? T(1) : T(0));
+      }
+    trE = tr3(E);
+    T trH = tr3(H);
+    T trHH = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) trHH += H[i][k] * H[k][i];
+    Jm1 = trH + T(0.5) * (trH * trH - trHH) + det3d(H);
+    J = T(1) + Jm1;
+    // G = F^{-T} = cof(F) / J
+    T iJ = T(1) / J;
+    G[0][0] = (F[1][1] * F[2][2] - F[1][2] * F[2][1]) * iJ;
+    G[0][1] = (F[1][2] * F[2][0] - F[1][0] * F[2][2]) * iJ;
+    G[0][2] = (F[1][0] * F[2][1] - F[1][1] * F[2][0]) * iJ;
+    G[1][0] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) * iJ;
+    G[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) * iJ;
+    G[1][2] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) * iJ;
+    G[2][0] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) * iJ;
+    G[2][1] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) * iJ;
+    G[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) * iJ;
+  }
+};
+
+template <int MODEL, typename T>
+struct Law;
+
+// St Venant-Kirchhoff: psi = mu tr(E^2) + lambda/2 (tr E)^2, P = F S.
+template <typename T>
+struct Law<FE_SVK, T> {
+  T F[3][3], S[3][3], B[3][3];
+  T mu, lam;
+  __device__ void init(const Kin<T> &k, const T H[3][3], T p0, T p1, T, T P[3][3]) {
+    mu = p0;
+    lam = p1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        F[i][j] = k.F[i][j];
+        S[i][j] = T(2) * mu * k.E[i][j] + (i == j ? lam * k.trE : T(0));
+      }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T s = T(0), bb = T(0);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          s += F[i][l] * S[l][j];
+          bb += F[i][l] * F[j][l];
+        }
+        P[i][j] = s;
+        B[i][j] = bb;
+      }
+  }
+  __device__ __forceinline__ void block(int i, int k, T C[3][3]) const {
+#pragma unroll
+    for (int J = 0; J < 3; ++J)
+#pragma unroll
+      for (int L = 0; L < 3; ++L)
+        C[J][L] = (i == k ? S[L][J] : T(0)) + mu * (F[i][L] * F[k][J] + (J == L ? B[i][k] : T(0))) +
+                  lam * F[i][J] * F[k][L];
+  }
+};
+
+// Compressible neo-Hookean: psi = mu/2 (I1 - 3) - mu ln J + lambda/2 (ln J)^2,
+// P = mu (F - F^{-T}) + lambda ln J F^{-T}.
+template <typename T>
+struct Law<FE_NEOHOOKE, T> {
+  T G[3][3];
+  T mu, lam, c1;
+  __device__ void init(const Kin<T> &k, const T H[3][3], T p0, T p1, T, T P[3][3]) {
+    mu = p0;
+    lam = p1;
+    T lnJ = mlog1p(k.Jm1);
+    c1 = mu - lam * lnJ;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) G[i][j] = k.G[i][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T gh = T(0);  // (F^{-T} H^T)_ij
+#pragma unroll
+        for (int l = 0; l < 3; ++l) gh += G[i][l] * H[j][l];
+        P[i][j] = mu * (H[i][j] + gh) + lam * lnJ * G[i][j];
+      }
+  }
+  __device__ __forceinline__ void block(int i, int k, T C[3][3]) const {
+#pragma unroll
+    for (int J = 0; J < 3; ++J)
+#pragma unroll
+      for (int L = 0; L < 3; ++L)
+        C[J][L] = (i == k && J == L ? mu : T(0)) + c1 * G[i][L] * G[k][J] + lam * G[i][J] * G[k][L];
+  }
+};
+
+// Decoupled Mooney-Rivlin: psi = C10 (J^{-2/3} I1 - 3) + C01 (J^{-4/3} I2 - 3)
+// + kappa/2 (J - 1)^2, with I1 = tr C, I2 = ((tr C)^2 - tr C^2)/2.
+template <typename T>
+struct Law<FE_MOONEY_RIVLIN, T> {
+  T F[3][3], G[3][3], R[3][3], Cm[3][3], B[3][3];
+  T cdd, gam, cff, cxg, cm;
+  __device__ void init(const Kin<T> &k, const T H[3][3], T c10, T c01, T kap, T P[3][3]) {
+    T lnJ = mlog1p(k.Jm1);
+    T a = c10 * mexp(T(-2.0 / 3.0) * lnJ);
+    T b = c01 * mexp(T(-4.0 / 3.0) * lnJ);
+    T J = k.J;
+    // stress: P = G (4a devE + b Q) + kappa (J-1) J G,
+    // Q = 4 devE + 8 trE devE - 8 dev(E^2)
+    T E2[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) s += k.E[i][l] * k.E[l][j];
+        E2[i][j] = s;
+      }
+    T trE2 = tr3(E2);
+    T M[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T dE = k.E[i][j] - (i == j ? k.trE / T(3) : T(0));
+        T dE2 = E2[i][j] - (i == j ? trE2 / T(3) : T(0));
+        M[i][j] = T(4) * a * dE + b * (T(4) * dE + T(8) * k.trE * dE - T(8) * dE2);
+      }
+    T pj = kap * k.Jm1 * J;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) s += k.G[i][l] * M[l][j];
+        P[i][j] = s + pj * k.G[i][j];
+      }
+    // tangent coefficients
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        F[i][j] = k.F[i][j];
+        G[i][j] = k.G[i][j];
+        Cm[i][j] = T(2) * k.E[i][j] + (i == j ? T(1) : T(0));
+      }
+    T I1 = tr3(Cm);
+    T trC2 = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) trC2 += Cm[i][j] * Cm[j][i];
+    T I2 = T(0.5) * (I1 * I1 - trC2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T fc = T(0), bb = T(0);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          fc += F[i][l] * Cm[l][j];
+          bb += F[i][l] * F[j][l];
+        }
+        B[i][j] = bb;
+        R[i][j] = T(-4.0 / 3.0) * a * F[i][j] + T(-8.0 / 3.0) * b * (I1 * F[i][j] - fc);
+      }
+    cdd = T(2) * a + T(2) * b * I1;
+    gam = T(4.0 / 9.0) * a * I1 + T(16.0 / 9.0) * b * I2 + kap * (T(2) * J - T(1)) * J;
+    cff = T(4) * b;
+    cxg = T(2.0 / 3.0) * a * I1 + T(4.0 / 3.0) * b * I2 - kap * (J * J - J);
+    cm = T(-2) * b;
+  }
+  __device__ __forceinline__ void block(int i, int k, T C[3][3]) const {
+#pragma unroll
+    for (int J = 0; J < 3; ++J)
+#pragma unroll
+      for (int L = 0; L < 3; ++L)
+        C[J][L] = (i == k && J == L ? cdd : T(0)) + R[i][J] * G[k][L] + G[i][J] * R[k][L] +
+                  gam * G[i][J] * G[k][L] + cff * F[i][J] * F[k][L] + cxg * G[i][L] * G[k][J] +
+                  cm * (F[i][L] * F[k][J] + (i == k ? Cm[L][J] : T(0)) + (J == L ? B[i][k] : T(0)));
+  }
+};
+
+}  // namespace fe

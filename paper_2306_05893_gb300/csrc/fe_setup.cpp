@@ -1,0 +1,542 @@
+// Host setup, once per topology: triplet stream -> CSR pattern by two
+// transposes (Section 4.2, Table "build pattern"), the map C and its inverse,
+// projective constraints folded into the pattern (Section 5.1), consistent
+// mass, element rest data, nested-dissection ordering of the free nodes and
+// the multifrontal symbolic analysis + level schedule (Section 6.1,
+// Eq. "regional problem").  Plain C++; no CUDA.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <numeric>
+
+#include "fe_ctx.h"
+
+namespace fe {
+
+int set_error(const fe_ctx *c, int code, const std::string &msg) {
+  if (c) const_cast<fe_ctx *>(c)->err = msg;
+  return code;
+}
+
+namespace {
+
+inline double det3(const double *m) {  // row-major 3x3
+  return m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+         m[2] * (m[3] * m[7] - m[4] * m[6]);
+}
+
+inline void inv3(const double *m, double *o) {  // row-major 3x3 inverse
+  double d = det3(m);
+  o[0] = (m[4] * m[8] - m[5] * m[7]) / d;
+  o[1] = (m[2] * m[7] - m[1] * m[8]) / d;
+  o[2] = (m[1] * m[5] - m[2] * m[4]) / d;
+  o[3] = (m[5] * m[6] - m[3] * m[8]) / d;
+  o[4] = (m[0] * m[8] - m[2] * m[6]) / d;
+  o[5] = (m[2] * m[3] - m[0] * m[5]) / d;
+  o[6] = (m[3] * m[7] - m[4] * m[6]) / d;
+  o[7] = (m[1] * m[6] - m[0] * m[7]) / d;
+  o[8] = (m[0] * m[4] - m[1] * m[3]) / d;
+}
+
+// Trilinear shape-function derivatives dN[a][r] at xi (corner order a = dx+2dy+4dz).
+void hex_dshape(const double xi[3], double N[8], double dN[8][3]) {
+  for (int a = 0; a < 8; ++a) {
+    double c[3] = {double(2 * (a & 1) - 1), double(2 * ((a >> 1) & 1) - 1),
+                   double(2 * ((a >> 2) & 1) - 1)};
+    double f[3] = {1 + c[0] * xi[0], 1 + c[1] * xi[1], 1 + c[2] * xi[2]};
+    N[a] = f[0] * f[1] * f[2] / 8.0;
+    dN[a][0] = c[0] * f[1] * f[2] / 8.0;
+    dN[a][1] = c[1] * f[0] * f[2] / 8.0;
+    dN[a][2] = c[2] * f[0] * f[1] / 8.0;
+  }
+}
+
+void hex_gauss(int q, double xi[3]) {
+  const double g = 1.0 / std::sqrt(3.0);
+  xi[0] = (2 * (q & 1) - 1) * g;
+  xi[1] = (2 * ((q >> 1) & 1) - 1) * g;
+  xi[2] = (2 * ((q >> 2) & 1) - 1) * g;
+}
+
+// ------------------------------------------------------------------ pattern
+// Two transposes of the uncompressed structure: the first groups the kept
+// triplets by column (rows unsorted), the second by row with columns sorted
+// and, for equal (row, col), triplets in fill order; equal neighbours are
+// then merged into one slot.  Fixed columns are skipped in the first pass,
+// fixed rows in the second and replaced by a lone diagonal slot.
+int build_csr(fe_ctx *c) {
+  const int npe = c->npe;
+  const int64_t E = c->n_elems, n = c->n;
+  const int64_t bpe = int64_t(npe) * npe * 9;  // triplets per element
+  c->ntrip = E * bpe;
+  if (c->ntrip >= (int64_t(1) << 31)) return set_error(c, FE_ERR_ARG, "too many triplets for int32 ids");
+  const int32_t *conn = c->conn.data();
+  const int8_t *fx = c->fixed_dof.data();
+  auto rc = [&](int64_t t, int32_t &row, int32_t &col) {
+    int64_t e = t / bpe, r = t % bpe;
+    int blk = int(r / 9), ik = int(r % 9);
+    int a = blk / npe, b = blk % npe;
+    row = 3 * conn[e * npe + a] + ik / 3;
+    col = 3 * conn[e * npe + b] + ik % 3;
+  };
+  // first transpose: X^T in the uncompressed structure
+  std::vector<int64_t> colptr(n + 1, 0);
+  for (int64_t t = 0; t < c->ntrip; ++t) {
+    int32_t r, k;
+    rc(t, r, k);
+    if (!fx[r] && !fx[k]) colptr[k + 1]++;
+  }
+  for (int64_t j = 0; j < n; ++j) colptr[j + 1] += colptr[j];
+  const int64_t kept = colptr[n];
+  std::vector<int32_t> xt_row(kept), xt_t(kept);
+  {
+    std::vector<int64_t> next(colptr.begin(), colptr.end() - 1);
+    for (int64_t t = 0; t < c->ntrip; ++t) {
+      int32_t r, k;
+      rc(t, r, k);
+      if (fx[r] || fx[k]) continue;
+      int64_t p = next[k]++;
+      xt_row[p] = r;
+      xt_t[p] = int32_t(t);
+    }
+  }
+  // second transpose: X = (X^T)^T, rows sorted, columns sorted, uncompressed
+  std::vector<int64_t> rp(n + 1, 0);
+  for (int64_t p = 0; p < kept; ++p) rp[xt_row[p] + 1]++;
+  for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+  std::vector<int32_t> x_col(kept);
+  c->slot_src.assign(kept, 0);
+  {
+    std::vector<int64_t> next(rp.begin(), rp.end() - 1);
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+        int64_t q = next[xt_row[p]]++;
+        x_col[q] = int32_t(j);
+        c->slot_src[q] = xt_t[p];
+      }
+  }
+  std::vector<int32_t>().swap(xt_row);
+  std::vector<int32_t>().swap(xt_t);
+  // merge duplicates -> CSR, C and the inverse map (slot_ptr, slot_src)
+  c->rowptr.assign(n + 1, 0);
+  c->colind.clear();
+  c->colind.reserve(kept / 4 + n);
+  c->slot_ptr.clear();
+  c->slot_ptr.reserve(kept / 4 + n + 1);
+  c->C.assign(c->ntrip, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    c->rowptr[i] = int32_t(c->colind.size());
+    if (fx[i]) {  // projected row: lone diagonal, no triplet maps to it
+      c->slot_ptr.push_back(rp[i]);
+      c->colind.push_back(int32_t(i));
+      continue;
+    }
+    int32_t last = -1;
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+      if (x_col[q] != last) {
+        last = x_col[q];
+        c->slot_ptr.push_back(q);
+        c->colind.push_back(last);
+      }
+      c->C[c->slot_src[q]] = int32_t(c->colind.size() - 1);
+    }
+  }
+  c->nnz = int64_t(c->colind.size());
+  if (c->nnz >= (int64_t(1) << 31)) return set_error(c, FE_ERR_ARG, "nnz exceeds int32");
+  c->rowptr[n] = int32_t(c->nnz);
+  c->slot_ptr.push_back(kept);
+  return FE_OK;
+}
+
+// --------------------------------------------------------- mass, rest data
+int build_mass_and_rest(fe_ctx *c) {
+  const int npe = c->npe;
+  const int64_t E = c->n_elems;
+  const double *X = c->X.data();
+  std::vector<double> me(size_t(E) * npe * npe);  // scalar consistent-mass blocks
+  if (c->elem_type == FE_TET4) {
+    c->rest_ncoef = 10;  // Dm^{-1} rows (grad N_1..3), volume
+    c->rest.assign(size_t(10) * E, 0.0);
+    for (int64_t e = 0; e < E; ++e) {
+      const int32_t *cn = &c->conn[e * 4];
+      double Dm[9];
+      for (int i = 0; i < 3; ++i)
+        for (int col = 0; col < 3; ++col) Dm[3 * i + col] = X[3 * cn[col + 1] + i] - X[3 * cn[0] + i];
+      double V = det3(Dm) / 6.0;
+      if (!(V > 0)) return set_error(c, FE_ERR_INVERTED, "tet " + std::to_string(e) + " has non-positive rest volume");
+      double G[9];
+      inv3(Dm, G);
+      for (int k = 0; k < 9; ++k) c->rest[size_t(k) * E + e] = G[k];
+      c->rest[size_t(9) * E + e] = V;
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) me[(e * 4 + a) * 4 + b] = c->rho * V / 20.0 * (a == b ? 2.0 : 1.0);
+    }
+  } else {
+    c->rest_ncoef = 200;  // per Gauss point: grad N (8 x 3), w det J0
+    c->rest.assign(size_t(200) * E, 0.0);
+    for (int64_t e = 0; e < E; ++e) {
+      const int32_t *cn = &c->conn[e * 8];
+      for (int a = 0; a < 64; ++a) me[e * 64 + a] = 0.0;
+      for (int q = 0; q < 8; ++q) {
+        double xi[3], N[8], dN[8][3];
+        hex_gauss(q, xi);
+        hex_dshape(xi, N, dN);
+        double J0[9] = {0};
+        for (int a = 0; a < 8; ++a)
+          for (int i = 0; i < 3; ++i)
+            for (int r = 0; r < 3; ++r) J0[3 * i + r] += X[3 * cn[a] + i] * dN[a][r];
+        double dj = det3(J0);
+        if (!(dj > 0)) return set_error(c, FE_ERR_INVERTED, "hex " + std::to_string(e) + " has non-positive rest Jacobian");
+        double Ji[9];
+        inv3(J0, Ji);
+        for (int a = 0; a < 8; ++a)
+          for (int J = 0; J < 3; ++J) {
+            double g = 0;
+            for (int r = 0; r < 3; ++r) g += dN[a][r] * Ji[3 * r + J];
+            c->rest[size_t(q * 25 + 3 * a + J) * E + e] = g;
+          }
+        c->rest[size_t(q * 25 + 24) * E + e] = dj;
+        for (int a = 0; a < 8; ++a)
+          for (int b = 0; b < 8; ++b) me[e * 64 + a * 8 + b] += c->rho * dj * N[a] * N[b];
+      }
+    }
+  }
+  // mass values on the pattern: gather through the inverse map (ascending t)
+  c->mass.assign(c->nnz, 0.0);
+  const int64_t bpe = int64_t(npe) * npe * 9;
+  for (int64_t s = 0; s < c->nnz; ++s) {
+    double acc = 0.0;
+    for (int64_t q = c->slot_ptr[s]; q < c->slot_ptr[s + 1]; ++q) {
+      int64_t t = c->slot_src[q];
+      int64_t e = t / bpe, r = t % bpe;
+      int blk = int(r / 9), ik = int(r % 9);
+      if (ik / 3 == ik % 3) acc += me[e * npe * npe + blk];
+    }
+    c->mass[s] = acc;
+  }
+  // node incidence lists (element-major, ascending) for the force gather
+  c->node_ptr.assign(c->n_nodes + 1, 0);
+  for (int64_t k = 0; k < E * npe; ++k) c->node_ptr[c->conn[k] + 1]++;
+  for (int64_t i = 0; i < c->n_nodes; ++i) c->node_ptr[i + 1] += c->node_ptr[i];
+  c->node_src.assign(E * npe, 0);
+  std::vector<int32_t> next(c->node_ptr.begin(), c->node_ptr.end() - 1);
+  for (int64_t k = 0; k < E * npe; ++k) c->node_src[next[c->conn[k]]++] = int32_t(k);
+  return FE_OK;
+}
+
+// ------------------------------------------------------- nested dissection
+struct ND {
+  fe_ctx *c;
+  std::vector<std::vector<int32_t>> adj;   // free-node graph
+  std::vector<int32_t> order;              // new node position -> node
+  std::vector<int32_t> tag;
+  int32_t stamp = 0;
+  int leaf = 64;
+  struct F { int32_t first, count, parent = -1; std::vector<int32_t> kids; };
+  std::vector<F> fr;
+
+  int32_t make_front(std::vector<int32_t> &S) {
+    std::sort(S.begin(), S.end());
+    F f;
+    f.first = int32_t(order.size());
+    f.count = int32_t(S.size());
+    order.insert(order.end(), S.begin(), S.end());
+    fr.push_back(f);
+    return int32_t(fr.size() - 1);
+  }
+
+  std::vector<int32_t> build(std::vector<int32_t> S) {
+    if (S.empty()) return {};
+    if (int(S.size()) <= leaf) return {make_front(S)};
+    // longest axis of the rest bounding box
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int32_t v : S)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], c->X[3 * v + d]);
+        hi[d] = std::max(hi[d], c->X[3 * v + d]);
+      }
+    int ax = 0;
+    for (int d = 1; d < 3; ++d)
+      if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
+    std::vector<std::pair<double, int32_t>> key(S.size());
+    for (size_t i = 0; i < S.size(); ++i) key[i] = {c->X[3 * S[i] + ax], S[i]};
+    std::sort(key.begin(), key.end());
+    // split at the widest coordinate gap near the median (a grid layer boundary)
+    int64_t N = int64_t(S.size()), mid = N / 2, w = std::max<int64_t>(1, N / 8);
+    int64_t best = mid;
+    double bgap = -1.0;
+    for (int64_t s = std::max<int64_t>(1, mid - w); s <= std::min<int64_t>(N - 1, mid + w); ++s) {
+      double g = key[s].first - key[s - 1].first;
+      if (g > bgap + 1e-15 * (std::fabs(key[s].first) + 1) ||
+          (std::fabs(g - bgap) <= 1e-15 * (std::fabs(key[s].first) + 1) &&
+           std::llabs(s - mid) < std::llabs(best - mid))) {
+        bgap = g;
+        best = s;
+      }
+    }
+    // side tags: 1 = left, 2 = right
+    int32_t sL = ++stamp, sR = ++stamp;
+    for (int64_t i = 0; i < N; ++i) tag[key[i].second] = (i < best) ? sL : sR;
+    std::vector<int32_t> bL, bR, L, R;
+    for (int64_t i = 0; i < N; ++i) {
+      int32_t v = key[i].second;
+      int32_t other = (i < best) ? sR : sL;
+      bool touch = false;
+      for (int32_t u : adj[v])
+        if (tag[u] == other) { touch = true; break; }
+      if (i < best) { L.push_back(v); if (touch) bL.push_back(v); }
+      else { R.push_back(v); if (touch) bR.push_back(v); }
+    }
+    std::vector<int32_t> sep, L2, R2;
+    if (bR.size() <= bL.size()) {
+      sep = bR;
+      int32_t ss = ++stamp;
+      for (int32_t v : sep) tag[v] = ss;
+      L2 = L;
+      for (int32_t v : R) if (tag[v] != ss) R2.push_back(v);
+    } else {
+      sep = bL;
+      int32_t ss = ++stamp;
+      for (int32_t v : sep) tag[v] = ss;
+      R2 = R;
+      for (int32_t v : L) if (tag[v] != ss) L2.push_back(v);
+    }
+    if (L2.empty() && R2.empty()) return {make_front(S)};
+    std::vector<int32_t> kids = build(L2);
+    std::vector<int32_t> kr = build(R2);
+    kids.insert(kids.end(), kr.begin(), kr.end());
+    if (sep.empty()) return kids;  // disconnected halves: independent subtrees
+    int32_t f = make_front(sep);
+    for (int32_t k : kids) { fr[k].parent = f; fr[f].kids.push_back(k); }
+    return {f};
+  }
+};
+
+int build_ordering(fe_ctx *c) {
+  const int npe = c->npe;
+  const int64_t nn = c->n_nodes;
+  std::vector<int8_t> fixed_node(nn, 0);
+  for (int32_t v : c->fixed_nodes) fixed_node[v] = 1;
+  ND nd;
+  nd.c = c;
+  nd.leaf = c->opt.nd_leaf_nodes > 0 ? c->opt.nd_leaf_nodes : 64;
+  nd.adj.assign(nn, {});
+  for (int64_t e = 0; e < c->n_elems; ++e)
+    for (int a = 0; a < npe; ++a) {
+      int32_t va = c->conn[e * npe + a];
+      if (fixed_node[va]) continue;
+      for (int b = 0; b < npe; ++b) {
+        int32_t vb = c->conn[e * npe + b];
+        if (b != a && !fixed_node[vb]) nd.adj[va].push_back(vb);
+      }
+    }
+  for (auto &l : nd.adj) {
+    std::sort(l.begin(), l.end());
+    l.erase(std::unique(l.begin(), l.end()), l.end());
+  }
+  nd.tag.assign(nn, 0);
+  std::vector<int32_t> S;
+  for (int64_t v = 0; v < nn; ++v)
+    if (!fixed_node[v]) S.push_back(int32_t(v));
+  nd.build(S);
+  const int64_t nfree_nodes = int64_t(nd.order.size());
+  std::vector<int32_t> pos(nn, -1);
+  for (int64_t i = 0; i < nfree_nodes; ++i) pos[nd.order[i]] = int32_t(i);
+
+  // DOF permutation: new DOF 3*pos + comp <-> original 3*node + comp
+  c->n_free = 3 * nfree_nodes;
+  c->perm.assign(c->n_free, 0);
+  c->iperm.assign(c->n, -1);
+  for (int64_t i = 0; i < nfree_nodes; ++i)
+    for (int k = 0; k < 3; ++k) {
+      c->perm[3 * i + k] = 3 * nd.order[i] + k;
+      c->iperm[3 * nd.order[i] + k] = int32_t(3 * i + k);
+    }
+
+  // multifrontal symbolic analysis on nodes (fronts are in postorder)
+  const int64_t nf = int64_t(nd.fr.size());
+  std::vector<std::vector<int32_t>> upd(nf);  // update node positions, ascending
+  std::vector<int32_t> mark(nfree_nodes, -1);
+  for (int64_t f = 0; f < nf; ++f) {
+    const auto &F = nd.fr[f];
+    int32_t last = F.first + F.count - 1;
+    std::vector<int32_t> &U = upd[f];
+    for (int32_t i = F.first; i <= last; ++i)
+      for (int32_t u : nd.adj[nd.order[i]]) {
+        int32_t pu = pos[u];
+        if (pu > last && mark[pu] != f) { mark[pu] = int32_t(f); U.push_back(pu); }
+      }
+    for (int32_t k : F.kids)
+      for (int32_t pu : upd[k])
+        if (pu > last && mark[pu] != f) { mark[pu] = int32_t(f); U.push_back(pu); }
+    std::sort(U.begin(), U.end());
+  }
+  c->fronts.assign(nf, Front());
+  int64_t f_total = 0, y_total = 0, w_total = 0, u_total = 0, rows_total = 0;
+  for (int64_t f = 0; f < nf; ++f) {
+    Front &F = c->fronts[f];
+    F.first = 3 * nd.fr[f].first;
+    F.npiv = 3 * nd.fr[f].count;
+    F.nupd = 3 * int32_t(upd[f].size());
+    F.parent = nd.fr[f].parent;
+    int lv = 0;
+    for (int32_t k : nd.fr[f].kids) lv = std::max(lv, c->fronts[k].level + 1);
+    F.level = lv;
+    int64_t m = F.m();
+    F.f_off = f_total; f_total += m * m;
+    F.y_off = y_total; y_total += m * F.npiv;
+    F.w_off = w_total; w_total += m;
+    F.u_off = u_total; u_total += F.nupd;
+    F.rows_off = rows_total; rows_total += F.nupd;
+  }
+  c->f_total = f_total; c->y_total = y_total; c->w_total = w_total; c->u_total = u_total;
+  c->upd_rows_new.assign(rows_total, 0);
+  c->upd_rows_old.assign(rows_total, 0);
+  for (int64_t f = 0; f < nf; ++f) {
+    const Front &F = c->fronts[f];
+    for (size_t j = 0; j < upd[f].size(); ++j)
+      for (int k = 0; k < 3; ++k) {
+        int32_t nw = 3 * upd[f][j] + k;
+        c->upd_rows_new[F.rows_off + 3 * j + k] = nw;
+        c->upd_rows_old[F.rows_off + 3 * j + k] = c->perm[nw];
+      }
+  }
+  // children lists and child -> parent relative maps
+  c->child_ptr.assign(nf + 1, 0);
+  for (int64_t f = 0; f < nf; ++f) c->child_ptr[f + 1] = int32_t(nd.fr[f].kids.size());
+  for (int64_t f = 0; f < nf; ++f) c->child_ptr[f + 1] += c->child_ptr[f];
+  c->child_list.assign(c->child_ptr[nf], 0);
+  for (int64_t f = 0; f < nf; ++f)
+    for (size_t k = 0; k < nd.fr[f].kids.size(); ++k) c->child_list[c->child_ptr[f] + k] = nd.fr[f].kids[k];
+  c->rmap.assign(rows_total, 0);
+  for (int64_t f = 0; f < nf; ++f) {
+    Front &F = c->fronts[f];
+    F.rmap_off = F.rows_off;
+    if (F.parent < 0) continue;
+    const Front &P = c->fronts[F.parent];
+    const int32_t *prow = &c->upd_rows_new[P.rows_off];
+    for (int32_t j = 0; j < F.nupd; ++j) {
+      int32_t nw = c->upd_rows_new[F.rows_off + j];
+      int32_t loc;
+      if (nw >= P.first && nw < P.first + P.npiv) {
+        loc = nw - P.first;
+      } else {
+        const int32_t *it = std::lower_bound(prow, prow + P.nupd, nw);
+        if (it == prow + P.nupd || *it != nw)
+          return set_error(c, FE_ERR_ARG, "symbolic analysis: update row missing in parent");
+        loc = P.npiv + int32_t(it - prow);
+      }
+      c->rmap[F.rows_off + j] = loc;
+    }
+  }
+  // A entries of every front (lower triangle in the new order), by column
+  c->fa_ptr.assign(nf + 1, 0);
+  c->fa_slot.clear();
+  c->fa_off.clear();
+  c->fa_colptr.clear();
+  for (int64_t f = 0; f < nf; ++f) {
+    const Front &F = c->fronts[f];
+    const int32_t m = F.m();
+    const int32_t *prow = &c->upd_rows_new[F.rows_off];
+    c->fa_ptr[f] = int64_t(c->fa_slot.size());
+    for (int32_t jl = 0; jl < F.npiv; ++jl) {
+      c->fa_colptr.push_back(int64_t(c->fa_slot.size()));
+      int32_t jn = F.first + jl, jo = c->perm[jn];
+      for (int32_t k = c->rowptr[jo]; k < c->rowptr[jo + 1]; ++k) {
+        int32_t in = c->iperm[c->colind[k]];
+        if (in < jn) continue;
+        int32_t lr;
+        if (in < F.first + F.npiv) {
+          lr = in - F.first;
+        } else {
+          const int32_t *it = std::lower_bound(prow, prow + F.nupd, in);
+          if (it == prow + F.nupd || *it != in)
+            return set_error(c, FE_ERR_ARG, "symbolic analysis: A entry outside its front");
+          lr = F.npiv + int32_t(it - prow);
+        }
+        c->fa_slot.push_back(k);
+        c->fa_off.push_back(lr + jl * m);
+      }
+    }
+    c->fa_colptr.push_back(int64_t(c->fa_slot.size()));
+  }
+  c->fa_ptr[nf] = int64_t(c->fa_slot.size());
+  if (c->f_total >= (int64_t(1) << 40)) return set_error(c, FE_ERR_OOM, "front storage too large");
+
+  // public views
+  c->front_first.resize(nf); c->front_npiv.resize(nf); c->front_nupd.resize(nf);
+  c->front_parent.resize(nf); c->front_level.resize(nf);
+  int maxlv = 0;
+  for (int64_t f = 0; f < nf; ++f) {
+    c->front_first[f] = c->fronts[f].first;
+    c->front_npiv[f] = c->fronts[f].npiv;
+    c->front_nupd[f] = c->fronts[f].nupd;
+    c->front_parent[f] = c->fronts[f].parent;
+    c->front_level[f] = c->fronts[f].level;
+    maxlv = std::max(maxlv, c->fronts[f].level);
+  }
+
+  // level schedule and static task lists
+  c->levels.assign(nf ? maxlv + 1 : 0, Level());
+  for (int64_t f = 0; f < nf; ++f) c->levels[c->fronts[f].level].fronts.push_back(int32_t(f));
+  double flops = 0;
+  for (auto &L : c->levels) {
+    int steps = 0;
+    for (int32_t f : L.fronts) steps = std::max(steps, (c->fronts[f].npiv + kNB - 1) / kNB);
+    L.steps = steps;
+    L.diag.assign(steps, {});
+    L.panel.assign(steps, {});
+    L.trail.assign(steps, {});
+    for (int32_t f : L.fronts) {
+      const Front &F = c->fronts[f];
+      const int32_t m = F.m(), p = F.npiv;
+      for (int32_t c0 = 0; c0 < m; c0 += 32) {
+        L.asm_tasks.push_back(f);
+        L.asm_tasks.push_back(c0);
+        L.asm_tasks.push_back(std::min(m, c0 + 32));
+      }
+      for (int32_t r0 = 0; r0 < m; r0 += kApplyRows) { L.fwd_tasks.push_back(f); L.fwd_tasks.push_back(r0); }
+      for (int32_t c0 = 0; c0 < p; c0 += 8) { L.bwd_tasks.push_back(f); L.bwd_tasks.push_back(c0); }
+      for (int s = 0; s * kNB < p; ++s) {
+        const int32_t k0 = s * kNB, kb = std::min(kNB, p - k0), k1 = k0 + kb;
+        auto push = [](std::vector<int32_t> &v, int32_t a, int32_t b, int32_t cc, int32_t d) {
+          v.push_back(a); v.push_back(b); v.push_back(cc); v.push_back(d);
+        };
+        push(L.diag[s], f, (T_DIAG << 24) | k0, kb, 0);
+        for (int32_t r0 = k1; r0 < m; r0 += kTile) push(L.panel[s], f, (T_PANEL << 24) | k0, r0, 0);
+        for (int32_t c0 = 0; c0 < k0; c0 += kTile) push(L.panel[s], f, (T_XK << 24) | k0, c0, 0);
+        for (int32_t j0 = k1; j0 < m; j0 += kTile)
+          for (int32_t i0 = j0; i0 < m; i0 += kTile) push(L.trail[s], f, (T_TRAIL << 24) | k0, i0, j0);
+        for (int32_t i0 = k1; i0 < m; i0 += kTile)
+          for (int32_t c0 = 0; c0 < k1; c0 += kTile) push(L.trail[s], f, (T_RUPD << 24) | k0, i0, c0);
+        double rem = double(m - k1);
+        flops += double(kb) * kb * kb / 3.0 * 2.0            // diag LDL^T + inverse
+                 + 2.0 * rem * kb * kb                        // panel
+                 + 2.0 * double(kb) * kb * k0                 // X_K
+                 + rem * (rem + 1.0) * kb                     // trailing (lower)
+                 + 2.0 * rem * double(k1) * kb;               // Y update
+      }
+    }
+  }
+  c->factor_flops = flops;
+  return FE_OK;
+}
+
+}  // namespace
+
+int build_pattern_host(fe_ctx *c) {
+  c->n = 3 * c->n_nodes;
+  c->fixed_dof.assign(c->n, 0);
+  for (int32_t v : c->fixed_nodes)
+    for (int k = 0; k < 3; ++k) c->fixed_dof[3 * int64_t(v) + k] = 1;
+  int st = build_csr(c);
+  if (st) return st;
+  st = build_mass_and_rest(c);
+  if (st) return st;
+  st = build_ordering(c);
+  if (st) return st;
+  c->built = true;
+  return FE_OK;
+}
+
+}  // namespace fe

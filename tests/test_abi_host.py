@@ -1,0 +1,150 @@
+"""CPU tests of the C-ABI library: symbols, and the host setup (Section 4.2
+pattern + map C by two transposes, Section 5.1 constraints, Section 6.1
+nested dissection and multifrontal structure) against the oracle."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+import fe_inputs as fi
+from oracle import fe_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fe():
+    from paper_2306_05893_gb300 import build
+    build.build()
+    import paper_2306_05893_gb300 as fe
+    fe.load()
+    return fe
+
+
+def test_library_exports_every_declared_symbol(fe):
+    header = open(os.path.join(ROOT, "include", "fe_hotpath.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char \*)\s*(fe_\w+)\s*\(", header, re.M))
+    assert {"fe_create", "fe_step", "fe_build_pattern", "fe_destroy"} <= declared
+    lib = ct.CDLL(fe.lib_path())
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    from paper_2306_05893_gb300 import _abi
+    assert declared == set(_abi.SIGNATURES), declared ^ set(_abi.SIGNATURES)
+
+
+def test_create_rejects_bad_input(fe):
+    mesh = fi.tet_beam(1, 1, 1)
+    conn = mesh.conn.copy()
+    conn[0, 0] = 10_000
+    with pytest.raises(fe.FEError):
+        fe.fe_create(0, mesh.X, conn, mesh.fixed_nodes, 0, 1000.0, [1.0, 1.0, 0.0], 0.01, 0.1, 0.01)
+    with pytest.raises(fe.FEError):
+        fe.fe_create(0, mesh.X, mesh.conn, mesh.fixed_nodes, 0, 1000.0, [1.0, 1.0, 0.0], -1.0, 0.1, 0.01)
+
+
+def _ctx(fe, mesh, **kw):
+    return fe.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, 0, 1000.0,
+                        [1e3, 1e4, 0.0], 0.01, 0.1, 0.01, **kw)
+
+
+MESHES = {
+    "tet-2x3x4": lambda: fi.tet_beam(2, 3, 4),
+    "tet-4x4x16": lambda: fi.tet_beam(4, 4, 16),
+    "hex-2x3x4-jitter": lambda: fi.hex_beam(2, 3, 4, jitter=0.1),
+    "hex-3x3x7": lambda: fi.hex_beam(3, 3, 7),
+    "tet-1x1x1-nofix": lambda: fi.TetBeam(1, 1, 1, fi.tet_beam(1, 1, 1).X, fi.tet_beam(1, 1, 1).conn,
+                                          np.zeros(0, np.int32)),
+}
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_pattern_and_map_bit_exact(fe, name):
+    mesh = MESHES[name]()
+    ctx = _ctx(fe, mesh)
+    n = 3 * mesh.n_nodes
+    fixed = (3 * mesh.fixed_nodes[:, None] + np.arange(3)).reshape(-1)
+    rp, ci, C = O.csr_pattern(n, mesh.conn, fixed)
+    np.testing.assert_array_equal(ctx.rowptr, rp)
+    np.testing.assert_array_equal(ctx.colind, ci)
+    np.testing.assert_array_equal(ctx.C, C)
+    # inverse map: every kept triplet once, slots ascending, ids ascending in a slot
+    slot_ptr, slot_src = ctx.inverse_map()
+    kept = np.nonzero(C >= 0)[0]
+    assert slot_src.size == kept.size
+    np.testing.assert_array_equal(np.sort(slot_src), kept)
+    for s in range(0, ctx.nnz, max(1, ctx.nnz // 200)):
+        seg = slot_src[slot_ptr[s]:slot_ptr[s + 1]]
+        assert np.all(C[seg] == s)
+        assert np.all(np.diff(seg) > 0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["tet-2x3x4", "hex-2x3x4-jitter"])
+def test_mass_on_pattern(fe, name):
+    mesh = MESHES[name]()
+    ctx = _ctx(fe, mesh)
+    m = O.Model(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, 0, (1, 1, 0), 1000.0, .01, .1, .01)
+    fixed = m.fixed_dofs
+    Mp = O.project(m.M, fixed)
+    expect = O.values_in_pattern(Mp, ctx.rowptr, ctx.colind)
+    fixed_rows = np.zeros(ctx.n, bool)
+    fixed_rows[fixed] = True
+    slot_row = np.repeat(np.arange(ctx.n), np.diff(ctx.rowptr))
+    expect[fixed_rows[slot_row]] = 0.0   # the library keeps 0 mass on projected rows
+    np.testing.assert_allclose(ctx.mass(), expect, rtol=1e-13, atol=1e-18)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name,leaf", [("tet-4x4x16", 8), ("tet-4x4x16", 64), ("hex-3x3x7", 4),
+                                       ("hex-2x3x4-jitter", 6)])
+def test_nested_dissection_structure(fe, name, leaf):
+    """perm is a permutation of the free DOFs; fronts are contiguous pivot
+    blocks in postorder; every A entry couples a front with itself or with
+    an ancestor (the separator property of Eq. "regional problem"), and lies
+    in the column front's pivot or update rows."""
+    mesh = MESHES[name]()
+    ctx = _ctx(fe, mesh, nd_leaf_nodes=leaf)
+    o = ctx.ordering()
+    perm, first, npiv, parent, level = o["perm"], o["first"], o["npiv"], o["parent"], o["level"]
+    n = ctx.n
+    fixed = np.zeros(n, bool)
+    fixed[(3 * mesh.fixed_nodes[:, None] + np.arange(3)).reshape(-1)] = True
+    np.testing.assert_array_equal(np.sort(perm), np.nonzero(~fixed)[0])
+    nf = first.size
+    assert first[0] == 0 and np.all(first[1:] == first[:-1] + npiv[:-1])
+    assert first[-1] + npiv[-1] == perm.size
+    for f in range(nf):
+        if parent[f] >= 0:
+            assert parent[f] > f and level[parent[f]] > level[f]
+    iperm = -np.ones(n, np.int64)
+    iperm[perm] = np.arange(perm.size)
+    front_of = np.repeat(np.arange(nf), npiv)
+    anc = [set() for _ in range(nf)]
+    for f in range(nf - 1, -1, -1):
+        p = parent[f]
+        anc[f] = {f} | (anc[p] if p >= 0 else set())
+    rows_of = [set(ctx_rows.tolist()) for ctx_rows in (fe.fe_get_front_rows(ctx.ctx, f) for f in range(nf))]
+    slot_row = np.repeat(np.arange(n), np.diff(ctx.rowptr))
+    for s in range(ctx.nnz):
+        i, j = slot_row[s], ctx.colind[s]
+        if fixed[i] or fixed[j]:
+            continue
+        fi_, fj = front_of[iperm[i]], front_of[iperm[j]]
+        assert fi_ in anc[fj] or fj in anc[fi_]
+        if iperm[i] > iperm[j] and fi_ != fj:       # lower entry outside the pivot block
+            assert i in rows_of[fj]
+    ctx.close()
+
+
+def test_device_calls_fail_loudly_without_gpu(fe):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    mesh = fi.tet_beam(1, 1, 2)
+    ctx = _ctx(fe, mesh)
+    with pytest.raises(fe.FEError) as ei:
+        ctx.step(np.zeros(ctx.n))
+    assert ei.value.status == 2
+    ctx.close()

@@ -1,0 +1,216 @@
+"""GPU parity: every stage of the CUDA path against the FP64 oracle, through
+the C ABI, on seeded meshes that span several tiles and ragged tails.
+
+Tolerances (relative to the largest entry of the oracle quantity):
+  FP64 path: element outputs and assembled A, b <= 1e-12 (same sums, other
+  rounding order); positions after N steps <= 1e-8 of the displacement.
+  Mixed path (FP32 element kernel, matrix, factor; FP64 residual): element
+  outputs <= 2e-5 (FP32 rounding of the contraction), A, b <= 2e-5; positions
+  after N steps <= 1e-4 of the displacement (the FP32 tangent perturbs A by
+  ~1e-7 relative; the residual is still driven to 1e-8 by FP64 refinement).
+"""
+import numpy as np
+import pytest
+
+import fe_inputs as fi
+from oracle import fe_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+LAWS = {fi.SVK: (3.4e3, 3.1e4, 0.0), fi.NEOHOOKE: (3.4e3, 3.1e4, 0.0),
+        fi.MOONEY_RIVLIN: (1.5e3, 5e2, 5e4)}
+
+
+def _mesh(kind):
+    return fi.tet_beam(3, 4, 9) if kind == "tet" else fi.hex_beam(3, 3, 7, jitter=0.1, seed=4)
+
+
+def _state(mesh, amp=0.05, seed=0):
+    rng = np.random.default_rng(seed)
+    q = mesh.X.reshape(-1) + amp * 0.01 * rng.standard_normal(mesh.X.size)
+    fixed = (3 * mesh.fixed_nodes[:, None] + np.arange(3)).reshape(-1)
+    q[fixed] = mesh.X.reshape(-1)[fixed]
+    v = 0.01 * rng.standard_normal(mesh.X.size)
+    v[fixed] = 0.0
+    p = 0.1 * rng.standard_normal(mesh.X.size)
+    return q, v, p
+
+
+def _ctx(fe, mesh, law, precision, **kw):
+    return fe.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, law, 1000.0, LAWS[law],
+                        0.01, 0.1, 0.01, precision=precision, **kw)
+
+
+@pytest.mark.parametrize("kind", ["tet", "hex"])
+@pytest.mark.parametrize("law", [fi.SVK, fi.NEOHOOKE, fi.MOONEY_RIVLIN])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_element_kernel(gpu_lib, kind, law, precision):
+    mesh = _mesh(kind)
+    q, _, _ = _state(mesh)
+    ctx = _ctx(gpu_lib, mesh, law, precision)
+    f, K = ctx.element_eval(q)
+    m = O.Model(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, law, LAWS[law], 1000., .01, .1, .01)
+    fo = m.element_force(q)
+    Ko = O.element_values_fill_order(m.element_tangent(q))
+    tol = 1e-12 if precision == 0 else 2e-5
+    assert np.abs(f - fo).max() <= tol * np.abs(fo).max()
+    assert np.abs(K - Ko).max() <= tol * np.abs(Ko).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind,law", [("tet", fi.SVK), ("tet", fi.MOONEY_RIVLIN), ("hex", fi.NEOHOOKE)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_assembly(gpu_lib, kind, law, precision):
+    mesh = _mesh(kind)
+    q, v, p = _state(mesh, seed=1)
+    ctx = _ctx(gpu_lib, mesh, law, precision)
+    ctx.set_state(q, v)
+    A, b = ctx.assemble(p)
+    m = O.Model(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, law, LAWS[law], 1000., .01, .1, .01)
+    Ao, bo = m.system(q, v, p)
+    Av = O.values_in_pattern(Ao, ctx.rowptr, ctx.colind)
+    tol = 1e-12 if precision == 0 else 2e-5
+    assert np.abs(A - Av).max() <= tol * np.abs(Av).max()
+    assert np.abs(b - bo).max() <= tol * np.abs(bo).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind,leaf", [("tet", 64), ("tet", 8), ("hex", 16), ("hex", 4)])
+def test_exact_factor_inverts_A(gpu_lib, kind, leaf):
+    """FP64 LDL^T of the current A applied level by level is A^{-1}."""
+    mesh = _mesh(kind)
+    q, v, p = _state(mesh, seed=2)
+    ctx = _ctx(gpu_lib, mesh, fi.NEOHOOKE, 0, nd_leaf_nodes=leaf)
+    ctx.set_state(q, v)
+    A, _ = ctx.assemble(p)
+    ctx.factor_now()
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal(ctx.n)
+    fixed = (3 * mesh.fixed_nodes[:, None] + np.arange(3)).reshape(-1)
+    r[fixed] = 0.0
+    z = ctx.apply_preconditioner(r)
+    import scipy.sparse as sp
+    S = sp.csr_matrix((A, ctx.colind, ctx.rowptr), shape=(ctx.n, ctx.n))
+    zo = O.direct_solve(S, r)
+    assert np.linalg.norm(z - zo) <= 1e-9 * np.linalg.norm(zo)
+    assert np.all(z[fixed] == 0.0)
+    ctx.close()
+
+
+def test_mixed_factor_is_a_close_preconditioner(gpu_lib):
+    mesh = _mesh("tet")
+    q, v, p = _state(mesh, seed=5)
+    ctx = _ctx(gpu_lib, mesh, fi.MOONEY_RIVLIN, 1)
+    ctx.set_state(q, v)
+    A, _ = ctx.assemble(p)
+    ctx.factor_now()
+    r = np.random.default_rng(4).standard_normal(ctx.n)
+    r[(3 * mesh.fixed_nodes[:, None] + np.arange(3)).reshape(-1)] = 0.0
+    z = ctx.apply_preconditioner(r)
+    import scipy.sparse as sp
+    S = sp.csr_matrix((A, ctx.colind, ctx.rowptr), shape=(ctx.n, ctx.n))
+    assert np.linalg.norm(S @ z - r) <= 1e-3 * np.linalg.norm(r)
+    ctx.close()
+
+
+def _rollout_pair(fe, wl, steps, **kw):
+    ctx = fe.FEContext.from_workload(wl, **kw)
+    om = O.Model.from_workload(wl)
+    q = wl.mesh.X.reshape(-1).copy()
+    v = np.zeros_like(q)
+    qg = np.empty_like(q)
+    vg = np.empty_like(q)
+    infos = []
+    for t in range(steps):
+        p = wl.p(t).reshape(-1)
+        infos.append(ctx.step(p, qg, vg))
+        q, v, _ = om.step(q, v, p)
+    ctx.close()
+    return qg, vg, q, v, infos
+
+
+def test_rollout_tet_svk_fp64_exact_factor(gpu_lib):
+    """The small FP64 tet beam, 10 steps, exact LDL^T every step (R = 1)."""
+    wl = fi.workload("tet4x4x16-svk-fp64")
+    qg, vg, qo, vo, infos = _rollout_pair(gpu_lib, wl, 10)
+    X = wl.mesh.X.reshape(-1)
+    assert np.linalg.norm(qg - qo) <= 1e-8 * np.linalg.norm(qo - X)
+    assert np.linalg.norm(vg - vo) <= 1e-8 * np.linalg.norm(vo)
+    assert all(i.iters <= 2 for i in infos), [i.iters for i in infos]
+    assert all(i.rel_residual <= 1e-10 for i in infos)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-4)])
+def test_rollout_tet_mr_lagged(gpu_lib, precision, tol):
+    """Mooney-Rivlin tet beam with gravity + end traction, lagged factor R = 5."""
+    wl = fi.workload("tet-mr", a=4, b=4, c=12)
+    wl.precision = precision
+    qg, vg, qo, vo, infos = _rollout_pair(gpu_lib, wl, 8)
+    X = wl.mesh.X.reshape(-1)
+    err = np.linalg.norm(qg - qo) / np.linalg.norm(qo - X)
+    assert err <= tol, err
+    assert all(i.rel_residual <= 1e-8 for i in infos)
+    ages = [i.factor_age for i in infos]
+    assert ages[:7] == [0, 1, 2, 3, 4, 5, 1], ages
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-4)])
+def test_rollout_hex_nh(gpu_lib, precision, tol):
+    wl = fi.workload("hex-nh", a=3, b=3, c=10)
+    wl.precision = precision
+    qg, vg, qo, vo, infos = _rollout_pair(gpu_lib, wl, 6)
+    X = wl.mesh.X.reshape(-1)
+    err = np.linalg.norm(qg - qo) / np.linalg.norm(qo - X)
+    assert err <= tol, err
+
+
+def test_zero_load_stays_at_rest(gpu_lib):
+    wl = fi.workload("tet4x4x16-svk-fp64")
+    ctx = gpu_lib.FEContext.from_workload(wl)
+    q = np.empty(ctx.n)
+    v = np.empty(ctx.n)
+    info = ctx.step(np.zeros(ctx.n), q, v)
+    assert np.all(q == wl.mesh.X.reshape(-1)) and np.all(v == 0.0)
+    assert info.iters == 0
+    ctx.close()
+
+
+def test_unconstrained_free_fall_closed_form(gpu_lib):
+    mesh0 = fi.tet_beam(2, 2, 5)
+    mesh = fi.TetBeam(2, 2, 5, mesh0.X, mesh0.conn, np.zeros(0, np.int32))
+    h, al = 0.01, 0.1
+    ctx = gpu_lib.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.NEOHOOKE, 1000.0,
+                            (3.4e3, 3.1e4, 0.0), h, al, 0.01)
+    p = fi.body_force(mesh, 1000.0, (0, 0, -9.81)).reshape(-1)
+    q = np.empty(ctx.n)
+    v = np.empty(ctx.n)
+    for t in range(1, 5):
+        ctx.step(p, q, v)
+        vt = -9.81 / al * (1 - (1 + h * al) ** (-t))
+        np.testing.assert_allclose(v.reshape(-1, 3)[:, 2], vt, rtol=1e-9)
+    ctx.close()
+
+
+def test_inverted_element_is_reported(gpu_lib):
+    mesh = fi.tet_beam(2, 2, 3)
+    ctx = gpu_lib.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.NEOHOOKE, 1000.0,
+                            (3.4e3, 3.1e4, 0.0), 0.01, 0.1, 0.01)
+    q = mesh.X.reshape(-1).copy()
+    far = mesh.n_nodes - 1
+    q[3 * far:3 * far + 3] = mesh.X[0] - 0.05      # pull a corner node through its tets
+    ctx.set_state(q, None)
+    with pytest.raises(gpu_lib.FEError) as ei:
+        ctx.step(np.zeros(ctx.n))
+    assert ei.value.status == 7
+    ctx.close()
+
+
+def test_iteration_cap_is_reported(gpu_lib):
+    wl = fi.workload("tet-mr", a=3, b=3, c=8)
+    ctx = gpu_lib.FEContext.from_workload(wl, precision=0, max_iters=1, refactor_every=100, tol=1e-14)
+    q = np.empty(ctx.n)
+    with pytest.raises(gpu_lib.FEError) as ei:
+        for t in range(0, 4):                     # the factor of A_0 is reused (R = 100)
+            ctx.step(wl.p(t).reshape(-1) * (1.0 + 50.0 * t), q, None)
+    assert ei.value.status == 5
+    ctx.close()
