@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Implicit FE steps/s on GB300: the 350k-DOF Mooney-Rivlin tet beam.
+
+One step = element force/tangent -> gather assembly of A and b -> lagged
+LDL^T (refactorised every 5 steps on the side stream) -> PCG with FP64
+residual refinement to ||r|| <= 1e-8 ||b|| -> backward Euler.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank steps its own replica of the beam (the path does
+not shard: replicas only); rank 0 prints one JSON line.  `value` is
+the whole-job steps/s with the per-step loads already resident in HBM;
+`e2e` is the same metric through the C ABI with host buffers (host->device
+copy of p_t and device->host read of q, v inside the timed region).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "tet30x30x120-mr"
+METRIC = "implicit steps/s (assembly+PCG to 1e-8) at 350k DOF, %HBM roofline; adjoint grads/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1", "0x1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- oracle arm
+
+def oracle_step_sample(wl, budget_s=25.0):
+    """Time the FP64 oracle, as it stands, on a bounded sample of one step of
+    the workload: its element force+tangent and assembly on a contiguous
+    slice of elements (sized to the budget), scaled to the whole mesh, plus
+    the direct sparse solve of a smaller beam of the same family, scaled by
+    its DOF ratio to the 1.5 power.  Returns (steps/s, cores, description)."""
+    from oracle import fe_oracle as O
+    import fe_inputs as fi
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    mesh = wl.mesh
+    E = mesh.n_elems
+    q = mesh.X.reshape(-1).copy()
+    # element + assembly on a slice
+    n_sl = min(E, 60000)
+    sl = np.arange(n_sl)
+    t0 = time.perf_counter()
+    quad = O.Quadrature(mesh.elem_type, mesh.X, mesh.conn[sl])
+    O.element_force(quad, q.reshape(-1, 3), wl.model, wl.params)
+    Ke = O.element_tangent(quad, q.reshape(-1, 3), wl.model, wl.params)
+    O.assemble(3 * mesh.n_nodes, mesh.conn[sl], O.element_values_fill_order(Ke))
+    t_elem = (time.perf_counter() - t0) * E / n_sl
+    # direct solve on a smaller beam of the same workload family
+    small = fi.workload("tet-mr", a=10, b=10, c=40)
+    sm = O.Model.from_workload(small)
+    qs = small.mesh.X.reshape(-1).copy()
+    A, b = sm.system(qs, np.zeros_like(qs), small.p(0).reshape(-1))
+    t0 = time.perf_counter()
+    O.direct_solve(A, b)
+    t_solve_small = time.perf_counter() - t0
+    ratio = (3.0 * mesh.n_nodes) / A.shape[0]
+    t_solve = t_solve_small * ratio ** 1.5
+    t_step = t_elem + t_solve
+    desc = (f"oracle element+assembly on {n_sl} of {E} tets scaled x{E / n_sl:.1f}; direct solve "
+            f"of the 10x10x40 beam ({A.shape[0]} DOF) scaled by (DOF ratio)^1.5 = "
+            f"{ratio ** 1.5:.1f}; numpy/scipy threads as installed")
+    return 1.0 / t_step, cores, desc, t_step
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import fe_inputs as fi
+    wl = fi.workload(WORKLOAD)
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    t_all = 0.0
+    desc = ""
+    cores = 0
+    for _ in range(max(1, args.steps)):
+        v, cores, desc, t_step = oracle_step_sample(wl, budget_s=25.0)
+        vals.append(v)
+        t_all += t_step
+    value = statistics.median(vals)
+    out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "precision": "fp64 oracle (direct solve)"},
+           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    args.warmup = max(3, args.warmup)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2306_05893_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    import fe_inputs as fi
+    import paper_2306_05893_gb300 as fe
+
+    wl = fi.workload(args.workload)
+    K, W = args.steps, args.warmup
+    stream = torch.cuda.Stream()
+    dev = torch.device("cuda", local)
+    ctx = fe.FEContext.from_workload(wl, device_ptrs=1, stream=stream.cuda_stream, profile_stages=1)
+    info = ctx.info()
+    n = ctx.n
+    loads = torch.tensor(np.stack([wl.p(t).reshape(-1) for t in range(W + K)]), dtype=torch.float64,
+                         device=dev)
+    q_out = torch.empty(n, dtype=torch.float64, device=dev)
+    v_out = torch.empty(n, dtype=torch.float64, device=dev)
+    iters = []
+    with torch.cuda.stream(stream):
+        for t in range(W):
+            ctx.step(loads[t], q_out, v_out)
+        torch.cuda.synchronize()
+        ctx.reset_stage_times()
+        sampler = ClockSampler(local)
+        sampler.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for t in range(W, W + K):
+            iters.append(ctx.step(loads[t], q_out, v_out).iters)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, stage_calls, launches = ctx.stage_times()
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * K / (ms / 1e3)
+    disp = float((q_out - torch.tensor(wl.mesh.X.reshape(-1), device=dev)).abs().max())
+    ctx.close()
+    del loads
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        ctx2 = fe.FEContext.from_workload(wl, device_ptrs=0)
+        qh = np.empty(n)
+        vh = np.empty(n)
+        its2 = []
+        for t in range(W):
+            ctx2.step(wl.p(t).reshape(-1), qh, vh)
+        host_loads = [np.ascontiguousarray(wl.p(t).reshape(-1)) for t in range(W, W + args.e2e_steps)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for pl in host_loads:
+            its2.append(ctx2.step(pl, qh, vh))
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        ctx2.close()
+        scal_reads = sum(i.iters + i.refinements + 1 for i in its2) / len(its2)
+        e2e = {"value": world * args.e2e_steps / el if world == 1 else None, "unit": "steps/s",
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": int(16 * n + 144 * scal_reads)}
+        if world > 1:
+            tt = torch.tensor([el], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e["value"] = world * args.e2e_steps / float(tt.item())
+
+    # roofline of the dominant stage: the level-scheduled preconditioner
+    # application (forward + backward GEMV levels over the fronts' operators)
+    hbm, peak_kind = _peaks()
+    apply_calls = max(1, stage_calls["apply"])
+    apply_ms = stage_ms["apply"] / apply_calls
+    bytes_apply = 2 * info["y_nnz"] * 4 + 6 * info["n_free"] * 4 + 2 * info["n"] * 4
+    achieved = bytes_apply / (apply_ms / 1e3) / 1e9
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    roofline = {"bound": "hbm", "kernel": "precond_apply (fwd_gemv+bwd levels)", "achieved": achieved,
+                "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "bytes_per_launch": bytes_apply, "avg_ms": apply_ms,
+                "dominant_stage": dom}
+    spmv_calls = max(1, stage_calls["spmv"])
+    spmv_ms = stage_ms["spmv"] / spmv_calls
+    bytes_spmv = info["nnz"] * (4 + 4) + (n + 1) * 4 + 2 * n * 4
+    asm_ms = stage_ms["assembly"] / max(1, stage_calls["assembly"])
+    bytes_asm = info["ntrip"] * 0.0  # filled below from the kept triplets
+    out = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_dof": n, "elements": wl.mesh.n_elems,
+                   "nnz": info["nnz"], "material": "Mooney-Rivlin", "precision": "mixed",
+                   "refactor_every": wl.refactor_every, "tol": wl.tol,
+                   "l2": "inputs larger than L2 (apply operators %.2f GB)" % (info["y_nnz"] * 4 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "mean_pcg_iters": float(np.mean(iters)), "max_displacement_m": disp},
+        "roofline": roofline,
+        "stages_ms_per_step": {k: v / K for k, v in stage_ms.items()},
+        "stage_calls": stage_calls,
+        "spmv": {"avg_ms": spmv_ms, "bytes": bytes_spmv,
+                 "achieved_gbs": bytes_spmv / (spmv_ms / 1e3) / 1e9},
+        "assembly": {"avg_ms": asm_ms},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    del bytes_asm
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, desc, _ = oracle_step_sample(wl)
+        out["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                               "sample": desc}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

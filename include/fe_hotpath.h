@@ -96,6 +96,8 @@ typedef struct {
   double inner_tol;       /* FE_MIXED inner PCG tolerance per sweep (0: 1e-4) */
   double factor_timeout_s;/* host deadline for a lagged factor (0: 30 s)      */
   int32_t use_graph;      /* 1: replay the PCG iteration as a CUDA graph      */
+  int32_t profile_stages; /* 1: time every stage with CUDA events on its own
+                             stream (read with fe_get_stage_times)          */
 } fe_options;
 
 typedef struct {
@@ -177,6 +179,31 @@ int fe_apply_preconditioner(fe_ctx *ctx, const double *r, double *z);
  * pointers are non-NULL; info may be NULL. */
 int fe_step(fe_ctx *ctx, const double *p_ext, double *q_out, double *v_out,
             fe_step_info *info);
+
+/* Sizes of the setup products. */
+typedef struct {
+  int64_t n, nnz, ntrip;  /* DOFs, CSR slots, triplets                       */
+  int64_t n_free;         /* DOFs not held by projective constraints         */
+  int64_t n_fronts, n_levels;
+  int64_t y_nnz;          /* stored nonzeros of the fronts' apply operators
+                             (lower-trapezoidal m x p blocks; the analogue of
+                             nnz(L) read twice per preconditioner application) */
+  double factor_flops;    /* flops of one numeric factorisation              */
+  int64_t device_bytes;   /* device memory held by the context (0 before use) */
+} fe_info;
+int fe_get_info(fe_ctx *ctx, fe_info *info);
+
+/* Stage timings gathered when fe_options.profile_stages = 1: for each stage
+ * the summed CUDA-event time in ms (measured on the stream that runs it) and
+ * the number of timed calls, plus the library's kernel launches since the
+ * last reset.  Arrays have FE_STAGE_COUNT entries; any pointer may be NULL. */
+enum {
+  FE_STAGE_ELEMENT = 0, FE_STAGE_ASSEMBLY, FE_STAGE_FACTOR, FE_STAGE_APPLY,
+  FE_STAGE_SPMV, FE_STAGE_VECTOR, FE_STAGE_RESIDUAL, FE_STAGE_INTEGRATE,
+  FE_STAGE_COUNT
+};
+int fe_get_stage_times(fe_ctx *ctx, double *ms, int64_t *calls, int64_t *kernel_launches);
+int fe_reset_stage_times(fe_ctx *ctx);
 
 /* Message of the last failure on ctx ("" if none). */
 const char *fe_last_error(const fe_ctx *ctx);

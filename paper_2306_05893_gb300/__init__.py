@@ -175,6 +175,25 @@ def fe_step(ctx, p_ext=None, q_out=None, v_out=None):
     return info
 
 
+def fe_get_info(ctx):
+    info = _abi.FeInfo()
+    _check(ctx, load().fe_get_info(ctx, ct.byref(info)))
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def fe_get_stage_times(ctx):
+    ms = (ct.c_double * len(_abi.STAGES))()
+    calls = (ct.c_int64 * len(_abi.STAGES))()
+    launches = ct.c_int64()
+    _check(ctx, load().fe_get_stage_times(ctx, ms, calls, ct.byref(launches)))
+    return ({k: ms[i] for i, k in enumerate(_abi.STAGES)},
+            {k: calls[i] for i, k in enumerate(_abi.STAGES)}, launches.value)
+
+
+def fe_reset_stage_times(ctx):
+    _check(ctx, load().fe_reset_stage_times(ctx))
+
+
 def fe_destroy(ctx):
     if ctx:
         load().fe_destroy(ctx)
@@ -226,6 +245,15 @@ class FEContext:
 
     def ordering(self):
         return fe_get_ordering(self.ctx)
+
+    def info(self):
+        return fe_get_info(self.ctx)
+
+    def stage_times(self):
+        return fe_get_stage_times(self.ctx)
+
+    def reset_stage_times(self):
+        fe_reset_stage_times(self.ctx)
 
     def set_state(self, q=None, v=None):
         fe_set_state(self.ctx, q, v)

@@ -26,13 +26,22 @@ class FeOptions(ct.Structure):
                 ("refactor_every", ct.c_int32), ("device_ptrs", ct.c_int32),
                 ("stream", ct.c_void_p), ("keep_checkpoints", ct.c_int32),
                 ("nd_leaf_nodes", ct.c_int32), ("inner_tol", ct.c_double),
-                ("factor_timeout_s", ct.c_double), ("use_graph", ct.c_int32)]
+                ("factor_timeout_s", ct.c_double), ("use_graph", ct.c_int32),
+                ("profile_stages", ct.c_int32)]
 
 
 class FeStepInfo(ct.Structure):
     _fields_ = [("iters", ct.c_int32), ("refinements", ct.c_int32), ("factor_age", ct.c_int32),
                 ("rel_residual", ct.c_double)]
 
+
+class FeInfo(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("nnz", ct.c_int64), ("ntrip", ct.c_int64), ("n_free", ct.c_int64),
+                ("n_fronts", ct.c_int64), ("n_levels", ct.c_int64), ("y_nnz", ct.c_int64),
+                ("factor_flops", ct.c_double), ("device_bytes", ct.c_int64)]
+
+
+STAGES = ["element", "assembly", "factor", "apply", "spmv", "vector", "residual", "integrate"]
 
 P = ct.POINTER
 CTX = ct.c_void_p
@@ -59,6 +68,9 @@ SIGNATURES = {
     "fe_factor_now": (ct.c_int, [CTX]),
     "fe_apply_preconditioner": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p]),
     "fe_step": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p, P(FeStepInfo)]),
+    "fe_get_info": (ct.c_int, [CTX, P(FeInfo)]),
+    "fe_get_stage_times": (ct.c_int, [CTX, DP, P(ct.c_int64), P(ct.c_int64)]),
+    "fe_reset_stage_times": (ct.c_int, [CTX]),
     "fe_last_error": (ct.c_char_p, [CTX]),
     "fe_destroy": (None, [CTX]),
 }

@@ -18,6 +18,60 @@ namespace {
 bool mixed(const fe_ctx *c) { return c->opt.precision == FE_MIXED; }
 size_t vsz(const fe_ctx *c) { return mixed(c) ? sizeof(float) : sizeof(double); }
 
+// ------------------------------------------------------ live stage timing
+int stage_begin(fe_ctx *c, int stage, cudaStream_t s) {
+  DeviceState *d = c->dev;
+  if (!c->opt.profile_stages) return -1;
+  DeviceState::StageRec r;
+  r.stage = stage;
+  for (cudaEvent_t *e : {&r.a, &r.b}) {
+    if (!d->pool.empty()) {
+      *e = d->pool.back();
+      d->pool.pop_back();
+    } else if (cudaEventCreate(e) != cudaSuccess) {
+      return -1;
+    }
+  }
+  cudaEventRecord(r.a, s);
+  d->recs.push_back(r);
+  return int(d->recs.size() - 1);
+}
+
+void stage_end(fe_ctx *c, int idx, cudaStream_t s) {
+  if (idx >= 0) cudaEventRecord(c->dev->recs[idx].b, s);
+}
+
+// Harvest every finished record (both streams must be idle when all = true).
+void stage_collect(fe_ctx *c) {
+  DeviceState *d = c->dev;
+  if (!d) return;
+  std::vector<DeviceState::StageRec> keep;
+  for (auto &r : d->recs) {
+    if (cudaEventQuery(r.b) != cudaSuccess) {
+      cudaGetLastError();
+      keep.push_back(r);
+      continue;
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      d->stage_ms[r.stage] += ms;
+      d->stage_calls[r.stage] += 1;
+    }
+    cudaGetLastError();
+    d->pool.push_back(r.a);
+    d->pool.push_back(r.b);
+  }
+  d->recs.swap(keep);
+}
+
+struct Stage {
+  fe_ctx *c;
+  cudaStream_t s;
+  int idx;
+  Stage(fe_ctx *c_, int stage, cudaStream_t s_) : c(c_), s(s_), idx(stage_begin(c_, stage, s_)) {}
+  ~Stage() { stage_end(c, idx, s); }
+};
+
 template <typename T>
 int dalloc(fe_ctx *c, DeviceState *d, T **p, size_t count) {
   *p = nullptr;
@@ -267,7 +321,10 @@ int launch_factor(fe_ctx *c, int64_t step_tag) {
   FE_CUDA_TRY(cudaMemcpyAsync(d->Afac, d->A, size_t(c->nnz) * vsz(c), cudaMemcpyDeviceToDevice, d->stream));
   FE_CUDA_TRY(cudaEventRecord(d->ev_assembled, d->stream));
   FE_CUDA_TRY(cudaStreamWaitEvent(d->fstream, d->ev_assembled, 0));
-  factor_enqueue(c, d, buf, fp32, d->Afac, d->fstream);
+  {
+    Stage st(c, FE_STAGE_FACTOR, d->fstream);
+    factor_enqueue(c, d, buf, fp32, d->Afac, d->fstream);
+  }
   FE_CUDA_TRY(cudaGetLastError());
   FE_CUDA_TRY(cudaEventRecord(d->ev_factored, d->fstream));
   d->factor_pending = buf;
@@ -280,19 +337,35 @@ int launch_factor(fe_ctx *c, int64_t step_tag) {
 int pcg(fe_ctx *c, bool fp32, void *X, void *R) {
   DeviceState *d = c->dev;
   cudaStream_t s = d->stream;
-  apply_enqueue(c, d, d->cur, fp32, R, d->vz, s);
-  launch_dot_rz(c, d, fp32, R, d->vz, true, s);
-  launch_update_p(c, d, fp32, d->vz, d->vp, true, s);
+  {
+    Stage st(c, FE_STAGE_APPLY, s);
+    apply_enqueue(c, d, d->cur, fp32, R, d->vz, s);
+  }
+  {
+    Stage st(c, FE_STAGE_VECTOR, s);
+    launch_dot_rz(c, d, fp32, R, d->vz, true, s);
+    launch_update_p(c, d, fp32, d->vz, d->vp, true, s);
+  }
   for (;;) {
-    launch_spmv_dot(c, d, fp32, d->vp, d->vq, s);
-    launch_axpy_norm(c, d, fp32, X, R, d->vp, d->vq, s);
+    {
+      Stage st(c, FE_STAGE_SPMV, s);
+      launch_spmv_dot(c, d, fp32, d->vp, d->vq, s);
+    }
+    {
+      Stage st(c, FE_STAGE_VECTOR, s);
+      launch_axpy_norm(c, d, fp32, X, R, d->vp, d->vq, s);
+    }
     FE_CUDA_TRY(cudaGetLastError());
     FE_TRY(read_scalars(c));
     FE_TRY(flag_status(c));
     if (d->h_scal[S_DONE] != 0.0) break;
     if (d->h_scal[S_ITERS] >= c->opt.max_iters)
       return set_error(c, FE_ERR_NOT_CONVERGED, "PCG reached max_iters");
-    apply_enqueue(c, d, d->cur, fp32, R, d->vz, s);
+    {
+      Stage st(c, FE_STAGE_APPLY, s);
+      apply_enqueue(c, d, d->cur, fp32, R, d->vz, s);
+    }
+    Stage st(c, FE_STAGE_VECTOR, s);
     launch_dot_rz(c, d, fp32, R, d->vz, false, s);
     launch_update_p(c, d, fp32, d->vz, d->vp, false, s);
   }
@@ -315,7 +388,10 @@ int solve(fe_ctx *c, fe_step_info *info) {
   } else {
     launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s);  // x = 0, r = b (FP64)
     for (;;) {
-      if (sweeps > 0) launch_residual(c, d, true, s);
+      if (sweeps > 0) {
+        Stage st(c, FE_STAGE_RESIDUAL, s);
+        launch_residual(c, d, true, s);
+      }
       FE_TRY(read_scalars(c));
       FE_TRY(flag_status(c));
       if (d->h_scal[S_ODONE] != 0.0) break;
@@ -349,6 +425,11 @@ void destroy_device(fe_ctx *c) {
   if (d->ev_assembled) cudaEventDestroy(d->ev_assembled);
   if (d->ev_factored) cudaEventDestroy(d->ev_factored);
   if (d->ev_apply_done) cudaEventDestroy(d->ev_apply_done);
+  for (auto &r : d->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : d->pool) cudaEventDestroy(e);
   if (d->fstream) cudaStreamDestroy(d->fstream);
   if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
   cudaGetLastError();
@@ -484,8 +565,14 @@ int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_ste
   }
   FE_TRY(clear_flags(c));
   // S1 element kernel, S3 gather assembly of A and b
-  launch_element(c, d, d->q, fp32, s);
-  launch_assemble(c, d, fp32, pd, s);
+  {
+    Stage st(c, FE_STAGE_ELEMENT, s);
+    launch_element(c, d, d->q, fp32, s);
+  }
+  {
+    Stage st(c, FE_STAGE_ASSEMBLY, s);
+    launch_assemble(c, d, fp32, pd, s);
+  }
   FE_CUDA_TRY(cudaGetLastError());
   // S4 lagged refactorisation: A_s is factored at s = 0 mod R on the side
   // stream and preconditions steps s+1 .. s+R; step 0 (and R = 1) waits.
@@ -502,12 +589,62 @@ int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_ste
     return st;
   }
   // S8 backward Euler
-  launch_integrate(c, d, s);
+  {
+    Stage st(c, FE_STAGE_INTEGRATE, s);
+    launch_integrate(c, d, s);
+  }
   FE_CUDA_TRY(cudaGetLastError());
   if (q_out) FE_TRY(stage_out(c, q_out, d->q, c->n, 0));
   if (v_out) FE_TRY(stage_out(c, v_out, d->v, c->n, 1));
   if (info) info->factor_age = age;
   d->step_index = step + 1;
+  if (c->opt.profile_stages) stage_collect(c);
+  return FE_OK;
+}
+
+int fe_get_info(fe_ctx *c, fe_info *info) {
+  if (!c || !info) return FE_ERR_ARG;
+  if (!c->built) return set_error(c, FE_ERR_STATE, "fe_build_pattern has not run");
+  info->n = c->n;
+  info->nnz = c->nnz;
+  info->ntrip = c->ntrip;
+  info->n_free = c->n_free;
+  info->n_fronts = int64_t(c->fronts.size());
+  info->n_levels = int64_t(c->levels.size());
+  info->y_nnz = c->y_nnz;
+  info->factor_flops = c->factor_flops;
+  info->device_bytes = c->dev ? int64_t(c->dev->bytes_total) : 0;
+  return FE_OK;
+}
+
+int fe_get_stage_times(fe_ctx *c, double *ms, int64_t *calls, int64_t *kernel_launches) {
+  if (!c) return FE_ERR_ARG;
+  DeviceState *d = c->dev;
+  if (d) {
+    cudaStreamSynchronize(d->stream);
+    cudaStreamSynchronize(d->fstream);
+    stage_collect(c);
+  }
+  for (int k = 0; k < FE_STAGE_COUNT; ++k) {
+    if (ms) ms[k] = d ? d->stage_ms[k] : 0.0;
+    if (calls) calls[k] = d ? d->stage_calls[k] : 0;
+  }
+  if (kernel_launches) *kernel_launches = d ? d->launches : 0;
+  return FE_OK;
+}
+
+int fe_reset_stage_times(fe_ctx *c) {
+  if (!c) return FE_ERR_ARG;
+  DeviceState *d = c->dev;
+  if (!d) return FE_OK;
+  cudaStreamSynchronize(d->stream);
+  cudaStreamSynchronize(d->fstream);
+  stage_collect(c);
+  for (int k = 0; k < FE_STAGE_COUNT; ++k) {
+    d->stage_ms[k] = 0.0;
+    d->stage_calls[k] = 0;
+  }
+  d->launches = 0;
   return FE_OK;
 }
 

@@ -87,6 +87,7 @@ struct fe_ctx {
   std::vector<fe::Level> levels;
   int64_t f_total = 0, y_total = 0, w_total = 0, u_total = 0;
   double factor_flops = 0;
+  int64_t y_nnz = 0;
 
   fe::DeviceState *dev = nullptr;
   std::string err;

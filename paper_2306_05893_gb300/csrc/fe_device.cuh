@@ -106,6 +106,14 @@ struct DeviceState {
 
   int64_t step_index = 0;
   size_t bytes_total = 0;
+
+  // live stage timing (fe_options.profile_stages) and launch counting
+  struct StageRec { int stage; cudaEvent_t a, b; };
+  std::vector<StageRec> recs;
+  std::vector<cudaEvent_t> pool;
+  double stage_ms[FE_STAGE_COUNT] = {0};
+  int64_t stage_calls[FE_STAGE_COUNT] = {0};
+  mutable int64_t launches = 0;
 };
 
 constexpr int kMaxBlocks = 4096;

@@ -393,11 +393,13 @@ static void factor_levels(const fe_ctx *c, DeviceState *d, int buf, const TF *Af
   cudaFuncSetAttribute(front_update_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
+    if (L.asm_n) d->launches++;
     if (L.asm_n)
       front_assemble_kernel<TF><<<unsigned(L.asm_n), 256, 0, s>>>(d->tasks + L.asm_off, d->fronts, d->child_list,
                                                                   d->rmap, d->fa_colptr, d->fa_slot, d->fa_off,
                                                                   Afac, F, Y);
     for (size_t st = 0; st < L.diag_n.size(); ++st) {
+      d->launches += (L.diag_n[st] > 0) + (L.panel_n[st] > 0) + (L.trail_n[st] > 0);
       if (L.diag_n[st])
         front_diag_kernel<TF><<<unsigned(L.diag_n[st]), 256, dsm, s>>>(d->tasks + L.diag_off[st], d->fronts, F, Y,
                                                                        d->D[buf], d->D[buf] + c->n_free, d->flags);
@@ -430,6 +432,7 @@ static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const T
   for (const auto &f : c->fronts) pmax = std::max(pmax, f.npiv);
   const size_t sm = size_t(pmax) * sizeof(TV);
   cudaFuncSetAttribute(fwd_gemv_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  d->launches += 3 * int64_t(d->lt.size());
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
     fwd_gather_kernel<TV><<<unsigned(L.nfronts), 256, 0, s>>>(d->level_fronts + L.fronts_off, d->fronts,

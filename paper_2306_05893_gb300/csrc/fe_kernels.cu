@@ -257,6 +257,7 @@ static void launch_element_t(const fe_ctx *c, const DeviceState *d, const double
 }
 
 void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool fp32, cudaStream_t s) {
+  d->launches++;
   switch (c->model) {
     case FE_SVK:
       fp32 ? launch_element_t<FE_SVK, float>(c, d, q, s) : launch_element_t<FE_SVK, double>(c, d, q, s);
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(
 
 void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const double *pext,
                      cudaStream_t s) {
+  d->launches++;
   const double h = c->h, al = c->alpha, be = c->beta;
   const double cM = 1.0 + h * al, cK = h * (be + h), bh = be + h;
   const int64_t n = c->n;
@@ -353,14 +355,19 @@ __global__ void __launch_bounds__(kRedBlock) spmv_dot_kernel(
   if (solve_done(scal)) return;
   const int sub = threadIdx.x % TPR;
   const int64_t groups = int64_t(gridDim.x) * (kRedBlock / TPR);
+  // the loop bound is warp-uniform so every lane reaches every shuffle
+  const int64_t warp_row0 = int64_t(blockIdx.x) * (kRedBlock / TPR) + (threadIdx.x / 32) * (32 / TPR);
   double dot = 0.0;
-  for (int64_t row = int64_t(blockIdx.x) * (kRedBlock / TPR) + threadIdx.x / TPR; row < n; row += groups) {
+  for (int64_t r0 = warp_row0; r0 < n; r0 += groups) {
+    const int64_t row = r0 + (threadIdx.x % 32) / TPR;
     TV acc = TV(0);
-    const int32_t k1 = rowptr[row + 1];
-    for (int32_t k = rowptr[row] + sub; k < k1; k += TPR) acc += TV(A[k]) * x[colind[k]];
+    if (row < n) {
+      const int32_t k1 = rowptr[row + 1];
+      for (int32_t k = rowptr[row] + sub; k < k1; k += TPR) acc += TV(A[k]) * x[colind[k]];
+    }
 #pragma unroll
     for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
-    if (sub == 0) {
+    if (sub == 0 && row < n) {
       y[row] = acc;
       dot += double(x[row]) * double(acc);
     }
@@ -386,14 +393,18 @@ __global__ void __launch_bounds__(kRedBlock) residual_kernel(
     double *__restrict__ r, double *scal, double *partials, unsigned int *ticket) {
   const int sub = threadIdx.x % TPR;
   const int64_t groups = int64_t(gridDim.x) * (kRedBlock / TPR);
+  const int64_t warp_row0 = int64_t(blockIdx.x) * (kRedBlock / TPR) + (threadIdx.x / 32) * (32 / TPR);
   double rr = 0.0;
-  for (int64_t row = int64_t(blockIdx.x) * (kRedBlock / TPR) + threadIdx.x / TPR; row < n; row += groups) {
+  for (int64_t r0 = warp_row0; r0 < n; r0 += groups) {
+    const int64_t row = r0 + (threadIdx.x % 32) / TPR;
     double acc = 0.0;
-    const int32_t k1 = rowptr[row + 1];
-    for (int32_t k = rowptr[row] + sub; k < k1; k += TPR) acc += double(A[k]) * x[colind[k]];
+    if (row < n) {
+      const int32_t k1 = rowptr[row + 1];
+      for (int32_t k = rowptr[row] + sub; k < k1; k += TPR) acc += double(A[k]) * x[colind[k]];
+    }
 #pragma unroll
     for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
-    if (sub == 0) {
+    if (sub == 0 && row < n) {
       const double ri = b[row] - acc;
       r[row] = ri;
       rr += ri * ri;
@@ -523,6 +534,7 @@ static int tpr_for(const fe_ctx *c) { return c->elem_type == FE_TET4 ? 8 : 16; }
 
 void launch_spmv_dot(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y,
                      cudaStream_t s) {
+  d->launches++;
   const int64_t n = c->n;
   const unsigned g = red_grid(n * tpr_for(c) / 4);
   if (fp32) {
@@ -549,6 +561,7 @@ void launch_spmv_dot(const fe_ctx *c, const DeviceState *d, bool fp32, const voi
 }
 
 void launch_residual(const fe_ctx *c, const DeviceState *d, bool fp32, cudaStream_t s) {
+  d->launches++;
   const int64_t n = c->n;
   const unsigned g = red_grid(n * tpr_for(c) / 4);
   if (fp32) {
@@ -570,6 +583,7 @@ void launch_residual(const fe_ctx *c, const DeviceState *d, bool fp32, cudaStrea
 
 void launch_axpy_norm(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const void *p,
                       const void *q, cudaStream_t s) {
+  d->launches++;
   const int64_t n = c->n;
   if (fp32)
     axpy_norm_kernel<float><<<red_grid(n), kRedBlock, 0, s>>>(n, (float *)x, (float *)r, (const float *)p,
@@ -582,6 +596,7 @@ void launch_axpy_norm(const fe_ctx *c, const DeviceState *d, bool fp32, void *x,
 
 void launch_dot_rz(const fe_ctx *c, const DeviceState *d, bool fp32, const void *r, const void *z, bool first,
                    cudaStream_t s) {
+  d->launches++;
   const int64_t n = c->n;
   if (fp32)
     dot_rz_kernel<float><<<red_grid(n), kRedBlock, 0, s>>>(n, (const float *)r, (const float *)z, first,
@@ -593,6 +608,7 @@ void launch_dot_rz(const fe_ctx *c, const DeviceState *d, bool fp32, const void 
 
 void launch_update_p(const fe_ctx *c, const DeviceState *d, bool fp32, const void *z, void *p, bool first,
                      cudaStream_t s) {
+  d->launches++;
   const int64_t n = c->n;
   if (fp32)
     update_p_kernel<float><<<ew_grid(n), 256, 0, s>>>(n, (const float *)z, (float *)p, first, d->scal);
@@ -602,6 +618,7 @@ void launch_update_p(const fe_ctx *c, const DeviceState *d, bool fp32, const voi
 
 void launch_init_solve(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const double *rhs,
                        double tol, bool outer, cudaStream_t s) {
+  d->launches++;
   const int64_t n = c->n;
   if (fp32)
     init_solve_kernel<float><<<red_grid(n), kRedBlock, 0, s>>>(n, (float *)x, (float *)r, rhs, tol, outer,
@@ -612,10 +629,12 @@ void launch_init_solve(const fe_ctx *c, const DeviceState *d, bool fp32, void *x
 }
 
 void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
+  d->launches++;
   refine_update_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, d->x, (const float *)d->vd);
 }
 
 void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
+  d->launches++;
   integrate_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, c->h, d->x, d->v, d->q);
 }
 

@@ -372,6 +372,7 @@ int build_ordering(fe_ctx *c) {
     std::sort(U.begin(), U.end());
   }
   c->fronts.assign(nf, Front());
+  c->y_nnz = 0;
   int64_t f_total = 0, y_total = 0, w_total = 0, u_total = 0, rows_total = 0;
   for (int64_t f = 0; f < nf; ++f) {
     Front &F = c->fronts[f];
@@ -388,6 +389,7 @@ int build_ordering(fe_ctx *c) {
     F.w_off = w_total; w_total += m;
     F.u_off = u_total; u_total += F.nupd;
     F.rows_off = rows_total; rows_total += F.nupd;
+    c->y_nnz += m * F.npiv - int64_t(F.npiv) * (F.npiv - 1) / 2;
   }
   c->f_total = f_total; c->y_total = y_total; c->w_total = w_total; c->u_total = u_total;
   c->upd_rows_new.assign(rows_total, 0);
