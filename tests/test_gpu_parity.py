@@ -79,7 +79,7 @@ def test_assembly(gpu_lib, kind, law, precision):
 def test_exact_factor_inverts_A(gpu_lib, kind, leaf):
     """FP64 LDL^T of the current A applied level by level is A^{-1}."""
     mesh = _mesh(kind)
-    q, v, p = _state(mesh, seed=2)
+    q, v, p = _state(mesh, amp=0.01, seed=2)     # A is SPD at this state
     ctx = _ctx(gpu_lib, mesh, fi.NEOHOOKE, 0, nd_leaf_nodes=leaf)
     ctx.set_state(q, v)
     A, _ = ctx.assemble(p)
@@ -99,7 +99,7 @@ def test_exact_factor_inverts_A(gpu_lib, kind, leaf):
 
 def test_mixed_factor_is_a_close_preconditioner(gpu_lib):
     mesh = _mesh("tet")
-    q, v, p = _state(mesh, seed=5)
+    q, v, p = _state(mesh, amp=0.01, seed=5)
     ctx = _ctx(gpu_lib, mesh, fi.MOONEY_RIVLIN, 1)
     ctx.set_state(q, v)
     A, _ = ctx.assemble(p)
@@ -110,6 +110,25 @@ def test_mixed_factor_is_a_close_preconditioner(gpu_lib):
     import scipy.sparse as sp
     S = sp.csr_matrix((A, ctx.colind, ctx.rowptr), shape=(ctx.n, ctx.n))
     assert np.linalg.norm(S @ z - r) <= 1e-3 * np.linalg.norm(r)
+    ctx.close()
+
+
+def test_indefinite_matrix_is_reported(gpu_lib):
+    """A random 5%-of-spacing jitter makes the neo-Hookean tangent indefinite
+    (the oracle's A has a negative eigenvalue there): the factor reports a
+    non-positive pivot as FE_ERR_BREAKDOWN (reading C-6)."""
+    mesh = _mesh("tet")
+    q, v, p = _state(mesh, amp=0.05, seed=2)
+    m = O.Model(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.NEOHOOKE,
+                LAWS[fi.NEOHOOKE], 1000., .01, .1, .01)
+    Ao, _ = m.system(q, v, p)
+    assert np.linalg.eigvalsh(Ao.toarray()).min() < 0
+    ctx = _ctx(gpu_lib, mesh, fi.NEOHOOKE, 0)
+    ctx.set_state(q, v)
+    ctx.assemble(p)
+    with pytest.raises(gpu_lib.FEError) as ei:
+        ctx.factor_now()
+    assert ei.value.status == 6
     ctx.close()
 
 
