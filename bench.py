@@ -98,62 +98,61 @@ class ClockSampler:
 
 # --------------------------------------------------------------- oracle arm
 
-def oracle_step_sample(wl, budget_s=25.0):
+def oracle_step_sample(wl):
     """Time the FP64 oracle, as it stands, on a bounded sample of one step of
-    the workload: its element force+tangent and assembly on a contiguous
-    slice of elements (sized to the budget), scaled to the whole mesh, plus
-    the direct sparse solve of a smaller beam of the same family, scaled by
-    its DOF ratio to the 1.5 power.  Returns (steps/s, cores, description)."""
+    the workload (about 10-20 s of host CPU): its element force + tangent +
+    triplet assembly on a contiguous slice of the elements, scaled to the
+    whole mesh, plus its direct sparse solve timed on two smaller beams of the
+    same family and extrapolated to the workload's DOF count with the fitted
+    power law t ~ n^k.  Returns (steps/s, cores, description, s/step)."""
     from oracle import fe_oracle as O
     import fe_inputs as fi
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     mesh = wl.mesh
     E = mesh.n_elems
+    n_dof = 3 * mesh.n_nodes
     q = mesh.X.reshape(-1).copy()
-    # element + assembly on a slice
     n_sl = min(E, 60000)
     sl = np.arange(n_sl)
-    t0 = time.perf_counter()
     quad = O.Quadrature(mesh.elem_type, mesh.X, mesh.conn[sl])
+    t0 = time.perf_counter()
     O.element_force(quad, q.reshape(-1, 3), wl.model, wl.params)
     Ke = O.element_tangent(quad, q.reshape(-1, 3), wl.model, wl.params)
-    O.assemble(3 * mesh.n_nodes, mesh.conn[sl], O.element_values_fill_order(Ke))
+    O.assemble(n_dof, mesh.conn[sl], O.element_values_fill_order(Ke))
     t_elem = (time.perf_counter() - t0) * E / n_sl
-    # direct solve on a smaller beam of the same workload family
-    small = fi.workload("tet-mr", a=10, b=10, c=40)
-    sm = O.Model.from_workload(small)
-    qs = small.mesh.X.reshape(-1).copy()
-    A, b = sm.system(qs, np.zeros_like(qs), small.p(0).reshape(-1))
-    t0 = time.perf_counter()
-    O.direct_solve(A, b)
-    t_solve_small = time.perf_counter() - t0
-    ratio = (3.0 * mesh.n_nodes) / A.shape[0]
-    t_solve = t_solve_small * ratio ** 1.5
+    pts = []
+    for a in (8, 12):
+        small = fi.workload("tet-mr", a=a, b=a, c=4 * a)
+        sm = O.Model.from_workload(small)
+        qs = small.mesh.X.reshape(-1).copy()
+        A, b = sm.system(qs, np.zeros_like(qs), small.p(0).reshape(-1))
+        t0 = time.perf_counter()
+        O.direct_solve(A, b)
+        pts.append((A.shape[0], time.perf_counter() - t0))
+    (n1, t1), (n2, t2) = pts
+    k = float(np.log(t2 / t1) / np.log(n2 / n1))
+    t_solve = t2 * (n_dof / n2) ** k
     t_step = t_elem + t_solve
-    desc = (f"oracle element+assembly on {n_sl} of {E} tets scaled x{E / n_sl:.1f}; direct solve "
-            f"of the 10x10x40 beam ({A.shape[0]} DOF) scaled by (DOF ratio)^1.5 = "
-            f"{ratio ** 1.5:.1f}; numpy/scipy threads as installed")
+    desc = (f"oracle element force+tangent+triplet assembly on {n_sl} of {E} tets scaled x{E / n_sl:.1f} "
+            f"({t_elem:.1f} s); oracle direct solve timed at {n1} and {n2} DOF ({t1:.2f} s, {t2:.2f} s), "
+            f"fitted t ~ n^{k:.2f}, extrapolated to {n_dof} DOF ({t_solve:.0f} s); one step = {t_step:.0f} s")
     return 1.0 / t_step, cores, desc, t_step
 
 
 def run_reference(args, rank):
+    """The oracle arm: each step is one bounded oracle sample (see above)."""
     if rank != 0:
         return
     import fe_inputs as fi
     wl = fi.workload(WORKLOAD)
-    vals = []
-    for _ in range(args.warmup):
-        pass
-    t_all = 0.0
-    desc = ""
-    cores = 0
-    for _ in range(max(1, args.steps)):
-        v, cores, desc, t_step = oracle_step_sample(wl, budget_s=25.0)
+    steps = max(1, min(args.steps, 8))
+    vals, desc, cores = [], "", 0
+    for _ in range(steps):
+        v, cores, desc, _ = oracle_step_sample(wl)
         vals.append(v)
-        t_all += t_step
     value = statistics.median(vals)
     out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+           "steps": steps, "warmup": 0, "ms_per_step": 1e3 / value,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOAD, "precision": "fp64 oracle (direct solve)"},
