@@ -71,65 +71,61 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
 }
 
 // ---------------------------------------------------------------- diagonal
-// Task (front, k0, kb): LDL^T of the kb x kb diagonal block in FP64, pivots
-// to D (and 1/D), L back into F, L^{-1} of the block into Y[K, K].
+// Task (front, k0, kb): LDL^T of the kb x kb diagonal block.  The eliminations
+// run in the factor's type TF; the pivots are accumulated in FP64 (dg) and
+// stored in FP64 with their inverses.  The same row operations applied to the
+// identity give L_KK^{-1} (Gauss-Jordan), written into Y[K, K]; L goes back
+// into F.  256 threads: lane c = tid % 64 owns column c, rows step by 4.
 template <typename TF>
 __global__ void __launch_bounds__(256) front_diag_kernel(const int32_t *__restrict__ tasks,
                                                          const DFront *__restrict__ fronts, TF *__restrict__ F,
                                                          TF *__restrict__ Y, double *__restrict__ D,
                                                          double *__restrict__ Dinv, int *flags) {
-  extern __shared__ double dsm[];
-  double *L = dsm;                 // [64][65]
-  double *Xi = dsm + 64 * 65;      // [64][65]
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  double *dg = reinterpret_cast<double *>(dsm_raw);                      // [64]
+  TF(*L)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double));
+  TF(*Xi)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double) + 64 * 65 * sizeof(TF));
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t k0 = t.y & 0xffffff, kb = t.z, m = fr.m;
   TF *Ff = F + fr.f_off;
-  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-    const int i = idx % kb, j = idx / kb;
-    L[i * 65 + j] = (i >= j) ? double(Ff[(k0 + i) + int64_t(k0 + j) * m]) : 0.0;
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
+    const int i = idx % 64, j = idx / 64;
+    const bool in = i < kb && j < kb;
+    L[i][j] = (in && i >= j) ? Ff[(k0 + i) + int64_t(k0 + j) * m] : TF(0);
+    Xi[i][j] = (i == j) ? TF(1) : TF(0);
   }
   __syncthreads();
+  if (threadIdx.x < kb) dg[threadIdx.x] = double(L[threadIdx.x][threadIdx.x]);
+  const int c = threadIdx.x & 63, r = threadIdx.x >> 6;
+  __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    double d = L[j * 65 + j];
+    double d = dg[j];
     if (!(d > 0.0)) {
       if (threadIdx.x == 0) atomicOr(flags, FLAG_PIVOT);
       d = 1.0;
     }
     const double invd = 1.0 / d;
-    const int T = kb - j - 1;
-    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-      const int ii = idx / T, kk = idx % T;
-      if (kk <= ii) {
-        const int i = j + 1 + ii, k = j + 1 + kk;
-        L[i * 65 + k] -= L[i * 65 + j] * L[k * 65 + j] * invd;
-      }
+    const TF tinv = TF(invd);
+    for (int i = j + 1 + r; i < kb; i += 4) {
+      const TF lij = L[i][j];
+      if (c > j && c < i) L[i][c] -= lij * L[c][j] * tinv;
+      if (c <= j) Xi[i][c] -= lij * tinv * Xi[j][c];
+      if (c == 0) dg[i] -= double(lij) * double(lij) * invd;
     }
     __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) L[i * 65 + j] *= invd;
+    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) L[i][j] *= tinv;
     if (threadIdx.x == 0) {
-      L[j * 65 + j] = d;
       D[fr.first + k0 + j] = d;
       Dinv[fr.first + k0 + j] = invd;
     }
     __syncthreads();
   }
-  // L^{-1} of the unit lower block, one column per thread
-  if (threadIdx.x < kb) {
-    const int c = threadIdx.x;
-    for (int i = 0; i < kb; ++i) Xi[i * 65 + c] = (i == c) ? 1.0 : 0.0;
-    for (int i = c + 1; i < kb; ++i) {
-      double s = 0.0;
-      for (int j = c; j < i; ++j) s += L[i * 65 + j] * Xi[j * 65 + c];
-      Xi[i * 65 + c] = -s;
-    }
-  }
-  __syncthreads();
   TF *Yf = Y + fr.y_off;
   for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
     const int i = idx % kb, j = idx / kb;
-    if (i > j) Ff[(k0 + i) + int64_t(k0 + j) * m] = TF(L[i * 65 + j]);
-    Yf[(k0 + i) + int64_t(k0 + j) * m] = TF(Xi[i * 65 + j]);
+    if (i > j) Ff[(k0 + i) + int64_t(k0 + j) * m] = L[i][j];
+    Yf[(k0 + i) + int64_t(k0 + j) * m] = Xi[i][j];
   }
 }
 
@@ -292,6 +288,89 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
   }
 }
 
+// FP32 variant of the trailing updates with 128 x 128 tiles: 256 threads, 8 x 8
+// outputs each from float4 shared-memory fragments (4 LDS.128 per 64 FMA), the
+// whole K = kb <= 64 panel in shared memory, and a read-modify-write epilogue
+// staged through shared memory so F and Y are updated with coalesced accesses.
+constexpr int kT128 = 128;
+constexpr int kLd128 = 132;  // padded row (16-byte aligned) of the k-major tiles
+
+__global__ void __launch_bounds__(256) front_update128_kernel(const int32_t *__restrict__ tasks,
+                                                              const DFront *__restrict__ fronts,
+                                                              float *__restrict__ F, float *__restrict__ Y,
+                                                              const double *__restrict__ D) {
+  extern __shared__ __align__(16) float usm128[];
+  float *As = usm128;                 // [64][kLd128]: As[l][i] = L[i0 + i, k0 + l]
+  float *Bs = usm128 + 64 * kLd128;   // [64][kLd128]: Bs[l][j]
+  float *Cs = usm128;                 // epilogue [128][129], reuses As/Bs
+  const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
+  const DFront fr = fronts[t.x];
+  const int kind = t.y >> 24;
+  const int32_t k0 = t.y & 0xffffff, i0 = t.z, j0 = t.w, m = fr.m;
+  const int32_t kb = (fr.npiv - k0) < 64 ? (fr.npiv - k0) : 64;
+  float *Ff = F + fr.f_off;
+  float *Yf = Y + fr.y_off;
+  for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
+    const int l = idx / kT128, i = idx % kT128;
+    const int32_t r = i0 + i;
+    As[l * kLd128 + i] = (r < m && l < kb) ? Ff[r + int64_t(k0 + l) * m] : 0.f;
+  }
+  if (kind == T_TRAIL) {
+    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
+      const int l = idx / kT128, j = idx % kT128;
+      const int32_t r = j0 + j;
+      Bs[l * kLd128 + j] = (r < m && l < kb) ? Ff[r + int64_t(k0 + l) * m] * float(D[fr.first + k0 + l]) : 0.f;
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
+      const int l = idx % 64, j = idx / 64;
+      const int32_t c = j0 + j;
+      Bs[l * kLd128 + j] = (l < kb && c < k0 + kb) ? Yf[(k0 + l) + int64_t(c) * m] : 0.f;
+    }
+  }
+  __syncthreads();
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+#pragma unroll 4
+  for (int l = 0; l < kb; ++l) {
+    const float4 a0 = *reinterpret_cast<const float4 *>(As + l * kLd128 + ty * 4);
+    const float4 a1 = *reinterpret_cast<const float4 *>(As + l * kLd128 + ty * 4 + 64);
+    const float4 b0 = *reinterpret_cast<const float4 *>(Bs + l * kLd128 + tx * 4);
+    const float4 b1 = *reinterpret_cast<const float4 *>(Bs + l * kLd128 + tx * 4 + 64);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = ty * 4 + (r & 3) + (r >> 2) * 64;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) Cs[i * 129 + tx * 4 + (c & 3) + (c >> 2) * 64] = acc[r][c];
+  }
+  __syncthreads();
+  if (kind == T_TRAIL) {
+    for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
+      const int j = idx / kT128, i = idx % kT128;
+      const int32_t r = i0 + i, c = j0 + j;
+      if (r < m && c < m && r >= c) Ff[r + int64_t(c) * m] -= Cs[i * 129 + j];
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
+      const int j = idx / kT128, i = idx % kT128;
+      const int32_t r = i0 + i, c = j0 + j;
+      if (r < m && c < k0 + kb) Yf[r + int64_t(c) * m] -= Cs[i * 129 + j];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ apply
 // Forward, part 1 (one block per front of the level): w = [r_P; 0] plus the
 // children's update vectors extend-added in fixed order.
@@ -386,11 +465,13 @@ template <typename TF>
 static void factor_levels(const fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cudaStream_t s) {
   TF *F = reinterpret_cast<TF *>(d->F);
   TF *Y = reinterpret_cast<TF *>(d->Y[buf]);
-  const size_t dsm = 2 * 64 * 65 * sizeof(double);
   const size_t tsm = 2 * 64 * 65 * sizeof(TF);
+  const size_t dsm = 64 * sizeof(double) + 2 * 64 * 65 * sizeof(TF);
   cudaFuncSetAttribute(front_diag_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dsm));
   cudaFuncSetAttribute(front_panel_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
   cudaFuncSetAttribute(front_update_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
+  const size_t t128 = 2 * 64 * kLd128 * sizeof(float);
+  cudaFuncSetAttribute(front_update128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t128));
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
     if (L.asm_n) d->launches++;
@@ -406,9 +487,14 @@ static void factor_levels(const fe_ctx *c, DeviceState *d, int buf, const TF *Af
       if (L.panel_n[st])
         front_panel_kernel<TF><<<unsigned(L.panel_n[st]), 256, tsm, s>>>(d->tasks + L.panel_off[st], d->fronts, F, Y,
                                                                        d->D[buf] + c->n_free);
-      if (L.trail_n[st])
-        front_update_kernel<TF><<<unsigned(L.trail_n[st]), 256, tsm, s>>>(d->tasks + L.trail_off[st], d->fronts, F, Y,
-                                                                        d->D[buf]);
+      if (L.trail_n[st]) {
+        if constexpr (sizeof(TF) == 4)
+          front_update128_kernel<<<unsigned(L.trail_n[st]), 256, t128, s>>>(d->tasks + L.trail_off[st], d->fronts,
+                                                                           F, Y, d->D[buf]);
+        else
+          front_update_kernel<TF><<<unsigned(L.trail_n[st]), 256, tsm, s>>>(d->tasks + L.trail_off[st], d->fronts, F,
+                                                                          Y, d->D[buf]);
+      }
     }
   }
 }

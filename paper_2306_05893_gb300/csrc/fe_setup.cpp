@@ -482,6 +482,8 @@ int build_ordering(fe_ctx *c) {
   c->levels.assign(nf ? maxlv + 1 : 0, Level());
   for (int64_t f = 0; f < nf; ++f) c->levels[c->fronts[f].level].fronts.push_back(int32_t(f));
   double flops = 0;
+  // trailing-update tile: 128 x 128 for the FP32 factor, 64 x 64 for FP64
+  const int32_t ut = c->opt.precision == FE_MIXED ? 128 : kTile;
   for (auto &L : c->levels) {
     int steps = 0;
     for (int32_t f : L.fronts) steps = std::max(steps, (c->fronts[f].npiv + kNB - 1) / kNB);
@@ -507,10 +509,10 @@ int build_ordering(fe_ctx *c) {
         push(L.diag[s], f, (T_DIAG << 24) | k0, kb, 0);
         for (int32_t r0 = k1; r0 < m; r0 += kTile) push(L.panel[s], f, (T_PANEL << 24) | k0, r0, 0);
         for (int32_t c0 = 0; c0 < k0; c0 += kTile) push(L.panel[s], f, (T_XK << 24) | k0, c0, 0);
-        for (int32_t j0 = k1; j0 < m; j0 += kTile)
-          for (int32_t i0 = j0; i0 < m; i0 += kTile) push(L.trail[s], f, (T_TRAIL << 24) | k0, i0, j0);
-        for (int32_t i0 = k1; i0 < m; i0 += kTile)
-          for (int32_t c0 = 0; c0 < k1; c0 += kTile) push(L.trail[s], f, (T_RUPD << 24) | k0, i0, c0);
+        for (int32_t j0 = k1; j0 < m; j0 += ut)
+          for (int32_t i0 = j0; i0 < m; i0 += ut) push(L.trail[s], f, (T_TRAIL << 24) | k0, i0, j0);
+        for (int32_t i0 = k1; i0 < m; i0 += ut)
+          for (int32_t c0 = 0; c0 < k1; c0 += ut) push(L.trail[s], f, (T_RUPD << 24) | k0, i0, c0);
         double rem = double(m - k1);
         flops += double(kb) * kb * kb / 3.0 * 2.0            // diag LDL^T + inverse
                  + 2.0 * rem * kb * kb                        // panel
