@@ -152,6 +152,11 @@ int ensure_device(fe_ctx *c) {
   FE_TRY(upload(c, d, &d->fixed_row, c->fixed_dof));
   FE_TRY(upload(c, d, &d->node_ptr, c->node_ptr));
   FE_TRY(upload(c, d, &d->node_src, c->node_src));
+  FE_TRY(upload(c, d, &d->bptr, c->bptr));
+  FE_TRY(upload(c, d, &d->bcol, c->bcol));
+  FE_TRY(upload(c, d, &d->bsrc_ptr, c->bsrc_ptr));
+  FE_TRY(upload(c, d, &d->bsrc, c->bsrc));
+  FE_TRY(upload(c, d, &d->bmass, c->bmass));
   // state
   FE_TRY(upload(c, d, &d->q, c->X));
   FE_TRY(dalloc(c, d, &d->v, n));
@@ -192,6 +197,7 @@ int ensure_device(fe_ctx *c) {
     o.child_begin = c->child_ptr[f]; o.child_end = c->child_ptr[f + 1];
     o.f_off = F.f_off; o.y_off = F.y_off; o.w_off = F.w_off; o.u_off = F.u_off;
     o.rows_off = F.rows_off; o.fac_off = fac;
+    o.ldy = F.ldy; o.pad_ = 0;
     fac += F.npiv + 1;
   }
   FE_TRY(upload(c, d, &d->fronts, df));
@@ -202,6 +208,8 @@ int ensure_device(fe_ctx *c) {
   FE_TRY(upload(c, d, &d->fa_slot, c->fa_slot));
   FE_TRY(upload(c, d, &d->fa_off, c->fa_off));
   FE_TRY(upload(c, d, &d->fa_colptr, c->fa_colptr));
+  FE_TRY(upload(c, d, &d->wsrc_ptr, c->wsrc_ptr));
+  FE_TRY(upload(c, d, &d->wsrc, c->wsrc));
   // task lists, int4-aligned
   std::vector<int32_t> all;
   std::vector<int32_t> lf;

@@ -12,7 +12,8 @@ namespace fe {
 
 constexpr int kNB = 64;        // panel width of the front factorisation
 constexpr int kTile = 64;      // tile edge of the front update kernels
-constexpr int kApplyRows = 64; // rows per task of the forward apply
+constexpr int kBwdCols = 32;   // pivot columns per task of the backward apply
+inline int fwd_rows(int precision) { return precision == FE_MIXED ? 128 : 64; }  // 32 threads x one 16-byte vector
 
 // Task kinds of the multifrontal factorisation (packed in int4.y >> 24).
 enum TaskKind { T_DIAG = 0, T_PANEL = 1, T_XK = 2, T_TRAIL = 3, T_RUPD = 4 };
@@ -29,6 +30,7 @@ struct Front {
   int64_t u_off = 0;      // offset of the update vector (nupd)
   int64_t rows_off = 0;   // offset into upd_rows_new / upd_rows_old
   int64_t rmap_off = 0;   // offset of this front's map into its parent's front
+  int32_t ldy = 0;        // leading dimension of Y (m rounded up to 4)
   int32_t m() const { return npiv + nupd; }
 };
 
@@ -39,8 +41,8 @@ struct Level {
   std::vector<int32_t> asm_tasks;     // (front, c0, c1) triples
   std::vector<std::vector<int32_t>> diag, panel, trail;  // int4 per task
   // apply task lists
-  std::vector<int32_t> fwd_tasks;     // (front, r0) pairs
-  std::vector<int32_t> bwd_tasks;     // (front, c0) pairs
+  std::vector<int32_t> fwd_tasks;     // (front, r0) pairs, kFwdRows-row blocks
+  std::vector<int32_t> bwd_tasks;     // (front, c0) pairs, kBwdCols-column blocks
 };
 
 struct DeviceState;  // defined in the CUDA translation unit
@@ -69,6 +71,11 @@ struct fe_ctx {
   std::vector<int32_t> slot_src;      // [slot_ptr[nnz]]
   std::vector<double> mass;           // [nnz]
   std::vector<int32_t> node_ptr, node_src;   // node -> (e * npe + a), ascending
+  // 3x3 node-block view of the pattern: node n's blocks [bptr[n], bptr[n+1])
+  // with column node bcol, contributing element blocks (e*npe + a)*npe + b in
+  // bsrc[bsrc_ptr[k] .. bsrc_ptr[k+1]] (ascending), block mass bmass (M = bmass I3)
+  std::vector<int32_t> bptr, bcol, bsrc_ptr, bsrc;
+  std::vector<double> bmass;
   std::vector<double> rest;           // element rest data, SoA [ncoef][n_elems]
   int32_t rest_ncoef = 0;
 
@@ -80,6 +87,7 @@ struct fe_ctx {
   std::vector<int32_t> front_first, front_npiv, front_nupd, front_parent, front_level;
   std::vector<int32_t> upd_rows_new, upd_rows_old;  // per front, update rows
   std::vector<int32_t> rmap;          // per child: positions in its parent's front
+  std::vector<int32_t> wsrc_ptr, wsrc; // per front position (w_off + pos): update-vector entries it gathers
   std::vector<int32_t> child_ptr, child_list;       // children of each front, ascending
   std::vector<int64_t> fa_ptr;        // per front, A entries: [fa_ptr[f], fa_ptr[f+1])
   std::vector<int32_t> fa_slot, fa_off;             // CSR slot, offset in the front

@@ -21,6 +21,7 @@ namespace fe {
 struct DFront {
   int32_t first, npiv, nupd, m;
   int32_t child_begin, child_end;    // into child_list
+  int32_t ldy, pad_;
   int64_t f_off, y_off, w_off, u_off, rows_off, fac_off;
 };
 
@@ -54,6 +55,8 @@ struct DeviceState {
   double *mass = nullptr;
   int8_t *fixed_row = nullptr;
   int32_t *node_ptr = nullptr, *node_src = nullptr;
+  int32_t *bptr = nullptr, *bcol = nullptr, *bsrc_ptr = nullptr, *bsrc = nullptr;
+  double *bmass = nullptr;
 
   // state
   double *q = nullptr, *v = nullptr, *pext = nullptr, *acc = nullptr;
@@ -82,6 +85,7 @@ struct DeviceState {
   DFront *fronts = nullptr;
   int32_t *perm = nullptr, *upd_rows_old = nullptr, *rmap = nullptr, *child_list = nullptr;
   int32_t *fa_slot = nullptr, *fa_off = nullptr;
+  int32_t *wsrc_ptr = nullptr, *wsrc = nullptr;
   int64_t *fa_colptr = nullptr;
   int32_t *tasks = nullptr;        // all task lists, concatenated
   void *F = nullptr;               // front scratch (factor type)

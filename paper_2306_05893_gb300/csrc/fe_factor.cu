@@ -38,8 +38,8 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
     TF *cp = Ff + int64_t(col) * m;
     for (int32_t r = col + threadIdx.x; r < m; r += blockDim.x) cp[r] = TF(0);
     if (col < p) {
-      TF *yp = Y + fr.y_off + int64_t(col) * m;
-      for (int32_t r = threadIdx.x; r < m; r += blockDim.x) yp[r] = TF(0);
+      TF *yp = Y + fr.y_off + int64_t(col) * fr.ldy;
+      for (int32_t r = threadIdx.x; r < fr.ldy; r += blockDim.x) yp[r] = TF(0);
     }
   }
   __syncthreads();
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) front_diag_kernel(const int32_t *__restri
   for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
     const int i = idx % kb, j = idx / kb;
     if (i > j) Ff[(k0 + i) + int64_t(k0 + j) * m] = L[i][j];
-    Yf[(k0 + i) + int64_t(k0 + j) * m] = Xi[i][j];
+    Yf[(k0 + i) + int64_t(k0 + j) * fr.ldy] = Xi[i][j];
   }
 }
 
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
   TF *Yf = Y + fr.y_off;
   for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
     const int i = idx % 64, j = idx / 64;
-    Ls[i][j] = (i < kb && j < kb && i >= j) ? Yf[(k0 + i) + int64_t(k0 + j) * m] : TF(0);
+    Ls[i][j] = (i < kb && j < kb && i >= j) ? Yf[(k0 + i) + int64_t(k0 + j) * fr.ldy] : TF(0);
   }
   const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
   if (kind == T_PANEL) {
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
   } else {  // T_XK
     for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
       const int j = idx % 64, c = idx / 64;
-      Bs[j][c] = (j < kb && a0 + c < k0) ? Yf[(k0 + j) + int64_t(a0 + c) * m] : TF(0);
+      Bs[j][c] = (j < kb && a0 + c < k0) ? Yf[(k0 + j) + int64_t(a0 + c) * fr.ldy] : TF(0);
     }
     __syncthreads();
     TF acc[4][4] = {};
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const int32_t c = a0 + tc + 16 * s;
-        if (c < k0) Yf[(k0 + i) + int64_t(c) * m] = acc[u][s];
+        if (c < k0) Yf[(k0 + i) + int64_t(c) * fr.ldy] = acc[u][s];
       }
     }
   }
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
     for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
       const int l = idx % 64, j = idx / 64;
       const int32_t c = j0 + j;
-      Bs[j][l] = (l < kb && c < k0 + kb) ? Yf[(k0 + l) + int64_t(c) * m] : TF(0);
+      Bs[j][l] = (l < kb && c < k0 + kb) ? Yf[(k0 + l) + int64_t(c) * fr.ldy] : TF(0);
     }
   }
   __syncthreads();
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int32_t r = i0 + tr + 16 * u;
-        if (r < m) Yf[r + int64_t(c) * m] -= acc[u][s];
+        if (r < m) Yf[r + int64_t(c) * fr.ldy] -= acc[u][s];
       }
     }
   }
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256) front_update128_kernel(const int32_t *__r
     for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
       const int l = idx % 64, j = idx / 64;
       const int32_t c = j0 + j;
-      Bs[l * kLd128 + j] = (l < kb && c < k0 + kb) ? Yf[(k0 + l) + int64_t(c) * m] : 0.f;
+      Bs[l * kLd128 + j] = (l < kb && c < k0 + kb) ? Yf[(k0 + l) + int64_t(c) * fr.ldy] : 0.f;
     }
   }
   __syncthreads();
@@ -366,97 +366,160 @@ __global__ void __launch_bounds__(256) front_update128_kernel(const int32_t *__r
     for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
       const int j = idx / kT128, i = idx % kT128;
       const int32_t r = i0 + i, c = j0 + j;
-      if (r < m && c < k0 + kb) Yf[r + int64_t(c) * m] -= Cs[i * 129 + j];
+      if (r < m && c < k0 + kb) Yf[r + int64_t(c) * fr.ldy] -= Cs[i * 129 + j];
     }
   }
 }
 
 // ------------------------------------------------------------------ apply
-// Forward, part 1 (one block per front of the level): w = [r_P; 0] plus the
-// children's update vectors extend-added in fixed order.
-template <typename TV>
-__global__ void __launch_bounds__(256) fwd_gather_kernel(const int32_t *__restrict__ level_fronts,
-                                                         const DFront *__restrict__ fronts,
-                                                         const int32_t *__restrict__ child_list,
-                                                         const int32_t *__restrict__ rmap,
-                                                         const int32_t *__restrict__ perm,
-                                                         const TV *__restrict__ r, TV *__restrict__ wbuf,
-                                                         const TV *__restrict__ ubuf) {
-  const DFront fr = fronts[level_fronts[blockIdx.x]];
-  TV *w = wbuf + fr.w_off;
-  for (int32_t i = threadIdx.x; i < fr.m; i += blockDim.x) w[i] = (i < fr.npiv) ? r[perm[fr.first + i]] : TV(0);
-  __syncthreads();
-  for (int32_t ci = fr.child_begin; ci < fr.child_end; ++ci) {
-    const DFront ch = fronts[child_list[ci]];
-    const int32_t *rm = rmap + ch.rows_off;
-    const TV *u = ubuf + ch.u_off;
-    for (int32_t j = threadIdx.x; j < ch.nupd; j += blockDim.x) w[rm[j]] += u[j];
-    __syncthreads();
-  }
-}
+// 16-byte vectors along the rows of Y (its leading dimension is a multiple of 4).
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
 
-// Forward, part 2, task (front, r0): rows [r0, r0+64) of Y w_P;
-// y_P (times D^{-1}) to yperm, U rows to the update vector.
+// Forward level, task (front, r0): rows [r0, r0 + 32*VW) of Y w_P, where
+// w = [r_P; 0] + the children's update vectors (gathered on the fly through
+// the position lists, children in fixed order).  256 threads: 32 row lanes
+// of VW consecutive rows (one 16-byte load per column) x 8 column groups.
+// Rows < p give y_P (times D^{-1}) into yperm, rows >= p the update vector.
 template <typename TF, typename TV>
-__global__ void __launch_bounds__(256) fwd_gemv_kernel(const int32_t *__restrict__ tasks,
-                                                       const DFront *__restrict__ fronts,
-                                                       const TF *__restrict__ Y,
-                                                       const double *__restrict__ Dinv,
-                                                       const TV *__restrict__ wbuf, TV *__restrict__ ubuf,
-                                                       TV *__restrict__ yperm) {
-  extern __shared__ unsigned char sraw[];
-  TV *wp = reinterpret_cast<TV *>(sraw);
-  __shared__ TV part[4][64];
+__global__ void __launch_bounds__(256) fwd_kernel(const int32_t *__restrict__ tasks,
+                                                  const DFront *__restrict__ fronts, const TF *__restrict__ Y,
+                                                  const double *__restrict__ Dinv,
+                                                  const int32_t *__restrict__ perm,
+                                                  const int32_t *__restrict__ wsrc_ptr,
+                                                  const int32_t *__restrict__ wsrc, const TV *__restrict__ r,
+                                                  TV *__restrict__ ubuf, TV *__restrict__ yperm) {
+  using V = typename Vec16<TF>::type;
+  constexpr int VW = Vec16<TF>::n;
+  constexpr int RB = 32 * VW;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  TV *part = reinterpret_cast<TV *>(fsm);      // [8][RB]
+  TV *wp = part + 8 * RB;                       // [jmax]
   const DFront fr = fronts[tasks[2 * blockIdx.x]];
   const int32_t r0 = tasks[2 * blockIdx.x + 1];
   const int32_t p = fr.npiv, m = fr.m;
-  const TV *w = wbuf + fr.w_off;
-  const int32_t rend = (r0 + 64 < m) ? r0 + 64 : m;
-  const int32_t jmax = (rend < p) ? rend : p;
-  for (int32_t j = threadIdx.x; j < jmax; j += blockDim.x) wp[j] = w[j];
-  __syncthreads();
-  const int lr = threadIdx.x & 63, g = threadIdx.x >> 6;
-  const int32_t row = r0 + lr;
-  TV acc = TV(0);
-  if (row < m) {
-    const int32_t je = (row < p) ? row + 1 : p;
-    const TF *yc = Y + fr.y_off + row;
-    for (int32_t j = g; j < je; j += 4) acc += TV(yc[int64_t(j) * m]) * wp[j];
+  const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
+  for (int32_t j = threadIdx.x; j < jmax; j += 256) {
+    const int64_t q0 = wsrc_ptr[fr.w_off + j], q1 = wsrc_ptr[fr.w_off + j + 1];
+    TV w = r[perm[fr.first + j]];
+    for (int64_t q = q0; q < q1; ++q) w += ubuf[wsrc[q]];
+    wp[j] = w;
   }
-  part[g][lr] = acc;
   __syncthreads();
-  if (g == 0 && row < m) {
-    const TV s = part[0][lr] + part[1][lr] + part[2][lr] + part[3][lr];
-    if (row < p)
-      yperm[fr.first + row] = TV(double(s) * Dinv[fr.first + row]);
-    else
-      ubuf[fr.u_off + row - p] = w[row] + s;
+  const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int32_t row = r0 + VW * rl;
+  TV acc[VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) acc[e] = TV(0);
+  if (row < m) {
+    const TF *yc = Y + fr.y_off + row;
+    int32_t j = g;
+    for (; j + 24 < jmax; j += 32) {
+      V v0 = *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy);
+      V v1 = *reinterpret_cast<const V *>(yc + int64_t(j + 8) * fr.ldy);
+      V v2 = *reinterpret_cast<const V *>(yc + int64_t(j + 16) * fr.ldy);
+      V v3 = *reinterpret_cast<const V *>(yc + int64_t(j + 24) * fr.ldy);
+      const TF *e0 = reinterpret_cast<const TF *>(&v0), *e1 = reinterpret_cast<const TF *>(&v1);
+      const TF *e2 = reinterpret_cast<const TF *>(&v2), *e3 = reinterpret_cast<const TF *>(&v3);
+      const TV w0 = wp[j], w1 = wp[j + 8], w2 = wp[j + 16], w3 = wp[j + 24];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0 + TV(e1[e]) * w1 + TV(e2[e]) * w2 + TV(e3[e]) * w3;
+    }
+    for (; j < jmax; j += 8) {
+      V v0 = *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy);
+      const TF *e0 = reinterpret_cast<const TF *>(&v0);
+      const TV w0 = wp[j];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < VW; ++e) part[g * RB + VW * rl + e] = acc[e];
+  __syncthreads();
+  for (int t = threadIdx.x; t < RB; t += 256) {
+    const int32_t i = r0 + t;
+    if (i >= m) continue;
+    TV s = TV(0);
+#pragma unroll
+    for (int gg = 0; gg < 8; ++gg) s += part[gg * RB + t];
+    if (i < p) {
+      yperm[fr.first + i] = TV(double(s) * Dinv[fr.first + i]);
+    } else {
+      TV w = TV(0);
+      for (int64_t q = wsrc_ptr[fr.w_off + i]; q < wsrc_ptr[fr.w_off + i + 1]; ++q) w += ubuf[wsrc[q]];
+      ubuf[fr.u_off + i - p] = w + s;
+    }
   }
 }
 
-// Backward, task (front, c0): one warp per pivot column j in [c0, c0+8):
-// z_j = sum_i Y[i, j] x_i, x = [D^{-1} y_P; z_U].
+// Backward level, task (front, c0): pivot columns [c0, c0 + 32); warp w owns
+// columns c0 + w + 8k (k = 0..3) and streams them together (four 16-byte
+// loads in flight per lane).  x = [D^{-1} y_P; z_U] is staged in shared
+// memory from the VW-aligned row at or below c0; rows above a column are
+// zeros of L^{-1}, so reading from the aligned row is exact.
 template <typename TF, typename TV>
 __global__ void __launch_bounds__(256) bwd_kernel(const int32_t *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
                                                   const int32_t *__restrict__ perm,
                                                   const int32_t *__restrict__ upd_rows_old,
                                                   const TV *__restrict__ yperm, TV *__restrict__ z) {
+  using V = typename Vec16<TF>::type;
+  constexpr int VW = Vec16<TF>::n;
+  extern __shared__ __align__(16) unsigned char bsm[];
+  TV *xs = reinterpret_cast<TV *>(bsm);
   const DFront fr = fronts[tasks[2 * blockIdx.x]];
-  const int32_t j = tasks[2 * blockIdx.x + 1] + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (j >= fr.npiv) return;
+  const int32_t c0 = tasks[2 * blockIdx.x + 1];
   const int32_t p = fr.npiv, m = fr.m;
-  const TF *yc = Y + fr.y_off + int64_t(j) * m;
+  const int32_t a0 = c0 & ~(VW - 1);
+  const int32_t nx = fr.ldy - a0;
   const int32_t *urows = upd_rows_old + fr.rows_off;
-  TV acc = TV(0);
-  for (int32_t i = j + lane; i < m; i += 32) {
-    const TV xi = (i < p) ? yperm[fr.first + i] : z[urows[i - p]];
-    acc += TV(yc[i]) * xi;
+  for (int32_t t = threadIdx.x; t < nx; t += 256) {
+    const int32_t i = a0 + t;
+    xs[t] = (i < c0 || i >= m) ? TV(0) : (i < p ? yperm[fr.first + i] : z[urows[i - p]]);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t jc[4];
+  const TF *yc[4];
+  int32_t i0[4];
+  TV acc[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    jc[k] = c0 + w + 8 * k;
+    const int32_t j = jc[k] < p ? jc[k] : c0;  // out-of-range columns read a valid one, result dropped
+    yc[k] = Y + fr.y_off + int64_t(j) * fr.ldy;
+    i0[k] = (j & ~(VW - 1)) + VW * lane;
+    acc[k] = TV(0);
+  }
+  const int32_t ilo = i0[0] < i0[3] ? i0[0] : i0[3];
+  for (int32_t off = 0; ilo + off < fr.ldy; off += 32 * VW) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int32_t i = i0[k] + off;
+      if (i < fr.ldy) {
+        V v = *reinterpret_cast<const V *>(yc[k] + i);
+        const TF *e = reinterpret_cast<const TF *>(&v);
+#pragma unroll
+        for (int q = 0; q < VW; ++q) acc[k] += TV(e[q]) * xs[i - a0 + q];
+      }
+    }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) z[perm[fr.first + j]] = acc;
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if (lane == 0 && jc[k] < p) z[perm[fr.first + jc[k]]] = acc[k];
+  }
 }
 
 // ------------------------------------------------------------ host drivers
@@ -511,24 +574,28 @@ template <typename TF, typename TV>
 static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, cudaStream_t s) {
   const TF *Y = reinterpret_cast<const TF *>(d->Y[buf]);
   const double *Dinv = d->D[buf] + c->n_free;
-  TV *w = reinterpret_cast<TV *>(d->wbuf);
   TV *u = reinterpret_cast<TV *>(d->ubuf);
   TV *yp = reinterpret_cast<TV *>(d->yperm);
-  int32_t pmax = 0;
-  for (const auto &f : c->fronts) pmax = std::max(pmax, f.npiv);
-  const size_t sm = size_t(pmax) * sizeof(TV);
-  cudaFuncSetAttribute(fwd_gemv_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-  d->launches += 3 * int64_t(d->lt.size());
+  int32_t pmax = 0, lmax = 0;
+  for (const auto &f : c->fronts) {
+    pmax = std::max(pmax, f.npiv);
+    lmax = std::max(lmax, f.ldy);
+  }
+  constexpr int RB = 32 * Vec16<TF>::n;
+  const size_t fsm = size_t(8 * RB + pmax) * sizeof(TV);
+  const size_t bsm = size_t(lmax) * sizeof(TV);
+  cudaFuncSetAttribute(fwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm));
+  cudaFuncSetAttribute(bwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bsm));
+  d->launches += 2 * int64_t(d->lt.size());
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
-    fwd_gather_kernel<TV><<<unsigned(L.nfronts), 256, 0, s>>>(d->level_fronts + L.fronts_off, d->fronts,
-                                                              d->child_list, d->rmap, d->perm, r, w, u);
-    fwd_gemv_kernel<TF, TV><<<unsigned(L.fwd_n), 256, sm, s>>>(d->tasks + L.fwd_off, d->fronts, Y, Dinv, w, u, yp);
+    fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, fsm, s>>>(d->tasks + L.fwd_off, d->fronts, Y, Dinv, d->perm,
+                                                           d->wsrc_ptr, d->wsrc, r, u, yp);
   }
   for (size_t lv = d->lt.size(); lv-- > 0;) {
     const auto &L = d->lt[lv];
-    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, 0, s>>>(d->tasks + L.bwd_off, d->fronts, Y, d->perm,
-                                                         d->upd_rows_old, yp, z);
+    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, bsm, s>>>(d->tasks + L.bwd_off, d->fronts, Y, d->perm,
+                                                           d->upd_rows_old, yp, z);
   }
 }
 

@@ -273,48 +273,87 @@ void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool
 }
 
 // ------------------------------------------------------ gather assembly
-// One warp per CSR row.  Slot s: K_s = sum of its triplets (ascending ids, as
-// the inverse of C lists them), A_s = cM M_s + cK K_s; the row of b gathers
-// the element forces of its node and subtracts (alpha M + (beta+h) K) v.
+// One warp per node over its 3x3 node blocks (lanes = blocks).  A block sums
+// its element blocks' 9 contiguous values in ascending order (the order of
+// the inverse of C, so every slot equals the per-slot sum), writes its 9
+// slots (rows 3n+i, position 3*bp + k in the row) and its share of
+// (alpha M + (beta+h) K) v; the node's element forces come from its
+// incidence list.  Fixed nodes keep the lone unit diagonal and b = 0.
 template <typename TK, typename TA>
-__global__ void __launch_bounds__(256) assemble_kernel(
-    int64_t n, int npe, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind,
-    const int32_t *__restrict__ slot_ptr, const int32_t *__restrict__ slot_src,
-    const TK *__restrict__ Ke, const double *__restrict__ mass, const TK *__restrict__ fe,
+__global__ void __launch_bounds__(256) assemble_block_kernel(
+    int64_t n_nodes, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ bptr,
+    const int32_t *__restrict__ bcol, const int32_t *__restrict__ bsrc_ptr, const int32_t *__restrict__ bsrc,
+    const double *__restrict__ bmass, const TK *__restrict__ Ke, const TK *__restrict__ fe,
     const int32_t *__restrict__ node_ptr, const int32_t *__restrict__ node_src,
     const int8_t *__restrict__ fixed_row, const double *__restrict__ v, const double *__restrict__ p,
     double cM, double cK, double al, double bh, TA *__restrict__ A, double *__restrict__ b) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t row = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n; row += warps) {
-    const int32_t s0 = rowptr[row], s1 = rowptr[row + 1];
-    if (fixed_row[row]) {
-      if (lane == 0) {
-        A[s0] = TA(1);
-        b[row] = 0.0;
+  for (int64_t nd = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); nd < n_nodes; nd += warps) {
+    const int64_t r0 = 3 * nd;
+    if (fixed_row[r0]) {
+      if (lane < 3) {
+        A[rowptr[r0 + lane]] = TA(1);
+        b[r0 + lane] = 0.0;
       }
       continue;
     }
-    double acc = 0.0;
-    for (int32_t s = s0 + lane; s < s1; s += 32) {
-      double Ks = 0.0;
-      const int32_t j1 = slot_ptr[s + 1];
-      for (int32_t j = slot_ptr[s]; j < j1; ++j) Ks += double(Ke[slot_src[j]]);
-      const double Ms = mass[s];
-      A[s] = TA(cM * Ms + cK * Ks);
-      acc += (al * Ms + bh * Ks) * v[colind[s]];
+    const int32_t rp0 = rowptr[r0], rp1 = rowptr[r0 + 1], rp2 = rowptr[r0 + 2];
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    for (int32_t k = bptr[nd] + lane; k < bptr[nd + 1]; k += 32) {
+      double blk[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) blk[q] = 0.0;
+      const int32_t j1 = bsrc_ptr[k + 1];
+      for (int32_t j = bsrc_ptr[k]; j < j1; ++j) {
+        const TK *src = Ke + int64_t(bsrc[j]) * 9;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) blk[q] += double(src[q]);
+      }
+      const double mb = bmass[k];
+      const int32_t bp = 3 * (k - bptr[nd]);
+      const int64_t cn = 3 * int64_t(bcol[k]);
+      const double v0 = v[cn], v1 = v[cn + 1], v2 = v[cn + 2];
+      const int32_t rps[3] = {rp0, rp1, rp2};
+      double part[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double vv[3] = {v0, v1, v2};
+        double s = 0.0;
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          const double Ms = (i == kk) ? mb : 0.0;
+          const double Ks = blk[3 * i + kk];
+          A[rps[i] + bp + kk] = TA(cM * Ms + cK * Ks);
+          s += (al * Ms + bh * Ks) * vv[kk];
+        }
+        part[i] = s;
+      }
+      acc0 += part[0];
+      acc1 += part[1];
+      acc2 += part[2];
     }
-    const int64_t node = row / 3;
-    const int comp = int(row - 3 * node);
-    double fs = 0.0;
-    for (int32_t j = node_ptr[node] + lane; j < node_ptr[node + 1]; j += 32)
-      fs += double(fe[int64_t(node_src[j]) * 3 + comp]);
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    for (int32_t j = node_ptr[nd] + lane; j < node_ptr[nd + 1]; j += 32) {
+      const TK *fs = fe + int64_t(node_src[j]) * 3;
+      f0 += double(fs[0]);
+      f1 += double(fs[1]);
+      f2 += double(fs[2]);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      fs += __shfl_xor_sync(0xffffffffu, fs, o);
+      acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+      acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+      acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+      f0 += __shfl_xor_sync(0xffffffffu, f0, o);
+      f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+      f2 += __shfl_xor_sync(0xffffffffu, f2, o);
     }
-    if (lane == 0) b[row] = (p ? p[row] : 0.0) - fs - acc;
+    if (lane < 3) {
+      const double acc = lane == 0 ? acc0 : (lane == 1 ? acc1 : acc2);
+      const double ff = lane == 0 ? f0 : (lane == 1 ? f1 : f2);
+      b[r0 + lane] = (p ? p[r0 + lane] : 0.0) - ff - acc;
+    }
   }
 }
 
@@ -323,16 +362,16 @@ void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const dou
   d->launches++;
   const double h = c->h, al = c->alpha, be = c->beta;
   const double cM = 1.0 + h * al, cK = h * (be + h), bh = be + h;
-  const int64_t n = c->n;
-  const unsigned grid = unsigned(std::min<int64_t>((n + 7) / 8, 152 * 64));
+  const int64_t nn = c->n_nodes;
+  const unsigned grid = unsigned(std::min<int64_t>((nn + 7) / 8, 152 * 64));
   if (fp32)
-    assemble_kernel<float, float><<<grid, 256, 0, s>>>(
-        n, c->npe, d->rowptr, d->colind, d->slot_ptr, d->slot_src, (const float *)d->Ke, d->mass,
+    assemble_block_kernel<float, float><<<grid, 256, 0, s>>>(
+        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const float *)d->Ke,
         (const float *)d->fe, d->node_ptr, d->node_src, d->fixed_row, d->v, pext, cM, cK, al, bh,
         (float *)d->A, d->b);
   else
-    assemble_kernel<double, double><<<grid, 256, 0, s>>>(
-        n, c->npe, d->rowptr, d->colind, d->slot_ptr, d->slot_src, (const double *)d->Ke, d->mass,
+    assemble_block_kernel<double, double><<<grid, 256, 0, s>>>(
+        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const double *)d->Ke,
         (const double *)d->fe, d->node_ptr, d->node_src, d->fixed_row, d->v, pext, cM, cK, al, bh,
         (double *)d->A, d->b);
 }

@@ -224,6 +224,36 @@ int build_mass_and_rest(fe_ctx *c) {
   return FE_OK;
 }
 
+// ------------------------------------------------------ node-block view
+// Every free node's three rows share one column structure (whole nodes are
+// fixed), so the pattern is a set of 3x3 node blocks and the 9 slots of a
+// block gather the same element blocks (e, a, b), whose 9 values are
+// contiguous in K_e.  The block lists come from the (0, 0) slot of each block.
+int build_blocks(fe_ctx *c) {
+  const int64_t nn = c->n_nodes;
+  c->bptr.assign(nn + 1, 0);
+  c->bcol.clear();
+  c->bsrc_ptr.clear();
+  c->bsrc.clear();
+  c->bmass.clear();
+  for (int64_t v = 0; v < nn; ++v) {
+    c->bptr[v] = int32_t(c->bcol.size());
+    const int64_t r0 = 3 * v;
+    if (c->fixed_dof[r0]) continue;
+    const int32_t s0 = c->rowptr[r0], s1 = c->rowptr[r0 + 1];
+    if ((s1 - s0) % 3 != 0) return set_error(c, FE_ERR_ARG, "row length not a multiple of 3");
+    for (int32_t s = s0; s < s1; s += 3) {
+      c->bcol.push_back(c->colind[s] / 3);
+      c->bsrc_ptr.push_back(int32_t(c->bsrc.size()));
+      for (int64_t q = c->slot_ptr[s]; q < c->slot_ptr[s + 1]; ++q) c->bsrc.push_back(c->slot_src[q] / 9);
+      c->bmass.push_back(c->mass[s]);
+    }
+  }
+  c->bptr[nn] = int32_t(c->bcol.size());
+  c->bsrc_ptr.push_back(int32_t(c->bsrc.size()));
+  return FE_OK;
+}
+
 // ------------------------------------------------------- nested dissection
 struct ND {
   fe_ctx *c;
@@ -384,8 +414,9 @@ int build_ordering(fe_ctx *c) {
     for (int32_t k : nd.fr[f].kids) lv = std::max(lv, c->fronts[k].level + 1);
     F.level = lv;
     int64_t m = F.m();
+    F.ldy = int32_t((m + 3) / 4 * 4);
     F.f_off = f_total; f_total += m * m;
-    F.y_off = y_total; y_total += m * F.npiv;
+    F.y_off = y_total; y_total += int64_t(F.ldy) * F.npiv;
     F.w_off = w_total; w_total += m;
     F.u_off = u_total; u_total += F.nupd;
     F.rows_off = rows_total; rows_total += F.nupd;
@@ -430,6 +461,23 @@ int build_ordering(fe_ctx *c) {
       }
       c->rmap[F.rows_off + j] = loc;
     }
+  }
+  // gather lists of the forward apply: front position -> children's update entries
+  {
+    std::vector<std::vector<int32_t>> lists(w_total);
+    for (int64_t f = 0; f < nf; ++f)
+      for (int32_t k : nd.fr[f].kids) {
+        const Front &Ch = c->fronts[k];
+        for (int32_t j = 0; j < Ch.nupd; ++j)
+          lists[c->fronts[f].w_off + c->rmap[Ch.rows_off + j]].push_back(int32_t(Ch.u_off + j));
+      }
+    c->wsrc_ptr.assign(w_total + 1, 0);
+    c->wsrc.clear();
+    for (int64_t q = 0; q < w_total; ++q) {
+      c->wsrc_ptr[q] = int32_t(c->wsrc.size());
+      c->wsrc.insert(c->wsrc.end(), lists[q].begin(), lists[q].end());
+    }
+    c->wsrc_ptr[w_total] = int32_t(c->wsrc.size());
   }
   // A entries of every front (lower triangle in the new order), by column
   c->fa_ptr.assign(nf + 1, 0);
@@ -484,6 +532,7 @@ int build_ordering(fe_ctx *c) {
   double flops = 0;
   // trailing-update tile: 128 x 128 for the FP32 factor, 64 x 64 for FP64
   const int32_t ut = c->opt.precision == FE_MIXED ? 128 : kTile;
+  const int32_t fr_rows = fwd_rows(c->opt.precision);
   for (auto &L : c->levels) {
     int steps = 0;
     for (int32_t f : L.fronts) steps = std::max(steps, (c->fronts[f].npiv + kNB - 1) / kNB);
@@ -499,8 +548,8 @@ int build_ordering(fe_ctx *c) {
         L.asm_tasks.push_back(c0);
         L.asm_tasks.push_back(std::min(m, c0 + 32));
       }
-      for (int32_t r0 = 0; r0 < m; r0 += kApplyRows) { L.fwd_tasks.push_back(f); L.fwd_tasks.push_back(r0); }
-      for (int32_t c0 = 0; c0 < p; c0 += 8) { L.bwd_tasks.push_back(f); L.bwd_tasks.push_back(c0); }
+      for (int32_t r0 = 0; r0 < m; r0 += fr_rows) { L.fwd_tasks.push_back(f); L.fwd_tasks.push_back(r0); }
+      for (int32_t c0 = 0; c0 < p; c0 += kBwdCols) { L.bwd_tasks.push_back(f); L.bwd_tasks.push_back(c0); }
       for (int s = 0; s * kNB < p; ++s) {
         const int32_t k0 = s * kNB, kb = std::min(kNB, p - k0), k1 = k0 + kb;
         auto push = [](std::vector<int32_t> &v, int32_t a, int32_t b, int32_t cc, int32_t d) {
@@ -536,6 +585,8 @@ int build_pattern_host(fe_ctx *c) {
   int st = build_csr(c);
   if (st) return st;
   st = build_mass_and_rest(c);
+  if (st) return st;
+  st = build_blocks(c);
   if (st) return st;
   st = build_ordering(c);
   if (st) return st;
