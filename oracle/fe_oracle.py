@@ -219,7 +219,8 @@ class Quadrature:
 
 
 def _params(params, E):
-    p = np.asarray(params, dtype=np.float64)
+    p = np.asarray(params)
+    p = p.astype(np.result_type(p.dtype, np.float64))  # complex parameters stay complex
     if p.ndim == 1:
         p = np.broadcast_to(p, (E, 3))
     return p[:, 0][:, None], p[:, 1][:, None], p[:, 2][:, None]   # [E, 1] each
@@ -358,7 +359,8 @@ class Model:
         fn = np.asarray(fixed_nodes, dtype=np.int64)
         self.fixed_dofs = (3 * fn[:, None] + np.arange(3)[None, :]).reshape(-1)
         self.model = model
-        self.params = np.asarray(params, dtype=np.float64)
+        self.params = np.asarray(params)
+        self.params = self.params.astype(np.result_type(self.params.dtype, np.float64))
         self.rho, self.h, self.alpha, self.beta = rho, h, alpha, beta
         self.quad = Quadrature(elem_type, self.X, self.conn)
         self.m_e = element_mass(elem_type, self.X, self.conn, rho)
@@ -430,3 +432,77 @@ def rollout(model, q0, v0, loads, n_steps):
         qs.append(q)
         vs.append(v)
     return np.array(qs), np.array(vs)
+
+
+# ================================================================ adjoint
+# Discrete adjoint of the rollout (reading C-12 of the reconstruction notes):
+# step residual R(a; q, v, s, p) = A(q, s) a - b(q, v, s, p) with every
+# element's energy scaled by s_e (Young's modulus E_e = s_e * E_ref at fixed
+# nu, or the three Mooney-Rivlin constants together).  Backwards:
+#   a_bar = h v_bar_{t+1} + h^2 q_bar_{t+1};   A_t lambda = a_bar
+#   q_bar_t = q_bar_{t+1} - (c_K dK[lambda] a + (beta+h) dK[lambda] v + K lambda)
+#   v_bar_t = v_bar_{t+1} + h q_bar_{t+1} - (alpha M + (beta+h) K) lambda
+#   s_bar_e -= lambda_e . (c_K K_e a_e + f_e + (beta+h) K_e v_e)
+#   p_bar_t = lambda
+# dK[lambda] u is the directional derivative of the element tangents along
+# lambda, taken here by a complex step of the analytic tangent.
+
+def _gather_elem(conn, x):
+    xe = np.asarray(x).reshape(-1, 3)[conn]
+    return xe.reshape(conn.shape[0], -1)
+
+
+def _scatter_elem(n_dof, conn, ve):
+    out = np.zeros(n_dof, dtype=ve.dtype)
+    dofs = (3 * conn[:, :, None] + np.arange(3)[None, None, :]).reshape(conn.shape[0], -1)
+    np.add.at(out, dofs.reshape(-1), ve.reshape(-1))
+    return out
+
+
+def rollout_with_history(model, q0, v0, loads, T):
+    qs, vs, accs = [q0.copy()], [v0.copy()], []
+    q, v = q0.copy(), v0.copy()
+    for t in range(T):
+        q, v, a = model.step(q, v, loads(t))
+        qs.append(q)
+        vs.append(v)
+        accs.append(a)
+    return qs, vs, accs
+
+
+def adjoint_rollout(model, q0, v0, loads, T, q_target, v_bar_T=None):
+    """Loss L = 1/2 ||q_T - q_target||^2 and its gradients:
+    returns (L, dL/ds [E] for the per-element energy scales, dL/dp [T, n])."""
+    h, al, be = model.h, model.alpha, model.beta
+    cK = h * (be + h)
+    qs, vs, accs = rollout_with_history(model, q0, v0, loads, T)
+    diff = qs[T] - q_target
+    loss = 0.5 * float(diff @ diff)
+    q_bar = diff.copy()
+    v_bar = np.zeros_like(q_bar) if v_bar_T is None else np.asarray(v_bar_T, dtype=np.float64).copy()
+    s_bar = np.zeros(model.conn.shape[0])
+    p_bar = np.zeros((T, model.n_dof))
+    conn = model.conn
+    for t in range(T - 1, -1, -1):
+        q, v, a = qs[t], vs[t], accs[t]
+        A, _ = model.system(q, v, loads(t))
+        a_bar = h * v_bar + h * h * q_bar
+        a_bar[model.fixed_dofs] = 0.0
+        lam = direct_solve(A, a_bar)
+        lam[model.fixed_dofs] = 0.0
+        Ke = model.element_tangent(q)
+        fe = model.element_force(q)
+        ae, ve, le = _gather_elem(conn, a), _gather_elem(conn, v), _gather_elem(conn, lam)
+        u = cK * ae + (be + h) * ve
+        eps = 1e-30
+        Kc = element_tangent(model.quad, (q + 1j * eps * lam).reshape(-1, 3), model.model, model.params)
+        dKu = np.einsum("eij,ej->ei", Kc.imag / eps, u)
+        Kl = np.einsum("eij,ej->ei", Ke, le)
+        gq = _scatter_elem(model.n_dof, conn, dKu + Kl)
+        Klam = _scatter_elem(model.n_dof, conn, Kl)
+        gv = al * (model.M @ lam) + (be + h) * Klam
+        s_bar -= np.einsum("ei,ei->e", le, cK * np.einsum("eij,ej->ei", Ke, ae) + fe
+                           + (be + h) * np.einsum("eij,ej->ei", Ke, ve))
+        p_bar[t] = lam
+        q_bar, v_bar = q_bar - gq, v_bar + h * q_bar - gv
+    return loss, s_bar, p_bar
