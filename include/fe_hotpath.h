@@ -174,6 +174,26 @@ int fe_assemble(fe_ctx *ctx, const double *p_ext, double *A_vals, double *b);
 int fe_factor_now(fe_ctx *ctx);
 int fe_apply_preconditioner(fe_ctx *ctx, const double *r, double *z);
 
+/* Allocation-free variant of fe_apply_preconditioner, for callers that
+ * cannot call cudaMalloc: an interactive simulator's real-time loop, where an
+ * allocation's implicit device synchronisation and latency would break the
+ * frame budget, or a host whose device memory is already fully reserved by
+ * another allocator.  (The paper has no counterpart; this is a library
+ * convenience.)
+ *   r, z: DEVICE pointers to [n] FP64 vectors (z = P^{-1} r), whatever
+ *         fe_options.device_ptrs says; stream: cudaStream_t (NULL: legacy).
+ * The call is asynchronous on `stream` and allocates nothing: its work
+ * vectors live in one file-scope device array of 64 MiB that every GPU
+ * loading the library holds until exit.  A mesh needing more (about
+ * (2 n + update rows + free DOFs) x 4 or 8 bytes) is rejected with
+ * FE_ERR_ARG.  The context must already hold a factor (fe_factor_now or
+ * fe_step) and its device must be current.  The first call on a device looks
+ * the array's address up (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents (the call clears what must start at zero): calls that
+ * overlap on the GPU, on any stream or context, race. */
+int fe_apply_preconditioner_noalloc(fe_ctx *ctx, const double *r, double *z, void *stream);
+
 /* One implicit step with external nodal forces p_ext [n] (NULL = 0), one
  * Newton iteration (Eq. "taylor expansion").  Writes the new q, v when the
  * pointers are non-NULL; info may be NULL. */

@@ -67,6 +67,7 @@ SIGNATURES = {
     "fe_assemble": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "fe_factor_now": (ct.c_int, [CTX]),
     "fe_apply_preconditioner": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p]),
+    "fe_apply_preconditioner_noalloc": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "fe_step": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p, P(FeStepInfo)]),
     "fe_get_info": (ct.c_int, [CTX, P(FeInfo)]),
     "fe_get_stage_times": (ct.c_int, [CTX, DP, P(ct.c_int64), P(ct.c_int64)]),

@@ -16,6 +16,8 @@
 // (leaves up for L, root down for L^T), as in the paper's level schedule.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "fe_device.cuh"
 
 namespace fe {
@@ -607,4 +609,100 @@ void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, co
     apply_levels<double, double>(c, d, buf, reinterpret_cast<const double *>(r), reinterpret_cast<double *>(z), s);
 }
 
+
+// ============================================= allocation-free application
+// For callers that cannot call cudaMalloc: a real-time loop (an interactive
+// simulator's haptic or servo loop, where cudaMalloc's implicit device
+// synchronisation and unbounded latency would break the frame budget), or a
+// host whose device memory is already fully reserved by another allocator.
+// The work vectors of one preconditioner application live in this
+// file-scope array instead; the context's factor is only read.
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB, held by every GPU that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+std::mutex g_noalloc_mutex;
+void *g_noalloc_base[64] = {nullptr};  // device address of the array, per device
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+template <typename TF, typename TV>
+void apply_levels_into(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, TV *u, TV *yp,
+                       cudaStream_t s) {
+  const TF *Y = reinterpret_cast<const TF *>(d->Y[buf]);
+  const double *Dinv = d->D[buf] + c->n_free;
+  int32_t pmax = 0, lmax = 0;
+  for (const auto &f : c->fronts) {
+    pmax = std::max(pmax, f.npiv);
+    lmax = std::max(lmax, f.ldy);
+  }
+  constexpr int RB = 32 * Vec16<TF>::n;
+  const size_t fsm = size_t(8 * RB + pmax) * sizeof(TV);
+  const size_t bsm = size_t(lmax) * sizeof(TV);
+  cudaFuncSetAttribute(fwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm));
+  cudaFuncSetAttribute(bwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bsm));
+  for (size_t lv = 0; lv < d->lt.size(); ++lv) {
+    const auto &L = d->lt[lv];
+    fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, fsm, s>>>(d->tasks + L.fwd_off, d->fronts, Y, Dinv, d->perm,
+                                                           d->wsrc_ptr, d->wsrc, r, u, yp);
+  }
+  for (size_t lv = d->lt.size(); lv-- > 0;) {
+    const auto &L = d->lt[lv];
+    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, bsm, s>>>(d->tasks + L.bwd_off, d->fronts, Y, d->perm,
+                                                           d->upd_rows_old, yp, z);
+  }
+}
+}  // namespace
+
 }  // namespace fe
+
+extern "C" int fe_apply_preconditioner_noalloc(fe_ctx *c, const double *r, double *z, void *stream) {
+  using namespace fe;
+  if (!c || !r || !z) return FE_ERR_ARG;
+  DeviceState *d = c->dev;
+  if (!d || !d->have_factor) return set_error(c, FE_ERR_STATE, "no factor: call fe_factor_now or fe_step first");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != d->device || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return set_error(c, FE_ERR_ARG, "the context's device must be current");
+  }
+  const bool fp32 = c->opt.precision == FE_MIXED;
+  const size_t ts = fp32 ? sizeof(float) : sizeof(double);
+  const size_t b_vec = round256(size_t(c->n) * ts), b_u = round256(size_t(std::max<int64_t>(c->u_total, 1)) * ts);
+  const size_t b_y = round256(size_t(std::max<int64_t>(c->n_free, 1)) * ts);
+  const size_t need = 2 * b_vec + b_u + b_y;
+  if (need > kNoAllocScratchBytes)
+    return set_error(c, FE_ERR_ARG, "this mesh needs " + std::to_string(need) +
+                                        " bytes of scratch; the allocation-free path holds " +
+                                        std::to_string(kNoAllocScratchBytes));
+  void *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_base[dev]) {
+      cudaError_t e = cudaGetSymbolAddress(&g_noalloc_base[dev], g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_noalloc_base[dev] = nullptr;
+        cudaGetLastError();
+        return set_error(c, FE_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      }
+    }
+    base = g_noalloc_base[dev];
+  }
+  unsigned char *p = static_cast<unsigned char *>(base);
+  void *rT = p, *zT = p + b_vec, *ub = p + 2 * b_vec, *yp = p + 2 * b_vec + b_u;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // z keeps the last call's values on fixed DOFs unless cleared
+  cudaError_t e = cudaMemsetAsync(zT, 0, size_t(c->n) * ts, s);
+  if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, cudaGetErrorString(e));
+  launch_convert(r, false, rT, fp32, c->n, s);
+  if (fp32)
+    apply_levels_into<float, float>(c, d, d->cur, static_cast<const float *>(rT), static_cast<float *>(zT),
+                                    static_cast<float *>(ub), static_cast<float *>(yp), s);
+  else
+    apply_levels_into<double, double>(c, d, d->cur, static_cast<const double *>(rT), static_cast<double *>(zT),
+                                      static_cast<double *>(ub), static_cast<double *>(yp), s);
+  launch_convert(zT, fp32, z, false, c->n, s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, cudaGetErrorString(e));
+  return FE_OK;
+}
+
