@@ -275,9 +275,16 @@ WORKLOADS = {
 
 
 def workload(name: str, **kw) -> Workload:
-    """Named workload; small variants: workload('tet-mr', a=4, b=4, c=16) etc."""
+    """Named workload; size variants of the same family either by keyword
+    (workload('tet-mr', a=4, b=4, c=16)) or by name ('tet20x20x80-mr',
+    'hex8x8x32-nh')."""
     if name in WORKLOADS:
         return WORKLOADS[name]()
+    import re
+    m = re.fullmatch(r"(tet|hex)(\d+)x(\d+)x(\d+)-(mr|nh)", name)
+    if m and (m.group(1), m.group(5)) in (("tet", "mr"), ("hex", "nh")):
+        a, b, c = int(m.group(2)), int(m.group(3)), int(m.group(4))
+        return _tet2(a, b, c) if m.group(1) == "tet" else _hex1(a, b, c)
     if name == "tet-mr":
         return _tet2(**kw)
     if name == "hex-nh":

@@ -225,6 +225,29 @@ enum {
 int fe_get_stage_times(fe_ctx *ctx, double *ms, int64_t *calls, int64_t *kernel_launches);
 int fe_reset_stage_times(fe_ctx *ctx);
 
+/* Replaces the material parameters ([n_elems * 3], element-major, the layout
+ * of fe_material with per_element = 1) without redoing the setup. */
+int fe_set_params(fe_ctx *ctx, const double *params);
+
+/* Discrete adjoint of the rollout recorded since the last
+ * fe_clear_checkpoints (fe_step stores (q_t, v_t, a_t) when
+ * fe_options.keep_checkpoints = 1).  Given dL/dq_T and dL/dv_T ([n] each;
+ * dL_dvT may be NULL = 0), sweeps the steps backwards: per step it rebuilds
+ * A_t, solves A_t lambda = h v_bar + h^2 q_bar with the PCG (A_t symmetric,
+ * lambda = 0 on fixed DOFs; lagged factor of the sweep refreshed every
+ * refactor_every steps), and updates
+ *   q_bar -= c_K dK[lambda] a + (beta + h) dK[lambda] v + K lambda,
+ *   v_bar += h q_bar - (alpha M + (beta + h) K) lambda,
+ *   s_bar_e -= lambda_e . (c_K K_e a_e + f_e + (beta + h) K_e v_e).
+ * Outputs: dL_ds [n_elems], the derivative with respect to a scale s_e of
+ * element e's energy (its material parameters all multiplied by s_e; for a
+ * per-element Young's modulus at fixed nu, dL/dE_e = dL_ds[e] / E_e), and
+ * dL_dp [T * n] (step-major; NULL to skip), the derivative with respect to
+ * the external forces of every step.  Pointers follow device_ptrs. */
+int fe_adjoint(fe_ctx *ctx, const double *dL_dqT, const double *dL_dvT, double *dL_ds, double *dL_dp);
+int fe_clear_checkpoints(fe_ctx *ctx);
+int fe_num_checkpoints(fe_ctx *ctx, int64_t *count);
+
 /* Message of the last failure on ctx ("" if none). */
 const char *fe_last_error(const fe_ctx *ctx);
 

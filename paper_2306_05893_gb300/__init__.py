@@ -194,6 +194,24 @@ def fe_reset_stage_times(ctx):
     _check(ctx, load().fe_reset_stage_times(ctx))
 
 
+def fe_set_params(ctx, params):
+    _check(ctx, load().fe_set_params(ctx, _ptr(_f64(params))))
+
+
+def fe_adjoint(ctx, dL_dqT, dL_dvT=None, dL_ds=None, dL_dp=None):
+    _check(ctx, load().fe_adjoint(ctx, _ptr(dL_dqT), _ptr(dL_dvT), _ptr(dL_ds), _ptr(dL_dp)))
+
+
+def fe_clear_checkpoints(ctx):
+    _check(ctx, load().fe_clear_checkpoints(ctx))
+
+
+def fe_num_checkpoints(ctx):
+    k = ct.c_int64()
+    _check(ctx, load().fe_num_checkpoints(ctx, ct.byref(k)))
+    return k.value
+
+
 def fe_destroy(ctx):
     if ctx:
         load().fe_destroy(ctx)
@@ -254,6 +272,20 @@ class FEContext:
 
     def reset_stage_times(self):
         fe_reset_stage_times(self.ctx)
+
+    def set_params(self, params):
+        fe_set_params(self.ctx, np.asarray(params, dtype=np.float64).reshape(-1, 3))
+
+    def clear_checkpoints(self):
+        fe_clear_checkpoints(self.ctx)
+
+    def adjoint(self, dL_dqT, dL_dvT=None, with_dp=True):
+        """Host arrays: returns (dL/ds [n_elems], dL/dp [T, n] or None)."""
+        T = fe_num_checkpoints(self.ctx)
+        ds = np.empty(self.n_elems)
+        dp = np.empty((T, self.n)) if with_dp else None
+        fe_adjoint(self.ctx, _f64(dL_dqT), None if dL_dvT is None else _f64(dL_dvT), ds, dp)
+        return ds, dp
 
     def set_state(self, q=None, v=None):
         fe_set_state(self.ctx, q, v)

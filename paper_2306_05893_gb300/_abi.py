@@ -72,6 +72,10 @@ SIGNATURES = {
     "fe_get_info": (ct.c_int, [CTX, P(FeInfo)]),
     "fe_get_stage_times": (ct.c_int, [CTX, DP, P(ct.c_int64), P(ct.c_int64)]),
     "fe_reset_stage_times": (ct.c_int, [CTX]),
+    "fe_set_params": (ct.c_int, [CTX, ct.c_void_p]),
+    "fe_adjoint": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "fe_clear_checkpoints": (ct.c_int, [CTX]),
+    "fe_num_checkpoints": (ct.c_int, [CTX, P(ct.c_int64)]),
     "fe_last_error": (ct.c_char_p, [CTX]),
     "fe_destroy": (None, [CTX]),
 }

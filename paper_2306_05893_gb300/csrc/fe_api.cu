@@ -426,6 +426,7 @@ void destroy_device(fe_ctx *c) {
   if (!d) return;
   cudaDeviceSynchronize();
   for (void *p : d->allocs) cudaFree(p);
+  for (double *p : d->ckpt) cudaFree(p);
   if (d->h_scal) cudaFreeHost(d->h_scal);
   if (d->stage_in) cudaFreeHost(d->stage_in);
   if (d->stage_out) cudaFreeHost(d->stage_out);
@@ -592,6 +593,18 @@ int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_ste
   const int age = int(step - d->cur_step);
   // S5-S7 PCG, S9 refinement
   int st = solve(c, info);
+  if (!st && c->opt.keep_checkpoints) {
+    double *ck = nullptr;
+    cudaError_t e = cudaMalloc(&ck, 3 * size_t(c->n) * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(c, FE_ERR_OOM, "checkpoint allocation failed");
+    }
+    d->ckpt.push_back(ck);
+    FE_CUDA_TRY(cudaMemcpyAsync(ck, d->q, c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    FE_CUDA_TRY(cudaMemcpyAsync(ck + c->n, d->v, c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    FE_CUDA_TRY(cudaMemcpyAsync(ck + 2 * c->n, d->x, c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
   if (st) {
     // leave the state untouched; a pending factor still completes on its stream
     return st;
@@ -607,6 +620,108 @@ int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_ste
   if (info) info->factor_age = age;
   d->step_index = step + 1;
   if (c->opt.profile_stages) stage_collect(c);
+  return FE_OK;
+}
+
+int fe_set_params(fe_ctx *c, const double *params) {
+  if (!c || !params) return FE_ERR_ARG;
+  for (int64_t e = 0; e < c->n_elems; ++e)
+    for (int k = 0; k < 3; ++k) c->params[3 * e + k] = params[3 * e + k];
+  if (c->dev) {
+    const int64_t E = c->n_elems;
+    std::vector<double> pt(3 * E);
+    for (int64_t e = 0; e < E; ++e)
+      for (int k = 0; k < 3; ++k) pt[k * E + e] = c->params[3 * e + k];
+    FE_CUDA_TRY(cudaStreamSynchronize(c->dev->stream));
+    FE_CUDA_TRY(cudaStreamSynchronize(c->dev->fstream));
+    FE_CUDA_TRY(cudaMemcpy(c->dev->params, pt.data(), pt.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return FE_OK;
+}
+
+int fe_clear_checkpoints(fe_ctx *c) {
+  if (!c) return FE_ERR_ARG;
+  if (!c->dev) return FE_OK;
+  cudaStreamSynchronize(c->dev->stream);
+  for (double *p : c->dev->ckpt) cudaFree(p);
+  c->dev->ckpt.clear();
+  return FE_OK;
+}
+
+int fe_num_checkpoints(fe_ctx *c, int64_t *count) {
+  if (!c || !count) return FE_ERR_ARG;
+  *count = c->dev ? int64_t(c->dev->ckpt.size()) : 0;
+  return FE_OK;
+}
+
+int fe_adjoint(fe_ctx *c, const double *dL_dqT, const double *dL_dvT, double *dL_ds, double *dL_dp) {
+  if (!c || !dL_dqT) return FE_ERR_ARG;
+  FE_TRY(ensure_device(c));
+  DeviceState *d = c->dev;
+  const int64_t T = int64_t(d->ckpt.size());
+  if (T == 0) return set_error(c, FE_ERR_STATE, "no checkpoints: run fe_step with keep_checkpoints = 1");
+  cudaStream_t s = d->stream;
+  const bool fp32 = mixed(c);
+  const int64_t n = c->n, E = c->n_elems;
+  if (!d->qbar) {
+    FE_TRY(dalloc(c, d, &d->qbar, n));
+    FE_TRY(dalloc(c, d, &d->vbar, n));
+    FE_TRY(dalloc(c, d, &d->sbar, E));
+    FE_TRY(dalloc(c, d, &d->ge, size_t(E) * 3 * c->npe));
+    FE_TRY(dalloc(c, d, &d->kl, size_t(E) * 3 * c->npe));
+  }
+  FE_TRY(stage_in(c, d->qbar, dL_dqT, n));
+  if (dL_dvT) {
+    FE_TRY(stage_in(c, d->vbar, dL_dvT, n));
+  } else {
+    FE_CUDA_TRY(cudaMemsetAsync(d->vbar, 0, n * sizeof(double), s));
+  }
+  FE_CUDA_TRY(cudaMemsetAsync(d->sbar, 0, E * sizeof(double), s));
+  FE_TRY(clear_flags(c));
+  if (d->factor_pending >= 0) FE_TRY(wait_factor(c));
+  const int R = c->opt.refactor_every;
+  double *qsave = d->q, *vsave = d->v;
+  int st = FE_OK;
+  for (int64_t t = T - 1; t >= 0 && st == FE_OK; --t) {
+    double *qt = d->ckpt[t], *vt = d->ckpt[t] + n, *at = d->ckpt[t] + 2 * n;
+    // A_t at (q_t, v_t): element kernel + assembly (b is overwritten below)
+    d->q = qt;
+    d->v = vt;
+    launch_element(c, d, qt, fp32, s);
+    launch_assemble(c, d, fp32, nullptr, s);
+    d->q = qsave;
+    d->v = vsave;
+    // lagged preconditioner for the reverse sweep: A_{T-1}, then every R steps
+    if ((T - 1 - t) % R == 0) {
+      st = launch_factor(c, t);
+      if (!st) st = wait_factor(c);
+      if (st) break;
+    }
+    launch_adjoint_rhs(c, d, d->qbar, d->vbar, d->b, s);
+    st = solve(c, nullptr);  // lambda in d->x
+    if (st) break;
+    launch_adjoint_element(c, d, fp32, qt, d->x, at, vt, d->ge, d->kl, d->sbar, s);
+    double *pb = nullptr;
+    if (dL_dp && c->opt.device_ptrs) pb = dL_dp + t * n;
+    launch_adjoint_gather(c, d, d->ge, d->kl, d->x, d->qbar, d->vbar, pb, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, cudaGetErrorString(e));
+    if (dL_dp && !c->opt.device_ptrs) {
+      st = stage_out(c, dL_dp + t * n, d->x, n, 0);
+      if (!st)
+        for (int64_t i = 0; i < n; ++i)
+          if (c->fixed_dof[i]) dL_dp[t * n + i] = 0.0;
+    }
+  }
+  d->q = qsave;
+  d->v = vsave;
+  if (st) return st;
+  FE_TRY(read_scalars(c));
+  FE_TRY(flag_status(c));
+  FE_CUDA_TRY(cudaStreamSynchronize(s));
+  if (dL_ds)
+    FE_CUDA_TRY(cudaMemcpy(dL_ds, d->sbar, E * sizeof(double),
+                           c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
   return FE_OK;
 }
 

@@ -118,6 +118,10 @@ struct DeviceState {
   double stage_ms[FE_STAGE_COUNT] = {0};
   int64_t stage_calls[FE_STAGE_COUNT] = {0};
   mutable int64_t launches = 0;
+
+  // adjoint: per-step checkpoints (q_t, v_t, a_t) and reverse-sweep buffers
+  std::vector<double *> ckpt;      // each [3n]: q_t, v_t, a_t
+  double *qbar = nullptr, *vbar = nullptr, *sbar = nullptr, *ge = nullptr, *kl = nullptr;
 };
 
 constexpr int kMaxBlocks = 4096;
@@ -145,6 +149,15 @@ void launch_init_solve(const fe_ctx *c, const DeviceState *d, bool fp32, void *x
 void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s);  // x += (double) vd
 void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s);
 void launch_convert(const void *src, bool src32, void *dst, bool dst32, int64_t n, cudaStream_t s);
+
+// (fe_adjoint.cu)
+void launch_adjoint_element(const fe_ctx *c, const DeviceState *d, bool fp32, const double *q, const double *lam,
+                            const double *acc, const double *v, double *ge, double *kl, double *sbar,
+                            cudaStream_t s);
+void launch_adjoint_gather(const fe_ctx *c, const DeviceState *d, const double *ge, const double *kl,
+                           const double *lam, double *qbar, double *vbar, double *pbar, cudaStream_t s);
+void launch_adjoint_rhs(const fe_ctx *c, const DeviceState *d, const double *qbar, const double *vbar,
+                        double *abar, cudaStream_t s);
 
 // (fe_factor.cu)
 int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Afac, cudaStream_t s);
