@@ -313,6 +313,13 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
 constexpr int kT128 = 128;
 constexpr int kLd128 = 132;  // padded row (16-byte aligned) of the k-major tiles
 
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool valid) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int sz = valid ? 4 : 0;  // 0: nothing is read, the 4 bytes are zero-filled
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __global__ void __launch_bounds__(256) front_update128_kernel(const int32_t *__restrict__ tasks,
                                                               const DFront *__restrict__ fronts,
                                                               float *__restrict__ F, float *__restrict__ Y,
@@ -320,7 +327,8 @@ __global__ void __launch_bounds__(256) front_update128_kernel(const int32_t *__r
   extern __shared__ __align__(16) float usm128[];
   float *As = usm128;                 // [64][kLd128]: As[l][i] = L[i0 + i, k0 + l]
   float *Bs = usm128 + 64 * kLd128;   // [64][kLd128]: Bs[l][j]
-  float *Cs = usm128;                 // epilogue [128][129], reuses As/Bs
+  float *Cs = usm128;                 // epilogue [128][129] (column j, row i), reuses As/Bs
+  __shared__ float Ds[64];
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int kind = t.y >> 24;
@@ -328,25 +336,35 @@ __global__ void __launch_bounds__(256) front_update128_kernel(const int32_t *__r
   const int32_t kb = (fr.npiv - k0) < 64 ? (fr.npiv - k0) : 64;
   float *Ff = F + fr.f_off;
   float *Yf = Y + fr.y_off;
+  // operand tiles: asynchronous copies, all in flight together
   for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
     const int l = idx / kT128, i = idx % kT128;
     const int32_t r = i0 + i;
-    As[l * kLd128 + i] = (r < m && l < kb) ? Ff[r + int64_t(k0 + l) * m] : 0.f;
+    const bool ok = r < m && l < kb;
+    cp_async4(As + l * kLd128 + i, ok ? Ff + r + int64_t(k0 + l) * m : Ff, ok);
   }
   if (kind == T_TRAIL) {
     for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
       const int l = idx / kT128, j = idx % kT128;
       const int32_t r = j0 + j;
-      Bs[l * kLd128 + j] = (r < m && l < kb) ? Ff[r + int64_t(k0 + l) * m] * float(D[fr.first + k0 + l]) : 0.f;
+      const bool ok = r < m && l < kb;
+      cp_async4(Bs + l * kLd128 + j, ok ? Ff + r + int64_t(k0 + l) * m : Ff, ok);
     }
+    if (threadIdx.x < 64) Ds[threadIdx.x] = threadIdx.x < kb ? float(D[fr.first + k0 + threadIdx.x]) : 0.f;
   } else {
     for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
       const int l = idx % 64, j = idx / 64;
       const int32_t c = j0 + j;
-      Bs[l * kLd128 + j] = (l < kb && c < k0 + kb) ? Yf[(k0 + l) + int64_t(c) * fr.ldy] : 0.f;
+      const bool ok = l < kb && c < k0 + kb;
+      cp_async4(Bs + l * kLd128 + j, ok ? Yf + (k0 + l) + int64_t(c) * fr.ldy : Yf, ok);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
+  if (kind == T_TRAIL) {  // B <- B diag(D)
+    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) Bs[(idx / kT128) * kLd128 + idx % kT128] *= Ds[idx / kT128];
+    __syncthreads();
+  }
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   float acc[8][8];
 #pragma unroll
@@ -367,24 +385,34 @@ __global__ void __launch_bounds__(256) front_update128_kernel(const int32_t *__r
       for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
   }
   __syncthreads();
+  // epilogue: fetch the C tile asynchronously, subtract in shared memory,
+  // write back coalesced (TRAIL: lower part only; RUPD: Y)
+  const bool trail = kind == T_TRAIL;
+  const int32_t cmax = trail ? m : k0 + kb;
+  for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
+    const int j = idx / kT128, i = idx % kT128;
+    const int32_t r = i0 + i, c = j0 + j;
+    const bool ok = r < m && c < cmax;
+    const float *src = trail ? Ff + r + int64_t(c) * m : Yf + r + int64_t(c) * fr.ldy;
+    cp_async4(Cs + j * 129 + i, ok ? src : Ff, ok);
+  }
+  cp_async_wait_all();
+  __syncthreads();
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int i = ty * 4 + (r & 3) + (r >> 2) * 64;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) Cs[i * 129 + tx * 4 + (c & 3) + (c >> 2) * 64] = acc[r][c];
+    for (int c = 0; c < 8; ++c) Cs[(tx * 4 + (c & 3) + (c >> 2) * 64) * 129 + i] -= acc[r][c];
   }
   __syncthreads();
-  if (kind == T_TRAIL) {
-    for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
-      const int j = idx / kT128, i = idx % kT128;
-      const int32_t r = i0 + i, c = j0 + j;
-      if (r < m && c < m && r >= c) Ff[r + int64_t(c) * m] -= Cs[i * 129 + j];
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
-      const int j = idx / kT128, i = idx % kT128;
-      const int32_t r = i0 + i, c = j0 + j;
-      if (r < m && c < k0 + kb) Yf[r + int64_t(c) * fr.ldy] -= Cs[i * 129 + j];
+  for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
+    const int j = idx / kT128, i = idx % kT128;
+    const int32_t r = i0 + i, c = j0 + j;
+    if (r >= m || c >= cmax) continue;
+    if (trail) {
+      if (r >= c) Ff[r + int64_t(c) * m] = Cs[j * 129 + i];
+    } else {
+      Yf[r + int64_t(c) * fr.ldy] = Cs[j * 129 + i];
     }
   }
 }
