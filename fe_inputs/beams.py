@@ -290,3 +290,24 @@ def workload(name: str, **kw) -> Workload:
     if name == "hex-nh":
         return _hex1(**kw)
     raise KeyError(name)
+
+
+@dataclasses.dataclass
+class BatchMember:
+    mesh: TetBeam
+    model: int
+    params: np.ndarray      # [3]
+    load: np.ndarray        # [n_nodes, 3] gravity dead load (constant in time)
+
+
+def batch_workload(n_beams: int = 64, seed: int = 7):
+    """Members of the batched workload (sizes and materials of batched_beams):
+    tet beams m x m x L, SVK or neo-Hookean with (E, nu), clamped at x = 0,
+    under gravity, h / alpha / beta / rho of the other workloads."""
+    out = []
+    for spec in batched_beams(n_beams, seed):
+        mesh = tet_beam(spec["m"], spec["m"], spec["L"])
+        mu, lam = lame_from_young(spec["E"], spec["nu"])
+        out.append(BatchMember(mesh, spec["model"], np.array([float(mu), float(lam), 0.0]),
+                               body_force(mesh, RHO, (0.0, 0.0, G_Z))))
+    return out

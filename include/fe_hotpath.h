@@ -116,6 +116,22 @@ int fe_options_default(fe_options *opt);
 int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alpha,
               double beta, const fe_options *opt, fe_ctx **out);
 
+/* Batched context: nb independent meshes (same element type and density,
+ * any models) stepped together as one block-diagonal system.  Every stage is
+ * one launch over all members (one element launch per material model); the
+ * CG keeps per-member scalars, so member k converges on its own test
+ * ||r_k|| <= tol ||b_k||.  Members are stored grouped by model: member
+ * order, node offsets [nb+1] and element offsets [nb+1] of the concatenated
+ * state come from fe_get_batch_layout; state and force vectors passed to
+ * the other calls are concatenations in that order. */
+int fe_create_batch(int32_t nb, const fe_mesh *meshes, const fe_material *mats, double h,
+                    double alpha, double beta, const fe_options *opt, fe_ctx **out);
+int fe_get_batch_layout(fe_ctx *ctx, int32_t *nb, const int32_t **member,
+                        const int64_t **node_off, const int64_t **elem_off);
+/* Per-member PCG iterations and final relative residuals of the last step
+ * ([nb] each, stored order; NULL to skip). */
+int fe_get_batch_stats(fe_ctx *ctx, int32_t *iters, double *rel_residual);
+
 /* Setup once per topology (Section 4.2, Table "build pattern"; Section 5.1;
  * Section 6.1): the triplet (row, col) stream in fill order
  *   t = ((e * npe + a) * npe + b) * 9 + 3 i + k   (value K_e[3a+i][3b+k]),

@@ -100,6 +100,48 @@ def fe_create(elem_type, X, conn, fixed_nodes, model, rho, params, h, alpha, bet
     return h_ctx
 
 
+def fe_create_batch(members, h, alpha, beta, rho, opts=None):
+    """members: list of (elem_type, X, conn, fixed_nodes, model, params)."""
+    lib = load()
+    keep = []
+    meshes = (_abi.FeMesh * len(members))()
+    mats = (_abi.FeMaterial * len(members))()
+    for k, (et, X, conn, fixed, model, params) in enumerate(members):
+        X = _f64(X).reshape(-1, 3)
+        conn = np.ascontiguousarray(conn, dtype=np.int32)
+        fixed = np.ascontiguousarray(fixed, dtype=np.int32).reshape(-1)
+        params = _f64(params)
+        keep += [X, conn, fixed, params]
+        meshes[k] = _abi.FeMesh(et, X.shape[0], conn.shape[0], _dptr(X),
+                                conn.ctypes.data_as(ct.POINTER(ct.c_int32)), fixed.size,
+                                fixed.ctypes.data_as(ct.POINTER(ct.c_int32)))
+        mats[k] = _abi.FeMaterial(model, float(rho), _dptr(params), 1 if params.ndim == 2 else 0)
+    opts = opts if opts is not None else options()
+    h_ctx = ct.c_void_p()
+    st = lib.fe_create_batch(len(members), meshes, mats, float(h), float(alpha), float(beta),
+                             ct.byref(opts), ct.byref(h_ctx))
+    if st != 0:
+        raise FEError(st, "fe_create_batch rejected its arguments")
+    return h_ctx
+
+
+def fe_get_batch_layout(ctx):
+    nb = ct.c_int32()
+    mem = ct.POINTER(ct.c_int32)()
+    no, eo = ct.POINTER(ct.c_int64)(), ct.POINTER(ct.c_int64)()
+    _check(ctx, load().fe_get_batch_layout(ctx, ct.byref(nb), ct.byref(mem), ct.byref(no), ct.byref(eo)))
+    k = nb.value
+    return (np.ctypeslib.as_array(mem, (k,)).copy(), np.ctypeslib.as_array(no, (k + 1,)).copy(),
+            np.ctypeslib.as_array(eo, (k + 1,)).copy())
+
+
+def fe_get_batch_stats(ctx, nb):
+    it = np.zeros(nb, np.int32)
+    rr = np.zeros(nb)
+    _check(ctx, load().fe_get_batch_stats(ctx, it.ctypes.data_as(ct.POINTER(ct.c_int32)), _dptr(rr)))
+    return it, rr
+
+
 def fe_build_pattern(ctx):
     _check(ctx, load().fe_build_pattern(ctx))
 
@@ -320,3 +362,36 @@ class FEContext:
     def step(self, p=None, q_out=None, v_out=None):
         p_arg = p if (p is None or hasattr(p, "data_ptr")) else _f64(p)
         return fe_step(self.ctx, p_arg, q_out, v_out)
+
+
+class FEBatch(FEContext):
+    """Independent meshes stepped together (fe_create_batch).  State and force
+    vectors are concatenations in the stored member order (grouped by
+    material model); `member`, `node_off` give that order and the offsets."""
+
+    def __init__(self, members, h, alpha, beta, rho, build=True, **opts):
+        self.n = 3 * sum(np.asarray(m[1]).reshape(-1, 3).shape[0] for m in members)
+        self.n_elems = sum(np.asarray(m[2]).shape[0] for m in members)
+        self.npe = np.asarray(members[0][2]).shape[1]
+        self.opts = options(**opts)
+        self.ctx = fe_create_batch(members, h, alpha, beta, rho, self.opts)
+        self.member, self.node_off, self.elem_off = fe_get_batch_layout(self.ctx)
+        self.nb = len(members)
+        if build:
+            fe_build_pattern(self.ctx)
+            self.rowptr, self.colind, self.C = fe_get_pattern(self.ctx)
+            self.nnz = self.colind.size
+
+    def concat(self, per_member):
+        """Concatenate per-member [n_k] (or [n_nodes_k, 3]) arrays in stored order."""
+        return np.concatenate([np.asarray(per_member[k], dtype=np.float64).reshape(-1) for k in self.member])
+
+    def split(self, vec):
+        """Inverse of concat: list of per-member arrays in the caller's order."""
+        out = [None] * self.nb
+        for s, k in enumerate(self.member):
+            out[k] = vec[3 * self.node_off[s]:3 * self.node_off[s + 1]]
+        return out
+
+    def stats(self):
+        return fe_get_batch_stats(self.ctx, self.nb)

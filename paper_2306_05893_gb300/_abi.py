@@ -53,6 +53,10 @@ SIGNATURES = {
     "fe_options_default": (ct.c_int, [P(FeOptions)]),
     "fe_create": (ct.c_int, [P(FeMesh), P(FeMaterial), ct.c_double, ct.c_double, ct.c_double,
                              P(FeOptions), P(CTX)]),
+    "fe_create_batch": (ct.c_int, [ct.c_int32, P(FeMesh), P(FeMaterial), ct.c_double, ct.c_double,
+                                   ct.c_double, P(FeOptions), P(CTX)]),
+    "fe_get_batch_layout": (ct.c_int, [CTX, P(ct.c_int32), P(I32P), P(P(ct.c_int64)), P(P(ct.c_int64))]),
+    "fe_get_batch_stats": (ct.c_int, [CTX, I32P, DP]),
     "fe_build_pattern": (ct.c_int, [CTX]),
     "fe_get_pattern": (ct.c_int, [CTX, P(ct.c_int64), P(ct.c_int64), P(I32P), P(I32P),
                                   P(ct.c_int64), P(I32P)]),

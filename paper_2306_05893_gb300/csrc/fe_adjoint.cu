@@ -122,12 +122,12 @@ __device__ __forceinline__ void adjoint_point(const T (&g)[NPE][3], T w, const T
 // One thread per element (tets: 1 point; hexes: 8 Gauss points).
 template <int MODEL, typename T, int NPE>
 __global__ void __launch_bounds__(128) adjoint_element_kernel(
-    int64_t E, const int32_t *__restrict__ conn, const double *__restrict__ rest,
+    int64_t E, int64_t e_begin, int64_t e_end, const int32_t *__restrict__ conn, const double *__restrict__ rest,
     const double *__restrict__ params, const double *__restrict__ X, const double *__restrict__ q,
     const double *__restrict__ lam, const double *__restrict__ acc, const double *__restrict__ v, double cK,
     double bh, double *__restrict__ ge_out, double *__restrict__ kl_out, double *__restrict__ sbar, int *flags) {
-  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= E) return;
+  const int64_t e = e_begin + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= e_end) return;
   int nd[NPE];
 #pragma unroll
   for (int a = 0; a < NPE; ++a) nd[a] = conn[e * NPE + a];
@@ -255,29 +255,30 @@ static void launch_adj_t(const fe_ctx *c, const DeviceState *d, const double *q,
                          cudaStream_t s) {
   const double h = c->h, cK = h * (c->beta + h), bh = c->beta + h;
   const int64_t E = c->n_elems;
-  const unsigned g = unsigned((E + 127) / 128);
+  const int64_t eb = c->model_range[MODEL][0], ee = c->model_range[MODEL][1];
+  if (ee <= eb) return;
+  const unsigned g = unsigned((ee - eb + 127) / 128);
   if (c->elem_type == FE_TET4)
-    adjoint_element_kernel<MODEL, T, 4><<<g, 128, 0, s>>>(E, d->conn, d->rest, d->params, d->X, q, lam, acc, v, cK,
-                                                          bh, ge, kl, sbar, d->flags);
+    adjoint_element_kernel<MODEL, T, 4><<<g, 128, 0, s>>>(E, eb, ee, d->conn, d->rest, d->params, d->X, q, lam, acc,
+                                                          v, cK, bh, ge, kl, sbar, d->flags);
   else
-    adjoint_element_kernel<MODEL, T, 8><<<g, 128, 0, s>>>(E, d->conn, d->rest, d->params, d->X, q, lam, acc, v, cK,
-                                                          bh, ge, kl, sbar, d->flags);
+    adjoint_element_kernel<MODEL, T, 8><<<g, 128, 0, s>>>(E, eb, ee, d->conn, d->rest, d->params, d->X, q, lam, acc,
+                                                          v, cK, bh, ge, kl, sbar, d->flags);
 }
 
 void launch_adjoint_element(const fe_ctx *c, const DeviceState *d, bool fp32, const double *q, const double *lam,
                             const double *acc, const double *v, double *ge, double *kl, double *sbar,
                             cudaStream_t s) {
-  d->launches++;
-  switch (c->model) {
-    case FE_SVK:
+  for (int md = FE_SVK; md <= FE_MOONEY_RIVLIN; ++md) {
+    if (c->model_range[md][1] <= c->model_range[md][0]) continue;
+    d->launches++;
+    if (md == FE_SVK)
       fp32 ? launch_adj_t<FE_SVK, float>(c, d, q, lam, acc, v, ge, kl, sbar, s)
            : launch_adj_t<FE_SVK, double>(c, d, q, lam, acc, v, ge, kl, sbar, s);
-      break;
-    case FE_NEOHOOKE:
+    else if (md == FE_NEOHOOKE)
       fp32 ? launch_adj_t<FE_NEOHOOKE, float>(c, d, q, lam, acc, v, ge, kl, sbar, s)
            : launch_adj_t<FE_NEOHOOKE, double>(c, d, q, lam, acc, v, ge, kl, sbar, s);
-      break;
-    default:
+    else
       fp32 ? launch_adj_t<FE_MOONEY_RIVLIN, float>(c, d, q, lam, acc, v, ge, kl, sbar, s)
            : launch_adj_t<FE_MOONEY_RIVLIN, double>(c, d, q, lam, acc, v, ge, kl, sbar, s);
   }

@@ -157,6 +157,18 @@ int ensure_device(fe_ctx *c) {
   FE_TRY(upload(c, d, &d->bsrc_ptr, c->bsrc_ptr));
   FE_TRY(upload(c, d, &d->bsrc, c->bsrc));
   FE_TRY(upload(c, d, &d->bmass, c->bmass));
+  {
+    std::vector<int64_t> sd(c->nseg + 1);
+    std::vector<int32_t> rs(c->n);
+    for (int32_t k = 0; k <= c->nseg; ++k) sd[k] = 3 * c->seg_node[k];
+    for (int32_t k = 0; k < c->nseg; ++k)
+      for (int64_t i = sd[k]; i < sd[k + 1]; ++i) rs[i] = k;
+    FE_TRY(upload(c, d, &d->seg_dof, sd));
+    FE_TRY(upload(c, d, &d->row_seg, rs));
+    FE_TRY(dalloc(c, d, &d->bscal, size_t(c->nseg) * B_COUNT));
+    FE_CUDA_TRY(cudaMemset(d->bscal, 0, size_t(c->nseg) * B_COUNT * sizeof(double)));
+    FE_CUDA_TRY(cudaMallocHost(&d->h_bscal, size_t(c->nseg) * B_COUNT * sizeof(double)));
+  }
   // state
   FE_TRY(upload(c, d, &d->q, c->X));
   FE_TRY(dalloc(c, d, &d->v, n));
@@ -380,10 +392,149 @@ int pcg(fe_ctx *c, bool fp32, void *X, void *R) {
   return FE_OK;
 }
 
+// SpMV autotuner: threads per CSR row chosen among {4, 8, 16, 32} by timing
+// y = A x on the assembled matrix (CUDA events, 3 runs each, median).
+int autotune_spmv(fe_ctx *c) {
+  DeviceState *d = c->dev;
+  if (d->spmv_tpr) return FE_OK;
+  const bool fp32 = mixed(c);
+  cudaEvent_t e0, e1;
+  FE_CUDA_TRY(cudaEventCreate(&e0));
+  FE_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_tpr = 8;
+  for (int tpr : {4, 8, 16, 32}) {
+    float t[3];
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, d->stream);
+      launch_spmv_plain(c, d, fp32, d->vp, d->vq, nullptr, tpr, d->stream);
+      cudaEventRecord(e1, d->stream);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t[rep], e0, e1);
+    }
+    std::sort(t, t + 3);
+    if (t[1] < best) {
+      best = t[1];
+      best_tpr = tpr;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FE_CUDA_TRY(cudaGetLastError());
+  d->spmv_tpr = best_tpr;
+  return FE_OK;
+}
+
+int read_batch_scalars(fe_ctx *c) {
+  DeviceState *d = c->dev;
+  FE_CUDA_TRY(cudaMemcpyAsync(d->h_bscal, d->bscal, size_t(c->nseg) * B_COUNT * sizeof(double),
+                              cudaMemcpyDeviceToHost, d->stream));
+  FE_CUDA_TRY(cudaMemcpyAsync(d->h_scal, d->scal, S_COUNT * sizeof(double) + 4 * sizeof(int),
+                              cudaMemcpyDeviceToHost, d->stream));
+  FE_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return FE_OK;
+}
+
+bool all_members(const fe_ctx *c, int slot) {
+  for (int32_t k = 0; k < c->nseg; ++k)
+    if (c->dev->h_bscal[k * B_COUNT + slot] == 0.0) return false;
+  return true;
+}
+
+double max_member(const fe_ctx *c, int slot) {
+  double m = 0.0;
+  for (int32_t k = 0; k < c->nseg; ++k) m = std::max(m, c->dev->h_bscal[k * B_COUNT + slot]);
+  return m;
+}
+
+// Batched PCG: per-member alpha, beta, residual and convergence.
+int pcg_batch(fe_ctx *c, bool fp32, void *X, void *R) {
+  DeviceState *d = c->dev;
+  cudaStream_t s = d->stream;
+  {
+    Stage st(c, FE_STAGE_APPLY, s);
+    apply_enqueue(c, d, d->cur, fp32, R, d->vz, s);
+  }
+  launch_seg_dot(c, d, fp32, R, d->vz, SEG_RZ_FIRST, 0.0, s);
+  launch_seg_update_p(c, d, fp32, d->vz, d->vp, true, s);
+  for (;;) {
+    {
+      Stage st(c, FE_STAGE_SPMV, s);
+      launch_spmv_plain(c, d, fp32, d->vp, d->vq, nullptr, d->spmv_tpr, s);
+    }
+    {
+      Stage st(c, FE_STAGE_VECTOR, s);
+      launch_seg_dot(c, d, fp32, d->vp, d->vq, SEG_PQ, 0.0, s);
+      launch_seg_axpy(c, d, fp32, X, R, d->vp, d->vq, s);
+      launch_seg_dot(c, d, fp32, R, R, SEG_RR, 0.0, s);
+    }
+    FE_CUDA_TRY(cudaGetLastError());
+    FE_TRY(read_batch_scalars(c));
+    FE_TRY(flag_status(c));
+    if (all_members(c, B_DONE)) break;
+    if (max_member(c, B_ITERS) >= c->opt.max_iters)
+      return set_error(c, FE_ERR_NOT_CONVERGED, "batched PCG reached max_iters");
+    {
+      Stage st(c, FE_STAGE_APPLY, s);
+      apply_enqueue(c, d, d->cur, fp32, R, d->vz, s);
+    }
+    Stage st(c, FE_STAGE_VECTOR, s);
+    launch_seg_dot(c, d, fp32, R, d->vz, SEG_RZ, 0.0, s);
+    launch_seg_update_p(c, d, fp32, d->vz, d->vp, false, s);
+  }
+  return FE_OK;
+}
+
+int solve_batch(fe_ctx *c, fe_step_info *info) {
+  DeviceState *d = c->dev;
+  cudaStream_t s = d->stream;
+  const bool fp32 = mixed(c);
+  FE_TRY(autotune_spmv(c));
+  int sweeps = 0;
+  launch_seg_init(c, d, false, d->x, d->r, d->b, false, s);
+  launch_seg_dot64(c, d, d->b, d->b, SEG_INIT_OUTER, c->opt.tol, s);
+  if (!fp32) {
+    FE_TRY(read_batch_scalars(c));
+    if (!all_members(c, B_DONE)) FE_TRY(pcg_batch(c, false, d->x, d->r));
+    sweeps = 1;
+  } else {
+    for (;;) {
+      if (sweeps > 0) {
+        Stage st(c, FE_STAGE_RESIDUAL, s);
+        launch_spmv_plain(c, d, true, d->x, d->r, d->b, d->spmv_tpr, s);  // r = b - A x (FP64)
+        launch_seg_dot64(c, d, d->r, d->r, SEG_ORR, 0.0, s);
+      }
+      FE_TRY(read_batch_scalars(c));
+      FE_TRY(flag_status(c));
+      if (all_members(c, B_ODONE)) break;
+      if (max_member(c, B_ITERS) >= c->opt.max_iters)
+        return set_error(c, FE_ERR_NOT_CONVERGED, "batched refinement reached max_iters");
+      launch_seg_init(c, d, true, d->vd, d->vr, d->r, true, s);
+      launch_seg_dot(c, d, true, d->vr, d->vr, SEG_INIT_INNER, c->opt.inner_tol, s);
+      FE_TRY(pcg_batch(c, true, d->vd, d->vr));
+      launch_refine_update(c, d, s);
+      ++sweeps;
+    }
+  }
+  if (info) {
+    double worst = 0.0;
+    for (int32_t k = 0; k < c->nseg; ++k) {
+      const double *b = d->h_bscal + k * B_COUNT;
+      const double rr = fp32 ? b[B_ORR] : b[B_RR];
+      if (b[B_BB] > 0) worst = std::max(worst, std::sqrt(rr / b[B_BB]));
+    }
+    info->rel_residual = worst;
+    info->iters = int32_t(max_member(c, B_ITERS));
+    info->refinements = sweeps;
+  }
+  return FE_OK;
+}
+
 // Solve A a = b into d->x (FP64): plain PCG, or FP64 residual refinement
 // around an FP32 inner PCG.
 int solve(fe_ctx *c, fe_step_info *info) {
   DeviceState *d = c->dev;
+  if (c->nseg > 1) return solve_batch(c, info);
   cudaStream_t s = d->stream;
   const bool fp32 = mixed(c);
   int sweeps = 0;
@@ -428,6 +579,7 @@ void destroy_device(fe_ctx *c) {
   for (void *p : d->allocs) cudaFree(p);
   for (double *p : d->ckpt) cudaFree(p);
   if (d->h_scal) cudaFreeHost(d->h_scal);
+  if (d->h_bscal) cudaFreeHost(d->h_bscal);
   if (d->stage_in) cudaFreeHost(d->stage_in);
   if (d->stage_out) cudaFreeHost(d->stage_out);
   if (d->stage_big) cudaFreeHost(d->stage_big);
@@ -722,6 +874,20 @@ int fe_adjoint(fe_ctx *c, const double *dL_dqT, const double *dL_dvT, double *dL
   if (dL_ds)
     FE_CUDA_TRY(cudaMemcpy(dL_ds, d->sbar, E * sizeof(double),
                            c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return FE_OK;
+}
+
+int fe_get_batch_stats(fe_ctx *c, int32_t *iters, double *rel_residual) {
+  if (!c) return FE_ERR_ARG;
+  DeviceState *d = c->dev;
+  for (int32_t k = 0; k < c->nseg; ++k) {
+    const double *b = d ? d->h_bscal + k * B_COUNT : nullptr;
+    if (iters) iters[k] = b ? int32_t(b[B_ITERS]) : 0;
+    if (rel_residual) {
+      const double rr = b ? (mixed(c) ? b[B_ORR] : b[B_RR]) : 0.0;
+      rel_residual[k] = (b && b[B_BB] > 0) ? std::sqrt(rr / b[B_BB]) : 0.0;
+    }
+  }
   return FE_OK;
 }
 

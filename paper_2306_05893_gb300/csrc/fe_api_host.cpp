@@ -66,11 +66,101 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
     if (!(c->opt.inner_tol > 0)) c->opt.inner_tol = 1e-4;
     if (!(c->opt.factor_timeout_s > 0)) c->opt.factor_timeout_s = 30.0;
     if (c->opt.nd_leaf_nodes <= 0) c->opt.nd_leaf_nodes = 64;
+    c->nseg = 1;
+    c->seg_node = {0, c->n_nodes};
+    c->seg_elem = {0, c->n_elems};
+    c->seg_member = {0};
+    c->seg_model = {c->model};
+    for (int k = 0; k < 3; ++k) c->model_range[k][0] = c->model_range[k][1] = 0;
+    c->model_range[c->model][1] = c->n_elems;
   } catch (const std::bad_alloc &) {
     delete c;
     return FE_ERR_OOM;
   }
   *out = c;
+  return FE_OK;
+}
+
+int fe_create_batch(int32_t nb, const fe_mesh *meshes, const fe_material *mats, double h, double alpha,
+                    double beta, const fe_options *opt, fe_ctx **out) {
+  if (!out) return FE_ERR_ARG;
+  *out = nullptr;
+  if (nb <= 0 || !meshes || !mats) return FE_ERR_ARG;
+  for (int32_t k = 0; k < nb; ++k) {
+    const fe_mesh &m = meshes[k];
+    if (!m.rest_xyz || !m.conn || m.n_nodes <= 0 || m.n_elems <= 0 || m.elem_type != meshes[0].elem_type ||
+        (m.n_fixed > 0 && !m.fixed_nodes) || mats[k].model < FE_SVK || mats[k].model > FE_MOONEY_RIVLIN ||
+        !mats[k].params || !(mats[k].rho > 0) || mats[k].rho != mats[0].rho)
+      return FE_ERR_ARG;
+  }
+  // members grouped by material model (stable), so each model is one element range
+  std::vector<int32_t> order;
+  for (int md = FE_SVK; md <= FE_MOONEY_RIVLIN; ++md)
+    for (int32_t k = 0; k < nb; ++k)
+      if (mats[k].model == md) order.push_back(k);
+  const int npe = meshes[0].elem_type == FE_TET4 ? 4 : 8;
+  int64_t NN = 0, NE = 0, NF = 0;
+  for (int32_t k = 0; k < nb; ++k) {
+    NN += meshes[k].n_nodes;
+    NE += meshes[k].n_elems;
+    NF += meshes[k].n_fixed;
+  }
+  try {
+    std::vector<double> X(3 * NN), P(3 * NE);
+    std::vector<int32_t> conn(npe * NE), fixed;
+    fixed.reserve(NF);
+    std::vector<int64_t> seg_node(nb + 1, 0), seg_elem(nb + 1, 0);
+    std::vector<int32_t> seg_model(nb);
+    for (int32_t s = 0; s < nb; ++s) {
+      const int32_t k = order[s];
+      const fe_mesh &m = meshes[k];
+      const int64_t n0 = seg_node[s], e0 = seg_elem[s];
+      if (n0 + m.n_nodes > (int64_t(1) << 29)) return FE_ERR_ARG;
+      for (int64_t i = 0; i < 3 * m.n_nodes; ++i) X[3 * n0 + i] = m.rest_xyz[i];
+      for (int64_t i = 0; i < npe * m.n_elems; ++i) {
+        if (m.conn[i] < 0 || m.conn[i] >= m.n_nodes) return FE_ERR_ARG;
+        conn[npe * e0 + i] = int32_t(m.conn[i] + n0);
+      }
+      for (int64_t i = 0; i < m.n_fixed; ++i) {
+        if (m.fixed_nodes[i] < 0 || m.fixed_nodes[i] >= m.n_nodes) return FE_ERR_ARG;
+        fixed.push_back(int32_t(m.fixed_nodes[i] + n0));
+      }
+      for (int64_t e = 0; e < m.n_elems; ++e)
+        for (int q = 0; q < 3; ++q)
+          P[3 * (e0 + e) + q] = mats[k].per_element ? mats[k].params[3 * e + q] : mats[k].params[q];
+      seg_node[s + 1] = n0 + m.n_nodes;
+      seg_elem[s + 1] = e0 + m.n_elems;
+      seg_model[s] = mats[k].model;
+    }
+    fe_mesh all{meshes[0].elem_type, NN, NE, X.data(), conn.data(), int64_t(fixed.size()), fixed.data()};
+    fe_material mat{mats[order[0]].model, mats[0].rho, P.data(), 1};
+    int st = fe_create(&all, &mat, h, alpha, beta, opt, out);
+    if (st) return st;
+    fe_ctx *c = *out;
+    c->nseg = nb;
+    c->seg_node = seg_node;
+    c->seg_elem = seg_elem;
+    c->seg_member = order;
+    c->seg_model = seg_model;
+    for (int md = 0; md < 3; ++md) c->model_range[md][0] = c->model_range[md][1] = 0;
+    for (int32_t s = 0; s < nb; ++s) {
+      const int md = seg_model[s];
+      if (c->model_range[md][1] == 0) c->model_range[md][0] = seg_elem[s];
+      c->model_range[md][1] = seg_elem[s + 1];
+    }
+  } catch (const std::bad_alloc &) {
+    return FE_ERR_OOM;
+  }
+  return FE_OK;
+}
+
+int fe_get_batch_layout(fe_ctx *c, int32_t *nb, const int32_t **member, const int64_t **node_off,
+                        const int64_t **elem_off) {
+  if (!c) return FE_ERR_ARG;
+  if (nb) *nb = c->nseg;
+  if (member) *member = c->seg_member.data();
+  if (node_off) *node_off = c->seg_node.data();
+  if (elem_off) *elem_off = c->seg_elem.data();
   return FE_OK;
 }
 

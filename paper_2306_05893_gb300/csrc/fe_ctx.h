@@ -62,6 +62,15 @@ struct fe_ctx {
   double h = 0, alpha = 0, beta = 0;
   fe_options opt{};
 
+  // batched context: members concatenated in the order of seg_member (grouped
+  // by material model); member k owns nodes [seg_node[k], seg_node[k+1]) and
+  // elements [seg_elem[k], seg_elem[k+1]); model_range[m] = element range of
+  // model m (empty when absent).  nseg = 1 for a plain context.
+  int32_t nseg = 1;
+  std::vector<int64_t> seg_node, seg_elem;
+  std::vector<int32_t> seg_member, seg_model;
+  int64_t model_range[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+
   // ---------------------------------------------------------- setup products
   bool built = false;
   int64_t n = 0, nnz = 0, ntrip = 0;

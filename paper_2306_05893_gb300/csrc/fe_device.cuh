@@ -35,6 +35,10 @@ enum {
   S_COUNT = 16
 };
 
+// Per-member scalars of a batched solve (double [nseg][B_COUNT]).
+enum { B_RZ = 0, B_PQ, B_ALPHA, B_BETA, B_RR, B_BB, B_TOL2, B_DONE, B_ITERS, B_ORR, B_OTOL2, B_ODONE, B_COUNT = 12 };
+enum { SEG_PQ = 0, SEG_RR, SEG_RZ_FIRST, SEG_RZ, SEG_INIT_OUTER, SEG_INIT_INNER, SEG_ORR };
+
 struct Buf {
   void *p = nullptr;
   size_t bytes = 0;
@@ -119,6 +123,12 @@ struct DeviceState {
   int64_t stage_calls[FE_STAGE_COUNT] = {0};
   mutable int64_t launches = 0;
 
+  // batched solve: member DOF ranges, row -> member, per-member scalars
+  int64_t *seg_dof = nullptr;
+  int32_t *row_seg = nullptr;
+  double *bscal = nullptr, *h_bscal = nullptr;
+  int spmv_tpr = 0;                // autotuned threads per CSR row (0: not yet)
+
   // adjoint: per-step checkpoints (q_t, v_t, a_t) and reverse-sweep buffers
   std::vector<double *> ckpt;      // each [3n]: q_t, v_t, a_t
   double *qbar = nullptr, *vbar = nullptr, *sbar = nullptr, *ge = nullptr, *kl = nullptr;
@@ -149,6 +159,20 @@ void launch_init_solve(const fe_ctx *c, const DeviceState *d, bool fp32, void *x
 void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s);  // x += (double) vd
 void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s);
 void launch_convert(const void *src, bool src32, void *dst, bool dst32, int64_t n, cudaStream_t s);
+
+// (fe_batch.cu)
+void launch_seg_dot(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, const void *y, int mode,
+                    double tol, cudaStream_t s);
+void launch_seg_dot64(const fe_ctx *c, const DeviceState *d, const double *x, const double *y, int mode, double tol,
+                      cudaStream_t s);
+void launch_seg_init(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const double *rhs,
+                     bool inner, cudaStream_t s);
+void launch_seg_axpy(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const void *p,
+                     const void *q, cudaStream_t s);
+void launch_seg_update_p(const fe_ctx *c, const DeviceState *d, bool fp32, const void *z, void *p, bool first,
+                         cudaStream_t s);
+void launch_spmv_plain(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y, const double *b,
+                       int tpr, cudaStream_t s);
 
 // (fe_adjoint.cu)
 void launch_adjoint_element(const fe_ctx *c, const DeviceState *d, bool fp32, const double *q, const double *lam,

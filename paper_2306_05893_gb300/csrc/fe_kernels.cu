@@ -66,7 +66,8 @@ __device__ __forceinline__ T ld_cast(const double *p) { return T(__ldg(p)); }
 // volume.  Outputs f_e [E][4][3] and K_e [E][144] in fill order
 // ((a*4 + b)*9 + 3i + k), staged through shared memory for coalesced stores.
 template <int MODEL, typename T, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, const int32_t *__restrict__ conn,
+__global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, int64_t e_begin, int64_t e_end,
+                                                    const int32_t *__restrict__ conn,
                                                     const double *__restrict__ rest,
                                                     const double *__restrict__ params,
                                                     const double *__restrict__ X,
@@ -75,9 +76,9 @@ __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, const int32_t *__
   extern __shared__ unsigned char smem_raw[];
   T *sk = reinterpret_cast<T *>(smem_raw);
   constexpr int LD = 145;
-  const int64_t e0 = int64_t(blockIdx.x) * BLOCK;
+  const int64_t e0 = e_begin + int64_t(blockIdx.x) * BLOCK;
   const int64_t e = e0 + threadIdx.x;
-  if (e < E) {
+  if (e < e_end) {
     const int4 cn = reinterpret_cast<const int4 *>(conn)[e];
     const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
     T g[4][3];
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, const int32_t *__
     }
   }
   __syncthreads();
-  const int64_t nvalid = (E - e0) < BLOCK ? (E - e0) : BLOCK;
+  const int64_t nvalid = (e_end - e0) < BLOCK ? (e_end - e0) : BLOCK;
   T *dst = K_out + e0 * 144;
   for (int64_t idx = threadIdx.x; idx < nvalid * 144; idx += BLOCK)
     dst[idx] = sk[(idx / 144) * LD + idx % 144];
@@ -153,7 +154,8 @@ __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, const int32_t *__
 // [8 * 25][E]: per Gauss point grad N (8 x 3) and w det J0.  Thread a owns
 // the block row a of K_e (72 values) and f_a.
 template <int MODEL, typename T, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, const int32_t *__restrict__ conn,
+__global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, int64_t e_end,
+                                                    const int32_t *__restrict__ conn,
                                                     const double *__restrict__ rest,
                                                     const double *__restrict__ params,
                                                     const double *__restrict__ X,
@@ -163,10 +165,10 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, const int32_t *__
   T *sk = reinterpret_cast<T *>(smem_raw);
   constexpr int EPB = BLOCK / 8;  // elements per block
   constexpr int LD = 577;
-  const int64_t e0 = int64_t(blockIdx.x) * EPB;
+  const int64_t e0 = e_begin + int64_t(blockIdx.x) * EPB;
   const int el = threadIdx.x >> 3, a = threadIdx.x & 7;
   const int64_t e = e0 + el;
-  if (e < E) {
+  if (e < e_end) {
     T u[8][3];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, const int32_t *__
       for (int c = 0; c < 9; ++c) row[b * 9 + c] = acc[b][c];
   }
   __syncthreads();
-  const int64_t nvalid = (E - e0) < EPB ? (E - e0) : EPB;
+  const int64_t nvalid = (e_end - e0) < EPB ? (e_end - e0) : EPB;
   T *dst = K_out + e0 * 576;
   for (int64_t idx = threadIdx.x; idx < nvalid * 576; idx += BLOCK)
     dst[idx] = sk[(idx / 576) * LD + idx % 576];
@@ -239,34 +241,36 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, const int32_t *__
 template <int MODEL, typename T>
 static void launch_element_t(const fe_ctx *c, const DeviceState *d, const double *q, cudaStream_t s) {
   const int64_t E = c->n_elems;
+  const int64_t eb = c->model_range[MODEL][0], ee = c->model_range[MODEL][1];
+  if (ee <= eb) return;
+  const int64_t EN = ee - eb;
   T *fo = reinterpret_cast<T *>(d->fe);
   T *Ko = reinterpret_cast<T *>(d->Ke);
   if (c->elem_type == FE_TET4) {
     constexpr int B = sizeof(T) == 8 ? 64 : 128;
     const size_t sm = size_t(B) * 145 * sizeof(T);
     cudaFuncSetAttribute(tet_kernel<MODEL, T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    tet_kernel<MODEL, T, B><<<unsigned((E + B - 1) / B), B, sm, s>>>(E, d->conn, d->rest, d->params,
-                                                                     d->X, q, fo, Ko, d->flags);
+    tet_kernel<MODEL, T, B><<<unsigned((EN + B - 1) / B), B, sm, s>>>(E, eb, ee, d->conn, d->rest, d->params,
+                                                                      d->X, q, fo, Ko, d->flags);
   } else {
     constexpr int B = 128, EPB = B / 8;
     const size_t sm = size_t(EPB) * 577 * sizeof(T);
     cudaFuncSetAttribute(hex_kernel<MODEL, T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    hex_kernel<MODEL, T, B><<<unsigned((E + EPB - 1) / EPB), B, sm, s>>>(E, d->conn, d->rest, d->params,
-                                                                        d->X, q, fo, Ko, d->flags);
+    hex_kernel<MODEL, T, B><<<unsigned((EN + EPB - 1) / EPB), B, sm, s>>>(E, eb, ee, d->conn, d->rest,
+                                                                         d->params, d->X, q, fo, Ko, d->flags);
   }
 }
 
 void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool fp32, cudaStream_t s) {
-  d->launches++;
-  switch (c->model) {
-    case FE_SVK:
+  // one launch per material model present (a batch groups its members by model)
+  for (int md = FE_SVK; md <= FE_MOONEY_RIVLIN; ++md) {
+    if (c->model_range[md][1] <= c->model_range[md][0]) continue;
+    d->launches++;
+    if (md == FE_SVK)
       fp32 ? launch_element_t<FE_SVK, float>(c, d, q, s) : launch_element_t<FE_SVK, double>(c, d, q, s);
-      break;
-    case FE_NEOHOOKE:
-      fp32 ? launch_element_t<FE_NEOHOOKE, float>(c, d, q, s)
-           : launch_element_t<FE_NEOHOOKE, double>(c, d, q, s);
-      break;
-    default:
+    else if (md == FE_NEOHOOKE)
+      fp32 ? launch_element_t<FE_NEOHOOKE, float>(c, d, q, s) : launch_element_t<FE_NEOHOOKE, double>(c, d, q, s);
+    else
       fp32 ? launch_element_t<FE_MOONEY_RIVLIN, float>(c, d, q, s)
            : launch_element_t<FE_MOONEY_RIVLIN, double>(c, d, q, s);
   }
@@ -509,9 +513,9 @@ template <typename TV>
 __global__ void update_p_kernel(int64_t n, const TV *__restrict__ z, TV *__restrict__ p, int first,
                                 const double *scal) {
   if (solve_done(scal)) return;
-  const TV be = first ? TV(0) : TV(scal[S_BETA]);
+  const TV be = TV(scal[S_BETA]);
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    p[i] = z[i] + be * p[i];
+    p[i] = first ? z[i] : z[i] + be * p[i];  // first: p = z, whatever p held
 }
 
 // Start of a (sub)solve: x = 0, r = rhs (cast), ||rhs||^2 -> tolerance.
