@@ -162,6 +162,94 @@ def run_reference(args, rank):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------- side metrics
+
+def measure_adjoint(fe, torch, T=20, reps=2):
+    """grads/s of the adjoint workload: hex 20x20x80 neo-Hookean beam with a
+    per-element log-normal Young's modulus (median 1e4, sigma 0.3, seed 11),
+    L = 1/2 ||q_T - q*||^2 after T steps (q* from the seed-12 field); one
+    gradient = forward rollout with checkpoints + reverse adjoint sweep."""
+    import fe_inputs as fi
+    mesh = fi.hex_beam(20, 20, 80, jitter=0.1, seed=1)
+    nu = 3.1e4 / (2 * (3.1e4 + 3.4e3))
+    base = np.array([*fi.lame_from_young(1.0, nu), 0.0])
+    E = fi.lognormal_modulus(mesh.n_elems, seed=11)
+    trac = fi.end_traction(mesh, (50.0, 0.0, 0.0)).reshape(-1)
+    ctx = fe.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.NEOHOOKE, 1000.0,
+                       E[:, None] * base[None, :], 0.01, 0.1, 0.01, precision=1, refactor_every=5,
+                       keep_checkpoints=1)
+    q = np.empty(ctx.n)
+    v = np.empty(ctx.n)
+    q0 = mesh.X.reshape(-1).copy()
+    qt = q0 + 1e-4
+
+    def one():
+        ctx.set_state(q0, np.zeros_like(q0))
+        ctx.clear_checkpoints()
+        for _ in range(T):
+            ctx.step(trac, q, v)
+        ds, _ = ctx.adjoint(q - qt, with_dp=False)
+        return ds
+
+    one()  # warm-up (factor buffers, first-call setup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    ctx.close()
+    return {"value": reps / el, "unit": "grads/s", "workload": "hex20x20x80-nh per-element E, T=20",
+            "n_dof": 3 * mesh.n_nodes, "precision": "mixed", "s_per_grad": el / reps}
+
+
+def run_batch(args, world, rank, local, torch, dist):
+    """Batched workload: 64 uneven tet beams (seed 7) stepped together; members
+    sharded over ranks by DOF (no collective on the data path)."""
+    import fe_inputs as fi
+    import paper_2306_05893_gb300 as fe
+    from paper_2306_05893_gb300.sharding import shard_members
+    mem = fi.batch_workload(64, seed=7)
+    mine = shard_members([3 * m.mesh.n_nodes for m in mem], world)[rank]
+    b = fe.FEBatch([(mem[k].mesh.elem_type, mem[k].mesh.X, mem[k].mesh.conn, mem[k].mesh.fixed_nodes,
+                     mem[k].model, mem[k].params) for k in mine], 0.01, 0.1, 0.01, 1000.0,
+                   precision=1, refactor_every=5, tol=1e-8)
+    # loads concatenated in the batch's stored member order
+    p = np.concatenate([mem[mine[k]].load.reshape(-1) for k in b.member])
+    q = np.empty(b.n)
+    v = np.empty(b.n)
+    for _ in range(args.warmup):
+        b.step(p, q, v)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.step(p, q, v)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([el], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el = float(tt.item())
+    ndof_all = sum(3 * m.mesh.n_nodes for m in mem) if world == 1 else None
+    dofs_mine = b.n
+    if world > 1:
+        t = torch.tensor([float(dofs_mine)], device="cuda")
+        dist.all_reduce(t)
+        ndof_all = float(t.item())
+    out = {"metric": "aggregate DOF*steps/s, batched tet beams", "value": ndof_all * args.steps / el,
+           "unit": "DOF*steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "batch64-tet (seed 7, 2k-40k DOF each)", "members": len(mem),
+                      "total_dof": ndof_all, "steps_per_s_per_beam": args.steps / el,
+                      "parallelism": f"members sharded over {world} ranks" if world > 1 else "single"}}
+    b.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 # --------------------------------------------------------------------- ours
 
 def main():
@@ -173,6 +261,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -194,6 +283,8 @@ def main():
     import fe_inputs as fi
     import paper_2306_05893_gb300 as fe
 
+    if args.workload == "batch64":
+        return run_batch(args, world, rank, local, torch, dist)
     wl = fi.workload(args.workload)
     K, W = args.steps, args.warmup
     stream = torch.cuda.Stream()
@@ -299,6 +390,8 @@ def main():
         "e2e": e2e,
     }
     del bytes_asm
+    if rank == 0 and not args.no_adjoint and args.workload == WORKLOAD:
+        out["adjoint"] = measure_adjoint(fe, torch)
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, desc, _ = oracle_step_sample(wl)
         out["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",

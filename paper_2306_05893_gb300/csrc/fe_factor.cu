@@ -98,11 +98,10 @@ __global__ void __launch_bounds__(256) front_diag_kernel(const int32_t *__restri
     Xi[i][j] = (i == j) ? TF(1) : TF(0);
   }
   __syncthreads();
-  __shared__ double s_inv[2];
+  __shared__ double s_inv[64];
   if (threadIdx.x < kb) dg[threadIdx.x] = double(L[threadIdx.x][threadIdx.x]);
   const int c = threadIdx.x & 63, r = threadIdx.x >> 6;
   __syncthreads();
-  // the pivot's FP64 inverse is computed once, by one thread, a step ahead
   if (threadIdx.x == 0) {
     double d0 = dg[0];
     if (!(d0 > 0.0)) {
@@ -112,33 +111,42 @@ __global__ void __launch_bounds__(256) front_diag_kernel(const int32_t *__restri
     s_inv[0] = 1.0 / d0;
   }
   __syncthreads();
+  // One barrier per pivot: columns stay unscaled until the write-back, and
+  // the lane that makes the last update of pivot j+1 (row j+1 at step j)
+  // computes its FP64 inverse right away.
   for (int j = 0; j < kb; ++j) {
-    const double invd = s_inv[j & 1];
+    const double invd = s_inv[j];
     const TF tinv = TF(invd);
     for (int i = j + 1 + r; i < kb; i += 4) {
       const TF lij = L[i][j];
       if (c > j && c < i) L[i][c] -= lij * L[c][j] * tinv;
       if (c <= j) Xi[i][c] -= lij * tinv * Xi[j][c];
-      if (c == i) dg[i] -= double(lij) * double(lij) * invd;  // FP64 pivots, one update per lane
-    }
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) L[i][j] *= tinv;
-    if (threadIdx.x == 0) {
-      double d = dg[j];
-      if (!(d > 0.0)) d = 1.0;
-      D[fr.first + k0 + j] = d;
-      Dinv[fr.first + k0 + j] = invd;
-      if (j + 1 < kb) {
-        double dn = dg[j + 1];
-        if (!(dn > 0.0)) {
-          atomicOr(flags, FLAG_PIVOT);
-          dn = 1.0;
+      if (c == i) {
+        const double di = dg[i] - double(lij) * double(lij) * invd;  // FP64 pivots
+        dg[i] = di;
+        if (i == j + 1) {
+          double dn = di;
+          if (!(dn > 0.0)) {
+            atomicOr(flags, FLAG_PIVOT);
+            dn = 1.0;
+          }
+          s_inv[i] = 1.0 / dn;
         }
-        s_inv[(j + 1) & 1] = 1.0 / dn;
       }
     }
     __syncthreads();
   }
+  if (threadIdx.x < kb) {
+    double d = dg[threadIdx.x];
+    if (!(d > 0.0)) d = 1.0;
+    D[fr.first + k0 + threadIdx.x] = d;
+    Dinv[fr.first + k0 + threadIdx.x] = s_inv[threadIdx.x];
+  }
+  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+    const int i = idx % kb, j = idx / kb;
+    if (i > j) L[i][j] *= TF(s_inv[j]);
+  }
+  __syncthreads();
   TF *Yf = Y + fr.y_off;
   for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
     const int i = idx % kb, j = idx / kb;

@@ -283,14 +283,18 @@ void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool
 // slots (rows 3n+i, position 3*bp + k in the row) and its share of
 // (alpha M + (beta+h) K) v; the node's element forces come from its
 // incidence list.  Fixed nodes keep the lone unit diagonal and b = 0.
-template <typename TK, typename TA>
+template <typename TK, typename TA, typename TS>
 __global__ void __launch_bounds__(256) assemble_block_kernel(
     int64_t n_nodes, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ bptr,
     const int32_t *__restrict__ bcol, const int32_t *__restrict__ bsrc_ptr, const int32_t *__restrict__ bsrc,
     const double *__restrict__ bmass, const TK *__restrict__ Ke, const TK *__restrict__ fe,
     const int32_t *__restrict__ node_ptr, const int32_t *__restrict__ node_src,
     const int8_t *__restrict__ fixed_row, const double *__restrict__ v, const double *__restrict__ p,
-    double cM, double cK, double al, double bh, TA *__restrict__ A, double *__restrict__ b) {
+    double cM_, double cK_, double al_, double bh_, TA *__restrict__ A, double *__restrict__ b) {
+  // TS: type of the block sums (FP64, or FP32 in the mixed path, whose K_e and
+  // A are FP32: GB300's FP64 pipe would otherwise bound this kernel); the row
+  // partials of b are reduced across the warp in FP64 either way.
+  const TS cM = TS(cM_), cK = TS(cK_), al = TS(al_), bh = TS(bh_);
   const int lane = threadIdx.x & 31;
   const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
   for (int64_t nd = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); nd < n_nodes; nd += warps) {
@@ -302,61 +306,51 @@ __global__ void __launch_bounds__(256) assemble_block_kernel(
       }
       continue;
     }
-    const int32_t rp0 = rowptr[r0], rp1 = rowptr[r0 + 1], rp2 = rowptr[r0 + 2];
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    const int32_t rps[3] = {rowptr[r0], rowptr[r0 + 1], rowptr[r0 + 2]};
+    TS acc[3] = {TS(0), TS(0), TS(0)};
     for (int32_t k = bptr[nd] + lane; k < bptr[nd + 1]; k += 32) {
-      double blk[9];
+      TS blk[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) blk[q] = 0.0;
+      for (int q = 0; q < 9; ++q) blk[q] = TS(0);
       const int32_t j1 = bsrc_ptr[k + 1];
       for (int32_t j = bsrc_ptr[k]; j < j1; ++j) {
         const TK *src = Ke + int64_t(bsrc[j]) * 9;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) blk[q] += double(src[q]);
+        for (int q = 0; q < 9; ++q) blk[q] += TS(src[q]);
       }
-      const double mb = bmass[k];
+      const TS mb = TS(bmass[k]);
       const int32_t bp = 3 * (k - bptr[nd]);
       const int64_t cn = 3 * int64_t(bcol[k]);
-      const double v0 = v[cn], v1 = v[cn + 1], v2 = v[cn + 2];
-      const int32_t rps[3] = {rp0, rp1, rp2};
-      double part[3];
+      const TS vv[3] = {TS(v[cn]), TS(v[cn + 1]), TS(v[cn + 2])};
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const double vv[3] = {v0, v1, v2};
-        double s = 0.0;
 #pragma unroll
         for (int kk = 0; kk < 3; ++kk) {
-          const double Ms = (i == kk) ? mb : 0.0;
-          const double Ks = blk[3 * i + kk];
+          const TS Ms = (i == kk) ? mb : TS(0);
+          const TS Ks = blk[3 * i + kk];
           A[rps[i] + bp + kk] = TA(cM * Ms + cK * Ks);
-          s += (al * Ms + bh * Ks) * vv[kk];
+          acc[i] += (al * Ms + bh * Ks) * vv[kk];
         }
-        part[i] = s;
       }
-      acc0 += part[0];
-      acc1 += part[1];
-      acc2 += part[2];
     }
-    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    TS fs[3] = {TS(0), TS(0), TS(0)};
     for (int32_t j = node_ptr[nd] + lane; j < node_ptr[nd + 1]; j += 32) {
-      const TK *fs = fe + int64_t(node_src[j]) * 3;
-      f0 += double(fs[0]);
-      f1 += double(fs[1]);
-      f2 += double(fs[2]);
+      const TK *f = fe + int64_t(node_src[j]) * 3;
+      fs[0] += TS(f[0]);
+      fs[1] += TS(f[1]);
+      fs[2] += TS(f[2]);
     }
+    double a0 = double(acc[0]) + double(fs[0]), a1 = double(acc[1]) + double(fs[1]),
+           a2 = double(acc[2]) + double(fs[2]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
-      acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
-      acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
-      f0 += __shfl_xor_sync(0xffffffffu, f0, o);
-      f1 += __shfl_xor_sync(0xffffffffu, f1, o);
-      f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
     }
     if (lane < 3) {
-      const double acc = lane == 0 ? acc0 : (lane == 1 ? acc1 : acc2);
-      const double ff = lane == 0 ? f0 : (lane == 1 ? f1 : f2);
-      b[r0 + lane] = (p ? p[r0 + lane] : 0.0) - ff - acc;
+      const double tot = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+      b[r0 + lane] = (p ? p[r0 + lane] : 0.0) - tot;
     }
   }
 }
@@ -369,12 +363,12 @@ void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const dou
   const int64_t nn = c->n_nodes;
   const unsigned grid = unsigned(std::min<int64_t>((nn + 7) / 8, 152 * 64));
   if (fp32)
-    assemble_block_kernel<float, float><<<grid, 256, 0, s>>>(
+    assemble_block_kernel<float, float, float><<<grid, 256, 0, s>>>(
         nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const float *)d->Ke,
         (const float *)d->fe, d->node_ptr, d->node_src, d->fixed_row, d->v, pext, cM, cK, al, bh,
         (float *)d->A, d->b);
   else
-    assemble_block_kernel<double, double><<<grid, 256, 0, s>>>(
+    assemble_block_kernel<double, double, double><<<grid, 256, 0, s>>>(
         nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const double *)d->Ke,
         (const double *)d->fe, d->node_ptr, d->node_src, d->fixed_row, d->v, pext, cM, cK, al, bh,
         (double *)d->A, d->b);
