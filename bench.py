@@ -318,6 +318,7 @@ def main():
         clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     stage_ms, stage_calls, launches = ctx.stage_times()
+    update_flops = ctx.update_flops()
     if world > 1:
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -352,18 +353,27 @@ def main():
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e["value"] = world * args.e2e_steps / float(tt.item())
 
-    # roofline of the dominant stage: the level-scheduled preconditioner
-    # application (forward + backward GEMV levels over the fronts' operators)
+    # roofline of the dominant kernel: the factor's trailing-update launches
+    # (FP32 SIMT FMA bound), and of the HBM-bound preconditioner application
     hbm, peak_kind = _peaks()
+    sm_mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0)) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s, 152 SMs x 128 FP32 lanes x FMA
+    upd_calls = max(1, stage_calls["factor_update"])
+    upd_ms = stage_ms["factor_update"] / upd_calls
+    upd_flops = update_flops / upd_calls
+    upd_tflops = upd_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "front_update128_kernel (factor trailing updates, FP32 SIMT)",
+                "achieved": upd_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": upd_tflops / fp32_peak,
+                "traffic": None, "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
+                "peak_source": f"derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x {sm_mhz:.0f} MHz"}
     apply_calls = max(1, stage_calls["apply"])
     apply_ms = stage_ms["apply"] / apply_calls
     bytes_apply = 2 * info["y_nnz"] * 4 + 6 * info["n_free"] * 4 + 2 * info["n"] * 4
     achieved = bytes_apply / (apply_ms / 1e3) / 1e9
-    dom = max(stage_ms, key=lambda k: stage_ms[k])
-    roofline = {"bound": "hbm", "kernel": "precond_apply (fwd_gemv+bwd levels)", "achieved": achieved,
-                "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "bytes_per_launch": bytes_apply, "avg_ms": apply_ms,
-                "dominant_stage": dom}
+    roofline_apply = {"bound": "hbm", "kernel": "precond apply (fwd_kernel + bwd_kernel, 22 launches)",
+                      "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                      "frac": achieved / hbm, "traffic": None, "bytes_per_launch": bytes_apply, "avg_ms": apply_ms}
     spmv_calls = max(1, stage_calls["spmv"])
     spmv_ms = stage_ms["spmv"] / spmv_calls
     bytes_spmv = info["nnz"] * (4 + 4) + (n + 1) * 4 + 2 * n * 4
@@ -380,6 +390,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single",
                    "mean_pcg_iters": float(np.mean(iters)), "max_displacement_m": disp},
         "roofline": roofline,
+        "roofline_apply": roofline_apply,
         "stages_ms_per_step": {k: v / K for k, v in stage_ms.items()},
         "stage_calls": stage_calls,
         "spmv": {"avg_ms": spmv_ms, "bytes": bytes_spmv,

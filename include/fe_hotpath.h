@@ -236,9 +236,13 @@ int fe_get_info(fe_ctx *ctx, fe_info *info);
 enum {
   FE_STAGE_ELEMENT = 0, FE_STAGE_ASSEMBLY, FE_STAGE_FACTOR, FE_STAGE_APPLY,
   FE_STAGE_SPMV, FE_STAGE_VECTOR, FE_STAGE_RESIDUAL, FE_STAGE_INTEGRATE,
+  FE_STAGE_FACTOR_UPDATE, /* the factor's trailing-update launches only */
   FE_STAGE_COUNT
 };
 int fe_get_stage_times(fe_ctx *ctx, double *ms, int64_t *calls, int64_t *kernel_launches);
+/* Algorithmic flops of the trailing-update launches timed so far (lower
+ * triangle of the Schur updates plus the apply-operator updates). */
+int fe_get_update_flops(fe_ctx *ctx, double *flops);
 int fe_reset_stage_times(fe_ctx *ctx);
 
 /* Replaces the material parameters ([n_elems * 3], element-major, the layout

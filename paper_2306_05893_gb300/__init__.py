@@ -232,6 +232,12 @@ def fe_get_stage_times(ctx):
             {k: calls[i] for i, k in enumerate(_abi.STAGES)}, launches.value)
 
 
+def fe_get_update_flops(ctx):
+    f = ct.c_double()
+    _check(ctx, load().fe_get_update_flops(ctx, ct.byref(f)))
+    return f.value
+
+
 def fe_reset_stage_times(ctx):
     _check(ctx, load().fe_reset_stage_times(ctx))
 
@@ -311,6 +317,9 @@ class FEContext:
 
     def stage_times(self):
         return fe_get_stage_times(self.ctx)
+
+    def update_flops(self):
+        return fe_get_update_flops(self.ctx)
 
     def reset_stage_times(self):
         fe_reset_stage_times(self.ctx)

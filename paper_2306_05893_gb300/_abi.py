@@ -41,7 +41,8 @@ class FeInfo(ct.Structure):
                 ("factor_flops", ct.c_double), ("device_bytes", ct.c_int64)]
 
 
-STAGES = ["element", "assembly", "factor", "apply", "spmv", "vector", "residual", "integrate"]
+STAGES = ["element", "assembly", "factor", "apply", "spmv", "vector", "residual", "integrate",
+          "factor_update"]
 
 P = ct.POINTER
 CTX = ct.c_void_p
@@ -76,6 +77,7 @@ SIGNATURES = {
     "fe_get_info": (ct.c_int, [CTX, P(FeInfo)]),
     "fe_get_stage_times": (ct.c_int, [CTX, DP, P(ct.c_int64), P(ct.c_int64)]),
     "fe_reset_stage_times": (ct.c_int, [CTX]),
+    "fe_get_update_flops": (ct.c_int, [CTX, DP]),
     "fe_set_params": (ct.c_int, [CTX, ct.c_void_p]),
     "fe_adjoint": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "fe_clear_checkpoints": (ct.c_int, [CTX]),

@@ -18,6 +18,8 @@ namespace {
 bool mixed(const fe_ctx *c) { return c->opt.precision == FE_MIXED; }
 size_t vsz(const fe_ctx *c) { return mixed(c) ? sizeof(float) : sizeof(double); }
 
+}  // namespace
+
 // ------------------------------------------------------ live stage timing
 int stage_begin(fe_ctx *c, int stage, cudaStream_t s) {
   DeviceState *d = c->dev;
@@ -40,6 +42,8 @@ int stage_begin(fe_ctx *c, int stage, cudaStream_t s) {
 void stage_end(fe_ctx *c, int idx, cudaStream_t s) {
   if (idx >= 0) cudaEventRecord(c->dev->recs[idx].b, s);
 }
+
+namespace {
 
 // Harvest every finished record (both streams must be idle when all = true).
 void stage_collect(fe_ctx *c) {
@@ -243,6 +247,7 @@ int ensure_device(fe_ctx *c) {
       T.panel_off.push_back(int64_t(all.size())); T.panel_n.push_back(int64_t(L.panel[s].size() / 4));
       all.insert(all.end(), L.panel[s].begin(), L.panel[s].end());
       T.trail_off.push_back(int64_t(all.size())); T.trail_n.push_back(int64_t(L.trail[s].size() / 4));
+      T.trail_flops.push_back(L.trail_flops[s]);
       all.insert(all.end(), L.trail[s].begin(), L.trail[s].end());
     }
     pad4();
@@ -922,6 +927,12 @@ int fe_get_stage_times(fe_ctx *c, double *ms, int64_t *calls, int64_t *kernel_la
   return FE_OK;
 }
 
+int fe_get_update_flops(fe_ctx *c, double *flops) {
+  if (!c || !flops) return FE_ERR_ARG;
+  *flops = c->dev ? c->dev->update_flops : 0.0;
+  return FE_OK;
+}
+
 int fe_reset_stage_times(fe_ctx *c) {
   if (!c) return FE_ERR_ARG;
   DeviceState *d = c->dev;
@@ -934,6 +945,7 @@ int fe_reset_stage_times(fe_ctx *c) {
     d->stage_calls[k] = 0;
   }
   d->launches = 0;
+  d->update_flops = 0.0;
   return FE_OK;
 }
 

@@ -40,6 +40,7 @@ struct Level {
   // factorisation task lists: assembly, then per step {diag, panel+xk, trail+rupd}
   std::vector<int32_t> asm_tasks;     // (front, c0, c1) triples
   std::vector<std::vector<int32_t>> diag, panel, trail;  // int4 per task
+  std::vector<double> trail_flops;    // algorithmic flops of each step's update launch
   // apply task lists
   std::vector<int32_t> fwd_tasks;     // (front, r0) pairs, kFwdRows-row blocks
   std::vector<int32_t> bwd_tasks;     // (front, c0) pairs, kBwdCols-column blocks

@@ -106,6 +106,7 @@ struct DeviceState {
   struct LevelTasks {
     int64_t asm_off = 0, asm_n = 0;
     std::vector<int64_t> diag_off, diag_n, panel_off, panel_n, trail_off, trail_n;
+    std::vector<double> trail_flops;
     int64_t fwd_off = 0, fwd_n = 0, bwd_off = 0, bwd_n = 0;
     int64_t nfronts = 0, fronts_off = 0;
   };
@@ -122,6 +123,7 @@ struct DeviceState {
   double stage_ms[FE_STAGE_COUNT] = {0};
   int64_t stage_calls[FE_STAGE_COUNT] = {0};
   mutable int64_t launches = 0;
+  double update_flops = 0.0;            // algorithmic flops of the timed update launches
 
   // batched solve: member DOF ranges, row -> member, per-member scalars
   int64_t *seg_dof = nullptr;
@@ -182,6 +184,10 @@ void launch_adjoint_gather(const fe_ctx *c, const DeviceState *d, const double *
                            const double *lam, double *qbar, double *vbar, double *pbar, cudaStream_t s);
 void launch_adjoint_rhs(const fe_ctx *c, const DeviceState *d, const double *qbar, const double *vbar,
                         double *abar, cudaStream_t s);
+
+// stage timing hooks (fe_api.cu); idx < 0 when profiling is off
+int stage_begin(fe_ctx *c, int stage, cudaStream_t s);
+void stage_end(fe_ctx *c, int idx, cudaStream_t s);
 
 // (fe_factor.cu)
 int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Afac, cudaStream_t s);

@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int32_t *__restrict__ ta
 // ------------------------------------------------------------ host drivers
 
 template <typename TF>
-static void factor_levels(const fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cudaStream_t s) {
+static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cudaStream_t s) {
   TF *F = reinterpret_cast<TF *>(d->F);
   TF *Y = reinterpret_cast<TF *>(d->Y[buf]);
   const size_t tsm = 2 * 64 * 65 * sizeof(TF);
@@ -605,12 +605,15 @@ static void factor_levels(const fe_ctx *c, DeviceState *d, int buf, const TF *Af
         front_panel_kernel<TF><<<unsigned(L.panel_n[st]), 256, tsm, s>>>(d->tasks + L.panel_off[st], d->fronts, F, Y,
                                                                        d->D[buf] + c->n_free);
       if (L.trail_n[st]) {
+        const int ev = stage_begin(c, FE_STAGE_FACTOR_UPDATE, s);
+        if (ev >= 0) d->update_flops += L.trail_flops[st];
         if constexpr (sizeof(TF) == 4)
           front_update128_kernel<<<unsigned(L.trail_n[st]), 256, t128, s>>>(d->tasks + L.trail_off[st], d->fronts,
                                                                            F, Y, d->D[buf]);
         else
           front_update_kernel<TF><<<unsigned(L.trail_n[st]), 256, tsm, s>>>(d->tasks + L.trail_off[st], d->fronts, F,
                                                                           Y, d->D[buf]);
+        stage_end(c, ev, s);
       }
     }
   }

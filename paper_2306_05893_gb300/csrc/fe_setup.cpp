@@ -540,6 +540,7 @@ int build_ordering(fe_ctx *c) {
     L.diag.assign(steps, {});
     L.panel.assign(steps, {});
     L.trail.assign(steps, {});
+    L.trail_flops.assign(steps, 0.0);
     for (int32_t f : L.fronts) {
       const Front &F = c->fronts[f];
       const int32_t m = F.m(), p = F.npiv;
@@ -563,6 +564,7 @@ int build_ordering(fe_ctx *c) {
         for (int32_t i0 = k1; i0 < m; i0 += ut)
           for (int32_t c0 = 0; c0 < k1; c0 += ut) push(L.trail[s], f, (T_RUPD << 24) | k0, i0, c0);
         double rem = double(m - k1);
+        L.trail_flops[s] += rem * (rem + 1.0) * kb + 2.0 * rem * double(k1) * kb;
         flops += double(kb) * kb * kb / 3.0 * 2.0            // diag LDL^T + inverse
                  + 2.0 * rem * kb * kb                        // panel
                  + 2.0 * double(kb) * kb * k0                 // X_K
