@@ -73,6 +73,20 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
 }
 
 // ---------------------------------------------------------------- diagonal
+// 1/d in FP64 without an FP64 division (a long-latency operation on GB300,
+// and this one sits on the serial path of the block): FP32 reciprocal, then
+// one Newton step in FP64, x (2 - d x).  A non-positive pivot is flagged and
+// replaced by 1 so the factorisation finishes without NaNs.
+__device__ __forceinline__ double pivot_inverse(double d, int *flags) {
+  if (!(d > 0.0)) {
+    atomicOr(flags, FLAG_PIVOT);
+    d = 1.0;
+  }
+  if (d < 1e-30 || d > 1e30) return 1.0 / d;  // outside FP32's comfortable range
+  const double x = double(__frcp_rn(float(d)));
+  return x * (2.0 - d * x);
+}
+
 // Task (front, k0, kb): LDL^T of the kb x kb diagonal block.  The eliminations
 // run in the factor's type TF; the pivots are accumulated in FP64 (dg) and
 // stored in FP64 with their inverses.  The same row operations applied to the
@@ -102,18 +116,11 @@ __global__ void __launch_bounds__(256) front_diag_kernel(const int32_t *__restri
   if (threadIdx.x < kb) dg[threadIdx.x] = double(L[threadIdx.x][threadIdx.x]);
   const int c = threadIdx.x & 63, r = threadIdx.x >> 6;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double d0 = dg[0];
-    if (!(d0 > 0.0)) {
-      atomicOr(flags, FLAG_PIVOT);
-      d0 = 1.0;
-    }
-    s_inv[0] = 1.0 / d0;
-  }
+  if (threadIdx.x == 0) s_inv[0] = pivot_inverse(dg[0], flags);
   __syncthreads();
   // One barrier per pivot: columns stay unscaled until the write-back, and
   // the lane that makes the last update of pivot j+1 (row j+1 at step j)
-  // computes its FP64 inverse right away.
+  // computes its inverse right away.
   for (int j = 0; j < kb; ++j) {
     const double invd = s_inv[j];
     const TF tinv = TF(invd);
@@ -124,14 +131,7 @@ __global__ void __launch_bounds__(256) front_diag_kernel(const int32_t *__restri
       if (c == i) {
         const double di = dg[i] - double(lij) * double(lij) * invd;  // FP64 pivots
         dg[i] = di;
-        if (i == j + 1) {
-          double dn = di;
-          if (!(dn > 0.0)) {
-            atomicOr(flags, FLAG_PIVOT);
-            dn = 1.0;
-          }
-          s_inv[i] = 1.0 / dn;
-        }
+        if (i == j + 1) s_inv[i] = pivot_inverse(di, flags);
       }
     }
     __syncthreads();
@@ -425,6 +425,149 @@ __global__ void __launch_bounds__(256) front_update128_kernel(const int32_t *__r
   }
 }
 
+// Tensor-core variant of the FP32 trailing updates: warp-level m16n8k8 TF32
+// MMAs with a 3xTF32 split (a = a_hi + a_lo, a*b ~ a_hi b_hi + a_hi b_lo +
+// a_lo b_hi) so products keep ~FP32 accuracy.  Same tiles, loads and
+// epilogue as front_update128_kernel; 8 warps as 2 (rows) x 4 (columns),
+// each warp 64 x 32 outputs = 4 x 4 MMA tiles.
+constexpr int kLdMma = 136;  // row stride: fragment loads hit 32 distinct banks
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(256) front_update_mma_kernel(const int32_t *__restrict__ tasks,
+                                                               const DFront *__restrict__ fronts,
+                                                               float *__restrict__ F, float *__restrict__ Y,
+                                                               const double *__restrict__ D) {
+  extern __shared__ __align__(16) float umm[];
+  float *As = umm;                  // [64][kLdMma]: As[l][i] = L[i0 + i, k0 + l]
+  float *Bs = umm + 64 * kLdMma;    // [64][kLdMma]: Bs[l][j]
+  float *Cs = umm;                  // epilogue [128][129] (column j, row i)
+  __shared__ float Ds[64];
+  const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
+  const DFront fr = fronts[t.x];
+  const int kind = t.y >> 24;
+  const int32_t k0 = t.y & 0xffffff, i0 = t.z, j0 = t.w, m = fr.m;
+  const int32_t kb = (fr.npiv - k0) < 64 ? (fr.npiv - k0) : 64;
+  float *Ff = F + fr.f_off;
+  float *Yf = Y + fr.y_off;
+  for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
+    const int l = idx / kT128, i = idx % kT128;
+    const int32_t r = i0 + i;
+    const bool ok = r < m && l < kb;
+    cp_async4(As + l * kLdMma + i, ok ? Ff + r + int64_t(k0 + l) * m : Ff, ok);
+  }
+  if (kind == T_TRAIL) {
+    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
+      const int l = idx / kT128, j = idx % kT128;
+      const int32_t r = j0 + j;
+      const bool ok = r < m && l < kb;
+      cp_async4(Bs + l * kLdMma + j, ok ? Ff + r + int64_t(k0 + l) * m : Ff, ok);
+    }
+    if (threadIdx.x < 64) Ds[threadIdx.x] = threadIdx.x < kb ? float(D[fr.first + k0 + threadIdx.x]) : 0.f;
+  } else {
+    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
+      const int l = idx % 64, j = idx / 64;
+      const int32_t c = j0 + j;
+      const bool ok = l < kb && c < k0 + kb;
+      cp_async4(Bs + l * kLdMma + j, ok ? Yf + (k0 + l) + int64_t(c) * fr.ldy : Yf, ok);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (kind == T_TRAIL) {
+    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256)
+      Bs[(idx / kT128) * kLdMma + idx % kT128] *= Ds[idx / kT128];
+    __syncthreads();
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int wm = warp & 1, wn = warp >> 1;      // 2 x 4 warps
+  float acc[4][4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[a][b][v] = 0.f;
+  const int ksteps = (kb + 7) / 8;  // zero-filled beyond kb
+  for (int ks = 0; ks < ksteps; ++ks) {
+    const int kk = 8 * ks;
+    uint32_t ah[4][4], al[4][4], bh[4][2], bl[4][2];
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+      const int mrow = wm * 64 + mt * 16 + g;
+      split_tf32(As[(kk + tq) * kLdMma + mrow], ah[mt][0], al[mt][0]);
+      split_tf32(As[(kk + tq) * kLdMma + mrow + 8], ah[mt][1], al[mt][1]);
+      split_tf32(As[(kk + tq + 4) * kLdMma + mrow], ah[mt][2], al[mt][2]);
+      split_tf32(As[(kk + tq + 4) * kLdMma + mrow + 8], ah[mt][3], al[mt][3]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int ncol = wn * 32 + nt * 8 + g;
+      split_tf32(Bs[(kk + tq) * kLdMma + ncol], bh[nt][0], bl[nt][0]);
+      split_tf32(Bs[(kk + tq + 4) * kLdMma + ncol], bh[nt][1], bl[nt][1]);
+    }
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        mma_tf32(acc[mt][nt], al[mt], bh[nt]);
+        mma_tf32(acc[mt][nt], ah[mt], bl[nt]);
+        mma_tf32(acc[mt][nt], ah[mt], bh[nt]);
+      }
+  }
+  __syncthreads();
+  const bool trail = kind == T_TRAIL;
+  const int32_t cmax = trail ? m : k0 + kb;
+  for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
+    const int j = idx / kT128, i = idx % kT128;
+    const int32_t r = i0 + i, c = j0 + j;
+    const bool ok = r < m && c < cmax;
+    const float *src = trail ? Ff + r + int64_t(c) * m : Yf + r + int64_t(c) * fr.ldy;
+    cp_async4(Cs + j * 129 + i, ok ? src : Ff, ok);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = wm * 64 + mt * 16 + g + 8 * (v >> 1);
+        const int j = wn * 32 + nt * 8 + 2 * tq + (v & 1);
+        Cs[j * 129 + i] -= acc[mt][nt][v];
+      }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
+    const int j = idx / kT128, i = idx % kT128;
+    const int32_t r = i0 + i, c = j0 + j;
+    if (r >= m || c >= cmax) continue;
+    if (trail) {
+      if (r >= c) Ff[r + int64_t(c) * m] = Cs[j * 129 + i];
+    } else {
+      Yf[r + int64_t(c) * fr.ldy] = Cs[j * 129 + i];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ apply
 // 16-byte vectors along the rows of Y (its leading dimension is a multiple of 4).
 template <typename T>
@@ -589,6 +732,8 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
   cudaFuncSetAttribute(front_update_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
   const size_t t128 = 2 * 64 * kLd128 * sizeof(float);
   cudaFuncSetAttribute(front_update128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t128));
+  const size_t tmma = 2 * 64 * kLdMma * sizeof(float);
+  cudaFuncSetAttribute(front_update_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tmma));
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
     if (L.asm_n) d->launches++;
@@ -608,8 +753,8 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
         const int ev = stage_begin(c, FE_STAGE_FACTOR_UPDATE, s);
         if (ev >= 0) d->update_flops += L.trail_flops[st];
         if constexpr (sizeof(TF) == 4)
-          front_update128_kernel<<<unsigned(L.trail_n[st]), 256, t128, s>>>(d->tasks + L.trail_off[st], d->fronts,
-                                                                           F, Y, d->D[buf]);
+          front_update_mma_kernel<<<unsigned(L.trail_n[st]), 256, tmma, s>>>(d->tasks + L.trail_off[st], d->fronts,
+                                                                            F, Y, d->D[buf]);
         else
           front_update_kernel<TF><<<unsigned(L.trail_n[st]), 256, tsm, s>>>(d->tasks + L.trail_off[st], d->fronts, F,
                                                                           Y, d->D[buf]);
