@@ -12,6 +12,7 @@ namespace fe {
 
 constexpr int kNB = 64;        // panel width of the front factorisation
 constexpr int kTile = 64;      // tile edge of the front update kernels
+constexpr int kSuper = 256;    // FP32 factor: trailing updates are applied once per kSuper pivots
 constexpr int kBwdCols = 32;   // pivot columns per task of the backward apply
 inline int fwd_rows(int precision) { return precision == FE_MIXED ? 128 : 64; }  // 32 threads x one 16-byte vector
 

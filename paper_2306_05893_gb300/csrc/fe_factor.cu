@@ -91,16 +91,23 @@ __device__ __forceinline__ double pivot_inverse(double d, int *flags) {
 // run in the factor's type TF; the pivots are accumulated in FP64 (dg) and
 // stored in FP64 with their inverses.  The same row operations applied to the
 // identity give L_KK^{-1} (Gauss-Jordan), written into Y[K, K]; L goes back
-// into F.  256 threads: lane c = tid % 64 owns column c, rows step by 4.
+// into F.  Warps 0-7: lane c = tid % 64 owns column c, rows step by 4.  Warp
+// 8 keeps the FP64 pivots: lane l owns rows l and l + 32, so the FP64 chain of
+// a pivot step is two updates deep instead of one per row (GB300's FP64 pipe
+// is narrow and long; serialising it per row dominated this kernel).
+constexpr int kDiagThreads = 288;
+
 template <typename TF>
-__global__ void __launch_bounds__(256) front_diag_kernel(const int32_t *__restrict__ tasks,
-                                                         const DFront *__restrict__ fronts, TF *__restrict__ F,
-                                                         TF *__restrict__ Y, double *__restrict__ D,
-                                                         double *__restrict__ Dinv, int *flags) {
+__global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t *__restrict__ tasks,
+                                                                  const DFront *__restrict__ fronts,
+                                                                  TF *__restrict__ F, TF *__restrict__ Y,
+                                                                  double *__restrict__ D,
+                                                                  double *__restrict__ Dinv, int *flags) {
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   double *dg = reinterpret_cast<double *>(dsm_raw);                      // [64]
   TF(*L)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double));
   TF(*Xi)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double) + 64 * 65 * sizeof(TF));
+  __shared__ double s_inv[64];
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t k0 = t.y & 0xffffff, kb = t.z, m = fr.m;
@@ -112,26 +119,38 @@ __global__ void __launch_bounds__(256) front_diag_kernel(const int32_t *__restri
     Xi[i][j] = (i == j) ? TF(1) : TF(0);
   }
   __syncthreads();
-  __shared__ double s_inv[64];
-  if (threadIdx.x < kb) dg[threadIdx.x] = double(L[threadIdx.x][threadIdx.x]);
+  const bool pivot_warp = threadIdx.x >= 256;
+  const int lane = threadIdx.x & 31;
+  if (pivot_warp) {
+    for (int i = lane; i < 64; i += 32) dg[i] = i < kb ? double(L[i][i]) : 1.0;
+    __syncwarp();
+    if (lane == 0) s_inv[0] = pivot_inverse(dg[0], flags);
+  }
+  __syncthreads();
   const int c = threadIdx.x & 63, r = threadIdx.x >> 6;
-  __syncthreads();
-  if (threadIdx.x == 0) s_inv[0] = pivot_inverse(dg[0], flags);
-  __syncthreads();
-  // One barrier per pivot: columns stay unscaled until the write-back, and
-  // the lane that makes the last update of pivot j+1 (row j+1 at step j)
-  // computes its inverse right away.
+  // One barrier per pivot.  Columns stay unscaled until the write-back: at
+  // step j column j of L holds the final Schur-complement entries F_ij, and
+  // the pivot warp folds F_ij^2 / d_j into the FP64 pivots of rows i > j,
+  // then inverts pivot j+1 for the next step.
   for (int j = 0; j < kb; ++j) {
     const double invd = s_inv[j];
-    const TF tinv = TF(invd);
-    for (int i = j + 1 + r; i < kb; i += 4) {
-      const TF lij = L[i][j];
-      if (c > j && c < i) L[i][c] -= lij * L[c][j] * tinv;
-      if (c <= j) Xi[i][c] -= lij * tinv * Xi[j][c];
-      if (c == i) {
-        const double di = dg[i] - double(lij) * double(lij) * invd;  // FP64 pivots
-        dg[i] = di;
-        if (i == j + 1) s_inv[i] = pivot_inverse(di, flags);
+    if (pivot_warp) {
+      const int i0 = lane, i1 = lane + 32;
+      double d0 = 0.0, d1 = 0.0;
+      if (i0 > j && i0 < kb) { const double l = double(L[i0][j]); d0 = dg[i0] - l * l * invd; }
+      if (i1 > j && i1 < kb) { const double l = double(L[i1][j]); d1 = dg[i1] - l * l * invd; }
+      if (i0 > j && i0 < kb) dg[i0] = d0;
+      if (i1 > j && i1 < kb) dg[i1] = d1;
+      if (j + 1 < kb) {
+        const double dn = ((j + 1) & 32) ? d1 : d0;
+        if (lane == ((j + 1) & 31)) s_inv[j + 1] = pivot_inverse(dn, flags);
+      }
+    } else {
+      const TF tinv = TF(invd);
+      for (int i = j + 1 + r; i < kb; i += 4) {
+        const TF lij = L[i][j] * tinv;
+        if (c > j && c < i) L[i][c] -= lij * L[c][j];
+        if (c <= j) Xi[i][c] -= lij * Xi[j][c];
       }
     }
     __syncthreads();
@@ -314,123 +333,40 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
   }
 }
 
-// FP32 variant of the trailing updates with 128 x 128 tiles: 256 threads, 8 x 8
-// outputs each from float4 shared-memory fragments (4 LDS.128 per 64 FMA), the
-// whole K = kb <= 64 panel in shared memory, and a read-modify-write epilogue
-// staged through shared memory so F and Y are updated with coalesced accesses.
+// FP32 trailing updates on the tensor cores.  Task (front, kind | chunks, i0,
+// j0) updates a 128 x 128 tile with the rank-K product of the factor columns
+// [k0, k0 + K), K = 64 x chunks <= kSuper:
+//   TRAIL  F[i, j] -= sum_l L[i, l] d_l L[j, l]    (lower part, r >= c)
+//   RUPD   Y[i, c] -= sum_l L[i, l] Y[l, c]         (c < k0 + K)
+// A task whose K range ends before the end of its superpanel (kSuper
+// columns) is an eager one: it updates only the columns (TRAIL) or rows
+// (RUPD) that are still inside the superpanel.  The superpanel's last panel
+// step then applies the whole superpanel at once (K up to kSuper) to the
+// rest of the front, so the trailing matrix is read and written once per
+// kSuper pivots instead of once per 64.
+//
+// Warp-level m16n8k8 TF32 MMAs with a 3xTF32 split (a = a_hi + a_lo,
+// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) keep ~FP32 accuracy.  8 warps as
+// 2 (rows) x 4 (columns), each 64 x 32 outputs = 4 x 4 MMA tiles.  K streams
+// through a 3-stage cp.async pipeline of 32-wide chunks; the epilogue stages
+// the C tile through shared memory so F and Y are read and written coalesced.
 constexpr int kT128 = 128;
-constexpr int kLd128 = 132;  // padded row (16-byte aligned) of the k-major tiles
+constexpr int kKc = 32;                            // K chunk per pipeline stage
+constexpr int kLdMma = 136;                        // row stride: fragment loads hit 32 distinct banks
+constexpr int kStages = 3;
+constexpr int kStageFloats = 2 * kKc * kLdMma;     // A and B chunk
+constexpr size_t kUpdateSmem = size_t(kStages) * kStageFloats * sizeof(float);
+static_assert(kUpdateSmem >= size_t(kT128) * 129 * sizeof(float), "epilogue tile must fit the stages");
 
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool valid) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   const int sz = valid ? 4 : 0;  // 0: nothing is read, the 4 bytes are zero-filled
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-__global__ void __launch_bounds__(256) front_update128_kernel(const int32_t *__restrict__ tasks,
-                                                              const DFront *__restrict__ fronts,
-                                                              float *__restrict__ F, float *__restrict__ Y,
-                                                              const double *__restrict__ D) {
-  extern __shared__ __align__(16) float usm128[];
-  float *As = usm128;                 // [64][kLd128]: As[l][i] = L[i0 + i, k0 + l]
-  float *Bs = usm128 + 64 * kLd128;   // [64][kLd128]: Bs[l][j]
-  float *Cs = usm128;                 // epilogue [128][129] (column j, row i), reuses As/Bs
-  __shared__ float Ds[64];
-  const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
-  const DFront fr = fronts[t.x];
-  const int kind = t.y >> 24;
-  const int32_t k0 = t.y & 0xffffff, i0 = t.z, j0 = t.w, m = fr.m;
-  const int32_t kb = (fr.npiv - k0) < 64 ? (fr.npiv - k0) : 64;
-  float *Ff = F + fr.f_off;
-  float *Yf = Y + fr.y_off;
-  // operand tiles: asynchronous copies, all in flight together
-  for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
-    const int l = idx / kT128, i = idx % kT128;
-    const int32_t r = i0 + i;
-    const bool ok = r < m && l < kb;
-    cp_async4(As + l * kLd128 + i, ok ? Ff + r + int64_t(k0 + l) * m : Ff, ok);
-  }
-  if (kind == T_TRAIL) {
-    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
-      const int l = idx / kT128, j = idx % kT128;
-      const int32_t r = j0 + j;
-      const bool ok = r < m && l < kb;
-      cp_async4(Bs + l * kLd128 + j, ok ? Ff + r + int64_t(k0 + l) * m : Ff, ok);
-    }
-    if (threadIdx.x < 64) Ds[threadIdx.x] = threadIdx.x < kb ? float(D[fr.first + k0 + threadIdx.x]) : 0.f;
-  } else {
-    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
-      const int l = idx % 64, j = idx / 64;
-      const int32_t c = j0 + j;
-      const bool ok = l < kb && c < k0 + kb;
-      cp_async4(Bs + l * kLd128 + j, ok ? Yf + (k0 + l) + int64_t(c) * fr.ldy : Yf, ok);
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  if (kind == T_TRAIL) {  // B <- B diag(D)
-    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) Bs[(idx / kT128) * kLd128 + idx % kT128] *= Ds[idx / kT128];
-    __syncthreads();
-  }
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  float acc[8][8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
-#pragma unroll 4
-  for (int l = 0; l < kb; ++l) {
-    const float4 a0 = *reinterpret_cast<const float4 *>(As + l * kLd128 + ty * 4);
-    const float4 a1 = *reinterpret_cast<const float4 *>(As + l * kLd128 + ty * 4 + 64);
-    const float4 b0 = *reinterpret_cast<const float4 *>(Bs + l * kLd128 + tx * 4);
-    const float4 b1 = *reinterpret_cast<const float4 *>(Bs + l * kLd128 + tx * 4 + 64);
-    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-      for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
-  }
-  __syncthreads();
-  // epilogue: fetch the C tile asynchronously, subtract in shared memory,
-  // write back coalesced (TRAIL: lower part only; RUPD: Y)
-  const bool trail = kind == T_TRAIL;
-  const int32_t cmax = trail ? m : k0 + kb;
-  for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
-    const int j = idx / kT128, i = idx % kT128;
-    const int32_t r = i0 + i, c = j0 + j;
-    const bool ok = r < m && c < cmax;
-    const float *src = trail ? Ff + r + int64_t(c) * m : Yf + r + int64_t(c) * fr.ldy;
-    cp_async4(Cs + j * 129 + i, ok ? src : Ff, ok);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int i = ty * 4 + (r & 3) + (r >> 2) * 64;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) Cs[(tx * 4 + (c & 3) + (c >> 2) * 64) * 129 + i] -= acc[r][c];
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
-    const int j = idx / kT128, i = idx % kT128;
-    const int32_t r = i0 + i, c = j0 + j;
-    if (r >= m || c >= cmax) continue;
-    if (trail) {
-      if (r >= c) Ff[r + int64_t(c) * m] = Cs[j * 129 + i];
-    } else {
-      Yf[r + int64_t(c) * fr.ldy] = Cs[j * 129 + i];
-    }
-  }
-}
-
-// Tensor-core variant of the FP32 trailing updates: warp-level m16n8k8 TF32
-// MMAs with a 3xTF32 split (a = a_hi + a_lo, a*b ~ a_hi b_hi + a_hi b_lo +
-// a_lo b_hi) so products keep ~FP32 accuracy.  Same tiles, loads and
-// epilogue as front_update128_kernel; 8 warps as 2 (rows) x 4 (columns),
-// each warp 64 x 32 outputs = 4 x 4 MMA tiles.
-constexpr int kLdMma = 136;  // row stride: fragment loads hit 32 distinct banks
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
@@ -451,54 +387,61 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__global__ void __launch_bounds__(256) front_update_mma_kernel(const int32_t *__restrict__ tasks,
-                                                               const DFront *__restrict__ fronts,
-                                                               float *__restrict__ F, float *__restrict__ Y,
-                                                               const double *__restrict__ D) {
+__global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *__restrict__ tasks,
+                                                                 const DFront *__restrict__ fronts,
+                                                                 float *__restrict__ F, float *__restrict__ Y,
+                                                                 const double *__restrict__ D) {
   extern __shared__ __align__(16) float umm[];
-  float *As = umm;                  // [64][kLdMma]: As[l][i] = L[i0 + i, k0 + l]
-  float *Bs = umm + 64 * kLdMma;    // [64][kLdMma]: Bs[l][j]
-  float *Cs = umm;                  // epilogue [128][129] (column j, row i)
-  __shared__ float Ds[64];
+  float *Cs = umm;  // epilogue [128][129] (column j, row i), reuses the stages
+  __shared__ float Ds[kSuper];
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
-  const int kind = t.y >> 24;
-  const int32_t k0 = t.y & 0xffffff, i0 = t.z, j0 = t.w, m = fr.m;
-  const int32_t kb = (fr.npiv - k0) < 64 ? (fr.npiv - k0) : 64;
+  const int kind = (t.y >> 24) & 7;
+  const int chunks = ((t.y >> 27) & 3) + 1;
+  const int32_t k0 = t.y & 0xffffff, i0 = t.z, j0 = t.w, m = fr.m, p = fr.npiv;
+  const int32_t kend = min(k0 + 64 * chunks, p);
+  const int32_t kw = kend - k0;
+  const int32_t s_end = min((k0 / kSuper + 1) * kSuper, p);
+  const bool eager = kend < s_end;
+  const bool trail = kind == T_TRAIL;
   float *Ff = F + fr.f_off;
   float *Yf = Y + fr.y_off;
-  for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
-    const int l = idx / kT128, i = idx % kT128;
-    const int32_t r = i0 + i;
-    const bool ok = r < m && l < kb;
-    cp_async4(As + l * kLdMma + i, ok ? Ff + r + int64_t(k0 + l) * m : Ff, ok);
-  }
-  if (kind == T_TRAIL) {
-    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
-      const int l = idx / kT128, j = idx % kT128;
-      const int32_t r = j0 + j;
-      const bool ok = r < m && l < kb;
-      cp_async4(Bs + l * kLdMma + j, ok ? Ff + r + int64_t(k0 + l) * m : Ff, ok);
+  for (int l = threadIdx.x; l < kSuper; l += 256) Ds[l] = (trail && l < kw) ? float(D[fr.first + k0 + l]) : 1.f;
+  const int nchunk = (kw + kKc - 1) / kKc;
+  auto load_chunk = [&](int q) {
+    float *As = umm + (q % kStages) * kStageFloats;  // As[l][i] = L[i0 + i, k0 + kKc q + l]
+    float *Bs = As + kKc * kLdMma;                    // Bs[l][j]
+    const int32_t kq = k0 + kKc * q;
+    for (int idx = threadIdx.x; idx < kKc * kT128; idx += 256) {
+      const int l = idx / kT128, i = idx % kT128;
+      const int32_t r = i0 + i;
+      const bool ok = r < m && kq + l < kend;
+      cp_async4(As + l * kLdMma + i, ok ? Ff + r + int64_t(kq + l) * m : Ff, ok);
     }
-    if (threadIdx.x < 64) Ds[threadIdx.x] = threadIdx.x < kb ? float(D[fr.first + k0 + threadIdx.x]) : 0.f;
-  } else {
-    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256) {
-      const int l = idx % 64, j = idx / 64;
-      const int32_t c = j0 + j;
-      const bool ok = l < kb && c < k0 + kb;
-      cp_async4(Bs + l * kLdMma + j, ok ? Yf + (k0 + l) + int64_t(c) * fr.ldy : Yf, ok);
+    if (trail) {
+      for (int idx = threadIdx.x; idx < kKc * kT128; idx += 256) {
+        const int l = idx / kT128, j = idx % kT128;
+        const int32_t r = j0 + j;
+        const bool ok = r < m && kq + l < kend;
+        cp_async4(Bs + l * kLdMma + j, ok ? Ff + r + int64_t(kq + l) * m : Ff, ok);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < kKc * kT128; idx += 256) {
+        const int l = idx % kKc, j = idx / kKc;
+        const int32_t c = j0 + j;
+        const bool ok = kq + l < kend && c < kend;
+        cp_async4(Bs + l * kLdMma + j, ok ? Yf + (kq + l) + int64_t(c) * fr.ldy : Yf, ok);
+      }
     }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  if (kind == T_TRAIL) {
-    for (int idx = threadIdx.x; idx < 64 * kT128; idx += 256)
-      Bs[(idx / kT128) * kLdMma + idx % kT128] *= Ds[idx / kT128];
-    __syncthreads();
+  };
+#pragma unroll
+  for (int q = 0; q < kStages - 1; ++q) {
+    if (q < nchunk) load_chunk(q);
+    cp_async_commit();
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tq = lane & 3;
-  const int wm = warp & 1, wn = warp >> 1;      // 2 x 4 warps
+  const int wm = warp & 1, wn = warp >> 1;
   float acc[4][4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -506,40 +449,52 @@ __global__ void __launch_bounds__(256) front_update_mma_kernel(const int32_t *__
     for (int b = 0; b < 4; ++b)
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[a][b][v] = 0.f;
-  const int ksteps = (kb + 7) / 8;  // zero-filled beyond kb
-  for (int ks = 0; ks < ksteps; ++ks) {
-    const int kk = 8 * ks;
-    uint32_t ah[4][4], al[4][4], bh[4][2], bl[4][2];
+  for (int q = 0; q < nchunk; ++q) {
+    cp_async_wait<kStages - 2>();  // chunk q has landed
+    __syncthreads();               // ... for every thread; stage (q - 1) % kStages is free
+    if (q + kStages - 1 < nchunk) load_chunk(q + kStages - 1);
+    cp_async_commit();
+    const float *As = umm + (q % kStages) * kStageFloats;
+    const float *Bs = As + kKc * kLdMma;
+    const float *Dq = Ds + kKc * q;
 #pragma unroll
-    for (int mt = 0; mt < 4; ++mt) {
-      const int mrow = wm * 64 + mt * 16 + g;
-      split_tf32(As[(kk + tq) * kLdMma + mrow], ah[mt][0], al[mt][0]);
-      split_tf32(As[(kk + tq) * kLdMma + mrow + 8], ah[mt][1], al[mt][1]);
-      split_tf32(As[(kk + tq + 4) * kLdMma + mrow], ah[mt][2], al[mt][2]);
-      split_tf32(As[(kk + tq + 4) * kLdMma + mrow + 8], ah[mt][3], al[mt][3]);
-    }
+    for (int kk = 0; kk < kKc; kk += 8) {
+      uint32_t ah[4][4], al[4][4], bh[4][2], bl[4][2];
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      const int ncol = wn * 32 + nt * 8 + g;
-      split_tf32(Bs[(kk + tq) * kLdMma + ncol], bh[nt][0], bl[nt][0]);
-      split_tf32(Bs[(kk + tq + 4) * kLdMma + ncol], bh[nt][1], bl[nt][1]);
-    }
-#pragma unroll
-    for (int mt = 0; mt < 4; ++mt)
+      for (int mt = 0; mt < 4; ++mt) {
+        const int mrow = wm * 64 + mt * 16 + g;
+        split_tf32(As[(kk + tq) * kLdMma + mrow], ah[mt][0], al[mt][0]);
+        split_tf32(As[(kk + tq) * kLdMma + mrow + 8], ah[mt][1], al[mt][1]);
+        split_tf32(As[(kk + tq + 4) * kLdMma + mrow], ah[mt][2], al[mt][2]);
+        split_tf32(As[(kk + tq + 4) * kLdMma + mrow + 8], ah[mt][3], al[mt][3]);
+      }
+      const float d0 = Dq[kk + tq], d1 = Dq[kk + tq + 4];
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
-        mma_tf32(acc[mt][nt], al[mt], bh[nt]);
-        mma_tf32(acc[mt][nt], ah[mt], bl[nt]);
-        mma_tf32(acc[mt][nt], ah[mt], bh[nt]);
+        const int ncol = wn * 32 + nt * 8 + g;
+        split_tf32(Bs[(kk + tq) * kLdMma + ncol] * d0, bh[nt][0], bl[nt][0]);
+        split_tf32(Bs[(kk + tq + 4) * kLdMma + ncol] * d1, bh[nt][1], bl[nt][1]);
       }
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          mma_tf32(acc[mt][nt], al[mt], bh[nt]);
+          mma_tf32(acc[mt][nt], ah[mt], bl[nt]);
+          mma_tf32(acc[mt][nt], ah[mt], bh[nt]);
+        }
+    }
   }
+  cp_async_wait_all();
   __syncthreads();
-  const bool trail = kind == T_TRAIL;
-  const int32_t cmax = trail ? m : k0 + kb;
+  // epilogue: TRAIL writes the lower part of columns < cmax (the superpanel's
+  // end for an eager task), RUPD rows < rmax of columns < kend
+  const int32_t cmax = trail ? (eager ? s_end : m) : kend;
+  const int32_t rmax = (!trail && eager) ? s_end : m;
   for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
     const int j = idx / kT128, i = idx % kT128;
     const int32_t r = i0 + i, c = j0 + j;
-    const bool ok = r < m && c < cmax;
+    const bool ok = r < rmax && c < cmax;
     const float *src = trail ? Ff + r + int64_t(c) * m : Yf + r + int64_t(c) * fr.ldy;
     cp_async4(Cs + j * 129 + i, ok ? src : Ff, ok);
   }
@@ -559,7 +514,7 @@ __global__ void __launch_bounds__(256) front_update_mma_kernel(const int32_t *__
   for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
     const int j = idx / kT128, i = idx % kT128;
     const int32_t r = i0 + i, c = j0 + j;
-    if (r >= m || c >= cmax) continue;
+    if (r >= rmax || c >= cmax) continue;
     if (trail) {
       if (r >= c) Ff[r + int64_t(c) * m] = Cs[j * 129 + i];
     } else {
@@ -730,10 +685,7 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
   cudaFuncSetAttribute(front_diag_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dsm));
   cudaFuncSetAttribute(front_panel_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
   cudaFuncSetAttribute(front_update_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
-  const size_t t128 = 2 * 64 * kLd128 * sizeof(float);
-  cudaFuncSetAttribute(front_update128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t128));
-  const size_t tmma = 2 * 64 * kLdMma * sizeof(float);
-  cudaFuncSetAttribute(front_update_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tmma));
+  cudaFuncSetAttribute(front_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kUpdateSmem));
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
     if (L.asm_n) d->launches++;
@@ -744,7 +696,7 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
     for (size_t st = 0; st < L.diag_n.size(); ++st) {
       d->launches += (L.diag_n[st] > 0) + (L.panel_n[st] > 0) + (L.trail_n[st] > 0);
       if (L.diag_n[st])
-        front_diag_kernel<TF><<<unsigned(L.diag_n[st]), 256, dsm, s>>>(d->tasks + L.diag_off[st], d->fronts, F, Y,
+        front_diag_kernel<TF><<<unsigned(L.diag_n[st]), kDiagThreads, dsm, s>>>(d->tasks + L.diag_off[st], d->fronts, F, Y,
                                                                        d->D[buf], d->D[buf] + c->n_free, d->flags);
       if (L.panel_n[st])
         front_panel_kernel<TF><<<unsigned(L.panel_n[st]), 256, tsm, s>>>(d->tasks + L.panel_off[st], d->fronts, F, Y,
@@ -753,8 +705,8 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
         const int ev = stage_begin(c, FE_STAGE_FACTOR_UPDATE, s);
         if (ev >= 0) d->update_flops += L.trail_flops[st];
         if constexpr (sizeof(TF) == 4)
-          front_update_mma_kernel<<<unsigned(L.trail_n[st]), 256, tmma, s>>>(d->tasks + L.trail_off[st], d->fronts,
-                                                                            F, Y, d->D[buf]);
+          front_update_tc_kernel<<<unsigned(L.trail_n[st]), 256, kUpdateSmem, s>>>(d->tasks + L.trail_off[st],
+                                                                                   d->fronts, F, Y, d->D[buf]);
         else
           front_update_kernel<TF><<<unsigned(L.trail_n[st]), 256, tsm, s>>>(d->tasks + L.trail_off[st], d->fronts, F,
                                                                           Y, d->D[buf]);

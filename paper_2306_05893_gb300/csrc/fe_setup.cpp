@@ -532,6 +532,7 @@ int build_ordering(fe_ctx *c) {
   double flops = 0;
   // trailing-update tile: 128 x 128 for the FP32 factor, 64 x 64 for FP64
   const int32_t ut = c->opt.precision == FE_MIXED ? 128 : kTile;
+  const int32_t sp = c->opt.precision == FE_MIXED ? kSuper : kNB;
   const int32_t fr_rows = fwd_rows(c->opt.precision);
   for (auto &L : c->levels) {
     int steps = 0;
@@ -559,11 +560,25 @@ int build_ordering(fe_ctx *c) {
         push(L.diag[s], f, (T_DIAG << 24) | k0, kb, 0);
         for (int32_t r0 = k1; r0 < m; r0 += kTile) push(L.panel[s], f, (T_PANEL << 24) | k0, r0, 0);
         for (int32_t c0 = 0; c0 < k0; c0 += kTile) push(L.panel[s], f, (T_XK << 24) | k0, c0, 0);
-        for (int32_t j0 = k1; j0 < m; j0 += ut)
+        // trailing and Y updates: eager inside the superpanel [s0, s1), the
+        // rest of the front once per superpanel with K = s1 - s0 (FP32 path)
+        const int32_t s0 = k0 / sp * sp, s1 = std::min(s0 + sp, p);
+        for (int32_t j0 = k1; j0 < s1; j0 += ut)
           for (int32_t i0 = j0; i0 < m; i0 += ut) push(L.trail[s], f, (T_TRAIL << 24) | k0, i0, j0);
-        for (int32_t i0 = k1; i0 < m; i0 += ut)
+        for (int32_t i0 = k1; i0 < s1; i0 += ut)
           for (int32_t c0 = 0; c0 < k1; c0 += ut) push(L.trail[s], f, (T_RUPD << 24) | k0, i0, c0);
-        double rem = double(m - k1);
+        if (k1 == s1) {
+          const int32_t chunks = (s1 - s0 + kNB - 1) / kNB;
+          const int32_t code = ((T_TRAIL | ((chunks - 1) << 3)) << 24) | s0;
+          const int32_t codeu = ((T_RUPD | ((chunks - 1) << 3)) << 24) | s0;
+          for (int32_t j0 = s1; j0 < m; j0 += ut)
+            for (int32_t i0 = j0; i0 < m; i0 += ut) push(L.trail[s], f, code, i0, j0);
+          for (int32_t i0 = s1; i0 < m; i0 += ut)
+            for (int32_t c0 = 0; c0 < s1; c0 += ut) push(L.trail[s], f, codeu, i0, c0);
+        }
+        // algorithmic flops of this panel's updates (the zero products of the
+        // superpanel's upper triangle in Y are not counted)
+        const double rem = double(m - k1);
         L.trail_flops[s] += rem * (rem + 1.0) * kb + 2.0 * rem * double(k1) * kb;
         flops += double(kb) * kb * kb / 3.0 * 2.0            // diag LDL^T + inverse
                  + 2.0 * rem * kb * kb                        // panel
