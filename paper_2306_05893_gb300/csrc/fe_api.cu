@@ -251,9 +251,9 @@ int ensure_device(fe_ctx *c) {
       all.insert(all.end(), L.trail[s].begin(), L.trail[s].end());
     }
     pad4();
-    T.fwd_off = int64_t(all.size()); T.fwd_n = int64_t(L.fwd_tasks.size() / 2);
+    T.fwd_off = int64_t(all.size()); T.fwd_n = int64_t(L.fwd_tasks.size() / 4);
     all.insert(all.end(), L.fwd_tasks.begin(), L.fwd_tasks.end());
-    T.bwd_off = int64_t(all.size()); T.bwd_n = int64_t(L.bwd_tasks.size() / 2);
+    T.bwd_off = int64_t(all.size()); T.bwd_n = int64_t(L.bwd_tasks.size() / 4);
     all.insert(all.end(), L.bwd_tasks.begin(), L.bwd_tasks.end());
   }
   FE_TRY(upload(c, d, &d->tasks, all));
@@ -266,6 +266,13 @@ int ensure_device(fe_ctx *c) {
   FE_TRY(dallocv(c, d, &d->wbuf, size_t(c->w_total) * ts));
   FE_TRY(dallocv(c, d, &d->ubuf, size_t(std::max<int64_t>(c->u_total, 1)) * ts));
   FE_TRY(dallocv(c, d, &d->yperm, size_t(std::max<int64_t>(c->n_free, 1)) * ts));
+  const size_t rb = mixed(c) ? 128 : 64;
+  FE_TRY(dallocv(c, d, &d->part_f, size_t(std::max<int64_t>(c->fwd_slots, 1)) * rb * ts));
+  FE_TRY(dallocv(c, d, &d->part_b, size_t(std::max<int64_t>(c->bwd_slots, 1)) * kBwdCols * ts));
+  FE_TRY(dalloc(c, d, &d->tick_f, size_t(std::max<int64_t>(c->fwd_slots, 1))));
+  FE_TRY(dalloc(c, d, &d->tick_b, size_t(std::max<int64_t>(c->bwd_slots, 1))));
+  FE_CUDA_TRY(cudaMemset(d->tick_f, 0, size_t(std::max<int64_t>(c->fwd_slots, 1)) * sizeof(int)));
+  FE_CUDA_TRY(cudaMemset(d->tick_b, 0, size_t(std::max<int64_t>(c->bwd_slots, 1)) * sizeof(int)));
   FE_CUDA_TRY(cudaDeviceSynchronize());
   return FE_OK;
 }

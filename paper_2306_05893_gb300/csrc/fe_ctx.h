@@ -14,6 +14,8 @@ constexpr int kNB = 64;        // panel width of the front factorisation
 constexpr int kTile = 64;      // tile edge of the front update kernels
 constexpr int kSuper = 256;    // FP32 factor: trailing updates are applied once per kSuper pivots
 constexpr int kBwdCols = 32;   // pivot columns per task of the backward apply
+constexpr int kFwdCols = 256;  // pivot columns per task of the forward apply (split over CTAs)
+constexpr int kBwdRows = 1024; // rows per task of the backward apply (split over CTAs)
 inline int fwd_rows(int precision) { return precision == FE_MIXED ? 128 : 64; }  // 32 threads x one 16-byte vector
 
 // Task kinds of the multifrontal factorisation (packed in int4.y >> 24).
@@ -43,8 +45,10 @@ struct Level {
   std::vector<std::vector<int32_t>> diag, panel, trail;  // int4 per task
   std::vector<double> trail_flops;    // algorithmic flops of each step's update launch
   // apply task lists
-  std::vector<int32_t> fwd_tasks;     // (front, r0) pairs, kFwdRows-row blocks
-  std::vector<int32_t> bwd_tasks;     // (front, c0) pairs, kBwdCols-column blocks
+  // (front, r0, j0, slot): rows [r0, r0 + fwd_rows) x pivot columns [j0, j0 + kFwdCols)
+  std::vector<int32_t> fwd_tasks;
+  // (front, c0, i0, slot): pivot columns [c0, c0 + kBwdCols) x rows [i0, i0 + kBwdRows)
+  std::vector<int32_t> bwd_tasks;
 };
 
 struct DeviceState;  // defined in the CUDA translation unit
@@ -105,6 +109,8 @@ struct fe_ctx {
   std::vector<int64_t> fa_colptr;     // per front: per local column start into fa_*
   std::vector<fe::Level> levels;
   int64_t f_total = 0, y_total = 0, w_total = 0, u_total = 0;
+  // partial-sum slots of the split apply tasks (slot = -1: a block done by one task)
+  int64_t fwd_slots = 0, bwd_slots = 0;
   double factor_flops = 0;
   int64_t y_nnz = 0;
 

@@ -96,6 +96,8 @@ struct DeviceState {
   void *Y[2] = {nullptr, nullptr}; // apply operators (double-buffered for the lag)
   double *D[2] = {nullptr, nullptr};
   void *wbuf = nullptr, *ubuf = nullptr, *yperm = nullptr;  // apply work vectors
+  void *part_f = nullptr, *part_b = nullptr;                // partial sums of split apply tasks
+  int *tick_f = nullptr, *tick_b = nullptr;                 // their tickets (zero between launches)
   int cur = 0;                     // buffer the solver reads
   int factor_pending = -1;         // buffer being written on fstream, or -1
   int64_t pending_step = -1;       // step whose A the pending factor holds

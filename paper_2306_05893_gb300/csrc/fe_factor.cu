@@ -538,34 +538,58 @@ struct Vec16<double> {
   static constexpr int n = 2;
 };
 
-// Forward level, task (front, r0): rows [r0, r0 + 32*VW) of Y w_P, where
-// w = [r_P; 0] + the children's update vectors (gathered on the fly through
-// the position lists, children in fixed order).  256 threads: 32 row lanes
-// of VW consecutive rows (one 16-byte load per column) x 8 column groups.
-// Rows < p give y_P (times D^{-1}) into yperm, rows >= p the update vector.
+// Deterministic combination of a block split over several CTAs: each CTA
+// stores its partial sums, and the last of the block's CTAs to arrive (a
+// ticket per block) adds the partials in chunk order, so the result does not
+// depend on which CTA finishes last.  Returns true in that last CTA, whose
+// ticket is reset for the next application.
+__device__ __forceinline__ bool last_of_block(int *ticket, int nch) {
+  __shared__ int s_last;
+  __threadfence();  // this thread's partials are visible device-wide ...
+  __syncthreads();  // ... for every thread of the CTA, before the ticket
+  if (threadIdx.x == 0) {
+    const int t = atomicAdd(ticket, 1);
+    s_last = (t == nch - 1);
+    if (s_last) *ticket = 0;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+// Forward level, task (front, r0, j0, slot): rows [r0, r0 + 32*VW) of Y w_P
+// over the pivot columns [j0, j0 + kFwdCols), where w = [r_P; 0] + the
+// children's update vectors (gathered on the fly through the position lists,
+// children in fixed order).  256 threads: 32 row lanes of VW consecutive rows
+// (one 16-byte load per column) x 8 column groups.  Rows < p give y_P (times
+// D^{-1}) into yperm, rows >= p the update vector.  Row blocks with more
+// than kFwdCols columns are split over CTAs (slot >= 0) so the few large
+// fronts near the root still stream Y with the whole GPU.
 template <typename TF, typename TV>
-__global__ void __launch_bounds__(256) fwd_kernel(const int32_t *__restrict__ tasks,
+__global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
                                                   const double *__restrict__ Dinv,
                                                   const int32_t *__restrict__ perm,
                                                   const int32_t *__restrict__ wsrc_ptr,
                                                   const int32_t *__restrict__ wsrc, const TV *__restrict__ r,
-                                                  TV *__restrict__ ubuf, TV *__restrict__ yperm) {
+                                                  TV *__restrict__ ubuf, TV *__restrict__ yperm,
+                                                  TV *__restrict__ part, int *__restrict__ tickets) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int RB = 32 * VW;
-  extern __shared__ __align__(16) unsigned char fsm[];
-  TV *part = reinterpret_cast<TV *>(fsm);      // [8][RB]
-  TV *wp = part + 8 * RB;                       // [jmax]
-  const DFront fr = fronts[tasks[2 * blockIdx.x]];
-  const int32_t r0 = tasks[2 * blockIdx.x + 1];
+  __shared__ TV gpart[8 * RB];
+  __shared__ TV wp[kFwdCols];
+  const int4 t = tasks[blockIdx.x];
+  const DFront fr = fronts[t.x];
+  const int32_t r0 = t.y, j0 = t.z, slot = t.w;
   const int32_t p = fr.npiv, m = fr.m;
   const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
-  for (int32_t j = threadIdx.x; j < jmax; j += 256) {
+  const int32_t j1 = (j0 + kFwdCols < jmax) ? j0 + kFwdCols : jmax;
+  for (int32_t j = j0 + threadIdx.x; j < j1; j += 256) {
     const int64_t q0 = wsrc_ptr[fr.w_off + j], q1 = wsrc_ptr[fr.w_off + j + 1];
     TV w = r[perm[fr.first + j]];
     for (int64_t q = q0; q < q1; ++q) w += ubuf[wsrc[q]];
-    wp[j] = w;
+    wp[j - j0] = w;
   }
   __syncthreads();
   const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
@@ -575,94 +599,126 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int32_t *__restrict__ ta
   for (int e = 0; e < VW; ++e) acc[e] = TV(0);
   if (row < m) {
     const TF *yc = Y + fr.y_off + row;
-    int32_t j = g;
-    for (; j + 24 < jmax; j += 32) {
+    int32_t j = j0 + g;
+    for (; j + 24 < j1; j += 32) {
       V v0 = *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy);
       V v1 = *reinterpret_cast<const V *>(yc + int64_t(j + 8) * fr.ldy);
       V v2 = *reinterpret_cast<const V *>(yc + int64_t(j + 16) * fr.ldy);
       V v3 = *reinterpret_cast<const V *>(yc + int64_t(j + 24) * fr.ldy);
       const TF *e0 = reinterpret_cast<const TF *>(&v0), *e1 = reinterpret_cast<const TF *>(&v1);
       const TF *e2 = reinterpret_cast<const TF *>(&v2), *e3 = reinterpret_cast<const TF *>(&v3);
-      const TV w0 = wp[j], w1 = wp[j + 8], w2 = wp[j + 16], w3 = wp[j + 24];
+      const TV w0 = wp[j - j0], w1 = wp[j + 8 - j0], w2 = wp[j + 16 - j0], w3 = wp[j + 24 - j0];
 #pragma unroll
       for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0 + TV(e1[e]) * w1 + TV(e2[e]) * w2 + TV(e3[e]) * w3;
     }
-    for (; j < jmax; j += 8) {
+    for (; j < j1; j += 8) {
       V v0 = *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy);
       const TF *e0 = reinterpret_cast<const TF *>(&v0);
-      const TV w0 = wp[j];
+      const TV w0 = wp[j - j0];
 #pragma unroll
       for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0;
     }
   }
 #pragma unroll
-  for (int e = 0; e < VW; ++e) part[g * RB + VW * rl + e] = acc[e];
+  for (int e = 0; e < VW; ++e) gpart[g * RB + VW * rl + e] = acc[e];
   __syncthreads();
-  for (int t = threadIdx.x; t < RB; t += 256) {
-    const int32_t i = r0 + t;
-    if (i >= m) continue;
-    TV s = TV(0);
+  TV sums[(RB + 255) / 256];
 #pragma unroll
-    for (int gg = 0; gg < 8; ++gg) s += part[gg * RB + t];
+  for (int k = 0; k < (RB + 255) / 256; ++k) {
+    const int tt = threadIdx.x + 256 * k;
+    TV sm = TV(0);
+    if (tt < RB) {
+#pragma unroll
+      for (int gg = 0; gg < 8; ++gg) sm += gpart[gg * RB + tt];
+    }
+    sums[k] = sm;
+  }
+  if (slot >= 0) {
+    const int nch = (jmax + kFwdCols - 1) / kFwdCols;
+#pragma unroll
+    for (int k = 0; k < (RB + 255) / 256; ++k) {
+      const int tt = threadIdx.x + 256 * k;
+      if (tt < RB) part[int64_t(slot + j0 / kFwdCols) * RB + tt] = sums[k];
+    }
+    if (!last_of_block(tickets + slot, nch)) return;
+#pragma unroll
+    for (int k = 0; k < (RB + 255) / 256; ++k) {
+      const int tt = threadIdx.x + 256 * k;
+      TV sm = TV(0);
+      if (tt < RB)
+        for (int ch = 0; ch < nch; ++ch) sm += __ldcg(part + int64_t(slot + ch) * RB + tt);
+      sums[k] = sm;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < (RB + 255) / 256; ++k) {
+    const int tt = threadIdx.x + 256 * k;
+    const int32_t i = r0 + tt;
+    if (tt >= RB || i >= m) continue;
     if (i < p) {
-      yperm[fr.first + i] = TV(double(s) * Dinv[fr.first + i]);
+      yperm[fr.first + i] = TV(double(sums[k]) * Dinv[fr.first + i]);
     } else {
       TV w = TV(0);
       for (int64_t q = wsrc_ptr[fr.w_off + i]; q < wsrc_ptr[fr.w_off + i + 1]; ++q) w += ubuf[wsrc[q]];
-      ubuf[fr.u_off + i - p] = w + s;
+      ubuf[fr.u_off + i - p] = w + sums[k];
     }
   }
 }
 
-// Backward level, task (front, c0): pivot columns [c0, c0 + 32); warp w owns
-// columns c0 + w + 8k (k = 0..3) and streams them together (four 16-byte
-// loads in flight per lane).  x = [D^{-1} y_P; z_U] is staged in shared
-// memory from the VW-aligned row at or below c0; rows above a column are
-// zeros of L^{-1}, so reading from the aligned row is exact.
+// Backward level, task (front, c0, i0, slot): pivot columns [c0, c0 + 32)
+// over the rows [i0, i0 + kBwdRows); warp w owns columns c0 + w + 8k
+// (k = 0..3) and streams them together (four 16-byte loads in flight per
+// lane).  x = [D^{-1} y_P; z_U] is staged in shared memory from the
+// VW-aligned row at or below c0; rows above a column are zeros of L^{-1}, so
+// reading from the aligned row is exact.  Columns longer than kBwdRows rows
+// are split over CTAs (slot >= 0) and combined in row-chunk order.
 template <typename TF, typename TV>
-__global__ void __launch_bounds__(256) bwd_kernel(const int32_t *__restrict__ tasks,
+__global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
                                                   const int32_t *__restrict__ perm,
                                                   const int32_t *__restrict__ upd_rows_old,
-                                                  const TV *__restrict__ yperm, TV *__restrict__ z) {
+                                                  const TV *__restrict__ yperm, TV *__restrict__ z,
+                                                  TV *__restrict__ part, int *__restrict__ tickets) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
-  extern __shared__ __align__(16) unsigned char bsm[];
-  TV *xs = reinterpret_cast<TV *>(bsm);
-  const DFront fr = fronts[tasks[2 * blockIdx.x]];
-  const int32_t c0 = tasks[2 * blockIdx.x + 1];
+  __shared__ __align__(16) TV xs[kBwdRows];
+  const int4 t = tasks[blockIdx.x];
+  const DFront fr = fronts[t.x];
+  const int32_t c0 = t.y, ilo0 = t.z, slot = t.w;
   const int32_t p = fr.npiv, m = fr.m;
   const int32_t a0 = c0 & ~(VW - 1);
-  const int32_t nx = fr.ldy - a0;
+  const int32_t xa = a0 > ilo0 ? a0 : ilo0;                                 // first row of this task
+  const int32_t xb = (ilo0 + kBwdRows < fr.ldy) ? ilo0 + kBwdRows : fr.ldy;  // end row
   const int32_t *urows = upd_rows_old + fr.rows_off;
-  for (int32_t t = threadIdx.x; t < nx; t += 256) {
-    const int32_t i = a0 + t;
-    xs[t] = (i < c0 || i >= m) ? TV(0) : (i < p ? yperm[fr.first + i] : z[urows[i - p]]);
+  for (int32_t tt = threadIdx.x; tt < xb - xa; tt += 256) {
+    const int32_t i = xa + tt;
+    xs[tt] = (i < c0 || i >= m) ? TV(0) : (i < p ? yperm[fr.first + i] : z[urows[i - p]]);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int32_t jc[4];
   const TF *yc[4];
-  int32_t i0[4];
+  int32_t ist[4];
   TV acc[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     jc[k] = c0 + w + 8 * k;
     const int32_t j = jc[k] < p ? jc[k] : c0;  // out-of-range columns read a valid one, result dropped
     yc[k] = Y + fr.y_off + int64_t(j) * fr.ldy;
-    i0[k] = (j & ~(VW - 1)) + VW * lane;
+    const int32_t ja = j & ~(VW - 1);
+    ist[k] = (ja > xa ? ja : xa) + VW * lane;
     acc[k] = TV(0);
   }
-  const int32_t ilo = i0[0] < i0[3] ? i0[0] : i0[3];
-  for (int32_t off = 0; ilo + off < fr.ldy; off += 32 * VW) {
+  const int32_t ilo = ist[0] < ist[3] ? ist[0] : ist[3];
+  for (int32_t off = 0; ilo + off < xb; off += 32 * VW) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int32_t i = i0[k] + off;
-      if (i < fr.ldy) {
+      const int32_t i = ist[k] + off;
+      if (i < xb) {
         V v = *reinterpret_cast<const V *>(yc[k] + i);
         const TF *e = reinterpret_cast<const TF *>(&v);
 #pragma unroll
-        for (int q = 0; q < VW; ++q) acc[k] += TV(e[q]) * xs[i - a0 + q];
+        for (int q = 0; q < VW; ++q) acc[k] += TV(e[q]) * xs[i - xa + q];
       }
     }
   }
@@ -670,7 +726,27 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int32_t *__restrict__ ta
   for (int k = 0; k < 4; ++k) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-    if (lane == 0 && jc[k] < p) z[perm[fr.first + jc[k]]] = acc[k];
+  }
+  if (slot < 0) {
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (jc[k] < p) z[perm[fr.first + jc[k]]] = acc[k];
+    }
+    return;
+  }
+  const int32_t k_first = a0 / kBwdRows;
+  const int nch = (fr.ldy - 1) / kBwdRows - k_first + 1;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) part[int64_t(slot + ilo0 / kBwdRows - k_first) * kBwdCols + w + 8 * k] = acc[k];
+  }
+  if (!last_of_block(tickets + slot, nch)) return;
+  if (threadIdx.x < kBwdCols) {
+    TV sm = TV(0);
+    for (int ch = 0; ch < nch; ++ch) sm += __ldcg(part + int64_t(slot + ch) * kBwdCols + threadIdx.x);
+    const int32_t j = c0 + threadIdx.x;
+    if (j < p) z[perm[fr.first + j]] = sm;
   }
 }
 
@@ -725,32 +801,30 @@ int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Af
 }
 
 template <typename TF, typename TV>
-static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, cudaStream_t s) {
+static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, TV *u, TV *yp,
+                              TV *part_f, TV *part_b, int *tick_f, int *tick_b, cudaStream_t s) {
   const TF *Y = reinterpret_cast<const TF *>(d->Y[buf]);
   const double *Dinv = d->D[buf] + c->n_free;
-  TV *u = reinterpret_cast<TV *>(d->ubuf);
-  TV *yp = reinterpret_cast<TV *>(d->yperm);
-  int32_t pmax = 0, lmax = 0;
-  for (const auto &f : c->fronts) {
-    pmax = std::max(pmax, f.npiv);
-    lmax = std::max(lmax, f.ldy);
-  }
-  constexpr int RB = 32 * Vec16<TF>::n;
-  const size_t fsm = size_t(8 * RB + pmax) * sizeof(TV);
-  const size_t bsm = size_t(lmax) * sizeof(TV);
-  cudaFuncSetAttribute(fwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm));
-  cudaFuncSetAttribute(bwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bsm));
   d->launches += 2 * int64_t(d->lt.size());
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
-    fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, fsm, s>>>(d->tasks + L.fwd_off, d->fronts, Y, Dinv, d->perm,
-                                                           d->wsrc_ptr, d->wsrc, r, u, yp);
+    fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, 0, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
+                                                         d->fronts, Y, Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp,
+                                                         part_f, tick_f);
   }
   for (size_t lv = d->lt.size(); lv-- > 0;) {
     const auto &L = d->lt[lv];
-    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, bsm, s>>>(d->tasks + L.bwd_off, d->fronts, Y, d->perm,
-                                                           d->upd_rows_old, yp, z);
+    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, 0, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
+                                                         d->fronts, Y, d->perm, d->upd_rows_old, yp, z, part_b,
+                                                         tick_b);
   }
+}
+
+template <typename TF, typename TV>
+static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, cudaStream_t s) {
+  apply_levels_with<TF, TV>(c, d, buf, r, z, reinterpret_cast<TV *>(d->ubuf), reinterpret_cast<TV *>(d->yperm),
+                            reinterpret_cast<TV *>(d->part_f), reinterpret_cast<TV *>(d->part_b), d->tick_f,
+                            d->tick_b, s);
 }
 
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
@@ -777,32 +851,6 @@ void *g_noalloc_base[64] = {nullptr};  // device address of the array, per devic
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
-template <typename TF, typename TV>
-void apply_levels_into(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, TV *u, TV *yp,
-                       cudaStream_t s) {
-  const TF *Y = reinterpret_cast<const TF *>(d->Y[buf]);
-  const double *Dinv = d->D[buf] + c->n_free;
-  int32_t pmax = 0, lmax = 0;
-  for (const auto &f : c->fronts) {
-    pmax = std::max(pmax, f.npiv);
-    lmax = std::max(lmax, f.ldy);
-  }
-  constexpr int RB = 32 * Vec16<TF>::n;
-  const size_t fsm = size_t(8 * RB + pmax) * sizeof(TV);
-  const size_t bsm = size_t(lmax) * sizeof(TV);
-  cudaFuncSetAttribute(fwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm));
-  cudaFuncSetAttribute(bwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bsm));
-  for (size_t lv = 0; lv < d->lt.size(); ++lv) {
-    const auto &L = d->lt[lv];
-    fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, fsm, s>>>(d->tasks + L.fwd_off, d->fronts, Y, Dinv, d->perm,
-                                                           d->wsrc_ptr, d->wsrc, r, u, yp);
-  }
-  for (size_t lv = d->lt.size(); lv-- > 0;) {
-    const auto &L = d->lt[lv];
-    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, bsm, s>>>(d->tasks + L.bwd_off, d->fronts, Y, d->perm,
-                                                           d->upd_rows_old, yp, z);
-  }
-}
 }  // namespace
 
 }  // namespace fe
@@ -821,7 +869,11 @@ extern "C" int fe_apply_preconditioner_noalloc(fe_ctx *c, const double *r, doubl
   const size_t ts = fp32 ? sizeof(float) : sizeof(double);
   const size_t b_vec = round256(size_t(c->n) * ts), b_u = round256(size_t(std::max<int64_t>(c->u_total, 1)) * ts);
   const size_t b_y = round256(size_t(std::max<int64_t>(c->n_free, 1)) * ts);
-  const size_t need = 2 * b_vec + b_u + b_y;
+  const size_t rb = fp32 ? 128 : 64;
+  const size_t b_pf = round256(size_t(std::max<int64_t>(c->fwd_slots, 1)) * rb * ts);
+  const size_t b_pb = round256(size_t(std::max<int64_t>(c->bwd_slots, 1)) * kBwdCols * ts);
+  const size_t b_t = round256(size_t(std::max<int64_t>(c->fwd_slots + c->bwd_slots, 1)) * sizeof(int));
+  const size_t need = 2 * b_vec + b_u + b_y + b_pf + b_pb + b_t;
   if (need > kNoAllocScratchBytes)
     return set_error(c, FE_ERR_ARG, "this mesh needs " + std::to_string(need) +
                                         " bytes of scratch; the allocation-free path holds " +
@@ -841,17 +893,24 @@ extern "C" int fe_apply_preconditioner_noalloc(fe_ctx *c, const double *r, doubl
   }
   unsigned char *p = static_cast<unsigned char *>(base);
   void *rT = p, *zT = p + b_vec, *ub = p + 2 * b_vec, *yp = p + 2 * b_vec + b_u;
+  void *pf = p + 2 * b_vec + b_u + b_y, *pb = p + 2 * b_vec + b_u + b_y + b_pf;
+  int *tf = reinterpret_cast<int *>(p + 2 * b_vec + b_u + b_y + b_pf + b_pb);
+  int *tb = tf + c->fwd_slots;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // z keeps the last call's values on fixed DOFs unless cleared
+  // z keeps the last call's values on fixed DOFs unless cleared; the split
+  // tasks' tickets start at zero
   cudaError_t e = cudaMemsetAsync(zT, 0, size_t(c->n) * ts, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tf, 0, b_t, s);
   if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, cudaGetErrorString(e));
   launch_convert(r, false, rT, fp32, c->n, s);
   if (fp32)
-    apply_levels_into<float, float>(c, d, d->cur, static_cast<const float *>(rT), static_cast<float *>(zT),
-                                    static_cast<float *>(ub), static_cast<float *>(yp), s);
+    apply_levels_with<float, float>(c, d, d->cur, static_cast<const float *>(rT), static_cast<float *>(zT),
+                                    static_cast<float *>(ub), static_cast<float *>(yp), static_cast<float *>(pf),
+                                    static_cast<float *>(pb), tf, tb, s);
   else
-    apply_levels_into<double, double>(c, d, d->cur, static_cast<const double *>(rT), static_cast<double *>(zT),
-                                      static_cast<double *>(ub), static_cast<double *>(yp), s);
+    apply_levels_with<double, double>(c, d, d->cur, static_cast<const double *>(rT), static_cast<double *>(zT),
+                                      static_cast<double *>(ub), static_cast<double *>(yp),
+                                      static_cast<double *>(pf), static_cast<double *>(pb), tf, tb, s);
   launch_convert(zT, fp32, z, false, c->n, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, cudaGetErrorString(e));

@@ -534,6 +534,8 @@ int build_ordering(fe_ctx *c) {
   const int32_t ut = c->opt.precision == FE_MIXED ? 128 : kTile;
   const int32_t sp = c->opt.precision == FE_MIXED ? kSuper : kNB;
   const int32_t fr_rows = fwd_rows(c->opt.precision);
+  const int32_t vw = c->opt.precision == FE_MIXED ? 4 : 2;  // rows per 16-byte vector of Y
+  c->fwd_slots = c->bwd_slots = 0;
   for (auto &L : c->levels) {
     int steps = 0;
     for (int32_t f : L.fronts) steps = std::max(steps, (c->fronts[f].npiv + kNB - 1) / kNB);
@@ -550,8 +552,28 @@ int build_ordering(fe_ctx *c) {
         L.asm_tasks.push_back(c0);
         L.asm_tasks.push_back(std::min(m, c0 + 32));
       }
-      for (int32_t r0 = 0; r0 < m; r0 += fr_rows) { L.fwd_tasks.push_back(f); L.fwd_tasks.push_back(r0); }
-      for (int32_t c0 = 0; c0 < p; c0 += kBwdCols) { L.bwd_tasks.push_back(f); L.bwd_tasks.push_back(c0); }
+      // apply tasks; a block split over several tasks owns consecutive
+      // partial-sum slots, reduced in order by the last task to finish
+      for (int32_t r0 = 0; r0 < m; r0 += fr_rows) {
+        const int32_t jmax = std::min(r0 + fr_rows, p);
+        const int32_t nch = std::max(1, (jmax + kFwdCols - 1) / kFwdCols);
+        const int32_t slot = nch > 1 ? int32_t(c->fwd_slots) : -1;
+        if (nch > 1) c->fwd_slots += nch;
+        for (int32_t k = 0; k < nch; ++k) {
+          L.fwd_tasks.push_back(f); L.fwd_tasks.push_back(r0);
+          L.fwd_tasks.push_back(k * kFwdCols); L.fwd_tasks.push_back(slot);
+        }
+      }
+      for (int32_t c0 = 0; c0 < p; c0 += kBwdCols) {
+        const int32_t a0 = c0 & ~(vw - 1);
+        const int32_t k0 = a0 / kBwdRows, k1 = (F.ldy - 1) / kBwdRows;
+        const int32_t slot = k1 > k0 ? int32_t(c->bwd_slots) : -1;
+        if (k1 > k0) c->bwd_slots += k1 - k0 + 1;
+        for (int32_t k = k0; k <= k1; ++k) {
+          L.bwd_tasks.push_back(f); L.bwd_tasks.push_back(c0);
+          L.bwd_tasks.push_back(k * kBwdRows); L.bwd_tasks.push_back(slot);
+        }
+      }
       for (int s = 0; s * kNB < p; ++s) {
         const int32_t k0 = s * kNB, kb = std::min(kNB, p - k0), k1 = k0 + kb;
         auto push = [](std::vector<int32_t> &v, int32_t a, int32_t b, int32_t cc, int32_t d) {
