@@ -73,28 +73,71 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
 }
 
 // ---------------------------------------------------------------- diagonal
-// 1/d in FP64 without an FP64 division (a long-latency operation on GB300,
-// and this one sits on the serial path of the block): FP32 reciprocal, then
-// one Newton step in FP64, x (2 - d x).  A non-positive pivot is flagged and
-// replaced by 1 so the factorisation finishes without NaNs.
+// Pivots of the FP32 factor are accumulated in double-float: a value is an
+// unevaluated sum hi + lo of two floats (~48-bit significand), updated with
+// the error-free transformations of Knuth (TwoSum) and Dekker (TwoProduct,
+// here through FMA).  GB300's FP64 pipe issues a warp instruction every ~64
+// cycles per SM sub-partition, so a pivot step's FP64 chain, which sits on
+// the block's serial path, cost more than the whole FP32 elimination step;
+// double-float keeps FP64-level pivots at FP32 latency.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF df_quick(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  DF p = df_two_prod(x.hi, y.hi);
+  p.lo = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo));
+  return df_quick(p.hi, p.lo);
+}
+__device__ __forceinline__ DF df_sub(DF x, DF y) {
+  DF s = df_two_sum(x.hi, -y.hi);
+  s.lo += x.lo - y.lo;
+  return df_quick(s.hi, s.lo);
+}
+// 1/d: the FP32 reciprocal refined by one Newton step x + x (1 - d x) with
+// the residual formed in double-float (error ~2^-46 relative).  A
+// non-positive pivot is flagged and replaced by 1 so the factorisation
+// finishes without NaNs.
+__device__ __forceinline__ DF df_pivot_inverse(DF d, int *flags) {
+  if (!(d.hi > 0.f)) {
+    atomicOr(flags, FLAG_PIVOT);
+    d = {1.f, 0.f};
+  }
+  const float x = __frcp_rn(d.hi);
+  const DF dx = df_mul(d, {x, 0.f});
+  const float r = (1.f - dx.hi) - dx.lo;
+  const DF q = df_two_prod(x, r);
+  DF out = df_quick(x, q.hi);
+  out.lo += q.lo;
+  return out;
+}
 __device__ __forceinline__ double pivot_inverse(double d, int *flags) {
   if (!(d > 0.0)) {
     atomicOr(flags, FLAG_PIVOT);
     d = 1.0;
   }
-  if (d < 1e-30 || d > 1e30) return 1.0 / d;  // outside FP32's comfortable range
-  const double x = double(__frcp_rn(float(d)));
-  return x * (2.0 - d * x);
+  return 1.0 / d;
 }
 
 // Task (front, k0, kb): LDL^T of the kb x kb diagonal block.  The eliminations
-// run in the factor's type TF; the pivots are accumulated in FP64 (dg) and
-// stored in FP64 with their inverses.  The same row operations applied to the
-// identity give L_KK^{-1} (Gauss-Jordan), written into Y[K, K]; L goes back
-// into F.  Warps 0-7: lane c = tid % 64 owns column c, rows step by 4.  Warp
-// 8 keeps the FP64 pivots: lane l owns rows l and l + 32, so the FP64 chain of
-// a pivot step is two updates deep instead of one per row (GB300's FP64 pipe
-// is narrow and long; serialising it per row dominated this kernel).
+// run in the factor's type TF; the pivots are accumulated in FP64 (FP64
+// factor) or double-float (FP32 factor) and stored in FP64 with their
+// inverses.  The same row operations applied to the identity give L_KK^{-1}
+// (Gauss-Jordan), written into Y[K, K]; L goes back into F.  Warps 0-7: lane
+// c = tid % 64 owns column c, rows step by 4.  Warp 8 keeps the pivots: lane
+// l owns rows l and l + 32, so a pivot step's chain is two updates deep
+// instead of one per row.
 constexpr int kDiagThreads = 288;
 
 template <typename TF>
@@ -103,11 +146,14 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
                                                                   TF *__restrict__ F, TF *__restrict__ Y,
                                                                   double *__restrict__ D,
                                                                   double *__restrict__ Dinv, int *flags) {
+  constexpr bool kDF = sizeof(TF) == 4;
   extern __shared__ __align__(16) unsigned char dsm_raw[];
-  double *dg = reinterpret_cast<double *>(dsm_raw);                      // [64]
+  double *dg = reinterpret_cast<double *>(dsm_raw);  // [64] FP64 pivots, or [64] DF pivots
+  DF *dgf = reinterpret_cast<DF *>(dsm_raw);
   TF(*L)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double));
   TF(*Xi)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double) + 64 * 65 * sizeof(TF));
-  __shared__ double s_inv[64];
+  __shared__ double s_inv[64];  // FP64 inverses, or DF inverses in the same bytes
+  DF *s_invf = reinterpret_cast<DF *>(s_inv);
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t k0 = t.y & 0xffffff, kb = t.z, m = fr.m;
@@ -122,31 +168,53 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
   const bool pivot_warp = threadIdx.x >= 256;
   const int lane = threadIdx.x & 31;
   if (pivot_warp) {
-    for (int i = lane; i < 64; i += 32) dg[i] = i < kb ? double(L[i][i]) : 1.0;
+    for (int i = lane; i < 64; i += 32) {
+      if constexpr (kDF)
+        dgf[i] = {i < kb ? float(L[i][i]) : 1.f, 0.f};
+      else
+        dg[i] = i < kb ? double(L[i][i]) : 1.0;
+    }
     __syncwarp();
-    if (lane == 0) s_inv[0] = pivot_inverse(dg[0], flags);
+    if (lane == 0) {
+      if constexpr (kDF)
+        s_invf[0] = df_pivot_inverse(dgf[0], flags);
+      else
+        s_inv[0] = pivot_inverse(dg[0], flags);
+    }
   }
   __syncthreads();
   const int c = threadIdx.x & 63, r = threadIdx.x >> 6;
   // One barrier per pivot.  Columns stay unscaled until the write-back: at
   // step j column j of L holds the final Schur-complement entries F_ij, and
-  // the pivot warp folds F_ij^2 / d_j into the FP64 pivots of rows i > j,
-  // then inverts pivot j+1 for the next step.
+  // the pivot warp folds F_ij^2 / d_j into the pivots of rows i > j, then
+  // inverts pivot j+1 for the next step.
   for (int j = 0; j < kb; ++j) {
-    const double invd = s_inv[j];
     if (pivot_warp) {
       const int i0 = lane, i1 = lane + 32;
-      double d0 = 0.0, d1 = 0.0;
-      if (i0 > j && i0 < kb) { const double l = double(L[i0][j]); d0 = dg[i0] - l * l * invd; }
-      if (i1 > j && i1 < kb) { const double l = double(L[i1][j]); d1 = dg[i1] - l * l * invd; }
-      if (i0 > j && i0 < kb) dg[i0] = d0;
-      if (i1 > j && i1 < kb) dg[i1] = d1;
-      if (j + 1 < kb) {
-        const double dn = ((j + 1) & 32) ? d1 : d0;
-        if (lane == ((j + 1) & 31)) s_inv[j + 1] = pivot_inverse(dn, flags);
+      const bool u0 = i0 > j && i0 < kb, u1 = i1 > j && i1 < kb;
+      if constexpr (kDF) {
+        const DF invd = s_invf[j];
+        DF d0 = {0.f, 0.f}, d1 = {0.f, 0.f};
+        if (u0) d0 = df_sub(dgf[i0], df_mul(df_two_prod(float(L[i0][j]), float(L[i0][j])), invd));
+        if (u1) d1 = df_sub(dgf[i1], df_mul(df_two_prod(float(L[i1][j]), float(L[i1][j])), invd));
+        if (u0) dgf[i0] = d0;
+        if (u1) dgf[i1] = d1;
+        if (j + 1 < kb && lane == ((j + 1) & 31)) s_invf[j + 1] = df_pivot_inverse(((j + 1) & 32) ? d1 : d0, flags);
+      } else {
+        const double invd = s_inv[j];
+        double d0 = 0.0, d1 = 0.0;
+        if (u0) { const double l = double(L[i0][j]); d0 = dg[i0] - l * l * invd; }
+        if (u1) { const double l = double(L[i1][j]); d1 = dg[i1] - l * l * invd; }
+        if (u0) dg[i0] = d0;
+        if (u1) dg[i1] = d1;
+        if (j + 1 < kb && lane == ((j + 1) & 31)) s_inv[j + 1] = pivot_inverse(((j + 1) & 32) ? d1 : d0, flags);
       }
     } else {
-      const TF tinv = TF(invd);
+      TF tinv;
+      if constexpr (kDF)
+        tinv = s_invf[j].hi;
+      else
+        tinv = TF(s_inv[j]);
       for (int i = j + 1 + r; i < kb; i += 4) {
         const TF lij = L[i][j] * tinv;
         if (c > j && c < i) L[i][c] -= lij * L[c][j];
@@ -156,14 +224,26 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     __syncthreads();
   }
   if (threadIdx.x < kb) {
-    double d = dg[threadIdx.x];
+    double d, dinv;
+    if constexpr (kDF) {
+      d = double(dgf[threadIdx.x].hi) + double(dgf[threadIdx.x].lo);
+      dinv = double(s_invf[threadIdx.x].hi) + double(s_invf[threadIdx.x].lo);
+    } else {
+      d = dg[threadIdx.x];
+      dinv = s_inv[threadIdx.x];
+    }
     if (!(d > 0.0)) d = 1.0;
     D[fr.first + k0 + threadIdx.x] = d;
-    Dinv[fr.first + k0 + threadIdx.x] = s_inv[threadIdx.x];
+    Dinv[fr.first + k0 + threadIdx.x] = dinv;
   }
   for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
     const int i = idx % kb, j = idx / kb;
-    if (i > j) L[i][j] *= TF(s_inv[j]);
+    TF sc;
+    if constexpr (kDF)
+      sc = s_invf[j].hi;
+    else
+      sc = TF(s_inv[j]);
+    if (i > j) L[i][j] *= sc;
   }
   __syncthreads();
   TF *Yf = Y + fr.y_off;
