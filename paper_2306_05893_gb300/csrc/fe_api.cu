@@ -316,6 +316,8 @@ int flag_status(fe_ctx *c) {
   if (f & FLAG_INVERTED) return set_error(c, FE_ERR_INVERTED, "an element has det F <= 0");
   if (f & FLAG_PIVOT) return set_error(c, FE_ERR_BREAKDOWN, "LDL^T pivot <= 0");
   if (f & FLAG_BREAKDOWN) return set_error(c, FE_ERR_BREAKDOWN, "CG breakdown (p^T A p <= 0 or r^T z <= 0)");
+  if (f & FLAG_WAIT_TIMEOUT)
+    return set_error(c, FE_ERR_TIMEOUT, "a tensor-core completion wait in the factor update gave up");
   return FE_OK;
 }
 

@@ -26,7 +26,7 @@ struct DFront {
 };
 
 // Error flags raised by kernels (bit mask in DeviceState::flags[0]).
-enum { FLAG_INVERTED = 1, FLAG_PIVOT = 2, FLAG_BREAKDOWN = 4 };
+enum { FLAG_INVERTED = 1, FLAG_PIVOT = 2, FLAG_BREAKDOWN = 4, FLAG_WAIT_TIMEOUT = 8 };
 
 // Scalars of the PCG kept on the device (double).
 enum {

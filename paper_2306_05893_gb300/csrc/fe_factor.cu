@@ -425,28 +425,39 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
 // rest of the front, so the trailing matrix is read and written once per
 // kSuper pivots instead of once per 64.
 //
-// Warp-level m16n8k8 TF32 MMAs with a 3xTF32 split (a = a_hi + a_lo,
-// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) keep ~FP32 accuracy.  8 warps as
-// 2 (rows) x 4 (columns), each 64 x 32 outputs = 4 x 4 MMA tiles.  K streams
-// through a 3-stage cp.async pipeline of 32-wide chunks; the epilogue stages
-// the C tile through shared memory so F and Y are read and written coalesced.
+// Blackwell tensor cores (tcgen05, kind::tf32) with a 3xTF32 split
+// (a = a_hi + a_lo, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) so products keep
+// ~FP32 accuracy.  Per 32-wide K chunk all 256 threads load the operands
+// from global memory into registers, split each element once, and store the
+// four operands (A_hi, A_lo, B_hi, B_lo) into shared memory in the K-major,
+// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix; 128 B
+// between 8-row groups, 2048 B between 4-column K groups).  One thread issues
+// the 12 MMAs of the chunk (M = N = 128, K = 8 each) into a 128 x 128 FP32
+// accumulator in tensor memory and commits them to an mbarrier; the next
+// chunk's global loads are in flight meanwhile.  The epilogue reads the
+// accumulator with tcgen05.ld (warp w: lanes 32 (w % 4) .., columns
+// 64 (w / 4) ..) and updates F or Y in place with coalesced accesses.
 constexpr int kT128 = 128;
-constexpr int kKc = 32;                            // K chunk per pipeline stage
-constexpr int kLdMma = 136;                        // row stride: fragment loads hit 32 distinct banks
-constexpr int kStages = 3;
-constexpr int kStageFloats = 2 * kKc * kLdMma;     // A and B chunk
-constexpr size_t kUpdateSmem = size_t(kStages) * kStageFloats * sizeof(float);
-static_assert(kUpdateSmem >= size_t(kT128) * 129 * sizeof(float), "epilogue tile must fit the stages");
+constexpr int kKc = 32;                              // K chunk
+constexpr int kOpBytes = kT128 * kKc * 4;            // one operand of one chunk: 16 KB
+constexpr int kUmmaLbo = 2048;                       // K-direction core-matrix stride
+constexpr int kUmmaSbo = 128;                        // M/N-direction (8-row group) stride
+// operands + mbarrier/TMEM slot, padded so every byte an MMA of this
+// layout can address lies inside the CTA's shared memory
+constexpr size_t kUpdateSmem = size_t(96) << 10;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;     // give up an mbarrier wait after 1 s
 
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool valid) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  const int sz = valid ? 4 : 0;  // 0: nothing is read, the 4 bytes are zero-filled
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
+// tcgen05 instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B
+// TF32 (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(kT128 >> 3) << 17) |
+                                (uint32_t(kT128 >> 4) << 24);
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  // start address >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4 (32-45),
+  // fixed 0b001 at bits 46-48, no swizzle (bits 61-63 = 0)
+  return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(kUmmaLbo >> 4) << 16) | (uint64_t(kUmmaSbo >> 4) << 32) |
+         (uint64_t(1) << 46);
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
@@ -454,25 +465,43 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
-  hi = to_tf32(x);
-  lo = to_tf32(x - __uint_as_float(hi));
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// Bounded wait on the mbarrier phase with the given parity; false if the
+// limit ran out.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
 }
 
 __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *__restrict__ tasks,
                                                                  const DFront *__restrict__ fronts,
                                                                  float *__restrict__ F, float *__restrict__ Y,
-                                                                 const double *__restrict__ D) {
-  extern __shared__ __align__(16) float umm[];
-  float *Cs = umm;  // epilogue [128][129] (column j, row i), reuses the stages
+                                                                 const double *__restrict__ D, int *flags) {
+  extern __shared__ __align__(1024) unsigned char usm[];
+  float *sAh = reinterpret_cast<float *>(usm);
+  float *sAl = reinterpret_cast<float *>(usm + kOpBytes);
+  float *sBh = reinterpret_cast<float *>(usm + 2 * kOpBytes);
+  float *sBl = reinterpret_cast<float *>(usm + 3 * kOpBytes);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(usm + 4 * kOpBytes);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(usm + 4 * kOpBytes + 8);
   __shared__ float Ds[kSuper];
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
@@ -486,121 +515,129 @@ __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *
   const bool trail = kind == T_TRAIL;
   float *Ff = F + fr.f_off;
   float *Yf = Y + fr.y_off;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int l = threadIdx.x; l < kSuper; l += 256) Ds[l] = (trail && l < kw) ? float(D[fr.first + k0 + l]) : 1.f;
+  const uint32_t bar_a = smem_u32(bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kT128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  // Element e = 32 u + lane of this warp's share: block b = warp + 8 u holds
+  // rows 8 (b % 16) + lane / 4 and K columns 4 (b / 16) + lane % 4; its byte
+  // offset in an operand is (b / 16) LBO + (b % 16) SBO + 4 lane.
   const int nchunk = (kw + kKc - 1) / kKc;
+  float ra[16], rb[16];
   auto load_chunk = [&](int q) {
-    float *As = umm + (q % kStages) * kStageFloats;  // As[l][i] = L[i0 + i, k0 + kKc q + l]
-    float *Bs = As + kKc * kLdMma;                    // Bs[l][j]
     const int32_t kq = k0 + kKc * q;
-    for (int idx = threadIdx.x; idx < kKc * kT128; idx += 256) {
-      const int l = idx / kT128, i = idx % kT128;
-      const int32_t r = i0 + i;
-      const bool ok = r < m && kq + l < kend;
-      cp_async4(As + l * kLdMma + i, ok ? Ff + r + int64_t(kq + l) * m : Ff, ok);
-    }
-    if (trail) {
-      for (int idx = threadIdx.x; idx < kKc * kT128; idx += 256) {
-        const int l = idx / kT128, j = idx % kT128;
-        const int32_t r = j0 + j;
-        const bool ok = r < m && kq + l < kend;
-        cp_async4(Bs + l * kLdMma + j, ok ? Ff + r + int64_t(kq + l) * m : Ff, ok);
-      }
-    } else {
-      for (int idx = threadIdx.x; idx < kKc * kT128; idx += 256) {
-        const int l = idx % kKc, j = idx / kKc;
-        const int32_t c = j0 + j;
-        const bool ok = kq + l < kend && c < kend;
-        cp_async4(Bs + l * kLdMma + j, ok ? Yf + (kq + l) + int64_t(c) * fr.ldy : Yf, ok);
-      }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int b = warp + 8 * u;
+      const int row = 8 * (b % 16) + (lane >> 2);
+      const int32_t l = kq + 4 * (b / 16) + (lane & 3);
+      const bool lok = l < kend;
+      const int32_t ra_row = i0 + row, rb_row = j0 + row;
+      ra[u] = (lok && ra_row < m) ? Ff[ra_row + int64_t(l) * m] : 0.f;
+      if (trail)
+        rb[u] = (lok && rb_row < m) ? Ff[rb_row + int64_t(l) * m] * Ds[l - k0] : 0.f;
+      else
+        rb[u] = (lok && rb_row < kend) ? Yf[l + int64_t(rb_row) * fr.ldy] : 0.f;
     }
   };
-#pragma unroll
-  for (int q = 0; q < kStages - 1; ++q) {
-    if (q < nchunk) load_chunk(q);
-    cp_async_commit();
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, tq = lane & 3;
-  const int wm = warp & 1, wn = warp >> 1;
-  float acc[4][4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[a][b][v] = 0.f;
+  __syncthreads();  // Ds ready
+  load_chunk(0);
+  bool ok = true;
   for (int q = 0; q < nchunk; ++q) {
-    cp_async_wait<kStages - 2>();  // chunk q has landed
-    __syncthreads();               // ... for every thread; stage (q - 1) % kStages is free
-    if (q + kStages - 1 < nchunk) load_chunk(q + kStages - 1);
-    cp_async_commit();
-    const float *As = umm + (q % kStages) * kStageFloats;
-    const float *Bs = As + kKc * kLdMma;
-    const float *Dq = Ds + kKc * q;
+    if (q > 0) ok = ok && mbar_wait(bar_a, uint32_t(q - 1) & 1u);  // chunk q-1's MMAs have read the operands
 #pragma unroll
-    for (int kk = 0; kk < kKc; kk += 8) {
-      uint32_t ah[4][4], al[4][4], bh[4][2], bl[4][2];
+    for (int u = 0; u < 16; ++u) {
+      const int b = warp + 8 * u;
+      const int off = (b / 16) * (kUmmaLbo / 4) + (b % 16) * (kUmmaSbo / 4) + lane;
+      const uint32_t ah = to_tf32(ra[u]), bh = to_tf32(rb[u]);
+      sAh[off] = __uint_as_float(ah);
+      sAl[off] = __uint_as_float(to_tf32(ra[u] - __uint_as_float(ah)));
+      sBh[off] = __uint_as_float(bh);
+      sBl[off] = __uint_as_float(to_tf32(rb[u] - __uint_as_float(bh)));
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic-proxy stores -> tensor core
+    __syncthreads();
+    if (threadIdx.x == 0 && ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
 #pragma unroll
-      for (int mt = 0; mt < 4; ++mt) {
-        const int mrow = wm * 64 + mt * 16 + g;
-        split_tf32(As[(kk + tq) * kLdMma + mrow], ah[mt][0], al[mt][0]);
-        split_tf32(As[(kk + tq) * kLdMma + mrow + 8], ah[mt][1], al[mt][1]);
-        split_tf32(As[(kk + tq + 4) * kLdMma + mrow], ah[mt][2], al[mt][2]);
-        split_tf32(As[(kk + tq + 4) * kLdMma + mrow + 8], ah[mt][3], al[mt][3]);
+      for (int s = 0; s < kKc / 8; ++s) {
+        const uint32_t ko = uint32_t(s) * 2 * kUmmaLbo;  // two K groups of 4 per MMA
+        const uint64_t dah = umma_desc(ah + ko), dal = umma_desc(al + ko);
+        const uint64_t dbh = umma_desc(bh + ko), dbl = umma_desc(bl + ko);
+        const uint32_t acc0 = (q > 0 || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dal), "l"(dbh), "r"(kIdescTf32), "r"(acc0)
+            : "memory");
+        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah), "l"(dbl),
+                     "r"(kIdescTf32)
+                     : "memory");
+        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah), "l"(dbh),
+                     "r"(kIdescTf32)
+                     : "memory");
       }
-      const float d0 = Dq[kk + tq], d1 = Dq[kk + tq + 4];
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_a)
+                   : "memory");
+    }
+    if (q + 1 < nchunk) load_chunk(q + 1);
+  }
+  ok = ok && mbar_wait(bar_a, uint32_t(nchunk - 1) & 1u);
+  ok = __syncthreads_and(ok) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (ok) {
+    // epilogue: TRAIL writes the lower part of columns < cmax (the
+    // superpanel's end for an eager task), RUPD rows < rmax of columns < kend
+    const int32_t cmax = trail ? (eager ? s_end : m) : kend;
+    const int32_t rmax = (!trail && eager) ? s_end : m;
+    const int g = warp & 3, h = warp >> 2;
+    const int32_t r = i0 + 32 * g + lane;
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int ncol = wn * 32 + nt * 8 + g;
-        split_tf32(Bs[(kk + tq) * kLdMma + ncol] * d0, bh[nt][0], bl[nt][0]);
-        split_tf32(Bs[(kk + tq + 4) * kLdMma + ncol] * d1, bh[nt][1], bl[nt][1]);
-      }
+    for (int x = 0; x < 2; ++x) {
+      uint32_t v[32];
+      const uint32_t ta = tmem + (uint32_t(32 * g) << 16) + uint32_t(64 * h + 32 * x);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+          "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(ta));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (r < rmax) {
 #pragma unroll
-      for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          mma_tf32(acc[mt][nt], al[mt], bh[nt]);
-          mma_tf32(acc[mt][nt], ah[mt], bl[nt]);
-          mma_tf32(acc[mt][nt], ah[mt], bh[nt]);
+        for (int e = 0; e < 32; ++e) {
+          const int32_t cc = j0 + 64 * h + 32 * x + e;
+          if (cc < cmax && (!trail || r >= cc)) {
+            float *dst = trail ? Ff + r + int64_t(cc) * m : Yf + r + int64_t(cc) * fr.ldy;
+            *dst -= __uint_as_float(v[e]);
+          }
         }
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // epilogue: TRAIL writes the lower part of columns < cmax (the superpanel's
-  // end for an eager task), RUPD rows < rmax of columns < kend
-  const int32_t cmax = trail ? (eager ? s_end : m) : kend;
-  const int32_t rmax = (!trail && eager) ? s_end : m;
-  for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
-    const int j = idx / kT128, i = idx % kT128;
-    const int32_t r = i0 + i, c = j0 + j;
-    const bool ok = r < rmax && c < cmax;
-    const float *src = trail ? Ff + r + int64_t(c) * m : Yf + r + int64_t(c) * fr.ldy;
-    cp_async4(Cs + j * 129 + i, ok ? src : Ff, ok);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-#pragma unroll
-  for (int mt = 0; mt < 4; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int i = wm * 64 + mt * 16 + g + 8 * (v >> 1);
-        const int j = wn * 32 + nt * 8 + 2 * tq + (v & 1);
-        Cs[j * 129 + i] -= acc[mt][nt][v];
       }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < kT128 * kT128; idx += 256) {
-    const int j = idx / kT128, i = idx % kT128;
-    const int32_t r = i0 + i, c = j0 + j;
-    if (r >= rmax || c >= cmax) continue;
-    if (trail) {
-      if (r >= c) Ff[r + int64_t(c) * m] = Cs[j * 129 + i];
-    } else {
-      Yf[r + int64_t(c) * fr.ldy] = Cs[j * 129 + i];
     }
+  } else if (threadIdx.x == 0) {
+    atomicOr(flags, FLAG_WAIT_TIMEOUT);
   }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kT128) : "memory");
 }
 
 // ------------------------------------------------------------------ apply
@@ -862,7 +899,8 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
         if (ev >= 0) d->update_flops += L.trail_flops[st];
         if constexpr (sizeof(TF) == 4)
           front_update_tc_kernel<<<unsigned(L.trail_n[st]), 256, kUpdateSmem, s>>>(d->tasks + L.trail_off[st],
-                                                                                   d->fronts, F, Y, d->D[buf]);
+                                                                                   d->fronts, F, Y, d->D[buf],
+                                                                                   d->flags);
         else
           front_update_kernel<TF><<<unsigned(L.trail_n[st]), 256, tsm, s>>>(d->tasks + L.trail_off[st], d->fronts, F,
                                                                           Y, d->D[buf]);
