@@ -134,10 +134,17 @@ __device__ __forceinline__ double pivot_inverse(double d, int *flags) {
 // run in the factor's type TF; the pivots are accumulated in FP64 (FP64
 // factor) or double-float (FP32 factor) and stored in FP64 with their
 // inverses.  The same row operations applied to the identity give L_KK^{-1}
-// (Gauss-Jordan), written into Y[K, K]; L goes back into F.  Warps 0-7: lane
-// c = tid % 64 owns column c, rows step by 4.  Warp 8 keeps the pivots: lane
-// l owns rows l and l + 32, so a pivot step's chain is two updates deep
-// instead of one per row.
+// (Gauss-Jordan), written into Y[K, K]; L goes back into F.
+//
+// Warps 0-7 hold the block in registers: thread (tr, tc) = (tid / 16,
+// tid % 16) owns rows tr + 16a and columns tc + 16b (a, b < 4).  An entry
+// (i, c) holds L_ic until its column is final (after step c - 1), is then
+// saved and restarts as the Gauss-Jordan entry Xi_ic, so one register and one
+// FMA per entry and step serve both.  At step j the pivot column F_:j
+// (unscaled) and the Gauss-Jordan row Xi_j: come from double-buffered
+// shared vectors written by their owners at step j - 1: one barrier per
+// pivot.  Warp 8 keeps the pivots (lane l: rows l and l + 32) and inverts
+// pivot j + 1 during step j.
 constexpr int kDiagThreads = 288;
 
 template <typename TF>
@@ -150,8 +157,9 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
   extern __shared__ __align__(16) unsigned char dsm_raw[];
   double *dg = reinterpret_cast<double *>(dsm_raw);  // [64] FP64 pivots, or [64] DF pivots
   DF *dgf = reinterpret_cast<DF *>(dsm_raw);
-  TF(*L)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double));
-  TF(*Xi)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double) + 64 * 65 * sizeof(TF));
+  TF(*Ls)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double));  // input, then final L (unscaled)
+  TF(*Xs)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double) + 64 * 65 * sizeof(TF));
+  __shared__ TF colb[2][64], xrow[2][64];
   __shared__ double s_inv[64];  // FP64 inverses, or DF inverses in the same bytes
   DF *s_invf = reinterpret_cast<DF *>(s_inv);
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
@@ -160,19 +168,32 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
   TF *Ff = F + fr.f_off;
   for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
     const int i = idx % 64, j = idx / 64;
-    const bool in = i < kb && j < kb;
-    L[i][j] = (in && i >= j) ? Ff[(k0 + i) + int64_t(k0 + j) * m] : TF(0);
-    Xi[i][j] = (i == j) ? TF(1) : TF(0);
+    Ls[i][j] = (i < kb && j < kb && i >= j) ? Ff[(k0 + i) + int64_t(k0 + j) * m] : TF(0);
   }
   __syncthreads();
   const bool pivot_warp = threadIdx.x >= 256;
   const int lane = threadIdx.x & 31;
-  if (pivot_warp) {
+  const int tr = (threadIdx.x & 255) >> 4, tc = threadIdx.x & 15;
+  TF R[4][4];
+  if (!pivot_warp) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = tr + 16 * a, c = tc + 16 * b;
+        // column 0 is final from the start: it restarts as Xi at once
+        R[a][b] = (c == 0 && i > 0) ? TF(0) : Ls[i][c];
+      }
+    if (threadIdx.x < 64) {
+      colb[0][threadIdx.x] = Ls[threadIdx.x][0];
+      xrow[0][threadIdx.x] = threadIdx.x == 0 ? TF(1) : TF(0);
+    }
+  } else {
     for (int i = lane; i < 64; i += 32) {
       if constexpr (kDF)
-        dgf[i] = {i < kb ? float(L[i][i]) : 1.f, 0.f};
+        dgf[i] = {i < kb ? float(Ls[i][i]) : 1.f, 0.f};
       else
-        dg[i] = i < kb ? double(L[i][i]) : 1.0;
+        dg[i] = i < kb ? double(Ls[i][i]) : 1.0;
     }
     __syncwarp();
     if (lane == 0) {
@@ -183,28 +204,25 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     }
   }
   __syncthreads();
-  const int c = threadIdx.x & 63, r = threadIdx.x >> 6;
-  // One barrier per pivot.  Columns stay unscaled until the write-back: at
-  // step j column j of L holds the final Schur-complement entries F_ij, and
-  // the pivot warp folds F_ij^2 / d_j into the pivots of rows i > j, then
-  // inverts pivot j+1 for the next step.
   for (int j = 0; j < kb; ++j) {
+    const int cur = j & 1, nxt = cur ^ 1;
     if (pivot_warp) {
       const int i0 = lane, i1 = lane + 32;
       const bool u0 = i0 > j && i0 < kb, u1 = i1 > j && i1 < kb;
+      const TF f0 = colb[cur][i0], f1 = colb[cur][i1];
       if constexpr (kDF) {
         const DF invd = s_invf[j];
         DF d0 = {0.f, 0.f}, d1 = {0.f, 0.f};
-        if (u0) d0 = df_sub(dgf[i0], df_mul(df_two_prod(float(L[i0][j]), float(L[i0][j])), invd));
-        if (u1) d1 = df_sub(dgf[i1], df_mul(df_two_prod(float(L[i1][j]), float(L[i1][j])), invd));
+        if (u0) d0 = df_sub(dgf[i0], df_mul(df_two_prod(float(f0), float(f0)), invd));
+        if (u1) d1 = df_sub(dgf[i1], df_mul(df_two_prod(float(f1), float(f1)), invd));
         if (u0) dgf[i0] = d0;
         if (u1) dgf[i1] = d1;
         if (j + 1 < kb && lane == ((j + 1) & 31)) s_invf[j + 1] = df_pivot_inverse(((j + 1) & 32) ? d1 : d0, flags);
       } else {
         const double invd = s_inv[j];
         double d0 = 0.0, d1 = 0.0;
-        if (u0) { const double l = double(L[i0][j]); d0 = dg[i0] - l * l * invd; }
-        if (u1) { const double l = double(L[i1][j]); d1 = dg[i1] - l * l * invd; }
+        if (u0) d0 = dg[i0] - double(f0) * double(f0) * invd;
+        if (u1) d1 = dg[i1] - double(f1) * double(f1) * invd;
         if (u0) dg[i0] = d0;
         if (u1) dg[i1] = d1;
         if (j + 1 < kb && lane == ((j + 1) & 31)) s_inv[j + 1] = pivot_inverse(((j + 1) & 32) ? d1 : d0, flags);
@@ -215,13 +233,60 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
         tinv = s_invf[j].hi;
       else
         tinv = TF(s_inv[j]);
-      for (int i = j + 1 + r; i < kb; i += 4) {
-        const TF lij = L[i][j] * tinv;
-        if (c > j && c < i) L[i][c] -= lij * L[c][j];
-        if (c <= j) Xi[i][c] -= lij * Xi[j][c];
+      TF lij[4], val[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = tr + 16 * a;
+        lij[a] = i > j ? colb[cur][i] * tinv : TF(0);
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = tc + 16 * b;
+        val[b] = c > j ? colb[cur][c] : xrow[cur][c];  // L update right of j, Gauss-Jordan at or left of j
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) R[a][b] -= lij[a] * val[b];
+      // publish column j+1 (final now) and row j+1 of Xi for the next step
+      const int jn = j + 1;
+      if (tc == (jn & 15)) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (16 * b + tc != jn) continue;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = tr + 16 * a;
+            colb[nxt][i] = R[a][b];
+            if (i > jn) {
+              Ls[i][jn] = R[a][b];
+              R[a][b] = TF(0);  // restarts as Xi_{i, j+1}
+            }
+          }
+        }
+      }
+      if (tr == (jn & 15)) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (16 * a + tr != jn) continue;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int c = tc + 16 * b;
+            xrow[nxt][c] = c < jn ? R[a][b] : (c == jn ? TF(1) : TF(0));
+          }
+        }
       }
     }
     __syncthreads();
+  }
+  if (!pivot_warp) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = tr + 16 * a, c = tc + 16 * b;
+        Xs[i][c] = i > c ? R[a][b] : (i == c ? TF(1) : TF(0));
+      }
   }
   if (threadIdx.x < kb) {
     double d, dinv;
@@ -236,6 +301,8 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     D[fr.first + k0 + threadIdx.x] = d;
     Dinv[fr.first + k0 + threadIdx.x] = dinv;
   }
+  __syncthreads();
+  TF *Yf = Y + fr.y_off;
   for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
     const int i = idx % kb, j = idx / kb;
     TF sc;
@@ -243,14 +310,8 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
       sc = s_invf[j].hi;
     else
       sc = TF(s_inv[j]);
-    if (i > j) L[i][j] *= sc;
-  }
-  __syncthreads();
-  TF *Yf = Y + fr.y_off;
-  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-    const int i = idx % kb, j = idx / kb;
-    if (i > j) Ff[(k0 + i) + int64_t(k0 + j) * m] = L[i][j];
-    Yf[(k0 + i) + int64_t(k0 + j) * fr.ldy] = Xi[i][j];
+    if (i > j) Ff[(k0 + i) + int64_t(k0 + j) * m] = Ls[i][j] * sc;
+    Yf[(k0 + i) + int64_t(k0 + j) * fr.ldy] = Xs[i][j];
   }
 }
 
