@@ -503,9 +503,7 @@ constexpr int kKc = 32;                              // K chunk
 constexpr int kOpBytes = kT128 * kKc * 4;            // one operand of one chunk: 16 KB
 constexpr int kUmmaLbo = 2048;                       // K-direction core-matrix stride
 constexpr int kUmmaSbo = 128;                        // M/N-direction (8-row group) stride
-// operands + mbarrier/TMEM slot, padded so every byte an MMA of this
-// layout can address lies inside the CTA's shared memory
-constexpr size_t kUpdateSmem = size_t(96) << 10;
+constexpr size_t kUpdateSmem = size_t(4) * kOpBytes + 128;  // operands + mbarrier/TMEM slot
 constexpr uint64_t kWaitLimitNs = 1000000000ull;     // give up an mbarrier wait after 1 s
 
 // tcgen05 instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B
@@ -594,69 +592,80 @@ __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  // Element e = 32 u + lane of this warp's share: block b = warp + 8 u holds
-  // rows 8 (b % 16) + lane / 4 and K columns 4 (b / 16) + lane % 4; its byte
-  // offset in an operand is (b / 16) LBO + (b % 16) SBO + 4 lane.
+  // Warp w loads K columns 4 w + lane % 4 of the chunk for rows 8 u + lane / 4
+  // (u < 16): the core matrix (row group u, K group w), at byte offset
+  // w LBO + u SBO + 4 lane of an operand.  Chunk q + 1 is loaded into the
+  // second register set while chunk q is split, stored and multiplied.
   const int nchunk = (kw + kKc - 1) / kKc;
-  float ra[16], rb[16];
-  auto load_chunk = [&](int q) {
-    const int32_t kq = k0 + kKc * q;
+  const int lr = lane >> 2, lk = 4 * warp + (lane & 3);
+  float ra[2][16], rb[2][16];
+  auto load_chunk = [&](int q, float (&xa)[16], float (&xb)[16]) {
+    const int32_t l = k0 + kKc * q + lk;
+    const bool lok = l < kend;
+    const float *pa = Ff + (i0 + lr) + int64_t(l) * m;
+    const float *pb = trail ? Ff + (j0 + lr) + int64_t(l) * m : Yf + l + int64_t(j0 + lr) * fr.ldy;
+    const int64_t sb = trail ? 8 : int64_t(8) * fr.ldy;
+    const int32_t bmax = trail ? m : kend;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
-      const int b = warp + 8 * u;
-      const int row = 8 * (b % 16) + (lane >> 2);
-      const int32_t l = kq + 4 * (b / 16) + (lane & 3);
-      const bool lok = l < kend;
-      const int32_t ra_row = i0 + row, rb_row = j0 + row;
-      ra[u] = (lok && ra_row < m) ? Ff[ra_row + int64_t(l) * m] : 0.f;
-      if (trail)
-        rb[u] = (lok && rb_row < m) ? Ff[rb_row + int64_t(l) * m] * Ds[l - k0] : 0.f;
-      else
-        rb[u] = (lok && rb_row < kend) ? Yf[l + int64_t(rb_row) * fr.ldy] : 0.f;
+      xa[u] = (lok && i0 + lr + 8 * u < m) ? pa[8 * u] : 0.f;
+      xb[u] = (lok && j0 + lr + 8 * u < bmax) ? pb[sb * u] : 0.f;
     }
   };
-  __syncthreads();  // Ds ready
-  load_chunk(0);
-  bool ok = true;
-  for (int q = 0; q < nchunk; ++q) {
-    if (q > 0) ok = ok && mbar_wait(bar_a, uint32_t(q - 1) & 1u);  // chunk q-1's MMAs have read the operands
+  auto store_chunk = [&](int q, const float (&xa)[16], const float (&xb)[16]) {
+    const float dl = Ds[min(kKc * q + lk, kSuper - 1)];
+    const int off0 = warp * (kUmmaLbo / 4) + lane;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
-      const int b = warp + 8 * u;
-      const int off = (b / 16) * (kUmmaLbo / 4) + (b % 16) * (kUmmaSbo / 4) + lane;
-      const uint32_t ah = to_tf32(ra[u]), bh = to_tf32(rb[u]);
+      const int off = off0 + u * (kUmmaSbo / 4);
+      const float bv = xb[u] * dl;
+      const uint32_t ah = to_tf32(xa[u]), bh = to_tf32(bv);
       sAh[off] = __uint_as_float(ah);
-      sAl[off] = __uint_as_float(to_tf32(ra[u] - __uint_as_float(ah)));
+      sAl[off] = __uint_as_float(to_tf32(xa[u] - __uint_as_float(ah)));
       sBh[off] = __uint_as_float(bh);
-      sBl[off] = __uint_as_float(to_tf32(rb[u] - __uint_as_float(bh)));
+      sBl[off] = __uint_as_float(to_tf32(bv - __uint_as_float(bh)));
     }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic-proxy stores -> tensor core
-    __syncthreads();
-    if (threadIdx.x == 0 && ok) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
+  };
+  auto issue_chunk = [&](int q) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
 #pragma unroll
-      for (int s = 0; s < kKc / 8; ++s) {
-        const uint32_t ko = uint32_t(s) * 2 * kUmmaLbo;  // two K groups of 4 per MMA
-        const uint64_t dah = umma_desc(ah + ko), dal = umma_desc(al + ko);
-        const uint64_t dbh = umma_desc(bh + ko), dbl = umma_desc(bl + ko);
-        const uint32_t acc0 = (q > 0 || s > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(dal), "l"(dbh), "r"(kIdescTf32), "r"(acc0)
-            : "memory");
-        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah), "l"(dbl),
-                     "r"(kIdescTf32)
-                     : "memory");
-        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah), "l"(dbh),
-                     "r"(kIdescTf32)
-                     : "memory");
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_a)
+    for (int s = 0; s < kKc / 8; ++s) {
+      const uint32_t ko = uint32_t(s) * 2 * kUmmaLbo;  // two K groups of 4 per MMA
+      const uint64_t dah = umma_desc(ah + ko), dal = umma_desc(al + ko);
+      const uint64_t dbh = umma_desc(bh + ko), dbl = umma_desc(bl + ko);
+      const uint32_t acc0 = (q > 0 || s > 0) ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(dal), "l"(dbh), "r"(kIdescTf32), "r"(acc0)
+          : "memory");
+      asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah), "l"(dbl),
+                   "r"(kIdescTf32)
+                   : "memory");
+      asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah), "l"(dbh),
+                   "r"(kIdescTf32)
                    : "memory");
     }
-    if (q + 1 < nchunk) load_chunk(q + 1);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_a)
+                 : "memory");
+  };
+  __syncthreads();  // Ds ready
+  load_chunk(0, ra[0], rb[0]);
+  bool ok = true;
+  for (int q = 0; q < nchunk; q += 2) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int qq = q + h;
+      if (qq < nchunk) {
+        if (qq + 1 < nchunk) load_chunk(qq + 1, ra[h ^ 1], rb[h ^ 1]);
+        if (qq > 0) ok = ok && mbar_wait(bar_a, uint32_t(qq - 1) & 1u);  // chunk qq-1's MMAs have read the operands
+        store_chunk(qq, ra[h], rb[h]);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic-proxy stores -> tensor core
+        __syncthreads();
+        if (threadIdx.x == 0 && ok) issue_chunk(qq);
+      }
+    }
   }
   ok = ok && mbar_wait(bar_a, uint32_t(nchunk - 1) & 1u);
   ok = __syncthreads_and(ok) != 0;
@@ -668,28 +677,33 @@ __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *
     const int32_t rmax = (!trail && eager) ? s_end : m;
     const int g = warp & 3, h = warp >> 2;
     const int32_t r = i0 + 32 * g + lane;
+    float *base = trail ? Ff + r : Yf + r;
+    const int64_t ld = trail ? int64_t(m) : int64_t(fr.ldy);
+#pragma unroll 1
+    for (int x = 0; x < 4; ++x) {
+      const int32_t c0 = j0 + 64 * h + 16 * x;
+      // all loads of the row's 16 entries first, then the stores (a store
+      // between two loads would expose one memory latency per entry)
+      float old[16];
 #pragma unroll
-    for (int x = 0; x < 2; ++x) {
-      uint32_t v[32];
-      const uint32_t ta = tmem + (uint32_t(32 * g) << 16) + uint32_t(64 * h + 32 * x);
+      for (int e = 0; e < 16; ++e) {
+        const int32_t cc = c0 + e;
+        const bool in = r < rmax && cc < cmax && (!trail || r >= cc);
+        old[e] = in ? base[int64_t(cc) * ld] : 0.f;
+      }
+      uint32_t v[16];
+      const uint32_t ta = tmem + (uint32_t(32 * g) << 16) + uint32_t(64 * h + 16 * x);
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
-          "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
           : "r"(ta));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (r < rmax) {
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          const int32_t cc = j0 + 64 * h + 32 * x + e;
-          if (cc < cmax && (!trail || r >= cc)) {
-            float *dst = trail ? Ff + r + int64_t(cc) * m : Yf + r + int64_t(cc) * fr.ldy;
-            *dst -= __uint_as_float(v[e]);
-          }
-        }
+      for (int e = 0; e < 16; ++e) {
+        const int32_t cc = c0 + e;
+        const bool in = r < rmax && cc < cmax && (!trail || r >= cc);
+        if (in) base[int64_t(cc) * ld] = old[e] - __uint_as_float(v[e]);
       }
     }
   } else if (threadIdx.x == 0) {
