@@ -46,9 +46,21 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
   }
   __syncthreads();
   const int32_t ce = c1 < p ? c1 : p;
-  for (int32_t col = c0; col < ce; ++col) {
-    const int64_t e0 = fa_colptr[fr.fac_off + col], e1 = fa_colptr[fr.fac_off + col + 1];
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) Ff[fa_off[e]] = A[fa_slot[e]];
+  if (ce > c0) {  // the entries of columns [c0, ce) are contiguous in the fa lists
+    const int64_t e0 = fa_colptr[fr.fac_off + c0], e1 = fa_colptr[fr.fac_off + ce];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += 4 * 256) {
+      int32_t off[4];
+      TF v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t ee = e + 256 * k;
+        off[k] = ee < e1 ? fa_off[ee] : -1;
+        v[k] = ee < e1 ? A[fa_slot[ee]] : TF(0);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (off[k] >= 0) Ff[off[k]] = v[k];
+    }
   }
   __syncthreads();
   for (int32_t ci = fr.child_begin; ci < fr.child_end; ++ci) {
@@ -66,7 +78,25 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
     for (int32_t j = jlo; j < jhi; ++j) {
       const TF *src = Fc + int64_t(pc + j) * mc + pc;
       TF *dst = Ff + int64_t(rm[j]) * m;
-      for (int32_t i = j + threadIdx.x; i < nu; i += blockDim.x) dst[rm[i]] += src[i];
+      // 8 rows per thread in flight: all loads of a batch before its stores
+      // (a store ahead of the next load would expose one latency per row);
+      // the child's rows map to distinct parent rows, so a batch never
+      // reads what it writes
+      for (int32_t i = j + threadIdx.x; i < nu; i += 8 * 256) {
+        int32_t ri[8];
+        TF sv[8], dv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int32_t ii = i + 256 * k;
+          ri[k] = ii < nu ? rm[ii] : -1;
+          sv[k] = ii < nu ? src[ii] : TF(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dv[k] = ri[k] >= 0 ? dst[ri[k]] : TF(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (ri[k] >= 0) dst[ri[k]] = dv[k] + sv[k];
+      }
     }
     __syncthreads();
   }
