@@ -139,9 +139,9 @@ __device__ __forceinline__ DF df_sub(DF x, DF y) {
 // the residual formed in double-float (error ~2^-46 relative).  A
 // non-positive pivot is flagged and replaced by 1 so the factorisation
 // finishes without NaNs.
-__device__ __forceinline__ DF df_pivot_inverse(DF d, int *flags) {
+__device__ __forceinline__ DF df_pivot_inverse(DF d, int *flags, bool report) {
   if (!(d.hi > 0.f)) {
-    atomicOr(flags, FLAG_PIVOT);
+    if (report) atomicOr(flags, FLAG_PIVOT);
     d = {1.f, 0.f};
   }
   const float x = __frcp_rn(d.hi);
@@ -152,30 +152,34 @@ __device__ __forceinline__ DF df_pivot_inverse(DF d, int *flags) {
   out.lo += q.lo;
   return out;
 }
-__device__ __forceinline__ double pivot_inverse(double d, int *flags) {
+__device__ __forceinline__ double pivot_inverse(double d, int *flags, bool report) {
   if (!(d > 0.0)) {
-    atomicOr(flags, FLAG_PIVOT);
+    if (report) atomicOr(flags, FLAG_PIVOT);
     d = 1.0;
   }
   return 1.0 / d;
 }
 
 // Task (front, k0, kb): LDL^T of the kb x kb diagonal block.  The eliminations
-// run in the factor's type TF; the pivots are accumulated in FP64 (FP64
-// factor) or double-float (FP32 factor) and stored in FP64 with their
-// inverses.  The same row operations applied to the identity give L_KK^{-1}
-// (Gauss-Jordan), written into Y[K, K]; L goes back into F.
+// run in the factor's type TF with the pivots of the running Schur
+// complement in TF; the pivots D are then recomputed from the final
+// (unscaled) columns in FP64 (FP64 factor) or double-float (FP32 factor),
+// d_i = a_ii - sum_j F_ij^2 / d_j, and stored in FP64 with their inverses,
+// which also scale the stored L.  The same row operations applied to the
+// identity give L_KK^{-1} (Gauss-Jordan), written into Y[K, K]; L goes back
+// into F.
 //
-// Warps 0-7 hold the block in registers: thread (tr, tc) = (tid / 16,
+// 256 threads hold the block in registers: thread (tr, tc) = (tid / 16,
 // tid % 16) owns rows tr + 16a and columns tc + 16b (a, b < 4).  An entry
 // (i, c) holds L_ic until its column is final (after step c - 1), is then
 // saved and restarts as the Gauss-Jordan entry Xi_ic, so one register and one
-// FMA per entry and step serve both.  At step j the pivot column F_:j
-// (unscaled) and the Gauss-Jordan row Xi_j: come from double-buffered
-// shared vectors written by their owners at step j - 1: one barrier per
-// pivot.  Warp 8 keeps the pivots (lane l: rows l and l + 32) and inverts
-// pivot j + 1 during step j.
-constexpr int kDiagThreads = 288;
+// FMA per entry and step serve both.  At step j the pivot column F_:j, its
+// pivot's reciprocal and the Gauss-Jordan row Xi_j: come from
+// double-buffered shared vectors written by their owners at step j - 1: one
+// barrier per pivot, and no FP64 or double-float work on that serial path
+// (GB300's FP64 pipe issues a warp instruction only every ~64 cycles per SM
+// sub-partition).
+constexpr int kDiagThreads = 256;
 
 template <typename TF>
 __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t *__restrict__ tasks,
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
   DF *dgf = reinterpret_cast<DF *>(dsm_raw);
   TF(*Ls)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double));  // input, then final L (unscaled)
   TF(*Xs)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double) + 64 * 65 * sizeof(TF));
-  __shared__ TF colb[2][64], xrow[2][64];
+  __shared__ TF colb[2][64], xrow[2][64], pinv[2];
   __shared__ double s_inv[64];  // FP64 inverses, or DF inverses in the same bytes
   DF *s_invf = reinterpret_cast<DF *>(s_inv);
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
@@ -201,123 +205,109 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     Ls[i][j] = (i < kb && j < kb && i >= j) ? Ff[(k0 + i) + int64_t(k0 + j) * m] : TF(0);
   }
   __syncthreads();
-  const bool pivot_warp = threadIdx.x >= 256;
-  const int lane = threadIdx.x & 31;
-  const int tr = (threadIdx.x & 255) >> 4, tc = threadIdx.x & 15;
+  auto safe_inv = [](TF d) { return d > TF(0) ? TF(1) / d : TF(1); };
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
   TF R[4][4];
-  if (!pivot_warp) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = tr + 16 * a, c = tc + 16 * b;
-        // column 0 is final from the start: it restarts as Xi at once
-        R[a][b] = (c == 0 && i > 0) ? TF(0) : Ls[i][c];
-      }
-    if (threadIdx.x < 64) {
-      colb[0][threadIdx.x] = Ls[threadIdx.x][0];
-      xrow[0][threadIdx.x] = threadIdx.x == 0 ? TF(1) : TF(0);
+    for (int b = 0; b < 4; ++b) {
+      const int i = tr + 16 * a, c = tc + 16 * b;
+      // column 0 is final from the start: it restarts as Xi at once
+      R[a][b] = (c == 0 && i > 0) ? TF(0) : Ls[i][c];
     }
-  } else {
-    for (int i = lane; i < 64; i += 32) {
-      if constexpr (kDF)
-        dgf[i] = {i < kb ? float(Ls[i][i]) : 1.f, 0.f};
-      else
-        dg[i] = i < kb ? double(Ls[i][i]) : 1.0;
-    }
-    __syncwarp();
-    if (lane == 0) {
-      if constexpr (kDF)
-        s_invf[0] = df_pivot_inverse(dgf[0], flags);
-      else
-        s_inv[0] = pivot_inverse(dg[0], flags);
-    }
+  if (threadIdx.x < 64) {
+    colb[0][threadIdx.x] = Ls[threadIdx.x][0];
+    xrow[0][threadIdx.x] = threadIdx.x == 0 ? TF(1) : TF(0);
   }
+  if (threadIdx.x == 0) pinv[0] = safe_inv(Ls[0][0]);
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
     const int cur = j & 1, nxt = cur ^ 1;
-    if (pivot_warp) {
-      const int i0 = lane, i1 = lane + 32;
-      const bool u0 = i0 > j && i0 < kb, u1 = i1 > j && i1 < kb;
-      const TF f0 = colb[cur][i0], f1 = colb[cur][i1];
-      if constexpr (kDF) {
-        const DF invd = s_invf[j];
-        DF d0 = {0.f, 0.f}, d1 = {0.f, 0.f};
-        if (u0) d0 = df_sub(dgf[i0], df_mul(df_two_prod(float(f0), float(f0)), invd));
-        if (u1) d1 = df_sub(dgf[i1], df_mul(df_two_prod(float(f1), float(f1)), invd));
-        if (u0) dgf[i0] = d0;
-        if (u1) dgf[i1] = d1;
-        if (j + 1 < kb && lane == ((j + 1) & 31)) s_invf[j + 1] = df_pivot_inverse(((j + 1) & 32) ? d1 : d0, flags);
-      } else {
-        const double invd = s_inv[j];
-        double d0 = 0.0, d1 = 0.0;
-        if (u0) d0 = dg[i0] - double(f0) * double(f0) * invd;
-        if (u1) d1 = dg[i1] - double(f1) * double(f1) * invd;
-        if (u0) dg[i0] = d0;
-        if (u1) dg[i1] = d1;
-        if (j + 1 < kb && lane == ((j + 1) & 31)) s_inv[j + 1] = pivot_inverse(((j + 1) & 32) ? d1 : d0, flags);
-      }
-    } else {
-      TF tinv;
-      if constexpr (kDF)
-        tinv = s_invf[j].hi;
-      else
-        tinv = TF(s_inv[j]);
-      TF lij[4], val[4];
+    const TF tinv = pinv[cur];
+    TF lij[4], val[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = tr + 16 * a;
-        lij[a] = i > j ? colb[cur][i] * tinv : TF(0);
-      }
+    for (int a = 0; a < 4; ++a) {
+      const int i = tr + 16 * a;
+      lij[a] = i > j ? colb[cur][i] * tinv : TF(0);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = tc + 16 * b;
+      val[b] = c > j ? colb[cur][c] : xrow[cur][c];  // L update right of j, Gauss-Jordan at or left of j
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) R[a][b] -= lij[a] * val[b];
+    // publish column j+1 (final now), its pivot's reciprocal, and row j+1 of Xi
+    const int jn = j + 1;
+    if (tc == (jn & 15)) {
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const int c = tc + 16 * b;
-        val[b] = c > j ? colb[cur][c] : xrow[cur][c];  // L update right of j, Gauss-Jordan at or left of j
-      }
+        if (16 * b + tc != jn) continue;
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) R[a][b] -= lij[a] * val[b];
-      // publish column j+1 (final now) and row j+1 of Xi for the next step
-      const int jn = j + 1;
-      if (tc == (jn & 15)) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          if (16 * b + tc != jn) continue;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const int i = tr + 16 * a;
-            colb[nxt][i] = R[a][b];
-            if (i > jn) {
-              Ls[i][jn] = R[a][b];
-              R[a][b] = TF(0);  // restarts as Xi_{i, j+1}
-            }
+        for (int a = 0; a < 4; ++a) {
+          const int i = tr + 16 * a;
+          colb[nxt][i] = R[a][b];
+          if (i == jn) pinv[nxt] = safe_inv(R[a][b]);
+          if (i > jn) {
+            Ls[i][jn] = R[a][b];
+            R[a][b] = TF(0);  // restarts as Xi_{i, j+1}
           }
         }
       }
-      if (tr == (jn & 15)) {
+    }
+    if (tr == (jn & 15)) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          if (16 * a + tr != jn) continue;
+      for (int a = 0; a < 4; ++a) {
+        if (16 * a + tr != jn) continue;
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int c = tc + 16 * b;
-            xrow[nxt][c] = c < jn ? R[a][b] : (c == jn ? TF(1) : TF(0));
-          }
+        for (int b = 0; b < 4; ++b) {
+          const int c = tc + 16 * b;
+          xrow[nxt][c] = c < jn ? R[a][b] : (c == jn ? TF(1) : TF(0));
         }
       }
     }
     __syncthreads();
   }
-  if (!pivot_warp) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = tr + 16 * a, c = tc + 16 * b;
-        Xs[i][c] = i > c ? R[a][b] : (i == c ? TF(1) : TF(0));
+    for (int b = 0; b < 4; ++b) {
+      const int i = tr + 16 * a, c = tc + 16 * b;
+      Xs[i][c] = i > c ? R[a][b] : (i == c ? TF(1) : TF(0));
+    }
+  // pivots from the final columns, in FP64 / double-float: warp 0, lane l
+  // keeps rows l and l + 32
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x, i0 = lane, i1 = lane + 32;
+    if constexpr (kDF) {
+      DF d0 = {i0 < kb ? float(Ls[i0][i0]) : 1.f, 0.f}, d1 = {i1 < kb ? float(Ls[i1][i1]) : 1.f, 0.f};
+      for (int j = 0; j < kb; ++j) {
+        const float djh = __shfl_sync(0xffffffffu, j < 32 ? d0.hi : d1.hi, j & 31);
+        const float djl = __shfl_sync(0xffffffffu, j < 32 ? d0.lo : d1.lo, j & 31);
+        const DF inv = df_pivot_inverse({djh, djl}, flags, lane == (j & 31));
+        if (lane == (j & 31)) s_invf[j] = inv;
+        if (i0 > j && i0 < kb) d0 = df_sub(d0, df_mul(df_two_prod(float(Ls[i0][j]), float(Ls[i0][j])), inv));
+        if (i1 > j && i1 < kb) d1 = df_sub(d1, df_mul(df_two_prod(float(Ls[i1][j]), float(Ls[i1][j])), inv));
       }
+      dgf[i0] = d0;
+      dgf[i1] = d1;
+    } else {
+      double d0 = i0 < kb ? double(Ls[i0][i0]) : 1.0, d1 = i1 < kb ? double(Ls[i1][i1]) : 1.0;
+      for (int j = 0; j < kb; ++j) {
+        const double dj = __shfl_sync(0xffffffffu, j < 32 ? d0 : d1, j & 31);
+        const double inv = pivot_inverse(dj, flags, lane == (j & 31));
+        if (lane == (j & 31)) s_inv[j] = inv;
+        if (i0 > j && i0 < kb) d0 -= double(Ls[i0][j]) * double(Ls[i0][j]) * inv;
+        if (i1 > j && i1 < kb) d1 -= double(Ls[i1][j]) * double(Ls[i1][j]) * inv;
+      }
+      dg[i0] = d0;
+      dg[i1] = d1;
+    }
   }
+  __syncthreads();
   if (threadIdx.x < kb) {
     double d, dinv;
     if constexpr (kDF) {
@@ -331,7 +321,6 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     D[fr.first + k0 + threadIdx.x] = d;
     Dinv[fr.first + k0 + threadIdx.x] = dinv;
   }
-  __syncthreads();
   TF *Yf = Y + fr.y_off;
   for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
     const int i = idx % kb, j = idx / kb;
