@@ -768,14 +768,32 @@ __device__ __forceinline__ bool last_of_block(int *ticket, int nch) {
   return s_last;
 }
 
+// Bulk copies (TMA engine, cp.async.bulk) of contiguous global ranges into
+// shared memory, completing on an mbarrier; the waits are bounded in time and
+// report FLAG_WAIT_TIMEOUT.
+__device__ __forceinline__ void bulk_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void bar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
 // Forward level, task (front, r0, j0, slot): rows [r0, r0 + 32*VW) of Y w_P
 // over the pivot columns [j0, j0 + kFwdCols), where w = [r_P; 0] + the
 // children's update vectors (gathered on the fly through the position lists,
-// children in fixed order).  256 threads: 32 row lanes of VW consecutive rows
-// (one 16-byte load per column) x 8 column groups.  Rows < p give y_P (times
-// D^{-1}) into yperm, rows >= p the update vector.  Row blocks with more
-// than kFwdCols columns are split over CTAs (slot >= 0) so the few large
-// fronts near the root still stream Y with the whole GPU.
+// children in fixed order).  The task's column segments of Y (32*VW
+// contiguous rows each, 16-byte aligned since ldy is a multiple of 4) are
+// bulk-copied into shared memory at once while the threads gather w; then
+// 256 threads: 32 row lanes of VW consecutive rows x 8 column groups.  Rows
+// < p give y_P (times D^{-1}) into yperm, rows >= p the update vector.  Row
+// blocks with more than kFwdCols columns are split over CTAs (slot >= 0) so
+// the few large fronts near the root still stream Y with the whole GPU.
 template <typename TF, typename TV>
 __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
@@ -784,18 +802,33 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
                                                   const int32_t *__restrict__ wsrc_ptr,
                                                   const int32_t *__restrict__ wsrc, const TV *__restrict__ r,
                                                   TV *__restrict__ ubuf, TV *__restrict__ yperm,
-                                                  TV *__restrict__ part, int *__restrict__ tickets) {
+                                                  TV *__restrict__ part, int *__restrict__ tickets, int *flags) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int RB = 32 * VW;
+  extern __shared__ __align__(128) unsigned char fsm[];
+  TF *ys = reinterpret_cast<TF *>(fsm);  // [kFwdCols][RB]
   __shared__ TV gpart[8 * RB];
   __shared__ TV wp[kFwdCols];
+  __shared__ __align__(8) uint64_t bar;
   const int4 t = tasks[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t r0 = t.y, j0 = t.z, slot = t.w;
   const int32_t p = fr.npiv, m = fr.m;
   const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
   const int32_t j1 = (j0 + kFwdCols < jmax) ? j0 + kFwdCols : jmax;
+  const int32_t nrow = (fr.ldy - r0 < RB) ? fr.ldy - r0 : RB;
+  const uint32_t bar_a = smem_u32(&bar);
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
+      bar_init(bar_a);
+      bulk_expect(bar_a, uint32_t(j1 - j0) * uint32_t(nrow) * sizeof(TF));
+    }
+    __syncwarp();
+    const TF *src = Y + fr.y_off + r0;
+    for (int32_t j = j0 + threadIdx.x; j < j1; j += 32)
+      bulk_copy(smem_u32(ys + (j - j0) * RB), src + int64_t(j) * fr.ldy, uint32_t(nrow) * sizeof(TF), bar_a);
+  }
   for (int32_t j = j0 + threadIdx.x; j < j1; j += 256) {
     const int64_t q0 = wsrc_ptr[fr.w_off + j], q1 = wsrc_ptr[fr.w_off + j + 1];
     TV w = r[perm[fr.first + j]];
@@ -803,33 +836,36 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
     wp[j - j0] = w;
   }
   __syncthreads();
+  const bool ok = __syncthreads_and(mbar_wait(bar_a, 0)) != 0;
   const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int32_t row = r0 + VW * rl;
   TV acc[VW];
 #pragma unroll
   for (int e = 0; e < VW; ++e) acc[e] = TV(0);
-  if (row < m) {
-    const TF *yc = Y + fr.y_off + row;
-    int32_t j = j0 + g;
-    for (; j + 24 < j1; j += 32) {
-      V v0 = *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy);
-      V v1 = *reinterpret_cast<const V *>(yc + int64_t(j + 8) * fr.ldy);
-      V v2 = *reinterpret_cast<const V *>(yc + int64_t(j + 16) * fr.ldy);
-      V v3 = *reinterpret_cast<const V *>(yc + int64_t(j + 24) * fr.ldy);
+  if (ok && row < m) {
+    const TF *yc = ys + VW * rl;
+    int32_t jj = g;
+    const int32_t nj = j1 - j0;
+    for (; jj + 24 < nj; jj += 32) {
+      const V v0 = *reinterpret_cast<const V *>(yc + jj * RB);
+      const V v1 = *reinterpret_cast<const V *>(yc + (jj + 8) * RB);
+      const V v2 = *reinterpret_cast<const V *>(yc + (jj + 16) * RB);
+      const V v3 = *reinterpret_cast<const V *>(yc + (jj + 24) * RB);
       const TF *e0 = reinterpret_cast<const TF *>(&v0), *e1 = reinterpret_cast<const TF *>(&v1);
       const TF *e2 = reinterpret_cast<const TF *>(&v2), *e3 = reinterpret_cast<const TF *>(&v3);
-      const TV w0 = wp[j - j0], w1 = wp[j + 8 - j0], w2 = wp[j + 16 - j0], w3 = wp[j + 24 - j0];
+      const TV w0 = wp[jj], w1 = wp[jj + 8], w2 = wp[jj + 16], w3 = wp[jj + 24];
 #pragma unroll
       for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0 + TV(e1[e]) * w1 + TV(e2[e]) * w2 + TV(e3[e]) * w3;
     }
-    for (; j < j1; j += 8) {
-      V v0 = *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy);
+    for (; jj < nj; jj += 8) {
+      const V v0 = *reinterpret_cast<const V *>(yc + jj * RB);
       const TF *e0 = reinterpret_cast<const TF *>(&v0);
-      const TV w0 = wp[j - j0];
+      const TV w0 = wp[jj];
 #pragma unroll
       for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0;
     }
   }
+  if (!ok && threadIdx.x == 0) atomicOr(flags, FLAG_WAIT_TIMEOUT);
 #pragma unroll
   for (int e = 0; e < VW; ++e) gpart[g * RB + VW * rl + e] = acc[e];
   __syncthreads();
@@ -877,62 +913,87 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
 }
 
 // Backward level, task (front, c0, i0, slot): pivot columns [c0, c0 + 32)
-// over the rows [i0, i0 + kBwdRows); warp w owns columns c0 + w + 8k
-// (k = 0..3) and streams them together (four 16-byte loads in flight per
-// lane).  x = [D^{-1} y_P; z_U] is staged in shared memory from the
-// VW-aligned row at or below c0; rows above a column are zeros of L^{-1}, so
-// reading from the aligned row is exact.  Columns longer than kBwdRows rows
-// are split over CTAs (slot >= 0) and combined in row-chunk order.
+// over the rows [i0, i0 + BR), BR = 2 KB / sizeof(TF).  Each column's
+// segment (from the VW-aligned row at or below the column, 16-byte aligned)
+// is bulk-copied into shared memory while the threads stage
+// x = [D^{-1} y_P; z_U]; rows above a column are zeros of L^{-1}, so reading
+// from the aligned row is exact.  Warp w owns columns c0 + w + 8k (k < 4).
+// Columns longer than BR rows are split over CTAs (slot >= 0) and combined
+// in row-chunk order.
 template <typename TF, typename TV>
 __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
                                                   const int32_t *__restrict__ perm,
                                                   const int32_t *__restrict__ upd_rows_old,
                                                   const TV *__restrict__ yperm, TV *__restrict__ z,
-                                                  TV *__restrict__ part, int *__restrict__ tickets) {
+                                                  TV *__restrict__ part, int *__restrict__ tickets, int *flags) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
-  __shared__ __align__(16) TV xs[kBwdRows];
+  constexpr int BR = 2048 / int(sizeof(TF));
+  extern __shared__ __align__(128) unsigned char bsm[];
+  TF *ys = reinterpret_cast<TF *>(bsm);  // [kBwdCols][BR]
+  __shared__ __align__(16) TV xs[BR];
+  __shared__ __align__(8) uint64_t bar;
   const int4 t = tasks[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t c0 = t.y, ilo0 = t.z, slot = t.w;
   const int32_t p = fr.npiv, m = fr.m;
   const int32_t a0 = c0 & ~(VW - 1);
-  const int32_t xa = a0 > ilo0 ? a0 : ilo0;                                 // first row of this task
-  const int32_t xb = (ilo0 + kBwdRows < fr.ldy) ? ilo0 + kBwdRows : fr.ldy;  // end row
+  const int32_t xa = a0 > ilo0 ? a0 : ilo0;                       // first row of this task
+  const int32_t xb = (ilo0 + BR < fr.ldy) ? ilo0 + BR : fr.ldy;  // end row
+  const int32_t ncol = (p - c0 < kBwdCols) ? p - c0 : kBwdCols;
+  const uint32_t bar_a = smem_u32(&bar);
+  if (threadIdx.x < 32) {
+    // bytes of column c0 + k: rows [max(aligned(c0 + k), xa), xb)
+    uint32_t mine = 0;
+    const int32_t jj = threadIdx.x;
+    int32_t st = 0;
+    if (jj < ncol) {
+      const int32_t ja = (c0 + jj) & ~(VW - 1);
+      st = ja > xa ? ja : xa;
+      mine = st < xb ? uint32_t(xb - st) * sizeof(TF) : 0u;
+    }
+    uint32_t total = mine;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    if (threadIdx.x == 0) {
+      bar_init(bar_a);
+      bulk_expect(bar_a, total);
+    }
+    __syncwarp();
+    if (mine)
+      bulk_copy(smem_u32(ys + jj * BR + (st - xa)), Y + fr.y_off + int64_t(c0 + jj) * fr.ldy + st, mine, bar_a);
+  }
   const int32_t *urows = upd_rows_old + fr.rows_off;
   for (int32_t tt = threadIdx.x; tt < xb - xa; tt += 256) {
     const int32_t i = xa + tt;
     xs[tt] = (i < c0 || i >= m) ? TV(0) : (i < p ? yperm[fr.first + i] : z[urows[i - p]]);
   }
   __syncthreads();
+  const bool ok = __syncthreads_and(mbar_wait(bar_a, 0)) != 0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t jc[4];
-  const TF *yc[4];
-  int32_t ist[4];
+  int32_t jc[4], ist[4];
   TV acc[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     jc[k] = c0 + w + 8 * k;
-    const int32_t j = jc[k] < p ? jc[k] : c0;  // out-of-range columns read a valid one, result dropped
-    yc[k] = Y + fr.y_off + int64_t(j) * fr.ldy;
-    const int32_t ja = j & ~(VW - 1);
-    ist[k] = (ja > xa ? ja : xa) + VW * lane;
+    const int32_t ja = jc[k] & ~(VW - 1);
+    ist[k] = (jc[k] < p && ok) ? (ja > xa ? ja : xa) + VW * lane : xb;  // out-of-range columns do nothing
     acc[k] = TV(0);
   }
-  const int32_t ilo = ist[0] < ist[3] ? ist[0] : ist[3];
-  for (int32_t off = 0; ilo + off < xb; off += 32 * VW) {
+  for (int32_t off = 0; off < xb - xa; off += 32 * VW) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int32_t i = ist[k] + off;
       if (i < xb) {
-        V v = *reinterpret_cast<const V *>(yc[k] + i);
+        const V v = *reinterpret_cast<const V *>(ys + (w + 8 * k) * BR + (i - xa));
         const TF *e = reinterpret_cast<const TF *>(&v);
 #pragma unroll
         for (int q = 0; q < VW; ++q) acc[k] += TV(e[q]) * xs[i - xa + q];
       }
     }
   }
+  if (!ok && threadIdx.x == 0) atomicOr(flags, FLAG_WAIT_TIMEOUT);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
 #pragma unroll
@@ -946,11 +1007,11 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
     }
     return;
   }
-  const int32_t k_first = a0 / kBwdRows;
-  const int nch = (fr.ldy - 1) / kBwdRows - k_first + 1;
+  const int32_t k_first = a0 / BR;
+  const int nch = (fr.ldy - 1) / BR - k_first + 1;
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) part[int64_t(slot + ilo0 / kBwdRows - k_first) * kBwdCols + w + 8 * k] = acc[k];
+    for (int k = 0; k < 4; ++k) part[int64_t(slot + ilo0 / BR - k_first) * kBwdCols + w + 8 * k] = acc[k];
   }
   if (!last_of_block(tickets + slot, nch)) return;
   if (threadIdx.x < kBwdCols) {
@@ -1017,18 +1078,23 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
                               TV *part_f, TV *part_b, int *tick_f, int *tick_b, cudaStream_t s) {
   const TF *Y = reinterpret_cast<const TF *>(d->Y[buf]);
   const double *Dinv = d->D[buf] + c->n_free;
+  constexpr int RB = 32 * Vec16<TF>::n;
+  constexpr size_t fsm = size_t(kFwdCols) * RB * sizeof(TF);
+  constexpr size_t bsm = size_t(kBwdCols) * 2048;
+  cudaFuncSetAttribute(fwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm));
+  cudaFuncSetAttribute(bwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bsm));
   d->launches += 2 * int64_t(d->lt.size());
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
-    fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, 0, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
-                                                         d->fronts, Y, Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp,
-                                                         part_f, tick_f);
+    fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, fsm, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
+                                                           d->fronts, Y, Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u,
+                                                           yp, part_f, tick_f, d->flags);
   }
   for (size_t lv = d->lt.size(); lv-- > 0;) {
     const auto &L = d->lt[lv];
-    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, 0, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
-                                                         d->fronts, Y, d->perm, d->upd_rows_old, yp, z, part_b,
-                                                         tick_b);
+    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, bsm, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
+                                                           d->fronts, Y, d->perm, d->upd_rows_old, yp, z, part_b,
+                                                           tick_b, d->flags);
   }
 }
 
