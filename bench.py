@@ -278,6 +278,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default=None,
+                    help="override the workload's precision (default: the workload's own)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -302,6 +304,8 @@ def main():
     if args.workload == "batch64":
         return run_batch(args, world, rank, local, torch, dist)
     wl = fi.workload(args.workload)
+    if args.precision is not None:
+        wl.precision = 1 if args.precision == "mixed" else 0
     K, W = args.steps, args.warmup
     stream = torch.cuda.Stream()
     dev = torch.device("cuda", local)
@@ -397,7 +401,7 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+f64" if wl.precision else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_dof": n, "elements": wl.mesh.n_elems,
                    "nnz": info["nnz"], "material": MATERIAL_NAMES[wl.model],
                    "precision": "mixed" if wl.precision else "fp64",

@@ -162,24 +162,24 @@ __device__ __forceinline__ double pivot_inverse(double d, int *flags, bool repor
 
 // Task (front, k0, kb): LDL^T of the kb x kb diagonal block.  The eliminations
 // run in the factor's type TF with the pivots of the running Schur
-// complement in TF; the pivots D are then recomputed from the final
+// complement in TF; the pivots D are accumulated beside them from the final
 // (unscaled) columns in FP64 (FP64 factor) or double-float (FP32 factor),
-// d_i = a_ii - sum_j F_ij^2 / d_j, and stored in FP64 with their inverses,
-// which also scale the stored L.  The same row operations applied to the
-// identity give L_KK^{-1} (Gauss-Jordan), written into Y[K, K]; L goes back
-// into F.
+// d_i = a_ii - sum_j F_ij^2 / d_j, by a ninth warp (lane l: rows l and
+// l + 32), and stored in FP64 with their inverses, which also scale the
+// stored L.  The same row operations applied to the identity give L_KK^{-1}
+// (Gauss-Jordan), written into Y[K, K]; L goes back into F.
 //
-// 256 threads hold the block in registers: thread (tr, tc) = (tid / 16,
+// Warps 0-7 hold the block in registers: thread (tr, tc) = (tid / 16,
 // tid % 16) owns rows tr + 16a and columns tc + 16b (a, b < 4).  An entry
 // (i, c) holds L_ic until its column is final (after step c - 1), is then
 // saved and restarts as the Gauss-Jordan entry Xi_ic, so one register and one
 // FMA per entry and step serve both.  At step j the pivot column F_:j, its
 // pivot's reciprocal and the Gauss-Jordan row Xi_j: come from
 // double-buffered shared vectors written by their owners at step j - 1: one
-// barrier per pivot, and no FP64 or double-float work on that serial path
+// barrier per pivot, and no FP64 or double-float work gates the next step
 // (GB300's FP64 pipe issues a warp instruction only every ~64 cycles per SM
 // sub-partition).
-constexpr int kDiagThreads = 256;
+constexpr int kDiagThreads = 288;
 
 template <typename TF>
 __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t *__restrict__ tasks,
@@ -206,7 +206,9 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
   }
   __syncthreads();
   auto safe_inv = [](TF d) { return d > TF(0) ? TF(1) / d : TF(1); };
-  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  const bool pivot_warp = threadIdx.x >= 256;
+  const int lane = threadIdx.x & 31;
+  const int tr = (threadIdx.x & 255) >> 4, tc = threadIdx.x & 15;
   TF R[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -221,90 +223,106 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     xrow[0][threadIdx.x] = threadIdx.x == 0 ? TF(1) : TF(0);
   }
   if (threadIdx.x == 0) pinv[0] = safe_inv(Ls[0][0]);
+  // pivot warp: lane l keeps rows l and l + 32 in FP64 / double-float
+  DF p0 = {1.f, 0.f}, p1 = {1.f, 0.f};
+  double q0 = 1.0, q1 = 1.0;
+  if (pivot_warp) {
+    if constexpr (kDF) {
+      p0 = {lane < kb ? float(Ls[lane][lane]) : 1.f, 0.f};
+      p1 = {lane + 32 < kb ? float(Ls[lane + 32][lane + 32]) : 1.f, 0.f};
+    } else {
+      q0 = lane < kb ? double(Ls[lane][lane]) : 1.0;
+      q1 = lane + 32 < kb ? double(Ls[lane + 32][lane + 32]) : 1.0;
+    }
+  }
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
     const int cur = j & 1, nxt = cur ^ 1;
-    const TF tinv = pinv[cur];
-    TF lij[4], val[4];
+    if (pivot_warp) {
+      // fold column j (final, unscaled) into the pivots of rows > j; runs
+      // beside the elimination, which uses the FP32 pivots
+      const int i0 = lane, i1 = lane + 32;
+      const TF f0 = colb[cur][i0], f1 = colb[cur][i1];
+      if constexpr (kDF) {
+        const float djh = __shfl_sync(0xffffffffu, j < 32 ? p0.hi : p1.hi, j & 31);
+        const float djl = __shfl_sync(0xffffffffu, j < 32 ? p0.lo : p1.lo, j & 31);
+        const DF inv = df_pivot_inverse({djh, djl}, flags, lane == (j & 31));
+        if (lane == (j & 31)) s_invf[j] = inv;
+        if (i0 > j && i0 < kb) p0 = df_sub(p0, df_mul(df_two_prod(float(f0), float(f0)), inv));
+        if (i1 > j && i1 < kb) p1 = df_sub(p1, df_mul(df_two_prod(float(f1), float(f1)), inv));
+      } else {
+        const double dj = __shfl_sync(0xffffffffu, j < 32 ? q0 : q1, j & 31);
+        const double inv = pivot_inverse(dj, flags, lane == (j & 31));
+        if (lane == (j & 31)) s_inv[j] = inv;
+        if (i0 > j && i0 < kb) q0 -= double(f0) * double(f0) * inv;
+        if (i1 > j && i1 < kb) q1 -= double(f1) * double(f1) * inv;
+      }
+    } else {
+      const TF tinv = pinv[cur];
+      TF lij[4], val[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int i = tr + 16 * a;
-      lij[a] = i > j ? colb[cur][i] * tinv : TF(0);
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int c = tc + 16 * b;
-      val[b] = c > j ? colb[cur][c] : xrow[cur][c];  // L update right of j, Gauss-Jordan at or left of j
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) R[a][b] -= lij[a] * val[b];
-    // publish column j+1 (final now), its pivot's reciprocal, and row j+1 of Xi
-    const int jn = j + 1;
-    if (tc == (jn & 15)) {
+      for (int a = 0; a < 4; ++a) {
+        const int i = tr + 16 * a;
+        lij[a] = i > j ? colb[cur][i] * tinv : TF(0);
+      }
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        if (16 * b + tc != jn) continue;
+        const int c = tc + 16 * b;
+        val[b] = c > j ? colb[cur][c] : xrow[cur][c];  // L update right of j, Gauss-Jordan at or left of j
+      }
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int i = tr + 16 * a;
-          colb[nxt][i] = R[a][b];
-          if (i == jn) pinv[nxt] = safe_inv(R[a][b]);
-          if (i > jn) {
-            Ls[i][jn] = R[a][b];
-            R[a][b] = TF(0);  // restarts as Xi_{i, j+1}
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) R[a][b] -= lij[a] * val[b];
+      // publish column j+1 (final now), its pivot's reciprocal, and row j+1 of Xi
+      const int jn = j + 1;
+      if (tc == (jn & 15)) {
+        const int bs = jn >> 4;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (b != bs) continue;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = tr + 16 * a;
+            colb[nxt][i] = R[a][b];
+            if (i == jn) pinv[nxt] = safe_inv(R[a][b]);
+            if (i > jn) {
+              Ls[i][jn] = R[a][b];
+              R[a][b] = TF(0);  // restarts as Xi_{i, j+1}
+            }
           }
         }
       }
-    }
-    if (tr == (jn & 15)) {
+      if (tr == (jn & 15)) {
+        const int as = jn >> 4;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        if (16 * a + tr != jn) continue;
+        for (int a = 0; a < 4; ++a) {
+          if (a != as) continue;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int c = tc + 16 * b;
-          xrow[nxt][c] = c < jn ? R[a][b] : (c == jn ? TF(1) : TF(0));
+          for (int b = 0; b < 4; ++b) {
+            const int c = tc + 16 * b;
+            xrow[nxt][c] = c < jn ? R[a][b] : (c == jn ? TF(1) : TF(0));
+          }
         }
       }
     }
     __syncthreads();
   }
+  if (!pivot_warp) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = tr + 16 * a, c = tc + 16 * b;
-      Xs[i][c] = i > c ? R[a][b] : (i == c ? TF(1) : TF(0));
-    }
-  // pivots from the final columns, in FP64 / double-float: warp 0, lane l
-  // keeps rows l and l + 32
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x, i0 = lane, i1 = lane + 32;
+      for (int b = 0; b < 4; ++b) {
+        const int i = tr + 16 * a, c = tc + 16 * b;
+        Xs[i][c] = i > c ? R[a][b] : (i == c ? TF(1) : TF(0));
+      }
+  } else {
     if constexpr (kDF) {
-      DF d0 = {i0 < kb ? float(Ls[i0][i0]) : 1.f, 0.f}, d1 = {i1 < kb ? float(Ls[i1][i1]) : 1.f, 0.f};
-      for (int j = 0; j < kb; ++j) {
-        const float djh = __shfl_sync(0xffffffffu, j < 32 ? d0.hi : d1.hi, j & 31);
-        const float djl = __shfl_sync(0xffffffffu, j < 32 ? d0.lo : d1.lo, j & 31);
-        const DF inv = df_pivot_inverse({djh, djl}, flags, lane == (j & 31));
-        if (lane == (j & 31)) s_invf[j] = inv;
-        if (i0 > j && i0 < kb) d0 = df_sub(d0, df_mul(df_two_prod(float(Ls[i0][j]), float(Ls[i0][j])), inv));
-        if (i1 > j && i1 < kb) d1 = df_sub(d1, df_mul(df_two_prod(float(Ls[i1][j]), float(Ls[i1][j])), inv));
-      }
-      dgf[i0] = d0;
-      dgf[i1] = d1;
+      dgf[lane] = p0;
+      dgf[lane + 32] = p1;
     } else {
-      double d0 = i0 < kb ? double(Ls[i0][i0]) : 1.0, d1 = i1 < kb ? double(Ls[i1][i1]) : 1.0;
-      for (int j = 0; j < kb; ++j) {
-        const double dj = __shfl_sync(0xffffffffu, j < 32 ? d0 : d1, j & 31);
-        const double inv = pivot_inverse(dj, flags, lane == (j & 31));
-        if (lane == (j & 31)) s_inv[j] = inv;
-        if (i0 > j && i0 < kb) d0 -= double(Ls[i0][j]) * double(Ls[i0][j]) * inv;
-        if (i1 > j && i1 < kb) d1 -= double(Ls[i1][j]) * double(Ls[i1][j]) * inv;
-      }
-      dg[i0] = d0;
-      dg[i1] = d1;
+      dg[lane] = q0;
+      dg[lane + 32] = q1;
     }
   }
   __syncthreads();
