@@ -786,32 +786,24 @@ __device__ __forceinline__ bool last_of_block(int *ticket, int nch) {
   return s_last;
 }
 
-// Bulk copies (TMA engine, cp.async.bulk) of contiguous global ranges into
-// shared memory, completing on an mbarrier; the waits are bounded in time and
-// report FLAG_WAIT_TIMEOUT.
-__device__ __forceinline__ void bulk_expect(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+// element q of a 16-byte vector held in registers (q is a compile-time
+// constant after unrolling, so no address is taken)
+__device__ __forceinline__ float vget(const float4 &v, int q) {
+  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
 }
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void bar_init(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
+__device__ __forceinline__ double vget(const double2 &v, int q) { return q == 0 ? v.x : v.y; }
 
 // Forward level, task (front, r0, j0, slot): rows [r0, r0 + 32*VW) of Y w_P
 // over the pivot columns [j0, j0 + kFwdCols), where w = [r_P; 0] + the
 // children's update vectors (gathered on the fly through the position lists,
-// children in fixed order).  The task's column segments of Y (32*VW
-// contiguous rows each, 16-byte aligned since ldy is a multiple of 4) are
-// bulk-copied into shared memory at once while the threads gather w; then
-// 256 threads: 32 row lanes of VW consecutive rows x 8 column groups.  Rows
-// < p give y_P (times D^{-1}) into yperm, rows >= p the update vector.  Row
-// blocks with more than kFwdCols columns are split over CTAs (slot >= 0) so
-// the few large fronts near the root still stream Y with the whole GPU.
+// children in fixed order).  256 threads: 32 row lanes of VW consecutive
+// rows (one 16-byte load per column) x 8 column groups of 16 columns.  Every
+// thread issues all its loads of Y (16 vectors) before the gathers of w and
+// of the epilogue's child sums, so a CTA exposes about one memory latency
+// instead of one per dependent phase.  Rows < p give y_P (times D^{-1}) into
+// yperm, rows >= p the update vector.  Row blocks with more than kFwdCols
+// columns are split over CTAs (slot >= 0) so the few large fronts near the
+// root still stream Y with the whole GPU.
 template <typename TF, typename TV>
 __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
@@ -820,32 +812,29 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
                                                   const int32_t *__restrict__ wsrc_ptr,
                                                   const int32_t *__restrict__ wsrc, const TV *__restrict__ r,
                                                   TV *__restrict__ ubuf, TV *__restrict__ yperm,
-                                                  TV *__restrict__ part, int *__restrict__ tickets, int *flags) {
+                                                  TV *__restrict__ part, int *__restrict__ tickets) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int RB = 32 * VW;
-  extern __shared__ __align__(128) unsigned char fsm[];
-  TF *ys = reinterpret_cast<TF *>(fsm);  // [kFwdCols][RB]
+  constexpr int NS = kFwdCols / 8;  // columns per warp
   __shared__ TV gpart[8 * RB];
   __shared__ TV wp[kFwdCols];
-  __shared__ __align__(8) uint64_t bar;
   const int4 t = tasks[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t r0 = t.y, j0 = t.z, slot = t.w;
   const int32_t p = fr.npiv, m = fr.m;
   const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
   const int32_t j1 = (j0 + kFwdCols < jmax) ? j0 + kFwdCols : jmax;
-  const int32_t nrow = (fr.ldy - r0 < RB) ? fr.ldy - r0 : RB;
-  const uint32_t bar_a = smem_u32(&bar);
-  if (threadIdx.x < 32) {
-    if (threadIdx.x == 0) {
-      bar_init(bar_a);
-      bulk_expect(bar_a, uint32_t(j1 - j0) * uint32_t(nrow) * sizeof(TF));
+  const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int32_t row = r0 + VW * rl;
+  V yv[NS];
+  {
+    const TF *yc = Y + fr.y_off + row;
+#pragma unroll
+    for (int s2 = 0; s2 < NS; ++s2) {
+      const int32_t j = j0 + g + 8 * s2;
+      yv[s2] = (row < m && j < j1) ? *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy) : V{};
     }
-    __syncwarp();
-    const TF *src = Y + fr.y_off + r0;
-    for (int32_t j = j0 + threadIdx.x; j < j1; j += 32)
-      bulk_copy(smem_u32(ys + (j - j0) * RB), src + int64_t(j) * fr.ldy, uint32_t(nrow) * sizeof(TF), bar_a);
   }
   for (int32_t j = j0 + threadIdx.x; j < j1; j += 256) {
     const int64_t q0 = wsrc_ptr[fr.w_off + j], q1 = wsrc_ptr[fr.w_off + j + 1];
@@ -853,37 +842,25 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
     for (int64_t q = q0; q < q1; ++q) w += ubuf[wsrc[q]];
     wp[j - j0] = w;
   }
+  // the epilogue's child contributions (rows >= p), also ahead of the FMAs
+  TV csum = TV(0);
+  const bool last_chunk = j1 == jmax;
+  if (threadIdx.x < RB && last_chunk) {
+    const int32_t i = r0 + threadIdx.x;
+    if (i >= p && i < m)
+      for (int64_t q = wsrc_ptr[fr.w_off + i]; q < wsrc_ptr[fr.w_off + i + 1]; ++q) csum += ubuf[wsrc[q]];
+  }
   __syncthreads();
-  const bool ok = __syncthreads_and(mbar_wait(bar_a, 0)) != 0;
-  const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int32_t row = r0 + VW * rl;
   TV acc[VW];
 #pragma unroll
   for (int e = 0; e < VW; ++e) acc[e] = TV(0);
-  if (ok && row < m) {
-    const TF *yc = ys + VW * rl;
-    int32_t jj = g;
-    const int32_t nj = j1 - j0;
-    for (; jj + 24 < nj; jj += 32) {
-      const V v0 = *reinterpret_cast<const V *>(yc + jj * RB);
-      const V v1 = *reinterpret_cast<const V *>(yc + (jj + 8) * RB);
-      const V v2 = *reinterpret_cast<const V *>(yc + (jj + 16) * RB);
-      const V v3 = *reinterpret_cast<const V *>(yc + (jj + 24) * RB);
-      const TF *e0 = reinterpret_cast<const TF *>(&v0), *e1 = reinterpret_cast<const TF *>(&v1);
-      const TF *e2 = reinterpret_cast<const TF *>(&v2), *e3 = reinterpret_cast<const TF *>(&v3);
-      const TV w0 = wp[jj], w1 = wp[jj + 8], w2 = wp[jj + 16], w3 = wp[jj + 24];
 #pragma unroll
-      for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0 + TV(e1[e]) * w1 + TV(e2[e]) * w2 + TV(e3[e]) * w3;
-    }
-    for (; jj < nj; jj += 8) {
-      const V v0 = *reinterpret_cast<const V *>(yc + jj * RB);
-      const TF *e0 = reinterpret_cast<const TF *>(&v0);
-      const TV w0 = wp[jj];
+  for (int s2 = 0; s2 < NS; ++s2) {
+    const int jj = g + 8 * s2;
+    const TV w = jj < j1 - j0 ? wp[jj] : TV(0);
 #pragma unroll
-      for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0;
-    }
+    for (int q = 0; q < VW; ++q) acc[q] += TV(vget(yv[s2], q)) * w;
   }
-  if (!ok && threadIdx.x == 0) atomicOr(flags, FLAG_WAIT_TIMEOUT);
 #pragma unroll
   for (int e = 0; e < VW; ++e) gpart[g * RB + VW * rl + e] = acc[e];
   __syncthreads();
@@ -906,6 +883,12 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
       if (tt < RB) part[int64_t(slot + j0 / kFwdCols) * RB + tt] = sums[k];
     }
     if (!last_of_block(tickets + slot, nch)) return;
+    // the last CTA may not be the one that gathered csum: gather again
+    if (!last_chunk && threadIdx.x < RB) {
+      const int32_t i = r0 + threadIdx.x;
+      if (i >= p && i < m)
+        for (int64_t q = wsrc_ptr[fr.w_off + i]; q < wsrc_ptr[fr.w_off + i + 1]; ++q) csum += ubuf[wsrc[q]];
+    }
 #pragma unroll
     for (int k = 0; k < (RB + 255) / 256; ++k) {
       const int tt = threadIdx.x + 256 * k;
@@ -920,38 +903,33 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
     const int tt = threadIdx.x + 256 * k;
     const int32_t i = r0 + tt;
     if (tt >= RB || i >= m) continue;
-    if (i < p) {
+    if (i < p)
       yperm[fr.first + i] = TV(double(sums[k]) * Dinv[fr.first + i]);
-    } else {
-      TV w = TV(0);
-      for (int64_t q = wsrc_ptr[fr.w_off + i]; q < wsrc_ptr[fr.w_off + i + 1]; ++q) w += ubuf[wsrc[q]];
-      ubuf[fr.u_off + i - p] = w + sums[k];
-    }
+    else
+      ubuf[fr.u_off + i - p] = csum + sums[k];
   }
 }
 
 // Backward level, task (front, c0, i0, slot): pivot columns [c0, c0 + 32)
-// over the rows [i0, i0 + BR), BR = 2 KB / sizeof(TF).  Each column's
-// segment (from the VW-aligned row at or below the column, 16-byte aligned)
-// is bulk-copied into shared memory while the threads stage
-// x = [D^{-1} y_P; z_U]; rows above a column are zeros of L^{-1}, so reading
-// from the aligned row is exact.  Warp w owns columns c0 + w + 8k (k < 4).
-// Columns longer than BR rows are split over CTAs (slot >= 0) and combined
-// in row-chunk order.
+// over the rows [i0, i0 + BR), BR = 2 KB / sizeof(TF), from the VW-aligned
+// row at or below each column (rows above a column are zeros of L^{-1}, so
+// reading from the aligned row is exact).  Warp w owns columns c0 + w + 8k
+// (k < 4); every lane issues all its loads of Y (4 columns x 4 vectors)
+// before x = [D^{-1} y_P; z_U] is staged in shared memory.  Columns longer
+// than BR rows are split over CTAs (slot >= 0) and combined in row-chunk
+// order.
 template <typename TF, typename TV>
 __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
                                                   const int32_t *__restrict__ perm,
                                                   const int32_t *__restrict__ upd_rows_old,
                                                   const TV *__restrict__ yperm, TV *__restrict__ z,
-                                                  TV *__restrict__ part, int *__restrict__ tickets, int *flags) {
+                                                  TV *__restrict__ part, int *__restrict__ tickets) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int BR = 2048 / int(sizeof(TF));
-  extern __shared__ __align__(128) unsigned char bsm[];
-  TF *ys = reinterpret_cast<TF *>(bsm);  // [kBwdCols][BR]
+  constexpr int NI = BR / (32 * VW);  // vectors per lane and column
   __shared__ __align__(16) TV xs[BR];
-  __shared__ __align__(8) uint64_t bar;
   const int4 t = tasks[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t c0 = t.y, ilo0 = t.z, slot = t.w;
@@ -959,28 +937,20 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
   const int32_t a0 = c0 & ~(VW - 1);
   const int32_t xa = a0 > ilo0 ? a0 : ilo0;                       // first row of this task
   const int32_t xb = (ilo0 + BR < fr.ldy) ? ilo0 + BR : fr.ldy;  // end row
-  const int32_t ncol = (p - c0 < kBwdCols) ? p - c0 : kBwdCols;
-  const uint32_t bar_a = smem_u32(&bar);
-  if (threadIdx.x < 32) {
-    // bytes of column c0 + k: rows [max(aligned(c0 + k), xa), xb)
-    uint32_t mine = 0;
-    const int32_t jj = threadIdx.x;
-    int32_t st = 0;
-    if (jj < ncol) {
-      const int32_t ja = (c0 + jj) & ~(VW - 1);
-      st = ja > xa ? ja : xa;
-      mine = st < xb ? uint32_t(xb - st) * sizeof(TF) : 0u;
-    }
-    uint32_t total = mine;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t jc[4], ist[4];
+  V yv[4][NI];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-    if (threadIdx.x == 0) {
-      bar_init(bar_a);
-      bulk_expect(bar_a, total);
+  for (int k = 0; k < 4; ++k) {
+    jc[k] = c0 + w + 8 * k;
+    const int32_t ja = jc[k] & ~(VW - 1);
+    ist[k] = jc[k] < p ? (ja > xa ? ja : xa) + VW * lane : xb;  // out-of-range columns do nothing
+    const TF *yc = Y + fr.y_off + int64_t(jc[k] < p ? jc[k] : c0) * fr.ldy;
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      const int32_t i = ist[k] + 32 * VW * it;
+      yv[k][it] = i < xb ? *reinterpret_cast<const V *>(yc + i) : V{};
     }
-    __syncwarp();
-    if (mine)
-      bulk_copy(smem_u32(ys + jj * BR + (st - xa)), Y + fr.y_off + int64_t(c0 + jj) * fr.ldy + st, mine, bar_a);
   }
   const int32_t *urows = upd_rows_old + fr.rows_off;
   for (int32_t tt = threadIdx.x; tt < xb - xa; tt += 256) {
@@ -988,30 +958,19 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
     xs[tt] = (i < c0 || i >= m) ? TV(0) : (i < p ? yperm[fr.first + i] : z[urows[i - p]]);
   }
   __syncthreads();
-  const bool ok = __syncthreads_and(mbar_wait(bar_a, 0)) != 0;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t jc[4], ist[4];
   TV acc[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    jc[k] = c0 + w + 8 * k;
-    const int32_t ja = jc[k] & ~(VW - 1);
-    ist[k] = (jc[k] < p && ok) ? (ja > xa ? ja : xa) + VW * lane : xb;  // out-of-range columns do nothing
     acc[k] = TV(0);
-  }
-  for (int32_t off = 0; off < xb - xa; off += 32 * VW) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int32_t i = ist[k] + off;
+    for (int it = 0; it < NI; ++it) {
+      const int32_t i = ist[k] + 32 * VW * it;
       if (i < xb) {
-        const V v = *reinterpret_cast<const V *>(ys + (w + 8 * k) * BR + (i - xa));
-        const TF *e = reinterpret_cast<const TF *>(&v);
 #pragma unroll
-        for (int q = 0; q < VW; ++q) acc[k] += TV(e[q]) * xs[i - xa + q];
+        for (int q = 0; q < VW; ++q) acc[k] += TV(vget(yv[k][it], q)) * xs[i - xa + q];
       }
     }
   }
-  if (!ok && threadIdx.x == 0) atomicOr(flags, FLAG_WAIT_TIMEOUT);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
 #pragma unroll
@@ -1096,23 +1055,18 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
                               TV *part_f, TV *part_b, int *tick_f, int *tick_b, cudaStream_t s) {
   const TF *Y = reinterpret_cast<const TF *>(d->Y[buf]);
   const double *Dinv = d->D[buf] + c->n_free;
-  constexpr int RB = 32 * Vec16<TF>::n;
-  constexpr size_t fsm = size_t(kFwdCols) * RB * sizeof(TF);
-  constexpr size_t bsm = size_t(kBwdCols) * 2048;
-  cudaFuncSetAttribute(fwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsm));
-  cudaFuncSetAttribute(bwd_kernel<TF, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bsm));
   d->launches += 2 * int64_t(d->lt.size());
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
-    fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, fsm, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
-                                                           d->fronts, Y, Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u,
-                                                           yp, part_f, tick_f, d->flags);
+    fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, 0, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
+                                                         d->fronts, Y, Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp,
+                                                         part_f, tick_f);
   }
   for (size_t lv = d->lt.size(); lv-- > 0;) {
     const auto &L = d->lt[lv];
-    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, bsm, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
-                                                           d->fronts, Y, d->perm, d->upd_rows_old, yp, z, part_b,
-                                                           tick_b, d->flags);
+    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, 0, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
+                                                         d->fronts, Y, d->perm, d->upd_rows_old, yp, z, part_b,
+                                                         tick_b);
   }
 }
 
