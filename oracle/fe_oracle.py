@@ -411,6 +411,40 @@ class Model:
         q1 = q + self.h * v1
         return q1, v1, a
 
+    def newton_residual(self, q, v, p, a):
+        """Nonlinear backward-Euler residual of one step at the acceleration a:
+        R(a) = M a + f(q') + (alpha M + beta K(q')) v' - p with v' = v + h a,
+        q' = q + h v' (Eqs. "newton's law" and "implicit integration", the
+        Rayleigh damping taken at the end-of-step configuration), zero on the
+        fixed DOFs."""
+        h, al, be = self.h, self.alpha, self.beta
+        v1 = v + h * a
+        q1 = q + h * v1
+        R = self.M @ a + self.internal_force(q1) + al * (self.M @ v1) + be * (self.stiffness(q1) @ v1) - p
+        R[self.fixed_dofs] = 0.0
+        return R
+
+    def newton_step(self, q, v, p, iters):
+        """Backward Euler by `iters` Newton iterations on newton_residual.
+        Iteration 1 is the paper's linearised step (step()); iteration k > 1
+        solves A(q_k) delta = -R(a_k) with the same matrix form
+        A = (1 + h alpha) M + h (beta + h) K(q_k) at q_k = q + h v + h^2 a_k
+        (the derivative of K in the damping term is not taken) and sets
+        a_{k+1} = a_k + delta.  Returns q+, v+, a and the norms of the
+        corrections."""
+        h = self.h
+        _, _, a = self.step(q, v, p)
+        corr = []
+        for _ in range(1, iters):
+            qk = q + h * v + h * h * a
+            K = self.stiffness(qk)
+            A = project((1.0 + h * self.alpha) * self.M + h * (self.beta + h) * K, self.fixed_dofs)
+            delta = direct_solve(A, -self.newton_residual(q, v, p, a))
+            a = a + delta
+            corr.append(float(np.linalg.norm(delta)))
+        v1 = v + h * a
+        return q + h * v1, v1, a, corr
+
     def pattern(self):
         return csr_pattern(self.n_dof, self.conn, self.fixed_dofs)
 
