@@ -98,13 +98,24 @@ typedef struct {
   int32_t use_graph;      /* 1: replay the PCG iteration as a CUDA graph      */
   int32_t profile_stages; /* 1: time every stage with CUDA events on its own
                              stream (read with fe_get_stage_times)          */
+  int32_t newton_iters;   /* Newton iterations per step (0 or 1: the paper's
+                             single linearisation).  Iteration k > 1 solves
+                             A(q_k) d = p - f(q_k) - (alpha M + beta K(q_k)) v_k
+                             - M a_k at q_k = q + h v + h^2 a_k, v_k = v + h a_k,
+                             then a_{k+1} = a_k + d (lagged preconditioner).
+                             Not combinable with keep_checkpoints.            */
+  double newton_tol;      /* stop the iterations once ||d|| <= newton_tol ||a||
+                             (0: run all newton_iters)                        */
 } fe_options;
 
 typedef struct {
   int32_t iters;          /* PCG iterations of the step (all sweeps)          */
   int32_t refinements;    /* outer FP64 residual sweeps (FE_MIXED), else 1    */
   int32_t factor_age;     /* steps since the preconditioner's matrix          */
-  double rel_residual;    /* final ||b - A a|| / ||b|| (FP64)                 */
+  double rel_residual;    /* final ||b - A a|| / ||b|| (FP64) of the last
+                             linear solve                                     */
+  int32_t newton;         /* Newton iterations done (1: the paper's step)      */
+  double newton_correction; /* ||d|| / ||a|| of the last Newton correction    */
 } fe_step_info;
 
 /* Fills *opt with defaults: FP64, tol 1e-8, max_iters 1000, R = 1, host

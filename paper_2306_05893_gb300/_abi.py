@@ -27,12 +27,13 @@ class FeOptions(ct.Structure):
                 ("stream", ct.c_void_p), ("keep_checkpoints", ct.c_int32),
                 ("nd_leaf_nodes", ct.c_int32), ("inner_tol", ct.c_double),
                 ("factor_timeout_s", ct.c_double), ("use_graph", ct.c_int32),
-                ("profile_stages", ct.c_int32)]
+                ("profile_stages", ct.c_int32), ("newton_iters", ct.c_int32),
+                ("newton_tol", ct.c_double)]
 
 
 class FeStepInfo(ct.Structure):
     _fields_ = [("iters", ct.c_int32), ("refinements", ct.c_int32), ("factor_age", ct.c_int32),
-                ("rel_residual", ct.c_double)]
+                ("rel_residual", ct.c_double), ("newton", ct.c_int32), ("newton_correction", ct.c_double)]
 
 
 class FeInfo(ct.Structure):

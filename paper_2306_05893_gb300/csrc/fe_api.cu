@@ -266,6 +266,11 @@ int ensure_device(fe_ctx *c) {
   FE_TRY(dallocv(c, d, &d->wbuf, size_t(c->w_total) * ts));
   FE_TRY(dallocv(c, d, &d->ubuf, size_t(std::max<int64_t>(c->u_total, 1)) * ts));
   FE_TRY(dallocv(c, d, &d->yperm, size_t(std::max<int64_t>(c->n_free, 1)) * ts));
+  if (c->opt.newton_iters > 1) {
+    FE_TRY(dalloc(c, d, &d->na, size_t(c->n)));
+    FE_TRY(dalloc(c, d, &d->nq, size_t(c->n)));
+    FE_TRY(dalloc(c, d, &d->nv, size_t(c->n)));
+  }
   const size_t rb = mixed(c) ? 128 : 64;
   FE_TRY(dallocv(c, d, &d->part_f, size_t(std::max<int64_t>(c->fwd_slots, 1)) * rb * ts));
   FE_TRY(dallocv(c, d, &d->part_b, size_t(std::max<int64_t>(c->bwd_slots, 1)) * kBwdCols * ts));
@@ -681,7 +686,7 @@ int fe_assemble(fe_ctx *c, const double *p_ext, double *A_vals, double *b) {
   }
   FE_TRY(clear_flags(c));
   launch_element(c, d, d->q, mixed(c), d->stream);
-  launch_assemble(c, d, mixed(c), pd, d->stream);
+  launch_assemble(c, d, mixed(c), pd, d->v, nullptr, c->beta + c->h, d->stream);
   FE_CUDA_TRY(cudaGetLastError());
   if (A_vals) {
     double *tmp = nullptr;
@@ -746,7 +751,7 @@ int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_ste
   }
   {
     Stage st(c, FE_STAGE_ASSEMBLY, s);
-    launch_assemble(c, d, fp32, pd, s);
+    launch_assemble(c, d, fp32, pd, d->v, nullptr, c->beta + c->h, s);
   }
   FE_CUDA_TRY(cudaGetLastError());
   // S4 lagged refactorisation: A_s is factored at s = 0 mod R on the side
@@ -774,6 +779,43 @@ int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_ste
   if (st) {
     // leave the state untouched; a pending factor still completes on its stream
     return st;
+  }
+  // Newton iterations beyond the paper's single linearisation: at
+  // a_k, q_k = q + h v + h^2 a_k, v_k = v + h a_k; solve
+  // A(q_k) delta = p - f(q_k) - (alpha M + beta K(q_k)) v_k - M a_k with the
+  // current (lagged) preconditioner, a_{k+1} = a_k + delta.
+  int newton = 1;
+  double ncorr = 0.0;
+  if (c->opt.newton_iters > 1) {
+    FE_CUDA_TRY(cudaMemcpyAsync(d->na, d->x, c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    fe_step_info sub{};
+    for (int k = 1; k < c->opt.newton_iters; ++k) {
+      launch_newton_state(c, d, d->na, d->nq, d->nv, s);
+      {
+        Stage st(c, FE_STAGE_ELEMENT, s);
+        launch_element(c, d, d->nq, fp32, s);
+      }
+      {
+        Stage st(c, FE_STAGE_ASSEMBLY, s);
+        launch_assemble(c, d, fp32, pd, d->nv, d->na, c->beta, s);
+      }
+      FE_CUDA_TRY(cudaGetLastError());
+      st = solve(c, &sub);
+      if (st) return st;
+      if (info) info->iters += sub.iters;
+      launch_newton_update(c, d, d->x, d->na, s);
+      FE_TRY(read_scalars(c));
+      FE_TRY(flag_status(c));
+      ++newton;
+      ncorr = d->h_scal[S_NA] > 0 ? std::sqrt(d->h_scal[S_NDELTA] / d->h_scal[S_NA]) : 0.0;
+      if (ncorr <= c->opt.newton_tol) break;
+    }
+    FE_CUDA_TRY(cudaMemcpyAsync(d->x, d->na, c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (info) info->rel_residual = sub.rel_residual;
+  }
+  if (info) {
+    info->newton = newton;
+    info->newton_correction = ncorr;
   }
   // S8 backward Euler
   {
@@ -854,7 +896,7 @@ int fe_adjoint(fe_ctx *c, const double *dL_dqT, const double *dL_dvT, double *dL
     d->q = qt;
     d->v = vt;
     launch_element(c, d, qt, fp32, s);
-    launch_assemble(c, d, fp32, nullptr, s);
+    launch_assemble(c, d, fp32, nullptr, d->v, nullptr, c->beta + c->h, s);
     d->q = qsave;
     d->v = vsave;
     // lagged preconditioner for the reverse sweep: A_{T-1}, then every R steps

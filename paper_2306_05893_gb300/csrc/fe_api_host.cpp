@@ -23,6 +23,8 @@ int fe_options_default(fe_options *o) {
   o->inner_tol = 1e-4;
   o->factor_timeout_s = 30.0;
   o->use_graph = 0;
+  o->newton_iters = 1;
+  o->newton_tol = 0.0;
   return FE_OK;
 }
 
@@ -66,6 +68,11 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
     if (!(c->opt.inner_tol > 0)) c->opt.inner_tol = 1e-4;
     if (!(c->opt.factor_timeout_s > 0)) c->opt.factor_timeout_s = 30.0;
     if (c->opt.nd_leaf_nodes <= 0) c->opt.nd_leaf_nodes = 64;
+    if (c->opt.newton_iters <= 0) c->opt.newton_iters = 1;
+    if (c->opt.newton_iters > 1 && c->opt.keep_checkpoints) {
+      delete c;
+      return FE_ERR_ARG;  // the adjoint differentiates the single-linearisation step
+    }
     c->nseg = 1;
     c->seg_node = {0, c->n_nodes};
     c->seg_elem = {0, c->n_elems};

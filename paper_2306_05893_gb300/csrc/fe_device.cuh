@@ -31,7 +31,7 @@ enum { FLAG_INVERTED = 1, FLAG_PIVOT = 2, FLAG_BREAKDOWN = 4, FLAG_WAIT_TIMEOUT 
 // Scalars of the PCG kept on the device (double).
 enum {
   S_RZ = 0, S_RZ_NEW, S_PQ, S_ALPHA, S_BETA, S_RR, S_BB, S_TOL2, S_DONE, S_ITERS,
-  S_ORR, S_OTOL2, S_ODONE,
+  S_ORR, S_OTOL2, S_ODONE, S_NDELTA, S_NA,
   S_COUNT = 16
 };
 
@@ -96,6 +96,7 @@ struct DeviceState {
   void *Y[2] = {nullptr, nullptr}; // apply operators (double-buffered for the lag)
   double *D[2] = {nullptr, nullptr};
   void *wbuf = nullptr, *ubuf = nullptr, *yperm = nullptr;  // apply work vectors
+  double *na = nullptr, *nq = nullptr, *nv = nullptr;       // Newton iterate a_k, q_k, v_k
   void *part_f = nullptr, *part_b = nullptr;                // partial sums of split apply tasks
   int *tick_f = nullptr, *tick_b = nullptr;                 // their tickets (zero between launches)
   int cur = 0;                     // buffer the solver reads
@@ -143,7 +144,14 @@ constexpr int kMaxBlocks = 4096;
 // ------------------------------------------------------------ kernel launchers
 // (fe_kernels.cu)
 void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool fp32, cudaStream_t s);
-void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const double *pext, cudaStream_t s);
+// b = p - f - (alpha M + bh K) v - M w  (w may be NULL); A = (1 + h alpha) M + h (beta + h) K
+void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const double *pext, const double *v,
+                     const double *w, double bh, cudaStream_t s);
+// Newton iterate of the step: qk = q + h v + h^2 a, vk = v + h a
+void launch_newton_state(const fe_ctx *c, const DeviceState *d, const double *a, double *qk, double *vk,
+                         cudaStream_t s);
+// a += delta; S_NDELTA = ||delta||^2, S_NA = ||a||^2
+void launch_newton_update(const fe_ctx *c, const DeviceState *d, const double *delta, double *a, cudaStream_t s);
 // y = A x; S_PQ = x.y; S_ALPHA = S_RZ / S_PQ
 void launch_spmv_dot(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y, cudaStream_t s);
 // r = b - A x (FP64 accumulation); S_ORR, S_ODONE

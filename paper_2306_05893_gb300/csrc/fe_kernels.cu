@@ -289,8 +289,9 @@ __global__ void __launch_bounds__(256) assemble_block_kernel(
     const int32_t *__restrict__ bcol, const int32_t *__restrict__ bsrc_ptr, const int32_t *__restrict__ bsrc,
     const double *__restrict__ bmass, const TK *__restrict__ Ke, const TK *__restrict__ fe,
     const int32_t *__restrict__ node_ptr, const int32_t *__restrict__ node_src,
-    const int8_t *__restrict__ fixed_row, const double *__restrict__ v, const double *__restrict__ p,
-    double cM_, double cK_, double al_, double bh_, TA *__restrict__ A, double *__restrict__ b) {
+    const int8_t *__restrict__ fixed_row, const double *__restrict__ v, const double *__restrict__ w,
+    const double *__restrict__ p, double cM_, double cK_, double al_, double bh_, TA *__restrict__ A,
+    double *__restrict__ b) {
   // TS: type of the block sums (FP64, or FP32 in the mixed path, whose K_e and
   // A are FP32: GB300's FP64 pipe would otherwise bound this kernel); the row
   // partials of b are reduced across the warp in FP64 either way.
@@ -331,6 +332,7 @@ __global__ void __launch_bounds__(256) assemble_block_kernel(
           A[rps[i] + bp + kk] = TA(cM * Ms + cK * Ks);
           acc[i] += (al * Ms + bh * Ks) * vv[kk];
         }
+        if (w) acc[i] += mb * TS(w[cn + i]);  // the M w term of a Newton correction
       }
     }
     TS fs[3] = {TS(0), TS(0), TS(0)};
@@ -355,22 +357,22 @@ __global__ void __launch_bounds__(256) assemble_block_kernel(
   }
 }
 
-void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const double *pext,
-                     cudaStream_t s) {
+void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const double *pext, const double *v,
+                     const double *w, double bh, cudaStream_t s) {
   d->launches++;
   const double h = c->h, al = c->alpha, be = c->beta;
-  const double cM = 1.0 + h * al, cK = h * (be + h), bh = be + h;
+  const double cM = 1.0 + h * al, cK = h * (be + h);
   const int64_t nn = c->n_nodes;
   const unsigned grid = unsigned(std::min<int64_t>((nn + 7) / 8, 152 * 64));
   if (fp32)
     assemble_block_kernel<float, float, float><<<grid, 256, 0, s>>>(
         nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const float *)d->Ke,
-        (const float *)d->fe, d->node_ptr, d->node_src, d->fixed_row, d->v, pext, cM, cK, al, bh,
+        (const float *)d->fe, d->node_ptr, d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh,
         (float *)d->A, d->b);
   else
     assemble_block_kernel<double, double, double><<<grid, 256, 0, s>>>(
         nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const double *)d->Ke,
-        (const double *)d->fe, d->node_ptr, d->node_src, d->fixed_row, d->v, pext, cM, cK, al, bh,
+        (const double *)d->fe, d->node_ptr, d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh,
         (double *)d->A, d->b);
 }
 
@@ -557,6 +559,32 @@ __global__ void integrate_kernel(int64_t n, double h, const double *__restrict__
   }
 }
 
+__global__ void newton_state_kernel(int64_t n, double h, const double *__restrict__ q, const double *__restrict__ v,
+                                    const double *__restrict__ a, double *__restrict__ qk,
+                                    double *__restrict__ vk) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double vn = v[i] + h * a[i];
+    vk[i] = vn;
+    qk[i] = q[i] + h * vn;
+  }
+}
+
+// a += delta with ||delta||^2 and ||a||^2 (two deterministic grid sums)
+__global__ void __launch_bounds__(kRedBlock) newton_update_kernel(int64_t n, const double *__restrict__ delta,
+                                                                  double *__restrict__ a, double *scal,
+                                                                  double *partials, unsigned int *ticket) {
+  double dd = 0.0, aa = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * kRedBlock + threadIdx.x; i < n; i += int64_t(gridDim.x) * kRedBlock) {
+    const double di = delta[i], ai = a[i] + di;
+    a[i] = ai;
+    dd += di * di;
+    aa += ai * ai;
+  }
+  double tot;
+  if (grid_sum<kRedBlock>(dd, partials, ticket, &tot) && threadIdx.x == 0) scal[S_NDELTA] = tot;
+  if (grid_sum<kRedBlock>(aa, partials + gridDim.x, ticket + 1, &tot) && threadIdx.x == 0) scal[S_NA] = tot;
+}
+
 template <typename S, typename D>
 __global__ void convert_kernel(const S *__restrict__ src, D *__restrict__ dst, int64_t n) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
@@ -673,6 +701,17 @@ void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s)
 void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
   d->launches++;
   integrate_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, c->h, d->x, d->v, d->q);
+}
+
+void launch_newton_state(const fe_ctx *c, const DeviceState *d, const double *a, double *qk, double *vk,
+                         cudaStream_t s) {
+  d->launches++;
+  newton_state_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, c->h, d->q, d->v, a, qk, vk);
+}
+
+void launch_newton_update(const fe_ctx *c, const DeviceState *d, const double *delta, double *a, cudaStream_t s) {
+  d->launches++;
+  newton_update_kernel<<<red_grid(c->n), kRedBlock, 0, s>>>(c->n, delta, a, d->scal, d->partials, d->ticket);
 }
 
 void launch_convert(const void *src, bool src32, void *dst, bool dst32, int64_t n, cudaStream_t s) {

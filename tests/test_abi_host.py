@@ -42,6 +42,11 @@ def test_create_rejects_bad_input(fe):
         fe.fe_create(0, mesh.X, conn, mesh.fixed_nodes, 0, 1000.0, [1.0, 1.0, 0.0], 0.01, 0.1, 0.01)
     with pytest.raises(fe.FEError):
         fe.fe_create(0, mesh.X, mesh.conn, mesh.fixed_nodes, 0, 1000.0, [1.0, 1.0, 0.0], -1.0, 0.1, 0.01)
+    # the adjoint differentiates the single-linearisation step only
+    with pytest.raises(fe.FEError) as ei:
+        fe.fe_create(0, mesh.X, mesh.conn, mesh.fixed_nodes, 0, 1000.0, [1.0, 1.0, 0.0], 0.01, 0.1, 0.01,
+                     fe.options(newton_iters=3, keep_checkpoints=1))
+    assert ei.value.status == 1
 
 
 def _ctx(fe, mesh, **kw):
