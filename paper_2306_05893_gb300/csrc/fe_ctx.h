@@ -14,9 +14,8 @@ constexpr int kNB = 64;        // panel width of the front factorisation
 constexpr int kTile = 64;      // tile edge of the front update kernels
 constexpr int kSuper = 256;    // FP32 factor: trailing updates are applied once per kSuper pivots
 constexpr int kBwdCols = 32;   // pivot columns per task of the backward apply
-constexpr int kFwdCols = 128;  // pivot columns per task of the forward apply (split over CTAs)
-// rows per task of the backward apply (split over CTAs): 2 KB of each column
-inline int bwd_rows(int precision) { return precision == FE_MIXED ? 512 : 256; }
+constexpr int kFwdCols = 256;  // pivot columns per task of the forward apply (split over CTAs)
+constexpr int kBwdRows = 1024; // rows per task of the backward apply (split over CTAs)
 inline int fwd_rows(int precision) { return precision == FE_MIXED ? 128 : 64; }  // 32 threads x one 16-byte vector
 
 // Task kinds of the multifrontal factorisation (packed in int4.y >> 24).
@@ -48,7 +47,7 @@ struct Level {
   // apply task lists
   // (front, r0, j0, slot): rows [r0, r0 + fwd_rows) x pivot columns [j0, j0 + kFwdCols)
   std::vector<int32_t> fwd_tasks;
-  // (front, c0, i0, slot): pivot columns [c0, c0 + kBwdCols) x rows [i0, i0 + bwd_rows)
+  // (front, c0, i0, slot): pivot columns [c0, c0 + kBwdCols) x rows [i0, i0 + kBwdRows)
   std::vector<int32_t> bwd_tasks;
 };
 

@@ -786,24 +786,14 @@ __device__ __forceinline__ bool last_of_block(int *ticket, int nch) {
   return s_last;
 }
 
-// element q of a 16-byte vector held in registers (q is a compile-time
-// constant after unrolling, so no address is taken)
-__device__ __forceinline__ float vget(const float4 &v, int q) {
-  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
-}
-__device__ __forceinline__ double vget(const double2 &v, int q) { return q == 0 ? v.x : v.y; }
-
 // Forward level, task (front, r0, j0, slot): rows [r0, r0 + 32*VW) of Y w_P
 // over the pivot columns [j0, j0 + kFwdCols), where w = [r_P; 0] + the
 // children's update vectors (gathered on the fly through the position lists,
-// children in fixed order).  256 threads: 32 row lanes of VW consecutive
-// rows (one 16-byte load per column) x 8 column groups of 16 columns.  Every
-// thread issues all its loads of Y (16 vectors) before the gathers of w and
-// of the epilogue's child sums, so a CTA exposes about one memory latency
-// instead of one per dependent phase.  Rows < p give y_P (times D^{-1}) into
-// yperm, rows >= p the update vector.  Row blocks with more than kFwdCols
-// columns are split over CTAs (slot >= 0) so the few large fronts near the
-// root still stream Y with the whole GPU.
+// children in fixed order).  256 threads: 32 row lanes of VW consecutive rows
+// (one 16-byte load per column) x 8 column groups.  Rows < p give y_P (times
+// D^{-1}) into yperm, rows >= p the update vector.  Row blocks with more
+// than kFwdCols columns are split over CTAs (slot >= 0) so the few large
+// fronts near the root still stream Y with the whole GPU.
 template <typename TF, typename TV>
 __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
@@ -816,7 +806,6 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int RB = 32 * VW;
-  constexpr int NS = kFwdCols / 8;  // columns per warp
   __shared__ TV gpart[8 * RB];
   __shared__ TV wp[kFwdCols];
   const int4 t = tasks[blockIdx.x];
@@ -825,41 +814,39 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
   const int32_t p = fr.npiv, m = fr.m;
   const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
   const int32_t j1 = (j0 + kFwdCols < jmax) ? j0 + kFwdCols : jmax;
-  const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int32_t row = r0 + VW * rl;
-  V yv[NS];
-  {
-    const TF *yc = Y + fr.y_off + row;
-#pragma unroll
-    for (int s2 = 0; s2 < NS; ++s2) {
-      const int32_t j = j0 + g + 8 * s2;
-      yv[s2] = (row < m && j < j1) ? *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy) : V{};
-    }
-  }
   for (int32_t j = j0 + threadIdx.x; j < j1; j += 256) {
     const int64_t q0 = wsrc_ptr[fr.w_off + j], q1 = wsrc_ptr[fr.w_off + j + 1];
     TV w = r[perm[fr.first + j]];
     for (int64_t q = q0; q < q1; ++q) w += ubuf[wsrc[q]];
     wp[j - j0] = w;
   }
-  // the epilogue's child contributions (rows >= p), also ahead of the FMAs
-  TV csum = TV(0);
-  const bool last_chunk = j1 == jmax;
-  if (threadIdx.x < RB && last_chunk) {
-    const int32_t i = r0 + threadIdx.x;
-    if (i >= p && i < m)
-      for (int64_t q = wsrc_ptr[fr.w_off + i]; q < wsrc_ptr[fr.w_off + i + 1]; ++q) csum += ubuf[wsrc[q]];
-  }
   __syncthreads();
+  const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int32_t row = r0 + VW * rl;
   TV acc[VW];
 #pragma unroll
   for (int e = 0; e < VW; ++e) acc[e] = TV(0);
+  if (row < m) {
+    const TF *yc = Y + fr.y_off + row;
+    int32_t j = j0 + g;
+    for (; j + 24 < j1; j += 32) {
+      V v0 = *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy);
+      V v1 = *reinterpret_cast<const V *>(yc + int64_t(j + 8) * fr.ldy);
+      V v2 = *reinterpret_cast<const V *>(yc + int64_t(j + 16) * fr.ldy);
+      V v3 = *reinterpret_cast<const V *>(yc + int64_t(j + 24) * fr.ldy);
+      const TF *e0 = reinterpret_cast<const TF *>(&v0), *e1 = reinterpret_cast<const TF *>(&v1);
+      const TF *e2 = reinterpret_cast<const TF *>(&v2), *e3 = reinterpret_cast<const TF *>(&v3);
+      const TV w0 = wp[j - j0], w1 = wp[j + 8 - j0], w2 = wp[j + 16 - j0], w3 = wp[j + 24 - j0];
 #pragma unroll
-  for (int s2 = 0; s2 < NS; ++s2) {
-    const int jj = g + 8 * s2;
-    const TV w = jj < j1 - j0 ? wp[jj] : TV(0);
+      for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0 + TV(e1[e]) * w1 + TV(e2[e]) * w2 + TV(e3[e]) * w3;
+    }
+    for (; j < j1; j += 8) {
+      V v0 = *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy);
+      const TF *e0 = reinterpret_cast<const TF *>(&v0);
+      const TV w0 = wp[j - j0];
 #pragma unroll
-    for (int q = 0; q < VW; ++q) acc[q] += TV(vget(yv[s2], q)) * w;
+      for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0;
+    }
   }
 #pragma unroll
   for (int e = 0; e < VW; ++e) gpart[g * RB + VW * rl + e] = acc[e];
@@ -883,12 +870,6 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
       if (tt < RB) part[int64_t(slot + j0 / kFwdCols) * RB + tt] = sums[k];
     }
     if (!last_of_block(tickets + slot, nch)) return;
-    // the last CTA may not be the one that gathered csum: gather again
-    if (!last_chunk && threadIdx.x < RB) {
-      const int32_t i = r0 + threadIdx.x;
-      if (i >= p && i < m)
-        for (int64_t q = wsrc_ptr[fr.w_off + i]; q < wsrc_ptr[fr.w_off + i + 1]; ++q) csum += ubuf[wsrc[q]];
-    }
 #pragma unroll
     for (int k = 0; k < (RB + 255) / 256; ++k) {
       const int tt = threadIdx.x + 256 * k;
@@ -903,21 +884,23 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
     const int tt = threadIdx.x + 256 * k;
     const int32_t i = r0 + tt;
     if (tt >= RB || i >= m) continue;
-    if (i < p)
+    if (i < p) {
       yperm[fr.first + i] = TV(double(sums[k]) * Dinv[fr.first + i]);
-    else
-      ubuf[fr.u_off + i - p] = csum + sums[k];
+    } else {
+      TV w = TV(0);
+      for (int64_t q = wsrc_ptr[fr.w_off + i]; q < wsrc_ptr[fr.w_off + i + 1]; ++q) w += ubuf[wsrc[q]];
+      ubuf[fr.u_off + i - p] = w + sums[k];
+    }
   }
 }
 
 // Backward level, task (front, c0, i0, slot): pivot columns [c0, c0 + 32)
-// over the rows [i0, i0 + BR), BR = 2 KB / sizeof(TF), from the VW-aligned
-// row at or below each column (rows above a column are zeros of L^{-1}, so
-// reading from the aligned row is exact).  Warp w owns columns c0 + w + 8k
-// (k < 4); every lane issues all its loads of Y (4 columns x 4 vectors)
-// before x = [D^{-1} y_P; z_U] is staged in shared memory.  Columns longer
-// than BR rows are split over CTAs (slot >= 0) and combined in row-chunk
-// order.
+// over the rows [i0, i0 + kBwdRows); warp w owns columns c0 + w + 8k
+// (k = 0..3) and streams them together (four 16-byte loads in flight per
+// lane).  x = [D^{-1} y_P; z_U] is staged in shared memory from the
+// VW-aligned row at or below c0; rows above a column are zeros of L^{-1}, so
+// reading from the aligned row is exact.  Columns longer than kBwdRows rows
+// are split over CTAs (slot >= 0) and combined in row-chunk order.
 template <typename TF, typename TV>
 __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
@@ -927,47 +910,44 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
                                                   TV *__restrict__ part, int *__restrict__ tickets) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
-  constexpr int BR = 2048 / int(sizeof(TF));
-  constexpr int NI = BR / (32 * VW);  // vectors per lane and column
-  __shared__ __align__(16) TV xs[BR];
+  __shared__ __align__(16) TV xs[kBwdRows];
   const int4 t = tasks[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t c0 = t.y, ilo0 = t.z, slot = t.w;
   const int32_t p = fr.npiv, m = fr.m;
   const int32_t a0 = c0 & ~(VW - 1);
-  const int32_t xa = a0 > ilo0 ? a0 : ilo0;                       // first row of this task
-  const int32_t xb = (ilo0 + BR < fr.ldy) ? ilo0 + BR : fr.ldy;  // end row
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t jc[4], ist[4];
-  V yv[4][NI];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    jc[k] = c0 + w + 8 * k;
-    const int32_t ja = jc[k] & ~(VW - 1);
-    ist[k] = jc[k] < p ? (ja > xa ? ja : xa) + VW * lane : xb;  // out-of-range columns do nothing
-    const TF *yc = Y + fr.y_off + int64_t(jc[k] < p ? jc[k] : c0) * fr.ldy;
-#pragma unroll
-    for (int it = 0; it < NI; ++it) {
-      const int32_t i = ist[k] + 32 * VW * it;
-      yv[k][it] = i < xb ? *reinterpret_cast<const V *>(yc + i) : V{};
-    }
-  }
+  const int32_t xa = a0 > ilo0 ? a0 : ilo0;                                 // first row of this task
+  const int32_t xb = (ilo0 + kBwdRows < fr.ldy) ? ilo0 + kBwdRows : fr.ldy;  // end row
   const int32_t *urows = upd_rows_old + fr.rows_off;
   for (int32_t tt = threadIdx.x; tt < xb - xa; tt += 256) {
     const int32_t i = xa + tt;
     xs[tt] = (i < c0 || i >= m) ? TV(0) : (i < p ? yperm[fr.first + i] : z[urows[i - p]]);
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t jc[4];
+  const TF *yc[4];
+  int32_t ist[4];
   TV acc[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
+    jc[k] = c0 + w + 8 * k;
+    const int32_t j = jc[k] < p ? jc[k] : c0;  // out-of-range columns read a valid one, result dropped
+    yc[k] = Y + fr.y_off + int64_t(j) * fr.ldy;
+    const int32_t ja = j & ~(VW - 1);
+    ist[k] = (ja > xa ? ja : xa) + VW * lane;
     acc[k] = TV(0);
+  }
+  const int32_t ilo = ist[0] < ist[3] ? ist[0] : ist[3];
+  for (int32_t off = 0; ilo + off < xb; off += 32 * VW) {
 #pragma unroll
-    for (int it = 0; it < NI; ++it) {
-      const int32_t i = ist[k] + 32 * VW * it;
+    for (int k = 0; k < 4; ++k) {
+      const int32_t i = ist[k] + off;
       if (i < xb) {
+        V v = *reinterpret_cast<const V *>(yc[k] + i);
+        const TF *e = reinterpret_cast<const TF *>(&v);
 #pragma unroll
-        for (int q = 0; q < VW; ++q) acc[k] += TV(vget(yv[k][it], q)) * xs[i - xa + q];
+        for (int q = 0; q < VW; ++q) acc[k] += TV(e[q]) * xs[i - xa + q];
       }
     }
   }
@@ -984,11 +964,11 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
     }
     return;
   }
-  const int32_t k_first = a0 / BR;
-  const int nch = (fr.ldy - 1) / BR - k_first + 1;
+  const int32_t k_first = a0 / kBwdRows;
+  const int nch = (fr.ldy - 1) / kBwdRows - k_first + 1;
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) part[int64_t(slot + ilo0 / BR - k_first) * kBwdCols + w + 8 * k] = acc[k];
+    for (int k = 0; k < 4; ++k) part[int64_t(slot + ilo0 / kBwdRows - k_first) * kBwdCols + w + 8 * k] = acc[k];
   }
   if (!last_of_block(tickets + slot, nch)) return;
   if (threadIdx.x < kBwdCols) {
