@@ -95,7 +95,11 @@ typedef struct {
   int32_t nd_leaf_nodes;  /* nested-dissection leaf size in nodes (0: 64)     */
   double inner_tol;       /* FE_MIXED inner PCG tolerance per sweep (0: 1e-4) */
   double factor_timeout_s;/* host deadline for a lagged factor (0: 30 s)      */
-  int32_t use_graph;      /* 1: replay the PCG iteration as a CUDA graph      */
+  int32_t use_graph;      /* 1: the PCG iterations run as a CUDA graph of
+                             kGraphIters iterations, replayed until the
+                             device-side convergence flag is set (one host
+                             read per replay; iterations after convergence
+                             exit at once, so results are bit-identical)      */
   int32_t profile_stages; /* 1: time every stage with CUDA events on its own
                              stream (read with fe_get_stage_times)          */
   int32_t newton_iters;   /* Newton iterations per step (0 or 1: the paper's
@@ -248,6 +252,7 @@ enum {
   FE_STAGE_ELEMENT = 0, FE_STAGE_ASSEMBLY, FE_STAGE_FACTOR, FE_STAGE_APPLY,
   FE_STAGE_SPMV, FE_STAGE_VECTOR, FE_STAGE_RESIDUAL, FE_STAGE_INTEGRATE,
   FE_STAGE_FACTOR_UPDATE, /* the factor's trailing-update launches only */
+  FE_STAGE_PCG_GRAPH,     /* PCG iterations replayed as CUDA graphs (use_graph) */
   FE_STAGE_COUNT
 };
 int fe_get_stage_times(fe_ctx *ctx, double *ms, int64_t *calls, int64_t *kernel_launches);

@@ -43,7 +43,7 @@ class FeInfo(ct.Structure):
 
 
 STAGES = ["element", "assembly", "factor", "apply", "spmv", "vector", "residual", "integrate",
-          "factor_update"]
+          "factor_update", "pcg_graph"]
 
 P = ct.POINTER
 CTX = ct.c_void_p

@@ -23,7 +23,7 @@ size_t vsz(const fe_ctx *c) { return mixed(c) ? sizeof(float) : sizeof(double); 
 // ------------------------------------------------------ live stage timing
 int stage_begin(fe_ctx *c, int stage, cudaStream_t s) {
   DeviceState *d = c->dev;
-  if (!c->opt.profile_stages) return -1;
+  if (!c->opt.profile_stages || stage < 0) return -1;
   DeviceState::StageRec r;
   r.stage = stage;
   for (cudaEvent_t *e : {&r.a, &r.b}) {
@@ -371,8 +371,66 @@ int launch_factor(fe_ctx *c, int64_t step_tag) {
   return FE_OK;
 }
 
+// One PCG iteration after the prologue: q = A p, alpha, x += alpha p,
+// r -= alpha q, then z = P^{-1} r, beta, p = z + beta p.  Every kernel
+// returns at once once the device flag S_DONE is set (converged, or the
+// iteration cap), so iterations enqueued past that point change nothing.
+static void pcg_iteration(fe_ctx *c, bool fp32, void *X, void *R, cudaStream_t s, bool timed) {
+  DeviceState *d = c->dev;
+  const double *done = d->scal + S_DONE;
+  {
+    Stage st(c, timed ? FE_STAGE_SPMV : -1, s);
+    launch_spmv_dot(c, d, fp32, d->vp, d->vq, s);
+  }
+  {
+    Stage st(c, timed ? FE_STAGE_VECTOR : -1, s);
+    launch_axpy_norm(c, d, fp32, X, R, d->vp, d->vq, s);
+  }
+  {
+    Stage st(c, timed ? FE_STAGE_APPLY : -1, s);
+    apply_enqueue(c, d, d->cur, fp32, R, d->vz, s, done);
+  }
+  Stage st(c, timed ? FE_STAGE_VECTOR : -1, s);
+  launch_dot_rz(c, d, fp32, R, d->vz, false, s);
+  launch_update_p(c, d, fp32, d->vz, d->vp, false, s);
+}
+
+// The graph of kGraphIters iterations for (precision, X, R, factor buffer),
+// captured once and cached.
+constexpr int kGraphIters = 4;
+
+static int pcg_graph(fe_ctx *c, bool fp32, void *X, void *R, DeviceState::PcgGraph **out) {
+  DeviceState *d = c->dev;
+  for (auto &g : d->graphs)
+    if (g.fp32 == fp32 && g.X == X && g.R == R && g.cur == d->cur) {
+      *out = &g;
+      return FE_OK;
+    }
+  cudaStream_t s = d->stream;
+  const int64_t l0 = d->launches;
+  FE_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < kGraphIters; ++k) pcg_iteration(c, fp32, X, R, s, false);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  d->graphs.push_back({fp32, X, R, d->cur, exec, d->launches - l0});
+  d->launches = l0;
+  *out = &d->graphs.back();
+  return FE_OK;
+}
+
+static int pcg_status(fe_ctx *c) {
+  if (c->dev->h_scal[S_DONE] == 2.0) return set_error(c, FE_ERR_NOT_CONVERGED, "PCG reached max_iters");
+  return FE_OK;
+}
+
 // PCG on (X, R) with the current factor; X = 0 and R = rhs were set by
-// init_solve.  Iterations accumulate in S_ITERS.
+// init_solve.  Iterations accumulate in S_ITERS.  One host read of the
+// device scalars per iteration, or per replay of the iteration graph.
 int pcg(fe_ctx *c, bool fp32, void *X, void *R) {
   DeviceState *d = c->dev;
   cudaStream_t s = d->stream;
@@ -384,6 +442,20 @@ int pcg(fe_ctx *c, bool fp32, void *X, void *R) {
     Stage st(c, FE_STAGE_VECTOR, s);
     launch_dot_rz(c, d, fp32, R, d->vz, true, s);
     launch_update_p(c, d, fp32, d->vz, d->vp, true, s);
+  }
+  if (c->opt.use_graph) {
+    DeviceState::PcgGraph *g = nullptr;
+    FE_TRY(pcg_graph(c, fp32, X, R, &g));
+    for (;;) {
+      {
+        Stage st(c, FE_STAGE_PCG_GRAPH, s);
+        FE_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+      }
+      d->launches += g->launches;
+      FE_TRY(read_scalars(c));
+      FE_TRY(flag_status(c));
+      if (d->h_scal[S_DONE] != 0.0) return pcg_status(c);
+    }
   }
   for (;;) {
     {
@@ -397,9 +469,7 @@ int pcg(fe_ctx *c, bool fp32, void *X, void *R) {
     FE_CUDA_TRY(cudaGetLastError());
     FE_TRY(read_scalars(c));
     FE_TRY(flag_status(c));
-    if (d->h_scal[S_DONE] != 0.0) break;
-    if (d->h_scal[S_ITERS] >= c->opt.max_iters)
-      return set_error(c, FE_ERR_NOT_CONVERGED, "PCG reached max_iters");
+    if (d->h_scal[S_DONE] != 0.0) return pcg_status(c);
     {
       Stage st(c, FE_STAGE_APPLY, s);
       apply_enqueue(c, d, d->cur, fp32, R, d->vz, s);
@@ -408,7 +478,6 @@ int pcg(fe_ctx *c, bool fp32, void *X, void *R) {
     launch_dot_rz(c, d, fp32, R, d->vz, false, s);
     launch_update_p(c, d, fp32, d->vz, d->vp, false, s);
   }
-  return FE_OK;
 }
 
 // SpMV autotuner: threads per CSR row chosen among {4, 8, 16, 32} by timing
@@ -610,6 +679,7 @@ void destroy_device(fe_ctx *c) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : d->pool) cudaEventDestroy(e);
+  for (auto &g : d->graphs) cudaGraphExecDestroy(g.exec);
   if (d->fstream) cudaStreamDestroy(d->fstream);
   if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
   cudaGetLastError();

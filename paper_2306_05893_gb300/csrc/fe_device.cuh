@@ -97,6 +97,14 @@ struct DeviceState {
   double *D[2] = {nullptr, nullptr};
   void *wbuf = nullptr, *ubuf = nullptr, *yperm = nullptr;  // apply work vectors
   double *na = nullptr, *nq = nullptr, *nv = nullptr;       // Newton iterate a_k, q_k, v_k
+  struct PcgGraph {                                         // captured PCG iteration blocks
+    bool fp32;
+    void *X, *R;
+    int cur;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<PcgGraph> graphs;
   void *part_f = nullptr, *part_b = nullptr;                // partial sums of split apply tasks
   int *tick_f = nullptr, *tick_b = nullptr;                 // their tickets (zero between launches)
   int cur = 0;                     // buffer the solver reads
@@ -201,7 +209,9 @@ void stage_end(fe_ctx *c, int idx, cudaStream_t s);
 
 // (fe_factor.cu)
 int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Afac, cudaStream_t s);
+// done: optional device flag; every kernel of the application returns at
+// once when it is non-zero (PCG iterations replayed past convergence)
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
-                   cudaStream_t s);
+                   cudaStream_t s, const double *done = nullptr);
 
 }  // namespace fe

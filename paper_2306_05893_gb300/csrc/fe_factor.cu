@@ -802,7 +802,9 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
                                                   const int32_t *__restrict__ wsrc_ptr,
                                                   const int32_t *__restrict__ wsrc, const TV *__restrict__ r,
                                                   TV *__restrict__ ubuf, TV *__restrict__ yperm,
-                                                  TV *__restrict__ part, int *__restrict__ tickets) {
+                                                  TV *__restrict__ part, int *__restrict__ tickets,
+                                                  const double *__restrict__ done) {
+  if (done && *done != 0.0) return;
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int RB = 32 * VW;
@@ -907,7 +909,9 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
                                                   const int32_t *__restrict__ perm,
                                                   const int32_t *__restrict__ upd_rows_old,
                                                   const TV *__restrict__ yperm, TV *__restrict__ z,
-                                                  TV *__restrict__ part, int *__restrict__ tickets) {
+                                                  TV *__restrict__ part, int *__restrict__ tickets,
+                                                  const double *__restrict__ done) {
+  if (done && *done != 0.0) return;
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   __shared__ __align__(16) TV xs[kBwdRows];
@@ -1032,7 +1036,8 @@ int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Af
 
 template <typename TF, typename TV>
 static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, TV *u, TV *yp,
-                              TV *part_f, TV *part_b, int *tick_f, int *tick_b, cudaStream_t s) {
+                              TV *part_f, TV *part_b, int *tick_f, int *tick_b, cudaStream_t s,
+                              const double *done = nullptr) {
   const TF *Y = reinterpret_cast<const TF *>(d->Y[buf]);
   const double *Dinv = d->D[buf] + c->n_free;
   d->launches += 2 * int64_t(d->lt.size());
@@ -1040,29 +1045,31 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
     const auto &L = d->lt[lv];
     fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, 0, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
                                                          d->fronts, Y, Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp,
-                                                         part_f, tick_f);
+                                                         part_f, tick_f, done);
   }
   for (size_t lv = d->lt.size(); lv-- > 0;) {
     const auto &L = d->lt[lv];
     bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, 0, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
                                                          d->fronts, Y, d->perm, d->upd_rows_old, yp, z, part_b,
-                                                         tick_b);
+                                                         tick_b, done);
   }
 }
 
 template <typename TF, typename TV>
-static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, cudaStream_t s) {
+static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, cudaStream_t s,
+                         const double *done) {
   apply_levels_with<TF, TV>(c, d, buf, r, z, reinterpret_cast<TV *>(d->ubuf), reinterpret_cast<TV *>(d->yperm),
                             reinterpret_cast<TV *>(d->part_f), reinterpret_cast<TV *>(d->part_b), d->tick_f,
-                            d->tick_b, s);
+                            d->tick_b, s, done);
 }
 
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
-                   cudaStream_t s) {
+                   cudaStream_t s, const double *done) {
   if (fp32)
-    apply_levels<float, float>(c, d, buf, reinterpret_cast<const float *>(r), reinterpret_cast<float *>(z), s);
+    apply_levels<float, float>(c, d, buf, reinterpret_cast<const float *>(r), reinterpret_cast<float *>(z), s, done);
   else
-    apply_levels<double, double>(c, d, buf, reinterpret_cast<const double *>(r), reinterpret_cast<double *>(z), s);
+    apply_levels<double, double>(c, d, buf, reinterpret_cast<const double *>(r), reinterpret_cast<double *>(z), s,
+                                 done);
 }
 
 

@@ -462,7 +462,8 @@ __global__ void __launch_bounds__(kRedBlock) axpy_norm_kernel(int64_t n, TV *__r
                                                               TV *__restrict__ r,
                                                               const TV *__restrict__ p,
                                                               const TV *__restrict__ q, double *scal,
-                                                              double *partials, unsigned int *ticket) {
+                                                              double *partials, unsigned int *ticket,
+                                                              double max_iters) {
   if (solve_done(scal)) return;
   const TV al = TV(scal[S_ALPHA]);
   double rr = 0.0;
@@ -476,7 +477,10 @@ __global__ void __launch_bounds__(kRedBlock) axpy_norm_kernel(int64_t n, TV *__r
   if (grid_sum<kRedBlock>(rr, partials, ticket, &tot) && threadIdx.x == 0) {
     scal[S_RR] = tot;
     scal[S_ITERS] += 1.0;
-    if (tot <= scal[S_TOL2]) scal[S_DONE] = 1.0;
+    if (tot <= scal[S_TOL2])
+      scal[S_DONE] = 1.0;
+    else if (scal[S_ITERS] >= max_iters)
+      scal[S_DONE] = 2.0;  // iteration cap: stops the solve, reported as not converged
   }
 }
 
@@ -652,11 +656,12 @@ void launch_axpy_norm(const fe_ctx *c, const DeviceState *d, bool fp32, void *x,
   const int64_t n = c->n;
   if (fp32)
     axpy_norm_kernel<float><<<red_grid(n), kRedBlock, 0, s>>>(n, (float *)x, (float *)r, (const float *)p,
-                                                              (const float *)q, d->scal, d->partials, d->ticket);
+                                                              (const float *)q, d->scal, d->partials, d->ticket,
+                                                              double(c->opt.max_iters));
   else
     axpy_norm_kernel<double><<<red_grid(n), kRedBlock, 0, s>>>(n, (double *)x, (double *)r,
                                                                (const double *)p, (const double *)q, d->scal,
-                                                               d->partials, d->ticket);
+                                                               d->partials, d->ticket, double(c->opt.max_iters));
 }
 
 void launch_dot_rz(const fe_ctx *c, const DeviceState *d, bool fp32, const void *r, const void *z, bool first,
