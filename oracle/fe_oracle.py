@@ -316,6 +316,30 @@ def csr_pattern(n_dof, conn, fixed_dofs):
     return rowptr, colind, C.astype(np.int32)
 
 
+def triplets_to_csr(n, rows, cols, vals, prev=None):
+    """Compressed matrix of a caller's triplet stream (Section 4.2 "Collect
+    data" and "Build matrix pattern").  Returns (keep, rowptr, colind, C,
+    values): keep is True when the (row, col) stream equals the previous one
+    `prev` = (rows, cols) element by element and in length (the filling-order
+    test of Algorithm "add"), the pattern has rows and columns ascending with
+    duplicates merged, C maps triplet t to its slot, and every slot's value is
+    the sum of its triplets in ascending t order.  Built by sorting unique
+    keys, not by the double transpose."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    keep = prev is not None and len(prev[0]) == len(rows) and bool(
+        np.array_equal(prev[0], rows) and np.array_equal(prev[1], cols))
+    keys = rows * n + cols
+    uniq, C = np.unique(keys, return_inverse=True)
+    colind = (uniq % n).astype(np.int32)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, uniq // n + 1, 1)
+    rowptr = np.cumsum(rowptr).astype(np.int32)
+    values = np.zeros(uniq.shape[0], dtype=np.float64)
+    np.add.at(values, C, np.asarray(vals, dtype=np.float64))  # in ascending t per slot
+    return keep, rowptr, colind, C.astype(np.int32), values
+
+
 def assemble(n_dof, conn, values_fill_order):
     """Unconstrained global matrix: plain sum of every triplet (COO -> CSR)."""
     row, col = triplet_dofs(conn)
