@@ -290,6 +290,54 @@ const char *fe_last_error(const fe_ctx *ctx);
 /* Frees every host and device resource of ctx (NULL is a no-op). */
 void fe_destroy(fe_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Generic triplet ingestion (Section 4.2, "Collect data", "Build matrix
+ * pattern", Algorithm "add"): any caller-side FE code hands over, every
+ * step, its stream of (row, col, value) contributions to an n x n matrix in
+ * its own filling order.  When the (row, col) stream equals the previous
+ * call's element by element and in length (the filling-order test), the
+ * CSR pattern and the map C are kept and only the values are merged on the
+ * GPU: slot s = sum of its triplets in ascending stream order, one thread
+ * per slot, no atomics (bit-reproducible).  Otherwise the pattern is
+ * rebuilt on the host by two counting-sort transposes ("full assembly") and
+ * uploaded.  The handle owns its device memory; one device, one caller
+ * thread at a time.
+ * ---------------------------------------------------------------------- */
+typedef struct fe_trip fe_trip;
+
+/* New handle for n x n matrices (n >= 1) on the current device. */
+int fe_trip_create(int64_t n, fe_trip **out);
+
+/* Merges the stream: rows, cols [ntrip] int32 in [0, n), vals [ntrip]
+ * FP64.  device_ptrs = 0: host arrays (compared with the previous stream on
+ * the host); 1: device arrays on stream `stream` (compared on the device,
+ * one flag read back).  *rebuilt (may be NULL) = 1 when the pattern was
+ * (re)built.  An index outside [0, n) is FE_ERR_ARG (checked whenever the
+ * pattern is built; an unchanged stream was checked when first seen).
+ * ntrip = 0 gives an empty pattern.  The merged values stay on the device
+ * until the next call (fe_trip_values, fe_trip_device_csr). */
+int fe_trip_assemble(fe_trip *t, int64_t ntrip, const int32_t *rows, const int32_t *cols, const double *vals,
+                     int32_t device_ptrs, void *stream, int32_t *rebuilt);
+
+/* Borrowed host views of the pattern (valid until the next rebuild or
+ * fe_trip_destroy): rowptr [n + 1], colind [nnz], scatter = C [ntrip]. */
+int fe_trip_pattern(fe_trip *t, int64_t *nnz, const int32_t **rowptr, const int32_t **colind,
+                    const int32_t **scatter);
+
+/* Copies the merged values [nnz] to `out` (host, or device when
+ * device_ptrs = 1) on `stream`; host copies are complete on return. */
+int fe_trip_values(fe_trip *t, double *out, int32_t device_ptrs, void *stream);
+
+/* Borrowed device views of the CSR matrix (valid until the next
+ * fe_trip_assemble or fe_trip_destroy). */
+int fe_trip_device_csr(fe_trip *t, const int32_t **rowptr, const int32_t **colind, const double **vals);
+
+/* Message of the last failure on t ("" if none). */
+const char *fe_trip_last_error(const fe_trip *t);
+
+/* Frees the handle (NULL is a no-op). */
+void fe_trip_destroy(fe_trip *t);
+
 #ifdef __cplusplus
 }
 #endif

@@ -265,6 +265,88 @@ def fe_destroy(ctx):
         load().fe_destroy(ctx)
 
 
+# ------------------------------------------------- generic triplet ingestion
+
+def _check_trip(t, status):
+    if status != 0:
+        msg = _LIB.fe_trip_last_error(t) if t else b""
+        raise FEError(status, (msg or b"").decode())
+
+
+def fe_trip_create(n):
+    lib = load()
+    h = ct.c_void_p()
+    st = lib.fe_trip_create(int(n), ct.byref(h))
+    if st:
+        raise FEError(st, "fe_trip_create failed")
+    return h
+
+
+def fe_trip_assemble(t, rows, cols, vals, stream=None):
+    """rows/cols int32 and vals float64, all numpy (host) or all CUDA tensors
+    (device, on `stream`).  Returns True when the pattern was rebuilt."""
+    dev = hasattr(vals, "data_ptr") and getattr(vals, "is_cuda", False)
+    if not dev:
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        vals = _f64(vals)
+    s = None if stream is None else ct.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    rebuilt = ct.c_int32()
+    _check_trip(t, load().fe_trip_assemble(t, int(rows.shape[0]), _ptr(rows), _ptr(cols), _ptr(vals),
+                                           1 if dev else 0, s, ct.byref(rebuilt)))
+    return bool(rebuilt.value)
+
+
+def fe_trip_pattern(t, n):
+    nnz = ct.c_int64()
+    rp, ci, C = (ct.POINTER(ct.c_int32)() for _ in range(3))
+    _check_trip(t, load().fe_trip_pattern(t, ct.byref(nnz), ct.byref(rp), ct.byref(ci), ct.byref(C)))
+    return (np.ctypeslib.as_array(rp, (n + 1,)).copy(),
+            np.ctypeslib.as_array(ci, (nnz.value,)).copy() if nnz.value else np.zeros(0, np.int32),
+            nnz.value, C)
+
+
+def fe_trip_values(t, nnz):
+    out = np.empty(nnz, dtype=np.float64)
+    if nnz:
+        _check_trip(t, load().fe_trip_values(t, _ptr(out), 0, None))
+    return out
+
+
+class TripletAssembler:
+    """Owns one fe_trip: merges a caller's (row, col, value) stream into an
+    n x n CSR matrix on the GPU, keeping the pattern while the filling order
+    is unchanged."""
+
+    def __init__(self, n):
+        self.n = int(n)
+        self.t = fe_trip_create(self.n)
+        self.ntrip = 0
+
+    def assemble(self, rows, cols, vals, stream=None):
+        self.ntrip = int(rows.shape[0])
+        return fe_trip_assemble(self.t, rows, cols, vals, stream)
+
+    def pattern(self):
+        rp, ci, nnz, C = fe_trip_pattern(self.t, self.n)
+        return rp, ci, (np.ctypeslib.as_array(C, (self.ntrip,)).copy() if self.ntrip else np.zeros(0, np.int32))
+
+    def values(self):
+        rp, _, nnz, _ = fe_trip_pattern(self.t, self.n)
+        return fe_trip_values(self.t, nnz)
+
+    def close(self):
+        if self.t:
+            load().fe_trip_destroy(self.t)
+            self.t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- wrapper
 
 class FEContext:

@@ -85,6 +85,14 @@ SIGNATURES = {
     "fe_num_checkpoints": (ct.c_int, [CTX, P(ct.c_int64)]),
     "fe_last_error": (ct.c_char_p, [CTX]),
     "fe_destroy": (None, [CTX]),
+    "fe_trip_create": (ct.c_int, [ct.c_int64, P(ct.c_void_p)]),
+    "fe_trip_assemble": (ct.c_int, [CTX, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int32,
+                                    ct.c_void_p, P(ct.c_int32)]),
+    "fe_trip_pattern": (ct.c_int, [CTX, P(ct.c_int64), P(I32P), P(I32P), P(I32P)]),
+    "fe_trip_values": (ct.c_int, [CTX, ct.c_void_p, ct.c_int32, ct.c_void_p]),
+    "fe_trip_device_csr": (ct.c_int, [CTX, P(ct.c_void_p), P(ct.c_void_p), P(ct.c_void_p)]),
+    "fe_trip_last_error": (ct.c_char_p, [CTX]),
+    "fe_trip_destroy": (None, [CTX]),
 }
 
 

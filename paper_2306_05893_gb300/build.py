@@ -17,7 +17,8 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfe_hotpath.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fe_setup.cpp", "fe_api_host.cpp", "fe_api.cu", "fe_kernels.cu", "fe_factor.cu", "fe_adjoint.cu", "fe_batch.cu"]
+SOURCES = ["fe_setup.cpp", "fe_api_host.cpp", "fe_api.cu", "fe_kernels.cu", "fe_factor.cu", "fe_adjoint.cu", "fe_batch.cu",
+           "fe_triplets.cu"]
 
 
 def _nvcc():
