@@ -767,6 +767,30 @@ struct Vec16<double> {
   static constexpr int n = 2;
 };
 
+// Programmatic dependent launch: the next kernel in the stream may start
+// once every CTA of this one has signalled, and waits for this kernel's
+// completion (and memory) before touching what it produced.  Both are no-ops
+// for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Deterministic combination of a block split over several CTAs: each CTA
 // stores its partial sums, and the last of the block's CTAs to arrive (a
 // ticket per block) adds the partials in chunk order, so the result does not
@@ -804,18 +828,22 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
                                                   TV *__restrict__ ubuf, TV *__restrict__ yperm,
                                                   TV *__restrict__ part, int *__restrict__ tickets,
                                                   const double *__restrict__ done) {
-  if (done && *done != 0.0) return;
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int RB = 32 * VW;
   __shared__ TV gpart[8 * RB];
   __shared__ TV wp[kFwdCols];
+  // launched as a programmatic dependent of the previous level: the task
+  // descriptors are static, everything else waits for that level
+  pdl_launch_dependents();
   const int4 t = tasks[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t r0 = t.y, j0 = t.z, slot = t.w;
   const int32_t p = fr.npiv, m = fr.m;
   const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
   const int32_t j1 = (j0 + kFwdCols < jmax) ? j0 + kFwdCols : jmax;
+  pdl_wait();
+  if (done && *done != 0.0) return;
   for (int32_t j = j0 + threadIdx.x; j < j1; j += 256) {
     const int64_t q0 = wsrc_ptr[fr.w_off + j], q1 = wsrc_ptr[fr.w_off + j + 1];
     TV w = r[perm[fr.first + j]];
@@ -911,10 +939,10 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
                                                   const TV *__restrict__ yperm, TV *__restrict__ z,
                                                   TV *__restrict__ part, int *__restrict__ tickets,
                                                   const double *__restrict__ done) {
-  if (done && *done != 0.0) return;
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   __shared__ __align__(16) TV xs[kBwdRows];
+  pdl_launch_dependents();
   const int4 t = tasks[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t c0 = t.y, ilo0 = t.z, slot = t.w;
@@ -922,6 +950,8 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
   const int32_t a0 = c0 & ~(VW - 1);
   const int32_t xa = a0 > ilo0 ? a0 : ilo0;                                 // first row of this task
   const int32_t xb = (ilo0 + kBwdRows < fr.ldy) ? ilo0 + kBwdRows : fr.ldy;  // end row
+  pdl_wait();
+  if (done && *done != 0.0) return;
   const int32_t *urows = upd_rows_old + fr.rows_off;
   for (int32_t tt = threadIdx.x; tt < xb - xa; tt += 256) {
     const int32_t i = xa + tt;
@@ -1043,15 +1073,13 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
   d->launches += 2 * int64_t(d->lt.size());
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
-    fwd_kernel<TF, TV><<<unsigned(L.fwd_n), 256, 0, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
-                                                         d->fronts, Y, Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp,
-                                                         part_f, tick_f, done);
+    launch_pdl(fwd_kernel<TF, TV>, unsigned(L.fwd_n), s, reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
+               d->fronts, Y, Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp, part_f, tick_f, done);
   }
   for (size_t lv = d->lt.size(); lv-- > 0;) {
     const auto &L = d->lt[lv];
-    bwd_kernel<TF, TV><<<unsigned(L.bwd_n), 256, 0, s>>>(reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
-                                                         d->fronts, Y, d->perm, d->upd_rows_old, yp, z, part_b,
-                                                         tick_b, done);
+    launch_pdl(bwd_kernel<TF, TV>, unsigned(L.bwd_n), s, reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
+               d->fronts, Y, d->perm, d->upd_rows_old, yp, z, part_b, tick_b, done);
   }
 }
 
