@@ -22,6 +22,31 @@
 
 namespace fe {
 
+// Programmatic dependent launch: the next kernel in the stream may start
+// once every CTA of this one has signalled, and waits for this kernel's
+// completion (and memory) before touching what it produced.  Both are no-ops
+// for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // -------------------------------------------------------------- assembly
 // Task (front, c0, c1): zero the lower part of columns [c0, c1) of F and of
 // the pivot columns of Y, scatter the A entries of those columns, then add
@@ -32,10 +57,12 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
     const int32_t *__restrict__ child_list, const int32_t *__restrict__ rmap,
     const int64_t *__restrict__ fa_colptr, const int32_t *__restrict__ fa_slot,
     const int32_t *__restrict__ fa_off, const TF *__restrict__ A, TF *__restrict__ F, TF *__restrict__ Y) {
+  pdl_launch_dependents();
   const int32_t f = tasks[3 * blockIdx.x], c0 = tasks[3 * blockIdx.x + 1], c1 = tasks[3 * blockIdx.x + 2];
   const DFront fr = fronts[f];
   const int32_t m = fr.m, p = fr.npiv;
   TF *Ff = F + fr.f_off;
+  pdl_wait();
   for (int32_t col = c0; col < c1; ++col) {
     TF *cp = Ff + int64_t(col) * m;
     for (int32_t r = col + threadIdx.x; r < m; r += blockDim.x) cp[r] = TF(0);
@@ -196,10 +223,12 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
   __shared__ TF colb[2][64], xrow[2][64], pinv[2];
   __shared__ double s_inv[64];  // FP64 inverses, or DF inverses in the same bytes
   DF *s_invf = reinterpret_cast<DF *>(s_inv);
+  pdl_launch_dependents();
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t k0 = t.y & 0xffffff, kb = t.z, m = fr.m;
   TF *Ff = F + fr.f_off;
+  pdl_wait();
   for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
     const int i = idx % 64, j = idx / 64;
     Ls[i][j] = (i < kb && j < kb && i >= j) ? Ff[(k0 + i) + int64_t(k0 + j) * m] : TF(0);
@@ -363,6 +392,7 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
   extern __shared__ unsigned char psm[];
   TF(*Ls)[65] = reinterpret_cast<TF(*)[65]>(psm);
   TF(*Bs)[65] = reinterpret_cast<TF(*)[65]>(psm + 64 * 65 * sizeof(TF));
+  pdl_launch_dependents();
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int kind = t.y >> 24;
@@ -370,6 +400,7 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
   const int32_t kb = (fr.npiv - k0) < 64 ? (fr.npiv - k0) : 64;
   TF *Ff = F + fr.f_off;
   TF *Yf = Y + fr.y_off;
+  pdl_wait();
   for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
     const int i = idx % 64, j = idx / 64;
     Ls[i][j] = (i < kb && j < kb && i >= j) ? Yf[(k0 + i) + int64_t(k0 + j) * fr.ldy] : TF(0);
@@ -447,6 +478,7 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
   extern __shared__ unsigned char usm[];
   TF(*As)[65] = reinterpret_cast<TF(*)[65]>(usm);
   TF(*Bs)[65] = reinterpret_cast<TF(*)[65]>(usm + 64 * 65 * sizeof(TF));
+  pdl_launch_dependents();
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int kind = t.y >> 24;
@@ -454,6 +486,7 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
   const int32_t kb = (fr.npiv - k0) < 64 ? (fr.npiv - k0) : 64;
   TF *Ff = F + fr.f_off;
   TF *Yf = Y + fr.y_off;
+  pdl_wait();
   for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
     const int i = idx % 64, l = idx / 64;
     const int32_t r = i0 + i;
@@ -599,6 +632,7 @@ __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *
   uint64_t *bar = reinterpret_cast<uint64_t *>(usm + 4 * kOpBytes);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(usm + 4 * kOpBytes + 8);
   __shared__ float Ds[kSuper];
+  pdl_launch_dependents();
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int kind = (t.y >> 24) & 7;
@@ -612,6 +646,7 @@ __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *
   float *Ff = F + fr.f_off;
   float *Yf = Y + fr.y_off;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  pdl_wait();
   for (int l = threadIdx.x; l < kSuper; l += 256) Ds[l] = (trail && l < kw) ? float(D[fr.first + k0 + l]) : 1.f;
   const uint32_t bar_a = smem_u32(bar);
   if (threadIdx.x == 0) {
@@ -766,30 +801,6 @@ struct Vec16<double> {
   using type = double2;
   static constexpr int n = 2;
 };
-
-// Programmatic dependent launch: the next kernel in the stream may start
-// once every CTA of this one has signalled, and waits for this kernel's
-// completion (and memory) before touching what it produced.  Both are no-ops
-// for a kernel launched without the attribute.
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
 
 // Deterministic combination of a block split over several CTAs: each CTA
 // stores its partial sums, and the last of the block's CTAs to arrive (a
@@ -1029,27 +1040,25 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
     const auto &L = d->lt[lv];
     if (L.asm_n) d->launches++;
     if (L.asm_n)
-      front_assemble_kernel<TF><<<unsigned(L.asm_n), 256, 0, s>>>(d->tasks + L.asm_off, d->fronts, d->child_list,
-                                                                  d->rmap, d->fa_colptr, d->fa_slot, d->fa_off,
-                                                                  Afac, F, Y);
+      launch_pdl(front_assemble_kernel<TF>, unsigned(L.asm_n), 256, 0, s, d->tasks + L.asm_off, d->fronts,
+                 d->child_list, d->rmap, d->fa_colptr, d->fa_slot, d->fa_off, Afac, F, Y);
     for (size_t st = 0; st < L.diag_n.size(); ++st) {
       d->launches += (L.diag_n[st] > 0) + (L.panel_n[st] > 0) + (L.trail_n[st] > 0);
       if (L.diag_n[st])
-        front_diag_kernel<TF><<<unsigned(L.diag_n[st]), kDiagThreads, dsm, s>>>(d->tasks + L.diag_off[st], d->fronts, F, Y,
-                                                                       d->D[buf], d->D[buf] + c->n_free, d->flags);
+        launch_pdl(front_diag_kernel<TF>, unsigned(L.diag_n[st]), kDiagThreads, dsm, s, d->tasks + L.diag_off[st],
+                   d->fronts, F, Y, d->D[buf], d->D[buf] + c->n_free, d->flags);
       if (L.panel_n[st])
-        front_panel_kernel<TF><<<unsigned(L.panel_n[st]), 256, tsm, s>>>(d->tasks + L.panel_off[st], d->fronts, F, Y,
-                                                                       d->D[buf] + c->n_free);
+        launch_pdl(front_panel_kernel<TF>, unsigned(L.panel_n[st]), 256, tsm, s, d->tasks + L.panel_off[st],
+                   d->fronts, F, Y, d->D[buf] + c->n_free);
       if (L.trail_n[st]) {
         const int ev = stage_begin(c, FE_STAGE_FACTOR_UPDATE, s);
         if (ev >= 0) d->update_flops += L.trail_flops[st];
         if constexpr (sizeof(TF) == 4)
-          front_update_tc_kernel<<<unsigned(L.trail_n[st]), 256, kUpdateSmem, s>>>(d->tasks + L.trail_off[st],
-                                                                                   d->fronts, F, Y, d->D[buf],
-                                                                                   d->flags);
+          launch_pdl(front_update_tc_kernel, unsigned(L.trail_n[st]), 256, kUpdateSmem, s,
+                     d->tasks + L.trail_off[st], d->fronts, F, Y, d->D[buf], d->flags);
         else
-          front_update_kernel<TF><<<unsigned(L.trail_n[st]), 256, tsm, s>>>(d->tasks + L.trail_off[st], d->fronts, F,
-                                                                          Y, d->D[buf]);
+          launch_pdl(front_update_kernel<TF>, unsigned(L.trail_n[st]), 256, tsm, s, d->tasks + L.trail_off[st],
+                     d->fronts, F, Y, d->D[buf]);
         stage_end(c, ev, s);
       }
     }
@@ -1073,12 +1082,12 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
   d->launches += 2 * int64_t(d->lt.size());
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
-    launch_pdl(fwd_kernel<TF, TV>, unsigned(L.fwd_n), s, reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
+    launch_pdl(fwd_kernel<TF, TV>, unsigned(L.fwd_n), 256, 0, s, reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
                d->fronts, Y, Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp, part_f, tick_f, done);
   }
   for (size_t lv = d->lt.size(); lv-- > 0;) {
     const auto &L = d->lt[lv];
-    launch_pdl(bwd_kernel<TF, TV>, unsigned(L.bwd_n), s, reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
+    launch_pdl(bwd_kernel<TF, TV>, unsigned(L.bwd_n), 256, 0, s, reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
                d->fronts, Y, d->perm, d->upd_rows_old, yp, z, part_b, tick_b, done);
   }
 }
