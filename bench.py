@@ -387,21 +387,25 @@ def main():
     upd_ms = stage_ms["factor_update"] / upd_calls
     upd_flops = update_flops / upd_calls
     upd_tflops = upd_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
-    roofline = {"bound": "tensor", "kernel": "front_update_tc_kernel (factor trailing updates, 3xTF32 mma.sync)",
+    roofline = {"bound": "tensor", "kernel": "front_update_tc_kernel (factor trailing updates, tcgen05 kind::tf32, 3xTF32)",
                 "achieved": upd_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": upd_tflops / tf32_peak,
                 "traffic": None, "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
                 "peak_source": tf32_src,
                 "note": "achieved counts algorithmic flops; 3xTF32 issues 3 TF32 MMAs per product, so frac <= 1/3"}
+    # (inside replayed PCG graphs the iterations are timed as one stage, so
+    # the apply and SpMV figures cover the graph-free first application only)
+    vb = 4 if wl.precision else 8
     apply_calls = max(1, stage_calls["apply"])
     apply_ms = stage_ms["apply"] / apply_calls
-    bytes_apply = 2 * info["y_nnz"] * 4 + 6 * info["n_free"] * 4 + 2 * info["n"] * 4
-    achieved = bytes_apply / (apply_ms / 1e3) / 1e9
-    roofline_apply = {"bound": "hbm", "kernel": "precond apply (fwd_kernel + bwd_kernel, 22 launches)",
+    bytes_apply = 2 * info["y_nnz"] * vb + 6 * info["n_free"] * vb + 2 * info["n"] * vb
+    achieved = bytes_apply / (apply_ms / 1e3) / 1e9 if apply_ms > 0 else None
+    roofline_apply = {"bound": "hbm", "kernel": "precond apply (fwd_kernel + bwd_kernel per level)",
                       "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                      "frac": achieved / hbm, "traffic": None, "bytes_per_launch": bytes_apply, "avg_ms": apply_ms}
+                      "frac": achieved / hbm if achieved else None, "traffic": None,
+                      "bytes_per_launch": bytes_apply, "avg_ms": apply_ms}
     spmv_calls = max(1, stage_calls["spmv"])
     spmv_ms = stage_ms["spmv"] / spmv_calls
-    bytes_spmv = info["nnz"] * (4 + 4) + (n + 1) * 4 + 2 * n * 4
+    bytes_spmv = info["nnz"] * (vb + 4) + (n + 1) * 4 + 2 * n * vb
     asm_ms = stage_ms["assembly"] / max(1, stage_calls["assembly"])
     bytes_asm = info["ntrip"] * 0.0  # filled below from the kept triplets
     out = {
@@ -421,7 +425,7 @@ def main():
         "stages_ms_per_step": {k: v / K for k, v in stage_ms.items()},
         "stage_calls": stage_calls,
         "spmv": {"avg_ms": spmv_ms, "bytes": bytes_spmv,
-                 "achieved_gbs": bytes_spmv / (spmv_ms / 1e3) / 1e9},
+                 "achieved_gbs": bytes_spmv / (spmv_ms / 1e3) / 1e9 if spmv_ms > 0 else None},
         "assembly": {"avg_ms": asm_ms},
         "gpu_launches": int(launches),
         "clocks": clocks,

@@ -365,10 +365,15 @@ int build_ordering(fe_ctx *c) {
     l.erase(std::unique(l.begin(), l.end()), l.end());
   }
   nd.tag.assign(nn, 0);
-  std::vector<int32_t> S;
-  for (int64_t v = 0; v < nn; ++v)
-    if (!fixed_node[v]) S.push_back(int32_t(v));
-  nd.build(S);
+  // one dissection per batch member: members share no edge, and their
+  // coordinates overlap, so a joint geometric bisection would cut them all
+  // with one shared separator; each member's tree is a root of the forest
+  for (int32_t k = 0; k < c->nseg; ++k) {
+    std::vector<int32_t> S;
+    for (int64_t v = c->seg_node[k]; v < c->seg_node[k + 1]; ++v)
+      if (!fixed_node[v]) S.push_back(int32_t(v));
+    nd.build(S);
+  }
   const int64_t nfree_nodes = int64_t(nd.order.size());
   std::vector<int32_t> pos(nn, -1);
   for (int64_t i = 0; i < nfree_nodes; ++i) pos[nd.order[i]] = int32_t(i);
