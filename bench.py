@@ -387,11 +387,19 @@ def main():
     upd_ms = stage_ms["factor_update"] / upd_calls
     upd_flops = update_flops / upd_calls
     upd_tflops = upd_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
-    roofline = {"bound": "tensor", "kernel": "front_update_tc_kernel (factor trailing updates, tcgen05 kind::tf32, 3xTF32)",
-                "achieved": upd_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": upd_tflops / tf32_peak,
-                "traffic": None, "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
-                "peak_source": tf32_src,
-                "note": "achieved counts algorithmic flops; 3xTF32 issues 3 TF32 MMAs per product, so frac <= 1/3"}
+    if wl.precision:
+        roofline = {"bound": "tensor",
+                    "kernel": "front_update_tc_kernel (factor trailing updates, tcgen05 kind::tf32, 3xTF32)",
+                    "achieved": upd_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": upd_tflops / tf32_peak,
+                    "traffic": None, "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
+                    "peak_source": tf32_src,
+                    "note": "achieved counts algorithmic flops; 3xTF32 issues 3 TF32 MMAs per product, "
+                            "so frac <= 1/3"}
+    else:
+        roofline = {"bound": "alu", "kernel": "front_update_kernel<double> (factor trailing updates, FP64)",
+                    "achieved": upd_tflops, "peak": 1.25, "unit": "TFLOP/s", "frac": upd_tflops / 1.25,
+                    "traffic": None, "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
+                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on this pool)"}
     # (inside replayed PCG graphs the iterations are timed as one stage, so
     # the apply and SpMV figures cover the graph-free first application only)
     vb = 4 if wl.precision else 8
