@@ -801,6 +801,12 @@ struct Vec16<double> {
   using type = double2;
   static constexpr int n = 2;
 };
+// element q of a 16-byte vector held in registers (q is a compile-time
+// constant after unrolling, so no address is taken)
+__device__ __forceinline__ float vget(const float4 &v, int q) {
+  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ double vget(const double2 &v, int q) { return q == 0 ? v.x : v.y; }
 
 // Deterministic combination of a block split over several CTAs: each CTA
 // stores its partial sums, and the last of the block's CTAs to arrive (a
@@ -823,12 +829,18 @@ __device__ __forceinline__ bool last_of_block(int *ticket, int nch) {
 
 // Forward level, task (front, r0, j0, slot): rows [r0, r0 + 32*VW) of Y w_P
 // over the pivot columns [j0, j0 + kFwdCols), where w = [r_P; 0] + the
-// children's update vectors (gathered on the fly through the position lists,
-// children in fixed order).  256 threads: 32 row lanes of VW consecutive rows
-// (one 16-byte load per column) x 8 column groups.  Rows < p give y_P (times
-// D^{-1}) into yperm, rows >= p the update vector.  Row blocks with more
-// than kFwdCols columns are split over CTAs (slot >= 0) so the few large
-// fronts near the root still stream Y with the whole GPU.
+// children's update vectors (gathered through the position lists, children
+// in fixed order).  256 threads: 32 row lanes of VW consecutive rows (one
+// 16-byte load per column) x 8 column groups, loads of the next 4 columns in
+// flight while the current ones are used.  Launched as a programmatic
+// dependent of the previous level: the static data (descriptors, gather
+// indices, the first Y vectors) is loaded before waiting for that level, the
+// vectors it produced after.  Rows < p give y_P (times D^{-1}) into yperm,
+// rows >= p the update vector.  Row blocks with more than kFwdCols columns
+// are split over CTAs (slot >= 0) so the few large fronts near the root
+// still stream Y with the whole GPU.
+constexpr int kPre = 4;  // gather sources prefetched per position
+
 template <typename TF, typename TV>
 __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
@@ -839,13 +851,12 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
                                                   TV *__restrict__ ubuf, TV *__restrict__ yperm,
                                                   TV *__restrict__ part, int *__restrict__ tickets,
                                                   const double *__restrict__ done) {
+  static_assert(kFwdCols == 256, "one gathered column per thread");
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int RB = 32 * VW;
   __shared__ TV gpart[8 * RB];
   __shared__ TV wp[kFwdCols];
-  // launched as a programmatic dependent of the previous level: the task
-  // descriptors are static, everything else waits for that level
   pdl_launch_dependents();
   const int4 t = tasks[blockIdx.x];
   const DFront fr = fronts[t.x];
@@ -853,40 +864,83 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
   const int32_t p = fr.npiv, m = fr.m;
   const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
   const int32_t j1 = (j0 + kFwdCols < jmax) ? j0 + kFwdCols : jmax;
-  pdl_wait();
-  if (done && *done != 0.0) return;
-  for (int32_t j = j0 + threadIdx.x; j < j1; j += 256) {
-    const int64_t q0 = wsrc_ptr[fr.w_off + j], q1 = wsrc_ptr[fr.w_off + j + 1];
-    TV w = r[perm[fr.first + j]];
-    for (int64_t q = q0; q < q1; ++q) w += ubuf[wsrc[q]];
-    wp[j - j0] = w;
+  // static gather indices: column j0 + tid of w, and row r0 + tid's child sum
+  const int32_t jg = j0 + int32_t(threadIdx.x);
+  int32_t gq0 = 0, gq1 = 0, gperm = 0, gsrc[kPre];
+  if (jg < j1) {
+    gq0 = wsrc_ptr[fr.w_off + jg];
+    gq1 = wsrc_ptr[fr.w_off + jg + 1];
+    gperm = perm[fr.first + jg];
   }
-  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kPre; ++k) gsrc[k] = gq0 + k < gq1 ? wsrc[gq0 + k] : -1;
+  const int32_t ie = r0 + int32_t(threadIdx.x);
+  int32_t eq0 = 0, eq1 = 0, esrc[kPre];
+  if (threadIdx.x < RB && ie >= p && ie < m) {
+    eq0 = wsrc_ptr[fr.w_off + ie];
+    eq1 = wsrc_ptr[fr.w_off + ie + 1];
+  }
+#pragma unroll
+  for (int k = 0; k < kPre; ++k) esrc[k] = eq0 + k < eq1 ? wsrc[eq0 + k] : -1;
+  // first Y vectors
   const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int32_t row = r0 + VW * rl;
+  const TF *yc = Y + fr.y_off + row;
+  int32_t jq = j0 + g;
+  bool have = row < m && jq + 24 < j1;
+  V c0{}, c1{}, c2{}, c3{};
+  if (have) {
+    c0 = *reinterpret_cast<const V *>(yc + int64_t(jq) * fr.ldy);
+    c1 = *reinterpret_cast<const V *>(yc + int64_t(jq + 8) * fr.ldy);
+    c2 = *reinterpret_cast<const V *>(yc + int64_t(jq + 16) * fr.ldy);
+    c3 = *reinterpret_cast<const V *>(yc + int64_t(jq + 24) * fr.ldy);
+  }
+  pdl_wait();
+  if (done && *done != 0.0) return;
+  if (jg < j1) {
+    TV w = r[gperm];
+#pragma unroll
+    for (int k = 0; k < kPre; ++k)
+      if (gsrc[k] >= 0) w += ubuf[gsrc[k]];
+    for (int32_t q = gq0 + kPre; q < gq1; ++q) w += ubuf[wsrc[q]];
+    wp[jg - j0] = w;
+  }
+  TV csum = TV(0);
+#pragma unroll
+  for (int k = 0; k < kPre; ++k)
+    if (esrc[k] >= 0) csum += ubuf[esrc[k]];
+  for (int32_t q = eq0 + kPre; q < eq1; ++q) csum += ubuf[wsrc[q]];
+  __syncthreads();
   TV acc[VW];
 #pragma unroll
   for (int e = 0; e < VW; ++e) acc[e] = TV(0);
-  if (row < m) {
-    const TF *yc = Y + fr.y_off + row;
-    int32_t j = j0 + g;
-    for (; j + 24 < j1; j += 32) {
-      V v0 = *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy);
-      V v1 = *reinterpret_cast<const V *>(yc + int64_t(j + 8) * fr.ldy);
-      V v2 = *reinterpret_cast<const V *>(yc + int64_t(j + 16) * fr.ldy);
-      V v3 = *reinterpret_cast<const V *>(yc + int64_t(j + 24) * fr.ldy);
-      const TF *e0 = reinterpret_cast<const TF *>(&v0), *e1 = reinterpret_cast<const TF *>(&v1);
-      const TF *e2 = reinterpret_cast<const TF *>(&v2), *e3 = reinterpret_cast<const TF *>(&v3);
-      const TV w0 = wp[j - j0], w1 = wp[j + 8 - j0], w2 = wp[j + 16 - j0], w3 = wp[j + 24 - j0];
-#pragma unroll
-      for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0 + TV(e1[e]) * w1 + TV(e2[e]) * w2 + TV(e3[e]) * w3;
+  while (have) {
+    const int32_t jn = jq + 32;
+    const bool nhave = jn + 24 < j1;
+    V n0{}, n1{}, n2{}, n3{};
+    if (nhave) {
+      n0 = *reinterpret_cast<const V *>(yc + int64_t(jn) * fr.ldy);
+      n1 = *reinterpret_cast<const V *>(yc + int64_t(jn + 8) * fr.ldy);
+      n2 = *reinterpret_cast<const V *>(yc + int64_t(jn + 16) * fr.ldy);
+      n3 = *reinterpret_cast<const V *>(yc + int64_t(jn + 24) * fr.ldy);
     }
-    for (; j < j1; j += 8) {
-      V v0 = *reinterpret_cast<const V *>(yc + int64_t(j) * fr.ldy);
-      const TF *e0 = reinterpret_cast<const TF *>(&v0);
-      const TV w0 = wp[j - j0];
+    const TV w0 = wp[jq - j0], w1 = wp[jq + 8 - j0], w2 = wp[jq + 16 - j0], w3 = wp[jq + 24 - j0];
 #pragma unroll
-      for (int e = 0; e < VW; ++e) acc[e] += TV(e0[e]) * w0;
+    for (int e = 0; e < VW; ++e)
+      acc[e] += TV(vget(c0, e)) * w0 + TV(vget(c1, e)) * w1 + TV(vget(c2, e)) * w2 + TV(vget(c3, e)) * w3;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+    jq = jn;
+    have = nhave;
+  }
+  if (row < m) {
+    for (; jq < j1; jq += 8) {
+      const V v0 = *reinterpret_cast<const V *>(yc + int64_t(jq) * fr.ldy);
+      const TV w0 = wp[jq - j0];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) acc[e] += TV(vget(v0, e)) * w0;
     }
   }
 #pragma unroll
@@ -925,23 +979,23 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
     const int tt = threadIdx.x + 256 * k;
     const int32_t i = r0 + tt;
     if (tt >= RB || i >= m) continue;
-    if (i < p) {
+    if (i < p)
       yperm[fr.first + i] = TV(double(sums[k]) * Dinv[fr.first + i]);
-    } else {
-      TV w = TV(0);
-      for (int64_t q = wsrc_ptr[fr.w_off + i]; q < wsrc_ptr[fr.w_off + i + 1]; ++q) w += ubuf[wsrc[q]];
-      ubuf[fr.u_off + i - p] = w + sums[k];
-    }
+    else
+      ubuf[fr.u_off + i - p] = csum + sums[k];
   }
 }
 
 // Backward level, task (front, c0, i0, slot): pivot columns [c0, c0 + 32)
-// over the rows [i0, i0 + kBwdRows); warp w owns columns c0 + w + 8k
-// (k = 0..3) and streams them together (four 16-byte loads in flight per
-// lane).  x = [D^{-1} y_P; z_U] is staged in shared memory from the
-// VW-aligned row at or below c0; rows above a column are zeros of L^{-1}, so
-// reading from the aligned row is exact.  Columns longer than kBwdRows rows
-// are split over CTAs (slot >= 0) and combined in row-chunk order.
+// over the rows [i0, i0 + kBwdRows); warp w owns columns c0 + w + 8k (k < 4)
+// and streams them together, the next four 16-byte loads per lane in flight
+// while the current ones are used.  x = [D^{-1} y_P; z_U] is staged in
+// shared memory from the VW-aligned row at or below c0; rows above a column
+// are zeros of L^{-1}, so reading from the aligned row is exact.  The static
+// data (descriptors, the update rows' positions, the first Y vectors) is
+// loaded before waiting for the previous level.  Columns longer than
+// kBwdRows rows are split over CTAs (slot >= 0) and combined in row-chunk
+// order.
 template <typename TF, typename TV>
 __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
@@ -952,6 +1006,7 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
                                                   const double *__restrict__ done) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
+  constexpr int XS = kBwdRows / 256;  // staged rows per thread
   __shared__ __align__(16) TV xs[kBwdRows];
   pdl_launch_dependents();
   const int4 t = tasks[blockIdx.x];
@@ -961,19 +1016,20 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
   const int32_t a0 = c0 & ~(VW - 1);
   const int32_t xa = a0 > ilo0 ? a0 : ilo0;                                 // first row of this task
   const int32_t xb = (ilo0 + kBwdRows < fr.ldy) ? ilo0 + kBwdRows : fr.ldy;  // end row
-  pdl_wait();
-  if (done && *done != 0.0) return;
+  // static: where each staged row comes from (-1: zero, >= 0: yperm index,
+  // <= -2: z index -2 - idx)
   const int32_t *urows = upd_rows_old + fr.rows_off;
-  for (int32_t tt = threadIdx.x; tt < xb - xa; tt += 256) {
+  int32_t xsrc[XS];
+#pragma unroll
+  for (int k = 0; k < XS; ++k) {
+    const int32_t tt = int32_t(threadIdx.x) + 256 * k;
     const int32_t i = xa + tt;
-    xs[tt] = (i < c0 || i >= m) ? TV(0) : (i < p ? yperm[fr.first + i] : z[urows[i - p]]);
+    xsrc[k] = -1;
+    if (tt < xb - xa && i >= c0 && i < m) xsrc[k] = i < p ? fr.first + i : -2 - urows[i - p];
   }
-  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t jc[4];
+  int32_t jc[4], ist[4];
   const TF *yc[4];
-  int32_t ist[4];
-  TV acc[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     jc[k] = c0 + w + 8 * k;
@@ -981,19 +1037,35 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
     yc[k] = Y + fr.y_off + int64_t(j) * fr.ldy;
     const int32_t ja = j & ~(VW - 1);
     ist[k] = (ja > xa ? ja : xa) + VW * lane;
-    acc[k] = TV(0);
   }
+  V cv[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cv[k] = ist[k] < xb ? *reinterpret_cast<const V *>(yc[k] + ist[k]) : V{};
+  pdl_wait();
+  if (done && *done != 0.0) return;
+#pragma unroll
+  for (int k = 0; k < XS; ++k) {
+    const int32_t tt = int32_t(threadIdx.x) + 256 * k;
+    if (tt < xb - xa) xs[tt] = xsrc[k] == -1 ? TV(0) : (xsrc[k] >= 0 ? yperm[xsrc[k]] : z[-2 - xsrc[k]]);
+  }
+  __syncthreads();
+  TV acc[4] = {TV(0), TV(0), TV(0), TV(0)};
   const int32_t ilo = ist[0] < ist[3] ? ist[0] : ist[3];
   for (int32_t off = 0; ilo + off < xb; off += 32 * VW) {
+    V nv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int32_t i = ist[k] + off + 32 * VW;
+      nv[k] = i < xb ? *reinterpret_cast<const V *>(yc[k] + i) : V{};
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int32_t i = ist[k] + off;
       if (i < xb) {
-        V v = *reinterpret_cast<const V *>(yc[k] + i);
-        const TF *e = reinterpret_cast<const TF *>(&v);
 #pragma unroll
-        for (int q = 0; q < VW; ++q) acc[k] += TV(e[q]) * xs[i - xa + q];
+        for (int q = 0; q < VW; ++q) acc[k] += TV(vget(cv[k], q)) * xs[i - xa + q];
       }
+      cv[k] = nv[k];
     }
   }
 #pragma unroll
