@@ -57,6 +57,11 @@ def _tf32_peak():
 
 MATERIAL_NAMES = {0: "Saint Venant-Kirchhoff", 1: "neo-Hookean", 2: "Mooney-Rivlin"}
 
+# DRAM bytes per launch of the update kernel on the 350k-DOF workload, from one
+# ncu capture (profiles/dram_traffic_tet30x30x120-mr.md); None when the
+# kernel changed after the capture or for another workload
+UPDATE_TRAFFIC = {"tet30x30x120-mr": 188.74e6}
+
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
@@ -391,7 +396,7 @@ def main():
         roofline = {"bound": "tensor",
                     "kernel": "front_update_tc_kernel (factor trailing updates, tcgen05 kind::tf32, 3xTF32)",
                     "achieved": upd_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": upd_tflops / tf32_peak,
-                    "traffic": None, "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
+                    "traffic": UPDATE_TRAFFIC.get(args.workload), "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
                     "peak_source": tf32_src,
                     "note": "achieved counts algorithmic flops; 3xTF32 issues 3 TF32 MMAs per product, "
                             "so frac <= 1/3"}
