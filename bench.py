@@ -57,9 +57,10 @@ def _tf32_peak():
 
 MATERIAL_NAMES = {0: "Saint Venant-Kirchhoff", 1: "neo-Hookean", 2: "Mooney-Rivlin"}
 
-# DRAM bytes per launch of the update kernel on the 350k-DOF workload, from one
-# ncu capture (profiles/dram_traffic_tet30x30x120-mr.md); None when the
-# kernel changed after the capture or for another workload
+# DRAM bytes per launch of the update kernel on the 350k-DOF workload: one ncu
+# capture of dram__bytes_read.sum + dram__bytes_write.sum over the 194 update
+# launches of a factorisation, divided by 194.  To be retaken (or dropped)
+# whenever the kernel changes; other workloads report None.
 UPDATE_TRAFFIC = {"tet30x30x120-mr": 188.74e6}
 
 
