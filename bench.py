@@ -317,7 +317,7 @@ def main():
     if args.precision is not None:
         wl.precision = 1 if args.precision == "mixed" else 0
     K, W = args.steps, args.warmup
-    stream = torch.cuda.Stream()
+    stream = torch.cuda.Stream(priority=-1)  # above the library's background factor stream
     dev = torch.device("cuda", local)
     ctx = fe.FEContext.from_workload(wl, device_ptrs=1, stream=stream.cuda_stream, profile_stages=1,
                                      nd_leaf_nodes=args.nd_leaf, use_graph=1 if args.graph else 0)

@@ -90,7 +90,11 @@ typedef struct {
   int32_t refactor_every; /* R: factor A_s at steps s = 0 mod R; that factor
                              preconditions steps s+1 .. s+R (step 0 uses A_0)  */
   int32_t device_ptrs;    /* 1: state/force buffers are device pointers       */
-  void *stream;           /* cudaStream_t for device_ptrs = 1 (NULL: legacy)  */
+  void *stream;           /* cudaStream_t for device_ptrs = 1 (NULL: the
+                             library's own stream, created at the highest
+                             priority).  The lagged factorisation runs on a
+                             library stream at the lowest priority: a
+                             caller's stream should have a higher one.      */
   int32_t keep_checkpoints; /* store (q_t, v_t) of every step for fe_adjoint  */
   int32_t nd_leaf_nodes;  /* nested-dissection leaf size in nodes (0: 64)     */
   double inner_tol;       /* FE_MIXED inner PCG tolerance per sweep (0: 1e-4) */

@@ -119,13 +119,19 @@ int ensure_device(fe_ctx *c) {
   DeviceState *d = new DeviceState();
   c->dev = d;
   FE_CUDA_TRY(cudaGetDevice(&d->device));
+  // The lagged factorisation is background work with R steps of slack: its
+  // stream gets the lowest priority, the library's own main stream the
+  // highest, so the CTA scheduler serves the PCG first (a caller's stream
+  // keeps the priority the caller gave it).
+  int prio_low = 0, prio_high = 0;
+  FE_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
   if (c->opt.device_ptrs && c->opt.stream) {
     d->stream = reinterpret_cast<cudaStream_t>(c->opt.stream);
   } else {
-    FE_CUDA_TRY(cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking));
+    FE_CUDA_TRY(cudaStreamCreateWithPriority(&d->stream, cudaStreamNonBlocking, prio_high));
     d->own_stream = true;
   }
-  FE_CUDA_TRY(cudaStreamCreateWithFlags(&d->fstream, cudaStreamNonBlocking));
+  FE_CUDA_TRY(cudaStreamCreateWithPriority(&d->fstream, cudaStreamNonBlocking, prio_low));
   FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_assembled, cudaEventDisableTiming));
   FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_factored, cudaEventDisableTiming));
   FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_apply_done, cudaEventDisableTiming));
