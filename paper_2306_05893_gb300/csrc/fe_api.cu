@@ -219,7 +219,8 @@ int ensure_device(fe_ctx *c) {
     o.child_begin = c->child_ptr[f]; o.child_end = c->child_ptr[f + 1];
     o.f_off = F.f_off; o.y_off = F.y_off; o.w_off = F.w_off; o.u_off = F.u_off;
     o.rows_off = F.rows_off; o.fac_off = fac;
-    o.ldy = F.ldy; o.pad_ = 0;
+    o.ldy = F.ldy; o.parent = F.parent;
+    o.nfwd = c->front_nfwd[f]; o.nbwd = c->front_nbwd[f];
     fac += F.npiv + 1;
   }
   FE_TRY(upload(c, d, &d->fronts, df));
@@ -276,6 +277,21 @@ int ensure_device(fe_ctx *c) {
     FE_TRY(dalloc(c, d, &d->na, size_t(c->n)));
     FE_TRY(dalloc(c, d, &d->nq, size_t(c->n)));
     FE_TRY(dalloc(c, d, &d->nv, size_t(c->n)));
+  }
+  // dataflow application: task lists and counters; the counters start in
+  // their reset state (forward: pending children; backward: 0 done) and
+  // every application leaves the other direction's counters reset
+  FE_TRY(upload(c, d, &d->apply_fwd, c->apply_fwd));
+  FE_TRY(upload(c, d, &d->apply_bwd, c->apply_bwd));
+  d->n_apply_fwd = int64_t(c->apply_fwd.size() / 4);
+  d->n_apply_bwd = int64_t(c->apply_bwd.size() / 4);
+  {
+    std::vector<int> pend(nf), zero(nf, 0);
+    for (int64_t f = 0; f < nf; ++f) pend[f] = c->child_ptr[f + 1] - c->child_ptr[f];
+    FE_TRY(upload(c, d, &d->df_pend, pend));
+    FE_TRY(upload(c, d, &d->df_fdone, zero));
+    FE_TRY(upload(c, d, &d->df_bdone, zero));
+    FE_TRY(upload(c, d, &d->df_ctl, std::vector<int>(4, 0)));
   }
   const size_t rb = mixed(c) ? 128 : 64;
   FE_TRY(dallocv(c, d, &d->part_f, size_t(std::max<int64_t>(c->fwd_slots, 1)) * rb * ts));

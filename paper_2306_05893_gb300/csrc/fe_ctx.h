@@ -111,6 +111,11 @@ struct fe_ctx {
   int64_t f_total = 0, y_total = 0, w_total = 0, u_total = 0;
   // partial-sum slots of the split apply tasks (slot = -1: a block done by one task)
   int64_t fwd_slots = 0, bwd_slots = 0;
+  // dataflow application: every level's tasks in one list per direction
+  // (level order for the forward solve, reverse level order backward) and
+  // the number of tasks of every front in each
+  std::vector<int32_t> apply_fwd, apply_bwd;  // int4 per task
+  std::vector<int32_t> front_nfwd, front_nbwd;
   double factor_flops = 0;
   int64_t y_nnz = 0;
 

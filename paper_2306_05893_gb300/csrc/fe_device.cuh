@@ -21,7 +21,8 @@ namespace fe {
 struct DFront {
   int32_t first, npiv, nupd, m;
   int32_t child_begin, child_end;    // into child_list
-  int32_t ldy, pad_;
+  int32_t ldy, parent;               // parent front (-1: a root)
+  int32_t nfwd, nbwd;                // tasks of this front in the dataflow application lists
   int64_t f_off, y_off, w_off, u_off, rows_off, fac_off;
 };
 
@@ -107,6 +108,12 @@ struct DeviceState {
   std::vector<PcgGraph> graphs;
   void *part_f = nullptr, *part_b = nullptr;                // partial sums of split apply tasks
   int *tick_f = nullptr, *tick_b = nullptr;                 // their tickets (zero between launches)
+  // dataflow application: task lists, per-front counters (forward: children
+  // still pending; backward: tasks done), task queues and the abort flag
+  int32_t *apply_fwd = nullptr, *apply_bwd = nullptr;
+  int64_t n_apply_fwd = 0, n_apply_bwd = 0;
+  int *df_pend = nullptr, *df_fdone = nullptr, *df_bdone = nullptr, *df_ctl = nullptr;
+  int df_grid = 0;                                          // resident CTAs of the application kernels
   int cur = 0;                     // buffer the solver reads
   int factor_pending = -1;         // buffer being written on fstream, or -1
   int64_t pending_step = -1;       // step whose A the pending factor holds

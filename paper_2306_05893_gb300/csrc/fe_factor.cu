@@ -827,22 +827,56 @@ __device__ __forceinline__ bool last_of_block(int *ticket, int nch) {
   return s_last;
 }
 
-// Forward level, task (front, r0, j0, slot): rows [r0, r0 + 32*VW) of Y w_P
-// over the pivot columns [j0, j0 + kFwdCols), where w = [r_P; 0] + the
-// children's update vectors (gathered through the position lists, children
-// in fixed order).  256 threads: 32 row lanes of VW consecutive rows (one
-// 16-byte load per column) x 8 column groups, loads of the next 4 columns in
-// flight while the current ones are used.  Launched as a programmatic
-// dependent of the previous level: the static data (descriptors, gather
-// indices, the first Y vectors) is loaded before waiting for that level, the
-// vectors it produced after.  Rows < p give y_P (times D^{-1}) into yperm,
-// rows >= p the update vector.  Row blocks with more than kFwdCols columns
-// are split over CTAs (slot >= 0) so the few large fronts near the root
-// still stream Y with the whole GPU.
+// The preconditioner application as a dataflow over the front tree: one
+// persistent launch per direction.  CTAs take tasks from a queue in the
+// lists' order (forward: every level's tasks, leaves first; backward: root
+// first), which is a topological order of the dependencies, and a task waits
+// only for tasks fetched before it (held by running CTAs), so the waits
+// always end; they are bounded in time anyway (FLAG_WAIT_TIMEOUT, then every
+// later wait gives up at once through the abort word).  Dependencies:
+// forward, a front's tasks wait until all its children are done (counter
+// of pending children, decremented by each child's last task); backward,
+// until all tasks of the parent are done.  Vectors written by other tasks
+// of the same launch are read through L2 (ld.cg), never a stale L1 line.
+// Control words df_ctl: [0] forward queue, [1] backward queue, [2] forward
+// abort, [3] backward abort; each launch resets the other direction's words.
+constexpr uint64_t kDepWaitNs = 1000000000ull;
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// thread 0: wait until *p == target (or abort / timeout); true when satisfied
+__device__ __forceinline__ bool dep_wait(const int *p, int target, int *abort_word, int *flags) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (ld_acquire(p) == target) return true;
+    if (ld_acquire(abort_word) != 0) return false;
+    if (global_ns() - t0 > kDepWaitNs) {
+      atomicOr(flags, FLAG_WAIT_TIMEOUT);
+      atomicExch(abort_word, 1);
+      return false;
+    }
+    __nanosleep(64);
+  }
+}
+
+// Forward task (front, r0, j0, slot): rows [r0, r0 + 32*VW) of Y w_P over the
+// pivot columns [j0, j0 + kFwdCols), where w = [r_P; 0] + the children's
+// update vectors (gathered through the position lists, children in fixed
+// order).  256 threads: 32 row lanes of VW consecutive rows (one 16-byte
+// load per column) x 8 column groups, the next 4 columns' loads in flight
+// while the current ones are used.  Static data (descriptors, gather
+// indices, the first Y vectors) is loaded before the dependency wait.  Rows
+// < p give y_P (times D^{-1}) into yperm, rows >= p the update vector.  Row
+// blocks with more than kFwdCols columns are split over tasks (slot >= 0)
+// and combined in chunk order by the last one (deterministic).
 constexpr int kPre = 4;  // gather sources prefetched per position
 
 template <typename TF, typename TV>
-__global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks,
+__global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks, int64_t ntask,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
                                                   const double *__restrict__ Dinv,
                                                   const int32_t *__restrict__ perm,
@@ -850,249 +884,304 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
                                                   const int32_t *__restrict__ wsrc, const TV *__restrict__ r,
                                                   TV *__restrict__ ubuf, TV *__restrict__ yperm,
                                                   TV *__restrict__ part, int *__restrict__ tickets,
-                                                  const double *__restrict__ done) {
+                                                  int *pend, int *fdone, int *bdone, int *ctl, int nfronts,
+                                                  int *flags, const double *__restrict__ done) {
   static_assert(kFwdCols == 256, "one gathered column per thread");
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int RB = 32 * VW;
   __shared__ TV gpart[8 * RB];
   __shared__ TV wp[kFwdCols];
-  pdl_launch_dependents();
-  const int4 t = tasks[blockIdx.x];
-  const DFront fr = fronts[t.x];
-  const int32_t r0 = t.y, j0 = t.z, slot = t.w;
-  const int32_t p = fr.npiv, m = fr.m;
-  const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
-  const int32_t j1 = (j0 + kFwdCols < jmax) ? j0 + kFwdCols : jmax;
-  // static gather indices: column j0 + tid of w, and row r0 + tid's child sum
-  const int32_t jg = j0 + int32_t(threadIdx.x);
-  int32_t gq0 = 0, gq1 = 0, gperm = 0, gsrc[kPre];
-  if (jg < j1) {
-    gq0 = wsrc_ptr[fr.w_off + jg];
-    gq1 = wsrc_ptr[fr.w_off + jg + 1];
-    gperm = perm[fr.first + jg];
-  }
-#pragma unroll
-  for (int k = 0; k < kPre; ++k) gsrc[k] = gq0 + k < gq1 ? wsrc[gq0 + k] : -1;
-  const int32_t ie = r0 + int32_t(threadIdx.x);
-  int32_t eq0 = 0, eq1 = 0, esrc[kPre];
-  if (threadIdx.x < RB && ie >= p && ie < m) {
-    eq0 = wsrc_ptr[fr.w_off + ie];
-    eq1 = wsrc_ptr[fr.w_off + ie + 1];
-  }
-#pragma unroll
-  for (int k = 0; k < kPre; ++k) esrc[k] = eq0 + k < eq1 ? wsrc[eq0 + k] : -1;
-  // first Y vectors
-  const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int32_t row = r0 + VW * rl;
-  const TF *yc = Y + fr.y_off + row;
-  int32_t jq = j0 + g;
-  bool have = row < m && jq + 24 < j1;
-  V c0{}, c1{}, c2{}, c3{};
-  if (have) {
-    c0 = *reinterpret_cast<const V *>(yc + int64_t(jq) * fr.ldy);
-    c1 = *reinterpret_cast<const V *>(yc + int64_t(jq + 8) * fr.ldy);
-    c2 = *reinterpret_cast<const V *>(yc + int64_t(jq + 16) * fr.ldy);
-    c3 = *reinterpret_cast<const V *>(yc + int64_t(jq + 24) * fr.ldy);
-  }
-  pdl_wait();
+  __shared__ int s_task, s_ok;
   if (done && *done != 0.0) return;
-  if (jg < j1) {
-    TV w = r[gperm];
-#pragma unroll
-    for (int k = 0; k < kPre; ++k)
-      if (gsrc[k] >= 0) w += ubuf[gsrc[k]];
-    for (int32_t q = gq0 + kPre; q < gq1; ++q) w += ubuf[wsrc[q]];
-    wp[jg - j0] = w;
+  // leave the backward counters reset for the backward launch that follows
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < nfronts; i += gridDim.x * 256) bdone[i] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl[1] = 0;
+    ctl[3] = 0;
   }
-  TV csum = TV(0);
-#pragma unroll
-  for (int k = 0; k < kPre; ++k)
-    if (esrc[k] >= 0) csum += ubuf[esrc[k]];
-  for (int32_t q = eq0 + kPre; q < eq1; ++q) csum += ubuf[wsrc[q]];
-  __syncthreads();
-  TV acc[VW];
-#pragma unroll
-  for (int e = 0; e < VW; ++e) acc[e] = TV(0);
-  while (have) {
-    const int32_t jn = jq + 32;
-    const bool nhave = jn + 24 < j1;
-    V n0{}, n1{}, n2{}, n3{};
-    if (nhave) {
-      n0 = *reinterpret_cast<const V *>(yc + int64_t(jn) * fr.ldy);
-      n1 = *reinterpret_cast<const V *>(yc + int64_t(jn + 8) * fr.ldy);
-      n2 = *reinterpret_cast<const V *>(yc + int64_t(jn + 16) * fr.ldy);
-      n3 = *reinterpret_cast<const V *>(yc + int64_t(jn + 24) * fr.ldy);
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(ctl + 0, 1);
+    __syncthreads();
+    const int64_t ti = s_task;
+    if (ti >= ntask) break;
+    const int4 t = tasks[ti];
+    const DFront fr = fronts[t.x];
+    const int32_t r0 = t.y, j0 = t.z, slot = t.w;
+    const int32_t p = fr.npiv, m = fr.m;
+    const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
+    const int32_t j1 = (j0 + kFwdCols < jmax) ? j0 + kFwdCols : jmax;
+    // static gather indices: column j0 + tid of w, and row r0 + tid's child sum
+    const int32_t jg = j0 + int32_t(threadIdx.x);
+    int32_t gq0 = 0, gq1 = 0, gperm = 0, gsrc[kPre];
+    if (jg < j1) {
+      gq0 = wsrc_ptr[fr.w_off + jg];
+      gq1 = wsrc_ptr[fr.w_off + jg + 1];
+      gperm = perm[fr.first + jg];
     }
-    const TV w0 = wp[jq - j0], w1 = wp[jq + 8 - j0], w2 = wp[jq + 16 - j0], w3 = wp[jq + 24 - j0];
 #pragma unroll
-    for (int e = 0; e < VW; ++e)
-      acc[e] += TV(vget(c0, e)) * w0 + TV(vget(c1, e)) * w1 + TV(vget(c2, e)) * w2 + TV(vget(c3, e)) * w3;
-    c0 = n0;
-    c1 = n1;
-    c2 = n2;
-    c3 = n3;
-    jq = jn;
-    have = nhave;
-  }
-  if (row < m) {
-    for (; jq < j1; jq += 8) {
-      const V v0 = *reinterpret_cast<const V *>(yc + int64_t(jq) * fr.ldy);
-      const TV w0 = wp[jq - j0];
-#pragma unroll
-      for (int e = 0; e < VW; ++e) acc[e] += TV(vget(v0, e)) * w0;
+    for (int k = 0; k < kPre; ++k) gsrc[k] = gq0 + k < gq1 ? wsrc[gq0 + k] : -1;
+    const int32_t ie = r0 + int32_t(threadIdx.x);
+    int32_t eq0 = 0, eq1 = 0, esrc[kPre];
+    if (threadIdx.x < RB && ie >= p && ie < m) {
+      eq0 = wsrc_ptr[fr.w_off + ie];
+      eq1 = wsrc_ptr[fr.w_off + ie + 1];
     }
-  }
 #pragma unroll
-  for (int e = 0; e < VW; ++e) gpart[g * RB + VW * rl + e] = acc[e];
-  __syncthreads();
-  TV sums[(RB + 255) / 256];
-#pragma unroll
-  for (int k = 0; k < (RB + 255) / 256; ++k) {
-    const int tt = threadIdx.x + 256 * k;
-    TV sm = TV(0);
-    if (tt < RB) {
-#pragma unroll
-      for (int gg = 0; gg < 8; ++gg) sm += gpart[gg * RB + tt];
+    for (int k = 0; k < kPre; ++k) esrc[k] = eq0 + k < eq1 ? wsrc[eq0 + k] : -1;
+    const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int32_t row = r0 + VW * rl;
+    const TF *yc = Y + fr.y_off + row;
+    int32_t jq = j0 + g;
+    bool have = row < m && jq + 24 < j1;
+    V c0{}, c1{}, c2{}, c3{};
+    if (have) {
+      c0 = *reinterpret_cast<const V *>(yc + int64_t(jq) * fr.ldy);
+      c1 = *reinterpret_cast<const V *>(yc + int64_t(jq + 8) * fr.ldy);
+      c2 = *reinterpret_cast<const V *>(yc + int64_t(jq + 16) * fr.ldy);
+      c3 = *reinterpret_cast<const V *>(yc + int64_t(jq + 24) * fr.ldy);
     }
-    sums[k] = sm;
-  }
-  if (slot >= 0) {
-    const int nch = (jmax + kFwdCols - 1) / kFwdCols;
+    // the children's update vectors must be complete
+    if (threadIdx.x == 0) s_ok = dep_wait(pend + t.x, 0, ctl + 2, flags);
+    __syncthreads();
+    if (s_ok) {
+      if (jg < j1) {
+        TV w = r[gperm];
 #pragma unroll
-    for (int k = 0; k < (RB + 255) / 256; ++k) {
-      const int tt = threadIdx.x + 256 * k;
-      if (tt < RB) part[int64_t(slot + j0 / kFwdCols) * RB + tt] = sums[k];
+        for (int k = 0; k < kPre; ++k)
+          if (gsrc[k] >= 0) w += __ldcg(ubuf + gsrc[k]);
+        for (int32_t q = gq0 + kPre; q < gq1; ++q) w += __ldcg(ubuf + wsrc[q]);
+        wp[jg - j0] = w;
+      }
     }
-    if (!last_of_block(tickets + slot, nch)) return;
+    TV csum = TV(0);
+    if (s_ok) {
+#pragma unroll
+      for (int k = 0; k < kPre; ++k)
+        if (esrc[k] >= 0) csum += __ldcg(ubuf + esrc[k]);
+      for (int32_t q = eq0 + kPre; q < eq1; ++q) csum += __ldcg(ubuf + wsrc[q]);
+    }
+    __syncthreads();
+    TV acc[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) acc[e] = TV(0);
+    if (!s_ok) have = false;
+    while (have) {
+      const int32_t jn = jq + 32;
+      const bool nhave = jn + 24 < j1;
+      V n0{}, n1{}, n2{}, n3{};
+      if (nhave) {
+        n0 = *reinterpret_cast<const V *>(yc + int64_t(jn) * fr.ldy);
+        n1 = *reinterpret_cast<const V *>(yc + int64_t(jn + 8) * fr.ldy);
+        n2 = *reinterpret_cast<const V *>(yc + int64_t(jn + 16) * fr.ldy);
+        n3 = *reinterpret_cast<const V *>(yc + int64_t(jn + 24) * fr.ldy);
+      }
+      const TV w0 = wp[jq - j0], w1 = wp[jq + 8 - j0], w2 = wp[jq + 16 - j0], w3 = wp[jq + 24 - j0];
+#pragma unroll
+      for (int e = 0; e < VW; ++e)
+        acc[e] += TV(vget(c0, e)) * w0 + TV(vget(c1, e)) * w1 + TV(vget(c2, e)) * w2 + TV(vget(c3, e)) * w3;
+      c0 = n0;
+      c1 = n1;
+      c2 = n2;
+      c3 = n3;
+      jq = jn;
+      have = nhave;
+    }
+    if (s_ok && row < m) {
+      for (; jq < j1; jq += 8) {
+        const V v0 = *reinterpret_cast<const V *>(yc + int64_t(jq) * fr.ldy);
+        const TV w0 = wp[jq - j0];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) acc[e] += TV(vget(v0, e)) * w0;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < VW; ++e) gpart[g * RB + VW * rl + e] = acc[e];
+    __syncthreads();
+    TV sums[(RB + 255) / 256];
 #pragma unroll
     for (int k = 0; k < (RB + 255) / 256; ++k) {
       const int tt = threadIdx.x + 256 * k;
       TV sm = TV(0);
-      if (tt < RB)
-        for (int ch = 0; ch < nch; ++ch) sm += __ldcg(part + int64_t(slot + ch) * RB + tt);
+      if (tt < RB) {
+#pragma unroll
+        for (int gg = 0; gg < 8; ++gg) sm += gpart[gg * RB + tt];
+      }
       sums[k] = sm;
     }
-  }
+    bool final = true;
+    if (slot >= 0) {
+      const int nch = (jmax + kFwdCols - 1) / kFwdCols;
 #pragma unroll
-  for (int k = 0; k < (RB + 255) / 256; ++k) {
-    const int tt = threadIdx.x + 256 * k;
-    const int32_t i = r0 + tt;
-    if (tt >= RB || i >= m) continue;
-    if (i < p)
-      yperm[fr.first + i] = TV(double(sums[k]) * Dinv[fr.first + i]);
-    else
-      ubuf[fr.u_off + i - p] = csum + sums[k];
+      for (int k = 0; k < (RB + 255) / 256; ++k) {
+        const int tt = threadIdx.x + 256 * k;
+        if (tt < RB) part[int64_t(slot + j0 / kFwdCols) * RB + tt] = sums[k];
+      }
+      final = last_of_block(tickets + slot, nch);
+      if (final) {
+#pragma unroll
+        for (int k = 0; k < (RB + 255) / 256; ++k) {
+          const int tt = threadIdx.x + 256 * k;
+          TV sm = TV(0);
+          if (tt < RB)
+            for (int ch = 0; ch < nch; ++ch) sm += __ldcg(part + int64_t(slot + ch) * RB + tt);
+          sums[k] = sm;
+        }
+      }
+    }
+    if (final) {
+#pragma unroll
+      for (int k = 0; k < (RB + 255) / 256; ++k) {
+        const int tt = threadIdx.x + 256 * k;
+        const int32_t i = r0 + tt;
+        if (tt >= RB || i >= m) continue;
+        if (i < p)
+          yperm[fr.first + i] = TV(double(sums[k]) * Dinv[fr.first + i]);
+        else
+          ubuf[fr.u_off + i - p] = csum + sums[k];
+      }
+    }
+    // completion: the front's last task releases the parent
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int c = atomicAdd(fdone + t.x, 1);
+      if (c == fr.nfwd - 1 && fr.parent >= 0) {
+        __threadfence();
+        atomicSub(pend + fr.parent, 1);
+      }
+    }
   }
 }
 
-// Backward level, task (front, c0, i0, slot): pivot columns [c0, c0 + 32)
-// over the rows [i0, i0 + kBwdRows); warp w owns columns c0 + w + 8k (k < 4)
-// and streams them together, the next four 16-byte loads per lane in flight
-// while the current ones are used.  x = [D^{-1} y_P; z_U] is staged in
-// shared memory from the VW-aligned row at or below c0; rows above a column
-// are zeros of L^{-1}, so reading from the aligned row is exact.  The static
-// data (descriptors, the update rows' positions, the first Y vectors) is
-// loaded before waiting for the previous level.  Columns longer than
-// kBwdRows rows are split over CTAs (slot >= 0) and combined in row-chunk
-// order.
+// Backward task (front, c0, i0, slot): pivot columns [c0, c0 + 32) over the
+// rows [i0, i0 + kBwdRows); warp w owns columns c0 + w + 8k (k < 4) and
+// streams them together, the next four 16-byte loads per lane in flight.
+// x = [D^{-1} y_P; z_U] is staged in shared memory from the VW-aligned row at
+// or below c0 (rows above a column are zeros of L^{-1}, so reading from the
+// aligned row is exact); z_U was written by the parent's tasks.  Columns
+// longer than kBwdRows rows are split over tasks (slot >= 0) and combined in
+// row-chunk order.  Also resets the forward counters for the next
+// application.
 template <typename TF, typename TV>
-__global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks,
+__global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks, int64_t ntask,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
                                                   const int32_t *__restrict__ perm,
                                                   const int32_t *__restrict__ upd_rows_old,
                                                   const TV *__restrict__ yperm, TV *__restrict__ z,
                                                   TV *__restrict__ part, int *__restrict__ tickets,
-                                                  const double *__restrict__ done) {
+                                                  int *pend, int *fdone, int *bdone, int *ctl, int nfronts,
+                                                  int *flags, const double *__restrict__ done) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int XS = kBwdRows / 256;  // staged rows per thread
   __shared__ __align__(16) TV xs[kBwdRows];
-  pdl_launch_dependents();
-  const int4 t = tasks[blockIdx.x];
-  const DFront fr = fronts[t.x];
-  const int32_t c0 = t.y, ilo0 = t.z, slot = t.w;
-  const int32_t p = fr.npiv, m = fr.m;
-  const int32_t a0 = c0 & ~(VW - 1);
-  const int32_t xa = a0 > ilo0 ? a0 : ilo0;                                 // first row of this task
-  const int32_t xb = (ilo0 + kBwdRows < fr.ldy) ? ilo0 + kBwdRows : fr.ldy;  // end row
-  // static: where each staged row comes from (-1: zero, >= 0: yperm index,
-  // <= -2: z index -2 - idx)
-  const int32_t *urows = upd_rows_old + fr.rows_off;
-  int32_t xsrc[XS];
-#pragma unroll
-  for (int k = 0; k < XS; ++k) {
-    const int32_t tt = int32_t(threadIdx.x) + 256 * k;
-    const int32_t i = xa + tt;
-    xsrc[k] = -1;
-    if (tt < xb - xa && i >= c0 && i < m) xsrc[k] = i < p ? fr.first + i : -2 - urows[i - p];
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t jc[4], ist[4];
-  const TF *yc[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    jc[k] = c0 + w + 8 * k;
-    const int32_t j = jc[k] < p ? jc[k] : c0;  // out-of-range columns read a valid one, result dropped
-    yc[k] = Y + fr.y_off + int64_t(j) * fr.ldy;
-    const int32_t ja = j & ~(VW - 1);
-    ist[k] = (ja > xa ? ja : xa) + VW * lane;
-  }
-  V cv[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) cv[k] = ist[k] < xb ? *reinterpret_cast<const V *>(yc[k] + ist[k]) : V{};
-  pdl_wait();
+  __shared__ int s_task, s_ok;
   if (done && *done != 0.0) return;
-#pragma unroll
-  for (int k = 0; k < XS; ++k) {
-    const int32_t tt = int32_t(threadIdx.x) + 256 * k;
-    if (tt < xb - xa) xs[tt] = xsrc[k] == -1 ? TV(0) : (xsrc[k] >= 0 ? yperm[xsrc[k]] : z[-2 - xsrc[k]]);
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < nfronts; i += gridDim.x * 256) {
+    pend[i] = fronts[i].child_end - fronts[i].child_begin;
+    fdone[i] = 0;
   }
-  __syncthreads();
-  TV acc[4] = {TV(0), TV(0), TV(0), TV(0)};
-  const int32_t ilo = ist[0] < ist[3] ? ist[0] : ist[3];
-  for (int32_t off = 0; ilo + off < xb; off += 32 * VW) {
-    V nv[4];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl[0] = 0;
+    ctl[2] = 0;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(ctl + 1, 1);
+    __syncthreads();
+    const int64_t ti = s_task;
+    if (ti >= ntask) break;
+    const int4 t = tasks[ti];
+    const DFront fr = fronts[t.x];
+    const int32_t c0 = t.y, ilo0 = t.z, slot = t.w;
+    const int32_t p = fr.npiv, m = fr.m;
+    const int32_t a0 = c0 & ~(VW - 1);
+    const int32_t xa = a0 > ilo0 ? a0 : ilo0;                                 // first row of this task
+    const int32_t xb = (ilo0 + kBwdRows < fr.ldy) ? ilo0 + kBwdRows : fr.ldy;  // end row
+    // static: where each staged row comes from (-1: zero, >= 0: yperm index,
+    // <= -2: z index -2 - idx)
+    const int32_t *urows = upd_rows_old + fr.rows_off;
+    int32_t xsrc[XS];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int32_t i = ist[k] + off + 32 * VW;
-      nv[k] = i < xb ? *reinterpret_cast<const V *>(yc[k] + i) : V{};
+    for (int k = 0; k < XS; ++k) {
+      const int32_t tt = int32_t(threadIdx.x) + 256 * k;
+      const int32_t i = xa + tt;
+      xsrc[k] = -1;
+      if (tt < xb - xa && i >= c0 && i < m) xsrc[k] = i < p ? fr.first + i : -2 - urows[i - p];
     }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t jc[4], ist[4];
+    const TF *yc[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int32_t i = ist[k] + off;
-      if (i < xb) {
+      jc[k] = c0 + w + 8 * k;
+      const int32_t j = jc[k] < p ? jc[k] : c0;  // out-of-range columns read a valid one, result dropped
+      yc[k] = Y + fr.y_off + int64_t(j) * fr.ldy;
+      const int32_t ja = j & ~(VW - 1);
+      ist[k] = (ja > xa ? ja : xa) + VW * lane;
+    }
+    V cv[4];
 #pragma unroll
-        for (int q = 0; q < VW; ++q) acc[k] += TV(vget(cv[k], q)) * xs[i - xa + q];
+    for (int k = 0; k < 4; ++k) cv[k] = ist[k] < xb ? *reinterpret_cast<const V *>(yc[k] + ist[k]) : V{};
+    // the parent's solution entries must be complete
+    if (threadIdx.x == 0)
+      s_ok = fr.parent < 0 ? 1 : dep_wait(bdone + fr.parent, fronts[fr.parent].nbwd, ctl + 3, flags);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < XS; ++k) {
+      const int32_t tt = int32_t(threadIdx.x) + 256 * k;
+      if (tt < xb - xa)
+        xs[tt] = (xsrc[k] == -1 || !s_ok) ? TV(0) : (xsrc[k] >= 0 ? yperm[xsrc[k]] : __ldcg(z + (-2 - xsrc[k])));
+    }
+    __syncthreads();
+    TV acc[4] = {TV(0), TV(0), TV(0), TV(0)};
+    const int32_t ilo = ist[0] < ist[3] ? ist[0] : ist[3];
+    for (int32_t off = 0; ilo + off < xb; off += 32 * VW) {
+      V nv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int32_t i = ist[k] + off + 32 * VW;
+        nv[k] = i < xb ? *reinterpret_cast<const V *>(yc[k] + i) : V{};
       }
-      cv[k] = nv[k];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int32_t i = ist[k] + off;
+        if (i < xb && jc[k] < p) {
+#pragma unroll
+          for (int q = 0; q < VW; ++q) acc[k] += TV(vget(cv[k], q)) * xs[i - xa + q];
+        }
+        cv[k] = nv[k];
+      }
     }
-  }
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 4; ++k) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-  }
-  if (slot < 0) {
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (jc[k] < p) z[perm[fr.first + jc[k]]] = acc[k];
+      for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
     }
-    return;
-  }
-  const int32_t k_first = a0 / kBwdRows;
-  const int nch = (fr.ldy - 1) / kBwdRows - k_first + 1;
-  if (lane == 0) {
+    if (slot < 0) {
+      if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) part[int64_t(slot + ilo0 / kBwdRows - k_first) * kBwdCols + w + 8 * k] = acc[k];
-  }
-  if (!last_of_block(tickets + slot, nch)) return;
-  if (threadIdx.x < kBwdCols) {
-    TV sm = TV(0);
-    for (int ch = 0; ch < nch; ++ch) sm += __ldcg(part + int64_t(slot + ch) * kBwdCols + threadIdx.x);
-    const int32_t j = c0 + threadIdx.x;
-    if (j < p) z[perm[fr.first + j]] = sm;
+        for (int k = 0; k < 4; ++k)
+          if (jc[k] < p) z[perm[fr.first + jc[k]]] = acc[k];
+      }
+    } else {
+      const int32_t k_first = a0 / kBwdRows;
+      const int nch = (fr.ldy - 1) / kBwdRows - k_first + 1;
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          part[int64_t(slot + ilo0 / kBwdRows - k_first) * kBwdCols + w + 8 * k] = acc[k];
+      }
+      if (last_of_block(tickets + slot, nch) && threadIdx.x < kBwdCols) {
+        TV sm = TV(0);
+        for (int ch = 0; ch < nch; ++ch) sm += __ldcg(part + int64_t(slot + ch) * kBwdCols + threadIdx.x);
+        const int32_t j = c0 + threadIdx.x;
+        if (j < p) z[perm[fr.first + j]] = sm;
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(bdone + t.x, 1);
   }
 }
 
@@ -1151,17 +1240,24 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
                               const double *done = nullptr) {
   const TF *Y = reinterpret_cast<const TF *>(d->Y[buf]);
   const double *Dinv = d->D[buf] + c->n_free;
-  d->launches += 2 * int64_t(d->lt.size());
-  for (size_t lv = 0; lv < d->lt.size(); ++lv) {
-    const auto &L = d->lt[lv];
-    launch_pdl(fwd_kernel<TF, TV>, unsigned(L.fwd_n), 256, 0, s, reinterpret_cast<const int4 *>(d->tasks + L.fwd_off),
-               d->fronts, Y, Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp, part_f, tick_f, done);
+  const int nf = int(c->fronts.size());
+  // persistent grids: every resident CTA (at most one per task)
+  static int per_sm[2] = {0, 0};
+  if (!per_sm[0]) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], fwd_kernel<TF, TV>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], bwd_kernel<TF, TV>, 256, 0);
   }
-  for (size_t lv = d->lt.size(); lv-- > 0;) {
-    const auto &L = d->lt[lv];
-    launch_pdl(bwd_kernel<TF, TV>, unsigned(L.bwd_n), 256, 0, s, reinterpret_cast<const int4 *>(d->tasks + L.bwd_off),
-               d->fronts, Y, d->perm, d->upd_rows_old, yp, z, part_b, tick_b, done);
-  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device);
+  const unsigned gf = unsigned(std::max<int64_t>(1, std::min<int64_t>(d->n_apply_fwd, int64_t(sms) * std::max(1, per_sm[0]))));
+  const unsigned gb = unsigned(std::max<int64_t>(1, std::min<int64_t>(d->n_apply_bwd, int64_t(sms) * std::max(1, per_sm[1]))));
+  d->launches += 2;
+  fwd_kernel<TF, TV><<<gf, 256, 0, s>>>(reinterpret_cast<const int4 *>(d->apply_fwd), d->n_apply_fwd, d->fronts, Y,
+                                        Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp, part_f, tick_f, d->df_pend,
+                                        d->df_fdone, d->df_bdone, d->df_ctl, nf, d->flags, done);
+  bwd_kernel<TF, TV><<<gb, 256, 0, s>>>(reinterpret_cast<const int4 *>(d->apply_bwd), d->n_apply_bwd, d->fronts, Y,
+                                        d->perm, d->upd_rows_old, yp, z, part_b, tick_b, d->df_pend, d->df_fdone,
+                                        d->df_bdone, d->df_ctl, nf, d->flags, done);
 }
 
 template <typename TF, typename TV>

@@ -616,6 +616,19 @@ int build_ordering(fe_ctx *c) {
     }
   }
   c->factor_flops = flops;
+  c->apply_fwd.clear();
+  c->apply_bwd.clear();
+  c->front_nfwd.assign(nf, 0);
+  c->front_nbwd.assign(nf, 0);
+  for (const auto &L : c->levels) {
+    c->apply_fwd.insert(c->apply_fwd.end(), L.fwd_tasks.begin(), L.fwd_tasks.end());
+    for (size_t k = 0; k < L.fwd_tasks.size(); k += 4) c->front_nfwd[L.fwd_tasks[k]]++;
+  }
+  for (size_t lv = c->levels.size(); lv-- > 0;) {
+    const auto &L = c->levels[lv];
+    c->apply_bwd.insert(c->apply_bwd.end(), L.bwd_tasks.begin(), L.bwd_tasks.end());
+    for (size_t k = 0; k < L.bwd_tasks.size(); k += 4) c->front_nbwd[L.bwd_tasks[k]]++;
+  }
   return FE_OK;
 }
 
