@@ -284,6 +284,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--factor-tf32", action="store_true",
+                    help="mixed precision: plain TF32 products in the factor's trailing updates")
     ap.add_argument("--graph", action="store_true",
                     help="run the PCG iterations as replayed CUDA graphs (fe_options.use_graph)")
     ap.add_argument("--nd-leaf", type=int, default=0,
@@ -320,7 +322,8 @@ def main():
     stream = torch.cuda.Stream(priority=-1)  # above the library's background factor stream
     dev = torch.device("cuda", local)
     ctx = fe.FEContext.from_workload(wl, device_ptrs=1, stream=stream.cuda_stream, profile_stages=1,
-                                     nd_leaf_nodes=args.nd_leaf, use_graph=1 if args.graph else 0)
+                                     nd_leaf_nodes=args.nd_leaf, use_graph=1 if args.graph else 0,
+                                     factor_tf32=1 if args.factor_tf32 else 0)
     info = ctx.info()
     n = ctx.n
     loads = torch.tensor(np.stack([wl.p(t).reshape(-1) for t in range(W + K)]), dtype=torch.float64,
@@ -363,7 +366,8 @@ def main():
     e2e = None
     if args.e2e_steps > 0:
         ctx2 = fe.FEContext.from_workload(wl, device_ptrs=0, nd_leaf_nodes=args.nd_leaf,
-                                          use_graph=1 if args.graph else 0)
+                                          use_graph=1 if args.graph else 0,
+                                          factor_tf32=1 if args.factor_tf32 else 0)
         qh = np.empty(n)
         vh = np.empty(n)
         its2 = []
@@ -432,7 +436,7 @@ def main():
                    "refactor_every": wl.refactor_every, "tol": wl.tol,
                    "l2": "inputs larger than L2 (apply operators %.2f GB)" % (info["y_nnz"] * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single", "nd_leaf_nodes": args.nd_leaf or 64,
-                   "pcg_graph": bool(args.graph),
+                   "pcg_graph": bool(args.graph), "factor_tf32": bool(args.factor_tf32),
                    "mean_pcg_iters": float(np.mean(iters)), "max_displacement_m": disp},
         "roofline": roofline,
         "roofline_apply": roofline_apply,

@@ -114,6 +114,10 @@ typedef struct {
                              Not combinable with keep_checkpoints.            */
   double newton_tol;      /* stop the iterations once ||d|| <= newton_tol ||a||
                              (0: run all newton_iters)                        */
+  int32_t factor_tf32;    /* FE_MIXED: 0 = the factor's trailing updates keep
+                             FP32 accuracy (3xTF32 split on the tensor
+                             cores), 1 = plain TF32 products (faster; a
+                             coarser preconditioner, same final tolerance)   */
 } fe_options;
 
 typedef struct {

@@ -25,6 +25,7 @@ int fe_options_default(fe_options *o) {
   o->use_graph = 0;
   o->newton_iters = 1;
   o->newton_tol = 0.0;
+  o->factor_tf32 = 0;
   return FE_OK;
 }
 

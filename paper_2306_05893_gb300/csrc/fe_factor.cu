@@ -582,7 +582,9 @@ constexpr int kKc = 32;                              // K chunk
 constexpr int kOpBytes = kT128 * kKc * 4;            // one operand of one chunk: 16 KB
 constexpr int kUmmaLbo = 2048;                       // K-direction core-matrix stride
 constexpr int kUmmaSbo = 128;                        // M/N-direction (8-row group) stride
-constexpr size_t kUpdateSmem = size_t(4) * kOpBytes + 128;  // operands + mbarrier/TMEM slot
+// operands (hi and lo parts of A and B, or the TF32 parts alone) + mbarrier/TMEM slot
+template <int NMMA>
+constexpr size_t update_smem() { return size_t(NMMA == 3 ? 4 : 2) * kOpBytes + 128; }
 constexpr uint64_t kWaitLimitNs = 1000000000ull;     // give up an mbarrier wait after 1 s
 
 // tcgen05 instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B
@@ -629,17 +631,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+// NMMA = 3: the 3xTF32 split (FP32-accurate products); NMMA = 1: one TF32
+// MMA per product (operands rounded to TF32, ~1e-3 relative; the factor is
+// only a preconditioner and the solve is refined in FP64).
+template <int NMMA>
 __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *__restrict__ tasks,
                                                                  const DFront *__restrict__ fronts,
                                                                  float *__restrict__ F, float *__restrict__ Y,
                                                                  const double *__restrict__ D, int *flags) {
+  static_assert(NMMA == 1 || NMMA == 3, "3xTF32 or TF32");
+  constexpr int NB = NMMA == 3 ? 4 : 2;
   extern __shared__ __align__(1024) unsigned char usm[];
   float *sAh = reinterpret_cast<float *>(usm);
-  float *sAl = reinterpret_cast<float *>(usm + kOpBytes);
-  float *sBh = reinterpret_cast<float *>(usm + 2 * kOpBytes);
+  float *sBh = reinterpret_cast<float *>(usm + kOpBytes);
+  float *sAl = reinterpret_cast<float *>(usm + 2 * kOpBytes);  // NMMA = 3 only
   float *sBl = reinterpret_cast<float *>(usm + 3 * kOpBytes);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(usm + 4 * kOpBytes);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(usm + 4 * kOpBytes + 8);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(usm + NB * kOpBytes);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(usm + NB * kOpBytes + 8);
   __shared__ float Ds[kSuper];
   pdl_launch_dependents();
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
@@ -702,9 +710,11 @@ __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *
       const float bv = xb[u] * dl;
       const uint32_t ah = to_tf32(xa[u]), bh = to_tf32(bv);
       sAh[off] = __uint_as_float(ah);
-      sAl[off] = __uint_as_float(to_tf32(xa[u] - __uint_as_float(ah)));
       sBh[off] = __uint_as_float(bh);
-      sBl[off] = __uint_as_float(to_tf32(bv - __uint_as_float(bh)));
+      if constexpr (NMMA == 3) {
+        sAl[off] = __uint_as_float(to_tf32(xa[u] - __uint_as_float(ah)));
+        sBl[off] = __uint_as_float(to_tf32(bv - __uint_as_float(bh)));
+      }
     }
   };
   auto issue_chunk = [&](int q) {
@@ -716,17 +726,27 @@ __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *
       const uint64_t dah = umma_desc(ah + ko), dal = umma_desc(al + ko);
       const uint64_t dbh = umma_desc(bh + ko), dbl = umma_desc(bl + ko);
       const uint32_t acc0 = (q > 0 || s > 0) ? 1u : 0u;
-      asm volatile(
-          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-          " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-          "l"(dal), "l"(dbh), "r"(kIdescTf32), "r"(acc0)
-          : "memory");
-      asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah), "l"(dbl),
-                   "r"(kIdescTf32)
-                   : "memory");
-      asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah), "l"(dbh),
-                   "r"(kIdescTf32)
-                   : "memory");
+      if constexpr (NMMA == 3) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dal), "l"(dbh), "r"(kIdescTf32), "r"(acc0)
+            : "memory");
+        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah),
+                     "l"(dbl), "r"(kIdescTf32)
+                     : "memory");
+        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah),
+                     "l"(dbh), "r"(kIdescTf32)
+                     : "memory");
+      } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(dah), "l"(dbh), "r"(kIdescTf32), "r"(acc0)
+            : "memory");
+        (void)dal;
+        (void)dbl;
+      }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_a)
                  : "memory");
@@ -1186,7 +1206,8 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
   cudaFuncSetAttribute(front_diag_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dsm));
   cudaFuncSetAttribute(front_panel_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
   cudaFuncSetAttribute(front_update_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
-  cudaFuncSetAttribute(front_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kUpdateSmem));
+  cudaFuncSetAttribute(front_update_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(update_smem<3>()));
+  cudaFuncSetAttribute(front_update_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(update_smem<1>()));
   const size_t asm_smem = size_t(kAsmSeg) * sizeof(TF);
   cudaFuncSetAttribute(front_assemble_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(asm_smem));
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
@@ -1207,8 +1228,12 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
         const int ev = stage_begin(c, FE_STAGE_FACTOR_UPDATE, s);
         if (ev >= 0) d->update_flops += L.trail_flops[st];
         if constexpr (sizeof(TF) == 4)
-          launch_pdl(front_update_tc_kernel, unsigned(L.trail_n[st]), 256, kUpdateSmem, s,
-                     d->tasks + L.trail_off[st], d->fronts, F, Y, d->D[buf], d->flags);
+          if (c->opt.factor_tf32)
+            launch_pdl(front_update_tc_kernel<1>, unsigned(L.trail_n[st]), 256, update_smem<1>(), s,
+                       d->tasks + L.trail_off[st], d->fronts, F, Y, d->D[buf], d->flags);
+          else
+            launch_pdl(front_update_tc_kernel<3>, unsigned(L.trail_n[st]), 256, update_smem<3>(), s,
+                       d->tasks + L.trail_off[st], d->fronts, F, Y, d->D[buf], d->flags);
         else
           launch_pdl(front_update_kernel<TF>, unsigned(L.trail_n[st]), 256, tsm, s, d->tasks + L.trail_off[st],
                      d->fronts, F, Y, d->D[buf]);
