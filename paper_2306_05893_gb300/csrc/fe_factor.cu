@@ -68,73 +68,84 @@ __device__ __forceinline__ float vget(const float4 &v, int q) {
 __device__ __forceinline__ double vget(const double2 &v, int q) { return q == 0 ? v.x : v.y; }
 
 // -------------------------------------------------------------- assembly
-// Task (front, c0, c1): columns [c0, c1) of F (lower part) are built one at a
-// time in shared memory, in row segments of kAsmSeg: zeros, the column's A
-// entries, then every child's matching update-block column added in fixed
-// child order (deterministic), and written out once, coalesced; no global
-// read-modify-write and no separate zeroing pass.  The pivot columns of Y
-// are zeroed with 16-byte stores (ldy and y_off are multiples of 4).
-constexpr int kAsmSeg = 8192;  // rows per shared-memory segment
-
+// Task (front, c0, c1): zero the lower part of columns [c0, c1) of F and of
+// the pivot columns of Y, scatter the A entries of those columns, then add
+// every child's update block (children in fixed order: deterministic).
 template <typename TF>
 __global__ void __launch_bounds__(256) front_assemble_kernel(
     const int32_t *__restrict__ tasks, const DFront *__restrict__ fronts,
     const int32_t *__restrict__ child_list, const int32_t *__restrict__ rmap,
     const int64_t *__restrict__ fa_colptr, const int32_t *__restrict__ fa_slot,
     const int32_t *__restrict__ fa_off, const TF *__restrict__ A, TF *__restrict__ F, TF *__restrict__ Y) {
-  extern __shared__ __align__(16) unsigned char asm_raw[];
-  TF *colbuf = reinterpret_cast<TF *>(asm_raw);  // [kAsmSeg]
   pdl_launch_dependents();
   const int32_t f = tasks[3 * blockIdx.x], c0 = tasks[3 * blockIdx.x + 1], c1 = tasks[3 * blockIdx.x + 2];
   const DFront fr = fronts[f];
   const int32_t m = fr.m, p = fr.npiv;
   TF *Ff = F + fr.f_off;
   pdl_wait();
-  // Y pivot columns of the task: zero, 16 bytes at a time
-  {
-    const int32_t ce = c1 < p ? c1 : p;
-    using V = typename Vec16<TF>::type;
-    constexpr int VW = Vec16<TF>::n;
-    for (int32_t col = c0; col < ce; ++col) {
-      V *yp = reinterpret_cast<V *>(Y + fr.y_off + int64_t(col) * fr.ldy);
-      for (int32_t r = threadIdx.x; r < fr.ldy / VW; r += 256) yp[r] = V{};
+  for (int32_t col = c0; col < c1; ++col) {
+    TF *cp = Ff + int64_t(col) * m;
+    for (int32_t r = col + threadIdx.x; r < m; r += blockDim.x) cp[r] = TF(0);
+    if (col < p) {
+      TF *yp = Y + fr.y_off + int64_t(col) * fr.ldy;
+      for (int32_t r = threadIdx.x; r < fr.ldy; r += blockDim.x) yp[r] = TF(0);
     }
   }
-  for (int32_t col = c0; col < c1; ++col) {
-    for (int32_t s0 = col; s0 < m; s0 += kAsmSeg) {
-      const int32_t s1 = (s0 + kAsmSeg < m) ? s0 + kAsmSeg : m;
-      for (int32_t r = s0 + threadIdx.x; r < s1; r += 256) colbuf[r - s0] = TF(0);
-      __syncthreads();
-      if (col < p) {  // A entries of a pivot column (distinct rows)
-        const int64_t e0 = fa_colptr[fr.fac_off + col], e1 = fa_colptr[fr.fac_off + col + 1];
-        const int64_t base = int64_t(col) * m;
-        for (int64_t e = e0 + threadIdx.x; e < e1; e += 256) {
-          const int32_t r = int32_t(fa_off[e] - base);
-          if (r >= s0 && r < s1) colbuf[r - s0] = A[fa_slot[e]];
-        }
-        __syncthreads();
+  __syncthreads();
+  const int32_t ce = c1 < p ? c1 : p;
+  if (ce > c0) {  // the entries of columns [c0, ce) are contiguous in the fa lists
+    const int64_t e0 = fa_colptr[fr.fac_off + c0], e1 = fa_colptr[fr.fac_off + ce];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += 4 * 256) {
+      int32_t off[4];
+      TF v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t ee = e + 256 * k;
+        off[k] = ee < e1 ? fa_off[ee] : -1;
+        v[k] = ee < e1 ? A[fa_slot[ee]] : TF(0);
       }
-      for (int32_t ci = fr.child_begin; ci < fr.child_end; ++ci) {
-        const DFront ch = fronts[child_list[ci]];
-        const int32_t *rm = rmap + ch.rows_off;
-        const int32_t nu = ch.nupd, pc = ch.npiv, mc = ch.m;
-        // the child's update column mapped onto col (rm is increasing)
-        int32_t lo = 0, hi = nu;
-        while (lo < hi) { const int32_t mid = (lo + hi) >> 1; if (rm[mid] < col) lo = mid + 1; else hi = mid; }
-        if (lo >= nu || rm[lo] != col) continue;
-        const int32_t j = lo;
-        // its rows landing in [s0, s1): a contiguous range i in [ia, ib)
-        int32_t ia = j, ib = nu;
-        { int32_t l2 = j, h2 = nu; while (l2 < h2) { const int32_t mid = (l2 + h2) >> 1; if (rm[mid] < s0) l2 = mid + 1; else h2 = mid; } ia = l2; }
-        { int32_t l2 = ia, h2 = nu; while (l2 < h2) { const int32_t mid = (l2 + h2) >> 1; if (rm[mid] < s1) l2 = mid + 1; else h2 = mid; } ib = l2; }
-        const TF *src = F + ch.f_off + int64_t(pc + j) * mc + pc;
-        for (int32_t i = ia + threadIdx.x; i < ib; i += 256) colbuf[rm[i] - s0] += src[i];
-        __syncthreads();
-      }
-      TF *dst = Ff + int64_t(col) * m;
-      for (int32_t r = s0 + threadIdx.x; r < s1; r += 256) dst[r] = colbuf[r - s0];
-      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (off[k] >= 0) Ff[off[k]] = v[k];
     }
+  }
+  __syncthreads();
+  for (int32_t ci = fr.child_begin; ci < fr.child_end; ++ci) {
+    const DFront ch = fronts[child_list[ci]];
+    const int32_t *rm = rmap + ch.rows_off;
+    const int32_t nu = ch.nupd, pc = ch.npiv, mc = ch.m;
+    // child columns mapping into [c0, c1): contiguous since rm is increasing
+    int32_t lo = 0, hi = nu;
+    while (lo < hi) { int32_t mid = (lo + hi) >> 1; if (rm[mid] < c0) lo = mid + 1; else hi = mid; }
+    const int32_t jlo = lo;
+    hi = nu;
+    while (lo < hi) { int32_t mid = (lo + hi) >> 1; if (rm[mid] < c1) lo = mid + 1; else hi = mid; }
+    const int32_t jhi = lo;
+    const TF *Fc = F + ch.f_off;
+    for (int32_t j = jlo; j < jhi; ++j) {
+      const TF *src = Fc + int64_t(pc + j) * mc + pc;
+      TF *dst = Ff + int64_t(rm[j]) * m;
+      // 8 rows per thread in flight: all loads of a batch before its stores
+      // (a store ahead of the next load would expose one latency per row);
+      // the child's rows map to distinct parent rows, so a batch never
+      // reads what it writes
+      for (int32_t i = j + threadIdx.x; i < nu; i += 8 * 256) {
+        int32_t ri[8];
+        TF sv[8], dv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int32_t ii = i + 256 * k;
+          ri[k] = ii < nu ? rm[ii] : -1;
+          sv[k] = ii < nu ? src[ii] : TF(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dv[k] = ri[k] >= 0 ? dst[ri[k]] : TF(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (ri[k] >= 0) dst[ri[k]] = dv[k] + sv[k];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -1208,13 +1219,11 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
   cudaFuncSetAttribute(front_update_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
   cudaFuncSetAttribute(front_update_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(update_smem<3>()));
   cudaFuncSetAttribute(front_update_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(update_smem<1>()));
-  const size_t asm_smem = size_t(kAsmSeg) * sizeof(TF);
-  cudaFuncSetAttribute(front_assemble_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(asm_smem));
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
     if (L.asm_n) d->launches++;
     if (L.asm_n)
-      launch_pdl(front_assemble_kernel<TF>, unsigned(L.asm_n), 256, asm_smem, s, d->tasks + L.asm_off, d->fronts,
+      launch_pdl(front_assemble_kernel<TF>, unsigned(L.asm_n), 256, 0, s, d->tasks + L.asm_off, d->fronts,
                  d->child_list, d->rmap, d->fa_colptr, d->fa_slot, d->fa_off, Afac, F, Y);
     for (size_t st = 0; st < L.diag_n.size(); ++st) {
       d->launches += (L.diag_n[st] > 0) + (L.panel_n[st] > 0) + (L.trail_n[st] > 0);
