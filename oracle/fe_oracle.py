@@ -33,7 +33,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-SVK, NEOHOOKE, MOONEY_RIVLIN = 0, 1, 2
+SVK, NEOHOOKE, MOONEY_RIVLIN, COROTATIONAL = 0, 1, 2, 3
 TET4, HEX8 = 0, 1
 
 _I3 = np.eye(3)
@@ -190,6 +190,7 @@ class Quadrature:
         self.elem_type = elem_type
         self.conn = np.asarray(conn)
         Xe = np.asarray(X)[self.conn]                       # [E, npe, 3]
+        self.Xe = Xe
         if elem_type == TET4:
             Dm = np.swapaxes(Xe[:, 1:] - Xe[:, [0]], 1, 2)  # columns X_a - X_0
             Gm = np.linalg.inv(Dm)                           # row a-1 = grad N_a
@@ -226,6 +227,84 @@ def _params(params, E):
     return p[:, 0][:, None], p[:, 1][:, None], p[:, 2][:, None]   # [E, 1] each
 
 
+# ============================================ co-rotational linear elements
+# Section 3.1, Eq. "eqmodel": the rest stiffness K0_e = int B^T D B dV (B the
+# strain-displacement matrix, D the isotropic stress-strain matrix from
+# (mu, lambda)), rotated per element: with R_e the rotation of the polar
+# decomposition of the element's deformation gradient (for a hex, of its
+# volume average over the Gauss points),
+#   f_e = Rb K0_e (Rb^T x_e - X_e),   K_e = Rb K0_e Rb^T,   Rb = diag(R_e, ..).
+# The tangent leaves out the derivative of R_e (the usual co-rotational
+# stiffness), so there is no element energy.
+
+def voigt_B(gradN):
+    """[..., npe, 3] -> [..., 6, 3 npe]; strain order xx, yy, zz, xy, yz, zx
+    with engineering shears."""
+    npe = gradN.shape[-2]
+    B = np.zeros(gradN.shape[:-2] + (6, 3 * npe))
+    for a in range(npe):
+        gx, gy, gz = gradN[..., a, 0], gradN[..., a, 1], gradN[..., a, 2]
+        c = 3 * a
+        B[..., 0, c] = gx
+        B[..., 1, c + 1] = gy
+        B[..., 2, c + 2] = gz
+        B[..., 3, c], B[..., 3, c + 1] = gy, gx
+        B[..., 4, c + 1], B[..., 4, c + 2] = gz, gy
+        B[..., 5, c], B[..., 5, c + 2] = gz, gx
+    return B
+
+
+def voigt_D(mu, lam):
+    """[E, 1] parameters -> [E, 6, 6] isotropic stress-strain matrix."""
+    mu, lam = np.asarray(mu).reshape(-1), np.asarray(lam).reshape(-1)
+    D = np.zeros((mu.shape[0], 6, 6), dtype=np.result_type(mu, lam))
+    D[:, :3, :3] = lam[:, None, None]
+    for k in range(3):
+        D[:, k, k] += 2.0 * mu
+        D[:, 3 + k, 3 + k] = mu
+    return D
+
+
+def corot_rotation(quad, x):
+    """R_e [E, 3, 3] = the rotation of the polar decomposition F = R S of the
+    element's (volume-averaged) deformation gradient, by SVD."""
+    F = quad.deformation_gradient(x)
+    Fb = np.einsum("eq,eqiJ->eiJ", quad.w, F) / quad.w.sum(axis=1)[:, None, None]
+    U, _, Vt = np.linalg.svd(Fb)
+    d = np.sign(np.linalg.det(U @ Vt))
+    U = U.copy()
+    U[:, :, 2] *= d[:, None]  # a proper rotation (det = +1)
+    return U @ Vt
+
+
+def corot_K0(quad, params):
+    mu, lam, _ = _params(params, quad.conn.shape[0])
+    B = voigt_B(quad.gradN)                                   # [E, Q, 6, 3npe]
+    D = voigt_D(mu, lam)
+    return np.einsum("eq,eqsm,est,eqtn->emn", quad.w, B, D, B, optimize=True)
+
+
+def _block_rotation(R, npe):
+    E = R.shape[0]
+    Rb = np.zeros((E, 3 * npe, 3 * npe), dtype=R.dtype)
+    for a in range(npe):
+        Rb[:, 3 * a:3 * a + 3, 3 * a:3 * a + 3] = R
+    return Rb
+
+
+def corot_force(quad, x, params):
+    R = corot_rotation(quad, x)
+    Rb = _block_rotation(R, quad.npe)
+    xe = np.asarray(x)[quad.conn].reshape(R.shape[0], -1)
+    u_loc = np.einsum("emn,em->en", Rb, xe) - quad.Xe.reshape(R.shape[0], -1)   # Rb^T x - X
+    return np.einsum("emn,enk,ek->em", Rb, corot_K0(quad, params), u_loc)
+
+
+def corot_tangent(quad, x, params):
+    Rb = _block_rotation(corot_rotation(quad, x), quad.npe)
+    return np.einsum("emn,enk,elk->eml", Rb, corot_K0(quad, params), Rb)
+
+
 def element_energy(quad, x, model, params):
     """W_e = sum_q w_q psi(F_q)  -> [E]."""
     psi = LAWS[model][0]
@@ -236,6 +315,8 @@ def element_energy(quad, x, model, params):
 
 def element_force(quad, x, model, params):
     """f_e[3a+i] = sum_q w_q sum_J P_iJ gradN_aJ  (internal force dW_e/dx)."""
+    if model == COROTATIONAL:
+        return corot_force(quad, x, params)
     P = LAWS[model][1](quad.deformation_gradient(x), *_params(params, quad.conn.shape[0]))
     f = np.einsum("eq,eqiJ,eqaJ->eai", quad.w, P, quad.gradN)
     return f.reshape(f.shape[0], -1)
@@ -243,6 +324,8 @@ def element_force(quad, x, model, params):
 
 def element_tangent(quad, x, model, params):
     """K_e[3a+i, 3b+k] = sum_q w_q sum_JL CC_iJkL gradN_aJ gradN_bL."""
+    if model == COROTATIONAL:
+        return corot_tangent(quad, x, params)
     CC = LAWS[model][2](quad.deformation_gradient(x), *_params(params, quad.conn.shape[0]))
     K = np.einsum("eq,eqiJkL,eqaJ,eqbL->eaibk", quad.w, CC, quad.gradN, quad.gradN,
                   optimize=True)
