@@ -23,5 +23,5 @@ Conventions (all fixed here once, used by both sides):
 from .beams import (  # noqa: F401
     TetBeam, HexBeam, tet_beam, hex_beam, body_force, end_traction,
     end_face_tris, end_face_quads, lame_from_young, WORKLOADS, workload,
-    batched_beams, batch_workload, BatchMember, lognormal_modulus, SVK, NEOHOOKE, MOONEY_RIVLIN, TET4, HEX8,
+    batched_beams, batch_workload, BatchMember, lognormal_modulus, SVK, NEOHOOKE, MOONEY_RIVLIN, COROTATIONAL, TET4, HEX8,
 )

@@ -14,7 +14,7 @@ BETA = 0.01     # Rayleigh stiffness coefficient
 RHO = 1000.0    # kg/m^3
 G_Z = -9.81     # m/s^2
 
-SVK, NEOHOOKE, MOONEY_RIVLIN = 0, 1, 2
+SVK, NEOHOOKE, MOONEY_RIVLIN, COROTATIONAL = 0, 1, 2, 3
 TET4, HEX8 = 0, 1
 
 

@@ -53,7 +53,7 @@ typedef enum {
 } fe_status;
 
 enum { FE_TET4 = 0, FE_HEX8 = 1 };
-enum { FE_SVK = 0, FE_NEOHOOKE = 1, FE_MOONEY_RIVLIN = 2 };
+enum { FE_SVK = 0, FE_NEOHOOKE = 1, FE_MOONEY_RIVLIN = 2, FE_COROTATIONAL = 3 };
 enum { FE_FP64 = 0, FE_MIXED = 1 };
 
 /* Mesh (Section 3.1).  Local node order of a hex: a = dx + 2 dy + 4 dz.
@@ -71,9 +71,13 @@ typedef struct {
 } fe_mesh;
 
 /* Material (Section 3.1): params are (mu, lambda, unused) for St Venant-
- * Kirchhoff and neo-Hookean, (C10, C01, kappa) for Mooney-Rivlin; one triple
- * for the whole mesh, or one per element when per_element = 1
- * ([n_elems * 3], element-major).  rho is the mass density. */
+ * Kirchhoff, neo-Hookean and co-rotational linear elasticity, (C10, C01,
+ * kappa) for Mooney-Rivlin; one triple for the whole mesh, or one per element
+ * when per_element = 1 ([n_elems * 3], element-major).  rho is the mass
+ * density.  Co-rotational elements (Eq. "eqmodel": int B^T D B rotated by the
+ * polar decomposition of the element's mean deformation gradient) have no
+ * energy and a tangent without the rotation's derivative, so fe_adjoint
+ * refuses them (and keep_checkpoints with them). */
 typedef struct {
   int32_t model;
   double rho;

@@ -16,7 +16,7 @@ import os
 import numpy as np
 
 from . import _abi
-from ._abi import (FE_FP64, FE_HEX8, FE_MIXED, FE_MOONEY_RIVLIN, FE_NEOHOOKE,  # noqa: F401
+from ._abi import (FE_COROTATIONAL, FE_FP64, FE_HEX8, FE_MIXED, FE_MOONEY_RIVLIN, FE_NEOHOOKE,  # noqa: F401
                    FE_SVK, FE_TET4, FeOptions, FeStepInfo)
 
 _LIB = None

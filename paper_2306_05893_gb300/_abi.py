@@ -6,7 +6,7 @@ STATUS = {0: "FE_OK", 1: "FE_ERR_ARG", 2: "FE_ERR_CUDA", 3: "FE_ERR_OOM",
           4: "FE_ERR_PATTERN_CHANGED", 5: "FE_ERR_NOT_CONVERGED", 6: "FE_ERR_BREAKDOWN",
           7: "FE_ERR_INVERTED", 8: "FE_ERR_TIMEOUT", 9: "FE_ERR_STATE"}
 FE_TET4, FE_HEX8 = 0, 1
-FE_SVK, FE_NEOHOOKE, FE_MOONEY_RIVLIN = 0, 1, 2
+FE_SVK, FE_NEOHOOKE, FE_MOONEY_RIVLIN, FE_COROTATIONAL = 0, 1, 2, 3
 FE_FP64, FE_MIXED = 0, 1
 
 

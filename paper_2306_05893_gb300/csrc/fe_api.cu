@@ -956,6 +956,8 @@ int fe_num_checkpoints(fe_ctx *c, int64_t *count) {
 
 int fe_adjoint(fe_ctx *c, const double *dL_dqT, const double *dL_dvT, double *dL_ds, double *dL_dp) {
   if (!c || !dL_dqT) return FE_ERR_ARG;
+  if (c->model_range[FE_COROTATIONAL][1] > c->model_range[FE_COROTATIONAL][0])
+    return set_error(c, FE_ERR_ARG, "co-rotational elements have no adjoint (no energy, no exact tangent)");
   FE_TRY(ensure_device(c));
   DeviceState *d = c->dev;
   const int64_t T = int64_t(d->ckpt.size());

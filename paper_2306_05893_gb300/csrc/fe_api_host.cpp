@@ -36,7 +36,7 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
   if (!mesh || !mat || !mesh->rest_xyz || !mesh->conn || mesh->n_nodes <= 0 || mesh->n_elems <= 0)
     return FE_ERR_ARG;
   if (mesh->elem_type != FE_TET4 && mesh->elem_type != FE_HEX8) return FE_ERR_ARG;
-  if (mat->model < FE_SVK || mat->model > FE_MOONEY_RIVLIN || !mat->params) return FE_ERR_ARG;
+  if (mat->model < FE_SVK || mat->model > FE_COROTATIONAL || !mat->params) return FE_ERR_ARG;
   if (!(h > 0) || !(mat->rho > 0) || mesh->n_fixed < 0 || (mesh->n_fixed > 0 && !mesh->fixed_nodes))
     return FE_ERR_ARG;
   if (mesh->n_nodes > (int64_t(1) << 29)) return FE_ERR_ARG;
@@ -74,12 +74,16 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
       delete c;
       return FE_ERR_ARG;  // the adjoint differentiates the single-linearisation step
     }
+    if (c->model == FE_COROTATIONAL && c->opt.keep_checkpoints) {
+      delete c;
+      return FE_ERR_ARG;  // no energy, no exact tangent: no adjoint
+    }
     c->nseg = 1;
     c->seg_node = {0, c->n_nodes};
     c->seg_elem = {0, c->n_elems};
     c->seg_member = {0};
     c->seg_model = {c->model};
-    for (int k = 0; k < 3; ++k) c->model_range[k][0] = c->model_range[k][1] = 0;
+    for (int k = 0; k < 4; ++k) c->model_range[k][0] = c->model_range[k][1] = 0;
     c->model_range[c->model][1] = c->n_elems;
   } catch (const std::bad_alloc &) {
     delete c;
@@ -97,13 +101,13 @@ int fe_create_batch(int32_t nb, const fe_mesh *meshes, const fe_material *mats, 
   for (int32_t k = 0; k < nb; ++k) {
     const fe_mesh &m = meshes[k];
     if (!m.rest_xyz || !m.conn || m.n_nodes <= 0 || m.n_elems <= 0 || m.elem_type != meshes[0].elem_type ||
-        (m.n_fixed > 0 && !m.fixed_nodes) || mats[k].model < FE_SVK || mats[k].model > FE_MOONEY_RIVLIN ||
+        (m.n_fixed > 0 && !m.fixed_nodes) || mats[k].model < FE_SVK || mats[k].model > FE_COROTATIONAL ||
         !mats[k].params || !(mats[k].rho > 0) || mats[k].rho != mats[0].rho)
       return FE_ERR_ARG;
   }
   // members grouped by material model (stable), so each model is one element range
   std::vector<int32_t> order;
-  for (int md = FE_SVK; md <= FE_MOONEY_RIVLIN; ++md)
+  for (int md = FE_SVK; md <= FE_COROTATIONAL; ++md)
     for (int32_t k = 0; k < nb; ++k)
       if (mats[k].model == md) order.push_back(k);
   const int npe = meshes[0].elem_type == FE_TET4 ? 4 : 8;
@@ -150,7 +154,7 @@ int fe_create_batch(int32_t nb, const fe_mesh *meshes, const fe_material *mats, 
     c->seg_elem = seg_elem;
     c->seg_member = order;
     c->seg_model = seg_model;
-    for (int md = 0; md < 3; ++md) c->model_range[md][0] = c->model_range[md][1] = 0;
+    for (int md = 0; md < 4; ++md) c->model_range[md][0] = c->model_range[md][1] = 0;
     for (int32_t s = 0; s < nb; ++s) {
       const int md = seg_model[s];
       if (c->model_range[md][1] == 0) c->model_range[md][0] = seg_elem[s];

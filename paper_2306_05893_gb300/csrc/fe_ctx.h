@@ -75,7 +75,7 @@ struct fe_ctx {
   int32_t nseg = 1;
   std::vector<int64_t> seg_node, seg_elem;
   std::vector<int32_t> seg_member, seg_model;
-  int64_t model_range[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  int64_t model_range[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
 
   // ---------------------------------------------------------- setup products
   bool built = false;

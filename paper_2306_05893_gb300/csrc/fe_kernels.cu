@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, int64_t e_begin, 
     kin.init(H);
     if (!(kin.J > T(0))) atomicOr(flags, FLAG_INVERTED);
     Law<MODEL, T> law;
+    if constexpr (MODEL == FE_COROTATIONAL) law.set_frame(H);
     T P[3][3];
     law.init(kin, H, p0, p1, p2, P);
 #pragma unroll
@@ -178,6 +179,35 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, 
     }
     const T p0 = ld_cast<T>(params + e), p1 = ld_cast<T>(params + E + e),
             p2 = ld_cast<T>(params + 2 * E + e);
+    Law<MODEL, T> law;
+    if constexpr (MODEL == FE_COROTATIONAL) {
+      // the element frame from the volume-averaged displacement gradient
+      T Hb[3][3], vol = T(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) Hb[i][J] = T(0);
+#pragma unroll 1
+      for (int gp = 0; gp < 8; ++gp) {
+        const T w = ld_cast<T>(rest + (gp * 25 + 24) * E + e);
+        vol += w;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          T gb[3];
+#pragma unroll
+          for (int J = 0; J < 3; ++J) gb[J] = w * ld_cast<T>(rest + (gp * 25 + 3 * b + J) * E + e);
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int J = 0; J < 3; ++J) Hb[i][J] += u[b][i] * gb[J];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) Hb[i][J] /= vol;
+      law.set_frame(Hb);
+    }
     T acc[8][9];
 #pragma unroll
     for (int b = 0; b < 8; ++b)
@@ -205,7 +235,6 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, 
       Kin<T> kin;
       kin.init(H);
       if (!(kin.J > T(0)) && a == 0) atomicOr(flags, FLAG_INVERTED);
-      Law<MODEL, T> law;
       T P[3][3];
       law.init(kin, H, p0, p1, p2, P);
 #pragma unroll
@@ -263,16 +292,19 @@ static void launch_element_t(const fe_ctx *c, const DeviceState *d, const double
 
 void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool fp32, cudaStream_t s) {
   // one launch per material model present (a batch groups its members by model)
-  for (int md = FE_SVK; md <= FE_MOONEY_RIVLIN; ++md) {
+  for (int md = FE_SVK; md <= FE_COROTATIONAL; ++md) {
     if (c->model_range[md][1] <= c->model_range[md][0]) continue;
     d->launches++;
     if (md == FE_SVK)
       fp32 ? launch_element_t<FE_SVK, float>(c, d, q, s) : launch_element_t<FE_SVK, double>(c, d, q, s);
     else if (md == FE_NEOHOOKE)
       fp32 ? launch_element_t<FE_NEOHOOKE, float>(c, d, q, s) : launch_element_t<FE_NEOHOOKE, double>(c, d, q, s);
-    else
+    else if (md == FE_MOONEY_RIVLIN)
       fp32 ? launch_element_t<FE_MOONEY_RIVLIN, float>(c, d, q, s)
            : launch_element_t<FE_MOONEY_RIVLIN, double>(c, d, q, s);
+    else
+      fp32 ? launch_element_t<FE_COROTATIONAL, float>(c, d, q, s)
+           : launch_element_t<FE_COROTATIONAL, double>(c, d, q, s);
   }
 }
 

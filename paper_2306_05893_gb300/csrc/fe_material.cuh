@@ -243,4 +243,139 @@ struct Law<FE_MOONEY_RIVLIN, T> {
   }
 };
 
+// Co-rotational linear elasticity (Section 3.1, Eq. "eqmodel": the rest
+// stiffness int B^T D B rotated per element).  R is the rotation of the polar
+// decomposition F = R S of the element's mean deformation gradient (one F for
+// a tet, the volume average over the Gauss points for a hex).  With the
+// local strain eps = sym(R^T F) - I and sigma = lambda tr(eps) I + 2 mu eps,
+// P = R sigma and CC_iJkL = lambda R_iJ R_kL + mu (d_ik d_JL + R_iL R_kJ),
+// i.e. K_e = Rb K0_e Rb^T and f_e = Rb K0_e (Rb^T x_e - X_e).  Without
+// cancellation: S - I = Z is the Biot strain of the mean Green strain E
+// ((I + Z)^2 = I + 2E, Newton iterations Z <- (I + Z)^{-1} (Z^2/2 + E) from
+// Z = E), R = F (I + Z)^{-1}, and at a Gauss point
+// eps = Z + sym(R^T (H - Hbar)).
+template <typename T>
+__device__ __forceinline__ void inv3(const T m[3][3], T r[3][3]) {
+  const T c00 = m[1][1] * m[2][2] - m[1][2] * m[2][1], c01 = m[1][2] * m[2][0] - m[1][0] * m[2][2],
+          c02 = m[1][0] * m[2][1] - m[1][1] * m[2][0];
+  const T id = T(1) / (m[0][0] * c00 + m[0][1] * c01 + m[0][2] * c02);
+  r[0][0] = c00 * id;
+  r[1][0] = c01 * id;
+  r[2][0] = c02 * id;
+  r[0][1] = (m[0][2] * m[2][1] - m[0][1] * m[2][2]) * id;
+  r[1][1] = (m[0][0] * m[2][2] - m[0][2] * m[2][0]) * id;
+  r[2][1] = (m[0][1] * m[2][0] - m[0][0] * m[2][1]) * id;
+  r[0][2] = (m[0][1] * m[1][2] - m[0][2] * m[1][1]) * id;
+  r[1][2] = (m[0][2] * m[1][0] - m[0][0] * m[1][2]) * id;
+  r[2][2] = (m[0][0] * m[1][1] - m[0][1] * m[1][0]) * id;
+}
+
+template <typename T>
+struct Law<FE_COROTATIONAL, T> {
+  T R[3][3], Z[3][3], Hb[3][3];
+  T mu, lam;
+  // the element's frame from its mean displacement gradient
+  __device__ void set_frame(const T H[3][3]) {
+    T E[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Hb[i][j] = H[i][j];
+        T s = H[i][j] + H[j][i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s += H[k][i] * H[k][j];
+        E[i][j] = T(0.5) * s;
+        Z[i][j] = E[i][j];
+      }
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+      T A[3][3], Ai[3][3], Bm[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          A[i][j] = Z[i][j] + (i == j ? T(1) : T(0));
+          T zz = T(0);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) zz += Z[i][k] * Z[k][j];
+          Bm[i][j] = T(0.5) * zz + E[i][j];
+        }
+      inv3(A, Ai);
+      T N[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          T s = T(0);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) s += Ai[i][k] * Bm[k][j];
+          N[i][j] = s;
+        }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Z[i][j] = T(0.5) * (N[i][j] + N[j][i]);
+    }
+    T A[3][3], Ai[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) A[i][j] = Z[i][j] + (i == j ? T(1) : T(0));
+    inv3(A, Ai);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T s = Ai[i][j];  // (I + H) (I + Z)^{-1}
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s += H[i][k] * Ai[k][j];
+        R[i][j] = s;
+      }
+  }
+  __device__ void init(const Kin<T> &, const T H[3][3], T p0, T p1, T, T P[3][3]) {
+    mu = p0;
+    lam = p1;
+    T D[3][3], ep[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) D[i][j] = H[i][j] - Hb[i][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T a = T(0), b = T(0);  // (R^T D)_ij, (R^T D)_ji
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          a += R[k][i] * D[k][j];
+          b += R[k][j] * D[k][i];
+        }
+        ep[i][j] = Z[i][j] + T(0.5) * (a + b);
+      }
+    const T tre = tr3(ep);
+    T sg[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) sg[i][j] = T(2) * mu * ep[i][j] + (i == j ? lam * tre : T(0));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s += R[i][k] * sg[k][j];
+        P[i][j] = s;
+      }
+  }
+  __device__ __forceinline__ void block(int i, int k, T C[3][3]) const {
+#pragma unroll
+    for (int J = 0; J < 3; ++J)
+#pragma unroll
+      for (int L = 0; L < 3; ++L)
+        C[J][L] = lam * R[i][J] * R[k][L] + mu * ((i == k && J == L ? T(1) : T(0)) + R[i][L] * R[k][J]);
+  }
+};
+
 }  // namespace fe

@@ -18,7 +18,7 @@ from oracle import fe_oracle as O
 pytestmark = pytest.mark.gpu
 
 LAWS = {fi.SVK: (3.4e3, 3.1e4, 0.0), fi.NEOHOOKE: (3.4e3, 3.1e4, 0.0),
-        fi.MOONEY_RIVLIN: (1.5e3, 5e2, 5e4)}
+        fi.MOONEY_RIVLIN: (1.5e3, 5e2, 5e4), fi.COROTATIONAL: (3.4e3, 3.1e4, 0.0)}
 
 
 def _mesh(kind):
@@ -42,7 +42,7 @@ def _ctx(fe, mesh, law, precision, **kw):
 
 
 @pytest.mark.parametrize("kind", ["tet", "hex"])
-@pytest.mark.parametrize("law", [fi.SVK, fi.NEOHOOKE, fi.MOONEY_RIVLIN])
+@pytest.mark.parametrize("law", [fi.SVK, fi.NEOHOOKE, fi.MOONEY_RIVLIN, fi.COROTATIONAL])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_element_kernel(gpu_lib, kind, law, precision):
     mesh = _mesh(kind)
@@ -58,7 +58,8 @@ def test_element_kernel(gpu_lib, kind, law, precision):
     ctx.close()
 
 
-@pytest.mark.parametrize("kind,law", [("tet", fi.SVK), ("tet", fi.MOONEY_RIVLIN), ("hex", fi.NEOHOOKE)])
+@pytest.mark.parametrize("kind,law", [("tet", fi.SVK), ("tet", fi.MOONEY_RIVLIN), ("hex", fi.NEOHOOKE),
+                                      ("tet", fi.COROTATIONAL), ("hex", fi.COROTATIONAL)])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_assembly(gpu_lib, kind, law, precision):
     mesh = _mesh(kind)
@@ -139,6 +140,37 @@ def test_mixed_factor_with_superpanels(gpu_lib, kind, tf32, res_tol, sol_tol):
     assert np.linalg.norm(z - zo) <= sol_tol * np.linalg.norm(zo)
     assert np.all(z[fixed] == 0.0)
     ctx.close()
+
+
+@pytest.mark.parametrize("kind", ["tet", "hex"])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-4)])
+def test_rollout_corotational(gpu_lib, kind, precision, tol):
+    """Co-rotational beams sagging under gravity (large rotations, small
+    strains) follow the oracle's rollout."""
+    mesh = fi.tet_beam(3, 3, 10) if kind == "tet" else fi.hex_beam(3, 3, 10, jitter=0.1, seed=4)
+    mu, lam = fi.lame_from_young(1e4, 0.3)
+    grav = fi.body_force(mesh, 1000.0, (0.0, 0.0, -9.81)).reshape(-1)
+    ctx = gpu_lib.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.COROTATIONAL, 1000.0,
+                            (mu, lam, 0.0), 0.01, 0.1, 0.01, precision=precision, tol=1e-10, refactor_every=3)
+    m = O.Model(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, O.COROTATIONAL, (mu, lam, 0.0),
+                1000.0, 0.01, 0.1, 0.01)
+    q = mesh.X.reshape(-1).copy()
+    v = np.zeros_like(q)
+    qg, vg = np.empty_like(q), np.empty_like(q)
+    for t in range(8):
+        ctx.step(grav, qg, vg)
+        q, v, _ = m.step(q, v, grav)
+    disp = np.abs(q - mesh.X.reshape(-1)).max()
+    assert disp > 1e-3
+    assert np.abs(qg - q).max() <= tol * disp
+    ctx.close()
+
+
+def test_corotational_refuses_checkpoints(gpu_lib):
+    mesh = fi.tet_beam(2, 2, 3)
+    with pytest.raises(gpu_lib.FEError):
+        gpu_lib.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.COROTATIONAL, 1000.0,
+                          LAWS[fi.COROTATIONAL], 0.01, 0.1, 0.01, keep_checkpoints=1)
 
 
 def test_rollout_with_tf32_factor(gpu_lib):
