@@ -286,6 +286,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--factor-tf32", action="store_true",
                     help="mixed precision: plain TF32 products in the factor's trailing updates")
+    ap.add_argument("--precond-fp16", type=int, default=1, choices=[0, 1],
+                    help="mixed precision: the preconditioner applies a binary16 copy of Y")
     ap.add_argument("--graph", action="store_true",
                     help="run the PCG iterations as replayed CUDA graphs (fe_options.use_graph)")
     ap.add_argument("--nd-leaf", type=int, default=0,
@@ -323,7 +325,8 @@ def main():
     dev = torch.device("cuda", local)
     ctx = fe.FEContext.from_workload(wl, device_ptrs=1, stream=stream.cuda_stream, profile_stages=1,
                                      nd_leaf_nodes=args.nd_leaf, use_graph=1 if args.graph else 0,
-                                     factor_tf32=1 if args.factor_tf32 else 0)
+                                     factor_tf32=1 if args.factor_tf32 else 0,
+                                     precond_fp16=args.precond_fp16 if wl.precision else 0)
     info = ctx.info()
     n = ctx.n
     loads = torch.tensor(np.stack([wl.p(t).reshape(-1) for t in range(W + K)]), dtype=torch.float64,
@@ -367,7 +370,8 @@ def main():
     if args.e2e_steps > 0:
         ctx2 = fe.FEContext.from_workload(wl, device_ptrs=0, nd_leaf_nodes=args.nd_leaf,
                                           use_graph=1 if args.graph else 0,
-                                          factor_tf32=1 if args.factor_tf32 else 0)
+                                          factor_tf32=1 if args.factor_tf32 else 0,
+                                     precond_fp16=args.precond_fp16 if wl.precision else 0)
         qh = np.empty(n)
         vh = np.empty(n)
         its2 = []
@@ -415,7 +419,8 @@ def main():
     vb = 4 if wl.precision else 8
     apply_calls = max(1, stage_calls["apply"])
     apply_ms = stage_ms["apply"] / apply_calls
-    bytes_apply = 2 * info["y_nnz"] * vb + 6 * info["n_free"] * vb + 2 * info["n"] * vb
+    yb = 2 if (wl.precision and args.precond_fp16) else vb
+    bytes_apply = 2 * info["y_nnz"] * yb + 6 * info["n_free"] * vb + 2 * info["n"] * vb
     achieved = bytes_apply / (apply_ms / 1e3) / 1e9 if apply_ms > 0 else None
     roofline_apply = {"bound": "hbm", "kernel": "precond apply (fwd_kernel + bwd_kernel per level)",
                       "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
@@ -437,6 +442,7 @@ def main():
                    "l2": "inputs larger than L2 (apply operators %.2f GB)" % (info["y_nnz"] * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single", "nd_leaf_nodes": args.nd_leaf or 64,
                    "pcg_graph": bool(args.graph), "factor_tf32": bool(args.factor_tf32),
+                   "precond_fp16": bool(wl.precision and args.precond_fp16),
                    "mean_pcg_iters": float(np.mean(iters)), "max_displacement_m": disp},
         "roofline": roofline,
         "roofline_apply": roofline_apply,

@@ -122,6 +122,14 @@ typedef struct {
                              FP32 accuracy (3xTF32 split on the tensor
                              cores), 1 = plain TF32 products (faster; a
                              coarser preconditioner, same final tolerance)   */
+  int32_t precond_fp16;   /* FE_MIXED: 1 = the preconditioner applies a binary16
+                             copy of Y (made from the FP32 factor once per
+                             factorisation; entries rounded to nearest and
+                             clamped to +-65504), halving the bytes each PCG
+                             iteration streams; arithmetic stays FP32 and the
+                             solve is still refined to tol in FP64.  The copy
+                             keeps M^{-1} = Y^T D^{-1} Y symmetric positive
+                             definite.  Ignored for FE_FP64.                  */
 } fe_options;
 
 typedef struct {

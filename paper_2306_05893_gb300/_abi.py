@@ -28,7 +28,8 @@ class FeOptions(ct.Structure):
                 ("nd_leaf_nodes", ct.c_int32), ("inner_tol", ct.c_double),
                 ("factor_timeout_s", ct.c_double), ("use_graph", ct.c_int32),
                 ("profile_stages", ct.c_int32), ("newton_iters", ct.c_int32),
-                ("newton_tol", ct.c_double), ("factor_tf32", ct.c_int32)]
+                ("newton_tol", ct.c_double), ("factor_tf32", ct.c_int32),
+                ("precond_fp16", ct.c_int32)]
 
 
 class FeStepInfo(ct.Structure):

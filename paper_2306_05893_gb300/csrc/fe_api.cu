@@ -269,6 +269,7 @@ int ensure_device(fe_ctx *c) {
   for (int k = 0; k < 2; ++k) {
     FE_TRY(dallocv(c, d, &d->Y[k], size_t(c->y_total) * ts));
     FE_TRY(dalloc(c, d, &d->D[k], size_t(2 * std::max<int64_t>(c->n_free, 1))));
+    if (c->opt.precond_fp16) FE_TRY(dallocv(c, d, &d->Yh[k], size_t(c->y_total) * 2));
   }
   FE_TRY(dallocv(c, d, &d->wbuf, size_t(c->w_total) * ts));
   FE_TRY(dallocv(c, d, &d->ubuf, size_t(std::max<int64_t>(c->u_total, 1)) * ts));
@@ -293,7 +294,7 @@ int ensure_device(fe_ctx *c) {
     FE_TRY(upload(c, d, &d->df_bdone, zero));
     FE_TRY(upload(c, d, &d->df_ctl, std::vector<int>(4, 0)));
   }
-  const size_t rb = mixed(c) ? 128 : 64;
+  const size_t rb = size_t(fwd_rows(c->opt));
   FE_TRY(dallocv(c, d, &d->part_f, size_t(std::max<int64_t>(c->fwd_slots, 1)) * rb * ts));
   FE_TRY(dallocv(c, d, &d->part_b, size_t(std::max<int64_t>(c->bwd_slots, 1)) * kBwdCols * ts));
   FE_TRY(dalloc(c, d, &d->tick_f, size_t(std::max<int64_t>(c->fwd_slots, 1))));

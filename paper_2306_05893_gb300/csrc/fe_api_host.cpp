@@ -26,6 +26,7 @@ int fe_options_default(fe_options *o) {
   o->newton_iters = 1;
   o->newton_tol = 0.0;
   o->factor_tf32 = 0;
+  o->precond_fp16 = 0;
   return FE_OK;
 }
 
@@ -70,6 +71,8 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
     if (!(c->opt.factor_timeout_s > 0)) c->opt.factor_timeout_s = 30.0;
     if (c->opt.nd_leaf_nodes <= 0) c->opt.nd_leaf_nodes = 64;
     if (c->opt.newton_iters <= 0) c->opt.newton_iters = 1;
+    if (c->opt.precision != FE_MIXED) c->opt.precond_fp16 = 0;
+    c->opt.precond_fp16 = c->opt.precond_fp16 ? 1 : 0;
     if (c->opt.newton_iters > 1 && c->opt.keep_checkpoints) {
       delete c;
       return FE_ERR_ARG;  // the adjoint differentiates the single-linearisation step

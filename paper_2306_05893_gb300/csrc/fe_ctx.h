@@ -16,7 +16,9 @@ constexpr int kSuper = 256;    // FP32 factor: trailing updates are applied once
 constexpr int kBwdCols = 32;   // pivot columns per task of the backward apply
 constexpr int kFwdCols = 256;  // pivot columns per task of the forward apply (split over CTAs)
 constexpr int kBwdRows = 1024; // rows per task of the backward apply (split over CTAs)
-inline int fwd_rows(int precision) { return precision == FE_MIXED ? 128 : 64; }  // 32 threads x one 16-byte vector
+// rows of Y per 16-byte vector: 8 binary16, 4 FP32, 2 FP64 entries
+inline int y_vec(const fe_options &o) { return o.precision == FE_MIXED ? (o.precond_fp16 ? 8 : 4) : 2; }
+inline int fwd_rows(const fe_options &o) { return 32 * y_vec(o); }  // 32 threads x one 16-byte vector
 
 // Task kinds of the multifrontal factorisation (packed in int4.y >> 24).
 enum TaskKind { T_DIAG = 0, T_PANEL = 1, T_XK = 2, T_TRAIL = 3, T_RUPD = 4 };

@@ -95,6 +95,7 @@ struct DeviceState {
   int32_t *tasks = nullptr;        // all task lists, concatenated
   void *F = nullptr;               // front scratch (factor type)
   void *Y[2] = {nullptr, nullptr}; // apply operators (double-buffered for the lag)
+  void *Yh[2] = {nullptr, nullptr};  // their binary16 copies (precond_fp16)
   double *D[2] = {nullptr, nullptr};
   void *wbuf = nullptr, *ubuf = nullptr, *yperm = nullptr;  // apply work vectors
   double *na = nullptr, *nq = nullptr, *nv = nullptr;       // Newton iterate a_k, q_k, v_k

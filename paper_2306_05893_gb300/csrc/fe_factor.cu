@@ -14,6 +14,7 @@
 // are dense GEMVs over Y, parallel across all rows/columns of all fronts of
 // a level: the only serial dependency left is the level order
 // (leaves up for L, root down for L^T), as in the paper's level schedule.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -47,9 +48,14 @@ static void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, si
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
-// 16-byte vectors along the rows of Y (its leading dimension is a multiple of 4).
+// 16-byte vectors along the rows of Y (its leading dimension is a multiple of 8).
 template <typename T>
 struct Vec16;
+template <>
+struct Vec16<__half> {
+  using type = uint4;
+  static constexpr int n = 8;
+};
 template <>
 struct Vec16<float> {
   using type = float4;
@@ -66,6 +72,26 @@ __device__ __forceinline__ float vget(const float4 &v, int q) {
   return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
 }
 __device__ __forceinline__ double vget(const double2 &v, int q) { return q == 0 ? v.x : v.y; }
+__device__ __forceinline__ float vget(const uint4 &v, int q) {
+  const uint32_t w = q < 2 ? v.x : q < 4 ? v.y : q < 6 ? v.z : v.w;
+  return __half2float(__ushort_as_half(static_cast<unsigned short>((q & 1) ? (w >> 16) : (w & 0xffffu))));
+}
+
+// Binary16 copy of Y for the application (precond_fp16): round to nearest,
+// clamped to the largest finite binary16 so that no entry becomes infinite.
+// 8 entries per thread (y_total is a multiple of 8).
+__global__ void __launch_bounds__(256) y_to_half_kernel(const float4 *__restrict__ Y, uint4 *__restrict__ Yh,
+                                                        int64_t n8) {
+  for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < n8; i += int64_t(gridDim.x) * 256) {
+    const float4 a = Y[2 * i], b = Y[2 * i + 1];
+    auto h2 = [](float x, float y) {
+      const float lim = 65504.f;
+      const __half2 h = __floats2half2_rn(fminf(fmaxf(x, -lim), lim), fminf(fmaxf(y, -lim), lim));
+      return *reinterpret_cast<const uint32_t *>(&h);
+    };
+    Yh[i] = make_uint4(h2(a.x, a.y), h2(a.z, a.w), h2(b.x, b.y), h2(b.z, b.w));
+  }
+}
 
 // -------------------------------------------------------------- assembly
 // Task (front, c0, c1): zero the lower part of columns [c0, c1) of F and of
@@ -1075,6 +1101,24 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
   }
 }
 
+// VW consecutive entries of the staged x (16-byte aligned) as vector loads
+template <int VW>
+__device__ __forceinline__ void xs_vec(const float *p, float (&x)[VW]) {
+#pragma unroll
+  for (int h = 0; h < VW / 4; ++h) {
+    const float4 t = reinterpret_cast<const float4 *>(p)[h];
+    x[4 * h] = t.x; x[4 * h + 1] = t.y; x[4 * h + 2] = t.z; x[4 * h + 3] = t.w;
+  }
+}
+template <int VW>
+__device__ __forceinline__ void xs_vec(const double *p, double (&x)[VW]) {
+#pragma unroll
+  for (int h = 0; h < VW / 2; ++h) {
+    const double2 t = reinterpret_cast<const double2 *>(p)[h];
+    x[2 * h] = t.x; x[2 * h + 1] = t.y;
+  }
+}
+
 // Backward task (front, c0, i0, slot): pivot columns [c0, c0 + 32) over the
 // rows [i0, i0 + kBwdRows); warp w owns columns c0 + w + 8k (k < 4) and
 // streams them together, the next four 16-byte loads per lane in flight.
@@ -1131,19 +1175,21 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
       if (tt < xb - xa && i >= c0 && i < m) xsrc[k] = i < p ? fr.first + i : -2 - urows[i - p];
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int32_t jc[4], ist[4];
+    // the four columns are all read from the task's first row (rows above a
+    // column's diagonal hold zeros of L^{-1}), so one vector load of the
+    // staged x per row block serves all of them, without bank conflicts
+    int32_t jc[4];
     const TF *yc[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       jc[k] = c0 + w + 8 * k;
       const int32_t j = jc[k] < p ? jc[k] : c0;  // out-of-range columns read a valid one, result dropped
       yc[k] = Y + fr.y_off + int64_t(j) * fr.ldy;
-      const int32_t ja = j & ~(VW - 1);
-      ist[k] = (ja > xa ? ja : xa) + VW * lane;
     }
+    const int32_t ist = xa + VW * lane;
     V cv[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) cv[k] = ist[k] < xb ? *reinterpret_cast<const V *>(yc[k] + ist[k]) : V{};
+    for (int k = 0; k < 4; ++k) cv[k] = ist < xb ? *reinterpret_cast<const V *>(yc[k] + ist) : V{};
     // the parent's solution entries must be complete
     if (threadIdx.x == 0)
       s_ok = fr.parent < 0 ? 1 : dep_wait(bdone + fr.parent, fronts[fr.parent].nbwd, ctl + 3, flags);
@@ -1156,23 +1202,22 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
     }
     __syncthreads();
     TV acc[4] = {TV(0), TV(0), TV(0), TV(0)};
-    const int32_t ilo = ist[0] < ist[3] ? ist[0] : ist[3];
-    for (int32_t off = 0; ilo + off < xb; off += 32 * VW) {
+    for (int32_t off = 0; xa + off < xb; off += 32 * VW) {
+      const int32_t i = ist + off;
       V nv[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int32_t i = ist[k] + off + 32 * VW;
-        nv[k] = i < xb ? *reinterpret_cast<const V *>(yc[k] + i) : V{};
-      }
+      for (int k = 0; k < 4; ++k) nv[k] = i + 32 * VW < xb ? *reinterpret_cast<const V *>(yc[k] + i + 32 * VW) : V{};
+      if (i < xb) {
+        TV xv[VW];
+        xs_vec<VW>(xs + (i - xa), xv);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int32_t i = ist[k] + off;
-        if (i < xb && jc[k] < p) {
+        for (int k = 0; k < 4; ++k) {
 #pragma unroll
-          for (int q = 0; q < VW; ++q) acc[k] += TV(vget(cv[k], q)) * xs[i - xa + q];
+          for (int q = 0; q < VW; ++q) acc[k] += TV(vget(cv[k], q)) * xv[q];
         }
-        cv[k] = nv[k];
       }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cv[k] = nv[k];
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -1250,6 +1295,14 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
       }
     }
   }
+  if constexpr (sizeof(TF) == 4) {
+    if (c->opt.precond_fp16) {
+      const int64_t n8 = c->y_total / 8;
+      d->launches++;
+      y_to_half_kernel<<<unsigned(std::max<int64_t>(1, std::min<int64_t>((n8 + 255) / 256, 152 * 16))), 256, 0,
+                         s>>>(reinterpret_cast<const float4 *>(Y), reinterpret_cast<uint4 *>(d->Yh[buf]), n8);
+    }
+  }
 }
 
 int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Afac, cudaStream_t s) {
@@ -1264,7 +1317,7 @@ template <typename TF, typename TV>
 static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, TV *u, TV *yp,
                               TV *part_f, TV *part_b, int *tick_f, int *tick_b, cudaStream_t s,
                               const double *done = nullptr) {
-  const TF *Y = reinterpret_cast<const TF *>(d->Y[buf]);
+  const TF *Y = reinterpret_cast<const TF *>(sizeof(TF) == 2 ? d->Yh[buf] : d->Y[buf]);
   const double *Dinv = d->D[buf] + c->n_free;
   const int nf = int(c->fronts.size());
   // persistent grids: every resident CTA (at most one per task)
@@ -1296,7 +1349,10 @@ static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const T
 
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
                    cudaStream_t s, const double *done) {
-  if (fp32)
+  if (fp32 && c->opt.precond_fp16)
+    apply_levels<__half, float>(c, d, buf, reinterpret_cast<const float *>(r), reinterpret_cast<float *>(z), s,
+                                done);
+  else if (fp32)
     apply_levels<float, float>(c, d, buf, reinterpret_cast<const float *>(r), reinterpret_cast<float *>(z), s, done);
   else
     apply_levels<double, double>(c, d, buf, reinterpret_cast<const double *>(r), reinterpret_cast<double *>(z), s,
@@ -1337,7 +1393,7 @@ extern "C" int fe_apply_preconditioner_noalloc(fe_ctx *c, const double *r, doubl
   const size_t ts = fp32 ? sizeof(float) : sizeof(double);
   const size_t b_vec = round256(size_t(c->n) * ts), b_u = round256(size_t(std::max<int64_t>(c->u_total, 1)) * ts);
   const size_t b_y = round256(size_t(std::max<int64_t>(c->n_free, 1)) * ts);
-  const size_t rb = fp32 ? 128 : 64;
+  const size_t rb = size_t(fwd_rows(c->opt));
   const size_t b_pf = round256(size_t(std::max<int64_t>(c->fwd_slots, 1)) * rb * ts);
   const size_t b_pb = round256(size_t(std::max<int64_t>(c->bwd_slots, 1)) * kBwdCols * ts);
   const size_t b_t = round256(size_t(std::max<int64_t>(c->fwd_slots + c->bwd_slots, 1)) * sizeof(int));
@@ -1371,7 +1427,11 @@ extern "C" int fe_apply_preconditioner_noalloc(fe_ctx *c, const double *r, doubl
   if (e == cudaSuccess) e = cudaMemsetAsync(tf, 0, b_t, s);
   if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, cudaGetErrorString(e));
   launch_convert(r, false, rT, fp32, c->n, s);
-  if (fp32)
+  if (fp32 && c->opt.precond_fp16)
+    apply_levels_with<__half, float>(c, d, d->cur, static_cast<const float *>(rT), static_cast<float *>(zT),
+                                     static_cast<float *>(ub), static_cast<float *>(yp), static_cast<float *>(pf),
+                                     static_cast<float *>(pb), tf, tb, s);
+  else if (fp32)
     apply_levels_with<float, float>(c, d, d->cur, static_cast<const float *>(rT), static_cast<float *>(zT),
                                     static_cast<float *>(ub), static_cast<float *>(yp), static_cast<float *>(pf),
                                     static_cast<float *>(pb), tf, tb, s);

@@ -419,7 +419,7 @@ int build_ordering(fe_ctx *c) {
     for (int32_t k : nd.fr[f].kids) lv = std::max(lv, c->fronts[k].level + 1);
     F.level = lv;
     int64_t m = F.m();
-    F.ldy = int32_t((m + 3) / 4 * 4);
+    F.ldy = int32_t((m + 7) / 8 * 8);  // 16-byte vectors of binary16 entries stay aligned
     F.f_off = f_total; f_total += m * m;
     F.y_off = y_total; y_total += int64_t(F.ldy) * F.npiv;
     F.w_off = w_total; w_total += m;
@@ -538,8 +538,8 @@ int build_ordering(fe_ctx *c) {
   // trailing-update tile: 128 x 128 for the FP32 factor, 64 x 64 for FP64
   const int32_t ut = c->opt.precision == FE_MIXED ? 128 : kTile;
   const int32_t sp = c->opt.precision == FE_MIXED ? kSuper : kNB;
-  const int32_t fr_rows = fwd_rows(c->opt.precision);
-  const int32_t vw = c->opt.precision == FE_MIXED ? 4 : 2;  // rows per 16-byte vector of Y
+  const int32_t fr_rows = fwd_rows(c->opt);
+  const int32_t vw = y_vec(c->opt);  // rows per 16-byte vector of Y
   c->fwd_slots = c->bwd_slots = 0;
   for (auto &L : c->levels) {
     int steps = 0;

@@ -114,16 +114,17 @@ def test_mixed_factor_is_a_close_preconditioner(gpu_lib):
     ctx.close()
 
 
-@pytest.mark.parametrize("tf32,res_tol,sol_tol", [(0, 1e-4, 1e-3), (1, 3e-2, 3e-1)])
+@pytest.mark.parametrize("tf32,fp16,res_tol,sol_tol", [(0, 0, 1e-4, 1e-3), (1, 0, 3e-2, 3e-1),
+                                                     (0, 1, 3e-2, 3e-1)])
 @pytest.mark.parametrize("kind", ["tet", "hex"])
-def test_mixed_factor_with_superpanels(gpu_lib, kind, tf32, res_tol, sol_tol):
+def test_mixed_factor_with_superpanels(gpu_lib, kind, tf32, fp16, res_tol, sol_tol):
     """FP32 factor of fronts wider than one superpanel (256 pivots, applied
     to the rest of the front once per superpanel) with ragged tails: the
     preconditioned vector agrees with the FP64 direct solve to FP32 accuracy;
     a missed or doubled update would leave an O(1) error."""
     mesh = fi.tet_beam(10, 10, 40) if kind == "tet" else fi.hex_beam(9, 9, 30, jitter=0.1, seed=4)
     q, v, p = _state(mesh, amp=0.01, seed=6)
-    ctx = _ctx(gpu_lib, mesh, fi.NEOHOOKE, 1, factor_tf32=tf32)
+    ctx = _ctx(gpu_lib, mesh, fi.NEOHOOKE, 1, factor_tf32=tf32, precond_fp16=fp16)
     npiv = ctx.ordering()["npiv"]
     assert npiv.max() > 256 and np.any(npiv % 64 != 0)
     ctx.set_state(q, v)
@@ -171,6 +172,45 @@ def test_corotational_refuses_checkpoints(gpu_lib):
     with pytest.raises(gpu_lib.FEError):
         gpu_lib.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.COROTATIONAL, 1000.0,
                           LAWS[fi.COROTATIONAL], 0.01, 0.1, 0.01, keep_checkpoints=1)
+
+
+def test_fp16_copy_is_a_symmetric_close_preconditioner(gpu_lib):
+    """The binary16 copy of Y changes M^{-1} = Y^T D^{-1} Y only by the
+    entries' rounding: it stays symmetric (both sweeps read the same stored
+    entries) and positive, and close to the FP32 copy's result."""
+    mesh = _mesh("tet")
+    q, v, p = _state(mesh, amp=0.01, seed=5)
+    zs = {}
+    for fp16 in (0, 1):
+        ctx = _ctx(gpu_lib, mesh, fi.MOONEY_RIVLIN, 1, precond_fp16=fp16)
+        ctx.set_state(q, v)
+        A, _ = ctx.assemble(p)
+        ctx.factor_now()
+        rng = np.random.default_rng(4)
+        fixed = (3 * mesh.fixed_nodes[:, None] + np.arange(3)).reshape(-1)
+        r, s = rng.standard_normal(ctx.n), rng.standard_normal(ctx.n)
+        r[fixed] = s[fixed] = 0.0
+        zr, zs_ = ctx.apply_preconditioner(r), ctx.apply_preconditioner(s)
+        zs[fp16] = zr
+        scale = np.linalg.norm(r) * np.linalg.norm(zs_)
+        assert abs(r @ zs_ - s @ zr) <= 1e-5 * scale
+        assert r @ zr > 0 and s @ zs_ > 0
+        import scipy.sparse as sp
+        S = sp.csr_matrix((A, ctx.colind, ctx.rowptr), shape=(ctx.n, ctx.n))
+        assert np.linalg.norm(S @ zr - r) <= (1e-3 if fp16 == 0 else 1e-2) * np.linalg.norm(r)
+        ctx.close()
+    assert np.linalg.norm(zs[1] - zs[0]) <= 1e-2 * np.linalg.norm(zs[0])
+
+
+@pytest.mark.parametrize("kind", ["tet", "hex"])
+def test_rollout_with_fp16_preconditioner(gpu_lib, kind):
+    """The binary16 Y coarsens only the preconditioner: the FP64-refined
+    rollout follows the oracle to the mixed tolerance."""
+    wl = fi.workload("tet-mr", a=3, b=3, c=10) if kind == "tet" else fi.workload("hex-nh", a=3, b=3, c=10)
+    qg, vg, q, v, infos = _rollout_pair(gpu_lib, wl, 6, precision=1, precond_fp16=1)
+    disp = np.abs(q - wl.mesh.X.reshape(-1)).max()
+    assert np.abs(qg - q).max() <= 1e-4 * disp
+    assert all(i.rel_residual <= wl.tol for i in infos)
 
 
 def test_rollout_with_tf32_factor(gpu_lib):

@@ -17,14 +17,14 @@ import fe_inputs as fi
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_noalloc_apply_matches_regular_apply(gpu_lib, precision):
+@pytest.mark.parametrize("precision,fp16", [(0, 0), (1, 0), (1, 1)])
+def test_noalloc_apply_matches_regular_apply(gpu_lib, precision, fp16):
     import torch
     fe = gpu_lib
     lib = fe.load()
     mesh = fi.tet_beam(3, 4, 9)
     ctx = fe.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.NEOHOOKE, 1000.0,
-                       (3.4e3, 3.1e4, 0.0), 0.01, 0.1, 0.01, precision=precision)
+                       (3.4e3, 3.1e4, 0.0), 0.01, 0.1, 0.01, precision=precision, precond_fp16=fp16)
     rng = np.random.default_rng(11)
     q = mesh.X.reshape(-1) + 0.01 * 0.01 * rng.standard_normal(ctx.n)
     fixed = (3 * mesh.fixed_nodes[:, None] + np.arange(3)).reshape(-1)
