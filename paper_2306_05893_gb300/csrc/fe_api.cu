@@ -2,6 +2,7 @@
 // (element kernel -> gather assembly -> [lagged factor on the side stream]
 // -> PCG with the level-scheduled LDL^T preconditioner -> backward Euler),
 // and the stage-level calls used by the parity tests.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is reached through the runtime)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -100,6 +101,62 @@ int upload(fe_ctx *c, DeviceState *d, T **p, const std::vector<T> &h) {
   if (st) return st;
   if (!h.empty()) FE_CUDA_TRY(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
   return FE_OK;
+}
+
+// Tensor maps for the TMA loads of the FP32 factor's trailing updates.
+// Per front: F as a 2-D array (rows contiguous, leading dimension ldf),
+// 128 x 16 boxes (a 128-row tile of 16 columns); Y as a 2-D array (the
+// pivot rows of a column contiguous, leading dimension ldy), 4 x 128 boxes
+// (4 consecutive pivot rows of 128 columns, which land in shared memory as
+// one K group of the MMA operand layout), and Y again with all its rows in
+// 128 x 16 boxes (output tiles of the Y updates).  Out-of-range elements
+// read as 0.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int encode_tensor_maps(fe_ctx *c, DeviceState *d) {
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return set_error(c, FE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  }
+  const EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
+  const int64_t nf = int64_t(c->fronts.size());
+  std::vector<CUtensorMap> maps(size_t(5 * nf));
+  for (int64_t f = 0; f < nf; ++f) {
+    const Front &F = c->fronts[f];
+    const cuuint32_t es[2] = {1, 1};
+    {
+      const cuuint64_t dim[2] = {cuuint64_t(F.m()), cuuint64_t(F.m())};
+      const cuuint64_t stride[1] = {cuuint64_t(F.ldf) * 4};
+      const cuuint32_t box[2] = {128, 16};
+      float *base = reinterpret_cast<float *>(d->F) + F.f_off;
+      if (encode(&maps[size_t(f)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dim, stride, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return set_error(c, FE_ERR_CUDA, "tensor map of front " + std::to_string(f) + " (F) rejected");
+    }
+    for (int b = 0; b < 2; ++b) {
+      const cuuint64_t dim[2] = {cuuint64_t(F.npiv), cuuint64_t(F.npiv)};
+      const cuuint64_t stride[1] = {cuuint64_t(F.ldy) * 4};
+      const cuuint32_t box[2] = {4, 128};
+      float *base = reinterpret_cast<float *>(d->Y[b]) + F.y_off;
+      if (encode(&maps[size_t((1 + b) * nf + f)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dim, stride, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return set_error(c, FE_ERR_CUDA, "tensor map of front " + std::to_string(f) + " (Y) rejected");
+      const cuuint64_t dimc[2] = {cuuint64_t(F.m()), cuuint64_t(F.npiv)};
+      const cuuint32_t boxc[2] = {128, 16};
+      if (encode(&maps[size_t((3 + b) * nf + f)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dimc, stride, boxc, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return set_error(c, FE_ERR_CUDA, "tensor map of front " + std::to_string(f) + " (Y rows) rejected");
+    }
+  }
+  return upload(c, d, reinterpret_cast<CUtensorMap **>(&d->tmaps), maps);
 }
 
 #define FE_TRY(x)      \
@@ -219,7 +276,7 @@ int ensure_device(fe_ctx *c) {
     o.child_begin = c->child_ptr[f]; o.child_end = c->child_ptr[f + 1];
     o.f_off = F.f_off; o.y_off = F.y_off; o.w_off = F.w_off; o.u_off = F.u_off;
     o.rows_off = F.rows_off; o.fac_off = fac;
-    o.ldy = F.ldy; o.parent = F.parent;
+    o.ldy = F.ldy; o.parent = F.parent; o.ldf = F.ldf;
     o.nfwd = c->front_nfwd[f]; o.nbwd = c->front_nbwd[f];
     fac += F.npiv + 1;
   }
@@ -294,6 +351,7 @@ int ensure_device(fe_ctx *c) {
     FE_TRY(upload(c, d, &d->df_bdone, zero));
     FE_TRY(upload(c, d, &d->df_ctl, std::vector<int>(4, 0)));
   }
+  if (mixed(c)) FE_TRY(encode_tensor_maps(c, d));
   const size_t rb = size_t(fwd_rows(c->opt));
   FE_TRY(dallocv(c, d, &d->part_f, size_t(std::max<int64_t>(c->fwd_slots, 1)) * rb * ts));
   FE_TRY(dallocv(c, d, &d->part_b, size_t(std::max<int64_t>(c->bwd_slots, 1)) * kBwdCols * ts));

@@ -29,7 +29,8 @@ struct Front {
   int32_t nupd = 0;       // number of update rows (DOFs)
   int32_t parent = -1;
   int32_t level = 0;      // 0 = leaf; children are on lower levels
-  int64_t f_off = 0;      // offset of the dense m x m front (column-major)
+  int64_t f_off = 0;      // offset of the dense m x m front (column-major, leading dimension ldf)
+  int32_t ldf = 0;        // m rounded up to 4: every column starts 16-byte aligned (TMA tiles)
   int64_t y_off = 0;      // offset of the m x p apply operator Y
   int64_t w_off = 0;      // offset of the m-vector work buffer
   int64_t u_off = 0;      // offset of the update vector (nupd)

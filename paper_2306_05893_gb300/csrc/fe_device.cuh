@@ -23,6 +23,7 @@ struct DFront {
   int32_t child_begin, child_end;    // into child_list
   int32_t ldy, parent;               // parent front (-1: a root)
   int32_t nfwd, nbwd;                // tasks of this front in the dataflow application lists
+  int32_t ldf;                       // leading dimension of the front's F (multiple of 4)
   int64_t f_off, y_off, w_off, u_off, rows_off, fac_off;
 };
 
@@ -96,6 +97,12 @@ struct DeviceState {
   void *F = nullptr;               // front scratch (factor type)
   void *Y[2] = {nullptr, nullptr}; // apply operators (double-buffered for the lag)
   void *Yh[2] = {nullptr, nullptr};  // their binary16 copies (precond_fp16)
+  // TMA tensor maps of the FP32 factor (128-byte CUtensorMap objects, 64-byte
+  // aligned): [0, nf) one per front over F, [nf, 3 nf) one per front over
+  // the pivot rows of Y[0] then Y[1] (4 x 128 boxes), [3 nf, 5 nf) one per
+  // front over all rows of Y[0] then Y[1] (128 x 16 boxes); null for the
+  // FP64 factor
+  void *tmaps = nullptr;
   double *D[2] = {nullptr, nullptr};
   void *wbuf = nullptr, *ubuf = nullptr, *yperm = nullptr;  // apply work vectors
   double *na = nullptr, *nq = nullptr, *nv = nullptr;       // Newton iterate a_k, q_k, v_k

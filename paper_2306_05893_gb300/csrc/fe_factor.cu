@@ -14,6 +14,7 @@
 // are dense GEMVs over Y, parallel across all rows/columns of all fronts of
 // a level: the only serial dependency left is the level order
 // (leaves up for L, root down for L^T), as in the paper's level schedule.
+#include <cuda.h>  // CUtensorMap
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
   TF *Ff = F + fr.f_off;
   pdl_wait();
   for (int32_t col = c0; col < c1; ++col) {
-    TF *cp = Ff + int64_t(col) * m;
+    TF *cp = Ff + int64_t(col) * fr.ldf;
     for (int32_t r = col + threadIdx.x; r < m; r += blockDim.x) cp[r] = TF(0);
     if (col < p) {
       TF *yp = Y + fr.y_off + int64_t(col) * fr.ldy;
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
   for (int32_t ci = fr.child_begin; ci < fr.child_end; ++ci) {
     const DFront ch = fronts[child_list[ci]];
     const int32_t *rm = rmap + ch.rows_off;
-    const int32_t nu = ch.nupd, pc = ch.npiv, mc = ch.m;
+    const int32_t nu = ch.nupd, pc = ch.npiv;
     // child columns mapping into [c0, c1): contiguous since rm is increasing
     int32_t lo = 0, hi = nu;
     while (lo < hi) { int32_t mid = (lo + hi) >> 1; if (rm[mid] < c0) lo = mid + 1; else hi = mid; }
@@ -149,8 +150,8 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
     const int32_t jhi = lo;
     const TF *Fc = F + ch.f_off;
     for (int32_t j = jlo; j < jhi; ++j) {
-      const TF *src = Fc + int64_t(pc + j) * mc + pc;
-      TF *dst = Ff + int64_t(rm[j]) * m;
+      const TF *src = Fc + int64_t(pc + j) * ch.ldf + pc;
+      TF *dst = Ff + int64_t(rm[j]) * fr.ldf;
       // 8 rows per thread in flight: all loads of a batch before its stores
       // (a store ahead of the next load would expose one latency per row);
       // the child's rows map to distinct parent rows, so a batch never
@@ -272,12 +273,12 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
   pdl_launch_dependents();
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
-  const int32_t k0 = t.y & 0xffffff, kb = t.z, m = fr.m;
+  const int32_t k0 = t.y & 0xffffff, kb = t.z;
   TF *Ff = F + fr.f_off;
   pdl_wait();
   for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
     const int i = idx % 64, j = idx / 64;
-    Ls[i][j] = (i < kb && j < kb && i >= j) ? Ff[(k0 + i) + int64_t(k0 + j) * m] : TF(0);
+    Ls[i][j] = (i < kb && j < kb && i >= j) ? Ff[(k0 + i) + int64_t(k0 + j) * fr.ldf] : TF(0);
   }
   __syncthreads();
   auto safe_inv = [](TF d) { return d > TF(0) ? TF(1) / d : TF(1); };
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
       sc = s_invf[j].hi;
     else
       sc = TF(s_inv[j]);
-    if (i > j) Ff[(k0 + i) + int64_t(k0 + j) * m] = Ls[i][j] * sc;
+    if (i > j) Ff[(k0 + i) + int64_t(k0 + j) * fr.ldf] = Ls[i][j] * sc;
     Yf[(k0 + i) + int64_t(k0 + j) * fr.ldy] = Xs[i][j];
   }
 }
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
     for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
       const int i = idx % 64, j = idx / 64;
       const int32_t r = a0 + i;
-      Bs[i][j] = (r < m && j < kb) ? Ff[r + int64_t(k0 + j) * m] : TF(0);
+      Bs[i][j] = (r < m && j < kb) ? Ff[r + int64_t(k0 + j) * fr.ldf] : TF(0);
     }
     __syncthreads();
     TF acc[4][4] = {};
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int32_t r = a0 + tr * 4 + u;
-        if (r < m) Ff[r + int64_t(k0 + c) * m] = acc[u][s] * di;
+        if (r < m) Ff[r + int64_t(k0 + c) * fr.ldf] = acc[u][s] * di;
       }
     }
   } else {  // T_XK
@@ -536,13 +537,13 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
   for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
     const int i = idx % 64, l = idx / 64;
     const int32_t r = i0 + i;
-    As[i][l] = (r < m && l < kb) ? Ff[r + int64_t(k0 + l) * m] : TF(0);
+    As[i][l] = (r < m && l < kb) ? Ff[r + int64_t(k0 + l) * fr.ldf] : TF(0);
   }
   if (kind == T_TRAIL) {
     for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
       const int j = idx % 64, l = idx / 64;
       const int32_t r = j0 + j;
-      Bs[j][l] = (r < m && l < kb) ? Ff[r + int64_t(k0 + l) * m] * TF(D[fr.first + k0 + l]) : TF(0);
+      Bs[j][l] = (r < m && l < kb) ? Ff[r + int64_t(k0 + l) * fr.ldf] * TF(D[fr.first + k0 + l]) : TF(0);
     }
   } else {
     for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
@@ -573,7 +574,7 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int32_t r = i0 + tr + 16 * u;
-        if (r < m && r >= c) Ff[r + int64_t(c) * m] -= acc[u][s];
+        if (r < m && r >= c) Ff[r + int64_t(c) * fr.ldf] -= acc[u][s];
       }
     }
   } else {
@@ -604,24 +605,54 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
 //
 // Blackwell tensor cores (tcgen05, kind::tf32) with a 3xTF32 split
 // (a = a_hi + a_lo, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) so products keep
-// ~FP32 accuracy.  Per 32-wide K chunk all 256 threads load the operands
-// from global memory into registers, split each element once, and store the
-// four operands (A_hi, A_lo, B_hi, B_lo) into shared memory in the K-major,
-// no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix; 128 B
-// between 8-row groups, 2048 B between 4-column K groups).  One thread issues
-// the 12 MMAs of the chunk (M = N = 128, K = 8 each) into a 128 x 128 FP32
-// accumulator in tensor memory and commits them to an mbarrier; the next
-// chunk's global loads are in flight meanwhile.  The epilogue reads the
+// ~FP32 accuracy, fed by the TMA unit, with warp-specialised roles:
+//  * warp 8 (producer and MMA issuer) keeps a ring of kUStages raw K chunks
+//    (16 columns each) in flight: per chunk one tensor-map load of the
+//    128 x 16 A tile (F rows i0.., columns k..k + 16, rows contiguous) and
+//    either the 128 x 16 B tile of F (TRAIL) or four 4 x 128 boxes of Y
+//    (RUPD: pivot rows k.. of columns j0.., which land directly in the
+//    operand layout), plus the chunk's d_l, completing on the stage's
+//    mbarrier; it issues each chunk's MMAs (M = N = 128, K = 8 each) into a
+//    128 x 128 FP32 accumulator in tensor memory once the operands are
+//    ready, commits them to the operand stage's mbarrier, and refills the
+//    raw stage just consumed;
+//  * warps 0-7 turn raw chunk q into the MMA operands: the TF32 high and
+//    low parts (B scaled by d_l for TRAIL, columns at or past the task's K
+//    end zeroed) in the K-major, no-swizzle core-matrix layout (8 rows x 16
+//    bytes per core matrix; 128 B between 8-row groups, 2048 B between
+//    4-column K groups), into one of two operand stages, so the conversion
+//    of chunk q overlaps the MMAs of chunk q - 1.  A thread reads 4 columns
+//    of one row from the raw tile (consecutive rows across a warp: no bank
+//    conflicts) and writes them as one 16-byte vector (consecutive slots).
+// Epilogue: once the last MMAs have completed, warps 0-7 read the
 // accumulator with tcgen05.ld (warp w: lanes 32 (w % 4) .., columns
-// 64 (w / 4) ..) and updates F or Y in place with coalesced accesses.
+// 64 (w / 4) ..) and stage its negative (0 outside the task's range) in the
+// freed shared memory, and one thread adds the staged 128 x 128 tile to F
+// or Y with eight TMA reduce-add boxes (each entry receives exactly one
+// addition per launch: deterministic).  Every
+// mbarrier wait is bounded in time and gives up at once when another thread
+// of the CTA has given up (a shared abort word); the CTA then raises
+// FLAG_WAIT_TIMEOUT, waits (bounded) for the copies and MMAs it has in
+// flight, frees its tensor memory and returns.
 constexpr int kT128 = 128;
-constexpr int kKc = 32;                              // K chunk
-constexpr int kOpBytes = kT128 * kKc * 4;            // one operand of one chunk: 16 KB
+constexpr int kUK = 16;                              // K columns per chunk
+constexpr int kUStages = 3;                          // raw chunks in flight (TMA ring)
+constexpr int kUOpBytes = kT128 * kUK * 4;           // one operand of one chunk: 8 KB
+constexpr int kUThreads = 288;                       // 8 converter/epilogue warps + 1 producer/MMA warp
 constexpr int kUmmaLbo = 2048;                       // K-direction core-matrix stride
 constexpr int kUmmaSbo = 128;                        // M/N-direction (8-row group) stride
-// operands (hi and lo parts of A and B, or the TF32 parts alone) + mbarrier/TMEM slot
+// raw ring (A and B per stage) + two operand stages (hi and lo parts of A
+// and B, or the TF32 parts alone) + d_l per raw stage + mbarriers/TMEM slot:
+// 112.3 KB for 3xTF32, so that two CTAs fit on an SM (228 KB, 1 KB reserved
+// per CTA).  The staged output tile of the epilogue (64 KB) reuses the front.
 template <int NMMA>
-constexpr size_t update_smem() { return size_t(NMMA == 3 ? 4 : 2) * kOpBytes + 128; }
+__host__ __device__ constexpr int update_nop() { return NMMA == 3 ? 4 : 2; }
+constexpr int kUDqOff(int nop) { return kUStages * 2 * kUOpBytes + 2 * nop * kUOpBytes; }
+template <int NMMA>
+constexpr size_t update_smem() {
+  return size_t(kUDqOff(update_nop<NMMA>())) + kUStages * kUK * 4 + 128;
+}
+static_assert(kUStages * 2 * kUOpBytes + 2 * 2 * kUOpBytes >= kT128 * kT128 * 4, "the output tile fits the operand space");
 constexpr uint64_t kWaitLimitNs = 1000000000ull;     // give up an mbarrier wait after 1 s
 
 // tcgen05 instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B
@@ -636,56 +667,84 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
          (uint64_t(1) << 46);
 }
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-  return r;
+// TF32 parts by integer arithmetic on the FP32 bit pattern (full-rate ALU
+// instead of conversions): the high part rounds the 10-bit mantissa to
+// nearest (ties away from zero: add half a unit of the 13 dropped bits,
+// then clear them; a carry into the exponent is the correct rounding), the
+// low part x - hi is exact in FP32 and is truncated to TF32 (error at most
+// 2^-10 of it, i.e. ~2^-21 of x).
+__device__ __forceinline__ uint32_t tf32_hi(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
+__device__ __forceinline__ uint32_t tf32_lo(float x, uint32_t hi) {
+  return __float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Bounded wait on the mbarrier phase with the given parity; false if the
-// limit ran out.
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
   return t;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait on the mbarrier phase with the given parity; false if the
+// limit ran out or (when given) the abort word is set.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int *abort_word = nullptr) {
+  if (mbar_try(bar, parity)) return true;  // (the timer is read only when the phase is still open)
   const uint64_t t0 = global_ns();
   for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (mbar_try(bar, parity)) return true;
+    if ((abort_word && *abort_word) || global_ns() - t0 > kWaitLimitNs) return false;
   }
+}
+
+// 2-D tensor-map load into shared memory, completing on an mbarrier
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *map, int32_t x, int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// 2-D tensor-map reduce-add of one box from shared memory into global
+// memory (FP32 additions performed in L2; bulk async group)
+__device__ __forceinline__ void tma_reduce_add_2d(const void *map, int32_t x, int32_t y, uint32_t src) {
+  asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                   map),
+               "r"(x), "r"(y), "r"(src)
+               : "memory");
 }
 
 // NMMA = 3: the 3xTF32 split (FP32-accurate products); NMMA = 1: one TF32
 // MMA per product (operands rounded to TF32, ~1e-3 relative; the factor is
 // only a preconditioner and the solve is refined in FP64).
 template <int NMMA>
-__global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *__restrict__ tasks,
-                                                                 const DFront *__restrict__ fronts,
-                                                                 float *__restrict__ F, float *__restrict__ Y,
-                                                                 const double *__restrict__ D, int *flags) {
+__global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
+    const int32_t *__restrict__ tasks, const DFront *__restrict__ fronts, float *__restrict__ F,
+    float *__restrict__ Y, const double *__restrict__ D, const CUtensorMap *__restrict__ fmaps,
+    const CUtensorMap *__restrict__ ymaps, const CUtensorMap *__restrict__ ycmaps, int *flags) {
   static_assert(NMMA == 1 || NMMA == 3, "3xTF32 or TF32");
-  constexpr int NB = NMMA == 3 ? 4 : 2;
+  constexpr int NOP = update_nop<NMMA>();
+  constexpr int OPF = kUOpBytes / 4;  // floats per operand chunk
   extern __shared__ __align__(1024) unsigned char usm[];
-  float *sAh = reinterpret_cast<float *>(usm);
-  float *sBh = reinterpret_cast<float *>(usm + kOpBytes);
-  float *sAl = reinterpret_cast<float *>(usm + 2 * kOpBytes);  // NMMA = 3 only
-  float *sBl = reinterpret_cast<float *>(usm + 3 * kOpBytes);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(usm + NB * kOpBytes);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(usm + NB * kOpBytes + 8);
-  __shared__ float Ds[kSuper];
+  unsigned char *raw = usm;                                            // kUStages x (A, B)
+  unsigned char *opnd = usm + kUStages * 2 * kUOpBytes;                // 2 x NOP operands
+  float *Dq = reinterpret_cast<float *>(usm + kUDqOff(NOP));           // d_l of each raw stage
+  uint64_t *bars = reinterpret_cast<uint64_t *>(Dq + kUStages * kUK);  // full[3], ready[2], mma[2]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kUStages + 4);
+  int &s_abort = *reinterpret_cast<int *>(tmem_slot + 1);  // (dynamic: no static shared memory)
+  const volatile int *abort_word = &s_abort;
   pdl_launch_dependents();
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
@@ -697,14 +756,23 @@ __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *
   const int32_t s_end = min((k0 / kSuper + 1) * kSuper, p);
   const bool eager = kend < s_end;
   const bool trail = kind == T_TRAIL;
-  float *Ff = F + fr.f_off;
-  float *Yf = Y + fr.y_off;
+  const CUtensorMap *mapA = fmaps + t.x;
+  const CUtensorMap *mapB = trail ? fmaps + t.x : ymaps + t.x;
+  const CUtensorMap *mapC = trail ? fmaps + t.x : ycmaps + t.x;  // the output tile (F or all rows of Y)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nq = (kw + kUK - 1) / kUK;
+  const uint32_t bar_full = smem_u32(bars), bar_ready = bar_full + 8 * kUStages;
+  const uint32_t bar_mma = bar_ready + 16;
+  const uint32_t raw_u = smem_u32(raw), op_u = smem_u32(opnd);
   pdl_wait();
-  for (int l = threadIdx.x; l < kSuper; l += 256) Ds[l] = (trail && l < kw) ? float(D[fr.first + k0 + l]) : 1.f;
-  const uint32_t bar_a = smem_u32(bar);
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a) : "memory");
+    s_abort = 0;
+    for (int b = 0; b < kUStages; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_full + 8 * b) : "memory");
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(bar_ready + 8 * b) : "memory");  // 8 warps
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_mma + 8 * b) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -717,135 +785,200 @@ __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-
-  // Warp w loads K columns 4 w + lane % 4 of the chunk for rows 8 u + lane / 4
-  // (u < 16): the core matrix (row group u, K group w), at byte offset
-  // w LBO + u SBO + 4 lane of an operand.  Chunk q + 1 is loaded into the
-  // second register set while chunk q is split, stored and multiplied.
-  const int nchunk = (kw + kKc - 1) / kKc;
-  const int lr = lane >> 2, lk = 4 * warp + (lane & 3);
-  float ra[2][16], rb[2][16];
-  auto load_chunk = [&](int q, float (&xa)[16], float (&xb)[16]) {
-    const int32_t l = k0 + kKc * q + lk;
-    const bool lok = l < kend;
-    const float *pa = Ff + (i0 + lr) + int64_t(l) * m;
-    const float *pb = trail ? Ff + (j0 + lr) + int64_t(l) * m : Yf + l + int64_t(j0 + lr) * fr.ldy;
-    const int64_t sb = trail ? 8 : int64_t(8) * fr.ldy;
-    const int32_t bmax = trail ? m : kend;
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      xa[u] = (lok && i0 + lr + 8 * u < m) ? pa[8 * u] : 0.f;
-      xb[u] = (lok && j0 + lr + 8 * u < bmax) ? pb[sb * u] : 0.f;
-    }
-  };
-  auto store_chunk = [&](int q, const float (&xa)[16], const float (&xb)[16]) {
-    const float dl = Ds[min(kKc * q + lk, kSuper - 1)];
-    const int off0 = warp * (kUmmaLbo / 4) + lane;
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int off = off0 + u * (kUmmaSbo / 4);
-      const float bv = xb[u] * dl;
-      const uint32_t ah = to_tf32(xa[u]), bh = to_tf32(bv);
-      sAh[off] = __uint_as_float(ah);
-      sBh[off] = __uint_as_float(bh);
-      if constexpr (NMMA == 3) {
-        sAl[off] = __uint_as_float(to_tf32(xa[u] - __uint_as_float(ah)));
-        sBl[off] = __uint_as_float(to_tf32(bv - __uint_as_float(bh)));
-      }
-    }
-  };
-  auto issue_chunk = [&](int q) {
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
-#pragma unroll
-    for (int s = 0; s < kKc / 8; ++s) {
-      const uint32_t ko = uint32_t(s) * 2 * kUmmaLbo;  // two K groups of 4 per MMA
-      const uint64_t dah = umma_desc(ah + ko), dal = umma_desc(al + ko);
-      const uint64_t dbh = umma_desc(bh + ko), dbl = umma_desc(bl + ko);
-      const uint32_t acc0 = (q > 0 || s > 0) ? 1u : 0u;
-      if constexpr (NMMA == 3) {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(dal), "l"(dbh), "r"(kIdescTf32), "r"(acc0)
-            : "memory");
-        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah),
-                     "l"(dbl), "r"(kIdescTf32)
-                     : "memory");
-        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(dah),
-                     "l"(dbh), "r"(kIdescTf32)
-                     : "memory");
-      } else {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(dah), "l"(dbh), "r"(kIdescTf32), "r"(acc0)
-            : "memory");
-        (void)dal;
-        (void)dbl;
-      }
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_a)
-                 : "memory");
-  };
-  __syncthreads();  // Ds ready
-  load_chunk(0, ra[0], rb[0]);
   bool ok = true;
-  for (int q = 0; q < nchunk; q += 2) {
+  int issued = 0, mma_issued = 0;  // warp 8's view
+
+  if (warp == 8) {
+    // ------------------------------------------------ producer / MMA issuer
+    // raw chunk q into stage q % kUStages: d_l first (lanes 0-15), then the
+    // expected bytes and the TMA loads (lane 0)
+    // (the stage's mbarrier completes once the loads have landed and lane 0
+    // has arrived, after d_l is stored)
+    auto produce = [&](int q) {
+      const int s = q % kUStages;
+      const int32_t kq = k0 + kUK * q;
+      const uint32_t bar = bar_full + 8 * s;
+      const float dv = (lane < kUK && trail && kq + lane < kend) ? float(D[fr.first + kq + lane]) : 0.f;
+      if (lane == 0) {
+        asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(2 * kUOpBytes)
+                     : "memory");
+        const uint32_t dA = raw_u + uint32_t(s) * 2 * kUOpBytes, dB = dA + kUOpBytes;
+        tma_load_2d(dA, mapA, i0, kq, bar);
+        if (trail) {
+          tma_load_2d(dB, mapB, j0, kq, bar);
+        } else {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int qq = q + h;
-      if (qq < nchunk) {
-        if (qq + 1 < nchunk) load_chunk(qq + 1, ra[h ^ 1], rb[h ^ 1]);
-        if (qq > 0) ok = ok && mbar_wait(bar_a, uint32_t(qq - 1) & 1u);  // chunk qq-1's MMAs have read the operands
-        store_chunk(qq, ra[h], rb[h]);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic-proxy stores -> tensor core
-        __syncthreads();
-        if (threadIdx.x == 0 && ok) issue_chunk(qq);
+          for (int g = 0; g < 4; ++g) tma_load_2d(dB + uint32_t(g) * (kUOpBytes / 4), mapB, kq + 4 * g, j0, bar);
+        }
       }
+      if (lane < kUK) Dq[s * kUK + lane] = dv;
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+    };
+    for (; issued < min(kUStages, nq); ++issued) produce(issued);
+    for (int q = 0; q < nq && ok; ++q) {
+      const int o = q & 1;
+      if (lane == 0) ok = mbar_wait(bar_ready + 8 * o, uint32_t(q >> 1) & 1u, abort_word);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) break;
+      if (lane == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t ah = op_u + uint32_t(o) * NOP * kUOpBytes, bh = ah + kUOpBytes;
+        const uint32_t al = ah + 2 * kUOpBytes, bl = ah + 3 * kUOpBytes;
+#pragma unroll
+        for (int s = 0; s < kUK / 8; ++s) {
+          const uint32_t ko = uint32_t(s) * 2 * kUmmaLbo;  // two K groups of 4 per MMA
+          const uint32_t acc0 = (q > 0 || s > 0) ? 1u : 0u;
+          if constexpr (NMMA == 3) {
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(umma_desc(al + ko)), "l"(umma_desc(bh + ko)), "r"(kIdescTf32), "r"(acc0)
+                : "memory");
+            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem),
+                         "l"(umma_desc(ah + ko)), "l"(umma_desc(bl + ko)), "r"(kIdescTf32)
+                         : "memory");
+            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem),
+                         "l"(umma_desc(ah + ko)), "l"(umma_desc(bh + ko)), "r"(kIdescTf32)
+                         : "memory");
+          } else {
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(umma_desc(ah + ko)), "l"(umma_desc(bh + ko)), "r"(kIdescTf32), "r"(acc0)
+                : "memory");
+            (void)al;
+            (void)bl;
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         bar_mma + 8 * o)
+                     : "memory");
+      }
+      mma_issued = q + 1;
+      // the operands of chunk q being ready means raw stage q % kUStages
+      // has been read by every converter: refill it
+      if (issued < nq) produce(issued++);
     }
-  }
-  ok = ok && mbar_wait(bar_a, uint32_t(nchunk - 1) & 1u);
-  ok = __syncthreads_and(ok) != 0;
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (ok) {
-    // epilogue: TRAIL writes the lower part of columns < cmax (the
-    // superpanel's end for an eager task), RUPD rows < rmax of columns < kend
-    const int32_t cmax = trail ? (eager ? s_end : m) : kend;
-    const int32_t rmax = (!trail && eager) ? s_end : m;
-    const int g = warp & 3, h = warp >> 2;
-    const int32_t r = i0 + 32 * g + lane;
-    float *base = trail ? Ff + r : Yf + r;
-    const int64_t ld = trail ? int64_t(m) : int64_t(fr.ldy);
-#pragma unroll 1
-    for (int x = 0; x < 4; ++x) {
-      const int32_t c0 = j0 + 64 * h + 16 * x;
-      // all loads of the row's 16 entries first, then the stores (a store
-      // between two loads would expose one memory latency per entry)
-      float old[16];
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  } else {
+    // ------------------------------------------------------- converters
+    const int row = threadIdx.x & 127, gb = threadIdx.x >> 7;  // K groups gb and gb + 2
+    for (int q = 0; q < nq && ok; ++q) {
+      const int s = q % kUStages, o = q & 1;
+      ok = mbar_wait(bar_full + 8 * s, uint32_t(q / kUStages) & 1u, abort_word);
+      // the MMAs of chunk q - 2 have read operand stage o
+      if (ok && q >= 2) ok = mbar_wait(bar_mma + 8 * o, uint32_t((q - 2) >> 1) & 1u, abort_word);
+      if (!ok) break;
+      const float *rA = reinterpret_cast<const float *>(raw + s * 2 * kUOpBytes);
+      const float *rB = rA + OPF;
+      const float *dq = Dq + s * kUK;
+      float *ob = reinterpret_cast<float *>(opnd + o * NOP * kUOpBytes);
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int32_t cc = c0 + e;
-        const bool in = r < rmax && cc < cmax && (!trail || r >= cc);
-        old[e] = in ? base[int64_t(cc) * ld] : 0.f;
+      for (int gg = 0; gg < 2; ++gg) {
+        const int g = gb + 2 * gg;
+        const int kl = kUK * q + 4 * g;  // local column of the group's first entry
+        float a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = rA[(4 * g + i) * kT128 + row];  // raw A: [k][row]
+        if (trail) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) b[i] = rB[(4 * g + i) * kT128 + row] * dq[4 * g + i];
+        } else {  // raw B: [g][row][4], already the operand layout
+          const float4 v = *reinterpret_cast<const float4 *>(rB + g * (OPF / 4) + 4 * row);
+          b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (kl + i >= kw) a[i] = b[i] = 0.f;
+        const int off = g * (OPF / 4) + 4 * row;  // K group g, row: 16-byte slot
+        uint32_t ah[4], bh[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          ah[i] = tf32_hi(a[i]);
+          bh[i] = tf32_hi(b[i]);
+        }
+        *reinterpret_cast<uint4 *>(ob + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
+        *reinterpret_cast<uint4 *>(ob + OPF + off) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
+        if constexpr (NMMA == 3) {
+          uint32_t al[4], bl[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            al[i] = tf32_lo(a[i], ah[i]);
+            bl[i] = tf32_lo(b[i], bh[i]);
+          }
+          *reinterpret_cast<uint4 *>(ob + 2 * OPF + off) = make_uint4(al[0], al[1], al[2], al[3]);
+          *reinterpret_cast<uint4 *>(ob + 3 * OPF + off) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
+        }
       }
-      uint32_t v[16];
-      const uint32_t ta = tmem + (uint32_t(32 * g) << 16) + uint32_t(64 * h + 16 * x);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(ta));
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic-proxy stores -> tensor core
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar_ready + 8 * o) : "memory");
+    }
+    // the accumulator is complete (and every operand read: the shared
+    // memory is free for the staged tile)
+    if (ok && nq > 0) ok = mbar_wait(bar_mma + 8 * ((nq - 1) & 1), uint32_t((nq - 1) >> 1) & 1u, abort_word);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+      // TRAIL writes the lower part of columns < cmax (the superpanel's end
+      // for an eager task), RUPD rows < rmax of columns < kend; a delayed
+      // task's tile may start below the superpanel's end (its origin is
+      // rounded down to a multiple of 4), and those rows and columns are
+      // not touched
+      const int32_t cmax = trail ? (eager ? s_end : m) : kend;
+      const int32_t rmax = (!trail && eager) ? s_end : m;
+      const int32_t lo = eager ? 0 : s_end;
+      const int g = warp & 3, h = warp >> 2;
+      const int rl = 32 * g + lane;
+      const int32_t r = i0 + rl;
+      float *ct = reinterpret_cast<float *>(raw);  // staged tile: [column][row], the TMA box layout
+      // this row's columns in range, as tile-local bounds [clo, chi)
+      const bool rin = r < rmax && r >= lo;
+      const int32_t chi_g = trail ? min(cmax, r + 1) : cmax;
+      const int clo = trail ? max(0, lo - j0) : 0;
+      const int chi = rin ? max(0, min(kT128, chi_g - j0)) : 0;
+      // the warp's 64 accumulator columns in four loads and one wait (each
+      // tensor-memory access queues behind MMAs of the SM's other CTA)
+      uint32_t v[4][16];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const uint32_t ta = tmem + (uint32_t(32 * g) << 16) + uint32_t(64 * h + 16 * x);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];\n"
+            : "=r"(v[x][0]), "=r"(v[x][1]), "=r"(v[x][2]), "=r"(v[x][3]), "=r"(v[x][4]), "=r"(v[x][5]),
+              "=r"(v[x][6]), "=r"(v[x][7]), "=r"(v[x][8]), "=r"(v[x][9]), "=r"(v[x][10]), "=r"(v[x][11]),
+              "=r"(v[x][12]), "=r"(v[x][13]), "=r"(v[x][14]), "=r"(v[x][15])
+            : "r"(ta));
+      }
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int32_t cc = c0 + e;
-        const bool in = r < rmax && cc < cmax && (!trail || r >= cc);
-        if (in) base[int64_t(cc) * ld] = old[e] - __uint_as_float(v[e]);
+      for (int x = 0; x < 4; ++x) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int cl = 64 * h + 16 * x + e;
+          ct[cl * kT128 + rl] = (cl >= clo && cl < chi) ? -__uint_as_float(v[x][e]) : 0.f;
+        }
       }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic-proxy stores -> TMA
     }
-  } else if (threadIdx.x == 0) {
+  }
+  if (!ok) s_abort = 1;
+  ok = __syncthreads_and(ok) != 0;
+  if (ok && threadIdx.x == 0) {
+    // F (or Y) += the staged tile: eight TMA reduce-add boxes, clipped to
+    // the front (entries outside the task's range add 0)
+    for (int b = 0; b < 8; ++b) tma_reduce_add_2d(mapC, i0, j0 + 16 * b, raw_u + uint32_t(b) * kT128 * 16 * 4);
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+  }
+  if (!ok && warp == 8 && lane == 0) {
     atomicOr(flags, FLAG_WAIT_TIMEOUT);
+    // let the copies and MMAs still in flight finish before the shared and
+    // tensor memory are given up (each wait bounded)
+    for (int q = max(0, issued - kUStages); q < issued; ++q)
+      mbar_wait(bar_full + 8 * (q % kUStages), uint32_t(q / kUStages) & 1u);
+    if (mma_issued > 0) mbar_wait(bar_mma + 8 * ((mma_issued - 1) & 1), uint32_t((mma_issued - 1) >> 1) & 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -860,17 +993,24 @@ __global__ void __launch_bounds__(256, 2) front_update_tc_kernel(const int32_t *
 // ticket per block) adds the partials in chunk order, so the result does not
 // depend on which CTA finishes last.  Returns true in that last CTA, whose
 // ticket is reset for the next application.
+// The fences are thread 0's alone, after a CTA barrier: the barrier orders
+// every thread's partial-sum stores before thread 0's GPU-scope fence, and
+// fences are cumulative in the PTX memory model, so the ticket's increment
+// releases the whole CTA's stores (the pattern of a grid-wide barrier), at
+// the cost of one fence instead of one per thread.
 __device__ __forceinline__ bool last_of_block(int *ticket, int nch) {
   __shared__ int s_last;
-  __threadfence();  // this thread's partials are visible device-wide ...
-  __syncthreads();  // ... for every thread of the CTA, before the ticket
+  __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const int t = atomicAdd(ticket, 1);
     s_last = (t == nch - 1);
-    if (s_last) *ticket = 0;
+    if (s_last) {
+      *ticket = 0;
+      __threadfence();  // acquire: the other CTAs' partials, read after the barrier below
+    }
   }
   __syncthreads();
-  if (s_last) __threadfence();
   return s_last;
 }
 
@@ -921,9 +1061,10 @@ __device__ __forceinline__ bool dep_wait(const int *p, int target, int *abort_wo
 // blocks with more than kFwdCols columns are split over tasks (slot >= 0)
 // and combined in chunk order by the last one (deterministic).
 constexpr int kPre = 4;  // gather sources prefetched per position
+constexpr int kFwdU = 8;  // columns per thread per load round
 
 template <typename TF, typename TV>
-__global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks, int64_t ntask,
+__global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ tasks, int64_t ntask,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
                                                   const double *__restrict__ Dinv,
                                                   const int32_t *__restrict__ perm,
@@ -979,15 +1120,15 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
     const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int32_t row = r0 + VW * rl;
     const TF *yc = Y + fr.y_off + row;
+    // warp g owns columns j0 + g + 8u; each round issues the loads of kFwdU
+    // columns before using any (kFwdU 16-byte loads in flight per thread;
+    // the first round's go out before the dependency wait)
     int32_t jq = j0 + g;
-    bool have = row < m && jq + 24 < j1;
-    V c0{}, c1{}, c2{}, c3{};
-    if (have) {
-      c0 = *reinterpret_cast<const V *>(yc + int64_t(jq) * fr.ldy);
-      c1 = *reinterpret_cast<const V *>(yc + int64_t(jq + 8) * fr.ldy);
-      c2 = *reinterpret_cast<const V *>(yc + int64_t(jq + 16) * fr.ldy);
-      c3 = *reinterpret_cast<const V *>(yc + int64_t(jq + 24) * fr.ldy);
-    }
+    const bool live = row < m;
+    V cv[kFwdU];
+#pragma unroll
+    for (int u = 0; u < kFwdU; ++u)
+      cv[u] = (live && jq + 8 * u < j1) ? *reinterpret_cast<const V *>(yc + int64_t(jq + 8 * u) * fr.ldy) : V{};
     // the children's update vectors must be complete
     if (threadIdx.x == 0) s_ok = dep_wait(pend + t.x, 0, ctl + 2, flags);
     __syncthreads();
@@ -1012,34 +1153,21 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
     TV acc[VW];
 #pragma unroll
     for (int e = 0; e < VW; ++e) acc[e] = TV(0);
-    if (!s_ok) have = false;
-    while (have) {
-      const int32_t jn = jq + 32;
-      const bool nhave = jn + 24 < j1;
-      V n0{}, n1{}, n2{}, n3{};
-      if (nhave) {
-        n0 = *reinterpret_cast<const V *>(yc + int64_t(jn) * fr.ldy);
-        n1 = *reinterpret_cast<const V *>(yc + int64_t(jn + 8) * fr.ldy);
-        n2 = *reinterpret_cast<const V *>(yc + int64_t(jn + 16) * fr.ldy);
-        n3 = *reinterpret_cast<const V *>(yc + int64_t(jn + 24) * fr.ldy);
-      }
-      const TV w0 = wp[jq - j0], w1 = wp[jq + 8 - j0], w2 = wp[jq + 16 - j0], w3 = wp[jq + 24 - j0];
+    if (s_ok && live) {
+      for (;;) {
+        TV wv[kFwdU];
 #pragma unroll
-      for (int e = 0; e < VW; ++e)
-        acc[e] += TV(vget(c0, e)) * w0 + TV(vget(c1, e)) * w1 + TV(vget(c2, e)) * w2 + TV(vget(c3, e)) * w3;
-      c0 = n0;
-      c1 = n1;
-      c2 = n2;
-      c3 = n3;
-      jq = jn;
-      have = nhave;
-    }
-    if (s_ok && row < m) {
-      for (; jq < j1; jq += 8) {
-        const V v0 = *reinterpret_cast<const V *>(yc + int64_t(jq) * fr.ldy);
-        const TV w0 = wp[jq - j0];
+        for (int u = 0; u < kFwdU; ++u) wv[u] = jq + 8 * u < j1 ? wp[jq + 8 * u - j0] : TV(0);
 #pragma unroll
-        for (int e = 0; e < VW; ++e) acc[e] += TV(vget(v0, e)) * w0;
+        for (int e = 0; e < VW; ++e) {
+#pragma unroll
+          for (int u = 0; u < kFwdU; ++u) acc[e] += TV(vget(cv[u], e)) * wv[u];
+        }
+        jq += 8 * kFwdU;
+        if (jq >= j1) break;
+#pragma unroll
+        for (int u = 0; u < kFwdU; ++u)
+          cv[u] = jq + 8 * u < j1 ? *reinterpret_cast<const V *>(yc + int64_t(jq + 8 * u) * fr.ldy) : V{};
       }
     }
 #pragma unroll
@@ -1088,10 +1216,11 @@ __global__ void __launch_bounds__(256) fwd_kernel(const int4 *__restrict__ tasks
           ubuf[fr.u_off + i - p] = csum + sums[k];
       }
     }
-    // completion: the front's last task releases the parent
-    __threadfence();
+    // completion: the front's last task releases the parent (one fence, by
+    // thread 0 after the barrier, as in last_of_block)
     __syncthreads();
     if (threadIdx.x == 0) {
+      __threadfence();
       const int c = atomicAdd(fdone + t.x, 1);
       if (c == fr.nfwd - 1 && fr.parent >= 0) {
         __threadfence();
@@ -1129,7 +1258,7 @@ __device__ __forceinline__ void xs_vec(const double *p, double (&x)[VW]) {
 // row-chunk order.  Also resets the forward counters for the next
 // application.
 template <typename TF, typename TV>
-__global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks, int64_t ntask,
+__global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ tasks, int64_t ntask,
                                                   const DFront *__restrict__ fronts, const TF *__restrict__ Y,
                                                   const int32_t *__restrict__ perm,
                                                   const int32_t *__restrict__ upd_rows_old,
@@ -1186,10 +1315,19 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
       const int32_t j = jc[k] < p ? jc[k] : c0;  // out-of-range columns read a valid one, result dropped
       yc[k] = Y + fr.y_off + int64_t(j) * fr.ldy;
     }
+    // each round loads two row blocks of the four columns (eight 16-byte
+    // loads in flight per thread) before using any; the first round's go
+    // out before the dependency wait
     const int32_t ist = xa + VW * lane;
-    V cv[4];
+    V cv[2][4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) cv[k] = ist < xb ? *reinterpret_cast<const V *>(yc[k] + ist) : V{};
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int32_t i = ist + 32 * VW * h;
+        cv[h][k] = i < xb ? *reinterpret_cast<const V *>(yc[k] + i) : V{};
+      }
+    }
     // the parent's solution entries must be complete
     if (threadIdx.x == 0)
       s_ok = fr.parent < 0 ? 1 : dep_wait(bdone + fr.parent, fronts[fr.parent].nbwd, ctl + 3, flags);
@@ -1202,22 +1340,30 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
     }
     __syncthreads();
     TV acc[4] = {TV(0), TV(0), TV(0), TV(0)};
-    for (int32_t off = 0; xa + off < xb; off += 32 * VW) {
-      const int32_t i = ist + off;
-      V nv[4];
+    for (int32_t off = 0;;) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) nv[k] = i + 32 * VW < xb ? *reinterpret_cast<const V *>(yc[k] + i + 32 * VW) : V{};
-      if (i < xb) {
-        TV xv[VW];
-        xs_vec<VW>(xs + (i - xa), xv);
+      for (int h = 0; h < 2; ++h) {
+        const int32_t i = ist + off + 32 * VW * h;
+        if (i < xb) {
+          TV xv[VW];
+          xs_vec<VW>(xs + (i - xa), xv);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+          for (int k = 0; k < 4; ++k) {
 #pragma unroll
-          for (int q = 0; q < VW; ++q) acc[k] += TV(vget(cv[k], q)) * xv[q];
+            for (int q = 0; q < VW; ++q) acc[k] += TV(vget(cv[h][k], q)) * xv[q];
+          }
         }
       }
+      off += 64 * VW;
+      if (xa + off >= xb) break;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) cv[k] = nv[k];
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int32_t i = ist + off + 32 * VW * h;
+          cv[h][k] = i < xb ? *reinterpret_cast<const V *>(yc[k] + i) : V{};
+        }
+      }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -1245,9 +1391,11 @@ __global__ void __launch_bounds__(256) bwd_kernel(const int4 *__restrict__ tasks
         if (j < p) z[perm[fr.first + j]] = sm;
       }
     }
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(bdone + t.x, 1);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(bdone + t.x, 1);
+    }
   }
 }
 
@@ -1257,6 +1405,10 @@ template <typename TF>
 static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cudaStream_t s) {
   TF *F = reinterpret_cast<TF *>(d->F);
   TF *Y = reinterpret_cast<TF *>(d->Y[buf]);
+  const int64_t nf = int64_t(c->fronts.size());
+  const CUtensorMap *fmaps = reinterpret_cast<const CUtensorMap *>(d->tmaps);
+  const CUtensorMap *ymaps = fmaps ? fmaps + (1 + buf) * nf : nullptr;
+  const CUtensorMap *ycmaps = fmaps ? fmaps + (3 + buf) * nf : nullptr;
   const size_t tsm = 2 * 64 * 65 * sizeof(TF);
   const size_t dsm = 64 * sizeof(double) + 2 * 64 * 65 * sizeof(TF);
   cudaFuncSetAttribute(front_diag_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dsm));
@@ -1283,11 +1435,11 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
         if (ev >= 0) d->update_flops += L.trail_flops[st];
         if constexpr (sizeof(TF) == 4)
           if (c->opt.factor_tf32)
-            launch_pdl(front_update_tc_kernel<1>, unsigned(L.trail_n[st]), 256, update_smem<1>(), s,
-                       d->tasks + L.trail_off[st], d->fronts, F, Y, d->D[buf], d->flags);
+            launch_pdl(front_update_tc_kernel<1>, unsigned(L.trail_n[st]), kUThreads, update_smem<1>(), s,
+                       d->tasks + L.trail_off[st], d->fronts, F, Y, d->D[buf], fmaps, ymaps, ycmaps, d->flags);
           else
-            launch_pdl(front_update_tc_kernel<3>, unsigned(L.trail_n[st]), 256, update_smem<3>(), s,
-                       d->tasks + L.trail_off[st], d->fronts, F, Y, d->D[buf], d->flags);
+            launch_pdl(front_update_tc_kernel<3>, unsigned(L.trail_n[st]), kUThreads, update_smem<3>(), s,
+                       d->tasks + L.trail_off[st], d->fronts, F, Y, d->D[buf], fmaps, ymaps, ycmaps, d->flags);
         else
           launch_pdl(front_update_kernel<TF>, unsigned(L.trail_n[st]), 256, tsm, s, d->tasks + L.trail_off[st],
                      d->fronts, F, Y, d->D[buf]);

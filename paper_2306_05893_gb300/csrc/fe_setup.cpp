@@ -420,7 +420,8 @@ int build_ordering(fe_ctx *c) {
     F.level = lv;
     int64_t m = F.m();
     F.ldy = int32_t((m + 7) / 8 * 8);  // 16-byte vectors of binary16 entries stay aligned
-    F.f_off = f_total; f_total += m * m;
+    F.ldf = int32_t((m + 3) / 4 * 4);
+    F.f_off = f_total; f_total += int64_t(F.ldf) * m;
     F.y_off = y_total; y_total += int64_t(F.ldy) * F.npiv;
     F.w_off = w_total; w_total += m;
     F.u_off = u_total; u_total += F.nupd;
@@ -491,7 +492,6 @@ int build_ordering(fe_ctx *c) {
   c->fa_colptr.clear();
   for (int64_t f = 0; f < nf; ++f) {
     const Front &F = c->fronts[f];
-    const int32_t m = F.m();
     const int32_t *prow = &c->upd_rows_new[F.rows_off];
     c->fa_ptr[f] = int64_t(c->fa_slot.size());
     for (int32_t jl = 0; jl < F.npiv; ++jl) {
@@ -510,7 +510,7 @@ int build_ordering(fe_ctx *c) {
           lr = F.npiv + int32_t(it - prow);
         }
         c->fa_slot.push_back(k);
-        c->fa_off.push_back(lr + jl * m);
+        c->fa_off.push_back(lr + jl * F.ldf);
       }
     }
     c->fa_colptr.push_back(int64_t(c->fa_slot.size()));
@@ -598,9 +598,13 @@ int build_ordering(fe_ctx *c) {
           const int32_t chunks = (s1 - s0 + kNB - 1) / kNB;
           const int32_t code = ((T_TRAIL | ((chunks - 1) << 3)) << 24) | s0;
           const int32_t codeu = ((T_RUPD | ((chunks - 1) << 3)) << 24) | s0;
-          for (int32_t j0 = s1; j0 < m; j0 += ut)
+          // FP32 path: tiles start at a multiple of 4 rows (a TMA box must
+          // start 16-byte aligned); the rows and columns of the tile below
+          // s1 belong to the superpanel and are left alone by the kernel
+          const int32_t t1 = c->opt.precision == FE_MIXED ? (s1 & ~3) : s1;
+          for (int32_t j0 = t1; j0 < m; j0 += ut)
             for (int32_t i0 = j0; i0 < m; i0 += ut) push(L.trail[s], f, code, i0, j0);
-          for (int32_t i0 = s1; i0 < m; i0 += ut)
+          for (int32_t i0 = t1; i0 < m; i0 += ut)
             for (int32_t c0 = 0; c0 < s1; c0 += ut) push(L.trail[s], f, codeu, i0, c0);
         }
         // algorithmic flops of this panel's updates (the zero products of the
