@@ -61,7 +61,9 @@ MATERIAL_NAMES = {0: "Saint Venant-Kirchhoff", 1: "neo-Hookean", 2: "Mooney-Rivl
 # capture of dram__bytes_read.sum + dram__bytes_write.sum over the 194 update
 # launches of a factorisation, divided by 194.  To be retaken (or dropped)
 # whenever the kernel changes; other workloads report None.
-UPDATE_TRAFFIC = {"tet30x30x120-mr": 188.74e6}
+UPDATE_TRAFFIC = {"tet30x30x120-mr": 202.4e6}
+# DRAM bytes of one application (forward + backward) with the binary16 Y
+APPLY_TRAFFIC = {"tet30x30x120-mr": 1.927e9}
 
 
 class ClockSampler:
@@ -424,7 +426,8 @@ def main():
     achieved = bytes_apply / (apply_ms / 1e3) / 1e9 if apply_ms > 0 else None
     roofline_apply = {"bound": "hbm", "kernel": "precond apply (fwd_kernel + bwd_kernel per level)",
                       "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                      "frac": achieved / hbm if achieved else None, "traffic": None,
+                      "frac": achieved / hbm if achieved else None,
+                      "traffic": APPLY_TRAFFIC.get(args.workload) if (wl.precision and args.precond_fp16) else None,
                       "bytes_per_launch": bytes_apply, "avg_ms": apply_ms}
     spmv_calls = max(1, stage_calls["spmv"])
     spmv_ms = stage_ms["spmv"] / spmv_calls
