@@ -19,6 +19,10 @@ constexpr int kBwdRows = 1024; // rows per task of the backward apply (split ove
 // rows of Y per 16-byte vector: 8 binary16, 4 FP32, 2 FP64 entries
 inline int y_vec(const fe_options &o) { return o.precision == FE_MIXED ? (o.precond_fp16 ? 8 : 4) : 2; }
 inline int fwd_rows(const fe_options &o) { return 32 * y_vec(o); }  // 32 threads x one 16-byte vector
+// rows per backward task: twice as many for the binary16 Y, so a task moves the
+// same bytes (its fixed costs, the dependency wait, staging x and publishing,
+// are then spread over as much data as in the FP32 path)
+inline int bwd_rows(const fe_options &o) { return o.precision == FE_MIXED && o.precond_fp16 ? 2 * kBwdRows : kBwdRows; }
 
 // Task kinds of the multifrontal factorisation (packed in int4.y >> 24).
 enum TaskKind { T_DIAG = 0, T_PANEL = 1, T_XK = 2, T_TRAIL = 3, T_RUPD = 4 };

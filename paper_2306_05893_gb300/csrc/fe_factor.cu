@@ -647,10 +647,14 @@ constexpr int kUmmaSbo = 128;                        // M/N-direction (8-row gro
 // per CTA).  The staged output tile of the epilogue (64 KB) reuses the front.
 template <int NMMA>
 __host__ __device__ constexpr int update_nop() { return NMMA == 3 ? 4 : 2; }
-constexpr int kUDqOff(int nop) { return kUStages * 2 * kUOpBytes + 2 * nop * kUOpBytes; }
+// operand stages: two for 3xTF32 (4 operands of 8 KB each), four for TF32
+// (2 operands each) in the same space, so the plain-TF32 pipeline runs deeper
+template <int NMMA>
+__host__ __device__ constexpr int update_nops() { return NMMA == 3 ? 2 : 4; }
+constexpr int kUDqOff(int nop, int nops) { return kUStages * 2 * kUOpBytes + nops * nop * kUOpBytes; }
 template <int NMMA>
 constexpr size_t update_smem() {
-  return size_t(kUDqOff(update_nop<NMMA>())) + kUStages * kUK * 4 + 128;
+  return size_t(kUDqOff(update_nop<NMMA>(), update_nops<NMMA>())) + kUStages * kUK * 4 + 128;
 }
 static_assert(kUStages * 2 * kUOpBytes + 2 * 2 * kUOpBytes >= kT128 * kT128 * 4, "the output tile fits the operand space");
 constexpr uint64_t kWaitLimitNs = 1000000000ull;     // give up an mbarrier wait after 1 s
@@ -736,13 +740,14 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
     const CUtensorMap *__restrict__ ymaps, const CUtensorMap *__restrict__ ycmaps, int *flags) {
   static_assert(NMMA == 1 || NMMA == 3, "3xTF32 or TF32");
   constexpr int NOP = update_nop<NMMA>();
+  constexpr int NOS = update_nops<NMMA>();  // operand stages
   constexpr int OPF = kUOpBytes / 4;  // floats per operand chunk
   extern __shared__ __align__(1024) unsigned char usm[];
   unsigned char *raw = usm;                                            // kUStages x (A, B)
   unsigned char *opnd = usm + kUStages * 2 * kUOpBytes;                // 2 x NOP operands
-  float *Dq = reinterpret_cast<float *>(usm + kUDqOff(NOP));           // d_l of each raw stage
+  float *Dq = reinterpret_cast<float *>(usm + kUDqOff(NOP, NOS));      // d_l of each raw stage
   uint64_t *bars = reinterpret_cast<uint64_t *>(Dq + kUStages * kUK);  // full[3], ready[2], mma[2]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kUStages + 4);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kUStages + 2 * NOS);
   int &s_abort = *reinterpret_cast<int *>(tmem_slot + 1);  // (dynamic: no static shared memory)
   const volatile int *abort_word = &s_abort;
   pdl_launch_dependents();
@@ -762,14 +767,14 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nq = (kw + kUK - 1) / kUK;
   const uint32_t bar_full = smem_u32(bars), bar_ready = bar_full + 8 * kUStages;
-  const uint32_t bar_mma = bar_ready + 16;
+  const uint32_t bar_mma = bar_ready + 8 * NOS;
   const uint32_t raw_u = smem_u32(raw), op_u = smem_u32(opnd);
   pdl_wait();
   if (threadIdx.x == 0) {
     s_abort = 0;
     for (int b = 0; b < kUStages; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_full + 8 * b) : "memory");
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NOS; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(bar_ready + 8 * b) : "memory");  // 8 warps
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_mma + 8 * b) : "memory");
     }
@@ -817,8 +822,8 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
     };
     for (; issued < min(kUStages, nq); ++issued) produce(issued);
     for (int q = 0; q < nq && ok; ++q) {
-      const int o = q & 1;
-      if (lane == 0) ok = mbar_wait(bar_ready + 8 * o, uint32_t(q >> 1) & 1u, abort_word);
+      const int o = q % NOS;
+      if (lane == 0) ok = mbar_wait(bar_ready + 8 * o, uint32_t(q / NOS) & 1u, abort_word);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       if (!ok) break;
       if (lane == 0) {
@@ -865,10 +870,10 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
     // ------------------------------------------------------- converters
     const int row = threadIdx.x & 127, gb = threadIdx.x >> 7;  // K groups gb and gb + 2
     for (int q = 0; q < nq && ok; ++q) {
-      const int s = q % kUStages, o = q & 1;
+      const int s = q % kUStages, o = q % NOS;
       ok = mbar_wait(bar_full + 8 * s, uint32_t(q / kUStages) & 1u, abort_word);
-      // the MMAs of chunk q - 2 have read operand stage o
-      if (ok && q >= 2) ok = mbar_wait(bar_mma + 8 * o, uint32_t((q - 2) >> 1) & 1u, abort_word);
+      // the MMAs of chunk q - NOS have read operand stage o
+      if (ok && q >= NOS) ok = mbar_wait(bar_mma + 8 * o, uint32_t((q - NOS) / NOS) & 1u, abort_word);
       if (!ok) break;
       const float *rA = reinterpret_cast<const float *>(raw + s * 2 * kUOpBytes);
       const float *rB = rA + OPF;
@@ -917,7 +922,7 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
     }
     // the accumulator is complete (and every operand read: the shared
     // memory is free for the staged tile)
-    if (ok && nq > 0) ok = mbar_wait(bar_mma + 8 * ((nq - 1) & 1), uint32_t((nq - 1) >> 1) & 1u, abort_word);
+    if (ok && nq > 0) ok = mbar_wait(bar_mma + 8 * ((nq - 1) % NOS), uint32_t((nq - 1) / NOS) & 1u, abort_word);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (ok) {
       // TRAIL writes the lower part of columns < cmax (the superpanel's end
@@ -978,7 +983,7 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
     // tensor memory are given up (each wait bounded)
     for (int q = max(0, issued - kUStages); q < issued; ++q)
       mbar_wait(bar_full + 8 * (q % kUStages), uint32_t(q / kUStages) & 1u);
-    if (mma_issued > 0) mbar_wait(bar_mma + 8 * ((mma_issued - 1) & 1), uint32_t((mma_issued - 1) >> 1) & 1u);
+    if (mma_issued > 0) mbar_wait(bar_mma + 8 * ((mma_issued - 1) % NOS), uint32_t((mma_issued - 1) / NOS) & 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -1249,12 +1254,13 @@ __device__ __forceinline__ void xs_vec(const double *p, double (&x)[VW]) {
 }
 
 // Backward task (front, c0, i0, slot): pivot columns [c0, c0 + 32) over the
-// rows [i0, i0 + kBwdRows); warp w owns columns c0 + w + 8k (k < 4) and
-// streams them together, the next four 16-byte loads per lane in flight.
+// rows [i0, i0 + BR) (BR = kBwdRows, twice that for the binary16 Y); warp w
+// owns columns c0 + w + 8k (k < 4) and streams them together, eight 16-byte
+// loads per lane in flight.
 // x = [D^{-1} y_P; z_U] is staged in shared memory from the VW-aligned row at
 // or below c0 (rows above a column are zeros of L^{-1}, so reading from the
 // aligned row is exact); z_U was written by the parent's tasks.  Columns
-// longer than kBwdRows rows are split over tasks (slot >= 0) and combined in
+// longer than BR rows are split over tasks (slot >= 0) and combined in
 // row-chunk order.  Also resets the forward counters for the next
 // application.
 template <typename TF, typename TV>
@@ -1268,8 +1274,9 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
                                                   int *flags, const double *__restrict__ done) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
-  constexpr int XS = kBwdRows / 256;  // staged rows per thread
-  __shared__ __align__(16) TV xs[kBwdRows];
+  constexpr int BR = sizeof(TF) == 2 ? 2 * kBwdRows : kBwdRows;  // rows per task
+  constexpr int XS = BR / 256;                                   // staged rows per thread
+  __shared__ __align__(16) TV xs[BR];
   __shared__ int s_task, s_ok;
   if (done && *done != 0.0) return;
   for (int i = blockIdx.x * 256 + threadIdx.x; i < nfronts; i += gridDim.x * 256) {
@@ -1291,7 +1298,7 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
     const int32_t p = fr.npiv, m = fr.m;
     const int32_t a0 = c0 & ~(VW - 1);
     const int32_t xa = a0 > ilo0 ? a0 : ilo0;                                 // first row of this task
-    const int32_t xb = (ilo0 + kBwdRows < fr.ldy) ? ilo0 + kBwdRows : fr.ldy;  // end row
+    const int32_t xb = (ilo0 + BR < fr.ldy) ? ilo0 + BR : fr.ldy;  // end row
     // static: where each staged row comes from (-1: zero, >= 0: yperm index,
     // <= -2: z index -2 - idx)
     const int32_t *urows = upd_rows_old + fr.rows_off;
@@ -1377,12 +1384,12 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
           if (jc[k] < p) z[perm[fr.first + jc[k]]] = acc[k];
       }
     } else {
-      const int32_t k_first = a0 / kBwdRows;
-      const int nch = (fr.ldy - 1) / kBwdRows - k_first + 1;
+      const int32_t k_first = a0 / BR;
+      const int nch = (fr.ldy - 1) / BR - k_first + 1;
       if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          part[int64_t(slot + ilo0 / kBwdRows - k_first) * kBwdCols + w + 8 * k] = acc[k];
+          part[int64_t(slot + ilo0 / BR - k_first) * kBwdCols + w + 8 * k] = acc[k];
       }
       if (last_of_block(tickets + slot, nch) && threadIdx.x < kBwdCols) {
         TV sm = TV(0);

@@ -540,6 +540,7 @@ int build_ordering(fe_ctx *c) {
   const int32_t sp = c->opt.precision == FE_MIXED ? kSuper : kNB;
   const int32_t fr_rows = fwd_rows(c->opt);
   const int32_t vw = y_vec(c->opt);  // rows per 16-byte vector of Y
+  const int32_t br = bwd_rows(c->opt);
   c->fwd_slots = c->bwd_slots = 0;
   for (auto &L : c->levels) {
     int steps = 0;
@@ -571,12 +572,12 @@ int build_ordering(fe_ctx *c) {
       }
       for (int32_t c0 = 0; c0 < p; c0 += kBwdCols) {
         const int32_t a0 = c0 & ~(vw - 1);
-        const int32_t k0 = a0 / kBwdRows, k1 = (F.ldy - 1) / kBwdRows;
+        const int32_t k0 = a0 / br, k1 = (F.ldy - 1) / br;
         const int32_t slot = k1 > k0 ? int32_t(c->bwd_slots) : -1;
         if (k1 > k0) c->bwd_slots += k1 - k0 + 1;
         for (int32_t k = k0; k <= k1; ++k) {
           L.bwd_tasks.push_back(f); L.bwd_tasks.push_back(c0);
-          L.bwd_tasks.push_back(k * kBwdRows); L.bwd_tasks.push_back(slot);
+          L.bwd_tasks.push_back(k * br); L.bwd_tasks.push_back(slot);
         }
       }
       for (int s = 0; s * kNB < p; ++s) {
