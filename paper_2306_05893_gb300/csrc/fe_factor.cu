@@ -998,22 +998,28 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
 // ticket per block) adds the partials in chunk order, so the result does not
 // depend on which CTA finishes last.  Returns true in that last CTA, whose
 // ticket is reset for the next application.
-// The fences are thread 0's alone, after a CTA barrier: the barrier orders
-// every thread's partial-sum stores before thread 0's GPU-scope fence, and
-// fences are cumulative in the PTX memory model, so the ticket's increment
-// releases the whole CTA's stores (the pattern of a grid-wide barrier), at
-// the cost of one fence instead of one per thread.
+// The ordering is thread 0's alone, after a CTA barrier: the barrier orders
+// every thread's partial-sum stores before thread 0's GPU-scope
+// acquire-release increment of the ticket, and release is cumulative in the
+// PTX memory model, so the increment releases the whole CTA's stores and, in
+// the last CTA, acquires the other CTAs' (the pattern of a grid-wide
+// barrier), with one ordered atomic instead of a fence per thread.
+__device__ __forceinline__ int atom_add_acq_rel(int *p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.add.s32 %0, [%1], %2;\n" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release(int *p, int v) {
+  asm volatile("red.release.gpu.add.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool last_of_block(int *ticket, int nch) {
   __shared__ int s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    const int t = atomicAdd(ticket, 1);
+    const int t = atom_add_acq_rel(ticket, 1);
     s_last = (t == nch - 1);
-    if (s_last) {
-      *ticket = 0;
-      __threadfence();  // acquire: the other CTAs' partials, read after the barrier below
-    }
+    if (s_last) *ticket = 0;
   }
   __syncthreads();
   return s_last;
@@ -1066,6 +1072,32 @@ __device__ __forceinline__ bool dep_wait(const int *p, int target, int *abort_wo
 // blocks with more than kFwdCols columns are split over tasks (slot >= 0)
 // and combined in chunk order by the last one (deterministic).
 constexpr int kPre = 4;  // gather sources prefetched per position
+
+// One task of look-ahead in the persistent apply kernels: a CTA takes the
+// index of its next task while it starts the current one, and lanes 0-5 of
+// warp 0 load that task's descriptor (its int4 and the 96-byte DFront of its
+// front) while the current task finishes, so the next task starts from
+// shared memory instead of three dependent global round trips.  (Taking a
+// task early cannot deadlock: tasks are handed out in topological order, so
+// the lowest unfinished task is always a CTA's current task, and its
+// dependencies are finished.)
+static_assert(sizeof(DFront) == 96, "the descriptor is copied as six 16-byte pieces");
+struct NextDesc {
+  int4 t, f;
+};
+__device__ __forceinline__ NextDesc load_desc(const int4 *__restrict__ tasks, const DFront *__restrict__ fronts,
+                                              int64_t tn, int64_t ntask, int lane) {
+  NextDesc d{};
+  if (tn < ntask && lane < 6) {
+    d.t = tasks[tn];
+    d.f = reinterpret_cast<const int4 *>(fronts + d.t.x)[lane];
+  }
+  return d;
+}
+__device__ __forceinline__ void store_desc(const NextDesc &d, int4 &s_t, DFront &s_fr, int lane) {
+  if (lane < 6) reinterpret_cast<int4 *>(&s_fr)[lane] = d.f;
+  if (lane == 0) s_t = d.t;
+}
 constexpr int kFwdU = 8;  // columns per thread per load round
 
 template <typename TF, typename TV>
@@ -1085,7 +1117,9 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
   constexpr int RB = 32 * VW;
   __shared__ TV gpart[8 * RB];
   __shared__ TV wp[kFwdCols];
-  __shared__ int s_task, s_ok;
+  __shared__ int s_task, s_next, s_ok;
+  __shared__ int4 s_t;
+  __shared__ __align__(16) DFront s_fr;
   if (done && *done != 0.0) return;
   // leave the backward counters reset for the backward launch that follows
   for (int i = blockIdx.x * 256 + threadIdx.x; i < nfronts; i += gridDim.x * 256) bdone[i] = 0;
@@ -1093,13 +1127,16 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     ctl[1] = 0;
     ctl[3] = 0;
   }
+  if (threadIdx.x == 0) s_task = atomicAdd(ctl + 0, 1);
+  __syncthreads();
+  if (threadIdx.x < 32) store_desc(load_desc(tasks, fronts, s_task, ntask, threadIdx.x), s_t, s_fr, threadIdx.x);
   for (;;) {
-    if (threadIdx.x == 0) s_task = atomicAdd(ctl + 0, 1);
-    __syncthreads();
+    __syncthreads();  // this task's index and descriptor
     const int64_t ti = s_task;
     if (ti >= ntask) break;
-    const int4 t = tasks[ti];
-    const DFront fr = fronts[t.x];
+    const int4 t = s_t;
+    const DFront fr = s_fr;
+    if (threadIdx.x == 0) s_next = atomicAdd(ctl + 0, 1);  // the next task, one ahead
     const int32_t r0 = t.y, j0 = t.z, slot = t.w;
     const int32_t p = fr.npiv, m = fr.m;
     const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
@@ -1175,6 +1212,8 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
           cv[u] = jq + 8 * u < j1 ? *reinterpret_cast<const V *>(yc + int64_t(jq + 8 * u) * fr.ldy) : V{};
       }
     }
+    NextDesc nd{};
+    if (threadIdx.x < 32) nd = load_desc(tasks, fronts, s_next, ntask, threadIdx.x);
 #pragma unroll
     for (int e = 0; e < VW; ++e) gpart[g * RB + VW * rl + e] = acc[e];
     __syncthreads();
@@ -1221,17 +1260,17 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
           ubuf[fr.u_off + i - p] = csum + sums[k];
       }
     }
-    // completion: the front's last task releases the parent (one fence, by
-    // thread 0 after the barrier, as in last_of_block)
+    // completion: the front's last task releases the parent (ordered
+    // atomics by thread 0 after the barrier, as in last_of_block; the last
+    // task's acquire on fdone carries the front's other tasks' stores into
+    // its release of the parent's counter)
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();
-      const int c = atomicAdd(fdone + t.x, 1);
-      if (c == fr.nfwd - 1 && fr.parent >= 0) {
-        __threadfence();
-        atomicSub(pend + fr.parent, 1);
-      }
+      const int c = atom_add_acq_rel(fdone + t.x, 1);
+      if (c == fr.nfwd - 1 && fr.parent >= 0) red_add_release(pend + fr.parent, -1);
+      s_task = s_next;
     }
+    if (threadIdx.x < 32) store_desc(nd, s_t, s_fr, threadIdx.x);
   }
 }
 
@@ -1277,7 +1316,9 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
   constexpr int BR = sizeof(TF) == 2 ? 2 * kBwdRows : kBwdRows;  // rows per task
   constexpr int XS = BR / 256;                                   // staged rows per thread
   __shared__ __align__(16) TV xs[BR];
-  __shared__ int s_task, s_ok;
+  __shared__ int s_task, s_next, s_ok;
+  __shared__ int4 s_t;
+  __shared__ __align__(16) DFront s_fr;
   if (done && *done != 0.0) return;
   for (int i = blockIdx.x * 256 + threadIdx.x; i < nfronts; i += gridDim.x * 256) {
     pend[i] = fronts[i].child_end - fronts[i].child_begin;
@@ -1287,13 +1328,16 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
     ctl[0] = 0;
     ctl[2] = 0;
   }
+  if (threadIdx.x == 0) s_task = atomicAdd(ctl + 1, 1);
+  __syncthreads();
+  if (threadIdx.x < 32) store_desc(load_desc(tasks, fronts, s_task, ntask, threadIdx.x), s_t, s_fr, threadIdx.x);
   for (;;) {
-    if (threadIdx.x == 0) s_task = atomicAdd(ctl + 1, 1);
-    __syncthreads();
+    __syncthreads();  // this task's index and descriptor
     const int64_t ti = s_task;
     if (ti >= ntask) break;
-    const int4 t = tasks[ti];
-    const DFront fr = fronts[t.x];
+    const int4 t = s_t;
+    const DFront fr = s_fr;
+    if (threadIdx.x == 0) s_next = atomicAdd(ctl + 1, 1);  // the next task, one ahead
     const int32_t c0 = t.y, ilo0 = t.z, slot = t.w;
     const int32_t p = fr.npiv, m = fr.m;
     const int32_t a0 = c0 & ~(VW - 1);
@@ -1372,6 +1416,8 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
         }
       }
     }
+    NextDesc nd{};
+    if (threadIdx.x < 32) nd = load_desc(tasks, fronts, s_next, ntask, threadIdx.x);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
 #pragma unroll
@@ -1400,9 +1446,10 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(bdone + t.x, 1);
+      red_add_release(bdone + t.x, 1);
+      s_task = s_next;
     }
+    if (threadIdx.x < 32) store_desc(nd, s_t, s_fr, threadIdx.x);
   }
 }
 
