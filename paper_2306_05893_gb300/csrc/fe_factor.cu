@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
 // Blackwell tensor cores (tcgen05, kind::tf32) with a 3xTF32 split
 // (a = a_hi + a_lo, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) so products keep
 // ~FP32 accuracy, fed by the TMA unit, with warp-specialised roles:
-//  * warp 8 (producer and MMA issuer) keeps a ring of kUStages raw K chunks
+//  * warp 8 (producer and MMA issuer) keeps a ring of 5-6 raw K chunks
 //    (16 columns each) in flight: per chunk one tensor-map load of the
 //    128 x 16 A tile (F rows i0.., columns k..k + 16, rows contiguous) and
 //    either the 128 x 16 B tile of F (TRAIL) or four 4 x 128 boxes of Y
@@ -636,9 +636,8 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
 // flight, frees its tensor memory and returns.
 constexpr int kT128 = 128;
 constexpr int kUK = 16;                              // K columns per chunk
-constexpr int kUStages = 3;                          // raw chunks in flight (TMA ring)
 constexpr int kUOpBytes = kT128 * kUK * 4;           // one operand of one chunk: 8 KB
-constexpr int kUThreads = 288;                       // 8 converter/epilogue warps + 1 producer/MMA warp
+constexpr int kUThreads = 320;  // 8 converter/epilogue warps, 1 MMA-issuer warp, 1 TMA-producer warp
 constexpr int kUmmaLbo = 2048;                       // K-direction core-matrix stride
 constexpr int kUmmaSbo = 128;                        // M/N-direction (8-row group) stride
 // raw ring (A and B per stage) + two operand stages (hi and lo parts of A
@@ -646,17 +645,22 @@ constexpr int kUmmaSbo = 128;                        // M/N-direction (8-row gro
 // 112.3 KB for 3xTF32, so that two CTAs fit on an SM (228 KB, 1 KB reserved
 // per CTA).  The staged output tile of the epilogue (64 KB) reuses the front.
 template <int NMMA>
-__host__ __device__ constexpr int update_nop() { return NMMA == 3 ? 4 : 2; }
-// operand stages: two for 3xTF32 (4 operands of 8 KB each), four for TF32
-// (2 operands each) in the same space, so the plain-TF32 pipeline runs deeper
+__host__ __device__ constexpr int update_nop() { return NMMA == 3 ? 2 : 1; }  // B operands in shared memory
+// operand stages (the A parts of a stage live in tensor memory) and raw
+// stages (the TMA ring): with A out of shared memory the space goes to raw
+// chunks in flight, which hide the TMA latency under load (≈ 2-3 µs)
 template <int NMMA>
-__host__ __device__ constexpr int update_nops() { return NMMA == 3 ? 2 : 4; }
-constexpr int kUDqOff(int nop, int nops) { return kUStages * 2 * kUOpBytes + nops * nop * kUOpBytes; }
+__host__ __device__ constexpr int update_nops() { return 2; }
+template <int NMMA>
+__host__ __device__ constexpr int update_nrs() { return NMMA == 3 ? 5 : 6; }
+constexpr int kUTmemCols = 256;  // accumulator [0, 128) + A of 4 stages (hi, lo: 16 columns each)
+constexpr int kUDqOff(int nrs, int nop, int nops) { return nrs * 2 * kUOpBytes + nops * nop * kUOpBytes; }
 template <int NMMA>
 constexpr size_t update_smem() {
-  return size_t(kUDqOff(update_nop<NMMA>(), update_nops<NMMA>())) + kUStages * kUK * 4 + 128;
+  return size_t(kUDqOff(update_nrs<NMMA>(), update_nop<NMMA>(), update_nops<NMMA>())) + update_nrs<NMMA>() * kUK * 4 +
+         256;
 }
-static_assert(kUStages * 2 * kUOpBytes + 2 * 2 * kUOpBytes >= kT128 * kT128 * 4, "the output tile fits the operand space");
+static_assert(5 * 2 * kUOpBytes >= kT128 * kT128 * 4, "the output tile fits the raw ring");
 constexpr uint64_t kWaitLimitNs = 1000000000ull;     // give up an mbarrier wait after 1 s
 
 // tcgen05 instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B
@@ -730,6 +734,17 @@ __device__ __forceinline__ void tma_reduce_add_2d(const void *map, int32_t x, in
                : "memory");
 }
 
+// 16 consecutive 32-bit tensor-memory columns of the calling thread's lane
+// (warp w writes lanes 32 (w % 4) ..), from registers
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
 // NMMA = 3: the 3xTF32 split (FP32-accurate products); NMMA = 1: one TF32
 // MMA per product (operands rounded to TF32, ~1e-3 relative; the factor is
 // only a preconditioner and the solve is refined in FP64).
@@ -743,11 +758,12 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
   constexpr int NOS = update_nops<NMMA>();  // operand stages
   constexpr int OPF = kUOpBytes / 4;  // floats per operand chunk
   extern __shared__ __align__(1024) unsigned char usm[];
-  unsigned char *raw = usm;                                            // kUStages x (A, B)
-  unsigned char *opnd = usm + kUStages * 2 * kUOpBytes;                // 2 x NOP operands
-  float *Dq = reinterpret_cast<float *>(usm + kUDqOff(NOP, NOS));      // d_l of each raw stage
-  uint64_t *bars = reinterpret_cast<uint64_t *>(Dq + kUStages * kUK);  // full[3], ready[2], mma[2]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kUStages + 2 * NOS);
+  constexpr int NRS = update_nrs<NMMA>();  // raw stages
+  unsigned char *raw = usm;                                            // NRS x (A, B)
+  unsigned char *opnd = usm + NRS * 2 * kUOpBytes;                     // NOS x NOP operands
+  float *Dq = reinterpret_cast<float *>(usm + kUDqOff(NRS, NOP, NOS));  // d_l of each raw stage
+  uint64_t *bars = reinterpret_cast<uint64_t *>(Dq + NRS * kUK);  // full[NRS], empty[NRS], ready[NOS], mma[NOS]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NRS + 2 * NOS);
   int &s_abort = *reinterpret_cast<int *>(tmem_slot + 1);  // (dynamic: no static shared memory)
   const volatile int *abort_word = &s_abort;
   pdl_launch_dependents();
@@ -766,14 +782,16 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
   const CUtensorMap *mapC = trail ? fmaps + t.x : ycmaps + t.x;  // the output tile (F or all rows of Y)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nq = (kw + kUK - 1) / kUK;
-  const uint32_t bar_full = smem_u32(bars), bar_ready = bar_full + 8 * kUStages;
+  const uint32_t bar_full = smem_u32(bars), bar_empty = bar_full + 8 * NRS, bar_ready = bar_empty + 8 * NRS;
   const uint32_t bar_mma = bar_ready + 8 * NOS;
   const uint32_t raw_u = smem_u32(raw), op_u = smem_u32(opnd);
   pdl_wait();
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int b = 0; b < kUStages; ++b)
+    for (int b = 0; b < NRS; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_full + 8 * b) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(bar_empty + 8 * b) : "memory");  // 8 warps
+    }
     for (int b = 0; b < NOS; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(bar_ready + 8 * b) : "memory");  // 8 warps
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_mma + 8 * b) : "memory");
@@ -782,7 +800,7 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kT128)
+                 "r"(kUTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
@@ -791,19 +809,30 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
-  int issued = 0, mma_issued = 0;  // warp 8's view
+  int issued = 0, mma_issued = 0;  // warp 9 (copies issued) and warp 8 (MMA chunks issued)
 
-  if (warp == 8) {
-    // ------------------------------------------------ producer / MMA issuer
-    // raw chunk q into stage q % kUStages: d_l first (lanes 0-15), then the
-    // expected bytes and the TMA loads (lane 0)
-    // (the stage's mbarrier completes once the loads have landed and lane 0
-    // has arrived, after d_l is stored)
-    auto produce = [&](int q) {
-      const int s = q % kUStages;
+  if (warp == 9) {
+    // ------------------------------------------------------------ producer
+    // raw chunk q into stage q % NRS once the converters have released the
+    // stage (its previous chunk): d_l (lanes 0-15, loaded one chunk ahead),
+    // then the expected bytes and the TMA loads (lane 0); the stage's
+    // mbarrier completes once the loads have landed and lane 0 has arrived
+    auto load_d = [&](int q) {
+      const int32_t kq = k0 + kUK * q;
+      return (q < nq && lane < kUK && trail && kq + lane < kend) ? float(D[fr.first + kq + lane]) : 0.f;
+    };
+    float dv_next = load_d(0);
+    for (int q = 0; q < nq && ok; ++q) {
+      const int s = q % NRS;
       const int32_t kq = k0 + kUK * q;
       const uint32_t bar = bar_full + 8 * s;
-      const float dv = (lane < kUK && trail && kq + lane < kend) ? float(D[fr.first + kq + lane]) : 0.f;
+      if (q >= NRS) {
+        if (lane == 0) ok = mbar_wait(bar_empty + 8 * s, uint32_t((q - NRS) / NRS) & 1u, abort_word);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) break;
+      }
+      const float dv = dv_next;
+      dv_next = load_d(q + 1);
       if (lane == 0) {
         asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(2 * kUOpBytes)
                      : "memory");
@@ -819,8 +848,10 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
       if (lane < kUK) Dq[s * kUK + lane] = dv;
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-    };
-    for (; issued < min(kUStages, nq); ++issued) produce(issued);
+      issued = q + 1;
+    }
+  } else if (warp == 8) {
+    // ---------------------------------------------------------- MMA issuer
     for (int q = 0; q < nq && ok; ++q) {
       const int o = q % NOS;
       if (lane == 0) ok = mbar_wait(bar_ready + 8 * o, uint32_t(q / NOS) & 1u, abort_word);
@@ -828,29 +859,32 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
       if (!ok) break;
       if (lane == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t ah = op_u + uint32_t(o) * NOP * kUOpBytes, bh = ah + kUOpBytes;
-        const uint32_t al = ah + 2 * kUOpBytes, bl = ah + 3 * kUOpBytes;
+        // A (hi, lo) in tensor memory, columns 128 + 32 o (+ 16 for lo);
+        // B (hi, lo) in shared memory
+        const uint32_t ah = tmem + 128u + 32u * uint32_t(o), al = ah + 16u;
+        const uint32_t bh = op_u + uint32_t(o) * NOP * kUOpBytes, bl = bh + kUOpBytes;
 #pragma unroll
         for (int s = 0; s < kUK / 8; ++s) {
           const uint32_t ko = uint32_t(s) * 2 * kUmmaLbo;  // two K groups of 4 per MMA
+          const uint32_t ka = uint32_t(s) * 8u;             // 8 K columns of A per MMA
           const uint32_t acc0 = (q > 0 || s > 0) ? 1u : 0u;
           if constexpr (NMMA == 3) {
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                "l"(umma_desc(al + ko)), "l"(umma_desc(bh + ko)), "r"(kIdescTf32), "r"(acc0)
+                " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem),
+                "r"(al + ka), "l"(umma_desc(bh + ko)), "r"(kIdescTf32), "r"(acc0)
                 : "memory");
-            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem),
-                         "l"(umma_desc(ah + ko)), "l"(umma_desc(bl + ko)), "r"(kIdescTf32)
+            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;\n" ::"r"(tmem), "r"(ah + ka),
+                         "l"(umma_desc(bl + ko)), "r"(kIdescTf32)
                          : "memory");
-            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem),
-                         "l"(umma_desc(ah + ko)), "l"(umma_desc(bh + ko)), "r"(kIdescTf32)
+            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;\n" ::"r"(tmem), "r"(ah + ka),
+                         "l"(umma_desc(bh + ko)), "r"(kIdescTf32)
                          : "memory");
           } else {
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                "l"(umma_desc(ah + ko)), "l"(umma_desc(bh + ko)), "r"(kIdescTf32), "r"(acc0)
+                " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem),
+                "r"(ah + ka), "l"(umma_desc(bh + ko)), "r"(kIdescTf32), "r"(acc0)
                 : "memory");
             (void)al;
             (void)bl;
@@ -861,64 +895,74 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
                      : "memory");
       }
       mma_issued = q + 1;
-      // the operands of chunk q being ready means raw stage q % kUStages
-      // has been read by every converter: refill it
-      if (issued < nq) produce(issued++);
     }
-    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
   } else {
     // ------------------------------------------------------- converters
-    const int row = threadIdx.x & 127, gb = threadIdx.x >> 7;  // K groups gb and gb + 2
+    // warps 0-3: A of rows 32 w + lane into tensor memory (the warp's own
+    // lane quarter); warps 4-7: B of rows 32 (w - 4) + lane into shared memory
+    const bool a_side = warp < 4;
+    const int row = 32 * (warp & 3) + lane;
     for (int q = 0; q < nq && ok; ++q) {
-      const int s = q % kUStages, o = q % NOS;
-      ok = mbar_wait(bar_full + 8 * s, uint32_t(q / kUStages) & 1u, abort_word);
+      const int s = q % NRS, o = q % NOS;
+      ok = mbar_wait(bar_full + 8 * s, uint32_t(q / NRS) & 1u, abort_word);
       // the MMAs of chunk q - NOS have read operand stage o
       if (ok && q >= NOS) ok = mbar_wait(bar_mma + 8 * o, uint32_t((q - NOS) / NOS) & 1u, abort_word);
       if (!ok) break;
       const float *rA = reinterpret_cast<const float *>(raw + s * 2 * kUOpBytes);
       const float *rB = rA + OPF;
-      const float *dq = Dq + s * kUK;
-      float *ob = reinterpret_cast<float *>(opnd + o * NOP * kUOpBytes);
+      const int kl0 = kUK * q;  // local column of the chunk's first entry
+      if (a_side) {
+        float a[kUK];
 #pragma unroll
-      for (int gg = 0; gg < 2; ++gg) {
-        const int g = gb + 2 * gg;
-        const int kl = kUK * q + 4 * g;  // local column of the group's first entry
-        float a[4], b[4];
+        for (int k = 0; k < kUK; ++k) a[k] = kl0 + k < kw ? rA[k * kT128 + row] : 0.f;  // raw A: [k][row]
+        uint32_t h[kUK];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = rA[(4 * g + i) * kT128 + row];  // raw A: [k][row]
-        if (trail) {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) b[i] = rB[(4 * g + i) * kT128 + row] * dq[4 * g + i];
-        } else {  // raw B: [g][row][4], already the operand layout
-          const float4 v = *reinterpret_cast<const float4 *>(rB + g * (OPF / 4) + 4 * row);
-          b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (kl + i >= kw) a[i] = b[i] = 0.f;
-        const int off = g * (OPF / 4) + 4 * row;  // K group g, row: 16-byte slot
-        uint32_t ah[4], bh[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          ah[i] = tf32_hi(a[i]);
-          bh[i] = tf32_hi(b[i]);
-        }
-        *reinterpret_cast<uint4 *>(ob + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
-        *reinterpret_cast<uint4 *>(ob + OPF + off) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
+        for (int k = 0; k < kUK; ++k) h[k] = tf32_hi(a[k]);
+        const uint32_t ta = tmem + (uint32_t(32 * warp) << 16) + 128u + 32u * uint32_t(o);
+        tmem_st16(ta, h);
         if constexpr (NMMA == 3) {
-          uint32_t al[4], bl[4];
+          uint32_t l[kUK];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            al[i] = tf32_lo(a[i], ah[i]);
-            bl[i] = tf32_lo(b[i], bh[i]);
-          }
-          *reinterpret_cast<uint4 *>(ob + 2 * OPF + off) = make_uint4(al[0], al[1], al[2], al[3]);
-          *reinterpret_cast<uint4 *>(ob + 3 * OPF + off) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
+          for (int k = 0; k < kUK; ++k) l[k] = tf32_lo(a[k], h[k]);
+          tmem_st16(ta + 16u, l);
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      } else {
+        const float *dq = Dq + s * kUK;
+        float *ob = reinterpret_cast<float *>(opnd + o * NOP * kUOpBytes);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          float b[4];
+          if (trail) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) b[i] = rB[(4 * g + i) * kT128 + row] * dq[4 * g + i];
+          } else {  // raw B: [g][row][4], already the operand layout
+            const float4 v = *reinterpret_cast<const float4 *>(rB + g * (OPF / 4) + 4 * row);
+            b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (kl0 + 4 * g + i >= kw) b[i] = 0.f;
+          const int off = g * (OPF / 4) + 4 * row;  // K group g, row: 16-byte slot
+          uint32_t bh[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) bh[i] = tf32_hi(b[i]);
+          *reinterpret_cast<uint4 *>(ob + off) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
+          if constexpr (NMMA == 3) {
+            uint32_t bl[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) bl[i] = tf32_lo(b[i], bh[i]);
+            *reinterpret_cast<uint4 *>(ob + OPF + off) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic-proxy stores -> tensor core
       }
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic-proxy stores -> tensor core
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar_ready + 8 * o) : "memory");
+      if (lane == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar_ready + 8 * o) : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar_empty + 8 * s) : "memory");
+      }
     }
     // the accumulator is complete (and every operand read: the shared
     // memory is free for the staged tile)
@@ -977,18 +1021,20 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
     asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
     asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   }
-  if (!ok && warp == 8 && lane == 0) {
+  // on a timeout: let the copies (warp 9) and MMAs (warp 8) still in flight
+  // finish before the shared and tensor memory are given up (each wait bounded)
+  if (!ok && warp == 9 && lane == 0) {
     atomicOr(flags, FLAG_WAIT_TIMEOUT);
-    // let the copies and MMAs still in flight finish before the shared and
-    // tensor memory are given up (each wait bounded)
-    for (int q = max(0, issued - kUStages); q < issued; ++q)
-      mbar_wait(bar_full + 8 * (q % kUStages), uint32_t(q / kUStages) & 1u);
+    for (int q = max(0, issued - NRS); q < issued; ++q)
+      mbar_wait(bar_full + 8 * (q % NRS), uint32_t(q / NRS) & 1u);
+  }
+  if (!ok && warp == 8 && lane == 0) {
     if (mma_issued > 0) mbar_wait(bar_mma + 8 * ((mma_issued - 1) % NOS), uint32_t((mma_issued - 1) / NOS) & 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kT128) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kUTmemCols) : "memory");
 }
 
 // ------------------------------------------------------------------ apply
