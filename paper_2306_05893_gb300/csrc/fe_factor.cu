@@ -911,10 +911,15 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
       const float *rA = reinterpret_cast<const float *>(raw + s * 2 * kUOpBytes);
       const float *rB = rA + OPF;
       const int kl0 = kUK * q;  // local column of the chunk's first entry
+      const float *dq = Dq + s * kUK;
       if (a_side) {
+        // A carries the d_l scaling of TRAIL (C -= (A D) B^T): the A side has
+        // the lighter conversion (its parts go to tensor memory in two stores)
         float a[kUK];
 #pragma unroll
-        for (int k = 0; k < kUK; ++k) a[k] = kl0 + k < kw ? rA[k * kT128 + row] : 0.f;  // raw A: [k][row]
+        for (int k = 0; k < kUK; ++k) a[k] = rA[k * kT128 + row];  // raw A: [k][row]
+#pragma unroll
+        for (int k = 0; k < kUK; ++k) a[k] = kl0 + k < kw ? (trail ? a[k] * dq[k] : a[k]) : 0.f;
         uint32_t h[kUK];
 #pragma unroll
         for (int k = 0; k < kUK; ++k) h[k] = tf32_hi(a[k]);
@@ -929,30 +934,34 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
         asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       } else {
-        const float *dq = Dq + s * kUK;
         float *ob = reinterpret_cast<float *>(opnd + o * NOP * kUOpBytes);
+        // all 16 loads of the row before any store (the raw and operand
+        // buffers could alias as far as the compiler knows)
+        float b[kUK];
+        if (trail) {
+#pragma unroll
+          for (int k = 0; k < kUK; ++k) b[k] = rB[k * kT128 + row];  // raw B: [k][row]
+        } else {  // raw B: [g][row][4], already the operand layout
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const float4 v = *reinterpret_cast<const float4 *>(rB + g * (OPF / 4) + 4 * row);
+            b[4 * g] = v.x; b[4 * g + 1] = v.y; b[4 * g + 2] = v.z; b[4 * g + 3] = v.w;
+          }
+        }
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-          float b[4];
-          if (trail) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) b[i] = rB[(4 * g + i) * kT128 + row] * dq[4 * g + i];
-          } else {  // raw B: [g][row][4], already the operand layout
-            const float4 v = *reinterpret_cast<const float4 *>(rB + g * (OPF / 4) + 4 * row);
-            b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            if (kl0 + 4 * g + i >= kw) b[i] = 0.f;
-          const int off = g * (OPF / 4) + 4 * row;  // K group g, row: 16-byte slot
           uint32_t bh[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) bh[i] = tf32_hi(b[i]);
+          for (int i = 0; i < 4; ++i) {
+            if (kl0 + 4 * g + i >= kw) b[4 * g + i] = 0.f;
+            bh[i] = tf32_hi(b[4 * g + i]);
+          }
+          const int off = g * (OPF / 4) + 4 * row;  // K group g, row: 16-byte slot
           *reinterpret_cast<uint4 *>(ob + off) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
           if constexpr (NMMA == 3) {
             uint32_t bl[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) bl[i] = tf32_lo(b[i], bh[i]);
+            for (int i = 0; i < 4; ++i) bl[i] = tf32_lo(b[4 * g + i], bh[i]);
             *reinterpret_cast<uint4 *>(ob + OPF + off) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
           }
         }
