@@ -20,7 +20,11 @@ What it computes, in the paper's order (arXiv 2306.05893, Section 3):
   * a direct sparse solve of A a = b, then backward Euler
     v+ = v + h a, q+ = q + h v+ (Eq. "implicit integration");
   * the CSR pattern and the triplet -> slot map C (Section 4.2), built here by
-    sorting unique (row, col) keys, i.e. independently of the double transpose.
+    sorting unique (row, col) keys, i.e. independently of the double transpose;
+  * frictionless contact against rigid planes by Lagrange multipliers
+    (Section "Lagrangian multipliers"): free motion, compliance
+    W = H A^{-1} H^T by one direct solve per constraint, projected
+    Gauss-Seidel, motion correction.
 
 Everything is numpy float64 (complex128 where a complex-step derivative is
 taken), vectorised over elements only: no blocking, fusion or reordering.
@@ -554,6 +558,63 @@ class Model:
 
     def pattern(self):
         return csr_pattern(self.n_dof, self.conn, self.fixed_dofs)
+
+    def contact_jacobian(self, nodes, normals):
+        """H (m x n_dof): row i is the unit normal n_i on the three DOFs of
+        node i (Section "Lagrangian multipliers", Eq. "KKT": the linearised
+        constraint equations of a deformable object against a rigid one)."""
+        m = len(nodes)
+        rows = np.repeat(np.arange(m), 3)
+        cols = (3 * np.asarray(nodes)[:, None] + np.arange(3)).reshape(-1)
+        return sp.csr_matrix((np.asarray(normals, float).reshape(-1), (rows, cols)), shape=(m, self.n_dof))
+
+    def contact_step(self, q, v, p, nodes, normals, offsets, sweeps=200, tol=1e-12):
+        """One step with frictionless contacts against rigid planes
+        n_i . x >= c_i (x the node's end-of-step position), in the paper's
+        three stages (Section "Lagrangian multipliers"):
+          * free motion: A a_free = b (the step without contacts);
+          * constraint resolution: compliance W = H A^{-1} H^T and the LCP
+            lambda >= 0, w = W lambda - (delta - H a_free) >= 0,
+            lambda . w = 0, solved by projected Gauss-Seidel; here
+            x_end = q + h v + h^2 a, so the constraint on the unknown a is
+            H a >= delta with delta_i = (c_i - n_i . (q + h v)_node) / h^2;
+          * motion correction: a = a_free + A^{-1} H^T lambda.
+        Returns q+, v+, a, lambda and W."""
+        A, b = self.system(q, v, p)
+        a_free = direct_solve(A, b)
+        H = self.contact_jacobian(nodes, normals)
+        Z = np.column_stack([direct_solve(A, H.getrow(i).toarray().ravel()) for i in range(H.shape[0])]) \
+            if H.shape[0] else np.zeros((self.n_dof, 0))
+        W = H @ Z
+        h = self.h
+        x_pred = (q + h * v).reshape(-1, 3)[np.asarray(nodes)]
+        delta = (np.asarray(offsets, float) - np.einsum("ij,ij->i", np.asarray(normals, float), x_pred)) / (h * h)
+        lam = pgs(W, delta - H @ a_free, sweeps, tol)
+        a = a_free + Z @ lam
+        v1 = v + h * a
+        return q + h * v1, v1, a, lam, W
+
+
+def pgs(W, r, sweeps, tol):
+    """Projected Gauss-Seidel for the LCP lambda >= 0, W lambda - r >= 0,
+    lambda . (W lambda - r) = 0 (the constraint-resolution step of Section
+    "Lagrangian multipliers"): constraints in index order, each set to the
+    non-negative value that zeroes its own residual given the others; stops
+    when a sweep changes no lambda by more than tol * max |lambda|.  A
+    constraint with W_ii <= 0 (a node that cannot move) keeps lambda = 0."""
+    m = W.shape[0]
+    lam = np.zeros(m)
+    for _ in range(sweeps):
+        dmax = 0.0
+        for i in range(m):
+            if W[i, i] <= 0.0:
+                continue
+            new = max(0.0, lam[i] + (r[i] - W[i] @ lam) / W[i, i])
+            dmax = max(dmax, abs(new - lam[i]))
+            lam[i] = new
+        if dmax <= tol * max(1e-300, np.abs(lam).max()):
+            break
+    return lam
 
 
 def direct_solve(A, b):
