@@ -227,6 +227,65 @@ def measure_adjoint(fe, torch, T=20, reps=2):
             "n_dof": 3 * mesh.n_nodes, "precision": "mixed", "s_per_grad": el / reps}
 
 
+def run_contact(args, world, rank, local, torch, dist):
+    """Contact workload (NEXT-3): the 107,163-DOF Mooney-Rivlin tet beam
+    (tet20x20x80-mr) with its free end moving down onto a rigid floor 2 mm
+    below its bottom face; 63 frictionless contacts (the bottom-face nodes
+    of the last three node layers at the free end), exact factor every step
+    (refactor_every = 1: the compliance is built with A^{-1}).  Replicas
+    only for N > 1 (no data-path collective)."""
+    import fe_inputs as fi
+    import paper_2306_05893_gb300 as fe
+    wl = fi.workload("tet20x20x80-mr")
+    mesh = wl.mesh
+    ctx = fe.FEContext.from_workload(wl, refactor_every=1, profile_stages=1,
+                                     precond_fp16=args.precond_fp16)
+    n = ctx.n
+    q0 = mesh.X.reshape(-1).copy()
+    v0 = np.zeros_like(q0)
+    v0.reshape(-1, 3)[:, 2] = -0.5 * mesh.X[:, 0] / mesh.X[:, 0].max()
+    fixed = (3 * mesh.fixed_nodes[:, None] + np.arange(3)).reshape(-1)
+    v0[fixed] = 0.0
+    xmax = mesh.X[:, 0].max()
+    nodes = np.nonzero((mesh.X[:, 2] == 0.0) & (mesh.X[:, 0] >= xmax - 2 * 0.01 - 1e-12))[0].astype(np.int32)
+    ctx.set_state(q0, v0)
+    ctx.set_contacts(nodes, np.tile([0.0, 0.0, 1.0], (len(nodes), 1)), np.full(len(nodes), -0.002))
+    q = np.empty(n)
+    p = [wl.p(t).reshape(-1) for t in range(args.warmup + args.steps)]
+    for t in range(args.warmup):
+        ctx.step(p[t], q, None)
+    ctx.reset_stage_times()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    active = []
+    for t in range(args.steps):
+        ctx.step(p[args.warmup + t], q, None)
+        active.append(int((ctx.contact_forces() > 0).sum()))
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([el], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el = float(tt.item())
+    stage_ms, stage_calls, _ = ctx.stage_times()
+    gap = q.reshape(-1, 3)[nodes, 2] + 0.002
+    ctx.close()
+    out = {"metric": "implicit steps/s with frictionless contacts (free motion + compliance + PGS + correction)",
+           "value": world * args.steps / el, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "contact: tet20x20x80-mr onto a floor, 63 contacts, R = 1",
+                      "n_dof": n, "contacts": int(len(nodes)), "mean_active": float(np.mean(active)),
+                      "min_gap_m": float(gap.min()),
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+           "contact_ms_per_step": stage_ms["contact"] / args.steps}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_batch(args, world, rank, local, torch, dist):
     """Batched workload: 64 uneven tet beams (seed 7) stepped together; members
     sharded over ranks by DOF (no collective on the data path)."""
@@ -319,6 +378,8 @@ def main():
 
     if args.workload == "batch64":
         return run_batch(args, world, rank, local, torch, dist)
+    if args.workload == "contact":
+        return run_contact(args, world, rank, local, torch, dist)
     wl = fi.workload(args.workload)
     if args.precision is not None:
         wl.precision = 1 if args.precision == "mixed" else 0

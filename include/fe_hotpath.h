@@ -130,6 +130,10 @@ typedef struct {
                              solve is still refined to tol in FP64.  The copy
                              keeps M^{-1} = Y^T D^{-1} Y symmetric positive
                              definite.  Ignored for FE_FP64.                  */
+  int32_t contact_sweeps; /* projected Gauss-Seidel sweeps at most per step with
+                             contacts (fe_set_contacts); default 200         */
+  double contact_tol;     /* stop when a sweep changes no multiplier by more
+                             than contact_tol * max |lambda|; default 1e-12  */
 } fe_options;
 
 typedef struct {
@@ -245,6 +249,30 @@ int fe_apply_preconditioner(fe_ctx *ctx, const double *r, double *z);
  * overlap on the GPU, on any stream or context, race. */
 int fe_apply_preconditioner_noalloc(fe_ctx *ctx, const double *r, double *z, void *stream);
 
+/* Frictionless contacts against rigid planes, by Lagrange multipliers
+ * (Section "Lagrangian multipliers", Eq. "KKT"), for every following step
+ * until replaced: constraint i asks that node nodes[i] end the step on the
+ * positive side of its plane, normals[3i..3i+2] . x >= offsets[i] (x the
+ * node's end-of-step position; the normal need not be unit length).  A step
+ * with contacts solves the free motion A a_free = b (the usual PCG), builds
+ * the compliance W = H P^{-1} H^T with the step's preconditioner P (the
+ * lagged factor; the exact A^{-1} when refactor_every = 1), one
+ * preconditioner application per constraint, solves the LCP
+ * lambda >= 0, W lambda >= delta - H a_free, complementary, by projected
+ * Gauss-Seidel (contact_sweeps, contact_tol), and corrects
+ * a = a_free + P^{-1} H^T lambda before integrating.  Constraints on fixed
+ * nodes keep lambda = 0.  Host arrays, copied; m = 0 removes the contacts;
+ * m <= 4096.  FE_ERR_ARG for a node out of range or a zero normal;
+ * FE_ERR_STATE with keep_checkpoints (the adjoint does not cover contacts)
+ * or newton_iters > 1. */
+int fe_set_contacts(fe_ctx *ctx, int32_t m, const int32_t *nodes, const double *normals,
+                    const double *offsets);
+
+/* The multipliers lambda [m] of the last step with contacts (host array):
+ * the contact force on the node is lambda_i times the normal, in the
+ * units of the equation of motion's right-hand side (N). */
+int fe_get_contact_forces(fe_ctx *ctx, double *lambda);
+
 /* One implicit step with external nodal forces p_ext [n] (NULL = 0), one
  * Newton iteration (Eq. "taylor expansion").  Writes the new q, v when the
  * pointers are non-NULL; info may be NULL. */
@@ -273,6 +301,7 @@ enum {
   FE_STAGE_SPMV, FE_STAGE_VECTOR, FE_STAGE_RESIDUAL, FE_STAGE_INTEGRATE,
   FE_STAGE_FACTOR_UPDATE, /* the factor's trailing-update launches only */
   FE_STAGE_PCG_GRAPH,     /* PCG iterations replayed as CUDA graphs (use_graph) */
+  FE_STAGE_CONTACT,       /* constraint resolution and motion correction      */
   FE_STAGE_COUNT
 };
 int fe_get_stage_times(fe_ctx *ctx, double *ms, int64_t *calls, int64_t *kernel_launches);

@@ -210,6 +210,23 @@ def fe_apply_preconditioner(ctx, r, z):
     _check(ctx, load().fe_apply_preconditioner(ctx, _ptr(r), _ptr(z)))
 
 
+def fe_set_contacts(ctx, nodes, normals, offsets):
+    nodes = np.ascontiguousarray(nodes, dtype=np.int32).reshape(-1)
+    normals = _f64(normals).reshape(-1)
+    offsets = _f64(offsets).reshape(-1)
+    m = nodes.size
+    if normals.size != 3 * m or offsets.size != m:
+        raise ValueError("nodes [m], normals [m, 3] and offsets [m] disagree")
+    _check(ctx, load().fe_set_contacts(ctx, m, _ptr(nodes), _ptr(normals), _ptr(offsets)))
+
+
+def fe_get_contact_forces(ctx, m):
+    lam = np.zeros(m)
+    if m:
+        _check(ctx, load().fe_get_contact_forces(ctx, _ptr(lam)))
+    return lam
+
+
 def fe_step(ctx, p_ext=None, q_out=None, v_out=None):
     info = FeStepInfo()
     st = load().fe_step(ctx, _ptr(p_ext), _ptr(q_out), _ptr(v_out), ct.byref(info))
@@ -449,6 +466,16 @@ class FEContext:
         z = np.empty(self.n)
         fe_apply_preconditioner(self.ctx, _f64(r), z)
         return z
+
+    def set_contacts(self, nodes, normals, offsets):
+        """Frictionless contacts against rigid planes n . x >= c for the
+        following steps (fe_set_contacts); empty arrays remove them."""
+        fe_set_contacts(self.ctx, nodes, normals, offsets)
+        self.n_contacts = int(np.asarray(nodes).size)
+
+    def contact_forces(self):
+        """Multipliers of the last step with contacts (fe_get_contact_forces)."""
+        return fe_get_contact_forces(self.ctx, getattr(self, "n_contacts", 0))
 
     def step(self, p=None, q_out=None, v_out=None):
         p_arg = p if (p is None or hasattr(p, "data_ptr")) else _f64(p)

@@ -29,7 +29,7 @@ class FeOptions(ct.Structure):
                 ("factor_timeout_s", ct.c_double), ("use_graph", ct.c_int32),
                 ("profile_stages", ct.c_int32), ("newton_iters", ct.c_int32),
                 ("newton_tol", ct.c_double), ("factor_tf32", ct.c_int32),
-                ("precond_fp16", ct.c_int32)]
+                ("precond_fp16", ct.c_int32), ("contact_sweeps", ct.c_int32), ("contact_tol", ct.c_double)]
 
 
 class FeStepInfo(ct.Structure):
@@ -44,7 +44,7 @@ class FeInfo(ct.Structure):
 
 
 STAGES = ["element", "assembly", "factor", "apply", "spmv", "vector", "residual", "integrate",
-          "factor_update", "pcg_graph"]
+          "factor_update", "pcg_graph", "contact"]
 
 P = ct.POINTER
 CTX = ct.c_void_p
@@ -74,6 +74,8 @@ SIGNATURES = {
     "fe_assemble": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "fe_factor_now": (ct.c_int, [CTX]),
     "fe_apply_preconditioner": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p]),
+    "fe_set_contacts": (ct.c_int, [CTX, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "fe_get_contact_forces": (ct.c_int, [CTX, ct.c_void_p]),
     "fe_apply_preconditioner_noalloc": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "fe_step": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p, P(FeStepInfo)]),
     "fe_get_info": (ct.c_int, [CTX, P(FeInfo)]),

@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfe_hotpath.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fe_setup.cpp", "fe_api_host.cpp", "fe_api.cu", "fe_kernels.cu", "fe_factor.cu", "fe_adjoint.cu", "fe_batch.cu",
-           "fe_triplets.cu"]
+           "fe_triplets.cu", "fe_contact.cu"]
 
 
 def _nvcc():

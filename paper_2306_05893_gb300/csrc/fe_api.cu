@@ -968,6 +968,11 @@ int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_ste
     info->newton = newton;
     info->newton_correction = ncorr;
   }
+  // contacts: constraint resolution and motion correction (NEXT-3)
+  if (!c->contact_node.empty() || d->c_m > 0) {
+    Stage st(c, FE_STAGE_CONTACT, s);
+    FE_TRY(contact_resolve(c, d, fp32));
+  }
   // S8 backward Euler
   {
     Stage st(c, FE_STAGE_INTEGRATE, s);

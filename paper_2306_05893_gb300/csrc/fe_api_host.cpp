@@ -27,6 +27,8 @@ int fe_options_default(fe_options *o) {
   o->newton_tol = 0.0;
   o->factor_tf32 = 0;
   o->precond_fp16 = 0;
+  o->contact_sweeps = 200;
+  o->contact_tol = 1e-12;
   return FE_OK;
 }
 
@@ -72,6 +74,8 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
     if (c->opt.nd_leaf_nodes <= 0) c->opt.nd_leaf_nodes = 64;
     if (c->opt.newton_iters <= 0) c->opt.newton_iters = 1;
     if (c->opt.precision != FE_MIXED) c->opt.precond_fp16 = 0;
+    if (c->opt.contact_sweeps <= 0) c->opt.contact_sweeps = 200;
+    if (!(c->opt.contact_tol > 0)) c->opt.contact_tol = 1e-12;
     c->opt.precond_fp16 = c->opt.precond_fp16 ? 1 : 0;
     if (c->opt.newton_iters > 1 && c->opt.keep_checkpoints) {
       delete c;

@@ -1,0 +1,223 @@
+// Frictionless contact against rigid planes by Lagrange multipliers
+// (Section "Lagrangian multipliers", Eq. "KKT"): after the free motion
+// A a_free = b of a step, the compliance W = H P^{-1} H^T is built with the
+// step's preconditioner P (one application per constraint: the columns
+// Z = P^{-1} H^T), the LCP lambda >= 0, w = W lambda - (delta - H a_free) >= 0,
+// lambda . w = 0 is solved by projected Gauss-Seidel, and the motion is
+// corrected, a = a_free + Z lambda.  Constraint i: n_i . x >= c_i for node
+// i's end-of-step position x = q + h v + h^2 a, i.e. on the unknown a:
+// n_i . a_node >= delta_i = (c_i - n_i . (q + h v)_node) / h^2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/fe_hotpath.h"
+#include "fe_device.cuh"
+
+namespace fe {
+
+namespace {
+
+constexpr int kMaxContacts = 4096;  // multipliers kept in shared memory by the solver (32 KB)
+
+// RHS of constraint i in the preconditioner's precision: n_i on node i's DOFs
+// (the vector is cleared before)
+template <typename T>
+__global__ void contact_column_kernel(T *r, const int32_t *__restrict__ node, const double *__restrict__ normal,
+                                      int i) {
+  if (threadIdx.x < 3) r[3 * int64_t(node[i]) + threadIdx.x] = T(normal[3 * i + threadIdx.x]);
+}
+
+// W[i m + j] = n_i . Z[:, j] at node i; rhs_i = delta_i - n_i . a_free(node i)
+__global__ void contact_compliance_kernel(const double *__restrict__ Z, const int32_t *__restrict__ node,
+                                          const double *__restrict__ normal, const double *__restrict__ off,
+                                          const double *__restrict__ q, const double *__restrict__ v,
+                                          const double *__restrict__ a, double h, int64_t n, int m,
+                                          double *__restrict__ W, double *__restrict__ rhs) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < int64_t(m) * m) {
+    const int i = int(t / m), j = int(t % m);
+    const int64_t base = 3 * int64_t(node[i]);
+    const double *zj = Z + int64_t(j) * n + base;
+    W[t] = normal[3 * i] * zj[0] + normal[3 * i + 1] * zj[1] + normal[3 * i + 2] * zj[2];
+  }
+  if (t < m) {
+    const int i = int(t);
+    const int64_t base = 3 * int64_t(node[i]);
+    double nx = 0.0, na = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      nx += normal[3 * i + k] * (q[base + k] + h * v[base + k]);
+      na += normal[3 * i + k] * a[base + k];
+    }
+    rhs[i] = (off[i] - nx) / (h * h) - na;
+  }
+}
+
+// Projected Gauss-Seidel on one warp: constraints in index order, each set
+// to the non-negative value that zeroes its own residual given the others
+// (the row's dot product over the warp, reduced by lane 0's butterfly and
+// broadcast, so every lane takes the same decision); stops when a sweep
+// changes no multiplier by more than tol * max |lambda|.  W_ii <= 0 (a node
+// that cannot move) keeps lambda_i = 0.
+__global__ void __launch_bounds__(32) pgs_kernel(const double *__restrict__ W, const double *__restrict__ r,
+                                                 double *__restrict__ lam, int m, int sweeps, double tol) {
+  __shared__ double sl[kMaxContacts];
+  const int lane = threadIdx.x;
+  for (int i = lane; i < m; i += 32) sl[i] = 0.0;
+  __syncwarp();
+  for (int sw = 0; sw < sweeps; ++sw) {
+    double dmax = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double *Wi = W + int64_t(i) * m;
+      double acc = 0.0;
+      for (int j = lane; j < m; j += 32) acc += Wi[j] * sl[j];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      acc = __shfl_sync(0xffffffffu, acc, 0);
+      const double wii = Wi[i];
+      if (wii > 0.0) {
+        const double old = sl[i];
+        const double nw = fmax(0.0, old + (r[i] - acc) / wii);
+        dmax = fmax(dmax, fabs(nw - old));
+        __syncwarp();
+        if (lane == 0) sl[i] = nw;
+      }
+      __syncwarp();
+    }
+    double lmax = 0.0;
+    for (int i = lane; i < m; i += 32) lmax = fmax(lmax, fabs(sl[i]));
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if (dmax <= tol * fmax(1e-300, lmax)) break;
+  }
+  for (int i = lane; i < m; i += 32) lam[i] = sl[i];
+}
+
+// a += Z lambda (Z column-major, n x m)
+__global__ void contact_correct_kernel(const double *__restrict__ Z, const double *__restrict__ lam, int64_t n,
+                                       int m, double *__restrict__ a) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double s = 0.0;
+  for (int j = 0; j < m; ++j) s += Z[int64_t(j) * n + r] * lam[j];
+  a[r] += s;
+}
+
+// (re)allocate a contact buffer, keeping the context's allocation list exact
+int regrow(fe_ctx *c, DeviceState *d, void **p, size_t bytes) {
+  if (*p) {
+    d->allocs.erase(std::remove(d->allocs.begin(), d->allocs.end(), *p), d->allocs.end());
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 8));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return set_error(c, FE_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes for contacts failed");
+  }
+  d->allocs.push_back(*p);
+  return FE_OK;
+}
+
+}  // namespace
+
+// Upload the constraint set (host copy in the context) to the device buffers.
+static int contact_upload(fe_ctx *c, DeviceState *d) {
+  const int64_t m = int64_t(c->contact_node.size());
+  if (m > d->c_cap) {
+    const int64_t cap = std::max<int64_t>(m, 2 * d->c_cap);
+    int st = regrow(c, d, reinterpret_cast<void **>(&d->c_node), size_t(cap) * sizeof(int32_t));
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_normal), size_t(3 * cap) * sizeof(double));
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_off), size_t(cap) * sizeof(double));
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_Z), size_t(cap) * size_t(c->n) * sizeof(double));
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_W), size_t(cap) * size_t(cap) * sizeof(double));
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_rhs), size_t(cap) * sizeof(double));
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_lam), size_t(cap) * sizeof(double));
+    if (st) {
+      d->c_cap = 0;
+      return st;
+    }
+    d->c_cap = cap;
+  }
+  if (m > 0) {
+    FE_CUDA_TRY(cudaMemcpy(d->c_node, c->contact_node.data(), size_t(m) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    FE_CUDA_TRY(cudaMemcpy(d->c_normal, c->contact_normal.data(), size_t(3 * m) * sizeof(double),
+                           cudaMemcpyHostToDevice));
+    FE_CUDA_TRY(cudaMemcpy(d->c_off, c->contact_offset.data(), size_t(m) * sizeof(double), cudaMemcpyHostToDevice));
+    FE_CUDA_TRY(cudaMemset(d->c_lam, 0, size_t(m) * sizeof(double)));
+  }
+  d->c_m = m;
+  d->c_dirty = false;
+  return FE_OK;
+}
+
+// Constraint resolution and motion correction of the current step: d->x
+// holds a_free on entry and the corrected a on return (all on d->stream).
+int contact_resolve(fe_ctx *c, DeviceState *d, bool fp32) {
+  cudaStream_t s = d->stream;
+  if (d->c_dirty) {
+    FE_CUDA_TRY(cudaStreamSynchronize(s));
+    const int st = contact_upload(c, d);
+    if (st) return st;
+  }
+  const int m = int(d->c_m);
+  if (m == 0) return FE_OK;
+  const int64_t n = c->n;
+  const size_t ts = fp32 ? sizeof(float) : sizeof(double);
+  // Z = P^{-1} H^T, one preconditioner application per constraint
+  for (int i = 0; i < m; ++i) {
+    FE_CUDA_TRY(cudaMemsetAsync(d->vr, 0, size_t(n) * ts, s));
+    if (fp32)
+      contact_column_kernel<float><<<1, 32, 0, s>>>(static_cast<float *>(d->vr), d->c_node, d->c_normal, i);
+    else
+      contact_column_kernel<double><<<1, 32, 0, s>>>(static_cast<double *>(d->vr), d->c_node, d->c_normal, i);
+    apply_enqueue(c, d, d->cur, fp32, d->vr, d->vz, s);
+    launch_convert(d->vz, fp32, d->c_Z + int64_t(i) * n, false, n, s);
+    d->launches += 2;
+  }
+  const int64_t cells = std::max<int64_t>(int64_t(m) * m, m);
+  contact_compliance_kernel<<<unsigned((cells + 255) / 256), 256, 0, s>>>(
+      d->c_Z, d->c_node, d->c_normal, d->c_off, d->q, d->v, d->x, c->h, n, m, d->c_W, d->c_rhs);
+  pgs_kernel<<<1, 32, 0, s>>>(d->c_W, d->c_rhs, d->c_lam, m, c->opt.contact_sweeps, c->opt.contact_tol);
+  contact_correct_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(d->c_Z, d->c_lam, n, m, d->x);
+  d->launches += 3;
+  FE_CUDA_TRY(cudaGetLastError());
+  return FE_OK;
+}
+
+}  // namespace fe
+
+extern "C" int fe_set_contacts(fe_ctx *c, int32_t m, const int32_t *nodes, const double *normals,
+                               const double *offsets) {
+  using namespace fe;
+  if (!c || m < 0 || m > kMaxContacts || (m > 0 && (!nodes || !normals || !offsets))) return FE_ERR_ARG;
+  if (m > 0 && (c->opt.keep_checkpoints || c->opt.newton_iters > 1))
+    return set_error(c, FE_ERR_STATE, "contacts need keep_checkpoints = 0 and newton_iters = 1");
+  for (int32_t i = 0; i < m; ++i) {
+    if (nodes[i] < 0 || nodes[i] >= c->n_nodes)
+      return set_error(c, FE_ERR_ARG, "contact " + std::to_string(i) + ": node out of range");
+    const double nn = normals[3 * i] * normals[3 * i] + normals[3 * i + 1] * normals[3 * i + 1] +
+                      normals[3 * i + 2] * normals[3 * i + 2];
+    if (!(nn > 0) || !std::isfinite(offsets[i]))
+      return set_error(c, FE_ERR_ARG, "contact " + std::to_string(i) + ": zero normal or non-finite offset");
+  }
+  c->contact_node.assign(nodes, nodes + m);
+  c->contact_normal.assign(normals, normals + 3 * int64_t(m));
+  c->contact_offset.assign(offsets, offsets + m);
+  if (c->dev) c->dev->c_dirty = true;
+  return FE_OK;
+}
+
+extern "C" int fe_get_contact_forces(fe_ctx *c, double *lambda) {
+  using namespace fe;
+  if (!c || !lambda) return FE_ERR_ARG;
+  const int64_t m = int64_t(c->contact_node.size());
+  if (m == 0) return FE_OK;
+  DeviceState *d = c->dev;
+  if (!d || d->c_m != m || !d->c_lam) return set_error(c, FE_ERR_STATE, "no step with these contacts yet");
+  FE_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  FE_CUDA_TRY(cudaMemcpy(lambda, d->c_lam, size_t(m) * sizeof(double), cudaMemcpyDeviceToHost));
+  return FE_OK;
+}

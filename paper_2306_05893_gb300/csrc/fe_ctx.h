@@ -126,6 +126,11 @@ struct fe_ctx {
   double factor_flops = 0;
   int64_t y_nnz = 0;
 
+  // contacts of the following steps (fe_set_contacts): node, normal and
+  // plane offset of each constraint n . x >= c
+  std::vector<int32_t> contact_node;
+  std::vector<double> contact_normal, contact_offset;
+
   fe::DeviceState *dev = nullptr;
   std::string err;
 };

@@ -103,6 +103,12 @@ struct DeviceState {
   // front over all rows of Y[0] then Y[1] (128 x 16 boxes); null for the
   // FP64 factor
   void *tmaps = nullptr;
+  // contacts (fe_contact.cu): constraint data, Z = P^{-1} H^T (n x m,
+  // column-major), compliance W (m x m), PGS right-hand side and multipliers
+  int32_t *c_node = nullptr;
+  double *c_normal = nullptr, *c_off = nullptr, *c_Z = nullptr, *c_W = nullptr, *c_rhs = nullptr, *c_lam = nullptr;
+  int64_t c_cap = 0, c_m = 0;
+  bool c_dirty = true;  // the context's constraint set changed since the last upload
   double *D[2] = {nullptr, nullptr};
   void *wbuf = nullptr, *ubuf = nullptr, *yperm = nullptr;  // apply work vectors
   double *na = nullptr, *nq = nullptr, *nv = nullptr;       // Newton iterate a_k, q_k, v_k
@@ -226,6 +232,9 @@ void stage_end(fe_ctx *c, int idx, cudaStream_t s);
 int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Afac, cudaStream_t s);
 // done: optional device flag; every kernel of the application returns at
 // once when it is non-zero (PCG iterations replayed past convergence)
+// contacts (fe_contact.cu): constraint resolution and motion correction of
+// the current step (d->x: a_free in, corrected a out)
+int contact_resolve(fe_ctx *c, DeviceState *d, bool fp32);
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
                    cudaStream_t s, const double *done = nullptr);
 
