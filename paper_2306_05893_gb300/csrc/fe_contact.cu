@@ -1,12 +1,15 @@
 // Frictionless contact against rigid planes by Lagrange multipliers
 // (Section "Lagrangian multipliers", Eq. "KKT"): after the free motion
 // A a_free = b of a step, the compliance W = H P^{-1} H^T is built with the
-// step's preconditioner P (one application per constraint: the columns
-// Z = P^{-1} H^T), the LCP lambda >= 0, w = W lambda - (delta - H a_free) >= 0,
-// lambda . w = 0 is solved by projected Gauss-Seidel, and the motion is
-// corrected, a = a_free + Z lambda.  Constraint i: n_i . x >= c_i for node
-// i's end-of-step position x = q + h v + h^2 a, i.e. on the unknown a:
-// n_i . a_node >= delta_i = (c_i - n_i . (q + h v)_node) / h^2.
+// step's preconditioner P = L D L^T, the LCP lambda >= 0,
+// w = W lambda - (delta - H a_free) >= 0, lambda . w = 0 is solved by
+// projected Gauss-Seidel, and the motion is corrected,
+// a = a_free + P^{-1} H^T lambda.  Since P^{-1} = L^{-T} D^{-1} L^{-1},
+// W = G^T D G with G = D^{-1} L^{-1} H^T: one forward solve per constraint
+// (the pivot output of the forward sweep) instead of a full application,
+// and a single full application for the correction.  Constraint i:
+// n_i . x >= c_i for node i's end-of-step position x = q + h v + h^2 a,
+// i.e. on the unknown a: n_i . a_node >= delta_i = (c_i - n_i . (q + h v)_node) / h^2.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,19 +34,36 @@ __global__ void contact_column_kernel(T *r, const int32_t *__restrict__ node, co
   if (threadIdx.x < 3) r[3 * int64_t(node[i]) + threadIdx.x] = T(normal[3 * i + threadIdx.x]);
 }
 
-// W[i m + j] = n_i . Z[:, j] at node i; rhs_i = delta_i - n_i . a_free(node i)
-__global__ void contact_compliance_kernel(const double *__restrict__ Z, const int32_t *__restrict__ node,
-                                          const double *__restrict__ normal, const double *__restrict__ off,
-                                          const double *__restrict__ q, const double *__restrict__ v,
-                                          const double *__restrict__ a, double h, int64_t n, int m,
-                                          double *__restrict__ W, double *__restrict__ rhs) {
-  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t < int64_t(m) * m) {
-    const int i = int(t / m), j = int(t % m);
-    const int64_t base = 3 * int64_t(node[i]);
-    const double *zj = Z + int64_t(j) * n + base;
-    W[t] = normal[3 * i] * zj[0] + normal[3 * i + 1] * zj[1] + normal[3 * i + 2] * zj[2];
+// W[i m + j] = W[j m + i] = sum_k G_i[k] d_k G_j[k] (block (i, j), j >= i;
+// per-thread partial sums in a fixed order, then a fixed-shape tree: the
+// result does not depend on scheduling, and W is exactly symmetric)
+template <typename T>
+__global__ void __launch_bounds__(256) contact_w_kernel(const T *__restrict__ G, const double *__restrict__ Dk,
+                                                        int64_t nf, int m, double *__restrict__ W) {
+  const int i = blockIdx.x, j = blockIdx.y;
+  if (j < i) return;
+  const T *gi = G + int64_t(i) * nf, *gj = G + int64_t(j) * nf;
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < nf; k += 256) acc += double(gi[k]) * Dk[k] * double(gj[k]);
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) {
+    W[int64_t(i) * m + j] = red[0];
+    W[int64_t(j) * m + i] = red[0];
+  }
+}
+
+// rhs_i = delta_i - n_i . a_free(node i)
+__global__ void contact_rhs_kernel(const int32_t *__restrict__ node, const double *__restrict__ normal,
+                                   const double *__restrict__ off, const double *__restrict__ q,
+                                   const double *__restrict__ v, const double *__restrict__ a, double h, int m,
+                                   double *__restrict__ rhs) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < m) {
     const int i = int(t);
     const int64_t base = 3 * int64_t(node[i]);
@@ -94,14 +114,22 @@ __global__ void __launch_bounds__(32) pgs_kernel(const double *__restrict__ W, c
   for (int i = lane; i < m; i += 32) lam[i] = sl[i];
 }
 
-// a += Z lambda (Z column-major, n x m)
-__global__ void contact_correct_kernel(const double *__restrict__ Z, const double *__restrict__ lam, int64_t n,
-                                       int m, double *__restrict__ a) {
+// r = H^T lambda in the solve's precision (the vector is cleared before;
+// one thread, constraints in order: several on one node add up
+// deterministically)
+template <typename T>
+__global__ void contact_force_kernel(T *r, const int32_t *__restrict__ node, const double *__restrict__ normal,
+                                     const double *__restrict__ lam, int m) {
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < m; ++i)
+    for (int k = 0; k < 3; ++k) r[3 * int64_t(node[i]) + k] += T(lam[i] * normal[3 * i + k]);
+}
+
+// a += z (z in the solve's precision)
+template <typename T>
+__global__ void add_vector_kernel(double *__restrict__ a, const T *__restrict__ z, int64_t n) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  double s = 0.0;
-  for (int j = 0; j < m; ++j) s += Z[int64_t(j) * n + r] * lam[j];
-  a[r] += s;
+  if (r < n) a[r] += double(z[r]);
 }
 
 // (re)allocate a contact buffer, keeping the context's allocation list exact
@@ -131,7 +159,8 @@ static int contact_upload(fe_ctx *c, DeviceState *d) {
     int st = regrow(c, d, reinterpret_cast<void **>(&d->c_node), size_t(cap) * sizeof(int32_t));
     if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_normal), size_t(3 * cap) * sizeof(double));
     if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_off), size_t(cap) * sizeof(double));
-    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_Z), size_t(cap) * size_t(c->n) * sizeof(double));
+    const size_t ts = c->opt.precision == FE_MIXED ? sizeof(float) : sizeof(double);
+    if (!st) st = regrow(c, d, &d->c_G, size_t(cap) * size_t(std::max<int64_t>(c->n_free, 1)) * ts);
     if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_W), size_t(cap) * size_t(cap) * sizeof(double));
     if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_rhs), size_t(cap) * sizeof(double));
     if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_lam), size_t(cap) * sizeof(double));
@@ -164,25 +193,39 @@ int contact_resolve(fe_ctx *c, DeviceState *d, bool fp32) {
   }
   const int m = int(d->c_m);
   if (m == 0) return FE_OK;
-  const int64_t n = c->n;
+  const int64_t n = c->n, nf = c->n_free;
   const size_t ts = fp32 ? sizeof(float) : sizeof(double);
-  // Z = P^{-1} H^T, one preconditioner application per constraint
+  // G_i = D^{-1} L^{-1} H^T e_i: one forward solve per constraint
   for (int i = 0; i < m; ++i) {
     FE_CUDA_TRY(cudaMemsetAsync(d->vr, 0, size_t(n) * ts, s));
     if (fp32)
       contact_column_kernel<float><<<1, 32, 0, s>>>(static_cast<float *>(d->vr), d->c_node, d->c_normal, i);
     else
       contact_column_kernel<double><<<1, 32, 0, s>>>(static_cast<double *>(d->vr), d->c_node, d->c_normal, i);
-    apply_enqueue(c, d, d->cur, fp32, d->vr, d->vz, s);
-    launch_convert(d->vz, fp32, d->c_Z + int64_t(i) * n, false, n, s);
-    d->launches += 2;
+    apply_forward_enqueue(c, d, d->cur, fp32, d->vr, static_cast<unsigned char *>(d->c_G) + size_t(i) * nf * ts, s);
+    d->launches += 1;
   }
-  const int64_t cells = std::max<int64_t>(int64_t(m) * m, m);
-  contact_compliance_kernel<<<unsigned((cells + 255) / 256), 256, 0, s>>>(
-      d->c_Z, d->c_node, d->c_normal, d->c_off, d->q, d->v, d->x, c->h, n, m, d->c_W, d->c_rhs);
+  // W = G^T D G, the PGS right-hand side, the multipliers
+  const dim3 wg = dim3(unsigned(m), unsigned(m), 1u);
+  if (fp32)
+    contact_w_kernel<float><<<wg, 256, 0, s>>>(static_cast<const float *>(d->c_G), d->D[d->cur], nf, m, d->c_W);
+  else
+    contact_w_kernel<double><<<wg, 256, 0, s>>>(static_cast<const double *>(d->c_G), d->D[d->cur], nf, m, d->c_W);
+  contact_rhs_kernel<<<unsigned((m + 255) / 256), 256, 0, s>>>(d->c_node, d->c_normal, d->c_off, d->q, d->v, d->x,
+                                                               c->h, m, d->c_rhs);
   pgs_kernel<<<1, 32, 0, s>>>(d->c_W, d->c_rhs, d->c_lam, m, c->opt.contact_sweeps, c->opt.contact_tol);
-  contact_correct_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(d->c_Z, d->c_lam, n, m, d->x);
-  d->launches += 3;
+  // motion correction: a += P^{-1} H^T lambda (one full application)
+  FE_CUDA_TRY(cudaMemsetAsync(d->vr, 0, size_t(n) * ts, s));
+  if (fp32)
+    contact_force_kernel<float><<<1, 32, 0, s>>>(static_cast<float *>(d->vr), d->c_node, d->c_normal, d->c_lam, m);
+  else
+    contact_force_kernel<double><<<1, 32, 0, s>>>(static_cast<double *>(d->vr), d->c_node, d->c_normal, d->c_lam, m);
+  apply_enqueue(c, d, d->cur, fp32, d->vr, d->vz, s);
+  if (fp32)
+    add_vector_kernel<float><<<unsigned((n + 255) / 256), 256, 0, s>>>(d->x, static_cast<const float *>(d->vz), n);
+  else
+    add_vector_kernel<double><<<unsigned((n + 255) / 256), 256, 0, s>>>(d->x, static_cast<const double *>(d->vz), n);
+  d->launches += 5;  // W, right-hand side, PGS, H^T lambda, a += z (the applications count their own)
   FE_CUDA_TRY(cudaGetLastError());
   return FE_OK;
 }

@@ -103,10 +103,11 @@ struct DeviceState {
   // front over all rows of Y[0] then Y[1] (128 x 16 boxes); null for the
   // FP64 factor
   void *tmaps = nullptr;
-  // contacts (fe_contact.cu): constraint data, Z = P^{-1} H^T (n x m,
-  // column-major), compliance W (m x m), PGS right-hand side and multipliers
+  // contacts (fe_contact.cu): constraint data, forward solves G, compliance
+  // W (m x m), PGS right-hand side and multipliers
   int32_t *c_node = nullptr;
-  double *c_normal = nullptr, *c_off = nullptr, *c_Z = nullptr, *c_W = nullptr, *c_rhs = nullptr, *c_lam = nullptr;
+  double *c_normal = nullptr, *c_off = nullptr, *c_W = nullptr, *c_rhs = nullptr, *c_lam = nullptr;
+  void *c_G = nullptr;  // forward solves D^{-1} L^{-1} H^T e_i, [m][n_free] in the solve's precision
   int64_t c_cap = 0, c_m = 0;
   bool c_dirty = true;  // the context's constraint set changed since the last upload
   double *D[2] = {nullptr, nullptr};
@@ -235,6 +236,9 @@ int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Af
 // contacts (fe_contact.cu): constraint resolution and motion correction of
 // the current step (d->x: a_free in, corrected a out)
 int contact_resolve(fe_ctx *c, DeviceState *d, bool fp32);
+// forward solve only (fe_factor.cu): yp [n_free] = D^{-1} L^{-1} r, pivot order
+void apply_forward_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *yp,
+                           cudaStream_t s);
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
                    cudaStream_t s, const double *done = nullptr);
 

@@ -1574,10 +1574,25 @@ int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Af
   return FE_OK;
 }
 
+// What a backward launch resets for the following forward launch (the
+// pending-children counters, the forward completion counters and the forward
+// queue and abort words), for a forward-only application.
+__global__ void dataflow_reset_kernel(const DFront *__restrict__ fronts, int *pend, int *fdone, int *ctl,
+                                      int nfronts) {
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < nfronts; i += gridDim.x * 256) {
+    pend[i] = fronts[i].child_end - fronts[i].child_begin;
+    fdone[i] = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl[0] = 0;
+    ctl[2] = 0;
+  }
+}
+
 template <typename TF, typename TV>
 static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, TV *u, TV *yp,
                               TV *part_f, TV *part_b, int *tick_f, int *tick_b, cudaStream_t s,
-                              const double *done = nullptr) {
+                              const double *done = nullptr, bool forward_only = false) {
   const TF *Y = reinterpret_cast<const TF *>(sizeof(TF) == 2 ? d->Yh[buf] : d->Y[buf]);
   const double *Dinv = d->D[buf] + c->n_free;
   const int nf = int(c->fronts.size());
@@ -1595,6 +1610,11 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
   fwd_kernel<TF, TV><<<gf, 256, 0, s>>>(reinterpret_cast<const int4 *>(d->apply_fwd), d->n_apply_fwd, d->fronts, Y,
                                         Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp, part_f, tick_f, d->df_pend,
                                         d->df_fdone, d->df_bdone, d->df_ctl, nf, d->flags, done);
+  if (forward_only) {
+    dataflow_reset_kernel<<<unsigned(std::min(1024, (nf + 255) / 256)), 256, 0, s>>>(d->fronts, d->df_pend,
+                                                                                      d->df_fdone, d->df_ctl, nf);
+    return;
+  }
   bwd_kernel<TF, TV><<<gb, 256, 0, s>>>(reinterpret_cast<const int4 *>(d->apply_bwd), d->n_apply_bwd, d->fronts, Y,
                                         d->perm, d->upd_rows_old, yp, z, part_b, tick_b, d->df_pend, d->df_fdone,
                                         d->df_bdone, d->df_ctl, nf, d->flags, done);
@@ -1606,6 +1626,25 @@ static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const T
   apply_levels_with<TF, TV>(c, d, buf, r, z, reinterpret_cast<TV *>(d->ubuf), reinterpret_cast<TV *>(d->yperm),
                             reinterpret_cast<TV *>(d->part_f), reinterpret_cast<TV *>(d->part_b), d->tick_f,
                             d->tick_b, s, done);
+}
+
+// Forward solve only: yp [n_free] = D^{-1} L^{-1} r in the pivot order
+// (the forward sweep's pivot output), for the compliance of contacts.
+void apply_forward_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *yp,
+                           cudaStream_t s) {
+  if (fp32 && c->opt.precond_fp16)
+    apply_levels_with<__half, float>(c, d, buf, static_cast<const float *>(r), nullptr, static_cast<float *>(d->ubuf),
+                                     static_cast<float *>(yp), static_cast<float *>(d->part_f),
+                                     static_cast<float *>(d->part_b), d->tick_f, d->tick_b, s, nullptr, true);
+  else if (fp32)
+    apply_levels_with<float, float>(c, d, buf, static_cast<const float *>(r), nullptr, static_cast<float *>(d->ubuf),
+                                    static_cast<float *>(yp), static_cast<float *>(d->part_f),
+                                    static_cast<float *>(d->part_b), d->tick_f, d->tick_b, s, nullptr, true);
+  else
+    apply_levels_with<double, double>(c, d, buf, static_cast<const double *>(r), nullptr,
+                                      static_cast<double *>(d->ubuf), static_cast<double *>(yp),
+                                      static_cast<double *>(d->part_f), static_cast<double *>(d->part_b), d->tick_f,
+                                      d->tick_b, s, nullptr, true);
 }
 
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
