@@ -1229,6 +1229,7 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     // the children's update vectors must be complete
     if (threadIdx.x == 0) s_ok = dep_wait(pend + t.x, 0, ctl + 2, flags);
     __syncthreads();
+    bool wnz = false;
     if (s_ok) {
       if (jg < j1) {
         TV w = r[gperm];
@@ -1237,6 +1238,7 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
           if (gsrc[k] >= 0) w += __ldcg(ubuf + gsrc[k]);
         for (int32_t q = gq0 + kPre; q < gq1; ++q) w += __ldcg(ubuf + wsrc[q]);
         wp[jg - j0] = w;
+        wnz = w != TV(0);
       }
     }
     TV csum = TV(0);
@@ -1246,11 +1248,14 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
         if (esrc[k] >= 0) csum += __ldcg(ubuf + esrc[k]);
       for (int32_t q = eq0 + kPre; q < eq1; ++q) csum += __ldcg(ubuf + wsrc[q]);
     }
-    __syncthreads();
+    // a block whose gathered w is all zero contributes exactly nothing (a
+    // sparse right-hand side, such as a contact's column, leaves most fronts
+    // at zero): Y is not streamed then
+    const bool wany = __syncthreads_or(wnz) != 0;
     TV acc[VW];
 #pragma unroll
     for (int e = 0; e < VW; ++e) acc[e] = TV(0);
-    if (s_ok && live) {
+    if (s_ok && live && wany) {
       for (;;) {
         TV wv[kFwdU];
 #pragma unroll
@@ -1438,15 +1443,20 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
     if (threadIdx.x == 0)
       s_ok = fr.parent < 0 ? 1 : dep_wait(bdone + fr.parent, fronts[fr.parent].nbwd, ctl + 3, flags);
     __syncthreads();
+    bool xnz = false;
 #pragma unroll
     for (int k = 0; k < XS; ++k) {
       const int32_t tt = int32_t(threadIdx.x) + 256 * k;
-      if (tt < xb - xa)
-        xs[tt] = (xsrc[k] == -1 || !s_ok) ? TV(0) : (xsrc[k] >= 0 ? yperm[xsrc[k]] : __ldcg(z + (-2 - xsrc[k])));
+      if (tt < xb - xa) {
+        const TV xv = (xsrc[k] == -1 || !s_ok) ? TV(0) : (xsrc[k] >= 0 ? yperm[xsrc[k]] : __ldcg(z + (-2 - xsrc[k])));
+        xs[tt] = xv;
+        xnz = xnz || xv != TV(0);
+      }
     }
-    __syncthreads();
+    // an all-zero x contributes exactly nothing: Y is not streamed then
+    const bool xany = __syncthreads_or(xnz) != 0;
     TV acc[4] = {TV(0), TV(0), TV(0), TV(0)};
-    for (int32_t off = 0;;) {
+    for (int32_t off = 0; xany;) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int32_t i = ist + off + 32 * VW * h;
