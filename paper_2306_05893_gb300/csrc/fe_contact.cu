@@ -25,6 +25,7 @@ namespace fe {
 namespace {
 
 constexpr int kMaxContacts = 4096;  // multipliers kept in shared memory by the solver (32 KB)
+constexpr int kRhsPerLaunch = 64;   // right-hand sides per forward launch (the front id's high byte)
 
 // RHS of constraint i in the preconditioner's precision: n_i on node i's DOFs
 // (the vector is cleared before)
@@ -32,6 +33,17 @@ template <typename T>
 __global__ void contact_column_kernel(T *r, const int32_t *__restrict__ node, const double *__restrict__ normal,
                                       int i) {
   if (threadIdx.x < 3) r[3 * int64_t(node[i]) + threadIdx.x] = T(normal[3 * i + threadIdx.x]);
+}
+
+// The right-hand sides H^T e_i of constraints i = i0 + k, k < nrhs (and
+// i < m), into the vectors r + k n (cleared before)
+template <typename T>
+__global__ void contact_group_kernel(T *r, int64_t n, const int32_t *__restrict__ node,
+                                     const double *__restrict__ normal, int i0, int m, int nrhs) {
+  const int k = threadIdx.x;
+  const int i = i0 + k;
+  if (k >= nrhs || i >= m) return;
+  for (int j = 0; j < 3; ++j) r[int64_t(k) * n + 3 * int64_t(node[i]) + j] = T(normal[3 * i + j]);
 }
 
 // W[i m + j] = W[j m + i] = sum_k G_i[k] d_k G_j[k] (block (i, j), j >= i;
@@ -159,11 +171,11 @@ static int contact_upload(fe_ctx *c, DeviceState *d) {
     int st = regrow(c, d, reinterpret_cast<void **>(&d->c_node), size_t(cap) * sizeof(int32_t));
     if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_normal), size_t(3 * cap) * sizeof(double));
     if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_off), size_t(cap) * sizeof(double));
-    const size_t ts = c->opt.precision == FE_MIXED ? sizeof(float) : sizeof(double);
-    if (!st) st = regrow(c, d, &d->c_G, size_t(cap) * size_t(std::max<int64_t>(c->n_free, 1)) * ts);
     if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_W), size_t(cap) * size_t(cap) * sizeof(double));
     if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_rhs), size_t(cap) * sizeof(double));
     if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_lam), size_t(cap) * sizeof(double));
+    if (!st && !d->c_pend)
+      st = regrow(c, d, reinterpret_cast<void **>(&d->c_pend), std::max<size_t>(c->fronts.size(), 1) * sizeof(int));
     if (st) {
       d->c_cap = 0;
       return st;
@@ -176,6 +188,59 @@ static int contact_upload(fe_ctx *c, DeviceState *d) {
                            cudaMemcpyHostToDevice));
     FE_CUDA_TRY(cudaMemcpy(d->c_off, c->contact_offset.data(), size_t(m) * sizeof(double), cudaMemcpyHostToDevice));
     FE_CUDA_TRY(cudaMemset(d->c_lam, 0, size_t(m) * sizeof(double)));
+  }
+  // the fronts on the constraints' paths to the root (a right-hand side
+  // H^T e_i is zero outside them, so their forward solve stays there), their
+  // tasks in the forward list's (topological) order and their numbers of
+  // children on the paths
+  if (m > 0) {
+    const int64_t nf = int64_t(c->fronts.size());
+    std::vector<int32_t> piv_front(size_t(std::max<int64_t>(c->n_free, 1)), -1);
+    for (int64_t f = 0; f < nf; ++f)
+      for (int32_t k = 0; k < c->fronts[f].npiv; ++k) piv_front[size_t(c->fronts[f].first + k)] = int32_t(f);
+    std::vector<char> on(size_t(nf), 0);
+    for (int64_t i = 0; i < m; ++i)
+      for (int k = 0; k < 3; ++k) {
+        const int32_t piv = c->iperm[3 * int64_t(c->contact_node[i]) + k];
+        for (int32_t f = piv >= 0 ? piv_front[piv] : -1; f >= 0 && !on[f]; f = c->fronts[f].parent) on[f] = 1;
+      }
+    std::vector<int32_t> sub;
+    for (size_t t = 0; t + 3 < c->apply_fwd.size(); t += 4)
+      if (on[c->apply_fwd[t]]) sub.insert(sub.end(), c->apply_fwd.begin() + t, c->apply_fwd.begin() + t + 4);
+    std::vector<int> pend(size_t(nf), 0);
+    for (int64_t f = 0; f < nf; ++f)
+      if (on[f] && c->fronts[f].parent >= 0) pend[c->fronts[f].parent]++;
+    // the right-hand sides of one launch (at most kRhsPerLaunch; the task's
+    // right-hand side rides in the front id's high byte), each subset task
+    // repeated for them in order (the list stays topological)
+    const int nr = int(std::min<int64_t>(m, kRhsPerLaunch));
+    std::vector<int32_t> multi;
+    multi.reserve(sub.size() * size_t(nr));
+    for (size_t t = 0; t + 3 < sub.size(); t += 4)
+      for (int k = 0; k < nr; ++k) {
+        multi.push_back(sub[t] | (k << 24));
+        multi.insert(multi.end(), sub.begin() + t + 1, sub.begin() + t + 4);
+      }
+    const size_t ts = c->opt.precision == FE_MIXED ? sizeof(float) : sizeof(double);
+    const int64_t groups = (m + nr - 1) / nr;
+    const size_t slots = size_t(std::max<int64_t>(c->fwd_slots, 1));
+    int st = regrow(c, d, reinterpret_cast<void **>(&d->c_tasks), std::max<size_t>(multi.size(), 4) * sizeof(int32_t));
+    if (!st) st = regrow(c, d, &d->c_G, size_t(groups * nr) * size_t(std::max<int64_t>(c->n_free, 1)) * ts);
+    if (!st) st = regrow(c, d, &d->c_r, size_t(nr) * size_t(c->n) * ts);
+    if (!st) st = regrow(c, d, &d->c_u, size_t(nr) * size_t(std::max<int64_t>(c->u_total, 1)) * ts);
+    if (!st) st = regrow(c, d, &d->c_part, size_t(nr) * slots * size_t(fwd_rows(c->opt)) * ts);
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_tick), size_t(nr) * slots * sizeof(int));
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_pendm), size_t(nr) * size_t(nf) * sizeof(int));
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_fdm), size_t(nr) * size_t(nf) * sizeof(int));
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_bdm), size_t(nf) * sizeof(int));
+    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_ctl), 4 * sizeof(int));
+    if (st) return st;
+    if (!multi.empty())
+      FE_CUDA_TRY(cudaMemcpy(d->c_tasks, multi.data(), multi.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    FE_CUDA_TRY(cudaMemcpy(d->c_pend, pend.data(), pend.size() * sizeof(int), cudaMemcpyHostToDevice));
+    FE_CUDA_TRY(cudaMemset(d->c_tick, 0, size_t(nr) * slots * sizeof(int)));
+    d->c_ntask = int64_t(multi.size() / 4);
+    d->c_nrhs = nr;
   }
   d->c_m = m;
   d->c_dirty = false;
@@ -195,14 +260,25 @@ int contact_resolve(fe_ctx *c, DeviceState *d, bool fp32) {
   if (m == 0) return FE_OK;
   const int64_t n = c->n, nf = c->n_free;
   const size_t ts = fp32 ? sizeof(float) : sizeof(double);
-  // G_i = D^{-1} L^{-1} H^T e_i: one forward solve per constraint
-  for (int i = 0; i < m; ++i) {
-    FE_CUDA_TRY(cudaMemsetAsync(d->vr, 0, size_t(n) * ts, s));
+  // G_i = D^{-1} L^{-1} H^T e_i: the forward solves of up to kRhsPerLaunch
+  // constraints per launch, over the fronts on the constraints' paths only
+  // (G and the update vectors outside them stay at the zeros written here)
+  const int nr = int(d->c_nrhs);
+  const int64_t groups = (m + nr - 1) / nr;
+  FE_CUDA_TRY(cudaMemsetAsync(d->c_G, 0, size_t(groups * nr) * size_t(nf) * ts, s));
+  for (int64_t gi = 0; gi < groups; ++gi) {
+    FE_CUDA_TRY(cudaMemsetAsync(d->c_r, 0, size_t(nr) * size_t(n) * ts, s));
+    FE_CUDA_TRY(cudaMemsetAsync(d->c_u, 0, size_t(nr) * size_t(std::max<int64_t>(c->u_total, 1)) * ts, s));
     if (fp32)
-      contact_column_kernel<float><<<1, 32, 0, s>>>(static_cast<float *>(d->vr), d->c_node, d->c_normal, i);
+      contact_group_kernel<float><<<1, kRhsPerLaunch, 0, s>>>(static_cast<float *>(d->c_r), n, d->c_node,
+                                                             d->c_normal, int(gi * nr), m, nr);
     else
-      contact_column_kernel<double><<<1, 32, 0, s>>>(static_cast<double *>(d->vr), d->c_node, d->c_normal, i);
-    apply_forward_enqueue(c, d, d->cur, fp32, d->vr, static_cast<unsigned char *>(d->c_G) + size_t(i) * nf * ts, s);
+      contact_group_kernel<double><<<1, kRhsPerLaunch, 0, s>>>(static_cast<double *>(d->c_r), n, d->c_node,
+                                                              d->c_normal, int(gi * nr), m, nr);
+    apply_forward_multi_enqueue(c, d, d->cur, fp32, d->c_r,
+                                static_cast<unsigned char *>(d->c_G) + size_t(gi * nr) * size_t(nf) * ts, d->c_tasks,
+                                d->c_ntask, d->c_pend, d->c_pendm, d->c_fdm, d->c_bdm, d->c_ctl, d->c_u, d->c_part,
+                                d->c_tick, nr, s);
     d->launches += 1;
   }
   // W = G^T D G, the PGS right-hand side, the multipliers

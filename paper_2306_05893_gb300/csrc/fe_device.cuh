@@ -108,6 +108,15 @@ struct DeviceState {
   int32_t *c_node = nullptr;
   double *c_normal = nullptr, *c_off = nullptr, *c_W = nullptr, *c_rhs = nullptr, *c_lam = nullptr;
   void *c_G = nullptr;  // forward solves D^{-1} L^{-1} H^T e_i, [m][n_free] in the solve's precision
+  // the fronts on the constraints' paths to the root: their forward tasks
+  // (topological order, each repeated for the c_nrhs right-hand sides of a
+  // launch) and their numbers of children on the paths; per right-hand side
+  // of a launch: input vectors, update vectors, partial sums, tickets,
+  // counters; the launch's control words
+  int32_t *c_tasks = nullptr;
+  int *c_pend = nullptr, *c_pendm = nullptr, *c_fdm = nullptr, *c_bdm = nullptr, *c_ctl = nullptr, *c_tick = nullptr;
+  void *c_r = nullptr, *c_u = nullptr, *c_part = nullptr;
+  int64_t c_ntask = 0, c_nrhs = 0;
   int64_t c_cap = 0, c_m = 0;
   bool c_dirty = true;  // the context's constraint set changed since the last upload
   double *D[2] = {nullptr, nullptr};
@@ -236,9 +245,11 @@ int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Af
 // contacts (fe_contact.cu): constraint resolution and motion correction of
 // the current step (d->x: a_free in, corrected a out)
 int contact_resolve(fe_ctx *c, DeviceState *d, bool fp32);
-// forward solve only (fe_factor.cu): yp [n_free] = D^{-1} L^{-1} r, pivot order
-void apply_forward_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *yp,
-                           cudaStream_t s);
+// forward solves of nrhs right-hand sides in one launch over a subset of
+// fronts closed under parents (fe_factor.cu)
+void apply_forward_multi_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *yp,
+                                 const int32_t *tasks, int64_t ntask, const int *pend_init, int *pend, int *fdone,
+                                 int *bdone, int *ctl, void *u, void *part, int *tickets, int nrhs, cudaStream_t s);
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
                    cudaStream_t s, const double *done = nullptr);
 

@@ -1137,6 +1137,13 @@ constexpr int kPre = 4;  // gather sources prefetched per position
 // the lowest unfinished task is always a CTA's current task, and its
 // dependencies are finished.)
 static_assert(sizeof(DFront) == 96, "the descriptor is copied as six 16-byte pieces");
+
+// Element strides between the right-hand sides of a multi-right-hand-side
+// forward solve (all zero for a single one): input vector, update vectors,
+// pivot output, partial sums, tickets, per-front counters.
+struct RhsStrides {
+  int64_t r, u, y, p, t, f;
+};
 struct NextDesc {
   int4 t, f;
 };
@@ -1145,7 +1152,7 @@ __device__ __forceinline__ NextDesc load_desc(const int4 *__restrict__ tasks, co
   NextDesc d{};
   if (tn < ntask && lane < 6) {
     d.t = tasks[tn];
-    d.f = reinterpret_cast<const int4 *>(fronts + d.t.x)[lane];
+    d.f = reinterpret_cast<const int4 *>(fronts + (d.t.x & 0xffffff))[lane];
   }
   return d;
 }
@@ -1165,7 +1172,8 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
                                                   TV *__restrict__ ubuf, TV *__restrict__ yperm,
                                                   TV *__restrict__ part, int *__restrict__ tickets,
                                                   int *pend, int *fdone, int *bdone, int *ctl, int nfronts,
-                                                  int *flags, const double *__restrict__ done) {
+                                                  int *flags, const double *__restrict__ done,
+                                                  RhsStrides rs = RhsStrides{}) {
   static_assert(kFwdCols == 256, "one gathered column per thread");
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
@@ -1193,6 +1201,17 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     const DFront fr = s_fr;
     if (threadIdx.x == 0) s_next = atomicAdd(ctl + 0, 1);  // the next task, one ahead
     const int32_t r0 = t.y, j0 = t.z, slot = t.w;
+    // a multi-right-hand-side list carries the right-hand side in the front
+    // id's high byte: its vectors, partial sums and counters are offset
+    const int32_t fid = t.x & 0xffffff;
+    const int64_t rk = t.x >> 24;
+    const TV *const rv = r + rk * rs.r;
+    TV *const uv = ubuf + rk * rs.u;
+    TV *const yv = yperm + rk * rs.y;
+    TV *const pv = part + rk * rs.p;
+    int *const tv = tickets + rk * rs.t;
+    int *const pendv = pend + rk * rs.f;
+    int *const fdonev = fdone + rk * rs.f;
     const int32_t p = fr.npiv, m = fr.m;
     const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
     const int32_t j1 = (j0 + kFwdCols < jmax) ? j0 + kFwdCols : jmax;
@@ -1227,16 +1246,16 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     for (int u = 0; u < kFwdU; ++u)
       cv[u] = (live && jq + 8 * u < j1) ? *reinterpret_cast<const V *>(yc + int64_t(jq + 8 * u) * fr.ldy) : V{};
     // the children's update vectors must be complete
-    if (threadIdx.x == 0) s_ok = dep_wait(pend + t.x, 0, ctl + 2, flags);
+    if (threadIdx.x == 0) s_ok = dep_wait(pendv + fid, 0, ctl + 2, flags);
     __syncthreads();
     bool wnz = false;
     if (s_ok) {
       if (jg < j1) {
-        TV w = r[gperm];
+        TV w = rv[gperm];
 #pragma unroll
         for (int k = 0; k < kPre; ++k)
-          if (gsrc[k] >= 0) w += __ldcg(ubuf + gsrc[k]);
-        for (int32_t q = gq0 + kPre; q < gq1; ++q) w += __ldcg(ubuf + wsrc[q]);
+          if (gsrc[k] >= 0) w += __ldcg(uv + gsrc[k]);
+        for (int32_t q = gq0 + kPre; q < gq1; ++q) w += __ldcg(uv + wsrc[q]);
         wp[jg - j0] = w;
         wnz = w != TV(0);
       }
@@ -1245,8 +1264,8 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     if (s_ok) {
 #pragma unroll
       for (int k = 0; k < kPre; ++k)
-        if (esrc[k] >= 0) csum += __ldcg(ubuf + esrc[k]);
-      for (int32_t q = eq0 + kPre; q < eq1; ++q) csum += __ldcg(ubuf + wsrc[q]);
+        if (esrc[k] >= 0) csum += __ldcg(uv + esrc[k]);
+      for (int32_t q = eq0 + kPre; q < eq1; ++q) csum += __ldcg(uv + wsrc[q]);
     }
     // a block whose gathered w is all zero contributes exactly nothing (a
     // sparse right-hand side, such as a contact's column, leaves most fronts
@@ -1294,16 +1313,16 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
 #pragma unroll
       for (int k = 0; k < (RB + 255) / 256; ++k) {
         const int tt = threadIdx.x + 256 * k;
-        if (tt < RB) part[int64_t(slot + j0 / kFwdCols) * RB + tt] = sums[k];
+        if (tt < RB) pv[int64_t(slot + j0 / kFwdCols) * RB + tt] = sums[k];
       }
-      final = last_of_block(tickets + slot, nch);
+      final = last_of_block(tv + slot, nch);
       if (final) {
 #pragma unroll
         for (int k = 0; k < (RB + 255) / 256; ++k) {
           const int tt = threadIdx.x + 256 * k;
           TV sm = TV(0);
           if (tt < RB)
-            for (int ch = 0; ch < nch; ++ch) sm += __ldcg(part + int64_t(slot + ch) * RB + tt);
+            for (int ch = 0; ch < nch; ++ch) sm += __ldcg(pv + int64_t(slot + ch) * RB + tt);
           sums[k] = sm;
         }
       }
@@ -1315,9 +1334,9 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
         const int32_t i = r0 + tt;
         if (tt >= RB || i >= m) continue;
         if (i < p)
-          yperm[fr.first + i] = TV(double(sums[k]) * Dinv[fr.first + i]);
+          yv[fr.first + i] = TV(double(sums[k]) * Dinv[fr.first + i]);
         else
-          ubuf[fr.u_off + i - p] = csum + sums[k];
+          uv[fr.u_off + i - p] = csum + sums[k];
       }
     }
     // completion: the front's last task releases the parent (ordered
@@ -1326,8 +1345,8 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     // its release of the parent's counter)
     __syncthreads();
     if (threadIdx.x == 0) {
-      const int c = atom_add_acq_rel(fdone + t.x, 1);
-      if (c == fr.nfwd - 1 && fr.parent >= 0) red_add_release(pend + fr.parent, -1);
+      const int c = atom_add_acq_rel(fdonev + fid, 1);
+      if (c == fr.nfwd - 1 && fr.parent >= 0) red_add_release(pendv + fr.parent, -1);
       s_task = s_next;
     }
     if (threadIdx.x < 32) store_desc(nd, s_t, s_fr, threadIdx.x);
@@ -1584,25 +1603,22 @@ int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Af
   return FE_OK;
 }
 
-// What a backward launch resets for the following forward launch (the
-// pending-children counters, the forward completion counters and the forward
-// queue and abort words), for a forward-only application.
-__global__ void dataflow_reset_kernel(const DFront *__restrict__ fronts, int *pend, int *fdone, int *ctl,
-                                      int nfronts) {
-  for (int i = blockIdx.x * 256 + threadIdx.x; i < nfronts; i += gridDim.x * 256) {
-    pend[i] = fronts[i].child_end - fronts[i].child_begin;
+// The per-right-hand-side forward counters of a multi-right-hand-side
+// launch set to the subset's own dependencies, and its control words cleared
+// (see apply_forward_multi_enqueue).
+__global__ void multi_reset_kernel(const int *__restrict__ pend_init, int *pend, int *fdone, int *ctl, int nfronts,
+                                   int64_t total) {
+  for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < total; i += int64_t(gridDim.x) * 256) {
+    pend[i] = pend_init[i % nfronts];
     fdone[i] = 0;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl[0] = 0;
-    ctl[2] = 0;
-  }
+  if (blockIdx.x == 0 && threadIdx.x < 4) ctl[threadIdx.x] = 0;
 }
 
 template <typename TF, typename TV>
 static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, TV *u, TV *yp,
                               TV *part_f, TV *part_b, int *tick_f, int *tick_b, cudaStream_t s,
-                              const double *done = nullptr, bool forward_only = false) {
+                              const double *done = nullptr) {
   const TF *Y = reinterpret_cast<const TF *>(sizeof(TF) == 2 ? d->Yh[buf] : d->Y[buf]);
   const double *Dinv = d->D[buf] + c->n_free;
   const int nf = int(c->fronts.size());
@@ -1620,11 +1636,6 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
   fwd_kernel<TF, TV><<<gf, 256, 0, s>>>(reinterpret_cast<const int4 *>(d->apply_fwd), d->n_apply_fwd, d->fronts, Y,
                                         Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp, part_f, tick_f, d->df_pend,
                                         d->df_fdone, d->df_bdone, d->df_ctl, nf, d->flags, done);
-  if (forward_only) {
-    dataflow_reset_kernel<<<unsigned(std::min(1024, (nf + 255) / 256)), 256, 0, s>>>(d->fronts, d->df_pend,
-                                                                                      d->df_fdone, d->df_ctl, nf);
-    return;
-  }
   bwd_kernel<TF, TV><<<gb, 256, 0, s>>>(reinterpret_cast<const int4 *>(d->apply_bwd), d->n_apply_bwd, d->fronts, Y,
                                         d->perm, d->upd_rows_old, yp, z, part_b, tick_b, d->df_pend, d->df_fdone,
                                         d->df_bdone, d->df_ctl, nf, d->flags, done);
@@ -1638,23 +1649,50 @@ static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const T
                             d->tick_b, s, done);
 }
 
-// Forward solve only: yp [n_free] = D^{-1} L^{-1} r in the pivot order
-// (the forward sweep's pivot output), for the compliance of contacts.
-void apply_forward_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *yp,
-                           cudaStream_t s) {
+// Forward solves of nrhs right-hand sides in one launch, over a subset of
+// the fronts (closed under taking parents) outside which every right-hand
+// side is zero.  tasks: the subset's forward tasks in topological order, each
+// repeated for the right-hand sides k < nrhs with k in the front id's high
+// byte; every right-hand side k has its own input r + k n, pivot output
+// yp + k n_free, update vectors u + k u_total, partial sums, tickets and
+// per-front counters (pend, fdone: nf each, pend set from pend_init, the
+// number of each front's children in the subset), and the launch has its
+// own control words, so the context's application state is not touched.  The
+// caller clears yp and u once (outside the subset they stay zero) and the
+// tickets once (the last CTA of a split block resets its ticket).
+void apply_forward_multi_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *yp,
+                                 const int32_t *tasks, int64_t ntask, const int *pend_init, int *pend, int *fdone,
+                                 int *bdone, int *ctl, void *u, void *part, int *tickets, int nrhs, cudaStream_t s) {
+  const int nf = int(c->fronts.size());
+  const int64_t total = int64_t(nf) * nrhs;
+  multi_reset_kernel<<<unsigned(std::min<int64_t>(1024, (total + 255) / 256)), 256, 0, s>>>(pend_init, pend, fdone,
+                                                                                           ctl, nf, total);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device);
+  const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(ntask, int64_t(sms) * 4)));
+  const int4 *tk = reinterpret_cast<const int4 *>(tasks);
+  const double *Dinv = d->D[buf] + c->n_free;
+  const RhsStrides rs{c->n, std::max<int64_t>(c->u_total, 1), c->n_free,
+                      std::max<int64_t>(c->fwd_slots, 1) * fwd_rows(c->opt), std::max<int64_t>(c->fwd_slots, 1), nf};
+  d->launches += 2;
   if (fp32 && c->opt.precond_fp16)
-    apply_levels_with<__half, float>(c, d, buf, static_cast<const float *>(r), nullptr, static_cast<float *>(d->ubuf),
-                                     static_cast<float *>(yp), static_cast<float *>(d->part_f),
-                                     static_cast<float *>(d->part_b), d->tick_f, d->tick_b, s, nullptr, true);
+    fwd_kernel<__half, float><<<g, 256, 0, s>>>(tk, ntask, d->fronts, static_cast<const __half *>(d->Yh[buf]), Dinv,
+                                                d->perm, d->wsrc_ptr, d->wsrc, static_cast<const float *>(r),
+                                                static_cast<float *>(u), static_cast<float *>(yp),
+                                                static_cast<float *>(part), tickets, pend, fdone, bdone, ctl, nf,
+                                                d->flags, nullptr, rs);
   else if (fp32)
-    apply_levels_with<float, float>(c, d, buf, static_cast<const float *>(r), nullptr, static_cast<float *>(d->ubuf),
-                                    static_cast<float *>(yp), static_cast<float *>(d->part_f),
-                                    static_cast<float *>(d->part_b), d->tick_f, d->tick_b, s, nullptr, true);
+    fwd_kernel<float, float><<<g, 256, 0, s>>>(tk, ntask, d->fronts, static_cast<const float *>(d->Y[buf]), Dinv,
+                                               d->perm, d->wsrc_ptr, d->wsrc, static_cast<const float *>(r),
+                                               static_cast<float *>(u), static_cast<float *>(yp),
+                                               static_cast<float *>(part), tickets, pend, fdone, bdone, ctl, nf,
+                                               d->flags, nullptr, rs);
   else
-    apply_levels_with<double, double>(c, d, buf, static_cast<const double *>(r), nullptr,
-                                      static_cast<double *>(d->ubuf), static_cast<double *>(yp),
-                                      static_cast<double *>(d->part_f), static_cast<double *>(d->part_b), d->tick_f,
-                                      d->tick_b, s, nullptr, true);
+    fwd_kernel<double, double><<<g, 256, 0, s>>>(tk, ntask, d->fronts, static_cast<const double *>(d->Y[buf]), Dinv,
+                                                 d->perm, d->wsrc_ptr, d->wsrc, static_cast<const double *>(r),
+                                                 static_cast<double *>(u), static_cast<double *>(yp),
+                                                 static_cast<double *>(part), tickets, pend, fdone, bdone, ctl, nf,
+                                                 d->flags, nullptr, rs);
 }
 
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
