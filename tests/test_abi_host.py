@@ -153,3 +153,37 @@ def test_device_calls_fail_loudly_without_gpu(fe):
         ctx.step(np.zeros(ctx.n))
     assert ei.value.status == 2
     ctx.close()
+
+
+def test_contact_arguments_checked_on_the_host(fe):
+    """fe_set_contacts validates on the host (no device needed): node range,
+    zero normals, non-finite offsets, the contact count limit, and the
+    combinations the contact step does not cover (checkpoints, Newton)."""
+    mesh = fi.tet_beam(1, 1, 2)
+    ctx = _ctx(fe, mesh)
+    ok_nodes, ok_normals, ok_offsets = [mesh.n_nodes - 1], [[0.0, 0.0, 1.0]], [-0.01]
+    ctx.set_contacts(ok_nodes, ok_normals, ok_offsets)
+    for nodes, normals, offsets in (([mesh.n_nodes], ok_normals, ok_offsets),
+                                    ([-1], ok_normals, ok_offsets),
+                                    (ok_nodes, [[0.0, 0.0, 0.0]], ok_offsets),
+                                    (ok_nodes, ok_normals, [float("nan")])):
+        with pytest.raises(fe.FEError) as ei:
+            ctx.set_contacts(nodes, normals, offsets)
+        assert ei.value.status == 1
+    many = np.zeros(4097, np.int32)
+    with pytest.raises(fe.FEError):
+        ctx.set_contacts(many, np.tile([0.0, 0.0, 1.0], (4097, 1)), np.zeros(4097))
+    ctx.set_contacts(np.zeros(0, np.int32), np.zeros((0, 3)), np.zeros(0))  # removing them is fine
+    ctx.close()
+    for kw in ({"keep_checkpoints": 1}, {"newton_iters": 2}):
+        c2 = _ctx(fe, mesh, **kw)
+        with pytest.raises(fe.FEError) as ei:
+            c2.set_contacts(ok_nodes, ok_normals, ok_offsets)
+        assert ei.value.status == 9
+        c2.close()
+
+
+def test_contact_option_defaults(fe):
+    o = fe.options()
+    assert o.contact_sweeps == 200 and o.contact_tol == 1e-12
+    assert o.precond_fp16 == 0 and o.factor_tf32 == 0
