@@ -605,35 +605,42 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
 //
 // Blackwell tensor cores (tcgen05, kind::tf32) with a 3xTF32 split
 // (a = a_hi + a_lo, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) so products keep
-// ~FP32 accuracy, fed by the TMA unit, with warp-specialised roles:
-//  * warp 8 (producer and MMA issuer) keeps a ring of 5-6 raw K chunks
-//    (16 columns each) in flight: per chunk one tensor-map load of the
-//    128 x 16 A tile (F rows i0.., columns k..k + 16, rows contiguous) and
-//    either the 128 x 16 B tile of F (TRAIL) or four 4 x 128 boxes of Y
-//    (RUPD: pivot rows k.. of columns j0.., which land directly in the
-//    operand layout), plus the chunk's d_l, completing on the stage's
-//    mbarrier; it issues each chunk's MMAs (M = N = 128, K = 8 each) into a
-//    128 x 128 FP32 accumulator in tensor memory once the operands are
-//    ready, commits them to the operand stage's mbarrier, and refills the
-//    raw stage just consumed;
-//  * warps 0-7 turn raw chunk q into the MMA operands: the TF32 high and
-//    low parts (B scaled by d_l for TRAIL, columns at or past the task's K
-//    end zeroed) in the K-major, no-swizzle core-matrix layout (8 rows x 16
-//    bytes per core matrix; 128 B between 8-row groups, 2048 B between
-//    4-column K groups), into one of two operand stages, so the conversion
-//    of chunk q overlaps the MMAs of chunk q - 1.  A thread reads 4 columns
-//    of one row from the raw tile (consecutive rows across a warp: no bank
-//    conflicts) and writes them as one 16-byte vector (consecutive slots).
+// ~FP32 accuracy, fed by the TMA unit, with warp-specialised roles (320
+// threads):
+//  * warp 9, producer: keeps a ring of 5-6 raw K chunks (16 columns each)
+//    in flight: per chunk one tensor-map load of the 128 x 16 A tile (F rows
+//    i0.., columns k..k + 16, rows contiguous) and either the 128 x 16 B
+//    tile of F (TRAIL) or four 4 x 128 boxes of Y (RUPD: pivot rows k.. of
+//    columns j0.., which land directly in the operand layout), plus the
+//    chunk's d_l (loaded one chunk ahead), completing on the stage's full
+//    mbarrier; a stage is refilled once the eight converter warps have
+//    arrived on its empty mbarrier;
+//  * warps 0-3, A converters: each thread owns one row (the warp's lane
+//    quarter of tensor memory), reads its 16 raw values (consecutive rows
+//    across a warp: no bank conflicts), scales them by d_l (TRAIL), splits
+//    them into TF32 high and low parts and writes both into tensor memory
+//    with two tcgen05.st (columns 128 + 32 stage);
+//  * warps 4-7, B converters: the same split for B (columns at or past the
+//    task's K end zeroed), stored as 16-byte vectors into one of two
+//    shared-memory operand stages in the K-major, no-swizzle core-matrix
+//    layout (8 rows x 16 bytes per core matrix; 128 B between 8-row groups,
+//    2048 B between 4-column K groups), so the conversion of chunk q
+//    overlaps the MMAs of chunk q - 1;
+//  * warp 8, MMA issuer: once all eight converter warps have arrived on a
+//    stage's ready mbarrier, one lane issues the chunk's MMAs (A from tensor
+//    memory, B from shared memory, M = N = 128, K = 8 each) into a 128 x 128
+//    FP32 accumulator in tensor memory and commits them to the operand
+//    stage's mbarrier.
 // Epilogue: once the last MMAs have completed, warps 0-7 read the
 // accumulator with tcgen05.ld (warp w: lanes 32 (w % 4) .., columns
 // 64 (w / 4) ..) and stage its negative (0 outside the task's range) in the
 // freed shared memory, and one thread adds the staged 128 x 128 tile to F
 // or Y with eight TMA reduce-add boxes (each entry receives exactly one
-// addition per launch: deterministic).  Every
-// mbarrier wait is bounded in time and gives up at once when another thread
-// of the CTA has given up (a shared abort word); the CTA then raises
-// FLAG_WAIT_TIMEOUT, waits (bounded) for the copies and MMAs it has in
-// flight, frees its tensor memory and returns.
+// addition per launch: deterministic).  Every mbarrier wait is bounded in
+// time and gives up at once when another thread of the CTA has given up (a
+// shared abort word); the CTA then raises FLAG_WAIT_TIMEOUT, waits (bounded)
+// for the copies and MMAs it has in flight, frees its tensor memory and
+// returns.
 constexpr int kT128 = 128;
 constexpr int kUK = 16;                              // K columns per chunk
 constexpr int kUOpBytes = kT128 * kUK * 4;           // one operand of one chunk: 8 KB
