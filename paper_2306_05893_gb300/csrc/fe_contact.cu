@@ -161,6 +161,15 @@ int regrow(fe_ctx *c, DeviceState *d, void **p, size_t bytes) {
   return FE_OK;
 }
 
+// grow a buffer to at least `bytes` (kept when large enough: a contact set
+// that changes every step does not reallocate)
+int grow(fe_ctx *c, DeviceState *d, void **p, size_t &cap, size_t bytes) {
+  if (*p && bytes <= cap) return FE_OK;
+  const int st = regrow(c, d, p, bytes);
+  cap = st ? 0 : std::max<size_t>(bytes, 8);
+  return st;
+}
+
 }  // namespace
 
 // Upload the constraint set (host copy in the context) to the device buffers.
@@ -224,16 +233,18 @@ static int contact_upload(fe_ctx *c, DeviceState *d) {
     const size_t ts = c->opt.precision == FE_MIXED ? sizeof(float) : sizeof(double);
     const int64_t groups = (m + nr - 1) / nr;
     const size_t slots = size_t(std::max<int64_t>(c->fwd_slots, 1));
-    int st = regrow(c, d, reinterpret_cast<void **>(&d->c_tasks), std::max<size_t>(multi.size(), 4) * sizeof(int32_t));
-    if (!st) st = regrow(c, d, &d->c_G, size_t(groups * nr) * size_t(std::max<int64_t>(c->n_free, 1)) * ts);
-    if (!st) st = regrow(c, d, &d->c_r, size_t(nr) * size_t(c->n) * ts);
-    if (!st) st = regrow(c, d, &d->c_u, size_t(nr) * size_t(std::max<int64_t>(c->u_total, 1)) * ts);
-    if (!st) st = regrow(c, d, &d->c_part, size_t(nr) * slots * size_t(fwd_rows(c->opt)) * ts);
-    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_tick), size_t(nr) * slots * sizeof(int));
-    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_pendm), size_t(nr) * size_t(nf) * sizeof(int));
-    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_fdm), size_t(nr) * size_t(nf) * sizeof(int));
-    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_bdm), size_t(nf) * sizeof(int));
-    if (!st) st = regrow(c, d, reinterpret_cast<void **>(&d->c_ctl), 4 * sizeof(int));
+    size_t *cb = d->c_bytes;
+    int st = grow(c, d, reinterpret_cast<void **>(&d->c_tasks), cb[0],
+                  std::max<size_t>(multi.size(), 4) * sizeof(int32_t));
+    if (!st) st = grow(c, d, &d->c_G, cb[1], size_t(groups * nr) * size_t(std::max<int64_t>(c->n_free, 1)) * ts);
+    if (!st) st = grow(c, d, &d->c_r, cb[2], size_t(nr) * size_t(c->n) * ts);
+    if (!st) st = grow(c, d, &d->c_u, cb[3], size_t(nr) * size_t(std::max<int64_t>(c->u_total, 1)) * ts);
+    if (!st) st = grow(c, d, &d->c_part, cb[4], size_t(nr) * slots * size_t(fwd_rows(c->opt)) * ts);
+    if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_tick), cb[5], size_t(nr) * slots * sizeof(int));
+    if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_pendm), cb[6], size_t(nr) * size_t(nf) * sizeof(int));
+    if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_fdm), cb[7], size_t(nr) * size_t(nf) * sizeof(int));
+    if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_bdm), cb[8], size_t(nf) * sizeof(int));
+    if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_ctl), cb[9], 4 * sizeof(int));
     if (st) return st;
     if (!multi.empty())
       FE_CUDA_TRY(cudaMemcpy(d->c_tasks, multi.data(), multi.size() * sizeof(int32_t), cudaMemcpyHostToDevice));

@@ -117,6 +117,7 @@ struct DeviceState {
   int *c_pend = nullptr, *c_pendm = nullptr, *c_fdm = nullptr, *c_bdm = nullptr, *c_ctl = nullptr, *c_tick = nullptr;
   void *c_r = nullptr, *c_u = nullptr, *c_part = nullptr;
   int64_t c_ntask = 0, c_nrhs = 0;
+  size_t c_bytes[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // capacities of the per-set buffers above
   int64_t c_cap = 0, c_m = 0;
   bool c_dirty = true;  // the context's constraint set changed since the last upload
   double *D[2] = {nullptr, nullptr};
