@@ -98,17 +98,32 @@ __global__ void __launch_bounds__(256) y_to_half_kernel(const float4 *__restrict
 // Task (front, c0, c1): zero the lower part of columns [c0, c1) of F and of
 // the pivot columns of Y, scatter the A entries of those columns, then add
 // every child's update block (children in fixed order: deterministic).
+//
+// Extend-add of one child: its update rows map to parent rows through the
+// increasing map rm, so the child columns landing in [c0, c1) are the
+// contiguous range [jlo, jhi) with jlo = #{rm < c0}, jhi = #{rm < c1}.  One
+// pass over rm stages it in shared memory and counts both (no dependent
+// binary-search loads); then warp w takes the columns jlo + w, jlo + w + 8,
+// ... in 32-row chunks, eight chunks' loads in flight per lane before their
+// stores.  Distinct (column, row) pairs of one child hit distinct parent
+// entries (rm is injective), so the warps never collide; children follow one
+// another behind a barrier (two children can share parent entries).
+constexpr int kRmCap = 4096;  // row maps longer than this are read from global memory
+
 template <typename TF>
 __global__ void __launch_bounds__(256) front_assemble_kernel(
     const int32_t *__restrict__ tasks, const DFront *__restrict__ fronts,
     const int32_t *__restrict__ child_list, const int32_t *__restrict__ rmap,
     const int64_t *__restrict__ fa_colptr, const int32_t *__restrict__ fa_slot,
     const int32_t *__restrict__ fa_off, const TF *__restrict__ A, TF *__restrict__ F, TF *__restrict__ Y) {
+  __shared__ int32_t rms[kRmCap];
+  __shared__ int s_cnt[2][2];  // (jlo, jhi) counts, double-buffered by child parity
   pdl_launch_dependents();
   const int32_t f = tasks[3 * blockIdx.x], c0 = tasks[3 * blockIdx.x + 1], c1 = tasks[3 * blockIdx.x + 2];
   const DFront fr = fronts[f];
   const int32_t m = fr.m, p = fr.npiv;
   TF *Ff = F + fr.f_off;
+  if (threadIdx.x < 4) s_cnt[threadIdx.x >> 1][threadIdx.x & 1] = 0;
   pdl_wait();
   for (int32_t col = c0; col < c1; ++col) {
     TF *cp = Ff + int64_t(col) * fr.ldf;
@@ -137,40 +152,59 @@ __global__ void __launch_bounds__(256) front_assemble_kernel(
     }
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int32_t ci = fr.child_begin; ci < fr.child_end; ++ci) {
+    const int b = (ci - fr.child_begin) & 1;
     const DFront ch = fronts[child_list[ci]];
     const int32_t *rm = rmap + ch.rows_off;
     const int32_t nu = ch.nupd, pc = ch.npiv;
-    // child columns mapping into [c0, c1): contiguous since rm is increasing
-    int32_t lo = 0, hi = nu;
-    while (lo < hi) { int32_t mid = (lo + hi) >> 1; if (rm[mid] < c0) lo = mid + 1; else hi = mid; }
-    const int32_t jlo = lo;
-    hi = nu;
-    while (lo < hi) { int32_t mid = (lo + hi) >> 1; if (rm[mid] < c1) lo = mid + 1; else hi = mid; }
-    const int32_t jhi = lo;
-    const TF *Fc = F + ch.f_off;
-    for (int32_t j = jlo; j < jhi; ++j) {
-      const TF *src = Fc + int64_t(pc + j) * ch.ldf + pc;
-      TF *dst = Ff + int64_t(rm[j]) * fr.ldf;
-      // 8 rows per thread in flight: all loads of a batch before its stores
-      // (a store ahead of the next load would expose one latency per row);
-      // the child's rows map to distinct parent rows, so a batch never
-      // reads what it writes
-      for (int32_t i = j + threadIdx.x; i < nu; i += 8 * 256) {
-        int32_t ri[8];
-        TF sv[8], dv[8];
+    const bool staged = nu <= kRmCap;
+    int n0 = 0, n1 = 0;
+    for (int32_t i = threadIdx.x; i < nu; i += blockDim.x) {
+      const int32_t v = rm[i];
+      if (staged) rms[i] = v;
+      n0 += v < c0;
+      n1 += v < c1;
+    }
+    n0 = __reduce_add_sync(0xffffffffu, n0);
+    n1 = __reduce_add_sync(0xffffffffu, n1);
+    if (lane == 0 && n1 > 0) {
+      atomicAdd(&s_cnt[b][0], n0);
+      atomicAdd(&s_cnt[b][1], n1);
+    }
+    __syncthreads();
+    const int32_t jlo = s_cnt[b][0], jhi = s_cnt[b][1];
+    // the other buffer was last read before the previous child's closing
+    // barrier; the next child accumulates into it after this child's
+    if (threadIdx.x < 2) s_cnt[b ^ 1][threadIdx.x] = 0;
+    const int32_t *rp = staged ? rms : rm;
+    const TF *Fc = F + ch.f_off + pc;
+    int32_t j = jlo + warp, r = j;  // this warp's current column and chunk start (warp-uniform)
+    while (j < jhi) {
+      TF sv[8], dv[8];
+      TF *dp[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int32_t ii = i + 256 * k;
-          ri[k] = ii < nu ? rm[ii] : -1;
-          sv[k] = ii < nu ? src[ii] : TF(0);
+      for (int k = 0; k < 8; ++k) {
+        sv[k] = TF(0);
+        dv[k] = TF(0);
+        dp[k] = nullptr;
+        if (j < jhi) {
+          const int32_t i = r + lane;
+          if (i < nu) {
+            sv[k] = Fc[int64_t(pc + j) * ch.ldf + i];
+            dp[k] = Ff + int64_t(rp[j]) * fr.ldf + rp[i];
+            dv[k] = *dp[k];
+          }
+          r += 32;
+          if (r >= nu) {
+            j += nwarp;
+            r = j;
+          }
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) dv[k] = ri[k] >= 0 ? dst[ri[k]] : TF(0);
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (ri[k] >= 0) dst[ri[k]] = dv[k] + sv[k];
       }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (dp[k]) *dp[k] = dv[k] + sv[k];
     }
     __syncthreads();
   }

@@ -550,14 +550,26 @@ int build_ordering(fe_ctx *c) {
     L.panel.assign(steps, {});
     L.trail.assign(steps, {});
     L.trail_flops.assign(steps, 0.0);
+    // assembly tasks: narrower column ranges for larger fronts (a task's
+    // work grows with the front's rows; the top levels hold few fronts), the
+    // largest fronts first so that the level's last wave is short
+    {
+      std::vector<int32_t> order(L.fronts);
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int32_t a, int32_t b) { return c->fronts[a].m() > c->fronts[b].m(); });
+      for (int32_t f : order) {
+        const int32_t m = c->fronts[f].m();
+        const int32_t w = m > 2048 ? 8 : m > 1024 ? 16 : 32;
+        for (int32_t c0 = 0; c0 < m; c0 += w) {
+          L.asm_tasks.push_back(f);
+          L.asm_tasks.push_back(c0);
+          L.asm_tasks.push_back(std::min(m, c0 + w));
+        }
+      }
+    }
     for (int32_t f : L.fronts) {
       const Front &F = c->fronts[f];
       const int32_t m = F.m(), p = F.npiv;
-      for (int32_t c0 = 0; c0 < m; c0 += 32) {
-        L.asm_tasks.push_back(f);
-        L.asm_tasks.push_back(c0);
-        L.asm_tasks.push_back(std::min(m, c0 + 32));
-      }
       // apply tasks; a block split over several tasks owns consecutive
       // partial-sum slots, reduced in order by the last task to finish
       for (int32_t r0 = 0; r0 < m; r0 += fr_rows) {
