@@ -284,10 +284,29 @@ __device__ __forceinline__ double pivot_inverse(double d, int *flags, bool repor
 // FMA per entry and step serve both.  At step j the pivot column F_:j, its
 // pivot's reciprocal and the Gauss-Jordan row Xi_j: come from
 // double-buffered shared vectors written by their owners at step j - 1: one
-// barrier per pivot, and no FP64 or double-float work gates the next step
-// (GB300's FP64 pipe issues a warp instruction only every ~64 cycles per SM
-// sub-partition).
+// barrier per pivot among warps 0-7 (named barrier 1), and no FP64 or
+// double-float work gates the next step (GB300's FP64 pipe issues a warp
+// instruction only every ~64 cycles per SM sub-partition).  The ninth warp
+// does not join that barrier: it follows the final columns as they land in
+// Ls through a progress word (release after the barrier, acquire before the
+// read), so its pivot chain overlaps the elimination.
 constexpr int kDiagThreads = 288;
+
+// block-scope acquire / release on a shared word (the pivot warp follows the
+// elimination's progress without joining its barriers)
+__device__ __forceinline__ int ld_acquire_cta_shared(const int *p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];\n"
+               : "=r"(v)
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p)))
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cta_shared(int *p, int v) {
+  asm volatile("st.release.cta.shared::cta.b32 [%0], %1;\n" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))),
+               "r"(v)
+               : "memory");
+}
 
 template <typename TF>
 __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t *__restrict__ tasks,
@@ -303,6 +322,7 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
   TF(*Xs)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double) + 64 * 65 * sizeof(TF));
   __shared__ TF colb[2][64], xrow[2][64], pinv[2];
   __shared__ double s_inv[64];  // FP64 inverses, or DF inverses in the same bytes
+  __shared__ int s_done;        // columns [0, s_done] of Ls hold their final values
   DF *s_invf = reinterpret_cast<DF *>(s_inv);
   pdl_launch_dependents();
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
@@ -310,9 +330,19 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
   const int32_t k0 = t.y & 0xffffff, kb = t.z;
   TF *Ff = F + fr.f_off;
   pdl_wait();
-  for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
-    const int i = idx % 64, j = idx / 64;
-    Ls[i][j] = (i < kb && j < kb && i >= j) ? Ff[(k0 + i) + int64_t(k0 + j) * fr.ldf] : TF(0);
+  {  // all of a thread's loads of the block in flight before its stores
+    constexpr int kPer = (64 * 64 + kDiagThreads - 1) / kDiagThreads;
+    TF v[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int idx = threadIdx.x + k * kDiagThreads, i = idx % 64, j = idx / 64;
+      v[k] = (idx < 64 * 64 && i < kb && j < kb && i >= j) ? Ff[(k0 + i) + int64_t(k0 + j) * fr.ldf] : TF(0);
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int idx = threadIdx.x + k * kDiagThreads;
+      if (idx < 64 * 64) Ls[idx % 64][idx / 64] = v[k];
+    }
   }
   __syncthreads();
   auto safe_inv = [](TF d) { return d > TF(0) ? TF(1) / d : TF(1); };
@@ -332,7 +362,10 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     colb[0][threadIdx.x] = Ls[threadIdx.x][0];
     xrow[0][threadIdx.x] = threadIdx.x == 0 ? TF(1) : TF(0);
   }
-  if (threadIdx.x == 0) pinv[0] = safe_inv(Ls[0][0]);
+  if (threadIdx.x == 0) {
+    pinv[0] = safe_inv(Ls[0][0]);
+    s_done = 0;
+  }
   // pivot warp: lane l keeps rows l and l + 32 in FP64 / double-float
   DF p0 = {1.f, 0.f}, p1 = {1.f, 0.f};
   double q0 = 1.0, q1 = 1.0;
@@ -346,13 +379,25 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     }
   }
   __syncthreads();
-  for (int j = 0; j < kb; ++j) {
-    const int cur = j & 1, nxt = cur ^ 1;
-    if (pivot_warp) {
-      // fold column j (final, unscaled) into the pivots of rows > j; runs
-      // beside the elimination, which uses the FP32 pivots
+  if (pivot_warp) {
+    // fold column j (final, unscaled) into the pivots of rows > j.  The
+    // elimination uses the FP32 pivots, so this chain runs beside it without
+    // joining its barriers: lane 0 waits (bounded) until column j is final
+    // in Ls, published by a release of s_done after the elimination's barrier.
+    for (int j = 0; j < kb; ++j) {
+      int late = 0;
+      if (lane == 0) {
+        for (int spins = 0; ld_acquire_cta_shared(&s_done) < j; ++spins)
+          if (spins > (1 << 24)) {
+            atomicOr(flags, FLAG_WAIT_TIMEOUT);
+            late = 1;
+            break;
+          }
+      }
+      __syncwarp();
+      if (__shfl_sync(0xffffffffu, late, 0)) break;
       const int i0 = lane, i1 = lane + 32;
-      const TF f0 = colb[cur][i0], f1 = colb[cur][i1];
+      const TF f0 = Ls[i0][j], f1 = Ls[i1][j];
       if constexpr (kDF) {
         const float djh = __shfl_sync(0xffffffffu, j < 32 ? p0.hi : p1.hi, j & 31);
         const float djl = __shfl_sync(0xffffffffu, j < 32 ? p0.lo : p1.lo, j & 31);
@@ -367,7 +412,10 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
         if (i0 > j && i0 < kb) q0 -= double(f0) * double(f0) * inv;
         if (i1 > j && i1 < kb) q1 -= double(f1) * double(f1) * inv;
       }
-    } else {
+    }
+  } else {
+    for (int j = 0; j < kb; ++j) {
+      const int cur = j & 1, nxt = cur ^ 1;
       const TF tinv = pinv[cur];
       TF lij[4], val[4];
 #pragma unroll
@@ -415,9 +463,12 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
           }
         }
       }
+      // the eight elimination warps only (named barrier 1)
+      asm volatile("bar.sync 1, 256;\n" ::: "memory");
+      if (threadIdx.x == 0) st_release_cta_shared(&s_done, jn);  // column j+1 is in Ls
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (!pivot_warp) {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
