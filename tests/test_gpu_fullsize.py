@@ -161,7 +161,6 @@ def check_steps(wl, ctx, steps=STEPS, n_nodes=200, seed=4, tol_oracle=1e-4, tol_
     rows = node_dofs(nodes)
     m = sub_model(wl, elements_touching(mesh.conn, nodes))
     fixed = node_dofs(mesh.fixed_nodes)
-    S = None
     worst = 0.0
     for t in range(steps):
         p = wl.p(t).reshape(-1)
