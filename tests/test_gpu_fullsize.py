@@ -18,7 +18,9 @@ computes one by one, from the elements that touch a seeded sample of nodes
     sampled rows.
 Properties that hold at any size cover the rest of each step: a solves the
 library's assembled system to the requested tolerance, q_{t+1} = q_t + h
-v_{t+1}, and the clamped face stays at rest.
+v_{t+1}, and the clamped face stays at rest.  Last, the FP64 exact factor of
+the same mesh at rest inverts A to 1e-9 (Section 3.3's preconditioner with
+no lag).
 
 Tolerances: element and assembly values 2e-5 of the largest sampled entry (FP32
 element math, as in the small-mesh parity tests), b during the steps 2e-5 of the
@@ -184,6 +186,25 @@ def check_steps(wl, ctx, steps=STEPS, n_nodes=200, seed=4, tol_oracle=1e-4, tol_
     return worst
 
 
+def check_exact_factor(wl, ctx, seed=5, tol=1e-9):
+    """FP64 factor of A at rest, applied once: z = A^{-1} r up to rounding.
+    On this mesh 13 fronts have more than 4,096 update rows, so the assembly
+    reads their row maps from global memory; a wrong extend-add anywhere
+    leaves an O(1) residual."""
+    A, _ = ctx.assemble()
+    ctx.factor_now()
+    rng = np.random.default_rng(seed)
+    r = rng.standard_normal(ctx.n)
+    fixed = node_dofs(wl.mesh.fixed_nodes)
+    r[fixed] = 0.0
+    z = ctx.apply_preconditioner(r)
+    S = sp.csr_matrix((A, np.asarray(ctx.colind), np.asarray(ctx.rowptr)), shape=(ctx.n, ctx.n))
+    res = np.linalg.norm(S @ z - r) / np.linalg.norm(r)
+    assert res <= tol
+    assert np.all(z[fixed] == 0.0)
+    return res
+
+
 # -------------------------------------------------------------------- tests
 
 @pytest.fixture(scope="module")
@@ -208,3 +229,12 @@ def test_fullsize_element_kernel_sampled(full):
 
 def test_fullsize_assembly_sampled_rows(full):
     check_assembly_rows(*full)
+
+
+def test_fullsize_exact_factor_inverts_A(gpu_lib):
+    wl = fi.workload(WORKLOAD)
+    ctx = gpu_lib.FEContext.from_workload(wl, precision=0, refactor_every=1)
+    try:
+        check_exact_factor(wl, ctx)
+    finally:
+        ctx.close()
