@@ -62,6 +62,20 @@ def test_shard_members_balanced_cover():
         assert max(loads) - min(loads) <= max(dofs)
 
 
+def test_shard_members_edge_cases():
+    from paper_2306_05893_gb300.sharding import shard_members
+    # more ranks than members: one member each, the rest empty
+    assert shard_members([5, 9, 7], 5) == [[1], [2], [0], [], []]
+    assert shard_members([], 3) == [[], [], []]
+    # equal sizes go round-robin in index order (deterministic ties)
+    assert shard_members([4, 4, 4, 4], 2) == [[0, 2], [1, 3]]
+    for bad in (0, -1):
+        with pytest.raises(ValueError):
+            shard_members([1, 2], bad)
+    with pytest.raises(ValueError):
+        shard_members([1, -2], 2)
+
+
 def _rank(rank, world, port, out_dir):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
