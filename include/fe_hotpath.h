@@ -174,12 +174,15 @@ int fe_get_batch_stats(fe_ctx *ctx, int32_t *iters, double *rel_residual);
 /* Setup once per topology (Section 4.2, Table "build pattern"; Section 5.1;
  * Section 6.1): the triplet (row, col) stream in fill order
  *   t = ((e * npe + a) * npe + b) * 9 + 3 i + k   (value K_e[3a+i][3b+k]),
- * the CSR pattern by two transposes with fixed rows/columns skipped, the map C
+ * the CSR pattern that two transposes of that stream give, with fixed
+ * rows/columns skipped (built row by row on the host's cores), the map C
  * (triplet -> CSR slot, -1 when dropped) and its inverse (per slot, its
  * triplets ascending), the consistent mass on that pattern, a nested-
  * dissection ordering of the free nodes, the multifrontal symbolic analysis
  * and the level schedule.  Host work only; device buffers are created at the
- * first call that needs the GPU.  Must precede every call below. */
+ * first call that needs the GPU.  Must precede every call below.
+ * FE_ERR_ARG: a free node that belongs to no element (its row would be
+ * empty and A singular); fix such nodes or drop them from the mesh. */
 int fe_build_pattern(fe_ctx *ctx);
 
 /* Borrowed host views of the setup products, valid until fe_destroy:

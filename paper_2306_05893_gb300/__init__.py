@@ -63,6 +63,16 @@ def _ptr(a):
     return a.ctypes.data_as(ct.c_void_p)
 
 
+def _arr(ptr, count, dtype):
+    """Copy of a library-owned array; empty arrays may come with a NULL pointer."""
+    count = int(count)
+    if count == 0 or not ptr:
+        if count:
+            raise FEError(-1, "library returned a NULL pointer for a non-empty array")
+        return np.zeros(0, dtype)
+    return np.ctypeslib.as_array(ptr, (count,)).copy()
+
+
 def _dptr(a):
     return a.ctypes.data_as(ct.POINTER(ct.c_double))
 
@@ -151,22 +161,20 @@ def fe_get_pattern(ctx):
     rp, ci, sc = (ct.POINTER(ct.c_int32)() for _ in range(3))
     _check(ctx, load().fe_get_pattern(ctx, ct.byref(n), ct.byref(nnz), ct.byref(rp), ct.byref(ci),
                                       ct.byref(nt), ct.byref(sc)))
-    return (np.ctypeslib.as_array(rp, (n.value + 1,)).copy(),
-            np.ctypeslib.as_array(ci, (nnz.value,)).copy(),
-            np.ctypeslib.as_array(sc, (nt.value,)).copy())
+    return (_arr(rp, n.value + 1, np.int32), _arr(ci, nnz.value, np.int32), _arr(sc, nt.value, np.int32))
 
 
 def fe_get_inverse_map(ctx, nnz):
     sp_, ss = ct.POINTER(ct.c_int64)(), ct.POINTER(ct.c_int32)()
     _check(ctx, load().fe_get_inverse_map(ctx, ct.byref(sp_), ct.byref(ss)))
-    slot_ptr = np.ctypeslib.as_array(sp_, (nnz + 1,)).copy()
-    return slot_ptr, np.ctypeslib.as_array(ss, (int(slot_ptr[-1]),)).copy()
+    slot_ptr = _arr(sp_, nnz + 1, np.int64)
+    return slot_ptr, _arr(ss, int(slot_ptr[-1]), np.int32)
 
 
 def fe_get_mass(ctx, nnz):
     mp = ct.POINTER(ct.c_double)()
     _check(ctx, load().fe_get_mass(ctx, ct.byref(mp)))
-    return np.ctypeslib.as_array(mp, (nnz,)).copy()
+    return _arr(mp, nnz, np.float64)
 
 
 def fe_get_ordering(ctx):
@@ -174,8 +182,8 @@ def fe_get_ordering(ctx):
     ptrs = [ct.POINTER(ct.c_int32)() for _ in range(6)]
     _check(ctx, load().fe_get_ordering(ctx, ct.byref(nf), ct.byref(ptrs[0]), ct.byref(nfr),
                                        *[ct.byref(p) for p in ptrs[1:]]))
-    perm = np.ctypeslib.as_array(ptrs[0], (nf.value,)).copy() if nf.value else np.zeros(0, np.int32)
-    fr = [np.ctypeslib.as_array(p, (nfr.value,)).copy() for p in ptrs[1:]]
+    perm = _arr(ptrs[0], nf.value, np.int32)
+    fr = [_arr(p, nfr.value, np.int32) for p in ptrs[1:]]
     return dict(perm=perm, first=fr[0], npiv=fr[1], nupd=fr[2], parent=fr[3], level=fr[4])
 
 
@@ -183,7 +191,7 @@ def fe_get_front_rows(ctx, f):
     nu = ct.c_int64()
     rp = ct.POINTER(ct.c_int32)()
     _check(ctx, load().fe_get_front_rows(ctx, int(f), ct.byref(nu), ct.byref(rp)))
-    return np.ctypeslib.as_array(rp, (nu.value,)).copy() if nu.value else np.zeros(0, np.int32)
+    return _arr(rp, nu.value, np.int32)
 
 
 def fe_set_state(ctx, q=None, v=None):

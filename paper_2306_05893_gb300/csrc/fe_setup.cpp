@@ -1,13 +1,16 @@
-// Host setup, once per topology: triplet stream -> CSR pattern by two
-// transposes (Section 4.2, Table "build pattern"), the map C and its inverse,
+// Host setup, once per topology: triplet stream -> the CSR pattern that two
+// transposes of it give (Section 4.2, Table "build pattern"; built per node
+// on the host's cores, bit-identical to the transposes), the map C and its inverse,
 // projective constraints folded into the pattern (Section 5.1), consistent
 // mass, element rest data, nested-dissection ordering of the free nodes and
 // the multifrontal symbolic analysis + level schedule (Section 6.1,
 // Eq. "regional problem").  Plain C++; no CUDA.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <numeric>
+#include <thread>
 
 #include "fe_ctx.h"
 
@@ -58,93 +61,157 @@ void hex_gauss(int q, double xi[3]) {
   xi[2] = (2 * ((q >> 2) & 1) - 1) * g;
 }
 
+// Runs f(begin, end) over [0, count) in chunks on the host's cores.  Each
+// index's output must go to a position fixed beforehand, so the result does
+// not depend on the number of threads or on their order.
+template <class F>
+void parallel_chunks(int64_t count, int64_t chunk, F &&f) {
+  unsigned nt = std::thread::hardware_concurrency();
+  nt = std::max(1u, std::min(nt, 64u));
+  if (count <= chunk || nt == 1) {
+    if (count > 0) f(int64_t(0), count);
+    return;
+  }
+  std::atomic<int64_t> next{0};
+  auto work = [&] {
+    for (;;) {
+      const int64_t b = next.fetch_add(chunk);
+      if (b >= count) break;
+      f(b, std::min(count, b + chunk));
+    }
+  };
+  std::vector<std::thread> pool;
+  for (unsigned i = 1; i < nt; ++i) {
+    try {
+      pool.emplace_back(work);
+    } catch (...) {
+      break;  // fewer threads: the calling thread still takes every chunk left
+    }
+  }
+  work();
+  for (auto &t : pool) t.join();
+}
+
 // ------------------------------------------------------------------ pattern
-// Two transposes of the uncompressed structure: the first groups the kept
-// triplets by column (rows unsorted), the second by row with columns sorted
-// and, for equal (row, col), triplets in fill order; equal neighbours are
-// then merged into one slot.  Fixed columns are skipped in the first pass,
-// fixed rows in the second and replaced by a lone diagonal slot.
+// The CSR pattern of the projected matrix, C and its inverse, as the two
+// transposes of the uncompressed triplet structure define them (rows
+// ascending, columns ascending, equal (row, col) merged with their triplets in
+// fill order), built row by row: a node's rows collect the (column, triplet)
+// pairs of the elements around the node, sorted by column and then triplet id.
+// Counts fix every row's output range first, so the nodes build in parallel.
+// All rows of a node carry the same columns; a fixed row keeps a lone
+// diagonal slot, a fixed column is dropped (C = -1).
 int build_csr(fe_ctx *c) {
   const int npe = c->npe;
-  const int64_t E = c->n_elems, n = c->n;
+  const int64_t E = c->n_elems, n = c->n, nn = c->n_nodes;
   const int64_t bpe = int64_t(npe) * npe * 9;  // triplets per element
   c->ntrip = E * bpe;
   if (c->ntrip >= (int64_t(1) << 31)) return set_error(c, FE_ERR_ARG, "too many triplets for int32 ids");
   const int32_t *conn = c->conn.data();
   const int8_t *fx = c->fixed_dof.data();
-  auto rc = [&](int64_t t, int32_t &row, int32_t &col) {
-    int64_t e = t / bpe, r = t % bpe;
-    int blk = int(r / 9), ik = int(r % 9);
-    int a = blk / npe, b = blk % npe;
-    row = 3 * conn[e * npe + a] + ik / 3;
-    col = 3 * conn[e * npe + b] + ik % 3;
-  };
-  // first transpose: X^T in the uncompressed structure
-  std::vector<int64_t> colptr(n + 1, 0);
-  for (int64_t t = 0; t < c->ntrip; ++t) {
-    int32_t r, k;
-    rc(t, r, k);
-    if (!fx[r] && !fx[k]) colptr[k + 1]++;
-  }
-  for (int64_t j = 0; j < n; ++j) colptr[j + 1] += colptr[j];
-  const int64_t kept = colptr[n];
-  std::vector<int32_t> xt_row(kept), xt_t(kept);
+  // node incidence lists (element-major, ascending); the force gather uses them too
+  c->node_ptr.assign(nn + 1, 0);
+  for (int64_t k = 0; k < E * npe; ++k) c->node_ptr[conn[k] + 1]++;
+  for (int64_t i = 0; i < nn; ++i) c->node_ptr[i + 1] += c->node_ptr[i];
+  c->node_src.assign(E * npe, 0);
   {
-    std::vector<int64_t> next(colptr.begin(), colptr.end() - 1);
-    for (int64_t t = 0; t < c->ntrip; ++t) {
-      int32_t r, k;
-      rc(t, r, k);
-      if (fx[r] || fx[k]) continue;
-      int64_t p = next[k]++;
-      xt_row[p] = r;
-      xt_t[p] = int32_t(t);
-    }
+    std::vector<int32_t> next(c->node_ptr.begin(), c->node_ptr.end() - 1);
+    for (int64_t k = 0; k < E * npe; ++k) c->node_src[next[conn[k]]++] = int32_t(k);
   }
-  // second transpose: X = (X^T)^T, rows sorted, columns sorted, uncompressed
-  std::vector<int64_t> rp(n + 1, 0);
-  for (int64_t p = 0; p < kept; ++p) rp[xt_row[p] + 1]++;
+  // free DOFs per element = kept columns of each of its free rows
+  std::vector<int32_t> kept_e(E);
+  for (int64_t e = 0; e < E; ++e) {
+    int32_t k = 0;
+    for (int a = 0; a < npe; ++a)
+      for (int j = 0; j < 3; ++j) k += fx[3 * int64_t(conn[e * npe + a]) + j] ? 0 : 1;
+    kept_e[e] = k;
+  }
+  for (int64_t v = 0; v < nn; ++v)
+    if (c->node_ptr[v] == c->node_ptr[v + 1] && !(fx[3 * v] && fx[3 * v + 1] && fx[3 * v + 2]))
+      return set_error(c, FE_ERR_ARG, "node " + std::to_string(v) + " is free but belongs to no element");
+  std::vector<int64_t> rp(n + 1, 0);  // kept triplets per row
+  for (int64_t v = 0; v < nn; ++v) {
+    int64_t cnt = 0;
+    for (int32_t p = c->node_ptr[v]; p < c->node_ptr[v + 1]; ++p) cnt += kept_e[c->node_src[p] / npe];
+    for (int i = 0; i < 3; ++i) rp[3 * v + i + 1] = fx[3 * v + i] ? 0 : cnt;
+  }
   for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
-  std::vector<int32_t> x_col(kept);
+  const int64_t kept = rp[n];
   c->slot_src.assign(kept, 0);
-  {
-    std::vector<int64_t> next(rp.begin(), rp.end() - 1);
-    for (int64_t j = 0; j < n; ++j)
-      for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
-        int64_t q = next[xt_row[p]]++;
-        x_col[q] = int32_t(j);
-        c->slot_src[q] = xt_t[p];
+  std::vector<int32_t> x_col(kept);
+  std::vector<int32_t> uniq(nn, 0);  // distinct columns of a node's free rows
+  const int32_t *nptr = c->node_ptr.data(), *nsrc = c->node_src.data();
+  int32_t *ssrc = c->slot_src.data();
+  parallel_chunks(nn, 512, [&](int64_t v0, int64_t v1) {
+    std::vector<uint64_t> keys;  // column << 32 | triplet id of the node's row 0
+    for (int64_t v = v0; v < v1; ++v) {
+      if (fx[3 * v] && fx[3 * v + 1] && fx[3 * v + 2]) continue;
+      keys.clear();
+      for (int32_t p = nptr[v]; p < nptr[v + 1]; ++p) {
+        const int64_t e = nsrc[p] / npe, a = nsrc[p] % npe;
+        const int64_t tb = (e * npe + a) * npe * 9;
+        for (int bb = 0; bb < npe; ++bb) {
+          const int64_t w = conn[e * npe + bb];
+          for (int k = 0; k < 3; ++k)
+            if (!fx[3 * w + k]) keys.push_back(uint64_t(3 * w + k) << 32 | uint64_t(tb + 9 * bb + k));
+        }
       }
-  }
-  std::vector<int32_t>().swap(xt_row);
-  std::vector<int32_t>().swap(xt_t);
-  // merge duplicates -> CSR, C and the inverse map (slot_ptr, slot_src)
-  c->rowptr.assign(n + 1, 0);
-  c->colind.clear();
-  c->colind.reserve(kept / 4 + n);
-  c->slot_ptr.clear();
-  c->slot_ptr.reserve(kept / 4 + n + 1);
+      std::sort(keys.begin(), keys.end());
+      int32_t u = 0;
+      uint64_t last = ~uint64_t(0);
+      for (uint64_t key : keys)
+        if ((key >> 32) != last) {
+          last = key >> 32;
+          ++u;
+        }
+      uniq[v] = u;
+      for (int i = 0; i < 3; ++i) {  // row 3v + i: triplet ids shift by 3i
+        const int64_t r = 3 * v + i;
+        if (fx[r]) continue;
+        int64_t q = rp[r];
+        for (uint64_t key : keys) {
+          x_col[q] = int32_t(key >> 32);
+          ssrc[q] = int32_t(uint32_t(key) + 3u * uint32_t(i));
+          ++q;
+        }
+      }
+    }
+  });
+  // slots: a free row has its node's distinct columns, a fixed row one
+  std::vector<int64_t> sp(n + 1, 0);
+  for (int64_t r = 0; r < n; ++r) sp[r + 1] = sp[r] + (fx[r] ? 1 : uniq[r / 3]);
+  const int64_t nnz = sp[n];
+  if (nnz >= (int64_t(1) << 31)) return set_error(c, FE_ERR_ARG, "nnz exceeds int32");
+  c->nnz = nnz;
+  c->rowptr.resize(n + 1);
+  for (int64_t r = 0; r <= n; ++r) c->rowptr[r] = int32_t(sp[r]);
+  c->colind.assign(nnz, 0);
+  c->slot_ptr.assign(nnz + 1, 0);
   c->C.assign(c->ntrip, -1);
-  for (int64_t i = 0; i < n; ++i) {
-    c->rowptr[i] = int32_t(c->colind.size());
-    if (fx[i]) {  // projected row: lone diagonal, no triplet maps to it
-      c->slot_ptr.push_back(rp[i]);
-      c->colind.push_back(int32_t(i));
-      continue;
-    }
-    int32_t last = -1;
-    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
-      if (x_col[q] != last) {
-        last = x_col[q];
-        c->slot_ptr.push_back(q);
-        c->colind.push_back(last);
+  int32_t *colind = c->colind.data(), *Cm = c->C.data();
+  int64_t *sptr = c->slot_ptr.data();
+  parallel_chunks(n, 1536, [&](int64_t r0, int64_t r1) {
+    for (int64_t r = r0; r < r1; ++r) {
+      int64_t s = sp[r];
+      if (fx[r]) {  // projected row: lone diagonal, no triplet maps to it
+        colind[s] = int32_t(r);
+        sptr[s] = rp[r];
+        continue;
       }
-      c->C[c->slot_src[q]] = int32_t(c->colind.size() - 1);
+      --s;
+      int32_t last = -1;
+      for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+        if (x_col[q] != last) {
+          last = x_col[q];
+          ++s;
+          colind[s] = last;
+          sptr[s] = q;
+        }
+        Cm[ssrc[q]] = int32_t(s);
+      }
     }
-  }
-  c->nnz = int64_t(c->colind.size());
-  if (c->nnz >= (int64_t(1) << 31)) return set_error(c, FE_ERR_ARG, "nnz exceeds int32");
-  c->rowptr[n] = int32_t(c->nnz);
-  c->slot_ptr.push_back(kept);
+  });
+  sptr[nnz] = kept;
   return FE_OK;
 }
 
@@ -204,23 +271,20 @@ int build_mass_and_rest(fe_ctx *c) {
   // mass values on the pattern: gather through the inverse map (ascending t)
   c->mass.assign(c->nnz, 0.0);
   const int64_t bpe = int64_t(npe) * npe * 9;
-  for (int64_t s = 0; s < c->nnz; ++s) {
-    double acc = 0.0;
-    for (int64_t q = c->slot_ptr[s]; q < c->slot_ptr[s + 1]; ++q) {
-      int64_t t = c->slot_src[q];
-      int64_t e = t / bpe, r = t % bpe;
-      int blk = int(r / 9), ik = int(r % 9);
-      if (ik / 3 == ik % 3) acc += me[e * npe * npe + blk];
+  // slots in parallel; each slot sums its triplets in ascending order
+  parallel_chunks(c->nnz, 4096, [&](int64_t s0, int64_t s1) {
+    for (int64_t s = s0; s < s1; ++s) {
+      double acc = 0.0;
+      for (int64_t q = c->slot_ptr[s]; q < c->slot_ptr[s + 1]; ++q) {
+        int64_t t = c->slot_src[q];
+        int64_t e = t / bpe, r = t % bpe;
+        int blk = int(r / 9), ik = int(r % 9);
+        if (ik / 3 == ik % 3) acc += me[e * npe * npe + blk];
+      }
+      c->mass[s] = acc;
     }
-    c->mass[s] = acc;
-  }
-  // node incidence lists (element-major, ascending) for the force gather
-  c->node_ptr.assign(c->n_nodes + 1, 0);
-  for (int64_t k = 0; k < E * npe; ++k) c->node_ptr[c->conn[k] + 1]++;
-  for (int64_t i = 0; i < c->n_nodes; ++i) c->node_ptr[i + 1] += c->node_ptr[i];
-  c->node_src.assign(E * npe, 0);
-  std::vector<int32_t> next(c->node_ptr.begin(), c->node_ptr.end() - 1);
-  for (int64_t k = 0; k < E * npe; ++k) c->node_src[next[c->conn[k]]++] = int32_t(k);
+  });
+  // (the node incidence lists for the force gather come from build_csr)
   return FE_OK;
 }
 

@@ -1,5 +1,6 @@
 """CPU tests of the C-ABI library: symbols, and the host setup (Section 4.2
-pattern + map C by two transposes, Section 5.1 constraints, Section 6.1
+pattern + map C, as two transposes of the triplet stream define them; Section
+5.1 constraints, Section 6.1
 nested dissection and multifrontal structure) against the oracle."""
 import ctypes as ct
 import os
@@ -61,7 +62,24 @@ MESHES = {
     "hex-3x3x7": lambda: fi.hex_beam(3, 3, 7),
     "tet-1x1x1-nofix": lambda: fi.TetBeam(1, 1, 1, fi.tet_beam(1, 1, 1).X, fi.tet_beam(1, 1, 1).conn,
                                           np.zeros(0, np.int32)),
+    # element order shuffled (row segments then hold triplets from scattered elements)
+    "tet-3x3x5-shuffled": lambda: _replace(fi.tet_beam(3, 3, 5), conn=_shuffled(fi.tet_beam(3, 3, 5).conn)),
+    # fixed nodes inside the mesh, not on one face
+    "hex-2x3x4-interior-fix": lambda: _replace(fi.hex_beam(2, 3, 4, jitter=0.1),
+                                               fixed_nodes=np.array([0, 7, 19, 30, 41], np.int32)),
+    # every node fixed: the pattern is the identity, no triplet is kept
+    "tet-2x2x3-all-fixed": lambda: _replace(fi.tet_beam(2, 2, 3),
+                                            fixed_nodes=np.arange(3 * 3 * 4, dtype=np.int32)),
 }
+
+
+def _replace(mesh, **kw):
+    import dataclasses
+    return dataclasses.replace(mesh, **kw)
+
+
+def _shuffled(conn, seed=5):
+    return conn[np.random.default_rng(seed).permutation(conn.shape[0])].copy()
 
 
 @pytest.mark.parametrize("name", list(MESHES))
@@ -83,6 +101,33 @@ def test_pattern_and_map_bit_exact(fe, name):
         seg = slot_src[slot_ptr[s]:slot_ptr[s + 1]]
         assert np.all(C[seg] == s)
         assert np.all(np.diff(seg) > 0)
+    ctx.close()
+
+
+def test_all_fixed_pattern_is_the_identity(fe):
+    mesh = MESHES["tet-2x2x3-all-fixed"]()
+    ctx = _ctx(fe, mesh)
+    n = 3 * mesh.n_nodes
+    np.testing.assert_array_equal(ctx.rowptr, np.arange(n + 1))
+    np.testing.assert_array_equal(ctx.colind, np.arange(n))
+    assert np.all(ctx.C == -1)
+    slot_ptr, slot_src = ctx.inverse_map()
+    assert slot_src.size == 0 and np.all(slot_ptr == 0)
+    ctx.close()
+
+
+def test_free_node_outside_every_element_is_rejected(fe):
+    mesh = fi.tet_beam(1, 1, 2)
+    X = np.vstack([mesh.X, [[1.0, 1.0, 1.0]]])  # an extra node no element uses
+    with pytest.raises(fe.FEError) as ei:
+        fe.FEContext(mesh.elem_type, X, mesh.conn, mesh.fixed_nodes, 0, 1000.0, [1e3, 1e4, 0.0],
+                     0.01, 0.1, 0.01)
+    assert ei.value.status == 1 and "belongs to no element" in str(ei.value)
+    # fixed, the same node is accepted (its row is a lone diagonal)
+    fixed = np.append(mesh.fixed_nodes, mesh.n_nodes).astype(np.int32)
+    ctx = fe.FEContext(mesh.elem_type, X, mesh.conn, fixed, 0, 1000.0, [1e3, 1e4, 0.0], 0.01, 0.1, 0.01)
+    r = 3 * mesh.n_nodes
+    assert list(ctx.colind[ctx.rowptr[r]:ctx.rowptr[r + 3]]) == [r, r + 1, r + 2]
     ctx.close()
 
 
