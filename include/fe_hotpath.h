@@ -151,7 +151,11 @@ typedef struct {
 int fe_options_default(fe_options *opt);
 
 /* Copies mesh, material, h, Rayleigh (alpha, beta) and options into a new
- * context (Section 3.2).  Touches no GPU.  *out is NULL on failure. */
+ * context (Section 3.2).  Touches no GPU.  *out is NULL on failure.
+ * FE_ERR_ARG: a NULL or empty mesh, an unknown element type or model, a
+ * node index out of range, h not finite and positive, rho not positive,
+ * alpha or beta negative or not finite (Rayleigh damping B = alpha M +
+ * beta K), or a non-finite rest coordinate or material parameter. */
 int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alpha,
               double beta, const fe_options *opt, fe_ctx **out);
 

@@ -40,8 +40,10 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
     return FE_ERR_ARG;
   if (mesh->elem_type != FE_TET4 && mesh->elem_type != FE_HEX8) return FE_ERR_ARG;
   if (mat->model < FE_SVK || mat->model > FE_COROTATIONAL || !mat->params) return FE_ERR_ARG;
-  if (!(h > 0) || !(mat->rho > 0) || mesh->n_fixed < 0 || (mesh->n_fixed > 0 && !mesh->fixed_nodes))
+  if (!(h > 0) || !std::isfinite(h) || !(mat->rho > 0) || !std::isfinite(mat->rho) || mesh->n_fixed < 0 ||
+      (mesh->n_fixed > 0 && !mesh->fixed_nodes))
     return FE_ERR_ARG;
+  if (!(alpha >= 0) || !std::isfinite(alpha) || !(beta >= 0) || !std::isfinite(beta)) return FE_ERR_ARG;
   if (mesh->n_nodes > (int64_t(1) << 29)) return FE_ERR_ARG;
   fe_ctx *c = new (std::nothrow) fe_ctx();
   if (!c) return FE_ERR_OOM;
@@ -51,6 +53,8 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
     c->n_nodes = mesh->n_nodes;
     c->n_elems = mesh->n_elems;
     c->X.assign(mesh->rest_xyz, mesh->rest_xyz + 3 * mesh->n_nodes);
+    for (double x : c->X)
+      if (!std::isfinite(x)) { delete c; return FE_ERR_ARG; }
     c->conn.assign(mesh->conn, mesh->conn + c->npe * mesh->n_elems);
     for (int32_t v : c->conn)
       if (v < 0 || v >= mesh->n_nodes) { delete c; return FE_ERR_ARG; }
@@ -62,6 +66,8 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
     c->params.resize(3 * mesh->n_elems);
     for (int64_t e = 0; e < mesh->n_elems; ++e)
       for (int k = 0; k < 3; ++k) c->params[3 * e + k] = mat->per_element ? mat->params[3 * e + k] : mat->params[k];
+    for (double p : c->params)
+      if (!std::isfinite(p)) { delete c; return FE_ERR_ARG; }
     c->h = h;
     c->alpha = alpha;
     c->beta = beta;

@@ -50,6 +50,27 @@ def test_create_rejects_bad_input(fe):
     assert ei.value.status == 1
 
 
+def test_create_rejects_non_finite_and_negative_damping(fe):
+    mesh = fi.tet_beam(1, 1, 1)
+    args = (0, mesh.X, mesh.conn, mesh.fixed_nodes, 0, 1000.0, [1.0, 1.0, 0.0])
+    for h, al, be in [(np.inf, 0.1, 0.01), (0.01, -0.1, 0.01), (0.01, 0.1, -1e-3), (0.01, np.nan, 0.01),
+                      (0.01, 0.1, np.inf)]:
+        with pytest.raises(fe.FEError) as ei:
+            fe.fe_create(*args, h, al, be)
+        assert ei.value.status == 1
+    X = mesh.X.copy()
+    X[3, 1] = np.nan
+    with pytest.raises(fe.FEError):
+        fe.fe_create(0, X, mesh.conn, mesh.fixed_nodes, 0, 1000.0, [1.0, 1.0, 0.0], 0.01, 0.1, 0.01)
+    with pytest.raises(fe.FEError):
+        fe.fe_create(0, mesh.X, mesh.conn, mesh.fixed_nodes, 0, 1000.0, [1.0, np.inf, 0.0], 0.01, 0.1, 0.01)
+    with pytest.raises(fe.FEError):
+        fe.fe_create(0, mesh.X, mesh.conn, mesh.fixed_nodes, 0, np.inf, [1.0, 1.0, 0.0], 0.01, 0.1, 0.01)
+    # zero damping is a valid Rayleigh model
+    ctx = fe.fe_create(0, mesh.X, mesh.conn, mesh.fixed_nodes, 0, 1000.0, [1.0, 1.0, 0.0], 0.01, 0.0, 0.0)
+    fe.fe_destroy(ctx)
+
+
 def _ctx(fe, mesh, **kw):
     return fe.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, 0, 1000.0,
                         [1e3, 1e4, 0.0], 0.01, 0.1, 0.01, **kw)
