@@ -186,7 +186,9 @@ int fe_get_batch_stats(fe_ctx *ctx, int32_t *iters, double *rel_residual);
  * and the level schedule.  Host work only; device buffers are created at the
  * first call that needs the GPU.  Must precede every call below.
  * FE_ERR_ARG: a free node that belongs to no element (its row would be
- * empty and A singular); fix such nodes or drop them from the mesh. */
+ * empty and A singular); fix such nodes or drop them from the mesh.
+ * The host part runs on all cores; the environment variable FE_HOST_THREADS
+ * (a positive integer) caps the threads.  The products do not depend on it. */
 int fe_build_pattern(fe_ctx *ctx);
 
 /* Borrowed host views of the setup products, valid until fe_destroy:

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <numeric>
 #include <thread>
 
@@ -61,13 +62,23 @@ void hex_gauss(int q, double xi[3]) {
   xi[2] = (2 * ((q >> 2) & 1) - 1) * g;
 }
 
+// Host threads for the setup: the hardware's, capped by FE_HOST_THREADS
+// when that is set to a positive integer, and by 64.
+unsigned host_threads() {
+  unsigned nt = std::thread::hardware_concurrency();
+  if (const char *env = std::getenv("FE_HOST_THREADS")) {
+    const long v = std::strtol(env, nullptr, 10);
+    if (v > 0) nt = unsigned(std::min<long>(v, 64));
+  }
+  return std::max(1u, std::min(nt, 64u));
+}
+
 // Runs f(begin, end) over [0, count) in chunks on the host's cores.  Each
 // index's output must go to a position fixed beforehand, so the result does
 // not depend on the number of threads or on their order.
 template <class F>
 void parallel_chunks(int64_t count, int64_t chunk, F &&f) {
-  unsigned nt = std::thread::hardware_concurrency();
-  nt = std::max(1u, std::min(nt, 64u));
+  const unsigned nt = host_threads();
   if (count <= chunk || nt == 1) {
     if (count > 0) f(int64_t(0), count);
     return;

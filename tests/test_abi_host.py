@@ -125,6 +125,27 @@ def test_pattern_and_map_bit_exact(fe, name):
     ctx.close()
 
 
+def test_setup_products_do_not_depend_on_host_threads(fe, monkeypatch):
+    """The pattern, C, its inverse and the mass are built on several host
+    threads with output ranges fixed beforehand: 1, 3 and all threads give
+    the same arrays bit for bit."""
+    base = fi.tet_beam(8, 8, 24)  # 2,025 nodes: every parallel phase takes several chunks
+    mesh = _replace(base, conn=_shuffled(base.conn))
+    outs = []
+    for nt in ("1", "3", None):
+        if nt is None:
+            monkeypatch.delenv("FE_HOST_THREADS", raising=False)
+        else:
+            monkeypatch.setenv("FE_HOST_THREADS", nt)
+        ctx = _ctx(fe, mesh)
+        sp_, ss = ctx.inverse_map()
+        outs.append((ctx.rowptr, ctx.colind, ctx.C, sp_, ss, ctx.mass()))
+        ctx.close()
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert a.dtype == b.dtype and np.array_equal(a, b)
+
+
 def test_all_fixed_pattern_is_the_identity(fe):
     mesh = MESHES["tet-2x2x3-all-fixed"]()
     ctx = _ctx(fe, mesh)
