@@ -129,7 +129,7 @@ def check_element_kernel(wl, ctx, n_elems=3000, seed=2, tol=2e-5):
 
 
 def compare_rows(ctx, A, b, Ao, bo, rows, tol, b_scale=None):
-    """Rows of the library's A and b against the oracle's.  b is judged against
+    """Rows of the library's A and b against the oracle's.  b is measured against
     b_scale when given (the size of the equation's terms): at rest b is the
     small dead load alone, while the FP32 element force leaves noise of the
     order of the stiffness times the rounding of F."""
