@@ -217,7 +217,9 @@ int fe_get_front_rows(fe_ctx *ctx, int64_t front, int64_t *n_upd, const int32_t 
 
 /* Sets the state (positions q and velocities v, [n] each; NULL keeps the
  * current value).  Default state: q = rest positions, v = 0.  v must vanish
- * on fixed DOFs (FE_ERR_ARG otherwise). */
+ * on fixed DOFs.  Host arrays (device_ptrs = 0) are checked before any
+ * device work: FE_ERR_ARG for a non-finite entry or a non-zero velocity on a
+ * fixed DOF. */
 int fe_set_state(fe_ctx *ctx, const double *q, const double *v);
 int fe_get_state(fe_ctx *ctx, double *q, double *v);
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstring>
 #include <thread>
@@ -776,10 +777,18 @@ extern "C" {
 
 int fe_set_state(fe_ctx *c, const double *q, const double *v) {
   if (!c) return FE_ERR_ARG;
+  if (!c->built) return set_error(c, FE_ERR_STATE, "fe_build_pattern has not run");
+  if (!c->opt.device_ptrs) {  // host arrays are checked before any device work
+    if (q)
+      for (int64_t i = 0; i < c->n; ++i)
+        if (!std::isfinite(q[i])) return set_error(c, FE_ERR_ARG, "q has a non-finite entry");
+    if (v)
+      for (int64_t i = 0; i < c->n; ++i) {
+        if (!std::isfinite(v[i])) return set_error(c, FE_ERR_ARG, "v has a non-finite entry");
+        if (c->fixed_dof[i] && v[i] != 0.0) return set_error(c, FE_ERR_ARG, "v must vanish on fixed DOFs");
+      }
+  }
   FE_TRY(ensure_device(c));
-  if (v && !c->opt.device_ptrs)
-    for (int64_t i = 0; i < c->n; ++i)
-      if (c->fixed_dof[i] && v[i] != 0.0) return set_error(c, FE_ERR_ARG, "v must vanish on fixed DOFs");
   if (q) FE_TRY(stage_in(c, c->dev->q, q, c->n));
   if (v) FE_TRY(stage_in(c, c->dev->v, v, c->n));
   FE_CUDA_TRY(cudaStreamSynchronize(c->dev->stream));

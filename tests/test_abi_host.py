@@ -146,6 +146,24 @@ def test_setup_products_do_not_depend_on_host_threads(fe, monkeypatch):
             assert a.dtype == b.dtype and np.array_equal(a, b)
 
 
+def test_set_state_checks_host_arrays_before_device_work(fe):
+    mesh = fi.tet_beam(1, 1, 2)
+    ctx = _ctx(fe, mesh)
+    q = mesh.X.reshape(-1).copy()
+    v = np.zeros_like(q)
+    bad_q = q.copy()
+    bad_q[7] = np.nan
+    bad_v = v.copy()
+    bad_v[-1] = np.inf
+    moving_fixed = v.copy()
+    moving_fixed[3 * int(mesh.fixed_nodes[0])] = 1e-3
+    for qq, vv in [(bad_q, None), (None, bad_v), (q, moving_fixed)]:
+        with pytest.raises(fe.FEError) as ei:
+            ctx.set_state(qq, vv)
+        assert ei.value.status == 1  # FE_ERR_ARG, decided on the host
+    ctx.close()
+
+
 def test_all_fixed_pattern_is_the_identity(fe):
     mesh = MESHES["tet-2x2x3-all-fixed"]()
     ctx = _ctx(fe, mesh)
