@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <new>
 #include <numeric>
 #include <thread>
 
@@ -84,11 +85,16 @@ void parallel_chunks(int64_t count, int64_t chunk, F &&f) {
     return;
   }
   std::atomic<int64_t> next{0};
+  std::atomic<bool> failed{false};
   auto work = [&] {
-    for (;;) {
-      const int64_t b = next.fetch_add(chunk);
-      if (b >= count) break;
-      f(b, std::min(count, b + chunk));
+    try {
+      for (;;) {
+        const int64_t b = next.fetch_add(chunk);
+        if (b >= count || failed.load()) break;
+        f(b, std::min(count, b + chunk));
+      }
+    } catch (...) {  // an exception must not leave a worker thread
+      failed.store(true);
     }
   };
   std::vector<std::thread> pool;
@@ -101,6 +107,7 @@ void parallel_chunks(int64_t count, int64_t chunk, F &&f) {
   }
   work();
   for (auto &t : pool) t.join();
+  if (failed.load()) throw std::bad_alloc();  // the only exception the bodies raise
 }
 
 // ------------------------------------------------------------------ pattern
