@@ -62,18 +62,21 @@ def _tr(A):
 
 
 def svk_psi(F, mu, lam, _=None):
+    """Saint Venant-Kirchhoff energy density mu tr(E^2) + lambda/2 (tr E)^2 (Section 3.1 names the law; textbook form)."""
     E = 0.5 * (np.swapaxes(F, -1, -2) @ F - _I3)
     trE = _tr(E)
     return mu * _tr(E @ E) + 0.5 * lam * trE * trE
 
 
 def svk_pk1(F, mu, lam, _=None):
+    """P = F S with S = 2 mu E + lambda tr(E) I: the derivative of svk_psi (Section 3.1)."""
     E = 0.5 * (np.swapaxes(F, -1, -2) @ F - _I3)
     S = 2.0 * _ex(mu, F) * E + _ex(lam, F) * _tr(E)[..., None, None] * _I3
     return F @ S
 
 
 def svk_tangent(F, mu, lam, _=None):
+    """CC = dP/dF of the Saint Venant-Kirchhoff law, exact, no projection (Section 3.1)."""
     E = 0.5 * (np.swapaxes(F, -1, -2) @ F - _I3)
     S = 2.0 * _ex(mu, F) * E + _ex(lam, F) * _tr(E)[..., None, None] * _I3
     B = F @ np.swapaxes(F, -1, -2)
@@ -85,6 +88,7 @@ def svk_tangent(F, mu, lam, _=None):
 
 
 def nh_psi(F, mu, lam, _=None):
+    """Compressible neo-Hookean energy mu/2 (I1 - 3) - mu ln J + lambda/2 (ln J)^2 with the invariants of Section 3.1 (Bonet-Wood form)."""
     J = np.linalg.det(F)
     lnJ = np.log(J)
     I1 = _tr(np.swapaxes(F, -1, -2) @ F)
@@ -92,12 +96,14 @@ def nh_psi(F, mu, lam, _=None):
 
 
 def nh_pk1(F, mu, lam, _=None):
+    """P = mu (F - F^-T) + lambda ln J F^-T: the derivative of nh_psi (Section 3.1)."""
     G = np.swapaxes(np.linalg.inv(F), -1, -2)
     lnJ = np.log(np.linalg.det(F))
     return _ex(mu, F) * (F - G) + (_ex(lam, F) * lnJ[..., None, None]) * G
 
 
 def nh_tangent(F, mu, lam, _=None):
+    """CC = dP/dF of the neo-Hookean law, exact, no projection (Section 3.1)."""
     G = np.swapaxes(np.linalg.inv(F), -1, -2)
     lnJ = np.log(np.linalg.det(F))
     CC = _ex4(mu) * np.einsum("ik,JL->iJkL", _I3, _I3)
@@ -117,12 +123,14 @@ def _mr_parts(F):
 
 
 def mr_psi(F, c10, c01, kappa):
+    """Decoupled Mooney-Rivlin energy C10 (J^-2/3 I1 - 3) + C01 (J^-4/3 I2 - 3) + kappa/2 (J - 1)^2 with the invariants I1, I2, J of Section 3.1."""
     _, I1, I2, J, _ = _mr_parts(F)
     return (c10 * (J ** (-2.0 / 3.0) * I1 - 3.0) + c01 * (J ** (-4.0 / 3.0) * I2 - 3.0)
             + 0.5 * kappa * (J - 1.0) ** 2)
 
 
 def mr_pk1(F, c10, c01, kappa):
+    """P = dpsi/dF of the decoupled Mooney-Rivlin law (Section 3.1), term by term."""
     C, I1, I2, J, G = _mr_parts(F)
     x = lambda s: s[..., None, None]  # noqa: E731
     J23, J43 = J ** (-2.0 / 3.0), J ** (-4.0 / 3.0)
@@ -134,6 +142,7 @@ def mr_pk1(F, c10, c01, kappa):
 
 
 def mr_tangent(F, c10, c01, kappa):
+    """CC = dP/dF of the decoupled Mooney-Rivlin law, exact, no projection (Section 3.1)."""
     C, I1, I2, J, G = _mr_parts(F)
     B = F @ np.swapaxes(F, -1, -2)
     x2 = lambda s: s[..., None, None]  # noqa: E731
@@ -170,7 +179,9 @@ def _hex_corners():
 
 def hex_shape(xi):
     """Trilinear shape functions N[8] and derivatives dN[8, 3] at xi on [-1,1]^3,
-    local node a at corner (2dx-1, 2dy-1, 2dz-1) with a = dx + 2dy + 4dz."""
+    local node a at corner (2dx-1, 2dy-1, 2dz-1) with a = dx + 2dy + 4dz.
+    Section 3.1: trilinear hexahedra.
+    """
     c = _hex_corners()
     f = 1.0 + c * np.asarray(xi)[None, :]
     N = np.prod(f, axis=1) / 8.0
@@ -182,13 +193,15 @@ def hex_shape(xi):
 
 
 def hex_gauss_points():
-    """2x2x2 Gauss points +-1/sqrt(3) (weight 1) in the local corner order."""
+    """2x2x2 Gauss points +-1/sqrt(3) (weight 1) in the local corner order.  Section 3.1: hexahedra integrated by 2x2x2 Gauss."""
     return _hex_corners() / math.sqrt(3.0)
 
 
 class Quadrature:
     """Rest-state data: gradN [E, Q, npe, 3] (w.r.t. rest coordinates X) and
-    weights w [E, Q] (volume for a tet; detJ0 for a hex Gauss point)."""
+    weights w [E, Q] (volume for a tet; detJ0 for a hex Gauss point).
+    Section 3.1: element kernels on P1 tets and trilinear hexes.
+    """
 
     def __init__(self, elem_type, X, conn):
         self.elem_type = elem_type
@@ -215,10 +228,11 @@ class Quadrature:
 
     @property
     def npe(self):
+        """Nodes per element (4 for P1 tets, 8 for trilinear hexes; Section 3.1)."""
         return self.conn.shape[1]
 
     def deformation_gradient(self, x):
-        """F[e, q] = sum_a x_a (outer) gradN_a."""
+        """F[e, q] = sum_a x_a (outer) gradN_a.  Section 3.1."""
         xe = np.asarray(x)[self.conn]                        # [E, npe, 3]
         return np.einsum("eai,eqaJ->eqiJ", xe, self.gradN)
 
@@ -243,7 +257,9 @@ def _params(params, E):
 
 def voigt_B(gradN):
     """[..., npe, 3] -> [..., 6, 3 npe]; strain order xx, yy, zz, xy, yz, zx
-    with engineering shears."""
+    with engineering shears.
+    Eq. "eqmodel": the linear-elastic K_0 of the co-rotational model.
+    """
     npe = gradN.shape[-2]
     B = np.zeros(gradN.shape[:-2] + (6, 3 * npe))
     for a in range(npe):
@@ -259,7 +275,7 @@ def voigt_B(gradN):
 
 
 def voigt_D(mu, lam):
-    """[E, 1] parameters -> [E, 6, 6] isotropic stress-strain matrix."""
+    """[E, 1] parameters -> [E, 6, 6] isotropic stress-strain matrix.  Eq. "eqmodel" (isotropic linear elasticity)."""
     mu, lam = np.asarray(mu).reshape(-1), np.asarray(lam).reshape(-1)
     D = np.zeros((mu.shape[0], 6, 6), dtype=np.result_type(mu, lam))
     D[:, :3, :3] = lam[:, None, None]
@@ -271,7 +287,9 @@ def voigt_D(mu, lam):
 
 def corot_rotation(quad, x):
     """R_e [E, 3, 3] = the rotation of the polar decomposition F = R S of the
-    element's (volume-averaged) deformation gradient, by SVD."""
+    element's (volume-averaged) deformation gradient, by SVD.
+    Eq. "eqmodel": the element rotation of the co-rotational model.
+    """
     F = quad.deformation_gradient(x)
     Fb = np.einsum("eq,eqiJ->eiJ", quad.w, F) / quad.w.sum(axis=1)[:, None, None]
     U, _, Vt = np.linalg.svd(Fb)
@@ -282,6 +300,7 @@ def corot_rotation(quad, x):
 
 
 def corot_K0(quad, params):
+    """Rest stiffness K0_e = sum_q w_q B^T D B of linear elasticity, the K_0 of the co-rotational model (Eq. "eqmodel")."""
     mu, lam, _ = _params(params, quad.conn.shape[0])
     B = voigt_B(quad.gradN)                                   # [E, Q, 6, 3npe]
     D = voigt_D(mu, lam)
@@ -297,6 +316,7 @@ def _block_rotation(R, npe):
 
 
 def corot_force(quad, x, params):
+    """f_e = R (K0 (R^T x - X)) of the co-rotational model (Eq. "eqmodel"), R from corot_rotation."""
     R = corot_rotation(quad, x)
     Rb = _block_rotation(R, quad.npe)
     xe = np.asarray(x)[quad.conn].reshape(R.shape[0], -1)
@@ -305,12 +325,13 @@ def corot_force(quad, x, params):
 
 
 def corot_tangent(quad, x, params):
+    """K_e = R K0 R^T: the co-rotational tangent with the rotation held fixed (Eq. "eqmodel")."""
     Rb = _block_rotation(corot_rotation(quad, x), quad.npe)
     return np.einsum("emn,enk,elk->eml", Rb, corot_K0(quad, params), Rb)
 
 
 def element_energy(quad, x, model, params):
-    """W_e = sum_q w_q psi(F_q)  -> [E]."""
+    """W_e = sum_q w_q psi(F_q)  -> [E].  Section 3.1: the elastic energy whose gradient is the internal force."""
     psi = LAWS[model][0]
     F = quad.deformation_gradient(x)
     a, b, c = _params(params, F.shape[0])
@@ -318,7 +339,7 @@ def element_energy(quad, x, model, params):
 
 
 def element_force(quad, x, model, params):
-    """f_e[3a+i] = sum_q w_q sum_J P_iJ gradN_aJ  (internal force dW_e/dx)."""
+    """f_e[3a+i] = sum_q w_q sum_J P_iJ gradN_aJ  (internal force dW_e/dx).  Section 3.1; Eq. "newton's law" uses f."""
     if model == COROTATIONAL:
         return corot_force(quad, x, params)
     P = LAWS[model][1](quad.deformation_gradient(x), *_params(params, quad.conn.shape[0]))
@@ -327,7 +348,7 @@ def element_force(quad, x, model, params):
 
 
 def element_tangent(quad, x, model, params):
-    """K_e[3a+i, 3b+k] = sum_q w_q sum_JL CC_iJkL gradN_aJ gradN_bL."""
+    """K_e[3a+i, 3b+k] = sum_q w_q sum_JL CC_iJkL gradN_aJ gradN_bL.  Section 3.1: K = df/dq, the K of Eq. "dynamic equation2"."""
     if model == COROTATIONAL:
         return corot_tangent(quad, x, params)
     CC = LAWS[model][2](quad.deformation_gradient(x), *_params(params, quad.conn.shape[0]))
@@ -338,7 +359,7 @@ def element_tangent(quad, x, model, params):
 
 
 def element_mass(elem_type, X, conn, rho):
-    """Consistent mass scalars m_e[a, b] = rho int N_a N_b dV (times I3 per block)."""
+    """Consistent mass scalars m_e[a, b] = rho int N_a N_b dV (times I3 per block).  Section 4.1: per-element mass, assembled like K."""
     X = np.asarray(X)
     if elem_type == TET4:
         Xe = X[conn]
@@ -359,7 +380,9 @@ def element_mass(elem_type, X, conn, rho):
 
 def triplet_dofs(conn):
     """(row, col) DOF of every triplet in the fill order
-    t = ((e*npe + a)*npe + b)*9 + 3i + k, value K_e[3a+i, 3b+k]."""
+    t = ((e*npe + a)*npe + b)*9 + 3i + k, value K_e[3a+i, 3b+k].
+    Section 4.2: the triplet stream of the element matrices.
+    """
     conn = np.asarray(conn, dtype=np.int64)
     E, npe = conn.shape
     a = np.arange(npe)
@@ -374,7 +397,7 @@ def triplet_dofs(conn):
 
 
 def element_values_fill_order(Ke):
-    """K_e [E, 3npe, 3npe] with index (3a+i, 3b+k) -> fill-order values [E*npe*npe*9]."""
+    """K_e [E, 3npe, 3npe] with index (3a+i, 3b+k) -> fill-order values [E*npe*npe*9].  Section 4.2: values in the triplet stream's filling order."""
     E, n, _ = Ke.shape
     npe = n // 3
     return Ke.reshape(E, npe, 3, npe, 3).transpose(0, 1, 3, 2, 4).reshape(-1)
@@ -428,20 +451,21 @@ def triplets_to_csr(n, rows, cols, vals, prev=None):
 
 
 def assemble(n_dof, conn, values_fill_order):
-    """Unconstrained global matrix: plain sum of every triplet (COO -> CSR)."""
+    """Unconstrained global matrix: plain sum of every triplet (COO -> CSR).
+    Section 4.2 ("Collect data"): duplicates summed."""
     row, col = triplet_dofs(conn)
     return sp.coo_matrix((values_fill_order, (row, col)), shape=(n_dof, n_dof)).tocsr()
 
 
 def mass_fill_order(m_scalar):
-    """Mass scalars m[e, a, b] -> fill-order triplet values (block m_ab * I3)."""
+    """Mass scalars m[e, a, b] -> fill-order triplet values (block m_ab * I3).  Section 4.1."""
     E, npe, _ = m_scalar.shape
     blk = m_scalar[:, :, :, None, None] * _I3[None, None, None]
     return blk.reshape(-1)
 
 
 def project(Afull, fixed_dofs):
-    """Projective constraints: clear fixed rows and columns, 1 on the diagonal."""
+    """Projective constraints: clear fixed rows and columns, 1 on the diagonal.  Section 5.1."""
     n = Afull.shape[0]
     keep = np.ones(n)
     keep[np.asarray(fixed_dofs, dtype=np.int64)] = 0.0
@@ -451,7 +475,7 @@ def project(Afull, fixed_dofs):
 
 
 def values_in_pattern(Aproj, rowptr, colind):
-    """Values of a sparse matrix read at every slot of a CSR pattern."""
+    """Values of a sparse matrix read at every slot of a CSR pattern.  Section 4.2: a matrix read on the compressed pattern."""
     n = rowptr.shape[0] - 1
     rows = np.repeat(np.arange(n), np.diff(rowptr))
     return np.asarray(Aproj[rows, colind]).reshape(-1)
@@ -460,7 +484,7 @@ def values_in_pattern(Aproj, rowptr, colind):
 # ================================================================ the model
 
 class Model:
-    """A mesh + material + time-integration parameters; state-independent data."""
+    """A mesh + material + time-integration parameters; state-independent data.  Section 3 (the step), Section 4 (assembly), Section 5.1 (constraints)."""
 
     def __init__(self, elem_type, X, conn, fixed_nodes, model, params, rho, h, alpha, beta):
         self.elem_type = elem_type
@@ -479,22 +503,28 @@ class Model:
 
     @classmethod
     def from_workload(cls, wl, params=None):
+        """The model of a seeded workload: mesh, law, h and the Rayleigh alpha, beta of
+        Eq. "dynamic equation1"."""
         m = wl.mesh
         return cls(m.elem_type, m.X, m.conn, m.fixed_nodes, wl.model,
                    wl.params if params is None else params, wl.rho, wl.h, wl.alpha, wl.beta)
 
     # -- per element
     def energy(self, q):
+        """Total elastic energy at positions q (Section 3.1)."""
         return element_energy(self.quad, q.reshape(-1, 3), self.model, self.params).sum()
 
     def element_force(self, q):
+        """Per-element internal forces f_e at q (Section 3.1)."""
         return element_force(self.quad, q.reshape(-1, 3), self.model, self.params)
 
     def element_tangent(self, q):
+        """Per-element tangents K_e = df_e/dq at q (Section 3.1)."""
         return element_tangent(self.quad, q.reshape(-1, 3), self.model, self.params)
 
     # -- assembled
     def internal_force(self, q):
+        """Assembled f(q) (Section 4.2 summation of the element forces)."""
         fe = self.element_force(q)
         f = np.zeros(self.n_dof, dtype=fe.dtype)
         dofs = (3 * self.conn[:, :, None] + np.arange(3)[None, None, :]).reshape(fe.shape[0], -1)
@@ -502,6 +532,7 @@ class Model:
         return f
 
     def stiffness(self, q):
+        """Assembled K(q), unprojected (Section 4.2)."""
         return assemble(self.n_dof, self.conn, element_values_fill_order(self.element_tangent(q)))
 
     def system(self, q, v, p):
@@ -515,7 +546,7 @@ class Model:
         return project(A, self.fixed_dofs), b
 
     def step(self, q, v, p):
-        """One backward-Euler step with one Newton iteration; direct solve."""
+        """One backward-Euler step with one Newton iteration; direct solve.  Eqs. "dynamic equation2" and "implicit integration"."""
         A, b = self.system(q, v, p)
         a = direct_solve(A, b)
         v1 = v + self.h * a
@@ -542,7 +573,9 @@ class Model:
         A = (1 + h alpha) M + h (beta + h) K(q_k) at q_k = q + h v + h^2 a_k
         (the derivative of K in the damping term is not taken) and sets
         a_{k+1} = a_k + delta.  Returns q+, v+, a and the norms of the
-        corrections."""
+        corrections.
+        Eqs. "newton's law" and "implicit integration".
+        """
         h = self.h
         _, _, a = self.step(q, v, p)
         corr = []
@@ -557,6 +590,7 @@ class Model:
         return q + h * v1, v1, a, corr
 
     def pattern(self):
+        """CSR pattern and map C of this mesh (Section 4.2, Section 5.1)."""
         return csr_pattern(self.n_dof, self.conn, self.fixed_dofs)
 
     def contact_jacobian(self, nodes, normals):
@@ -618,7 +652,7 @@ def pgs(W, r, sweeps, tol):
 
 
 def direct_solve(A, b):
-    """Sparse direct solve (SuperLU with a symmetric fill-reducing order)."""
+    """Sparse direct solve (SuperLU with a symmetric fill-reducing order).  The exact solve that the lagged LDL^T preconditioner of Section 3.3 approximates."""
     if A.shape[0] <= 3000:
         return np.linalg.solve(A.toarray(), b)
     lu = spla.splu(A.tocsc(), permc_spec="MMD_AT_PLUS_A")
@@ -626,7 +660,7 @@ def direct_solve(A, b):
 
 
 def rollout(model, q0, v0, loads, n_steps):
-    """q_t, v_t for t = 0..n_steps (loads(t) -> p_t as a [n_dof] vector)."""
+    """q_t, v_t for t = 0..n_steps (loads(t) -> p_t as a [n_dof] vector).  Eq. "implicit integration" iterated."""
     qs, vs = [q0.copy()], [v0.copy()]
     q, v = q0.copy(), v0.copy()
     for t in range(n_steps):
@@ -662,6 +696,7 @@ def _scatter_elem(n_dof, conn, ve):
 
 
 def rollout_with_history(model, q0, v0, loads, T):
+    """rollout keeping every (q_t, v_t, a_t): the checkpoints of the discrete adjoint (Eq. "implicit integration" iterated; the adjoint is not in the paper)."""
     qs, vs, accs = [q0.copy()], [v0.copy()], []
     q, v = q0.copy(), v0.copy()
     for t in range(T):
@@ -674,7 +709,9 @@ def rollout_with_history(model, q0, v0, loads, T):
 
 def adjoint_rollout(model, q0, v0, loads, T, q_target, v_bar_T=None):
     """Loss L = 1/2 ||q_T - q_target||^2 and its gradients:
-    returns (L, dL/ds [E] for the per-element energy scales, dL/dp [T, n])."""
+    returns (L, dL/ds [E] for the per-element energy scales, dL/dp [T, n]).
+    Not in the paper: the discrete adjoint of the step of Eq. "dynamic equation2".
+    """
     h, al, be = model.h, model.alpha, model.beta
     cK = h * (be + h)
     qs, vs, accs = rollout_with_history(model, q0, v0, loads, T)
