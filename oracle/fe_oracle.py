@@ -62,7 +62,8 @@ def _tr(A):
 
 
 def svk_psi(F, mu, lam, _=None):
-    """Saint Venant-Kirchhoff energy density mu tr(E^2) + lambda/2 (tr E)^2 (Section 3.1 names the law; textbook form)."""
+    """Saint Venant-Kirchhoff energy density mu tr(E^2) + lambda/2 (tr E)^2 (Section 3.1 names the
+    law; textbook form)."""
     E = 0.5 * (np.swapaxes(F, -1, -2) @ F - _I3)
     trE = _tr(E)
     return mu * _tr(E @ E) + 0.5 * lam * trE * trE
@@ -88,7 +89,8 @@ def svk_tangent(F, mu, lam, _=None):
 
 
 def nh_psi(F, mu, lam, _=None):
-    """Compressible neo-Hookean energy mu/2 (I1 - 3) - mu ln J + lambda/2 (ln J)^2 with the invariants of Section 3.1 (Bonet-Wood form)."""
+    """Compressible neo-Hookean energy mu/2 (I1 - 3) - mu ln J + lambda/2 (ln J)^2 with the
+    invariants of Section 3.1 (Bonet-Wood form)."""
     J = np.linalg.det(F)
     lnJ = np.log(J)
     I1 = _tr(np.swapaxes(F, -1, -2) @ F)
@@ -123,7 +125,8 @@ def _mr_parts(F):
 
 
 def mr_psi(F, c10, c01, kappa):
-    """Decoupled Mooney-Rivlin energy C10 (J^-2/3 I1 - 3) + C01 (J^-4/3 I2 - 3) + kappa/2 (J - 1)^2 with the invariants I1, I2, J of Section 3.1."""
+    """Decoupled Mooney-Rivlin energy C10 (J^-2/3 I1 - 3) + C01 (J^-4/3 I2 - 3) + kappa/2 (J - 1)^2
+    with the invariants I1, I2, J of Section 3.1."""
     _, I1, I2, J, _ = _mr_parts(F)
     return (c10 * (J ** (-2.0 / 3.0) * I1 - 3.0) + c01 * (J ** (-4.0 / 3.0) * I2 - 3.0)
             + 0.5 * kappa * (J - 1.0) ** 2)
@@ -193,7 +196,8 @@ def hex_shape(xi):
 
 
 def hex_gauss_points():
-    """2x2x2 Gauss points +-1/sqrt(3) (weight 1) in the local corner order.  Section 3.1: hexahedra integrated by 2x2x2 Gauss."""
+    """2x2x2 Gauss points +-1/sqrt(3) (weight 1) in the local corner order.  Section 3.1: hexahedra
+    integrated by 2x2x2 Gauss."""
     return _hex_corners() / math.sqrt(3.0)
 
 
@@ -275,7 +279,8 @@ def voigt_B(gradN):
 
 
 def voigt_D(mu, lam):
-    """[E, 1] parameters -> [E, 6, 6] isotropic stress-strain matrix.  Eq. "eqmodel" (isotropic linear elasticity)."""
+    """[E, 1] parameters -> [E, 6, 6] isotropic stress-strain matrix.  Eq. "eqmodel" (isotropic
+    linear elasticity)."""
     mu, lam = np.asarray(mu).reshape(-1), np.asarray(lam).reshape(-1)
     D = np.zeros((mu.shape[0], 6, 6), dtype=np.result_type(mu, lam))
     D[:, :3, :3] = lam[:, None, None]
@@ -300,7 +305,8 @@ def corot_rotation(quad, x):
 
 
 def corot_K0(quad, params):
-    """Rest stiffness K0_e = sum_q w_q B^T D B of linear elasticity, the K_0 of the co-rotational model (Eq. "eqmodel")."""
+    """Rest stiffness K0_e = sum_q w_q B^T D B of linear elasticity, the K_0 of the co-rotational
+    model (Eq. "eqmodel")."""
     mu, lam, _ = _params(params, quad.conn.shape[0])
     B = voigt_B(quad.gradN)                                   # [E, Q, 6, 3npe]
     D = voigt_D(mu, lam)
@@ -331,7 +337,8 @@ def corot_tangent(quad, x, params):
 
 
 def element_energy(quad, x, model, params):
-    """W_e = sum_q w_q psi(F_q)  -> [E].  Section 3.1: the elastic energy whose gradient is the internal force."""
+    """W_e = sum_q w_q psi(F_q)  -> [E].  Section 3.1: the elastic energy whose gradient is the
+    internal force."""
     psi = LAWS[model][0]
     F = quad.deformation_gradient(x)
     a, b, c = _params(params, F.shape[0])
@@ -339,7 +346,8 @@ def element_energy(quad, x, model, params):
 
 
 def element_force(quad, x, model, params):
-    """f_e[3a+i] = sum_q w_q sum_J P_iJ gradN_aJ  (internal force dW_e/dx).  Section 3.1; Eq. "newton's law" uses f."""
+    """f_e[3a+i] = sum_q w_q sum_J P_iJ gradN_aJ  (internal force dW_e/dx).  Section 3.1; Eq.
+    "newton's law" uses f."""
     if model == COROTATIONAL:
         return corot_force(quad, x, params)
     P = LAWS[model][1](quad.deformation_gradient(x), *_params(params, quad.conn.shape[0]))
@@ -348,7 +356,8 @@ def element_force(quad, x, model, params):
 
 
 def element_tangent(quad, x, model, params):
-    """K_e[3a+i, 3b+k] = sum_q w_q sum_JL CC_iJkL gradN_aJ gradN_bL.  Section 3.1: K = df/dq, the K of Eq. "dynamic equation2"."""
+    """K_e[3a+i, 3b+k] = sum_q w_q sum_JL CC_iJkL gradN_aJ gradN_bL.  Section 3.1: K = df/dq, the K
+    of Eq. "dynamic equation2"."""
     if model == COROTATIONAL:
         return corot_tangent(quad, x, params)
     CC = LAWS[model][2](quad.deformation_gradient(x), *_params(params, quad.conn.shape[0]))
@@ -359,7 +368,8 @@ def element_tangent(quad, x, model, params):
 
 
 def element_mass(elem_type, X, conn, rho):
-    """Consistent mass scalars m_e[a, b] = rho int N_a N_b dV (times I3 per block).  Section 4.1: per-element mass, assembled like K."""
+    """Consistent mass scalars m_e[a, b] = rho int N_a N_b dV (times I3 per block).  Section 4.1:
+    per-element mass, assembled like K."""
     X = np.asarray(X)
     if elem_type == TET4:
         Xe = X[conn]
@@ -397,7 +407,8 @@ def triplet_dofs(conn):
 
 
 def element_values_fill_order(Ke):
-    """K_e [E, 3npe, 3npe] with index (3a+i, 3b+k) -> fill-order values [E*npe*npe*9].  Section 4.2: values in the triplet stream's filling order."""
+    """K_e [E, 3npe, 3npe] with index (3a+i, 3b+k) -> fill-order values [E*npe*npe*9].  Section
+    4.2: values in the triplet stream's filling order."""
     E, n, _ = Ke.shape
     npe = n // 3
     return Ke.reshape(E, npe, 3, npe, 3).transpose(0, 1, 3, 2, 4).reshape(-1)
@@ -475,7 +486,8 @@ def project(Afull, fixed_dofs):
 
 
 def values_in_pattern(Aproj, rowptr, colind):
-    """Values of a sparse matrix read at every slot of a CSR pattern.  Section 4.2: a matrix read on the compressed pattern."""
+    """Values of a sparse matrix read at every slot of a CSR pattern.  Section 4.2: a matrix read
+    on the compressed pattern."""
     n = rowptr.shape[0] - 1
     rows = np.repeat(np.arange(n), np.diff(rowptr))
     return np.asarray(Aproj[rows, colind]).reshape(-1)
@@ -484,7 +496,8 @@ def values_in_pattern(Aproj, rowptr, colind):
 # ================================================================ the model
 
 class Model:
-    """A mesh + material + time-integration parameters; state-independent data.  Section 3 (the step), Section 4 (assembly), Section 5.1 (constraints)."""
+    """A mesh + material + time-integration parameters; state-independent data.  Section 3 (the
+    step), Section 4 (assembly), Section 5.1 (constraints)."""
 
     def __init__(self, elem_type, X, conn, fixed_nodes, model, params, rho, h, alpha, beta):
         self.elem_type = elem_type
@@ -546,7 +559,8 @@ class Model:
         return project(A, self.fixed_dofs), b
 
     def step(self, q, v, p):
-        """One backward-Euler step with one Newton iteration; direct solve.  Eqs. "dynamic equation2" and "implicit integration"."""
+        """One backward-Euler step with one Newton iteration; direct solve.  Eqs. "dynamic
+        equation2" and "implicit integration"."""
         A, b = self.system(q, v, p)
         a = direct_solve(A, b)
         v1 = v + self.h * a
@@ -652,7 +666,8 @@ def pgs(W, r, sweeps, tol):
 
 
 def direct_solve(A, b):
-    """Sparse direct solve (SuperLU with a symmetric fill-reducing order).  The exact solve that the lagged LDL^T preconditioner of Section 3.3 approximates."""
+    """Sparse direct solve (SuperLU with a symmetric fill-reducing order).  The exact solve that
+    the lagged LDL^T preconditioner of Section 3.3 approximates."""
     if A.shape[0] <= 3000:
         return np.linalg.solve(A.toarray(), b)
     lu = spla.splu(A.tocsc(), permc_spec="MMD_AT_PLUS_A")
@@ -660,7 +675,8 @@ def direct_solve(A, b):
 
 
 def rollout(model, q0, v0, loads, n_steps):
-    """q_t, v_t for t = 0..n_steps (loads(t) -> p_t as a [n_dof] vector).  Eq. "implicit integration" iterated."""
+    """q_t, v_t for t = 0..n_steps (loads(t) -> p_t as a [n_dof] vector).  Eq. "implicit
+    integration" iterated."""
     qs, vs = [q0.copy()], [v0.copy()]
     q, v = q0.copy(), v0.copy()
     for t in range(n_steps):
@@ -696,7 +712,8 @@ def _scatter_elem(n_dof, conn, ve):
 
 
 def rollout_with_history(model, q0, v0, loads, T):
-    """rollout keeping every (q_t, v_t, a_t): the checkpoints of the discrete adjoint (Eq. "implicit integration" iterated; the adjoint is not in the paper)."""
+    """rollout keeping every (q_t, v_t, a_t): the checkpoints of the discrete adjoint (Eq.
+    "implicit integration" iterated; the adjoint is not in the paper)."""
     qs, vs, accs = [q0.copy()], [v0.copy()], []
     q, v = q0.copy(), v0.copy()
     for t in range(T):
