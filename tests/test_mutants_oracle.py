@@ -6,8 +6,10 @@ unmodified copy passes.
 The mistakes cover the step's system (Eqs. "dynamic equation1/2": a dropped
 or sign-flipped damping term, a wrong stiffness or mass coefficient, the
 projection of fixed rows, Section 5.1), the integration (Eq. "implicit
-integration"), the material laws (Section 3.1) and the consistent mass
-(Section 4.1).
+integration"), the material laws and the hex quadrature (Section 3.1), the
+consistent mass (Section 4.1), the co-rotational rotation (Eq. "eqmodel"), the
+pattern (Section 4.2) and the contact stages (Section "Lagrangian
+multipliers": projection, offset scaling, correction sign).
 """
 import os
 import shutil
@@ -40,6 +42,13 @@ MUTANTS = [
     ("fixed rows of b not cleared",
      "        b[self.fixed_dofs] = 0.0\n        return project(A, self.fixed_dofs), b",
      "        return project(A, self.fixed_dofs), b"),
+    ("PGS without the projection onto lambda >= 0",
+     "new = max(0.0, lam[i] + (r[i] - W[i] @ lam) / W[i, i])", "new = lam[i] + (r[i] - W[i] @ lam) / W[i, i]"),
+    ("contact offset divided by h, not h^2", "x_pred)) / (h * h)", "x_pred)) / h"),
+    ("contact correction with the wrong sign", "a = a_free + Z @ lam", "a = a_free - Z @ lam"),
+    ("co-rotational rotation transposed", "    return U @ Vt\n", "    return np.swapaxes(U @ Vt, 1, 2)\n"),
+    ("pattern: fixed rows without their diagonal slot",
+     "uniq = np.unique(np.concatenate([keys, fd * n_dof + fd]))", "uniq = np.unique(keys)"),
 ]
 
 
