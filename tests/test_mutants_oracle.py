@@ -8,8 +8,9 @@ or sign-flipped damping term, a wrong stiffness or mass coefficient, the
 projection of fixed rows, Section 5.1), the integration (Eq. "implicit
 integration"), the material laws and the hex quadrature (Section 3.1), the
 consistent mass (Section 4.1), the co-rotational rotation (Eq. "eqmodel"), the
-pattern (Section 4.2) and the contact stages (Section "Lagrangian
-multipliers": projection, offset scaling, correction sign).
+pattern (Section 4.2), the contact stages (Section "Lagrangian
+multipliers": projection, offset scaling, correction sign) and the discrete
+adjoint (not in the paper: the chain of one step's residual).
 """
 import os
 import shutil
@@ -49,6 +50,12 @@ MUTANTS = [
     ("co-rotational rotation transposed", "    return U @ Vt\n", "    return np.swapaxes(U @ Vt, 1, 2)\n"),
     ("pattern: fixed rows without their diagonal slot",
      "uniq = np.unique(np.concatenate([keys, fd * n_dof + fd]))", "uniq = np.unique(keys)"),
+    ("adjoint: a_bar without the h^2 q_bar term",
+     "a_bar = h * v_bar + h * h * q_bar", "a_bar = h * v_bar + h * q_bar"),
+    ("adjoint: v_bar update without alpha M lambda",
+     "gv = al * (model.M @ lam) + (be + h) * Klam", "gv = (be + h) * Klam"),
+    ("adjoint: third-derivative term dK[lambda] dropped",
+     "gq = _scatter_elem(model.n_dof, conn, dKu + Kl)", "gq = _scatter_elem(model.n_dof, conn, Kl)"),
 ]
 
 
