@@ -9,7 +9,8 @@ projection of fixed rows, Section 5.1), the integration (Eq. "implicit
 integration"), the material laws and the hex quadrature (Section 3.1), the
 consistent mass (Section 4.1), the co-rotational rotation (Eq. "eqmodel"), the
 pattern (Section 4.2), the contact stages (Section "Lagrangian
-multipliers": projection, offset scaling, correction sign) and the discrete
+multipliers": projection, offset scaling, correction sign), the filling-order
+test of Algorithm "add" (Section 4.2), Newton's corrections and the discrete
 adjoint (not in the paper: the chain of one step's residual).
 """
 import os
@@ -56,6 +57,11 @@ MUTANTS = [
      "gv = al * (model.M @ lam) + (be + h) * Klam", "gv = (be + h) * Klam"),
     ("adjoint: third-derivative term dK[lambda] dropped",
      "gq = _scatter_elem(model.n_dof, conn, dKu + Kl)", "gq = _scatter_elem(model.n_dof, conn, Kl)"),
+    ("Newton: correction added with the wrong sign", "            a = a + delta\n", "            a = a - delta\n"),
+    ("Newton: K taken at the start of the step", "            K = self.stiffness(qk)\n",
+     "            K = self.stiffness(q)\n"),
+    ("filling-order test compares the rows only",
+     "np.array_equal(prev[0], rows) and np.array_equal(prev[1], cols))", "np.array_equal(prev[0], rows))"),
 ]
 
 

@@ -63,3 +63,11 @@ def test_filling_order_test():
     assert not O.triplets_to_csr(3, rows[:3], cols[:3], v[:3], prev=(rows, cols))[0]   # shorter stream
     order = np.array([3, 1, 2, 0])
     assert not O.triplets_to_csr(3, rows[order], cols[order], v, prev=(rows, cols))[0]  # same set, new order
+    # the test compares both indices of every triplet: one column changed with
+    # every row the same, or one row changed with every column the same
+    cols2 = cols.copy()
+    cols2[1] = 2
+    assert not O.triplets_to_csr(3, rows, cols2, v, prev=(rows, cols))[0]
+    rows2 = rows.copy()
+    rows2[3] = 2
+    assert not O.triplets_to_csr(3, rows2, cols, v, prev=(rows, cols))[0]
