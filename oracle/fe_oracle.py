@@ -18,7 +18,9 @@ What it computes, in the paper's order (arXiv 2306.05893, Section 3):
     b = p - f - (alpha M + (beta + h) K) v (Eq. "dynamic equation1" with the
     Rayleigh damping B = alpha M + beta K);
   * a direct sparse solve of A a = b, then backward Euler
-    v+ = v + h a, q+ = q + h v+ (Eq. "implicit integration");
+    v+ = v + h a, q+ = q + h v+ (Eq. "implicit integration"); for meshes
+    whose direct factor is too large for the host, the same step with a
+    Jacobi-preconditioned CG solve to a stated residual (cg_solve);
   * the CSR pattern and the triplet -> slot map C (Section 4.2), built here by
     sorting unique (row, col) keys, i.e. independently of the double transpose;
   * frictionless contact against rigid planes by Lagrange multipliers
@@ -567,6 +569,18 @@ class Model:
         q1 = q + self.h * v1
         return q1, v1, a
 
+    def step_cg(self, q, v, p, tol):
+        """The same step as step() with the linear system solved by Jacobi
+        CG to ||b - A a|| <= tol ||b|| (cg_solve) instead of the direct
+        solve: the CPU analogue of fast assembly + CG, and, at tol 1e-13, a
+        reference for meshes whose direct factor is too large for the host.
+        Returns q+, v+, a and the CG iterations."""
+        A, b = self.system(q, v, p)
+        a, its = cg_solve(A.tocsr(), b, tol)
+        v1 = v + self.h * a
+        q1 = q + self.h * v1
+        return q1, v1, a, its
+
     def newton_residual(self, q, v, p, a):
         """Nonlinear backward-Euler residual of one step at the acceleration a:
         R(a) = M a + f(q') + (alpha M + beta K(q')) v' - p with v' = v + h a,
@@ -672,6 +686,38 @@ def direct_solve(A, b):
         return np.linalg.solve(A.toarray(), b)
     lu = spla.splu(A.tocsc(), permc_spec="MMD_AT_PLUS_A")
     return lu.solve(b)
+
+
+def cg_solve(A, b, tol, maxiter=100000):
+    """Conjugate gradients (Hestenes-Stiefel) with the Jacobi preconditioner
+    diag(A)^-1 on the SPD system A x = b from x = 0, stopped once the true
+    residual satisfies ||b - A x||_2 <= tol ||b||_2: the stopping test the
+    paper's CG uses on the assembled system (Section 6.2, "System
+    solution"), here without the LDL^T preconditioner.  Returns (x, iterations).
+    Each iteration is one sparse product and a few vector updates."""
+    x = np.zeros_like(b)
+    bn = np.linalg.norm(b)
+    if bn == 0.0:
+        return x, 0
+    dinv = 1.0 / A.diagonal()
+    r = b.copy()
+    z = dinv * r
+    p = z.copy()
+    rz = r @ z
+    for k in range(1, maxiter + 1):
+        Ap = A @ p
+        alpha = rz / (p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        if np.linalg.norm(r) <= tol * bn:
+            r = b - A @ x                     # the recursion's residual drifts: confirm with the true one
+            if np.linalg.norm(r) <= tol * bn:
+                return x, k
+        z = dinv * r
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    raise RuntimeError("cg_solve: no convergence")
 
 
 def rollout(model, q0, v0, loads, n_steps):

@@ -422,3 +422,37 @@ def test_equilibrium_is_stationary():
     p = m.internal_force(q)
     q1, v1, a1 = m.step(q, np.zeros_like(q), p)
     assert np.abs(a1).max() < 1e-9 * np.abs(p).max() / m.M.diagonal().max()
+
+
+def test_cg_solve_reaches_the_direct_solution():
+    """The Jacobi CG of the oracle (cg_solve) against the dense solve on an
+    SPD system of a small beam: the returned residual meets the tolerance
+    and the solution agrees with numpy's dense solve within the tolerance
+    times the condition number's reach."""
+    wl = fi.workload("tet-mr", a=2, b=2, c=6)
+    m = O.Model.from_workload(wl)
+    q = wl.mesh.X.reshape(-1).copy()
+    A, b = m.system(q, np.zeros_like(q), wl.p(0).reshape(-1))
+    x, its = O.cg_solve(A.tocsr(), b, 1e-13)
+    assert its > 1
+    assert np.linalg.norm(b - A @ x) <= 1e-13 * np.linalg.norm(b)
+    xd = np.linalg.solve(A.toarray(), b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    x0, its0 = O.cg_solve(A.tocsr(), np.zeros_like(b), 1e-13)
+    assert its0 == 0 and not x0.any()
+
+
+def test_cg_step_matches_direct_step():
+    """step_cg at tol 1e-13 and step (direct solve) give the same positions
+    after three steps of the loaded Mooney-Rivlin beam, to 1e-10 of the
+    displacement."""
+    wl = fi.workload("tet-mr", a=2, b=2, c=6)
+    m = O.Model.from_workload(wl)
+    q = q2 = wl.mesh.X.reshape(-1).copy()
+    v = v2 = np.zeros_like(q)
+    for t in range(3):
+        p = wl.p(t).reshape(-1)
+        q, v, _ = m.step(q, v, p)
+        q2, v2, _, _ = m.step_cg(q2, v2, p, 1e-13)
+    X = wl.mesh.X.reshape(-1)
+    assert np.linalg.norm(q2 - q) <= 1e-10 * np.linalg.norm(q - X)
