@@ -2,8 +2,9 @@
 """Implicit FE steps/s on GB300: the 350k-DOF Mooney-Rivlin tet beam.
 
 One step = element force/tangent -> gather assembly of A and b -> lagged
-LDL^T (refactorised every 5 steps on the side stream) -> PCG with FP64
-residual refinement to ||r|| <= 1e-8 ||b|| -> backward Euler.
+LDL^T (A_s snapshot every 5 steps, factored on the side stream, first used k
+steps later) -> PCG with FP64 residual refinement to ||r|| <= 1e-8 ||b|| ->
+backward Euler.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -57,13 +58,44 @@ def _tf32_peak():
 
 MATERIAL_NAMES = {0: "Saint Venant-Kirchhoff", 1: "neo-Hookean", 2: "Mooney-Rivlin"}
 
-# DRAM bytes per launch of the update kernel on the 350k-DOF workload: one ncu
-# capture of dram__bytes_read.sum + dram__bytes_write.sum over the 194 update
-# launches of a factorisation, divided by 194.  To be retaken (or dropped)
-# whenever the kernel changes; other workloads report None.
-UPDATE_TRAFFIC = {"tet30x30x120-mr": 202.4e6}
-# DRAM bytes of one application (forward + backward) with the binary16 Y
-APPLY_TRAFFIC = {"tet30x30x120-mr": 1.927e9}
+def _source_sha(name):
+    """First 16 hex digits of the SHA-256 of a CUDA source file of the package."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_2306_05893_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _profile_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summaries: every line
+    'bench-traffic: {json}' under profiles/ names a kernel, the workload it
+    is scaled to, the bytes per launch, the capture date and the SHA of the
+    source file the kernel was built from.  An entry counts only while that
+    source is unchanged (a changed kernel has no traffic figure until it is
+    captured again)."""
+    out = {}
+    pdir = os.path.join(ROOT, "profiles")
+    for fn in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if not fn.endswith(".md"):
+            continue
+        with open(os.path.join(pdir, fn)) as f:
+            for line in f:
+                if not line.startswith("bench-traffic:"):
+                    continue
+                try:
+                    e = json.loads(line.split(":", 1)[1])
+                except ValueError:
+                    continue
+                if e.get("workload") != workload:
+                    continue
+                try:
+                    if _source_sha(e["source"]) != e["source_sha16"]:
+                        continue
+                except OSError:
+                    continue
+                e["profile"] = "profiles/" + fn
+                out[e["kernel"]] = e
+    return out
 
 
 class ClockSampler:
@@ -122,114 +154,111 @@ class ClockSampler:
 
 # --------------------------------------------------------------- oracle arm
 
-def oracle_step_sample(wl):
-    """Time the FP64 oracle, as it stands, on a bounded sample of one step of
-    the workload (about 10-20 s of host CPU): its element force + tangent +
-    triplet assembly on a contiguous slice of the elements, scaled to the
-    whole mesh, plus its direct sparse solve timed on two smaller beams of the
-    same family and extrapolated to the workload's DOF count with the fitted
-    power law t ~ n^k.  Returns (steps/s, cores, description, s/step)."""
+def oracle_step(wl, t=0, q=None, v=None):
+    """One full step of the FP64 oracle, as it stands, on the whole workload:
+    element force and tangent, triplet assembly, A and b, then its Jacobi CG
+    solve (cg_solve) to the workload's tolerance ||b - A a|| <= tol ||b||
+    and backward Euler: the CPU analogue of fast assembly + CG.  (The
+    oracle's direct solve does not finish in minutes at 350k DOF.)  The
+    model's setup (mass, rest data) is not timed.  Returns (seconds, CG
+    iterations, threads used = CPU time / wall time, q+, v+)."""
     from oracle import fe_oracle as O
-    import fe_inputs as fi
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    mesh = wl.mesh
-    E = mesh.n_elems
-    n_dof = 3 * mesh.n_nodes
-    q = mesh.X.reshape(-1).copy()
-    n_sl = min(E, 60000)
-    sl = np.arange(n_sl)
-    quad = O.Quadrature(mesh.elem_type, mesh.X, mesh.conn[sl])
-    t0 = time.perf_counter()
-    O.element_force(quad, q.reshape(-1, 3), wl.model, wl.params)
-    Ke = O.element_tangent(quad, q.reshape(-1, 3), wl.model, wl.params)
-    O.assemble(n_dof, mesh.conn[sl], O.element_values_fill_order(Ke))
-    t_elem = (time.perf_counter() - t0) * E / n_sl
-    pts = []
-    for a in (8, 12):
-        small = fi.workload("tet-mr", a=a, b=a, c=4 * a)
-        sm = O.Model.from_workload(small)
-        qs = small.mesh.X.reshape(-1).copy()
-        A, b = sm.system(qs, np.zeros_like(qs), small.p(0).reshape(-1))
-        t0 = time.perf_counter()
-        O.direct_solve(A, b)
-        pts.append((A.shape[0], time.perf_counter() - t0))
-    (n1, t1), (n2, t2) = pts
-    k = float(np.log(t2 / t1) / np.log(n2 / n1))
-    t_solve = t2 * (n_dof / n2) ** k
-    t_step = t_elem + t_solve
-    desc = (f"oracle element force+tangent+triplet assembly on {n_sl} of {E} tets scaled x{E / n_sl:.1f} "
-            f"({t_elem:.1f} s); oracle direct solve timed at {n1} and {n2} DOF ({t1:.2f} s, {t2:.2f} s), "
-            f"fitted t ~ n^{k:.2f}, extrapolated to {n_dof} DOF ({t_solve:.0f} s); one step = {t_step:.0f} s")
-    return 1.0 / t_step, cores, desc, t_step
+    om = O.Model.from_workload(wl)
+    if q is None:
+        q = wl.mesh.X.reshape(-1).copy()
+        v = np.zeros_like(q)
+    t0, c0 = time.perf_counter(), time.process_time()
+    q1, v1, _, its = om.step_cg(q, v, wl.p(t).reshape(-1), wl.tol)
+    el = time.perf_counter() - t0
+    return el, its, (time.process_time() - c0) / el, q1, v1
+
+
+def cpu_baseline(wl):
+    el, its, thr, _, _ = oracle_step(wl)
+    return {"value": 1.0 / el, "unit": "steps/s", "cores": max(1, int(round(thr))), "kind": "oracle",
+            "sample": f"one full FP64 oracle step of {wl.name} (all {wl.mesh.n_elems} elements, "
+                      f"{3 * wl.mesh.n_nodes} DOF): element force+tangent, triplet assembly, Jacobi CG "
+                      f"to {wl.tol:g} ({its} iterations), integration; measured, not extrapolated; "
+                      f"{el:.1f} s wall, {thr:.2f} threads busy on average"}
 
 
 def run_reference(args, rank):
-    """The oracle arm: each step is one bounded oracle sample (see above)."""
+    """The oracle arm: full oracle steps of the workload, at most 2 (each
+    about a minute of host CPU), timed one after the other from the rest
+    state; `steps` is the number actually run."""
     if rank != 0:
         return
     import fe_inputs as fi
     wl = fi.workload(WORKLOAD)
-    # bounded: at most 8 timed samples after at most 2 untimed ones (each
-    # sample is 10-30 s of CPU work), so the arm ends within a few minutes
-    steps = max(1, min(args.steps, 8))
-    warm = max(0, min(args.warmup, 2))
-    for _ in range(warm):
-        oracle_step_sample(wl)
-    vals, desc, cores = [], "", 0
-    for _ in range(steps):
-        v, cores, desc, _ = oracle_step_sample(wl)
-        vals.append(v)
-    value = statistics.median(vals)
+    steps = max(1, min(args.steps, 2))
+    q = v = None
+    times, its, thr = [], [], []
+    for t in range(steps):
+        el, it, th, q, v = oracle_step(wl, t, q, v)
+        times.append(el)
+        its.append(it)
+        thr.append(th)
+    tot = sum(times)
+    value = steps / tot
+    cores = max(1, int(round(float(np.mean(thr)))))
     out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
-           "steps": steps, "warmup": warm, "ms_per_step": 1e3 / value,
+           "steps": steps, "warmup": 0, "ms_per_step": 1e3 * tot / steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "precision": "fp64 oracle (direct solve)"},
+           "config": {"workload": WORKLOAD, "precision": "fp64 oracle (Jacobi CG to the workload tolerance)",
+                      "cg_iterations": its},
            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                            "sample": desc},
+                            "sample": f"{steps} full oracle steps of {WORKLOAD} from rest "
+                                      f"({', '.join('%.1f s' % x for x in times)}); CG iterations {its}"},
            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------------------- side metrics
 
-def measure_adjoint(fe, torch, T=20, reps=2):
+def measure_adjoint(fe, torch, T=20):
     """grads/s of the adjoint workload: hex 20x20x80 neo-Hookean beam with a
     per-element log-normal Young's modulus (median 1e4, sigma 0.3, seed 11),
-    L = 1/2 ||q_T - q*||^2 after T steps (q* from the seed-12 field); one
-    gradient = forward rollout with checkpoints + reverse adjoint sweep."""
+    L = 1/2 ||q_T - q*||^2 after T steps; one gradient = forward rollout with
+    checkpoints + reverse adjoint sweep.  Measured in the mixed path (2
+    gradients) and in FP64 (1 gradient), after one untimed gradient each."""
     import fe_inputs as fi
     mesh = fi.hex_beam(20, 20, 80, jitter=0.1, seed=1)
     nu = 3.1e4 / (2 * (3.1e4 + 3.4e3))
     base = np.array([*fi.lame_from_young(1.0, nu), 0.0])
     E = fi.lognormal_modulus(mesh.n_elems, seed=11)
     trac = fi.end_traction(mesh, (50.0, 0.0, 0.0)).reshape(-1)
-    ctx = fe.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.NEOHOOKE, 1000.0,
-                       E[:, None] * base[None, :], 0.01, 0.1, 0.01, precision=1, refactor_every=5,
-                       keep_checkpoints=1)
-    q = np.empty(ctx.n)
-    v = np.empty(ctx.n)
     q0 = mesh.X.reshape(-1).copy()
     qt = q0 + 1e-4
+    out = {"unit": "grads/s", "workload": "hex20x20x80-nh per-element E, T=20", "n_dof": 3 * mesh.n_nodes}
+    for prec, reps in ((1, 2), (0, 1)):
+        ctx = fe.FEContext(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.NEOHOOKE, 1000.0,
+                           E[:, None] * base[None, :], 0.01, 0.1, 0.01, precision=prec, refactor_every=5,
+                           keep_checkpoints=1)
+        q = np.empty(ctx.n)
+        v = np.empty(ctx.n)
 
-    def one():
-        ctx.set_state(q0, np.zeros_like(q0))
-        ctx.clear_checkpoints()
-        for _ in range(T):
-            ctx.step(trac, q, v)
-        ds, _ = ctx.adjoint(q - qt, with_dp=False)
-        return ds
+        def one():
+            ctx.set_state(q0, np.zeros_like(q0))
+            ctx.clear_checkpoints()
+            for _ in range(T):
+                ctx.step(trac, q, v)
+            ds, _ = ctx.adjoint(q - qt, with_dp=False)
+            return ds
 
-    one()  # warm-up (factor buffers, first-call setup)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        one()
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    ctx.close()
-    return {"value": reps / el, "unit": "grads/s", "workload": "hex20x20x80-nh per-element E, T=20",
-            "n_dof": 3 * mesh.n_nodes, "precision": "mixed", "s_per_grad": el / reps}
+        one()  # warm-up (factor buffers, first-call setup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            one()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        ctx.close()
+        key = "mixed" if prec else "fp64"
+        out[key] = {"value": reps / el, "s_per_grad": el / reps, "grads_timed": reps}
+    out["value"] = out["mixed"]["value"]
+    out["precision"] = "mixed (fp64 alongside)"
+    return out
 
 
 def run_contact(args, world, rank, local, torch, dist):
@@ -340,6 +369,58 @@ def run_batch(args, world, rank, local, torch, dist):
 
 # --------------------------------------------------------------------- ours
 
+def _ctx_for(fe, wl, args, **kw):
+    return fe.FEContext.from_workload(wl, nd_leaf_nodes=args.nd_leaf, use_graph=1 if args.graph else 0,
+                                      factor_tf32=1 if args.factor_tf32 else 0,
+                                      precond_fp16=args.precond_fp16 if wl.precision else 0,
+                                      factor_lag=args.lag, element_fp64=1 if args.element_fp64 else 0, **kw)
+
+
+def _streaming_rooflines(wl, info, stage_ms, stage_calls, hbm, peak_kind, args, traffic):
+    """Achieved HBM bandwidth of the streaming kernels from their algorithmic
+    bytes per launch (the units each launch processes times the bytes per
+    unit) and their average live launch time (CUDA events on the stream that
+    runs them)."""
+    n, nnz, E = info["n"], info["nnz"], wl.mesh.n_elems
+    npe = 4 if wl.mesh.elem_type == 0 else 8
+    mixed = bool(wl.precision)
+    kb = 4 if (mixed and not args.element_fp64) else 8     # stored tangent entry
+    ab = 4 if mixed else 8                                 # inner matrix / vector entry
+    kept, nblk = info["ntrip_kept"], info["n_blocks"]
+    nodes = wl.mesh.n_nodes
+    rest = (10 if npe == 4 else 200) * 8
+    bytes_ = {
+        # per element: K_e and f_e out, rest data + 3 parameters + connectivity in;
+        # per node: q and X in
+        "element": E * ((3 * npe) ** 2 * kb + 3 * npe * 8 + rest + 24 + 4 * npe) + nodes * 48,
+        # per gathered triplet its K_e value; per block its source list entry
+        # (kept / 9 of them), bsrc_ptr, column and mass; per slot A (and its
+        # FP64 copy in the mixed path); per element its forces and incidence;
+        # per row rowptr and v, p, b
+        "assembly": kept * kb + (kept // 9) * 4 + nblk * 16 + nnz * (ab + (8 if mixed else 0))
+        + E * (3 * npe * 8 + 4 * npe) + n * (4 + 24) + nodes * 8,
+        "spmv": nnz * (ab + 4) + (n + 1) * 4 + 2 * n * ab,
+        "residual": nnz * (8 + 4) + (n + 1) * 4 + 3 * n * 8,
+    }
+    yb = 2 if (mixed and args.precond_fp16) else ab
+    bytes_["apply"] = 2 * info["y_nnz"] * yb + 6 * info["n_free"] * ab + 2 * n * ab
+    kern = {"element": "tet_kernel" if npe == 4 else "hex_kernel", "assembly": "assemble_block_kernel",
+            "spmv": "spmv_dot_kernel", "residual": "residual_kernel", "apply": "fwd_kernel + bwd_kernel"}
+    out = {}
+    for k, b in bytes_.items():
+        calls = stage_calls.get(k, 0)
+        if not calls:
+            continue
+        ms = stage_ms[k] / calls
+        gbs = b / (ms / 1e3) / 1e9 if ms > 0 else None
+        tr = traffic.get(kern[k])
+        out[k] = {"kernel": kern[k], "bytes_per_launch": int(b), "avg_ms": ms, "achieved": gbs, "peak": hbm,
+                  "peak_kind": peak_kind, "unit": "GB/s", "frac": gbs / hbm if gbs else None,
+                  "traffic": tr["bytes_per_launch"] if tr else None,
+                  "traffic_source": f"{tr['profile']} ({tr['date']})" if tr else None}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,9 +428,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--lag", type=int, default=0,
+                    help="factor_lag k: the factor of A_s first preconditions step s+k (0: k = R)")
+    ap.add_argument("--element-fp64", action="store_true",
+                    help="mixed precision with FP64 element tangents (the FP64 system exactly)")
     ap.add_argument("--factor-tf32", action="store_true",
                     help="mixed precision: plain TF32 products in the factor's trailing updates")
     ap.add_argument("--precond-fp16", type=int, default=1, choices=[0, 1],
@@ -388,20 +473,19 @@ def main():
     wl = fi.workload(args.workload)
     if args.precision is not None:
         wl.precision = 1 if args.precision == "mixed" else 0
+    if args.lag <= 0:
+        args.lag = wl.refactor_every
     K, W = args.steps, args.warmup
     stream = torch.cuda.Stream(priority=-1)  # above the library's background factor stream
     dev = torch.device("cuda", local)
-    ctx = fe.FEContext.from_workload(wl, device_ptrs=1, stream=stream.cuda_stream, profile_stages=1,
-                                     nd_leaf_nodes=args.nd_leaf, use_graph=1 if args.graph else 0,
-                                     factor_tf32=1 if args.factor_tf32 else 0,
-                                     precond_fp16=args.precond_fp16 if wl.precision else 0)
+    ctx = _ctx_for(fe, wl, args, device_ptrs=1, stream=stream.cuda_stream, profile_stages=1)
     info = ctx.info()
     n = ctx.n
     loads = torch.tensor(np.stack([wl.p(t).reshape(-1) for t in range(W + K)]), dtype=torch.float64,
                          device=dev)
     q_out = torch.empty(n, dtype=torch.float64, device=dev)
     v_out = torch.empty(n, dtype=torch.float64, device=dev)
-    iters = []
+    iters, ages, refs = [], [], []
     with torch.cuda.stream(stream):
         for t in range(W):
             ctx.step(loads[t], q_out, v_out)
@@ -415,7 +499,10 @@ def main():
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for t in range(W, W + K):
-            iters.append(ctx.step(loads[t], q_out, v_out).iters)
+            si = ctx.step(loads[t], q_out, v_out)
+            iters.append(si.iters)
+            ages.append(si.factor_age)
+            refs.append(si.refinements)
         ev1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -433,20 +520,21 @@ def main():
     ctx.close()
     del loads
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: the same steps W .. W+K-1
+    # after the same warm-up, with the same stage instrumentation
     e2e = None
-    if args.e2e_steps > 0:
-        ctx2 = fe.FEContext.from_workload(wl, device_ptrs=0, nd_leaf_nodes=args.nd_leaf,
-                                          use_graph=1 if args.graph else 0,
-                                          factor_tf32=1 if args.factor_tf32 else 0,
-                                     precond_fp16=args.precond_fp16 if wl.precision else 0)
+    if not args.no_e2e:
+        ctx2 = _ctx_for(fe, wl, args, device_ptrs=0, profile_stages=1)
         qh = np.empty(n)
         vh = np.empty(n)
         its2 = []
         for t in range(W):
             ctx2.step(wl.p(t).reshape(-1), qh, vh)
-        host_loads = [np.ascontiguousarray(wl.p(t).reshape(-1)) for t in range(W, W + args.e2e_steps)]
+        host_loads = [np.ascontiguousarray(wl.p(t).reshape(-1)) for t in range(W, W + K)]
         torch.cuda.synchronize()
+        ctx2.reset_stage_times()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         for pl in host_loads:
             its2.append(ctx2.step(pl, qh, vh))
@@ -454,52 +542,41 @@ def main():
         el = time.perf_counter() - t0
         ctx2.close()
         scal_reads = sum(i.iters + i.refinements + 1 for i in its2) / len(its2)
-        e2e = {"value": world * args.e2e_steps / el if world == 1 else None, "unit": "steps/s",
-               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": int(16 * n + 144 * scal_reads)}
         if world > 1:
             tt = torch.tensor([el], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e["value"] = world * args.e2e_steps / float(tt.item())
+            el = float(tt.item())
+        e2e = {"value": world * K / el, "unit": "steps/s", "steps": K, "timer": "host clock",
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": int(16 * n + 144 * scal_reads)}
 
-    # roofline of the dominant kernel: the factor's trailing-update launches
-    # (tensor cores, 3xTF32), and of the HBM-bound preconditioner application
+    # roofline of the dominant kernel by share of the launch list: the
+    # factor's trailing-update launches (tensor cores, 3xTF32)
     hbm, peak_kind = _peaks()
     tf32_peak, tf32_src = _tf32_peak()
+    traffic = _profile_traffic(args.workload)
     upd_calls = max(1, stage_calls["factor_update"])
     upd_ms = stage_ms["factor_update"] / upd_calls
     upd_flops = update_flops / upd_calls
     upd_tflops = upd_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
+    tr = traffic.get("front_update_tc_kernel")
     if wl.precision:
         roofline = {"bound": "tensor",
-                    "kernel": "front_update_tc_kernel (factor trailing updates, tcgen05 kind::tf32, 3xTF32)",
+                    "kernel": "front_update_tc_kernel (factor trailing updates, tcgen05 kind::tf32, "
+                              + ("TF32" if args.factor_tf32 else "3xTF32") + ")",
                     "achieved": upd_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": upd_tflops / tf32_peak,
-                    "traffic": UPDATE_TRAFFIC.get(args.workload), "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
+                    "traffic": tr["bytes_per_launch"] if tr else None,
+                    "traffic_source": f"{tr['profile']} ({tr['date']})" if tr else None,
+                    "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
                     "peak_source": tf32_src,
                     "note": "achieved counts algorithmic flops; 3xTF32 issues 3 TF32 MMAs per product, "
-                            "so frac <= 1/3"}
+                            "so frac <= 1/3; the update launches run on the low-priority factor stream"}
     else:
         roofline = {"bound": "alu", "kernel": "front_update_kernel<double> (factor trailing updates, FP64)",
                     "achieved": upd_tflops, "peak": 1.25, "unit": "TFLOP/s", "frac": upd_tflops / 1.25,
                     "traffic": None, "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on this pool)"}
-    # (inside replayed PCG graphs the iterations are timed as one stage, so
-    # the apply and SpMV figures cover the graph-free first application only)
-    vb = 4 if wl.precision else 8
-    apply_calls = max(1, stage_calls["apply"])
-    apply_ms = stage_ms["apply"] / apply_calls
-    yb = 2 if (wl.precision and args.precond_fp16) else vb
-    bytes_apply = 2 * info["y_nnz"] * yb + 6 * info["n_free"] * vb + 2 * info["n"] * vb
-    achieved = bytes_apply / (apply_ms / 1e3) / 1e9 if apply_ms > 0 else None
-    roofline_apply = {"bound": "hbm", "kernel": "precond apply (fwd_kernel + bwd_kernel per level)",
-                      "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                      "frac": achieved / hbm if achieved else None,
-                      "traffic": APPLY_TRAFFIC.get(args.workload) if (wl.precision and args.precond_fp16) else None,
-                      "bytes_per_launch": bytes_apply, "avg_ms": apply_ms}
-    spmv_calls = max(1, stage_calls["spmv"])
-    spmv_ms = stage_ms["spmv"] / spmv_calls
-    bytes_spmv = info["nnz"] * (vb + 4) + (n + 1) * 4 + 2 * n * vb
-    asm_ms = stage_ms["assembly"] / max(1, stage_calls["assembly"])
-    bytes_asm = info["ntrip"] * 0.0  # filled below from the kept triplets
+    streaming = _streaming_rooflines(wl, info, stage_ms, stage_calls, hbm, peak_kind, args, traffic)
+    main_stages = ("element", "assembly", "apply", "spmv", "vector", "residual", "integrate")
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -507,30 +584,27 @@ def main():
         "config": {"workload": args.workload, "n_dof": n, "elements": wl.mesh.n_elems,
                    "nnz": info["nnz"], "material": MATERIAL_NAMES[wl.model],
                    "precision": "mixed" if wl.precision else "fp64",
-                   "refactor_every": wl.refactor_every, "tol": wl.tol,
+                   "element_fp64": bool(args.element_fp64),
+                   "refactor_every": wl.refactor_every, "factor_lag": args.lag, "tol": wl.tol,
                    "l2": "inputs larger than L2 (apply operators %.2f GB)" % (info["y_nnz"] * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single", "nd_leaf_nodes": args.nd_leaf or 64,
                    "pcg_graph": bool(args.graph), "factor_tf32": bool(args.factor_tf32),
                    "precond_fp16": bool(wl.precision and args.precond_fp16),
-                   "mean_pcg_iters": float(np.mean(iters)), "max_displacement_m": disp},
+                   "mean_pcg_iters": float(np.mean(iters)), "pcg_iters": iters, "factor_ages": ages,
+                   "refinements": refs, "max_displacement_m": disp},
         "roofline": roofline,
-        "roofline_apply": roofline_apply,
+        "roofline_streaming": streaming,
         "stages_ms_per_step": {k: v / K for k, v in stage_ms.items()},
+        "main_stream_stage_sum_ms": sum(stage_ms[k] for k in main_stages) / K,
         "stage_calls": stage_calls,
-        "spmv": {"avg_ms": spmv_ms, "bytes": bytes_spmv,
-                 "achieved_gbs": bytes_spmv / (spmv_ms / 1e3) / 1e9 if spmv_ms > 0 else None},
-        "assembly": {"avg_ms": asm_ms},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": e2e,
     }
-    del bytes_asm
     if rank == 0 and not args.no_adjoint and args.workload == WORKLOAD:
         out["adjoint"] = measure_adjoint(fe, torch)
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, desc, _ = oracle_step_sample(wl)
-        out["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                               "sample": desc}
+        out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

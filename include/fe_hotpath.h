@@ -86,13 +86,21 @@ typedef struct {
 } fe_material;
 
 typedef struct {
-  int32_t precision;      /* FE_FP64: all FP64.  FE_MIXED: FP32 tangent,
-                             SpMV and triangular solves, FP64 force, residual,
-                             dot products and pivots, iterative refinement. */
+  int32_t precision;      /* FE_FP64: all FP64.  FE_MIXED: FP32 element
+                             tangents K_e, inner PCG (SpMV, vectors), factor
+                             and triangular solves; FP64 element forces f_e,
+                             FP64 sums in the assembly (A is kept in FP64 for
+                             the residual and in FP32 for the inner solves),
+                             FP64 right-hand side b, residual, dot products
+                             and pivots; iterative refinement to tol.       */
   double tol;             /* stop when ||b - A a||_2 <= tol ||b||_2           */
   int32_t max_iters;      /* PCG iterations per step (all refinement sweeps)  */
-  int32_t refactor_every; /* R: factor A_s at steps s = 0 mod R; that factor
-                             preconditions steps s+1 .. s+R (step 0 uses A_0)  */
+  int32_t refactor_every; /* R: factor A_s at steps s = 0 mod R on the side
+                             stream; that factor preconditions steps
+                             s+k .. s+k+R-1 (k = factor_lag); steps 0 .. k+R-1
+                             use the factor of A_0, made synchronously at
+                             step 0.  R = 1: the exact factor of the step's
+                             own A every step (synchronous).                 */
   int32_t device_ptrs;    /* 1: state/force buffers are device pointers       */
   void *stream;           /* cudaStream_t for device_ptrs = 1 (NULL: the
                              library's own stream, created at the highest
@@ -102,7 +110,11 @@ typedef struct {
   int32_t keep_checkpoints; /* store (q_t, v_t) of every step for fe_adjoint  */
   int32_t nd_leaf_nodes;  /* nested-dissection leaf size in nodes (0: 64)     */
   double inner_tol;       /* FE_MIXED inner PCG tolerance per sweep (0: 1e-4) */
-  double factor_timeout_s;/* host deadline for a lagged factor (0: 30 s)      */
+  double factor_timeout_s;/* how long the step that first uses a lagged
+                             factor waits for it on the host before
+                             returning FE_ERR_TIMEOUT (0: 30 s); a
+                             synchronous factorisation (step 0, R = 1,
+                             fe_factor_now) waits up to max(this, 300 s)     */
   int32_t use_graph;      /* 1: the PCG iterations run as a CUDA graph of
                              kGraphIters iterations, replayed until the
                              device-side convergence flag is set (one host
@@ -134,6 +146,26 @@ typedef struct {
                              contacts (fe_set_contacts); default 200         */
   double contact_tol;     /* stop when a sweep changes no multiplier by more
                              than contact_tol * max |lambda|; default 1e-12  */
+  int32_t factor_lag;     /* k, 1 <= k <= R (0: 1): steps between the
+                             snapshot of A_s and the first step its factor
+                             preconditions (Eq. "asynchronous
+                             preconditioner": the factor becomes available
+                             several steps after the matrix it inverts).  A
+                             larger k gives the side stream k steps of the
+                             main stream's time to finish the factorisation,
+                             at the price of an older preconditioner.  The
+                             schedule is fixed, so iteration counts do not
+                             depend on timing.  Ignored when R = 1.          */
+  double dep_wait_s;      /* limit of every bounded dependency wait inside
+                             the preconditioner application's kernels
+                             (0: 1 s); a wait that runs out stops the
+                             application and the call reports FE_ERR_TIMEOUT */
+  int32_t element_fp64;   /* FE_MIXED only: 1 = the element kernel computes
+                             and stores the tangents K_e in FP64 too, so the
+                             FP64 copy of A equals the FP64 path's A and the
+                             refined solution reaches tol against the FP64
+                             system; the inner PCG, factor and solves stay
+                             FP32 (0: FP32 tangents, see precision)          */
 } fe_options;
 
 typedef struct {
@@ -229,7 +261,8 @@ int fe_get_state(fe_ctx *ctx, double *q, double *v);
 int fe_element_eval(fe_ctx *ctx, const double *q, double *f_e, double *K_e);
 
 /* Element kernel + fast assembly at the current state with external force
- * p_ext [n] (NULL = 0): A_vals [nnz] on the CSR pattern and b [n]
+ * p_ext [n] (NULL = 0): A_vals [nnz] on the CSR pattern (the FP64 matrix the
+ * residual uses: FP64 sums of the element tangents) and b [n]
  * (Eq. "dynamic equation2"; fixed rows: A_ii = 1, b_i = 0).  Either output
  * may be NULL. */
 int fe_assemble(fe_ctx *ctx, const double *p_ext, double *A_vals, double *b);
@@ -250,14 +283,23 @@ int fe_apply_preconditioner(fe_ctx *ctx, const double *r, double *z);
  *         fe_options.device_ptrs says; stream: cudaStream_t (NULL: legacy).
  * The call is asynchronous on `stream` and allocates nothing: its work
  * vectors live in one file-scope device array of 64 MiB that every GPU
- * loading the library holds until exit.  A mesh needing more (about
- * (2 n + update rows + free DOFs) x 4 or 8 bytes) is rejected with
- * FE_ERR_ARG.  The context must already hold a factor (fe_factor_now or
- * fe_step) and its device must be current.  The first call on a device looks
- * the array's address up (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the array and it keeps the last
- * call's contents (the call clears what must start at zero): calls that
- * overlap on the GPU, on any stream or context, race. */
+ * loading the library holds until exit.  A mesh needing more
+ * (fe_info.noalloc_bytes: about (2 n + update rows + free DOFs) x 4 or 8
+ * bytes) is rejected with FE_ERR_ARG before any GPU work.  The context must
+ * already hold a factor (fe_factor_now or fe_step) and its device must be
+ * current.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (the call
+ * clears what must start at zero): calls that overlap on the GPU, on any
+ * stream or context, race.
+ * Ordering with the context's own work: the call also uses the context's
+ * per-front counters and reads its current factor, so it starts on `stream`
+ * only after the work already queued on the context's stream (events, no
+ * allocation), and the context's later calls (steps, refactorisations,
+ * applications) wait for it.  If one of its bounded dependency waits runs
+ * out (fe_options.dep_wait_s), z is incomplete; the context's next fe_step
+ * or fe_apply_preconditioner then returns FE_ERR_TIMEOUT naming this call
+ * (once; the state is unchanged and the call can be repeated). */
 int fe_apply_preconditioner_noalloc(fe_ctx *ctx, const double *r, double *z, void *stream);
 
 /* Frictionless contacts against rigid planes, by Lagrange multipliers
@@ -300,6 +342,11 @@ typedef struct {
                              nnz(L) read twice per preconditioner application) */
   double factor_flops;    /* flops of one numeric factorisation              */
   int64_t device_bytes;   /* device memory held by the context (0 before use) */
+  int64_t noalloc_bytes;  /* scratch bytes fe_apply_preconditioner_noalloc
+                             needs for this mesh (its limit is 64 MiB)       */
+  int64_t ntrip_kept;     /* triplets the assembly gathers (C[t] >= 0)       */
+  int64_t n_blocks;       /* 3x3 node blocks of the free rows (nnz of the
+                             free rows / 9): the assembly's gather units     */
 } fe_info;
 int fe_get_info(fe_ctx *ctx, fe_info *info);
 
@@ -343,6 +390,17 @@ int fe_set_params(fe_ctx *ctx, const double *params);
 int fe_adjoint(fe_ctx *ctx, const double *dL_dqT, const double *dL_dvT, double *dL_ds, double *dL_dp);
 int fe_clear_checkpoints(fe_ctx *ctx);
 int fe_num_checkpoints(fe_ctx *ctx, int64_t *count);
+
+/* Test hook for failure detection without a GPU fault (not part of the
+ * paper's method): before the context's next preconditioner application,
+ * front `front` (0 <= front < n_fronts of fe_get_ordering) gets `extra` > 0
+ * more pending children than it has, so its forward tasks wait on a count
+ * that nothing reaches.  That wait runs out after fe_options.dep_wait_s; the
+ * application's kernels then stop taking tasks and the call that ran the
+ * application (fe_step, fe_apply_preconditioner) returns FE_ERR_TIMEOUT with
+ * the state unchanged.  The hold lasts one application: the backward launch
+ * resets every counter, so the next call runs normally. */
+int fe_debug_hold_front(fe_ctx *ctx, int64_t front, int32_t extra);
 
 /* Message of the last failure on ctx ("" if none). */
 const char *fe_last_error(const fe_ctx *ctx);

@@ -285,6 +285,10 @@ def fe_num_checkpoints(ctx):
     return k.value
 
 
+def fe_debug_hold_front(ctx, front, extra=1):
+    _check(ctx, load().fe_debug_hold_front(ctx, int(front), int(extra)))
+
+
 def fe_destroy(ctx):
     if ctx:
         load().fe_destroy(ctx)
@@ -469,6 +473,11 @@ class FEContext:
 
     def factor_now(self):
         fe_factor_now(self.ctx)
+
+    def hold_front(self, front, extra=1):
+        """Test hook (fe_debug_hold_front): the next application waits on
+        front `front` until fe_options.dep_wait_s runs out."""
+        fe_debug_hold_front(self.ctx, front, extra)
 
     def apply_preconditioner(self, r):
         z = np.empty(self.n)

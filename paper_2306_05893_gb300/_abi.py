@@ -29,7 +29,8 @@ class FeOptions(ct.Structure):
                 ("factor_timeout_s", ct.c_double), ("use_graph", ct.c_int32),
                 ("profile_stages", ct.c_int32), ("newton_iters", ct.c_int32),
                 ("newton_tol", ct.c_double), ("factor_tf32", ct.c_int32),
-                ("precond_fp16", ct.c_int32), ("contact_sweeps", ct.c_int32), ("contact_tol", ct.c_double)]
+                ("precond_fp16", ct.c_int32), ("contact_sweeps", ct.c_int32), ("contact_tol", ct.c_double),
+                ("factor_lag", ct.c_int32), ("dep_wait_s", ct.c_double), ("element_fp64", ct.c_int32)]
 
 
 class FeStepInfo(ct.Structure):
@@ -40,7 +41,8 @@ class FeStepInfo(ct.Structure):
 class FeInfo(ct.Structure):
     _fields_ = [("n", ct.c_int64), ("nnz", ct.c_int64), ("ntrip", ct.c_int64), ("n_free", ct.c_int64),
                 ("n_fronts", ct.c_int64), ("n_levels", ct.c_int64), ("y_nnz", ct.c_int64),
-                ("factor_flops", ct.c_double), ("device_bytes", ct.c_int64)]
+                ("factor_flops", ct.c_double), ("device_bytes", ct.c_int64), ("noalloc_bytes", ct.c_int64),
+                ("ntrip_kept", ct.c_int64), ("n_blocks", ct.c_int64)]
 
 
 STAGES = ["element", "assembly", "factor", "apply", "spmv", "vector", "residual", "integrate",
@@ -86,6 +88,7 @@ SIGNATURES = {
     "fe_adjoint": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "fe_clear_checkpoints": (ct.c_int, [CTX]),
     "fe_num_checkpoints": (ct.c_int, [CTX, P(ct.c_int64)]),
+    "fe_debug_hold_front": (ct.c_int, [CTX, ct.c_int64, ct.c_int32]),
     "fe_last_error": (ct.c_char_p, [CTX]),
     "fe_destroy": (None, [CTX]),
     "fe_trip_create": (ct.c_int, [ct.c_int64, P(ct.c_void_p)]),

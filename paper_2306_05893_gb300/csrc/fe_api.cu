@@ -193,6 +193,8 @@ int ensure_device(fe_ctx *c) {
   FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_assembled, cudaEventDisableTiming));
   FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_factored, cudaEventDisableTiming));
   FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_apply_done, cudaEventDisableTiming));
+  FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_main_tail, cudaEventDisableTiming));
+  FE_CUDA_TRY(cudaEventCreateWithFlags(&d->ev_noalloc_done, cudaEventDisableTiming));
 
   const int64_t n = c->n, E = c->n_elems, nf = int64_t(c->fronts.size());
   const int npe = c->npe, ke = 9 * npe * npe;
@@ -246,9 +248,11 @@ int ensure_device(fe_ctx *c) {
   FE_TRY(dalloc(c, d, &d->x, n));
   FE_TRY(dalloc(c, d, &d->r, n));
   FE_TRY(dalloc(c, d, &d->b, n));
-  FE_TRY(dallocv(c, d, &d->fe, size_t(E) * 3 * npe * ts));
-  FE_TRY(dallocv(c, d, &d->Ke, size_t(E) * ke * ts));
+  FE_TRY(dalloc(c, d, &d->fe, size_t(E) * 3 * npe));
+  FE_TRY(dallocv(c, d, &d->Ke, size_t(E) * ke * (c->opt.element_fp64 ? sizeof(double) : ts)));
   FE_TRY(dallocv(c, d, &d->A, size_t(c->nnz) * ts));
+  if (fp32) FE_TRY(dalloc(c, d, &d->A64, size_t(c->nnz)));
+  else d->A64 = static_cast<double *>(d->A);
   FE_TRY(dallocv(c, d, &d->Afac, size_t(c->nnz) * ts));
   FE_TRY(dallocv(c, d, &d->vz, n * ts));
   FE_TRY(dallocv(c, d, &d->vp, n * ts));
@@ -260,6 +264,7 @@ int ensure_device(fe_ctx *c) {
   d->flags = reinterpret_cast<int *>(d->scal + S_COUNT);
   FE_CUDA_TRY(cudaMemset(d->scal, 0, S_COUNT * sizeof(double) + 4 * sizeof(int)));
   FE_TRY(dalloc(c, d, &d->partials, kMaxBlocks));
+  FE_TRY(dallocv(c, d, reinterpret_cast<void **>(&d->tune_scal), S_COUNT * sizeof(double) + 4 * sizeof(int)));
   FE_TRY(dalloc(c, d, &d->ticket, 4));
   FE_CUDA_TRY(cudaMemset(d->ticket, 0, 4 * sizeof(unsigned int)));
   FE_CUDA_TRY(cudaMallocHost(&d->h_scal, S_COUNT * sizeof(double) + 4 * sizeof(int)));
@@ -400,30 +405,46 @@ int read_scalars(fe_ctx *c) {
 
 int flag_status(fe_ctx *c) {
   const int f = c->dev->h_flags[0];
+  // a wait that gave up leaves its outputs incomplete, so whatever the later
+  // kernels flagged follows from it: timeouts are reported first
+  if (f & FLAG_WAIT_TIMEOUT)
+    return set_error(c, FE_ERR_TIMEOUT, "a completion wait in the factorisation gave up");
+  if (f & FLAG_APPLY_TIMEOUT)
+    return set_error(c, FE_ERR_TIMEOUT, "a dependency wait in the preconditioner application gave up");
   if (f & FLAG_INVERTED) return set_error(c, FE_ERR_INVERTED, "an element has det F <= 0");
   if (f & FLAG_PIVOT) return set_error(c, FE_ERR_BREAKDOWN, "LDL^T pivot <= 0");
   if (f & FLAG_BREAKDOWN) return set_error(c, FE_ERR_BREAKDOWN, "CG breakdown (p^T A p <= 0 or r^T z <= 0)");
-  if (f & FLAG_WAIT_TIMEOUT)
-    return set_error(c, FE_ERR_TIMEOUT, "a tensor-core completion wait in the factor update gave up");
+  if (c->dev->h_flags[1] & FLAG_APPLY_TIMEOUT) {
+    // raised by an earlier allocation-free application: reported once
+    c->dev->h_flags[1] = 0;
+    FE_CUDA_TRY(cudaMemsetAsync(c->dev->flags + 1, 0, sizeof(int), c->dev->stream));
+    return set_error(c, FE_ERR_TIMEOUT,
+                     "an earlier fe_apply_preconditioner_noalloc gave up on a dependency wait (its z was incomplete)");
+  }
   return FE_OK;
 }
 
+// Clears the step's own error flags (word 0); word 1, raised by an
+// allocation-free application, stays until a flag check reports it.
 int clear_flags(fe_ctx *c) {
-  FE_CUDA_TRY(cudaMemsetAsync(c->dev->flags, 0, 4 * sizeof(int), c->dev->stream));
+  FE_CUDA_TRY(cudaMemsetAsync(c->dev->flags, 0, sizeof(int), c->dev->stream));
   return FE_OK;
 }
 
-// Wait (host deadline) until the factor launched on the side stream is done.
-int wait_factor(fe_ctx *c) {
+// Wait until the factor launched on the side stream is done: a lagged factor
+// with the host deadline factor_timeout_s, a synchronous one (the step's own
+// work) with at least 300 s.
+int wait_factor(fe_ctx *c, bool lagged) {
   DeviceState *d = c->dev;
   if (d->factor_pending < 0) return FE_OK;
+  const double limit = lagged ? c->opt.factor_timeout_s : std::max(c->opt.factor_timeout_s, 300.0);
   auto t0 = std::chrono::steady_clock::now();
   for (;;) {
     cudaError_t e = cudaEventQuery(d->ev_factored);
     if (e == cudaSuccess) break;
     if (e != cudaErrorNotReady) return set_error(c, FE_ERR_CUDA, std::string("factor: ") + cudaGetErrorString(e));
     double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (el > c->opt.factor_timeout_s) return set_error(c, FE_ERR_TIMEOUT, "lagged factor not ready before the deadline");
+    if (el > limit) return set_error(c, FE_ERR_TIMEOUT, "factor not ready before the deadline");
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
   FE_CUDA_TRY(cudaStreamWaitEvent(d->stream, d->ev_factored, 0));
@@ -453,55 +474,286 @@ int launch_factor(fe_ctx *c, int64_t step_tag) {
   return FE_OK;
 }
 
-// One PCG iteration after the prologue: q = A p, alpha, x += alpha p,
-// r -= alpha q, then z = P^{-1} r, beta, p = z + beta p.  Every kernel
-// returns at once once the device flag S_DONE is set (converged, or the
-// iteration cap), so iterations enqueued past that point change nothing.
-static void pcg_iteration(fe_ctx *c, bool fp32, void *X, void *R, cudaStream_t s, bool timed) {
-  DeviceState *d = c->dev;
-  const double *done = d->scal + S_DONE;
-  {
-    Stage st(c, timed ? FE_STAGE_SPMV : -1, s);
-    launch_spmv_dot(c, d, fp32, d->vp, d->vq, s);
-  }
-  {
-    Stage st(c, timed ? FE_STAGE_VECTOR : -1, s);
-    launch_axpy_norm(c, d, fp32, X, R, d->vp, d->vq, s);
-  }
-  {
-    Stage st(c, timed ? FE_STAGE_APPLY : -1, s);
-    apply_enqueue(c, d, d->cur, fp32, R, d->vz, s, done);
-  }
-  Stage st(c, timed ? FE_STAGE_VECTOR : -1, s);
-  launch_dot_rz(c, d, fp32, R, d->vz, false, s);
-  launch_update_p(c, d, fp32, d->vz, d->vp, false, s);
+// ------------------------------------------------------- whole-step graph
+// use_graph: the solve of a step (the PCG, and in the mixed path the FP64
+// refinement around it) and the integration run as one CUDA graph whose
+// loops are WHILE conditional nodes; a one-thread kernel at the end of each
+// loop body (and one before the loop) sets the loop's condition from the
+// device scalars, so the step makes no host read until it is done.
+
+// The graph being captured on s.
+static cudaGraph_t capturing_graph(cudaStream_t s) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess) return nullptr;
+  return g;
 }
 
-// The graph of kGraphIters iterations for (precision, X, R, factor buffer),
-// captured once and cached.
-constexpr int kGraphIters = 4;
+// Appends a WHILE node on handle h after everything captured so far on s;
+// returns its body graph, and the capture on s goes on after the node.
+static cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t *body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *edges = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &edges, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, edges, nd, &p);
+  if (e != cudaSuccess) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
 
-static int pcg_graph(fe_ctx *c, bool fp32, void *X, void *R, DeviceState::PcgGraph **out) {
+// PCG on (X, R) after init_solve: the prologue (z = P^{-1} r, rz, p = z),
+// then WHILE (S_DONE == 0) { q = A p, alpha; x += alpha p, r -= alpha q;
+// z = P^{-1} r; beta; p = z + beta p }.  Captured on s; the loop body on s2.
+static cudaError_t capture_pcg(fe_ctx *c, bool fp32, void *X, void *R, cudaStream_t s, cudaStream_t s2,
+                               DeviceState::StepGraph *sg) {
   DeviceState *d = c->dev;
-  for (auto &g : d->graphs)
-    if (g.fp32 == fp32 && g.X == X && g.R == R && g.cur == d->cur) {
-      *out = &g;
-      return FE_OK;
+  const double *done = d->scal + S_DONE;
+  int64_t l0 = d->launches;
+  apply_enqueue(c, d, d->cur, fp32, R, d->vz, s, done);
+  launch_dot_rz(c, d, fp32, R, d->vz, true, s);
+  launch_update_p(c, d, fp32, d->vz, d->vp, true, s);
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, capturing_graph(s), 0, 0);
+  if (e != cudaSuccess) return e;
+  launch_graph_cond(c, d, h, 0, s);
+  sg->k_pro += d->launches - l0;
+  cudaGraph_t body;
+  e = add_while(s, h, &body);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  l0 = d->launches;
+  launch_spmv_dot(c, d, fp32, d->vp, d->vq, s2);
+  launch_axpy_norm(c, d, fp32, X, R, d->vp, d->vq, s2);
+  apply_enqueue(c, d, d->cur, fp32, R, d->vz, s2, done);
+  launch_dot_rz(c, d, fp32, R, d->vz, false, s2);
+  launch_update_p(c, d, fp32, d->vz, d->vp, false, s2);
+  launch_graph_cond(c, d, h, 0, s2);
+  sg->k_inner = d->launches - l0;
+  return cudaStreamEndCapture(s2, &body);
+}
+
+// Captures the solve and the guarded integration of a step for the current
+// factor buffer.  FP64: init (x = 0, r = b), PCG.  Mixed: init; WHILE
+// (S_ODONE == 0, S_ITERS < max_iters) { inner init (d = 0, r32 = r); inner
+// PCG to inner_tol; x += d; r = b - A64 x }.
+static int build_step_graph(fe_ctx *c, DeviceState::StepGraph *sg) {
+  DeviceState *d = c->dev;
+  const bool fp32 = mixed(c);
+  cudaStream_t s = d->stream, s2 = nullptr, s3 = nullptr;
+  const int64_t l_save = d->launches;
+  *sg = DeviceState::StepGraph{};
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    if (!fp32) {
+      launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s);
+      sg->k_pro = 1;
+      e = capture_pcg(c, false, d->x, d->r, s, s2, sg);
+    } else {
+      launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s);  // x = 0, r = b (FP64)
+      cudaGraphConditionalHandle ho;
+      e = cudaGraphConditionalHandleCreate(&ho, capturing_graph(s), 0, 0);
+      if (e == cudaSuccess) {
+        launch_graph_cond(c, d, ho, 2, s);
+        sg->k_pro = 2;
+        cudaGraph_t body;
+        e = add_while(s, ho, &body);
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0,
+                                                                cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          const int64_t l0 = d->launches;
+          launch_init_solve(c, d, true, d->vd, d->vr, d->r, c->opt.inner_tol, false, s2);
+          DeviceState::StepGraph inner{};
+          e = capture_pcg(c, true, d->vd, d->vr, s2, s3, &inner);
+          launch_refine_update(c, d, s2);
+          launch_residual(c, d, true, s2);
+          launch_graph_cond(c, d, ho, 1, s2);
+          sg->k_outer = d->launches - l0 - inner.k_inner;
+          sg->k_inner = inner.k_inner;
+          cudaError_t e2 = cudaStreamEndCapture(s2, &body);
+          if (e == cudaSuccess) e = e2;
+        }
+      }
     }
-  cudaStream_t s = d->stream;
-  const int64_t l0 = d->launches;
-  FE_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < kGraphIters; ++k) pcg_iteration(c, fp32, X, R, s, false);
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamEndCapture(s, &graph);
-  if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-  d->graphs.push_back({fp32, X, R, d->cur, exec, d->launches - l0});
-  d->launches = l0;
-  *out = &d->graphs.back();
+    launch_integrate_guarded(c, d, fp32, s);
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&sg->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (s2) cudaStreamDestroy(s2);
+  if (s3) cudaStreamDestroy(s3);
+  d->launches = l_save;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    sg->exec = nullptr;
+    return set_error(c, FE_ERR_CUDA, std::string("whole-step graph: ") + cudaGetErrorString(e));
+  }
+  sg->cur = d->cur;
+  return FE_OK;
+}
+
+// The batched solve as one graph: the same kernels as pcg_batch and
+// solve_batch, with WHILE loops that go on while some member's PCG (or
+// refinement) has not converged, none has reached max_iters and no error
+// flag is set; a member that converged stops changing (its alpha is 0 and
+// its direction frozen).  The integration is guarded by every member
+// having converged.
+static cudaError_t capture_pcg_batch(fe_ctx *c, bool fp32, void *X, void *R, cudaStream_t s, cudaStream_t s2,
+                                     DeviceState::StepGraph *sg) {
+  DeviceState *d = c->dev;
+  int64_t l0 = d->launches;
+  apply_enqueue(c, d, d->cur, fp32, R, d->vz, s);
+  launch_seg_dot(c, d, fp32, R, d->vz, SEG_RZ_FIRST, 0.0, s);
+  launch_seg_update_p(c, d, fp32, d->vz, d->vp, true, s);
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, capturing_graph(s), 0, 0);
+  if (e != cudaSuccess) return e;
+  launch_seg_cond(c, d, h, 0, s);
+  sg->k_pro += d->launches - l0;
+  cudaGraph_t body;
+  e = add_while(s, h, &body);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  l0 = d->launches;
+  launch_batch_spmv(c, d, fp32, d->vp, d->vq, nullptr, s2);
+  launch_seg_dot(c, d, fp32, d->vp, d->vq, SEG_PQ, 0.0, s2);
+  launch_seg_axpy(c, d, fp32, X, R, d->vp, d->vq, s2);
+  launch_seg_dot(c, d, fp32, R, R, SEG_RR, 0.0, s2);
+  apply_enqueue(c, d, d->cur, fp32, R, d->vz, s2);
+  launch_seg_dot(c, d, fp32, R, d->vz, SEG_RZ, 0.0, s2);
+  launch_seg_update_p(c, d, fp32, d->vz, d->vp, false, s2);
+  launch_seg_cond(c, d, h, 0, s2);
+  sg->k_inner = d->launches - l0;
+  return cudaStreamEndCapture(s2, &body);
+}
+
+static int build_batch_graph(fe_ctx *c, DeviceState::StepGraph *sg) {
+  DeviceState *d = c->dev;
+  const bool fp32 = mixed(c);
+  cudaStream_t s = d->stream, s2 = nullptr, s3 = nullptr;
+  const int64_t l_save = d->launches;
+  *sg = DeviceState::StepGraph{};
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    launch_seg_init(c, d, false, d->x, d->r, d->b, false, s);
+    launch_seg_dot64(c, d, d->b, d->b, SEG_INIT_OUTER, c->opt.tol, s);
+    sg->k_pro = 2;
+    if (!fp32) {
+      e = capture_pcg_batch(c, false, d->x, d->r, s, s2, sg);
+    } else {
+      cudaGraphConditionalHandle ho;
+      e = cudaGraphConditionalHandleCreate(&ho, capturing_graph(s), 0, 0);
+      if (e == cudaSuccess) {
+        launch_seg_cond(c, d, ho, 2, s);
+        sg->k_pro += 1;
+        cudaGraph_t body;
+        e = add_while(s, ho, &body);
+        if (e == cudaSuccess)
+          e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          const int64_t l0 = d->launches;
+          launch_seg_init(c, d, true, d->vd, d->vr, d->r, true, s2);
+          launch_seg_dot(c, d, true, d->vr, d->vr, SEG_INIT_INNER, c->opt.inner_tol, s2);
+          DeviceState::StepGraph inner{};
+          e = capture_pcg_batch(c, true, d->vd, d->vr, s2, s3, &inner);
+          launch_refine_update(c, d, s2);
+          launch_batch_spmv(c, d, true, d->x, d->r, d->b, s2);  // r = b - A64 x (FP64)
+          launch_seg_dot64(c, d, d->r, d->r, SEG_ORR, 0.0, s2);
+          launch_seg_cond(c, d, ho, 1, s2);
+          sg->k_outer = d->launches - l0 - inner.k_inner;
+          sg->k_inner = inner.k_inner;
+          cudaError_t e2 = cudaStreamEndCapture(s2, &body);
+          if (e == cudaSuccess) e = e2;
+        }
+      }
+    }
+    launch_seg_cond(c, d, cudaGraphConditionalHandle{}, fp32 ? 4 : 3, s);
+    launch_integrate_guarded(c, d, fp32, s);
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&sg->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (s2) cudaStreamDestroy(s2);
+  if (s3) cudaStreamDestroy(s3);
+  d->launches = l_save;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    sg->exec = nullptr;
+    return set_error(c, FE_ERR_CUDA, std::string("batched whole-step graph: ") + cudaGetErrorString(e));
+  }
+  sg->cur = d->cur;
+  return FE_OK;
+}
+
+int read_batch_scalars(fe_ctx *c);
+bool all_members(const fe_ctx *c, int slot);
+double max_member(const fe_ctx *c, int slot);
+
+// The solve and integration of one step through the cached graph of the
+// current factor buffer; one host read at the end.
+static int solve_integrate_graph(fe_ctx *c, fe_step_info *info) {
+  DeviceState *d = c->dev;
+  const bool batch = c->nseg > 1;
+  if (batch) FE_TRY(tune_batch_spmv(c, d));
+  else FE_TRY(tune_spmv(c, d));
+  DeviceState::StepGraph &sg = d->step_graph[d->cur];
+  if (!sg.exec || sg.cur != d->cur) FE_TRY(batch ? build_batch_graph(c, &sg) : build_step_graph(c, &sg));
+  launch_pending_hold(d, d->stream);
+  {
+    Stage st(c, FE_STAGE_PCG_GRAPH, d->stream);
+    FE_CUDA_TRY(cudaGraphLaunch(sg.exec, d->stream));
+  }
+  if (batch) {
+    FE_TRY(read_batch_scalars(c));
+    const double iters = max_member(c, B_ITERS), sweeps = mixed(c) ? d->h_scal[S_SWEEPS] : 1.0;
+    d->launches += sg.k_pro + int64_t(iters) * sg.k_inner + int64_t(sweeps) * sg.k_outer + 2;
+    FE_TRY(flag_status(c));
+    if (!all_members(c, mixed(c) ? B_ODONE : B_DONE))
+      return set_error(c, FE_ERR_NOT_CONVERGED, "batched PCG reached max_iters");
+    if (info) {
+      double worst = 0.0;
+      for (int32_t k = 0; k < c->nseg; ++k) {
+        const double *b = d->h_bscal + k * B_COUNT;
+        const double rr = mixed(c) ? b[B_ORR] : b[B_RR];
+        if (b[B_BB] > 0) worst = std::max(worst, std::sqrt(rr / b[B_BB]));
+      }
+      info->rel_residual = worst;
+      info->iters = int32_t(iters);
+      info->refinements = int32_t(sweeps);
+    }
+    return FE_OK;
+  }
+  FE_TRY(read_scalars(c));
+  const double iters = d->h_scal[S_ITERS], sweeps = mixed(c) ? d->h_scal[S_SWEEPS] : 1.0;
+  d->launches += sg.k_pro + int64_t(iters) * sg.k_inner + int64_t(sweeps) * sg.k_outer + 1;
+  FE_TRY(flag_status(c));
+  const bool ok = mixed(c) ? d->h_scal[S_ODONE] == 1.0 : d->h_scal[S_DONE] == 1.0;
+  if (!ok) return set_error(c, FE_ERR_NOT_CONVERGED, "PCG reached max_iters");
+  if (info) {
+    info->iters = int32_t(iters);
+    info->refinements = int32_t(sweeps);
+    const double rr = mixed(c) ? d->h_scal[S_ORR] : d->h_scal[S_RR];
+    info->rel_residual = d->h_scal[S_BB] > 0 ? std::sqrt(rr / d->h_scal[S_BB]) : 0.0;
+  }
   return FE_OK;
 }
 
@@ -525,20 +777,6 @@ int pcg(fe_ctx *c, bool fp32, void *X, void *R) {
     launch_dot_rz(c, d, fp32, R, d->vz, true, s);
     launch_update_p(c, d, fp32, d->vz, d->vp, true, s);
   }
-  if (c->opt.use_graph) {
-    DeviceState::PcgGraph *g = nullptr;
-    FE_TRY(pcg_graph(c, fp32, X, R, &g));
-    for (;;) {
-      {
-        Stage st(c, FE_STAGE_PCG_GRAPH, s);
-        FE_CUDA_TRY(cudaGraphLaunch(g->exec, s));
-      }
-      d->launches += g->launches;
-      FE_TRY(read_scalars(c));
-      FE_TRY(flag_status(c));
-      if (d->h_scal[S_DONE] != 0.0) return pcg_status(c);
-    }
-  }
   for (;;) {
     {
       Stage st(c, FE_STAGE_SPMV, s);
@@ -560,39 +798,6 @@ int pcg(fe_ctx *c, bool fp32, void *X, void *R) {
     launch_dot_rz(c, d, fp32, R, d->vz, false, s);
     launch_update_p(c, d, fp32, d->vz, d->vp, false, s);
   }
-}
-
-// SpMV autotuner: threads per CSR row chosen among {4, 8, 16, 32} by timing
-// y = A x on the assembled matrix (CUDA events, 3 runs each, median).
-int autotune_spmv(fe_ctx *c) {
-  DeviceState *d = c->dev;
-  if (d->spmv_tpr) return FE_OK;
-  const bool fp32 = mixed(c);
-  cudaEvent_t e0, e1;
-  FE_CUDA_TRY(cudaEventCreate(&e0));
-  FE_CUDA_TRY(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_tpr = 8;
-  for (int tpr : {4, 8, 16, 32}) {
-    float t[3];
-    for (int rep = 0; rep < 3; ++rep) {
-      cudaEventRecord(e0, d->stream);
-      launch_spmv_plain(c, d, fp32, d->vp, d->vq, nullptr, tpr, d->stream);
-      cudaEventRecord(e1, d->stream);
-      cudaEventSynchronize(e1);
-      cudaEventElapsedTime(&t[rep], e0, e1);
-    }
-    std::sort(t, t + 3);
-    if (t[1] < best) {
-      best = t[1];
-      best_tpr = tpr;
-    }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  FE_CUDA_TRY(cudaGetLastError());
-  d->spmv_tpr = best_tpr;
-  return FE_OK;
 }
 
 int read_batch_scalars(fe_ctx *c) {
@@ -630,7 +835,7 @@ int pcg_batch(fe_ctx *c, bool fp32, void *X, void *R) {
   for (;;) {
     {
       Stage st(c, FE_STAGE_SPMV, s);
-      launch_spmv_plain(c, d, fp32, d->vp, d->vq, nullptr, d->spmv_tpr, s);
+      launch_batch_spmv(c, d, fp32, d->vp, d->vq, nullptr, s);
     }
     {
       Stage st(c, FE_STAGE_VECTOR, s);
@@ -659,7 +864,7 @@ int solve_batch(fe_ctx *c, fe_step_info *info) {
   DeviceState *d = c->dev;
   cudaStream_t s = d->stream;
   const bool fp32 = mixed(c);
-  FE_TRY(autotune_spmv(c));
+  FE_TRY(tune_batch_spmv(c, d));
   int sweeps = 0;
   launch_seg_init(c, d, false, d->x, d->r, d->b, false, s);
   launch_seg_dot64(c, d, d->b, d->b, SEG_INIT_OUTER, c->opt.tol, s);
@@ -671,7 +876,7 @@ int solve_batch(fe_ctx *c, fe_step_info *info) {
     for (;;) {
       if (sweeps > 0) {
         Stage st(c, FE_STAGE_RESIDUAL, s);
-        launch_spmv_plain(c, d, true, d->x, d->r, d->b, d->spmv_tpr, s);  // r = b - A x (FP64)
+        launch_batch_spmv(c, d, true, d->x, d->r, d->b, s);  // r = b - A64 x (FP64)
         launch_seg_dot64(c, d, d->r, d->r, SEG_ORR, 0.0, s);
       }
       FE_TRY(read_batch_scalars(c));
@@ -705,6 +910,7 @@ int solve_batch(fe_ctx *c, fe_step_info *info) {
 int solve(fe_ctx *c, fe_step_info *info) {
   DeviceState *d = c->dev;
   if (c->nseg > 1) return solve_batch(c, info);
+  FE_TRY(tune_spmv(c, d));
   cudaStream_t s = d->stream;
   const bool fp32 = mixed(c);
   int sweeps = 0;
@@ -756,12 +962,15 @@ void destroy_device(fe_ctx *c) {
   if (d->ev_assembled) cudaEventDestroy(d->ev_assembled);
   if (d->ev_factored) cudaEventDestroy(d->ev_factored);
   if (d->ev_apply_done) cudaEventDestroy(d->ev_apply_done);
+  if (d->ev_main_tail) cudaEventDestroy(d->ev_main_tail);
+  if (d->ev_noalloc_done) cudaEventDestroy(d->ev_noalloc_done);
   for (auto &r : d->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : d->pool) cudaEventDestroy(e);
-  for (auto &g : d->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto &g : d->step_graph)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (d->fstream) cudaStreamDestroy(d->fstream);
   if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
   cudaGetLastError();
@@ -819,16 +1028,16 @@ int fe_element_eval(fe_ctx *c, const double *q, double *f_e, double *K_e) {
   const int64_t nf = c->n_elems * 3 * c->npe, nk = c->n_elems * 9 * c->npe * c->npe;
   double *tmp = nullptr;
   FE_CUDA_TRY(cudaMalloc(&tmp, std::max(nf, nk) * sizeof(double)));
-  auto out = [&](double *dst, const void *src, int64_t cnt) -> int {
-    launch_convert(src, mixed(c), tmp, false, cnt, d->stream);
+  auto out = [&](double *dst, const void *src, bool src32, int64_t cnt) -> int {
+    launch_convert(src, src32, tmp, false, cnt, d->stream);
     FE_CUDA_TRY(cudaMemcpyAsync(dst, tmp, cnt * sizeof(double),
                                 c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d->stream));
     FE_CUDA_TRY(cudaStreamSynchronize(d->stream));
     return FE_OK;
   };
   int st = FE_OK;
-  if (f_e) st = out(f_e, d->fe, nf);
-  if (!st && K_e) st = out(K_e, d->Ke, nk);
+  if (f_e) st = out(f_e, d->fe, false, nf);
+  if (!st && K_e) st = out(K_e, d->Ke, mixed(c) && !c->opt.element_fp64, nk);
   cudaFree(tmp);
   if (st) return st;
   FE_TRY(read_scalars(c));
@@ -851,7 +1060,7 @@ int fe_assemble(fe_ctx *c, const double *p_ext, double *A_vals, double *b) {
   if (A_vals) {
     double *tmp = nullptr;
     FE_CUDA_TRY(cudaMalloc(&tmp, c->nnz * sizeof(double)));
-    launch_convert(d->A, mixed(c), tmp, false, c->nnz, d->stream);
+    launch_convert(d->A64, false, tmp, false, c->nnz, d->stream);  // the FP64 copy of A
     cudaError_t e = cudaMemcpyAsync(A_vals, tmp, c->nnz * sizeof(double),
                                     c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                     d->stream);
@@ -870,7 +1079,7 @@ int fe_factor_now(fe_ctx *c) {
   DeviceState *d = c->dev;
   FE_TRY(clear_flags(c));
   FE_TRY(launch_factor(c, d->step_index));
-  FE_TRY(wait_factor(c));
+  FE_TRY(wait_factor(c, false));
   FE_TRY(read_scalars(c));
   return flag_status(c);
 }
@@ -883,11 +1092,13 @@ int fe_apply_preconditioner(fe_ctx *c, const double *r, double *z) {
   FE_TRY(stage_in(c, d->r, r, c->n));
   const bool fp32 = mixed(c);
   launch_convert(d->r, false, d->vr, fp32, c->n, d->stream);
+  FE_TRY(clear_flags(c));
   apply_enqueue(c, d, d->cur, fp32, d->vr, d->vz, d->stream);
   launch_convert(d->vz, fp32, d->x, false, c->n, d->stream);
   FE_CUDA_TRY(cudaGetLastError());
   FE_TRY(stage_out(c, z, d->x, c->n, 0));
-  return FE_OK;
+  FE_TRY(read_scalars(c));
+  return flag_status(c);
 }
 
 int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_step_info *info) {
@@ -914,14 +1125,36 @@ int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_ste
     launch_assemble(c, d, fp32, pd, d->v, nullptr, c->beta + c->h, s);
   }
   FE_CUDA_TRY(cudaGetLastError());
-  // S4 lagged refactorisation: A_s is factored at s = 0 mod R on the side
-  // stream and preconditions steps s+1 .. s+R; step 0 (and R = 1) waits.
-  if (d->factor_pending >= 0) FE_TRY(wait_factor(c));
+  // S4 lagged refactorisation (Eq. "asynchronous preconditioner"): A_s is
+  // snapshot at s = 0 mod R and factored on the side stream; its factor
+  // replaces the current one at step s + k (k = factor_lag <= R), so it
+  // preconditions steps s+k .. s+k+R-1.  Step 0 (and R = 1) factors
+  // synchronously.  The schedule depends only on the step index.
+  const int lag = c->opt.factor_lag;
+  if (d->factor_pending >= 0 && (step >= d->pending_step + lag || step % R == 0))
+    FE_TRY(wait_factor(c, true));
   if (step % R == 0) {
     FE_TRY(launch_factor(c, step));
-    if (step == 0 || R == 1 || !d->have_factor) FE_TRY(wait_factor(c));
+    if (step == 0 || R == 1 || !d->have_factor) FE_TRY(wait_factor(c, false));
   }
   const int age = int(step - d->cur_step);
+  // use_graph: S5-S7 PCG, S9 refinement and S8 integration as one graph
+  // (no host read inside the step); contacts, Newton iterations and
+  // checkpoints take the host-driven path below
+  if (c->opt.use_graph && c->contact_node.empty() && d->c_m == 0 && c->opt.newton_iters <= 1 &&
+      !c->opt.keep_checkpoints) {
+    FE_TRY(solve_integrate_graph(c, info));
+    if (q_out) FE_TRY(stage_out(c, q_out, d->q, c->n, 0));
+    if (v_out) FE_TRY(stage_out(c, v_out, d->v, c->n, 1));
+    if (info) {
+      info->factor_age = age;
+      info->newton = 1;
+      info->newton_correction = 0.0;
+    }
+    d->step_index = step + 1;
+    if (c->opt.profile_stages) stage_collect(c);
+    return FE_OK;
+  }
   // S5-S7 PCG, S9 refinement
   int st = solve(c, info);
   if (!st && c->opt.keep_checkpoints) {
@@ -1053,7 +1286,7 @@ int fe_adjoint(fe_ctx *c, const double *dL_dqT, const double *dL_dvT, double *dL
   }
   FE_CUDA_TRY(cudaMemsetAsync(d->sbar, 0, E * sizeof(double), s));
   FE_TRY(clear_flags(c));
-  if (d->factor_pending >= 0) FE_TRY(wait_factor(c));
+  if (d->factor_pending >= 0) FE_TRY(wait_factor(c, false));
   const int R = c->opt.refactor_every;
   double *qsave = d->q, *vsave = d->v;
   int st = FE_OK;
@@ -1069,7 +1302,7 @@ int fe_adjoint(fe_ctx *c, const double *dL_dqT, const double *dL_dvT, double *dL
     // lagged preconditioner for the reverse sweep: A_{T-1}, then every R steps
     if ((T - 1 - t) % R == 0) {
       st = launch_factor(c, t);
-      if (!st) st = wait_factor(c);
+      if (!st) st = wait_factor(c, false);
       if (st) break;
     }
     launch_adjoint_rhs(c, d, d->qbar, d->vbar, d->b, s);
@@ -1126,6 +1359,20 @@ int fe_get_info(fe_ctx *c, fe_info *info) {
   info->y_nnz = c->y_nnz;
   info->factor_flops = c->factor_flops;
   info->device_bytes = c->dev ? int64_t(c->dev->bytes_total) : 0;
+  info->noalloc_bytes = noalloc_scratch_bytes(c);
+  info->ntrip_kept = c->slot_ptr.empty() ? 0 : c->slot_ptr.back();
+  info->n_blocks = int64_t(c->bcol.size());
+  return FE_OK;
+}
+
+int fe_debug_hold_front(fe_ctx *c, int64_t front, int32_t extra) {
+  if (!c) return FE_ERR_ARG;
+  if (!c->built) return set_error(c, FE_ERR_STATE, "fe_build_pattern has not run");
+  if (front < 0 || front >= int64_t(c->fronts.size()) || extra <= 0)
+    return set_error(c, FE_ERR_ARG, "front out of range or extra <= 0");
+  FE_TRY(ensure_device(c));
+  c->dev->df_hold = int(front);
+  c->dev->df_hold_extra = extra;
   return FE_OK;
 }
 

@@ -29,6 +29,9 @@ int fe_options_default(fe_options *o) {
   o->precond_fp16 = 0;
   o->contact_sweeps = 200;
   o->contact_tol = 1e-12;
+  o->factor_lag = 1;
+  o->dep_wait_s = 1.0;
+  o->element_fp64 = 0;
   return FE_OK;
 }
 
@@ -83,6 +86,14 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
     if (c->opt.contact_sweeps <= 0) c->opt.contact_sweeps = 200;
     if (!(c->opt.contact_tol > 0)) c->opt.contact_tol = 1e-12;
     c->opt.precond_fp16 = c->opt.precond_fp16 ? 1 : 0;
+    if (c->opt.factor_lag <= 0) c->opt.factor_lag = 1;
+    if (c->opt.refactor_every == 1) c->opt.factor_lag = 1;
+    if (c->opt.factor_lag > c->opt.refactor_every) {
+      delete c;
+      return FE_ERR_ARG;  // two factor buffers: the next snapshot must come after the swap
+    }
+    if (!(c->opt.dep_wait_s > 0) || !std::isfinite(c->opt.dep_wait_s)) c->opt.dep_wait_s = 1.0;
+    c->opt.element_fp64 = (c->opt.precision == FE_MIXED && c->opt.element_fp64) ? 1 : 0;
     if (c->opt.newton_iters > 1 && c->opt.keep_checkpoints) {
       delete c;
       return FE_ERR_ARG;  // the adjoint differentiates the single-linearisation step

@@ -6,6 +6,11 @@
 // in a fixed order (deterministic) and updates its scalars.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <string>
+#include <utility>
+#include <vector>
+
 #include "fe_device.cuh"
 
 namespace fe {
@@ -125,29 +130,126 @@ __global__ void seg_update_p_kernel(int64_t n, const TV *__restrict__ z, TV *__r
   }
 }
 
-// y = A x, TPR threads per row (warp-uniform loop bound)
-template <typename TA, typename TV, typename TACC, int TPR>
-__global__ void __launch_bounds__(256) spmv_kernel(int64_t n, const int32_t *__restrict__ rowptr,
-                                                   const int32_t *__restrict__ colind, const TA *__restrict__ A,
-                                                   const TV *__restrict__ x, const double *__restrict__ b,
-                                                   TACC *__restrict__ y) {
-  const int sub = threadIdx.x % TPR;
-  const int64_t groups = int64_t(gridDim.x) * (256 / TPR);
-  const int64_t warp_row0 = int64_t(blockIdx.x) * (256 / TPR) + (threadIdx.x / 32) * (32 / TPR);
-  for (int64_t r0 = warp_row0; r0 < n; r0 += groups) {
-    const int64_t row = r0 + (threadIdx.x % 32) / TPR;
-    TACC acc = TACC(0);
-    if (row < n) {
-      const int32_t k1 = rowptr[row + 1];
-      for (int32_t k = rowptr[row] + sub; k < k1; k += TPR) acc += TACC(A[k]) * TACC(x[colind[k]]);
+unsigned grid_for(int64_t n) { return unsigned(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16))); }
+
+constexpr int kBatchBlockNodes = 64;  // nodes per row block of the batched SpMV
+
+// Node-block SpMV over a table of row blocks (one CTA per block: a node
+// range inside one member).  Every free node's three rows share one column
+// structure of 3x3 blocks, so a block's column index is read once for its 9
+// values; LPN lanes per node, the three row sums reduced across them; fixed
+// nodes keep their lone diagonal.  MODE 0: y = A x in TV; MODE 1: y = b - A x
+// in FP64 (TA = double, the FP64 copy of A).
+template <typename TA, typename TV, int LPN, int MODE>
+__global__ void __launch_bounds__(256) batch_bspmv_kernel(const int2 *__restrict__ blocks,
+                                                          const int32_t *__restrict__ rowptr,
+                                                          const int32_t *__restrict__ bptr,
+                                                          const int32_t *__restrict__ bcol,
+                                                          const int8_t *__restrict__ fixed_row,
+                                                          const TA *__restrict__ A, const TV *__restrict__ x,
+                                                          const double *__restrict__ b, TV *__restrict__ y) {
+  const int2 blk = blocks[blockIdx.x];
+  const int sub = threadIdx.x % LPN;
+  for (int64_t n0 = blk.x + int64_t(threadIdx.x / 32) * (32 / LPN); n0 < blk.y; n0 += 256 / LPN) {
+    const int64_t nd = n0 + (threadIdx.x % 32) / LPN;  // the loop bound is warp-uniform
+    TV a0 = TV(0), a1 = TV(0), a2 = TV(0);
+    bool fixed = true;
+    if (nd < blk.y) {
+      fixed = fixed_row[3 * nd] != 0;
+      if (!fixed) {
+        const int32_t k0 = bptr[nd], k1 = bptr[nd + 1];
+        const int32_t r0 = rowptr[3 * nd], r1 = rowptr[3 * nd + 1], r2 = rowptr[3 * nd + 2];
+        for (int32_t k = k0 + sub; k < k1; k += LPN) {
+          const int64_t cc = 3 * int64_t(bcol[k]);
+          const TV x0 = x[cc], x1 = x[cc + 1], x2 = x[cc + 2];
+          const int32_t o = 3 * (k - k0);
+          a0 += TV(A[r0 + o]) * x0 + TV(A[r0 + o + 1]) * x1 + TV(A[r0 + o + 2]) * x2;
+          a1 += TV(A[r1 + o]) * x0 + TV(A[r1 + o + 1]) * x1 + TV(A[r1 + o + 2]) * x2;
+          a2 += TV(A[r2 + o]) * x0 + TV(A[r2 + o + 1]) * x1 + TV(A[r2 + o + 2]) * x2;
+        }
+      }
     }
 #pragma unroll
-    for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
-    if (sub == 0 && row < n) y[row] = b ? TACC(b[row]) - acc : acc;
+    for (int o = LPN / 2; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o, LPN);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o, LPN);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o, LPN);
+    }
+    if (sub == 0 && nd < blk.y) {
+      const TV acc[3] = {a0, a1, a2};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int64_t r = 3 * nd + i;
+        const TV yi = fixed ? TV(A[rowptr[r]]) * x[r] : acc[i];
+        y[r] = MODE == 0 ? yi : TV(b[r] - double(yi));
+      }
+    }
   }
 }
 
-unsigned grid_for(int64_t n) { return unsigned(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16))); }
+template <typename TA, typename TV, int MODE>
+void launch_class(const DeviceState::SpmvClass &k, const DeviceState *d, const TA *A, const TV *x, const double *b,
+                  TV *y, cudaStream_t s) {
+  if (!k.nblocks) return;
+  const unsigned g = unsigned(k.nblocks);
+  switch (k.lpn) {
+    case 4:
+      batch_bspmv_kernel<TA, TV, 4, MODE><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->bptr, d->bcol, d->fixed_row, A, x, b, y);
+      break;
+    case 8:
+      batch_bspmv_kernel<TA, TV, 8, MODE><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->bptr, d->bcol, d->fixed_row, A, x, b, y);
+      break;
+    case 32:
+      batch_bspmv_kernel<TA, TV, 32, MODE><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->bptr, d->bcol, d->fixed_row, A, x, b, y);
+      break;
+    default:
+      batch_bspmv_kernel<TA, TV, 16, MODE><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->bptr, d->bcol, d->fixed_row, A, x, b, y);
+  }
+}
+
+void run_class(const fe_ctx *c, const DeviceState *d, const DeviceState::SpmvClass &k, bool fp32, const void *x,
+               void *y, const double *b, cudaStream_t s) {
+  if (b)
+    launch_class<double, double, 1>(k, d, d->A64, static_cast<const double *>(x), b, static_cast<double *>(y), s);
+  else if (fp32)
+    launch_class<float, float, 0>(k, d, static_cast<const float *>(d->A), static_cast<const float *>(x), nullptr,
+                                  static_cast<float *>(y), s);
+  else
+    launch_class<double, double, 0>(k, d, static_cast<const double *>(d->A), static_cast<const double *>(x), nullptr,
+                                    static_cast<double *>(y), s);
+}
+
+// graph conditions of the batched solve (one CTA over the members)
+__global__ void __launch_bounds__(256) seg_cond_kernel(cudaGraphConditionalHandle h, double *bs, double *scal,
+                                                       int nseg, int mode, double max_iters, int *flags) {
+  __shared__ int s_open;
+  __shared__ double s_iters;
+  if (threadIdx.x == 0) {
+    s_open = 0;
+    s_iters = 0.0;
+  }
+  __syncthreads();
+  const int slot = (mode == 0 || mode == 3) ? B_DONE : B_ODONE;
+  int open = 0;
+  double it = 0.0;
+  for (int k = threadIdx.x; k < nseg; k += 256) {
+    open |= bs[int64_t(k) * B_COUNT + slot] == 0.0;
+    it = fmax(it, bs[int64_t(k) * B_COUNT + B_ITERS]);
+  }
+  if (open) atomicOr(&s_open, 1);
+  // non-negative doubles order like their bit patterns
+  if (it > 0.0) atomicMax(reinterpret_cast<unsigned long long *>(&s_iters), __double_as_longlong(it));
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (mode >= 3) {
+    flags[2] = (!s_open && flags[0] == 0) ? 1 : 0;
+    return;
+  }
+  if (mode == 2) scal[S_SWEEPS] = 0.0;
+  if (mode == 1) scal[S_SWEEPS] += 1.0;
+  const bool go = s_open && s_iters < max_iters && flags[0] == 0;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
 
 }  // namespace
 
@@ -201,37 +303,104 @@ void launch_seg_update_p(const fe_ctx *c, const DeviceState *d, bool fp32, const
                                                                d->bscal, first);
 }
 
-// y = A x (matrix/vector type), or y = b - A x in FP64 when b is given.
-template <int TPR>
-static void spmv_t(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y, const double *b,
-                   cudaStream_t s) {
-  const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>((c->n * TPR + 255) / 256, 152 * 8)));
-  if (b) {
-    if (fp32)
-      spmv_kernel<float, double, double, TPR><<<g, 256, 0, s>>>(c->n, d->rowptr, d->colind, (const float *)d->A,
-                                                                (const double *)x, b, (double *)y);
-    else
-      spmv_kernel<double, double, double, TPR><<<g, 256, 0, s>>>(c->n, d->rowptr, d->colind, (const double *)d->A,
-                                                                 (const double *)x, b, (double *)y);
-  } else {
-    if (fp32)
-      spmv_kernel<float, float, float, TPR><<<g, 256, 0, s>>>(c->n, d->rowptr, d->colind, (const float *)d->A,
-                                                              (const float *)x, nullptr, (float *)y);
-    else
-      spmv_kernel<double, double, double, TPR><<<g, 256, 0, s>>>(c->n, d->rowptr, d->colind, (const double *)d->A,
-                                                                 (const double *)x, nullptr, (double *)y);
-  }
+}  // namespace fe
+
+namespace fe {
+
+void launch_batch_spmv(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y, const double *b,
+                       cudaStream_t s) {
+  d->launches += int64_t(d->spmv_classes.size());
+  for (const auto &k : d->spmv_classes) run_class(c, d, k, fp32, x, y, b, s);
 }
 
-void launch_spmv_plain(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y, const double *b,
-                       int tpr, cudaStream_t s) {
+void launch_seg_cond(const fe_ctx *c, const DeviceState *d, cudaGraphConditionalHandle h, int mode,
+                     cudaStream_t s) {
   d->launches++;
-  switch (tpr) {
-    case 4: spmv_t<4>(c, d, fp32, x, y, b, s); break;
-    case 16: spmv_t<16>(c, d, fp32, x, y, b, s); break;
-    case 32: spmv_t<32>(c, d, fp32, x, y, b, s); break;
-    default: spmv_t<8>(c, d, fp32, x, y, b, s);
+  seg_cond_kernel<<<1, 256, 0, s>>>(h, d->bscal, d->scal, c->nseg, mode, double(c->opt.max_iters), d->flags);
+}
+
+// Size classes and row blocks of the batched SpMV, then each class's lanes
+// per node from {4, 8, 16, 32} by timing its own row blocks on the assembled
+// matrix (CUDA events, 3 runs each, the median).  Members are ordered by
+// their mean blocks per free node and cut into at most three classes of
+// about equal node counts: longer rows want more lanes per node.
+int tune_batch_spmv(fe_ctx *c, DeviceState *d) {
+  if (d->spmv_tuned) return FE_OK;
+  const int32_t nb = c->nseg;
+  std::vector<std::pair<double, int32_t>> mean(nb);
+  int64_t total_nodes = 0;
+  for (int32_t k = 0; k < nb; ++k) {
+    int64_t blocks = 0, freen = 0;
+    for (int64_t n = c->seg_node[k]; n < c->seg_node[k + 1]; ++n) {
+      if (c->fixed_dof[3 * n]) continue;
+      blocks += c->bptr[n + 1] - c->bptr[n];
+      ++freen;
+    }
+    mean[k] = {freen ? double(blocks) / double(freen) : 0.0, k};
+    total_nodes += c->seg_node[k + 1] - c->seg_node[k];
   }
+  std::stable_sort(mean.begin(), mean.end());
+  const int ncls = nb >= 3 ? 3 : nb;
+  d->spmv_classes.assign(ncls, DeviceState::SpmvClass());
+  int64_t acc = 0;
+  for (const auto &m : mean) {
+    const int32_t k = m.second;
+    const int cls = std::min<int>(ncls - 1, int(acc * ncls / std::max<int64_t>(total_nodes, 1)));
+    d->spmv_classes[cls].members.push_back(k);
+    acc += c->seg_node[k + 1] - c->seg_node[k];
+  }
+  for (auto &cl : d->spmv_classes) {
+    std::vector<int2> blk;
+    std::sort(cl.members.begin(), cl.members.end());
+    for (int32_t k : cl.members)
+      for (int64_t n0 = c->seg_node[k]; n0 < c->seg_node[k + 1]; n0 += kBatchBlockNodes)
+        blk.push_back(make_int2(int(n0), int(std::min<int64_t>(n0 + kBatchBlockNodes, c->seg_node[k + 1]))));
+    cl.nblocks = int64_t(blk.size());
+    if (!blk.empty()) {
+      cudaError_t e = cudaMalloc(&cl.blocks, blk.size() * sizeof(int2));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(c, FE_ERR_OOM, "batched SpMV schedule allocation failed");
+      }
+      d->allocs.push_back(cl.blocks);
+      FE_CUDA_TRY(cudaMemcpy(cl.blocks, blk.data(), blk.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    }
+  }
+  const bool fp32 = c->opt.precision == FE_MIXED;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FE_CUDA_TRY(cudaEventCreate(&e0));
+  cudaError_t er = cudaEventCreate(&e1);
+  for (auto &cl : d->spmv_classes) {
+    if (er != cudaSuccess || !cl.nblocks) continue;
+    float best = 1e30f;
+    int best_lpn = 16;
+    for (int lpn : {4, 8, 16, 32}) {
+      cl.lpn = lpn;
+      float t[3] = {0.f, 0.f, 0.f};
+      for (int rep = 0; rep < 3 && er == cudaSuccess; ++rep) {
+        er = cudaEventRecord(e0, d->stream);
+        if (er == cudaSuccess) run_class(c, d, cl, fp32, d->vp, d->vq, nullptr, d->stream);
+        if (er == cudaSuccess) er = cudaGetLastError();
+        if (er == cudaSuccess) er = cudaEventRecord(e1, d->stream);
+        if (er == cudaSuccess) er = cudaEventSynchronize(e1);
+        if (er == cudaSuccess) er = cudaEventElapsedTime(&t[rep], e0, e1);
+      }
+      std::sort(t, t + 3);
+      if (er == cudaSuccess && t[1] < best) {
+        best = t[1];
+        best_lpn = lpn;
+      }
+    }
+    cl.lpn = best_lpn;
+  }
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (er != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(c, FE_ERR_CUDA, std::string("batched SpMV autotuner: ") + cudaGetErrorString(er));
+  }
+  d->spmv_tuned = true;
+  return FE_OK;
 }
 
 }  // namespace fe

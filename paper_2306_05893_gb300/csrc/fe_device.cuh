@@ -27,13 +27,15 @@ struct DFront {
   int64_t f_off, y_off, w_off, u_off, rows_off, fac_off;
 };
 
-// Error flags raised by kernels (bit mask in DeviceState::flags[0]).
-enum { FLAG_INVERTED = 1, FLAG_PIVOT = 2, FLAG_BREAKDOWN = 4, FLAG_WAIT_TIMEOUT = 8 };
+// Error flags raised by kernels (bit mask in DeviceState::flags[0]; an
+// allocation-free application raises its own in flags[1], which stays set
+// until a later call of the context reports it).
+enum { FLAG_INVERTED = 1, FLAG_PIVOT = 2, FLAG_BREAKDOWN = 4, FLAG_WAIT_TIMEOUT = 8, FLAG_APPLY_TIMEOUT = 16 };
 
 // Scalars of the PCG kept on the device (double).
 enum {
   S_RZ = 0, S_RZ_NEW, S_PQ, S_ALPHA, S_BETA, S_RR, S_BB, S_TOL2, S_DONE, S_ITERS,
-  S_ORR, S_OTOL2, S_ODONE, S_NDELTA, S_NA,
+  S_ORR, S_OTOL2, S_ODONE, S_NDELTA, S_NA, S_SWEEPS,
   S_COUNT = 16
 };
 
@@ -52,6 +54,9 @@ struct DeviceState {
   cudaStream_t fstream = nullptr;  // factor side stream
   bool own_stream = false;
   cudaEvent_t ev_assembled = nullptr, ev_factored = nullptr, ev_apply_done = nullptr;
+  // ordering of fe_apply_preconditioner_noalloc on a caller's stream against
+  // the context's own stream, both ways (created with the device state)
+  cudaEvent_t ev_main_tail = nullptr, ev_noalloc_done = nullptr;
   std::vector<void *> allocs;
 
   // mesh / setup
@@ -69,11 +74,15 @@ struct DeviceState {
   double *stage_in = nullptr, *stage_out = nullptr;  // pinned host staging [n]
   double *stage_big = nullptr; size_t stage_big_bytes = 0;
 
-  // element outputs f_e, K_e in the element type (FP64, or FP32 when mixed)
-  void *fe = nullptr;
+  // element outputs: forces f_e in FP64; tangents K_e in FP64, or FP32 in
+  // the mixed path (unless element_fp64)
+  double *fe = nullptr;
   void *Ke = nullptr;
-  // system: A in the matrix type (+ the snapshot the factor reads), b in FP64
+  // system: A in the matrix type (FP64, or FP32 in the mixed path: the inner
+  // SpMV and the snapshot the factor reads), its FP64 copy A64 in the mixed
+  // path (the refinement residual; equal to A in the FP64 path), b in FP64
   void *A = nullptr;
+  double *A64 = nullptr;
   void *Afac = nullptr;
   double *b = nullptr;
 
@@ -123,14 +132,16 @@ struct DeviceState {
   double *D[2] = {nullptr, nullptr};
   void *wbuf = nullptr, *ubuf = nullptr, *yperm = nullptr;  // apply work vectors
   double *na = nullptr, *nq = nullptr, *nv = nullptr;       // Newton iterate a_k, q_k, v_k
-  struct PcgGraph {                                         // captured PCG iteration blocks
-    bool fp32;
-    void *X, *R;
-    int cur;
-    cudaGraphExec_t exec;
-    int64_t launches;
+  // whole-step graphs (use_graph): the solve (PCG, refinement) and the
+  // integration of a step as one graph with device-side WHILE loops, one
+  // per factor buffer the applications read; kernels per prologue, inner
+  // iteration and refinement sweep (launch counting)
+  struct StepGraph {
+    int cur = -1;
+    cudaGraphExec_t exec = nullptr;
+    int64_t k_pro = 0, k_inner = 0, k_outer = 0;
   };
-  std::vector<PcgGraph> graphs;
+  StepGraph step_graph[2];
   void *part_f = nullptr, *part_b = nullptr;                // partial sums of split apply tasks
   int *tick_f = nullptr, *tick_b = nullptr;                 // their tickets (zero between launches)
   // dataflow application: task lists, per-front counters (forward: children
@@ -139,6 +150,8 @@ struct DeviceState {
   int64_t n_apply_fwd = 0, n_apply_bwd = 0;
   int *df_pend = nullptr, *df_fdone = nullptr, *df_bdone = nullptr, *df_ctl = nullptr;
   int df_grid = 0;                                          // resident CTAs of the application kernels
+  mutable int df_hold = -1;        // fe_debug_hold_front: front held for the next application, or -1
+  int df_hold_extra = 0;
   int cur = 0;                     // buffer the solver reads
   int factor_pending = -1;         // buffer being written on fstream, or -1
   int64_t pending_step = -1;       // step whose A the pending factor holds
@@ -172,7 +185,21 @@ struct DeviceState {
   int64_t *seg_dof = nullptr;
   int32_t *row_seg = nullptr;
   double *bscal = nullptr, *h_bscal = nullptr;
-  int spmv_tpr = 0;                // autotuned threads per CSR row (0: not yet)
+  // batched SpMV schedule (fe_batch.cu): members grouped into size classes
+  // by their mean 3x3 blocks per node; each class is a table of row blocks
+  // (node ranges of at most kBatchBlockNodes nodes inside one member) and
+  // has its own lanes per node, chosen by timing the candidates
+  struct SpmvClass {
+    int lpn = 16;
+    int2 *blocks = nullptr;
+    int64_t nblocks = 0;
+    std::vector<int32_t> members;
+  };
+  std::vector<SpmvClass> spmv_classes;
+  bool spmv_tuned = false;
+  // single-mesh SpMV variants (tune_spmv): -1 until the first solve times them
+  int spmv_var = -1, res_var = -1;
+  double *tune_scal = nullptr;     // scratch scalars and flags of the timing runs
 
   // adjoint: per-step checkpoints (q_t, v_t, a_t) and reverse-sweep buffers
   std::vector<double *> ckpt;      // each [3n]: q_t, v_t, a_t
@@ -196,6 +223,8 @@ void launch_newton_update(const fe_ctx *c, const DeviceState *d, const double *d
 void launch_spmv_dot(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y, cudaStream_t s);
 // r = b - A x (FP64 accumulation); S_ORR, S_ODONE
 void launch_residual(const fe_ctx *c, const DeviceState *d, bool fp32, cudaStream_t s);
+// times the SpMV variants of both products once per context (first solve)
+int tune_spmv(fe_ctx *c, DeviceState *d);
 // x += alpha p; r -= alpha q; S_RR, S_DONE, S_ITERS
 void launch_axpy_norm(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const void *p,
                       const void *q, cudaStream_t s);
@@ -210,6 +239,15 @@ void launch_init_solve(const fe_ctx *c, const DeviceState *d, bool fp32, void *x
                        double tol, bool outer, cudaStream_t s);
 void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s);  // x += (double) vd
 void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s);
+// the same, skipped on the device unless the step's solve converged with no
+// error flag (the whole-step graph decides without a host read)
+void launch_integrate_guarded(const fe_ctx *c, const DeviceState *d, bool fp32, cudaStream_t s);
+// sets a graph conditional from the device scalars: mode 0, the inner PCG
+// goes on (S_DONE == 0); mode 1, the outer refinement goes on (S_ODONE == 0
+// and S_ITERS < max_iters; counts the sweep); mode 2, the same without
+// counting; every mode stops on an error flag
+void launch_graph_cond(const fe_ctx *c, const DeviceState *d, cudaGraphConditionalHandle h, int mode,
+                       cudaStream_t s);
 void launch_convert(const void *src, bool src32, void *dst, bool dst32, int64_t n, cudaStream_t s);
 
 // (fe_batch.cu)
@@ -223,8 +261,19 @@ void launch_seg_axpy(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, 
                      const void *q, cudaStream_t s);
 void launch_seg_update_p(const fe_ctx *c, const DeviceState *d, bool fp32, const void *z, void *p, bool first,
                          cudaStream_t s);
-void launch_spmv_plain(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y, const double *b,
-                       int tpr, cudaStream_t s);
+// batched node-block SpMV over the row-block schedule: y = A x in the
+// vector type, or y = b - A64 x in FP64 when b is given
+void launch_batch_spmv(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y, const double *b,
+                       cudaStream_t s);
+// builds the batched SpMV schedule (size classes, row blocks) and picks each
+// class's lanes per node by timing (CUDA events on the main stream)
+int tune_batch_spmv(fe_ctx *c, DeviceState *d);
+// graph conditions of the batched solve: mode 0, some member's inner PCG
+// goes on; mode 1/2, some member's refinement goes on (1 counts a sweep);
+// all stop at max_iters or on an error flag; mode 3 (FP64) / 4 (mixed)
+// writes flags[2] = 1 when every member converged with no error flag (the
+// guard of the integration)
+void launch_seg_cond(const fe_ctx *c, const DeviceState *d, cudaGraphConditionalHandle h, int mode, cudaStream_t s);
 
 // (fe_adjoint.cu)
 void launch_adjoint_element(const fe_ctx *c, const DeviceState *d, bool fp32, const double *q, const double *lam,
@@ -253,5 +302,11 @@ void apply_forward_multi_enqueue(const fe_ctx *c, const DeviceState *d, int buf,
                                  int *bdone, int *ctl, void *u, void *part, int *tickets, int nrhs, cudaStream_t s);
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
                    cudaStream_t s, const double *done = nullptr);
+// scratch bytes fe_apply_preconditioner_noalloc needs for this mesh (0
+// before the setup), and the size of its file-scope array
+int64_t noalloc_scratch_bytes(const fe_ctx *c);
+// fe_debug_hold_front: apply a pending hold on the stream (no-op without one)
+void launch_pending_hold(const DeviceState *d, cudaStream_t s);
+int64_t noalloc_scratch_limit();
 
 }  // namespace fe

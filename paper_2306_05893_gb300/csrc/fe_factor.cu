@@ -1185,7 +1185,8 @@ __device__ __forceinline__ bool last_of_block(int *ticket, int nch) {
 // of the same launch are read through L2 (ld.cg), never a stale L1 line.
 // Control words df_ctl: [0] forward queue, [1] backward queue, [2] forward
 // abort, [3] backward abort; each launch resets the other direction's words.
-constexpr uint64_t kDepWaitNs = 1000000000ull;
+// dependency waits of the application kernels give up after wait_ns
+// (fe_options.dep_wait_s), raising FLAG_APPLY_TIMEOUT and the launch's abort word
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
   int v;
@@ -1194,13 +1195,13 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 }
 
 // thread 0: wait until *p == target (or abort / timeout); true when satisfied
-__device__ __forceinline__ bool dep_wait(const int *p, int target, int *abort_word, int *flags) {
+__device__ __forceinline__ bool dep_wait(const int *p, int target, int *abort_word, int *flags, uint64_t wait_ns) {
   const uint64_t t0 = global_ns();
   for (;;) {
     if (ld_acquire(p) == target) return true;
     if (ld_acquire(abort_word) != 0) return false;
-    if (global_ns() - t0 > kDepWaitNs) {
-      atomicOr(flags, FLAG_WAIT_TIMEOUT);
+    if (global_ns() - t0 > wait_ns) {
+      atomicOr(flags, FLAG_APPLY_TIMEOUT);
       atomicExch(abort_word, 1);
       return false;
     }
@@ -1264,7 +1265,7 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
                                                   TV *__restrict__ ubuf, TV *__restrict__ yperm,
                                                   TV *__restrict__ part, int *__restrict__ tickets,
                                                   int *pend, int *fdone, int *bdone, int *ctl, int nfronts,
-                                                  int *flags, const double *__restrict__ done,
+                                                  int *flags, uint64_t wait_ns, const double *__restrict__ done,
                                                   RhsStrides rs = RhsStrides{}) {
   static_assert(kFwdCols == 256, "one gathered column per thread");
   using V = typename Vec16<TF>::type;
@@ -1338,7 +1339,7 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     for (int u = 0; u < kFwdU; ++u)
       cv[u] = (live && jq + 8 * u < j1) ? *reinterpret_cast<const V *>(yc + int64_t(jq + 8 * u) * fr.ldy) : V{};
     // the children's update vectors must be complete
-    if (threadIdx.x == 0) s_ok = dep_wait(pendv + fid, 0, ctl + 2, flags);
+    if (threadIdx.x == 0) s_ok = dep_wait(pendv + fid, 0, ctl + 2, flags, wait_ns);
     __syncthreads();
     bool wnz = false;
     if (s_ok) {
@@ -1481,7 +1482,7 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
                                                   const TV *__restrict__ yperm, TV *__restrict__ z,
                                                   TV *__restrict__ part, int *__restrict__ tickets,
                                                   int *pend, int *fdone, int *bdone, int *ctl, int nfronts,
-                                                  int *flags, const double *__restrict__ done) {
+                                                  int *flags, uint64_t wait_ns, const double *__restrict__ done) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int BR = sizeof(TF) == 2 ? 2 * kBwdRows : kBwdRows;  // rows per task
@@ -1552,7 +1553,7 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
     }
     // the parent's solution entries must be complete
     if (threadIdx.x == 0)
-      s_ok = fr.parent < 0 ? 1 : dep_wait(bdone + fr.parent, fronts[fr.parent].nbwd, ctl + 3, flags);
+      s_ok = fr.parent < 0 ? 1 : dep_wait(bdone + fr.parent, fronts[fr.parent].nbwd, ctl + 3, flags, wait_ns);
     __syncthreads();
     bool xnz = false;
 #pragma unroll
@@ -1707,9 +1708,22 @@ __global__ void multi_reset_kernel(const int *__restrict__ pend_init, int *pend,
   if (blockIdx.x == 0 && threadIdx.x < 4) ctl[threadIdx.x] = 0;
 }
 
+static uint64_t wait_ns_of(const fe_ctx *c) { return uint64_t(c->opt.dep_wait_s * 1e9); }
+
+// fe_debug_hold_front: one more pending child on a front for one application,
+// so its forward tasks wait on a count that nothing reaches (the backward
+// launch resets every counter afterwards)
+__global__ void hold_front_kernel(int *pend, int front, int extra) { pend[front] += extra; }
+
+void launch_pending_hold(const DeviceState *d, cudaStream_t s) {
+  if (d->df_hold < 0) return;
+  hold_front_kernel<<<1, 1, 0, s>>>(d->df_pend, d->df_hold, d->df_hold_extra);
+  d->df_hold = -1;
+}
+
 template <typename TF, typename TV>
 static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, const TV *r, TV *z, TV *u, TV *yp,
-                              TV *part_f, TV *part_b, int *tick_f, int *tick_b, cudaStream_t s,
+                              TV *part_f, TV *part_b, int *tick_f, int *tick_b, int *flags, cudaStream_t s,
                               const double *done = nullptr) {
   const TF *Y = reinterpret_cast<const TF *>(sizeof(TF) == 2 ? d->Yh[buf] : d->Y[buf]);
   const double *Dinv = d->D[buf] + c->n_free;
@@ -1724,13 +1738,21 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device);
   const unsigned gf = unsigned(std::max<int64_t>(1, std::min<int64_t>(d->n_apply_fwd, int64_t(sms) * std::max(1, per_sm[0]))));
   const unsigned gb = unsigned(std::max<int64_t>(1, std::min<int64_t>(d->n_apply_bwd, int64_t(sms) * std::max(1, per_sm[1]))));
+  {
+    // a pending test hold applies to the next application that runs, never
+    // to one captured into a graph (the whole-step graph applies it before
+    // its launch)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusNone) launch_pending_hold(d, s);
+  }
   d->launches += 2;
   fwd_kernel<TF, TV><<<gf, 256, 0, s>>>(reinterpret_cast<const int4 *>(d->apply_fwd), d->n_apply_fwd, d->fronts, Y,
                                         Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp, part_f, tick_f, d->df_pend,
-                                        d->df_fdone, d->df_bdone, d->df_ctl, nf, d->flags, done);
+                                        d->df_fdone, d->df_bdone, d->df_ctl, nf, flags, wait_ns_of(c), done);
   bwd_kernel<TF, TV><<<gb, 256, 0, s>>>(reinterpret_cast<const int4 *>(d->apply_bwd), d->n_apply_bwd, d->fronts, Y,
                                         d->perm, d->upd_rows_old, yp, z, part_b, tick_b, d->df_pend, d->df_fdone,
-                                        d->df_bdone, d->df_ctl, nf, d->flags, done);
+                                        d->df_bdone, d->df_ctl, nf, flags, wait_ns_of(c), done);
 }
 
 template <typename TF, typename TV>
@@ -1738,7 +1760,7 @@ static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const T
                          const double *done) {
   apply_levels_with<TF, TV>(c, d, buf, r, z, reinterpret_cast<TV *>(d->ubuf), reinterpret_cast<TV *>(d->yperm),
                             reinterpret_cast<TV *>(d->part_f), reinterpret_cast<TV *>(d->part_b), d->tick_f,
-                            d->tick_b, s, done);
+                            d->tick_b, d->flags, s, done);
 }
 
 // Forward solves of nrhs right-hand sides in one launch, over a subset of
@@ -1772,19 +1794,19 @@ void apply_forward_multi_enqueue(const fe_ctx *c, const DeviceState *d, int buf,
                                                 d->perm, d->wsrc_ptr, d->wsrc, static_cast<const float *>(r),
                                                 static_cast<float *>(u), static_cast<float *>(yp),
                                                 static_cast<float *>(part), tickets, pend, fdone, bdone, ctl, nf,
-                                                d->flags, nullptr, rs);
+                                                d->flags, wait_ns_of(c), nullptr, rs);
   else if (fp32)
     fwd_kernel<float, float><<<g, 256, 0, s>>>(tk, ntask, d->fronts, static_cast<const float *>(d->Y[buf]), Dinv,
                                                d->perm, d->wsrc_ptr, d->wsrc, static_cast<const float *>(r),
                                                static_cast<float *>(u), static_cast<float *>(yp),
                                                static_cast<float *>(part), tickets, pend, fdone, bdone, ctl, nf,
-                                               d->flags, nullptr, rs);
+                                               d->flags, wait_ns_of(c), nullptr, rs);
   else
     fwd_kernel<double, double><<<g, 256, 0, s>>>(tk, ntask, d->fronts, static_cast<const double *>(d->Y[buf]), Dinv,
                                                  d->perm, d->wsrc_ptr, d->wsrc, static_cast<const double *>(r),
                                                  static_cast<double *>(u), static_cast<double *>(yp),
                                                  static_cast<double *>(part), tickets, pend, fdone, bdone, ctl, nf,
-                                                 d->flags, nullptr, rs);
+                                                 d->flags, wait_ns_of(c), nullptr, rs);
 }
 
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
@@ -1815,13 +1837,45 @@ void *g_noalloc_base[64] = {nullptr};  // device address of the array, per devic
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
+// Byte offsets of the work vectors inside the array: the same vectors the
+// context allocates for fe_apply_preconditioner (the input and output in the
+// solve's precision, the update vectors, the permuted pivot vector, the split
+// tasks' partial sums and tickets), each 256-byte aligned.
+struct NoAllocLayout {
+  size_t r, z, u, yp, pf, pb, tk, need;
+};
+NoAllocLayout noalloc_layout(const fe_ctx *c) {
+  const size_t ts = c->opt.precision == FE_MIXED ? sizeof(float) : sizeof(double);
+  NoAllocLayout L{};
+  size_t o = 0;
+  L.r = o; o += round256(size_t(c->n) * ts);
+  L.z = o; o += round256(size_t(c->n) * ts);
+  L.u = o; o += round256(size_t(std::max<int64_t>(c->u_total, 1)) * ts);
+  L.yp = o; o += round256(size_t(std::max<int64_t>(c->n_free, 1)) * ts);
+  L.pf = o; o += round256(size_t(std::max<int64_t>(c->fwd_slots, 1)) * size_t(fwd_rows(c->opt)) * ts);
+  L.pb = o; o += round256(size_t(std::max<int64_t>(c->bwd_slots, 1)) * kBwdCols * ts);
+  L.tk = o; o += round256(size_t(std::max<int64_t>(c->fwd_slots + c->bwd_slots, 1)) * sizeof(int));
+  L.need = o;
+  return L;
+}
+
 }  // namespace
+
+int64_t noalloc_scratch_bytes(const fe_ctx *c) { return c->built ? int64_t(noalloc_layout(c).need) : 0; }
+int64_t noalloc_scratch_limit() { return int64_t(kNoAllocScratchBytes); }
 
 }  // namespace fe
 
 extern "C" int fe_apply_preconditioner_noalloc(fe_ctx *c, const double *r, double *z, void *stream) {
   using namespace fe;
   if (!c || !r || !z) return FE_ERR_ARG;
+  if (!c->built) return set_error(c, FE_ERR_STATE, "fe_build_pattern has not run");
+  // the size check needs only the setup products: no GPU is touched
+  const NoAllocLayout L = noalloc_layout(c);
+  if (L.need > kNoAllocScratchBytes)
+    return set_error(c, FE_ERR_ARG, "this mesh needs " + std::to_string(L.need) +
+                                        " bytes of scratch; the allocation-free path holds " +
+                                        std::to_string(kNoAllocScratchBytes));
   DeviceState *d = c->dev;
   if (!d || !d->have_factor) return set_error(c, FE_ERR_STATE, "no factor: call fe_factor_now or fe_step first");
   int dev = 0;
@@ -1830,18 +1884,6 @@ extern "C" int fe_apply_preconditioner_noalloc(fe_ctx *c, const double *r, doubl
     return set_error(c, FE_ERR_ARG, "the context's device must be current");
   }
   const bool fp32 = c->opt.precision == FE_MIXED;
-  const size_t ts = fp32 ? sizeof(float) : sizeof(double);
-  const size_t b_vec = round256(size_t(c->n) * ts), b_u = round256(size_t(std::max<int64_t>(c->u_total, 1)) * ts);
-  const size_t b_y = round256(size_t(std::max<int64_t>(c->n_free, 1)) * ts);
-  const size_t rb = size_t(fwd_rows(c->opt));
-  const size_t b_pf = round256(size_t(std::max<int64_t>(c->fwd_slots, 1)) * rb * ts);
-  const size_t b_pb = round256(size_t(std::max<int64_t>(c->bwd_slots, 1)) * kBwdCols * ts);
-  const size_t b_t = round256(size_t(std::max<int64_t>(c->fwd_slots + c->bwd_slots, 1)) * sizeof(int));
-  const size_t need = 2 * b_vec + b_u + b_y + b_pf + b_pb + b_t;
-  if (need > kNoAllocScratchBytes)
-    return set_error(c, FE_ERR_ARG, "this mesh needs " + std::to_string(need) +
-                                        " bytes of scratch; the allocation-free path holds " +
-                                        std::to_string(kNoAllocScratchBytes));
   void *base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -1856,32 +1898,42 @@ extern "C" int fe_apply_preconditioner_noalloc(fe_ctx *c, const double *r, doubl
     base = g_noalloc_base[dev];
   }
   unsigned char *p = static_cast<unsigned char *>(base);
-  void *rT = p, *zT = p + b_vec, *ub = p + 2 * b_vec, *yp = p + 2 * b_vec + b_u;
-  void *pf = p + 2 * b_vec + b_u + b_y, *pb = p + 2 * b_vec + b_u + b_y + b_pf;
-  int *tf = reinterpret_cast<int *>(p + 2 * b_vec + b_u + b_y + b_pf + b_pb);
+  void *rT = p + L.r, *zT = p + L.z, *ub = p + L.u, *yp = p + L.yp, *pf = p + L.pf, *pb = p + L.pb;
+  int *tf = reinterpret_cast<int *>(p + L.tk);
   int *tb = tf + c->fwd_slots;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // The application shares the context's per-front counters, task queues and
+  // factor buffer with the context's own steps and applications, which run
+  // on the context's stream: start after everything queued there (a factor
+  // swap included), and make the context's stream (and through it the next
+  // refactorisation, which snapshots on that stream) wait for this call.
+  cudaError_t e = cudaEventRecord(d->ev_main_tail, d->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, d->ev_main_tail, 0);
   // z keeps the last call's values on fixed DOFs unless cleared; the split
   // tasks' tickets start at zero
-  cudaError_t e = cudaMemsetAsync(zT, 0, size_t(c->n) * ts, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(tf, 0, b_t, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(zT, 0, size_t(c->n) * (fp32 ? sizeof(float) : sizeof(double)), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tf, 0, L.need - L.tk, s);
   if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, cudaGetErrorString(e));
+  // a dependency wait that runs out raises FLAG_APPLY_TIMEOUT in flags[1],
+  // which the context's next step reports
+  int *flags = d->flags + 1;
   launch_convert(r, false, rT, fp32, c->n, s);
   if (fp32 && c->opt.precond_fp16)
     apply_levels_with<__half, float>(c, d, d->cur, static_cast<const float *>(rT), static_cast<float *>(zT),
                                      static_cast<float *>(ub), static_cast<float *>(yp), static_cast<float *>(pf),
-                                     static_cast<float *>(pb), tf, tb, s);
+                                     static_cast<float *>(pb), tf, tb, flags, s);
   else if (fp32)
     apply_levels_with<float, float>(c, d, d->cur, static_cast<const float *>(rT), static_cast<float *>(zT),
                                     static_cast<float *>(ub), static_cast<float *>(yp), static_cast<float *>(pf),
-                                    static_cast<float *>(pb), tf, tb, s);
+                                    static_cast<float *>(pb), tf, tb, flags, s);
   else
     apply_levels_with<double, double>(c, d, d->cur, static_cast<const double *>(rT), static_cast<double *>(zT),
                                       static_cast<double *>(ub), static_cast<double *>(yp),
-                                      static_cast<double *>(pf), static_cast<double *>(pb), tf, tb, s);
+                                      static_cast<double *>(pf), static_cast<double *>(pb), tf, tb, flags, s);
   launch_convert(zT, fp32, z, false, c->n, s);
   e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaEventRecord(d->ev_noalloc_done, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(d->stream, d->ev_noalloc_done, 0);
   if (e != cudaSuccess) return set_error(c, FE_ERR_CUDA, cudaGetErrorString(e));
   return FE_OK;
 }
-

@@ -6,6 +6,9 @@
 // partials in a fixed order, summed in a fixed order by the last block.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <string>
+
 #include "fe_device.cuh"
 #include "fe_material.cuh"
 
@@ -62,16 +65,46 @@ __device__ __forceinline__ bool solve_done(const double *scal) { return scal[S_D
 template <typename T>
 __device__ __forceinline__ T ld_cast(const double *p) { return T(__ldg(p)); }
 
+// The tangent part of a tet: 144 entries of K_e = V grad N^T CC grad N in
+// fill order ((a*4 + b)*9 + 3i + k), into one shared-memory row.
+template <typename T, typename L>
+__device__ __forceinline__ void tet_tangent(const L &law, const T g[4][3], T V, T *row) {
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll 1
+    for (int k = i; k < 3; ++k) {
+      T C[3][3];
+      law.block(i, k, C);
+      T hb[4][3];
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) hb[b][J] = C[J][0] * g[b][0] + C[J][1] * g[b][1] + C[J][2] * g[b][2];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const T val = V * (g[a][0] * hb[b][0] + g[a][1] * hb[b][1] + g[a][2] * hb[b][2]);
+          row[(a * 4 + b) * 9 + 3 * i + k] = val;
+          if (i != k) row[(b * 4 + a) * 9 + 3 * k + i] = val;  // major symmetry of CC
+        }
+    }
+  }
+}
+
 // One thread per tet.  Rest data SoA [10][E]: rows of Dm^{-1} (= grad N_1..3),
-// volume.  Outputs f_e [E][4][3] and K_e [E][144] in fill order
-// ((a*4 + b)*9 + 3i + k), staged through shared memory for coalesced stores.
-template <int MODEL, typename T, int BLOCK>
+// volume.  Outputs f_e [E][4][3] (force type TF) and K_e [E][144] (tangent
+// type T) in fill order, K_e staged through shared memory for coalesced
+// stores.  With TF = double and T = float (the mixed path) the kinematics,
+// stress and force are evaluated in FP64 and the tangent in FP32 from the
+// same displacement gradient.
+template <int MODEL, typename T, typename TF, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, int64_t e_begin, int64_t e_end,
                                                     const int32_t *__restrict__ conn,
                                                     const double *__restrict__ rest,
                                                     const double *__restrict__ params,
                                                     const double *__restrict__ X,
-                                                    const double *__restrict__ q, T *__restrict__ f_out,
+                                                    const double *__restrict__ q, TF *__restrict__ f_out,
                                                     T *__restrict__ K_out, int *flags) {
   extern __shared__ unsigned char smem_raw[];
   T *sk = reinterpret_cast<T *>(smem_raw);
@@ -81,67 +114,66 @@ __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, int64_t e_begin, 
   if (e < e_end) {
     const int4 cn = reinterpret_cast<const int4 *>(conn)[e];
     const int nd[4] = {cn.x, cn.y, cn.z, cn.w};
-    T g[4][3];
+    TF g[4][3];
 #pragma unroll
     for (int a = 1; a < 4; ++a)
 #pragma unroll
-      for (int J = 0; J < 3; ++J) g[a][J] = ld_cast<T>(rest + (3 * (a - 1) + J) * E + e);
+      for (int J = 0; J < 3; ++J) g[a][J] = ld_cast<TF>(rest + (3 * (a - 1) + J) * E + e);
 #pragma unroll
     for (int J = 0; J < 3; ++J) g[0][J] = -(g[1][J] + g[2][J] + g[3][J]);
-    const T V = ld_cast<T>(rest + 9 * E + e);
-    const T p0 = ld_cast<T>(params + e), p1 = ld_cast<T>(params + E + e),
-            p2 = ld_cast<T>(params + 2 * E + e);
-    T H[3][3];
+    const TF V = ld_cast<TF>(rest + 9 * E + e);
+    const TF p0 = ld_cast<TF>(params + e), p1 = ld_cast<TF>(params + E + e), p2 = ld_cast<TF>(params + 2 * E + e);
+    TF H[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int J = 0; J < 3; ++J) H[i][J] = T(0);
+      for (int J = 0; J < 3; ++J) H[i][J] = TF(0);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         // displacement in FP64, then the working type
-        const T u = T(__ldg(q + 3 * nd[a] + i) - __ldg(X + 3 * nd[a] + i));
+        const TF u = TF(__ldg(q + 3 * nd[a] + i) - __ldg(X + 3 * nd[a] + i));
 #pragma unroll
         for (int J = 0; J < 3; ++J) H[i][J] += u * g[a][J];
       }
-    Kin<T> kin;
-    kin.init(H);
-    if (!(kin.J > T(0))) atomicOr(flags, FLAG_INVERTED);
-    Law<MODEL, T> law;
-    if constexpr (MODEL == FE_COROTATIONAL) law.set_frame(H);
-    T P[3][3];
-    law.init(kin, H, p0, p1, p2, P);
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        T s = T(0);
-#pragma unroll
-        for (int J = 0; J < 3; ++J) s += P[i][J] * g[a][J];
-        f_out[e * 12 + 3 * a + i] = V * s;
-      }
     T *row = sk + threadIdx.x * LD;
-#pragma unroll 1
-    for (int i = 0; i < 3; ++i) {
-#pragma unroll 1
-      for (int k = i; k < 3; ++k) {
-        T C[3][3];
-        law.block(i, k, C);
-        T hb[4][3];
+    {
+      Kin<TF> kin;
+      kin.init(H);
+      if (!(kin.J > TF(0))) atomicOr(flags, FLAG_INVERTED);
+      Law<MODEL, TF> law;
+      if constexpr (MODEL == FE_COROTATIONAL) law.set_frame(H);
+      TF P[3][3];
+      law.init(kin, H, p0, p1, p2, P);
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int J = 0; J < 3; ++J) hb[b][J] = C[J][0] * g[b][0] + C[J][1] * g[b][1] + C[J][2] * g[b][2];
+        for (int i = 0; i < 3; ++i) {
+          TF s = TF(0);
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+          for (int J = 0; J < 3; ++J) s += P[i][J] * g[a][J];
+          f_out[e * 12 + 3 * a + i] = V * s;
+        }
+      if constexpr (sizeof(T) == sizeof(TF)) tet_tangent<T>(law, g, V, row);
+    }
+    if constexpr (sizeof(T) != sizeof(TF)) {
+      // the tangent in its own (narrower) type from the same H
+      T gt[4][3], Ht[3][3], Pt[3][3];
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const T val = V * (g[a][0] * hb[b][0] + g[a][1] * hb[b][1] + g[a][2] * hb[b][2]);
-            row[(a * 4 + b) * 9 + 3 * i + k] = val;
-            if (i != k) row[(b * 4 + a) * 9 + 3 * k + i] = val;  // major symmetry of CC
-          }
-      }
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) gt[a][J] = T(g[a][J]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) Ht[i][J] = T(H[i][J]);
+      Kin<T> kt;
+      kt.init(Ht);
+      Law<MODEL, T> lt;
+      if constexpr (MODEL == FE_COROTATIONAL) lt.set_frame(Ht);
+      lt.init(kt, Ht, T(p0), T(p1), T(p2), Pt);
+      tet_tangent<T>(lt, gt, T(V), row);
     }
   }
   __syncthreads();
@@ -153,49 +185,52 @@ __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, int64_t e_begin, 
 
 // One thread per (hex, local node a); 8 Gauss points.  Rest data SoA
 // [8 * 25][E]: per Gauss point grad N (8 x 3) and w det J0.  Thread a owns
-// the block row a of K_e (72 values) and f_a.
-template <int MODEL, typename T, int BLOCK>
+// the block row a of K_e (72 values, tangent type T) and f_a (force type TF;
+// with TF = double and T = float the stress and force are evaluated in FP64
+// and the tangent in FP32 from the same displacement gradient).
+template <int MODEL, typename T, typename TF, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, int64_t e_end,
                                                     const int32_t *__restrict__ conn,
                                                     const double *__restrict__ rest,
                                                     const double *__restrict__ params,
                                                     const double *__restrict__ X,
-                                                    const double *__restrict__ q, T *__restrict__ f_out,
+                                                    const double *__restrict__ q, TF *__restrict__ f_out,
                                                     T *__restrict__ K_out, int *flags) {
   extern __shared__ unsigned char smem_raw[];
   T *sk = reinterpret_cast<T *>(smem_raw);
   constexpr int EPB = BLOCK / 8;  // elements per block
   constexpr int LD = 577;
+  constexpr bool SPLIT = sizeof(T) != sizeof(TF);
   const int64_t e0 = e_begin + int64_t(blockIdx.x) * EPB;
   const int el = threadIdx.x >> 3, a = threadIdx.x & 7;
   const int64_t e = e0 + el;
   if (e < e_end) {
-    T u[8][3];
+    TF u[8][3];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       const int nb = __ldg(conn + e * 8 + b);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) u[b][i] = T(__ldg(q + 3 * nb + i) - __ldg(X + 3 * nb + i));
+      for (int i = 0; i < 3; ++i) u[b][i] = TF(__ldg(q + 3 * nb + i) - __ldg(X + 3 * nb + i));
     }
-    const T p0 = ld_cast<T>(params + e), p1 = ld_cast<T>(params + E + e),
-            p2 = ld_cast<T>(params + 2 * E + e);
-    Law<MODEL, T> law;
+    const TF p0 = ld_cast<TF>(params + e), p1 = ld_cast<TF>(params + E + e), p2 = ld_cast<TF>(params + 2 * E + e);
+    Law<MODEL, TF> law;
+    Law<MODEL, T> lt;
     if constexpr (MODEL == FE_COROTATIONAL) {
       // the element frame from the volume-averaged displacement gradient
-      T Hb[3][3], vol = T(0);
+      TF Hb[3][3], vol = TF(0);
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int J = 0; J < 3; ++J) Hb[i][J] = T(0);
+        for (int J = 0; J < 3; ++J) Hb[i][J] = TF(0);
 #pragma unroll 1
       for (int gp = 0; gp < 8; ++gp) {
-        const T w = ld_cast<T>(rest + (gp * 25 + 24) * E + e);
+        const TF w = ld_cast<TF>(rest + (gp * 25 + 24) * E + e);
         vol += w;
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-          T gb[3];
+          TF gb[3];
 #pragma unroll
-          for (int J = 0; J < 3; ++J) gb[J] = w * ld_cast<T>(rest + (gp * 25 + 3 * b + J) * E + e);
+          for (int J = 0; J < 3; ++J) gb[J] = w * ld_cast<TF>(rest + (gp * 25 + 3 * b + J) * E + e);
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -207,49 +242,77 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, 
 #pragma unroll
         for (int J = 0; J < 3; ++J) Hb[i][J] /= vol;
       law.set_frame(Hb);
+      if constexpr (SPLIT) {
+        T Hbt[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int J = 0; J < 3; ++J) Hbt[i][J] = T(Hb[i][J]);
+        lt.set_frame(Hbt);
+      }
     }
     T acc[8][9];
 #pragma unroll
     for (int b = 0; b < 8; ++b)
 #pragma unroll
       for (int c = 0; c < 9; ++c) acc[b][c] = T(0);
-    T fa[3] = {T(0), T(0), T(0)};
+    TF fa[3] = {TF(0), TF(0), TF(0)};
 #pragma unroll 1
     for (int gp = 0; gp < 8; ++gp) {
-      T g[8][3];
+      TF g[8][3];
 #pragma unroll
       for (int b = 0; b < 8; ++b)
 #pragma unroll
-        for (int J = 0; J < 3; ++J) g[b][J] = ld_cast<T>(rest + (gp * 25 + 3 * b + J) * E + e);
-      const T w = ld_cast<T>(rest + (gp * 25 + 24) * E + e);
-      T H[3][3];
+        for (int J = 0; J < 3; ++J) g[b][J] = ld_cast<TF>(rest + (gp * 25 + 3 * b + J) * E + e);
+      const TF w = ld_cast<TF>(rest + (gp * 25 + 24) * E + e);
+      TF H[3][3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int J = 0; J < 3; ++J) {
-          T s = T(0);
+          TF s = TF(0);
 #pragma unroll
           for (int b = 0; b < 8; ++b) s += u[b][i] * g[b][J];
           H[i][J] = s;
         }
-      Kin<T> kin;
+      Kin<TF> kin;
       kin.init(H);
-      if (!(kin.J > T(0)) && a == 0) atomicOr(flags, FLAG_INVERTED);
-      T P[3][3];
+      if (!(kin.J > TF(0)) && a == 0) atomicOr(flags, FLAG_INVERTED);
+      TF P[3][3];
       law.init(kin, H, p0, p1, p2, P);
 #pragma unroll
       for (int i = 0; i < 3; ++i) fa[i] += w * (P[i][0] * g[a][0] + P[i][1] * g[a][1] + P[i][2] * g[a][2]);
+      // the tangent in type T: the same law object, or one in T from the same H
+      T gt[8][3];
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+#pragma unroll
+        for (int J = 0; J < 3; ++J) gt[b][J] = T(g[b][J]);
+      const T wt = T(w);
+      if constexpr (SPLIT) {
+        T Ht[3][3], Pt[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int J = 0; J < 3; ++J) Ht[i][J] = T(H[i][J]);
+        Kin<T> kt;
+        kt.init(Ht);
+        lt.init(kt, Ht, T(p0), T(p1), T(p2), Pt);
+      }
+      const auto &lk = [&]() -> const Law<MODEL, T> & {
+        if constexpr (SPLIT) return lt; else return law;
+      }();
 #pragma unroll 1
       for (int i = 0; i < 3; ++i)
 #pragma unroll 1
         for (int k = 0; k < 3; ++k) {
           T C[3][3];
-          law.block(i, k, C);
+          lk.block(i, k, C);
           T vL[3];
 #pragma unroll
-          for (int L = 0; L < 3; ++L) vL[L] = w * (g[a][0] * C[0][L] + g[a][1] * C[1][L] + g[a][2] * C[2][L]);
+          for (int L = 0; L < 3; ++L) vL[L] = wt * (gt[a][0] * C[0][L] + gt[a][1] * C[1][L] + gt[a][2] * C[2][L]);
 #pragma unroll
-          for (int b = 0; b < 8; ++b) acc[b][3 * i + k] += vL[0] * g[b][0] + vL[1] * g[b][1] + vL[2] * g[b][2];
+          for (int b = 0; b < 8; ++b) acc[b][3 * i + k] += vL[0] * gt[b][0] + vL[1] * gt[b][1] + vL[2] * gt[b][2];
         }
     }
 #pragma unroll
@@ -273,38 +336,41 @@ static void launch_element_t(const fe_ctx *c, const DeviceState *d, const double
   const int64_t eb = c->model_range[MODEL][0], ee = c->model_range[MODEL][1];
   if (ee <= eb) return;
   const int64_t EN = ee - eb;
-  T *fo = reinterpret_cast<T *>(d->fe);
+  double *fo = d->fe;
   T *Ko = reinterpret_cast<T *>(d->Ke);
   if (c->elem_type == FE_TET4) {
     constexpr int B = sizeof(T) == 8 ? 64 : 128;
     const size_t sm = size_t(B) * 145 * sizeof(T);
-    cudaFuncSetAttribute(tet_kernel<MODEL, T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    tet_kernel<MODEL, T, B><<<unsigned((EN + B - 1) / B), B, sm, s>>>(E, eb, ee, d->conn, d->rest, d->params,
-                                                                      d->X, q, fo, Ko, d->flags);
+    cudaFuncSetAttribute(tet_kernel<MODEL, T, double, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    tet_kernel<MODEL, T, double, B><<<unsigned((EN + B - 1) / B), B, sm, s>>>(E, eb, ee, d->conn, d->rest, d->params,
+                                                                              d->X, q, fo, Ko, d->flags);
   } else {
     constexpr int B = 128, EPB = B / 8;
     const size_t sm = size_t(EPB) * 577 * sizeof(T);
-    cudaFuncSetAttribute(hex_kernel<MODEL, T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    hex_kernel<MODEL, T, B><<<unsigned((EN + EPB - 1) / EPB), B, sm, s>>>(E, eb, ee, d->conn, d->rest,
-                                                                         d->params, d->X, q, fo, Ko, d->flags);
+    cudaFuncSetAttribute(hex_kernel<MODEL, T, double, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    hex_kernel<MODEL, T, double, B><<<unsigned((EN + EPB - 1) / EPB), B, sm, s>>>(E, eb, ee, d->conn, d->rest,
+                                                                                 d->params, d->X, q, fo, Ko, d->flags);
   }
 }
 
+// Element forces always in FP64; tangents in FP32 when fp32 (the mixed path)
+// unless element_fp64.
 void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool fp32, cudaStream_t s) {
+  const bool k32 = fp32 && !c->opt.element_fp64;
   // one launch per material model present (a batch groups its members by model)
   for (int md = FE_SVK; md <= FE_COROTATIONAL; ++md) {
     if (c->model_range[md][1] <= c->model_range[md][0]) continue;
     d->launches++;
     if (md == FE_SVK)
-      fp32 ? launch_element_t<FE_SVK, float>(c, d, q, s) : launch_element_t<FE_SVK, double>(c, d, q, s);
+      k32 ? launch_element_t<FE_SVK, float>(c, d, q, s) : launch_element_t<FE_SVK, double>(c, d, q, s);
     else if (md == FE_NEOHOOKE)
-      fp32 ? launch_element_t<FE_NEOHOOKE, float>(c, d, q, s) : launch_element_t<FE_NEOHOOKE, double>(c, d, q, s);
+      k32 ? launch_element_t<FE_NEOHOOKE, float>(c, d, q, s) : launch_element_t<FE_NEOHOOKE, double>(c, d, q, s);
     else if (md == FE_MOONEY_RIVLIN)
-      fp32 ? launch_element_t<FE_MOONEY_RIVLIN, float>(c, d, q, s)
-           : launch_element_t<FE_MOONEY_RIVLIN, double>(c, d, q, s);
+      k32 ? launch_element_t<FE_MOONEY_RIVLIN, float>(c, d, q, s)
+          : launch_element_t<FE_MOONEY_RIVLIN, double>(c, d, q, s);
     else
-      fp32 ? launch_element_t<FE_COROTATIONAL, float>(c, d, q, s)
-           : launch_element_t<FE_COROTATIONAL, double>(c, d, q, s);
+      k32 ? launch_element_t<FE_COROTATIONAL, float>(c, d, q, s)
+          : launch_element_t<FE_COROTATIONAL, double>(c, d, q, s);
   }
 }
 
@@ -313,69 +379,128 @@ void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool
 // its element blocks' 9 contiguous values in ascending order (the order of
 // the inverse of C, so every slot equals the per-slot sum), writes its 9
 // slots (rows 3n+i, position 3*bp + k in the row) and its share of
-// (alpha M + (beta+h) K) v; the node's element forces come from its
+// (alpha M + (beta+h) K) v; the node's element forces (FP64) come from its
 // incidence list.  Fixed nodes keep the lone unit diagonal and b = 0.
-template <typename TK, typename TA, typename TS>
+//
+// FP64 path: every sum in FP64.  Mixed path (FP32 tangents): GB300's FP64
+// pipe issues at a small fraction of the FP32 rate, and a conversion plus an
+// FP64 add per gathered value made this kernel ALU-bound, so the block sums
+// are kept as double-float pairs (hi + lo, Knuth's TwoSum: the exact sum of
+// the FP32 values to about 2^-46), and A = cM M + cK K is formed in
+// double-float (Dekker's product through FMA for cK K); A is written rounded
+// to FP32 (the inner solve and the factor) and as double(hi) + double(lo)
+// (the FP64 copy the refinement residual uses).  The damping part of b is
+// summed in FP32 per lane (its terms carry the FP32 tangent's rounding
+// already) and reduced across the warp in FP64 with the forces.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
+template <typename TK, typename TA>
 __global__ void __launch_bounds__(256) assemble_block_kernel(
     int64_t n_nodes, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ bptr,
     const int32_t *__restrict__ bcol, const int32_t *__restrict__ bsrc_ptr, const int32_t *__restrict__ bsrc,
-    const double *__restrict__ bmass, const TK *__restrict__ Ke, const TK *__restrict__ fe,
+    const double *__restrict__ bmass, const TK *__restrict__ Ke, const double *__restrict__ fe,
     const int32_t *__restrict__ node_ptr, const int32_t *__restrict__ node_src,
     const int8_t *__restrict__ fixed_row, const double *__restrict__ v, const double *__restrict__ w,
-    const double *__restrict__ p, double cM_, double cK_, double al_, double bh_, TA *__restrict__ A,
-    double *__restrict__ b) {
-  // TS: type of the block sums (FP64, or FP32 in the mixed path, whose K_e and
-  // A are FP32: GB300's FP64 pipe would otherwise bound this kernel); the row
-  // partials of b are reduced across the warp in FP64 either way.
-  const TS cM = TS(cM_), cK = TS(cK_), al = TS(al_), bh = TS(bh_);
+    const double *__restrict__ p, double cM, double cK, double al, double bh, TA *__restrict__ A,
+    double *__restrict__ A64, double *__restrict__ b) {
+  constexpr bool DF = sizeof(TK) == 4;  // FP32 tangents: double-float sums
   const int lane = threadIdx.x & 31;
   const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  // cK as a float pair (cK = ckh + ckl to 2^-48)
+  const float ckh = float(cK), ckl = float(cK - double(ckh));
   for (int64_t nd = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); nd < n_nodes; nd += warps) {
     const int64_t r0 = 3 * nd;
     if (fixed_row[r0]) {
       if (lane < 3) {
         A[rowptr[r0 + lane]] = TA(1);
+        if (A64) A64[rowptr[r0 + lane]] = 1.0;
         b[r0 + lane] = 0.0;
       }
       continue;
     }
     const int32_t rps[3] = {rowptr[r0], rowptr[r0 + 1], rowptr[r0 + 2]};
-    TS acc[3] = {TS(0), TS(0), TS(0)};
+    double acc[3] = {0.0, 0.0, 0.0};
+    float accf[3] = {0.f, 0.f, 0.f};
     for (int32_t k = bptr[nd] + lane; k < bptr[nd + 1]; k += 32) {
-      TS blk[9];
-#pragma unroll
-      for (int q = 0; q < 9; ++q) blk[q] = TS(0);
       const int32_t j1 = bsrc_ptr[k + 1];
-      for (int32_t j = bsrc_ptr[k]; j < j1; ++j) {
-        const TK *src = Ke + int64_t(bsrc[j]) * 9;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) blk[q] += TS(src[q]);
-      }
-      const TS mb = TS(bmass[k]);
+      const double mb = bmass[k];
       const int32_t bp = 3 * (k - bptr[nd]);
       const int64_t cn = 3 * int64_t(bcol[k]);
-      const TS vv[3] = {TS(v[cn]), TS(v[cn + 1]), TS(v[cn + 2])};
+      if constexpr (DF) {
+        float hi[9], lo[9];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
+        for (int q = 0; q < 9; ++q) hi[q] = lo[q] = 0.f;
+        for (int32_t j = bsrc_ptr[k]; j < j1; ++j) {
+          const TK *src = Ke + int64_t(bsrc[j]) * 9;
 #pragma unroll
-        for (int kk = 0; kk < 3; ++kk) {
-          const TS Ms = (i == kk) ? mb : TS(0);
-          const TS Ks = blk[3 * i + kk];
-          A[rps[i] + bp + kk] = TA(cM * Ms + cK * Ks);
-          acc[i] += (al * Ms + bh * Ks) * vv[kk];
+          for (int q = 0; q < 9; ++q) two_sum_acc(hi[q], lo[q], float(src[q]));
         }
-        if (w) acc[i] += mb * TS(w[cn + i]);  // the M w term of a Newton correction
+        // cM * mb once per block in FP64, as a float pair
+        const double m64 = cM * mb;
+        const float mh = float(m64), ml = float(m64 - double(mh));
+        const float alm = float(al * mb);
+        const float vv[3] = {float(v[cn]), float(v[cn + 1]), float(v[cn + 2])};
+        const float bhf = float(bh);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            const int q = 3 * i + kk;
+            // cK (hi + lo) in double-float, then + cM mb on the diagonal
+            float ph = ckh * hi[q];
+            float pl = fmaf(ckh, hi[q], -ph) + (ckh * lo[q] + ckl * hi[q]);
+            if (i == kk) {
+              const float s = ph + mh, bb = s - ph;
+              pl += ((ph - (s - bb)) + (mh - bb)) + ml;
+              ph = s;
+            }
+            const float sh = ph + pl;              // renormalise: sh = fl(ph + pl)
+            const float sl = pl - (sh - ph);
+            A[rps[i] + bp + kk] = TA(sh);
+            A64[rps[i] + bp + kk] = double(sh) + double(sl);
+            accf[i] += ((i == kk ? alm : 0.f) + bhf * hi[q]) * vv[kk];
+          }
+          if (w) acc[i] += mb * w[cn + i];  // the M w term of a Newton correction
+        }
+      } else {
+        double blk[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) blk[q] = 0.0;
+        for (int32_t j = bsrc_ptr[k]; j < j1; ++j) {
+          const TK *src = Ke + int64_t(bsrc[j]) * 9;
+#pragma unroll
+          for (int q = 0; q < 9; ++q) blk[q] += double(src[q]);
+        }
+        const double vv[3] = {v[cn], v[cn + 1], v[cn + 2]};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            const double Ms = (i == kk) ? mb : 0.0;
+            const double Ks = blk[3 * i + kk];
+            const double a = cM * Ms + cK * Ks;
+            A[rps[i] + bp + kk] = TA(a);
+            if (A64) A64[rps[i] + bp + kk] = a;
+            acc[i] += (al * Ms + bh * Ks) * vv[kk];
+          }
+          if (w) acc[i] += mb * w[cn + i];  // the M w term of a Newton correction
+        }
       }
     }
-    TS fs[3] = {TS(0), TS(0), TS(0)};
+    double fs[3] = {0.0, 0.0, 0.0};
     for (int32_t j = node_ptr[nd] + lane; j < node_ptr[nd + 1]; j += 32) {
-      const TK *f = fe + int64_t(node_src[j]) * 3;
-      fs[0] += TS(f[0]);
-      fs[1] += TS(f[1]);
-      fs[2] += TS(f[2]);
+      const double *f = fe + int64_t(node_src[j]) * 3;
+      fs[0] += f[0];
+      fs[1] += f[1];
+      fs[2] += f[2];
     }
-    double a0 = double(acc[0]) + double(fs[0]), a1 = double(acc[1]) + double(fs[1]),
-           a2 = double(acc[2]) + double(fs[2]);
+    double a0 = acc[0] + double(accf[0]) + fs[0], a1 = acc[1] + double(accf[1]) + fs[1],
+           a2 = acc[2] + double(accf[2]) + fs[2];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a0 += __shfl_xor_sync(0xffffffffu, a0, o);
@@ -396,16 +521,18 @@ void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const dou
   const double cM = 1.0 + h * al, cK = h * (be + h);
   const int64_t nn = c->n_nodes;
   const unsigned grid = unsigned(std::min<int64_t>((nn + 7) / 8, 152 * 64));
-  if (fp32)
-    assemble_block_kernel<float, float, float><<<grid, 256, 0, s>>>(
-        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const float *)d->Ke,
-        (const float *)d->fe, d->node_ptr, d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh,
-        (float *)d->A, d->b);
+  if (fp32 && !c->opt.element_fp64)
+    assemble_block_kernel<float, float><<<grid, 256, 0, s>>>(
+        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const float *)d->Ke, d->fe, d->node_ptr,
+        d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh, (float *)d->A, d->A64, d->b);
+  else if (fp32)
+    assemble_block_kernel<double, float><<<grid, 256, 0, s>>>(
+        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const double *)d->Ke, d->fe,
+        d->node_ptr, d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh, (float *)d->A, d->A64, d->b);
   else
-    assemble_block_kernel<double, double, double><<<grid, 256, 0, s>>>(
-        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const double *)d->Ke,
-        (const double *)d->fe, d->node_ptr, d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh,
-        (double *)d->A, d->b);
+    assemble_block_kernel<double, double><<<grid, 256, 0, s>>>(
+        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const double *)d->Ke, d->fe,
+        d->node_ptr, d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh, (double *)d->A, nullptr, d->b);
 }
 
 // ------------------------------------------------------------------ SpMV
@@ -452,6 +579,89 @@ __global__ void __launch_bounds__(kRedBlock) spmv_dot_kernel(
       scal[S_ALPHA] = 0.0;
     } else {
       scal[S_ALPHA] = scal[S_RZ] / tot;
+    }
+  }
+}
+
+// Node-block SpMV.  Every free node's three rows share one column structure
+// (3x3 blocks: columns 3 bcol[k] + kk, the values of row i at rowptr[3 nd + i]
+// + 3 (k - bptr[nd]) + kk, the order the gather assembly writes), so a
+// block's column index is read once for its 9 values instead of once per
+// value.  LPN lanes per node, each lane one block at a time (its three x
+// entries loaded once for the three rows), the three row sums reduced across
+// the node's lanes; fixed nodes keep their lone diagonal entry.
+// MODE 0: y = A x fused with x.y (then alpha = S_RZ / x.y, breakdown when
+// x.y <= 0), in the vector type; MODE 1: r = b - A x and ||r||^2 -> S_ORR,
+// S_ODONE, in FP64 (the refinement residual on the FP64 copy of A).
+template <typename TA, typename TV, int LPN, int MODE>
+__global__ void __launch_bounds__(kRedBlock) bspmv_kernel(
+    int64_t n_nodes, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ bptr,
+    const int32_t *__restrict__ bcol, const int8_t *__restrict__ fixed_row, const TA *__restrict__ A,
+    const TV *__restrict__ x, TV *__restrict__ y, const double *__restrict__ b, double *scal, double *partials,
+    unsigned int *ticket, int *flags) {
+  if (MODE == 0 && solve_done(scal)) return;
+  constexpr int GPW = 32 / LPN;  // nodes per warp
+  const int sub = threadIdx.x % LPN;
+  const int64_t groups = int64_t(gridDim.x) * (kRedBlock / LPN);
+  // the loop bound is warp-uniform so every lane reaches every shuffle
+  const int64_t warp_node0 = int64_t(blockIdx.x) * (kRedBlock / LPN) + (threadIdx.x / 32) * GPW;
+  double red = 0.0;
+  for (int64_t n0 = warp_node0; n0 < n_nodes; n0 += groups) {
+    const int64_t nd = n0 + (threadIdx.x % 32) / LPN;
+    TV a0 = TV(0), a1 = TV(0), a2 = TV(0);
+    bool fixed = true;
+    if (nd < n_nodes) {
+      fixed = fixed_row[3 * nd] != 0;
+      if (!fixed) {
+        const int32_t k0 = bptr[nd], k1 = bptr[nd + 1];
+        const int32_t r0 = rowptr[3 * nd], r1 = rowptr[3 * nd + 1], r2 = rowptr[3 * nd + 2];
+        for (int32_t k = k0 + sub; k < k1; k += LPN) {
+          const int64_t cc = 3 * int64_t(bcol[k]);
+          const TV x0 = x[cc], x1 = x[cc + 1], x2 = x[cc + 2];
+          const int32_t o = 3 * (k - k0);
+          a0 += TV(A[r0 + o]) * x0 + TV(A[r0 + o + 1]) * x1 + TV(A[r0 + o + 2]) * x2;
+          a1 += TV(A[r1 + o]) * x0 + TV(A[r1 + o + 1]) * x1 + TV(A[r1 + o + 2]) * x2;
+          a2 += TV(A[r2 + o]) * x0 + TV(A[r2 + o + 1]) * x1 + TV(A[r2 + o + 2]) * x2;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = LPN / 2; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o, LPN);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o, LPN);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o, LPN);
+    }
+    if (sub == 0 && nd < n_nodes) {
+      const TV acc[3] = {a0, a1, a2};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int64_t r = 3 * nd + i;
+        const TV yi = fixed ? TV(A[rowptr[r]]) * x[r] : acc[i];
+        if constexpr (MODE == 0) {
+          y[r] = yi;
+          red += double(x[r]) * double(yi);
+        } else {
+          const double ri = b[r] - double(yi);
+          y[r] = TV(ri);
+          red += ri * ri;
+        }
+      }
+    }
+  }
+  double tot;
+  if (grid_sum<kRedBlock>(red, partials, ticket, &tot) && threadIdx.x == 0) {
+    if constexpr (MODE == 0) {
+      scal[S_PQ] = tot;
+      if (!(tot > 0.0)) {
+        atomicOr(flags, FLAG_BREAKDOWN);
+        scal[S_DONE] = 1.0;
+        scal[S_ALPHA] = 0.0;
+      } else {
+        scal[S_ALPHA] = scal[S_RZ] / tot;
+      }
+    } else {
+      scal[S_ORR] = tot;
+      scal[S_ODONE] = (tot <= scal[S_OTOL2]) ? 1.0 : 0.0;
     }
   }
 }
@@ -574,6 +784,7 @@ __global__ void __launch_bounds__(kRedBlock) init_solve_kernel(int64_t n, TV *__
       scal[S_ORR] = tot;
       scal[S_ODONE] = (tot == 0.0) ? 1.0 : 0.0;
       scal[S_ITERS] = 0.0;
+      scal[S_SWEEPS] = 0.0;
     }
     scal[S_TOL2] = tol * tol * tot;
     scal[S_RR] = tot;
@@ -593,6 +804,31 @@ __global__ void integrate_kernel(int64_t n, double h, const double *__restrict__
     v[i] = vn;
     q[i] += h * vn;
   }
+}
+
+// mode 0: FP64 solve (S_DONE == 1), 1: refined mixed solve (S_ODONE == 1),
+// 2: batched solve (flags[2] == 1, set when every member converged)
+__global__ void integrate_guard_kernel(int64_t n, double h, const double *__restrict__ a, double *__restrict__ v,
+                                       double *__restrict__ q, const double *scal, const int *flags, int mode) {
+  const bool ok = flags[0] == 0 && (mode == 2 ? flags[2] == 1 : mode == 1 ? scal[S_ODONE] == 1.0 : scal[S_DONE] == 1.0);
+  if (!ok) return;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double vn = v[i] + h * a[i];
+    v[i] = vn;
+    q[i] += h * vn;
+  }
+}
+
+__global__ void graph_cond_kernel(cudaGraphConditionalHandle hnd, double *scal, const int *flags, int mode,
+                                  double max_iters) {
+  bool go;
+  if (mode == 0) {
+    go = scal[S_DONE] == 0.0;
+  } else {
+    go = scal[S_ODONE] == 0.0 && scal[S_ITERS] < max_iters;
+    if (mode == 1) scal[S_SWEEPS] += 1.0;
+  }
+  cudaGraphSetConditional(hnd, (go && flags[0] == 0) ? 1u : 0u);
 }
 
 __global__ void newton_state_kernel(int64_t n, double h, const double *__restrict__ q, const double *__restrict__ v,
@@ -631,55 +867,119 @@ static unsigned ew_grid(int64_t n) {
   return unsigned(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)));
 }
 
-static int tpr_for(const fe_ctx *c) { return c->elem_type == FE_TET4 ? 8 : 16; }
+// SpMV variants: 0-3 the node-block kernel with 4, 8, 16 or 32 lanes per
+// node, 4-5 the CSR kernel with 8 or 16 threads per row.  The first solve
+// of a context times them (tune_spmv) and keeps the fastest for each of the
+// two products: y = A x with x.y in the inner solve's type, and the FP64
+// residual r = b - A64 x.
+constexpr int kSpmvVariants = 6;
+
+template <typename TA, typename TV, int MODE>
+static void launch_spmv_variant(const fe_ctx *c, const DeviceState *d, int var, const TA *A, const TV *x, TV *y,
+                                const double *b, double *scal, int *flags, cudaStream_t s) {
+  const int64_t nn = c->n_nodes, n = c->n;
+  switch (var) {
+#define FE_BSPMV(V, L)                                                                                            \
+  case V:                                                                                                         \
+    bspmv_kernel<TA, TV, L, MODE><<<red_grid(nn * L), kRedBlock, 0, s>>>(nn, d->rowptr, d->bptr, d->bcol,          \
+                                                                       d->fixed_row, A, x, y, b, scal,           \
+                                                                       d->partials, d->ticket, flags);           \
+    break;
+    FE_BSPMV(0, 4)
+    FE_BSPMV(1, 8)
+    FE_BSPMV(2, 16)
+    FE_BSPMV(3, 32)
+#undef FE_BSPMV
+    default: {
+      const bool t16 = var == 5;
+      const unsigned g = red_grid(n * (t16 ? 16 : 8) / 4);
+      if constexpr (MODE == 0) {
+        if (t16)
+          spmv_dot_kernel<TA, TV, 16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, A, x, y, scal, d->partials,
+                                                              d->ticket, flags);
+        else
+          spmv_dot_kernel<TA, TV, 8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, A, x, y, scal, d->partials,
+                                                             d->ticket, flags);
+      } else {
+        if (t16)
+          residual_kernel<TA, 16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, A, x, b, y, scal, d->partials,
+                                                          d->ticket);
+        else
+          residual_kernel<TA, 8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, A, x, b, y, scal, d->partials,
+                                                         d->ticket);
+      }
+    }
+  }
+}
+
+static void spmv_dot_var(const fe_ctx *c, const DeviceState *d, int var, bool fp32, const void *x, void *y,
+                         double *scal, int *flags, cudaStream_t s) {
+  if (fp32)
+    launch_spmv_variant<float, float, 0>(c, d, var, (const float *)d->A, (const float *)x, (float *)y, nullptr, scal,
+                                         flags, s);
+  else
+    launch_spmv_variant<double, double, 0>(c, d, var, (const double *)d->A, (const double *)x, (double *)y, nullptr,
+                                           scal, flags, s);
+}
 
 void launch_spmv_dot(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, void *y,
                      cudaStream_t s) {
   d->launches++;
-  const int64_t n = c->n;
-  const unsigned g = red_grid(n * tpr_for(c) / 4);
-  if (fp32) {
-    if (tpr_for(c) == 8)
-      spmv_dot_kernel<float, float, 8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const float *)d->A,
-                                                               (const float *)x, (float *)y, d->scal,
-                                                               d->partials, d->ticket, d->flags);
-    else
-      spmv_dot_kernel<float, float, 16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const float *)d->A,
-                                                                (const float *)x, (float *)y, d->scal,
-                                                                d->partials, d->ticket, d->flags);
-  } else {
-    if (tpr_for(c) == 8)
-      spmv_dot_kernel<double, double, 8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind,
-                                                                 (const double *)d->A, (const double *)x,
-                                                                 (double *)y, d->scal, d->partials,
-                                                                 d->ticket, d->flags);
-    else
-      spmv_dot_kernel<double, double, 16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind,
-                                                                  (const double *)d->A, (const double *)x,
-                                                                  (double *)y, d->scal, d->partials,
-                                                                  d->ticket, d->flags);
-  }
+  spmv_dot_var(c, d, d->spmv_var, fp32, x, y, d->scal, d->flags, s);
 }
 
-void launch_residual(const fe_ctx *c, const DeviceState *d, bool fp32, cudaStream_t s) {
+void launch_residual(const fe_ctx *c, const DeviceState *d, bool, cudaStream_t s) {
+  // r = b - A64 x: the FP64 copy of A (A itself in the FP64 path)
   d->launches++;
-  const int64_t n = c->n;
-  const unsigned g = red_grid(n * tpr_for(c) / 4);
-  if (fp32) {
-    if (tpr_for(c) == 8)
-      residual_kernel<float, 8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const float *)d->A, d->x,
-                                                        d->b, d->r, d->scal, d->partials, d->ticket);
-    else
-      residual_kernel<float, 16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const float *)d->A, d->x,
-                                                         d->b, d->r, d->scal, d->partials, d->ticket);
-  } else {
-    if (tpr_for(c) == 8)
-      residual_kernel<double, 8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const double *)d->A,
-                                                         d->x, d->b, d->r, d->scal, d->partials, d->ticket);
-    else
-      residual_kernel<double, 16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, (const double *)d->A,
-                                                          d->x, d->b, d->r, d->scal, d->partials, d->ticket);
+  launch_spmv_variant<double, double, 1>(c, d, d->res_var, d->A64, d->x, d->r, d->b, d->scal, d->flags, s);
+}
+
+// Times every variant of both products (CUDA events on the main stream, 3
+// runs each, the median) on the assembled matrix; the timing runs write
+// their scalars and flags to scratch words, not the solve's.
+int tune_spmv(fe_ctx *c, DeviceState *d) {
+  if (d->spmv_var >= 0) return FE_OK;
+  const bool fp32 = c->opt.precision == FE_MIXED;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FE_CUDA_TRY(cudaEventCreate(&e0));
+  cudaError_t er = cudaEventCreate(&e1);
+  double *ts = d->tune_scal;
+  int *tf = reinterpret_cast<int *>(d->tune_scal + S_COUNT);
+  int best[2] = {2, 2};
+  for (int prod = 0; prod < 2 && er == cudaSuccess; ++prod) {
+    float bt = 1e30f;
+    for (int var = 0; var < kSpmvVariants && er == cudaSuccess; ++var) {
+      float t[3] = {0.f, 0.f, 0.f};
+      for (int rep = 0; rep < 3 && er == cudaSuccess; ++rep) {
+        er = cudaMemsetAsync(ts, 0, S_COUNT * sizeof(double) + 4 * sizeof(int), d->stream);
+        if (er == cudaSuccess) er = cudaEventRecord(e0, d->stream);
+        if (er == cudaSuccess) {
+          if (prod == 0)
+            spmv_dot_var(c, d, var, fp32, d->vp, d->vq, ts, tf, d->stream);
+          else
+            launch_spmv_variant<double, double, 1>(c, d, var, d->A64, d->x, d->r, d->b, ts, tf, d->stream);
+          er = cudaGetLastError();
+        }
+        if (er == cudaSuccess) er = cudaEventRecord(e1, d->stream);
+        if (er == cudaSuccess) er = cudaEventSynchronize(e1);
+        if (er == cudaSuccess) er = cudaEventElapsedTime(&t[rep], e0, e1);
+      }
+      std::sort(t, t + 3);
+      if (er == cudaSuccess && t[1] < bt) {
+        bt = t[1];
+        best[prod] = var;
+      }
+    }
   }
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (er != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(c, FE_ERR_CUDA, std::string("SpMV autotuner: ") + cudaGetErrorString(er));
+  }
+  d->spmv_var = best[0];
+  d->res_var = best[1];
+  return FE_OK;
 }
 
 void launch_axpy_norm(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const void *p,
@@ -738,6 +1038,18 @@ void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s)
 void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
   d->launches++;
   integrate_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, c->h, d->x, d->v, d->q);
+}
+
+void launch_integrate_guarded(const fe_ctx *c, const DeviceState *d, bool fp32, cudaStream_t s) {
+  d->launches++;
+  integrate_guard_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, c->h, d->x, d->v, d->q, d->scal, d->flags,
+                                                        c->nseg > 1 ? 2 : (fp32 ? 1 : 0));
+}
+
+void launch_graph_cond(const fe_ctx *c, const DeviceState *d, cudaGraphConditionalHandle h, int mode,
+                       cudaStream_t s) {
+  d->launches++;
+  graph_cond_kernel<<<1, 1, 0, s>>>(h, d->scal, d->flags, mode, double(c->opt.max_iters));
 }
 
 void launch_newton_state(const fe_ctx *c, const DeviceState *d, const double *a, double *qk, double *vk,

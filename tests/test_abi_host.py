@@ -292,3 +292,73 @@ def test_contact_option_defaults(fe):
     o = fe.options()
     assert o.contact_sweeps == 200 and o.contact_tol == 1e-12
     assert o.precond_fp16 == 0 and o.factor_tf32 == 0
+
+
+def test_schedule_and_wait_option_defaults(fe):
+    o = fe.options()
+    assert o.factor_lag == 1 and o.dep_wait_s == 1.0 and o.element_fp64 == 0
+
+
+def test_factor_lag_is_checked_on_the_host(fe):
+    """The lag k of the asynchronous factor (Eq. "asynchronous
+    preconditioner") must not exceed R: two factor buffers hold the factor in
+    use and the one being made, so the next snapshot must come after the
+    swap."""
+    mesh = fi.tet_beam(1, 1, 2)
+    for R, k in ((5, 5), (5, 1), (3, 2), (1, 7)):       # k is ignored for R = 1
+        _ctx(fe, mesh, refactor_every=R, factor_lag=k).close()
+    with pytest.raises(fe.FEError) as ei:
+        _ctx(fe, mesh, refactor_every=3, factor_lag=4)
+    assert ei.value.status == 1
+
+
+def _apply_work_bytes(info, ts, fwd_parts, bwd_parts, tickets):
+    """The allocation-free call's work vectors, each rounded up to 256 bytes:
+    input and output [n], update vectors [sum of update rows], permuted pivot
+    vector [n_free], split-task partial sums and tickets."""
+    r = lambda b: (b + 255) // 256 * 256
+    return 2 * r(info["n"] * ts) + r(info["u_total"] * ts) + r(info["n_free"] * ts) + \
+        r(fwd_parts * ts) + r(bwd_parts * ts) + r(tickets * 4)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_noalloc_scratch_size(fe, precision):
+    """fe_info.noalloc_bytes covers the regular application's work vectors:
+    at least the vectors whose sizes the setup fixes (n, the fronts' update
+    rows, the free DOFs), at most those plus the split tasks' partial sums
+    (bounded by one 256-row block per forward task and one 32-column block per
+    backward task); FP64 needs about twice the mixed path's bytes."""
+    mesh = fi.tet_beam(6, 6, 24)
+    ctx = _ctx(fe, mesh, precision=precision)
+    info = ctx.info()
+    order = ctx.ordering()
+    info["u_total"] = int(order["nupd"].sum())
+    ts = 8 if precision == 0 else 4
+    lo = _apply_work_bytes(info, ts, 1, 1, 1)
+    n_fwd = sum(int(np.ceil(m / 256.0)) * int(np.ceil(p / 256.0)) for m, p in
+                zip(order["npiv"] + order["nupd"], order["npiv"]))
+    n_bwd = sum(int(np.ceil(m / 1024.0)) * int(np.ceil(p / 32.0)) for m, p in
+                zip(order["npiv"] + order["nupd"], order["npiv"]))
+    hi = _apply_work_bytes(info, ts, 256 * n_fwd, 32 * n_bwd, n_fwd + n_bwd)
+    assert lo <= info["noalloc_bytes"] <= hi, (lo, info["noalloc_bytes"], hi)
+    ctx.close()
+
+
+def test_noalloc_rejects_oversize_mesh_on_the_host(fe):
+    """A mesh whose work vectors exceed the 64 MiB array (an FP64 beam of
+    660,633 DOF needs about 70 MiB) is refused with FE_ERR_ARG before any GPU
+    work, so the check runs here without a device; a small mesh passes the
+    size check and is refused only for the missing factor (FE_ERR_STATE)."""
+    lib = fe.load()
+    big = fi.tet_beam(40, 40, 130)
+    ctx = _ctx(fe, big)
+    assert ctx.info()["noalloc_bytes"] > 64 * 2 ** 20
+    dummy = ct.c_void_p(16)      # never dereferenced: the call stops at the size check
+    st = lib.fe_apply_preconditioner_noalloc(ctx.ctx, dummy, dummy, None)
+    assert st == 1
+    assert b"bytes of scratch" in lib.fe_last_error(ctx.ctx)
+    ctx.close()
+    small = _ctx(fe, fi.tet_beam(1, 1, 2))
+    assert 0 < small.info()["noalloc_bytes"] <= 64 * 2 ** 20
+    assert lib.fe_apply_preconditioner_noalloc(small.ctx, dummy, dummy, None) == 9
+    small.close()

@@ -117,3 +117,75 @@ def test_autograd_function(gpu_lib):
     assert np.linalg.norm(scale.grad.numpy() - so) <= 1e-8 * np.linalg.norm(so)
     assert np.linalg.norm(P.grad.numpy() - po) <= 1e-8 * np.linalg.norm(po)
     ctx.close()
+
+
+# ------------------------------------------ the adjoint workload (reading C-10)
+
+def _modulus_beam(a, b, c, T):
+    """The adjoint workload's beam: trilinear hexes jittered by +-10% of the
+    spacing (seed 1), neo-Hookean with nu = lambda / (2 (lambda + mu)) of
+    (3.4e3, 3.1e4) Pa, per-element Young's modulus log-normal (median 1e4,
+    sigma 0.3, seed 11), the free end pulled by 50 Pa for T steps; the target
+    positions come from the seed-12 modulus field."""
+    mesh = fi.hex_beam(a, b, c, jitter=0.1, seed=1)
+    nu = 3.1e4 / (2 * (3.1e4 + 3.4e3))
+    base = np.array([*fi.lame_from_young(1.0, nu), 0.0])
+    E = fi.lognormal_modulus(mesh.n_elems, seed=11)
+    Et = fi.lognormal_modulus(mesh.n_elems, seed=12)
+    trac = fi.end_traction(mesh, (50.0, 0.0, 0.0)).reshape(-1)
+    return mesh, base, E, Et, np.tile(trac, (T, 1))
+
+
+def _fd_check(gpu_lib, mesh, base, E, Et, loads, n_dirs, seed=13, eps=1e-6):
+    """Adjoint dL/ds . d against central differences of the GPU rollout,
+    L(E (1 + eps d)), d ~ N(0, I) normalised (reading C-13: FP64, exact
+    factor every step, solves to 1e-13)."""
+    q0 = mesh.X.reshape(-1).copy()
+    ctx = _gpu_ctx(gpu_lib, mesh, fi.NEOHOOKE, base, Et, R=1)
+    ctx._q0 = q0
+    qt = np.empty(ctx.n)
+    ctx.set_state(q0, np.zeros_like(q0))
+    for t in range(loads.shape[0]):
+        ctx.step(loads[t], qt, None)
+    ctx.set_params(E[:, None] * base[None, :])
+    _, ds, _ = _gpu_loss_and_grad(ctx, loads, qt)
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(n_dirs):
+        d = rng.standard_normal(E.size)
+        d /= np.linalg.norm(d)
+        Ls = []
+        for sgn in (1.0, -1.0):
+            ctx.set_params((E * (1 + sgn * eps * d))[:, None] * base[None, :])
+            Ls.append(_gpu_loss_and_grad(ctx, loads, qt, grad=False)[0])
+        fd = (Ls[0] - Ls[1]) / (2 * eps)
+        rel = abs(ds @ d - fd) / abs(fd)
+        worst = max(worst, rel)
+        assert rel <= 1e-5, (rel, ds @ d, fd)
+    ctx.close()
+    return ds, qt, worst
+
+
+def test_adjoint_workload_small_beam_16_directions(gpu_lib):
+    """The 4 x 4 x 16 hex beam (1,275 DOF) over T = 20 steps: 16 central
+    difference directions, and the oracle's adjoint of the same loss."""
+    mesh, base, E, Et, loads = _modulus_beam(4, 4, 16, 20)
+    ds, qt, worst = _fd_check(gpu_lib, mesh, base, E, Et, loads, 16)
+    q0 = mesh.X.reshape(-1).copy()
+    m = O.Model(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.NEOHOOKE,
+                E[:, None] * base[None, :], 1000.0, 0.01, 0.1, 0.01)
+    _, so, _ = O.adjoint_rollout(m, q0, np.zeros_like(q0), lambda t: loads[t], loads.shape[0], qt)
+    assert np.linalg.norm(ds - so) <= 1e-8 * np.linalg.norm(so)
+    print(f"16 directions: worst |adjoint - FD| / |FD| = {worst:.2e}")
+
+
+def test_adjoint_workload_full_beam_2_directions(gpu_lib):
+    """The 20 x 20 x 80 hex beam (107,163 DOF, the adjoint workload's own
+    mesh) over T = 20 steps: 2 central-difference directions.  A normalised
+    direction spreads over 32,000 elements (about 6e-3 each), so eps = 1e-6
+    would move the positions by ~1e-11 m, where the rounding of coordinates
+    of ~1 m (1e-16 m) already leaves ~1e-4 of FD noise; eps = 1e-4 keeps the
+    perturbation per element below 1e-6 and the truncation error O(eps^2)."""
+    mesh, base, E, Et, loads = _modulus_beam(20, 20, 80, 20)
+    _, _, worst = _fd_check(gpu_lib, mesh, base, E, Et, loads, 2, eps=1e-4)
+    print(f"107k DOF, 2 directions: worst |adjoint - FD| / |FD| = {worst:.2e}")

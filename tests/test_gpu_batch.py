@@ -1,7 +1,8 @@
 """Batched stepping (S11) on the GPU against per-member oracle rollouts: each
 member of a batch of uneven beams (SVK and neo-Hookean) must follow its own
-FP64 oracle trajectory (FP64 <= 1e-8, mixed <= 1e-4 of the displacement) and
-report its own PCG iterations and residual."""
+FP64 oracle trajectory (FP64 <= 1e-8, mixed <= 1e-5 of the displacement) and
+report its own PCG iterations and residual, with the solve host-driven or
+as one graph whose loops end on the device (use_graph), bit-identical."""
 import numpy as np
 import pytest
 
@@ -23,11 +24,13 @@ def _small_members():
     return out
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-4)])
-def test_batch_members_follow_their_oracles(gpu_lib, precision, tol):
+@pytest.mark.parametrize("use_graph", [0, 1])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-5)])
+def test_batch_members_follow_their_oracles(gpu_lib, precision, tol, use_graph):
     mem = _small_members()
     b = gpu_lib.FEBatch([(m.mesh.elem_type, m.mesh.X, m.mesh.conn, m.mesh.fixed_nodes, m.model, m.params)
-                         for m in mem], 0.01, 0.1, 0.01, 1000.0, precision=precision, refactor_every=2)
+                         for m in mem], 0.01, 0.1, 0.01, 1000.0, precision=precision, refactor_every=2,
+                        use_graph=use_graph)
     p = b.concat([m.load for m in mem])
     q = np.empty(b.n)
     v = np.empty(b.n)
@@ -47,3 +50,24 @@ def test_batch_members_follow_their_oracles(gpu_lib, precision, tol):
         err = np.linalg.norm(qs[k] - qo[T]) / np.linalg.norm(qo[T] - X)
         assert err <= tol, (k, err)
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_graph_equals_host_driven_solve(gpu_lib, precision):
+    """The batched solve as one graph runs the host-driven solve's kernels in
+    the same order: identical states after several steps."""
+    mem = _small_members()
+    out = []
+    for use_graph in (0, 1):
+        b = gpu_lib.FEBatch([(m.mesh.elem_type, m.mesh.X, m.mesh.conn, m.mesh.fixed_nodes, m.model, m.params)
+                             for m in mem], 0.01, 0.1, 0.01, 1000.0, precision=precision, refactor_every=3,
+                            use_graph=use_graph)
+        p = b.concat([m.load for m in mem])
+        q, v = np.empty(b.n), np.empty(b.n)
+        its = [b.step(p, q, v).iters for _ in range(5)]
+        out.append((q.copy(), v.copy(), its, b.stats()[0].copy()))
+        b.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+    np.testing.assert_array_equal(out[0][3], out[1][3])
