@@ -5,10 +5,11 @@ x 120 cubes, 6 tets each; gravity plus the sinusoidal end traction) after
 integration"), at a fixed sample of DOFs.
 
 The oracle's direct solve does not finish in minutes at this size, so every
-step solves its system with the oracle's Jacobi CG to ||b - A a|| <= 1e-13
-||b|| (oracle.fe_oracle.Model.step_cg), far below the 1e-8 the GPU path is
-held to.  Calls only the oracle and the seeded workload generator; run from
-the repository root:
+step solves its system with the oracle's Jacobi CG to ||b - A a|| <= 1e-12
+||b|| (oracle.fe_oracle.Model.step_cg), four orders below the 1e-8 the GPU
+path is held to.  (The true residual of FP64 CG on this system levels off
+near 4e-13 of ||b||, so 1e-13 is out of reach.)  Calls only the oracle and
+the seeded workload generator; run from the repository root:
 
     python tests/golden/make_fullsize_reference.py
 """
@@ -26,7 +27,7 @@ import fe_inputs as fi  # noqa: E402
 from oracle import fe_oracle as O  # noqa: E402
 
 STEPS = 10
-TOL = 1e-13
+TOL = 1e-12
 
 
 def sample_dofs(n_nodes, X):
