@@ -166,6 +166,21 @@ typedef struct {
                              refined solution reaches tol against the FP64
                              system; the inner PCG, factor and solves stay
                              FP32 (0: FP32 tangents, see precision)          */
+  int32_t warm_start;     /* 1: a step's PCG starts from the previous step's
+                             acceleration instead of 0 (the stopping test
+                             ||b - A a|| <= tol ||b|| is unchanged, so the
+                             result differs from a cold start only within the
+                             tolerance); fe_set_state resets the guess to 0.
+                             Single meshes; batches start from 0.            */
+  int32_t spmv_variant;   /* -1 (default): the first solve times the SpMV
+                             variants on the assembled matrix and keeps the
+                             fastest (batches: lanes per node for each size
+                             class).  0-3: the node-block kernel with 4, 8,
+                             16 or 32 lanes per node; 4, 5: CSR with 8 or 16
+                             threads per row (batches use 16 lanes for 4 and
+                             5).  Variants sum each row in a different order,
+                             so runs that must agree bit for bit across
+                             contexts fix one.                               */
 } fe_options;
 
 typedef struct {

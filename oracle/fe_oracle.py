@@ -577,9 +577,8 @@ class Model:
         Returns q+, v+, a and the CG iterations."""
         A, b = self.system(q, v, p)
         a, its = cg_solve(A.tocsr(), b, tol)
-        v1 = v + self.h * a
-        q1 = q + self.h * v1
-        return q1, v1, a, its
+        v_next = v + self.h * a
+        return q + self.h * v_next, v_next, a, its
 
     def newton_residual(self, q, v, p, a):
         """Nonlinear backward-Euler residual of one step at the acceleration a:

@@ -30,7 +30,8 @@ class FeOptions(ct.Structure):
                 ("profile_stages", ct.c_int32), ("newton_iters", ct.c_int32),
                 ("newton_tol", ct.c_double), ("factor_tf32", ct.c_int32),
                 ("precond_fp16", ct.c_int32), ("contact_sweeps", ct.c_int32), ("contact_tol", ct.c_double),
-                ("factor_lag", ct.c_int32), ("dep_wait_s", ct.c_double), ("element_fp64", ct.c_int32)]
+                ("factor_lag", ct.c_int32), ("dep_wait_s", ct.c_double), ("element_fp64", ct.c_int32),
+                ("warm_start", ct.c_int32), ("spmv_variant", ct.c_int32)]
 
 
 class FeStepInfo(ct.Structure):

@@ -245,6 +245,8 @@ int ensure_device(fe_ctx *c) {
   FE_CUDA_TRY(cudaMemset(d->v, 0, n * sizeof(double)));
   FE_TRY(dalloc(c, d, &d->pext, n));
   FE_TRY(dalloc(c, d, &d->acc, n));
+  FE_TRY(dalloc(c, d, &d->a_prev, n));
+  FE_CUDA_TRY(cudaMemset(d->a_prev, 0, n * sizeof(double)));
   FE_TRY(dalloc(c, d, &d->x, n));
   FE_TRY(dalloc(c, d, &d->r, n));
   FE_TRY(dalloc(c, d, &d->b, n));
@@ -558,17 +560,25 @@ static int build_step_graph(fe_ctx *c, DeviceState::StepGraph *sg) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    if (!fp32) {
-      launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s);
+    const bool warm = c->opt.warm_start != 0;
+    if (warm) e = cudaMemcpyAsync(d->x, d->a_prev, c->n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && !fp32) {
+      launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s, warm);
       sg->k_pro = 1;
+      if (warm) {
+        launch_residual(c, d, false, s);
+        launch_warm_fixup(c, d, s);
+        sg->k_pro += 2;
+      }
       e = capture_pcg(c, false, d->x, d->r, s, s2, sg);
-    } else {
-      launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s);  // x = 0, r = b (FP64)
+    } else if (e == cudaSuccess) {
+      launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s, warm);  // x = 0 (or kept), r = b
+      if (warm) launch_residual(c, d, true, s);  // r = b - A64 x
       cudaGraphConditionalHandle ho;
       e = cudaGraphConditionalHandleCreate(&ho, capturing_graph(s), 0, 0);
       if (e == cudaSuccess) {
         launch_graph_cond(c, d, ho, 2, s);
-        sg->k_pro = 2;
+        sg->k_pro = warm ? 3 : 2;
         cudaGraph_t body;
         e = add_while(s, ho, &body);
         if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0,
@@ -907,23 +917,28 @@ int solve_batch(fe_ctx *c, fe_step_info *info) {
 
 // Solve A a = b into d->x (FP64): plain PCG, or FP64 residual refinement
 // around an FP32 inner PCG.
-int solve(fe_ctx *c, fe_step_info *info) {
+int solve(fe_ctx *c, fe_step_info *info, bool warm) {
   DeviceState *d = c->dev;
   if (c->nseg > 1) return solve_batch(c, info);
   FE_TRY(tune_spmv(c, d));
   cudaStream_t s = d->stream;
   const bool fp32 = mixed(c);
   int sweeps = 0;
+  if (warm) FE_CUDA_TRY(cudaMemcpyAsync(d->x, d->a_prev, c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (!fp32) {
-    launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s);
+    launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s, warm);
+    if (warm) {  // r = b - A x and its norm become the PCG's starting point
+      launch_residual(c, d, false, s);
+      launch_warm_fixup(c, d, s);
+    }
     FE_TRY(read_scalars(c));
     if (d->h_scal[S_DONE] == 0.0) FE_TRY(pcg(c, false, d->x, d->r));
     sweeps = 1;
     if (info) info->rel_residual = d->h_scal[S_BB] > 0 ? std::sqrt(d->h_scal[S_RR] / d->h_scal[S_BB]) : 0.0;
   } else {
-    launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s);  // x = 0, r = b (FP64)
+    launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s, warm);  // x = 0 (or kept), r = b
     for (;;) {
-      if (sweeps > 0) {
+      if (sweeps > 0 || warm) {
         Stage st(c, FE_STAGE_RESIDUAL, s);
         launch_residual(c, d, true, s);
       }
@@ -1000,6 +1015,8 @@ int fe_set_state(fe_ctx *c, const double *q, const double *v) {
   FE_TRY(ensure_device(c));
   if (q) FE_TRY(stage_in(c, c->dev->q, q, c->n));
   if (v) FE_TRY(stage_in(c, c->dev->v, v, c->n));
+  // a new state: the next warm start begins from 0 again
+  FE_CUDA_TRY(cudaMemsetAsync(c->dev->a_prev, 0, c->n * sizeof(double), c->dev->stream));
   FE_CUDA_TRY(cudaStreamSynchronize(c->dev->stream));
   return FE_OK;
 }
@@ -1156,7 +1173,7 @@ int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_ste
     return FE_OK;
   }
   // S5-S7 PCG, S9 refinement
-  int st = solve(c, info);
+  int st = solve(c, info, c->opt.warm_start && c->nseg == 1);
   if (!st && c->opt.keep_checkpoints) {
     double *ck = nullptr;
     cudaError_t e = cudaMalloc(&ck, 3 * size_t(c->n) * sizeof(double));
@@ -1193,7 +1210,7 @@ int fe_step(fe_ctx *c, const double *p_ext, double *q_out, double *v_out, fe_ste
         launch_assemble(c, d, fp32, pd, d->nv, d->na, c->beta, s);
       }
       FE_CUDA_TRY(cudaGetLastError());
-      st = solve(c, &sub);
+      st = solve(c, &sub, false);
       if (st) return st;
       if (info) info->iters += sub.iters;
       launch_newton_update(c, d, d->x, d->na, s);
@@ -1306,7 +1323,7 @@ int fe_adjoint(fe_ctx *c, const double *dL_dqT, const double *dL_dvT, double *dL
       if (st) break;
     }
     launch_adjoint_rhs(c, d, d->qbar, d->vbar, d->b, s);
-    st = solve(c, nullptr);  // lambda in d->x
+    st = solve(c, nullptr, false);  // lambda in d->x
     if (st) break;
     launch_adjoint_element(c, d, fp32, qt, d->x, at, vt, d->ge, d->kl, d->sbar, s);
     double *pb = nullptr;

@@ -32,6 +32,8 @@ int fe_options_default(fe_options *o) {
   o->factor_lag = 1;
   o->dep_wait_s = 1.0;
   o->element_fp64 = 0;
+  o->warm_start = 0;
+  o->spmv_variant = -1;
   return FE_OK;
 }
 
@@ -94,6 +96,11 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
     }
     if (!(c->opt.dep_wait_s > 0) || !std::isfinite(c->opt.dep_wait_s)) c->opt.dep_wait_s = 1.0;
     c->opt.element_fp64 = (c->opt.precision == FE_MIXED && c->opt.element_fp64) ? 1 : 0;
+    c->opt.warm_start = c->opt.warm_start ? 1 : 0;
+    if (c->opt.spmv_variant < -1 || c->opt.spmv_variant > 5) {
+      delete c;
+      return FE_ERR_ARG;
+    }
     if (c->opt.newton_iters > 1 && c->opt.keep_checkpoints) {
       delete c;
       return FE_ERR_ARG;  // the adjoint differentiates the single-linearisation step

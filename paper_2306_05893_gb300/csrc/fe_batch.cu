@@ -370,7 +370,12 @@ int tune_batch_spmv(fe_ctx *c, DeviceState *d) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   FE_CUDA_TRY(cudaEventCreate(&e0));
   cudaError_t er = cudaEventCreate(&e1);
+  const int fixed = c->opt.spmv_variant;
   for (auto &cl : d->spmv_classes) {
+    if (fixed >= 0) {  // fixed by the caller: no timing
+      cl.lpn = fixed <= 3 ? (4 << fixed) : 16;
+      continue;
+    }
     if (er != cudaSuccess || !cl.nblocks) continue;
     float best = 1e30f;
     int best_lpn = 16;

@@ -71,6 +71,7 @@ struct DeviceState {
 
   // state
   double *q = nullptr, *v = nullptr, *pext = nullptr, *acc = nullptr;
+  double *a_prev = nullptr;        // the last step's acceleration (warm start; 0 after fe_set_state)
   double *stage_in = nullptr, *stage_out = nullptr;  // pinned host staging [n]
   double *stage_big = nullptr; size_t stage_big_bytes = 0;
 
@@ -236,7 +237,10 @@ void launch_update_p(const fe_ctx *c, const DeviceState *d, bool fp32, const voi
                      cudaStream_t s);
 // x = 0, r = rhs; tolerances (outer: S_BB, S_OTOL2, S_ORR, S_ODONE, S_ITERS = 0)
 void launch_init_solve(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const double *rhs,
-                       double tol, bool outer, cudaStream_t s);
+                       double tol, bool outer, cudaStream_t s, bool keep_x = false);
+// warm start of the FP64 PCG after the residual r = b - A x: S_RR = S_ORR,
+// S_DONE = S_ODONE (or 1 when b = 0)
+void launch_warm_fixup(const fe_ctx *c, const DeviceState *d, cudaStream_t s);
 void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s);  // x += (double) vd
 void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s);
 // the same, skipped on the device unless the step's solve converged with no

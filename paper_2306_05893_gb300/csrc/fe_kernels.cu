@@ -768,11 +768,12 @@ __global__ void __launch_bounds__(kRedBlock) init_solve_kernel(int64_t n, TV *__
                                                                TV *__restrict__ r,
                                                                const double *__restrict__ rhs,
                                                                double tol, int outer, double *scal,
-                                                               double *partials, unsigned int *ticket) {
+                                                               double *partials, unsigned int *ticket,
+                                                               int keep_x) {
   double s = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * kRedBlock + threadIdx.x; i < n; i += int64_t(gridDim.x) * kRedBlock) {
     const double v = rhs[i];
-    x[i] = TV(0);
+    if (!keep_x) x[i] = TV(0);  // a warm start keeps x (its residual follows)
     r[i] = TV(v);
     s += v * v;
   }
@@ -798,24 +799,29 @@ __global__ void refine_update_kernel(int64_t n, double *__restrict__ x, const fl
 }
 
 __global__ void integrate_kernel(int64_t n, double h, const double *__restrict__ a, double *__restrict__ v,
-                                 double *__restrict__ q) {
+                                 double *__restrict__ q, double *__restrict__ a_prev) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const double vn = v[i] + h * a[i];
+    const double ai = a[i];
+    const double vn = v[i] + h * ai;
     v[i] = vn;
     q[i] += h * vn;
+    a_prev[i] = ai;  // the next step's warm start
   }
 }
 
 // mode 0: FP64 solve (S_DONE == 1), 1: refined mixed solve (S_ODONE == 1),
 // 2: batched solve (flags[2] == 1, set when every member converged)
 __global__ void integrate_guard_kernel(int64_t n, double h, const double *__restrict__ a, double *__restrict__ v,
-                                       double *__restrict__ q, const double *scal, const int *flags, int mode) {
+                                       double *__restrict__ q, double *__restrict__ a_prev, const double *scal,
+                                       const int *flags, int mode) {
   const bool ok = flags[0] == 0 && (mode == 2 ? flags[2] == 1 : mode == 1 ? scal[S_ODONE] == 1.0 : scal[S_DONE] == 1.0);
   if (!ok) return;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const double vn = v[i] + h * a[i];
+    const double ai = a[i];
+    const double vn = v[i] + h * ai;
     v[i] = vn;
     q[i] += h * vn;
+    a_prev[i] = ai;  // the next step's warm start
   }
 }
 
@@ -939,6 +945,10 @@ void launch_residual(const fe_ctx *c, const DeviceState *d, bool, cudaStream_t s
 // their scalars and flags to scratch words, not the solve's.
 int tune_spmv(fe_ctx *c, DeviceState *d) {
   if (d->spmv_var >= 0) return FE_OK;
+  if (c->opt.spmv_variant >= 0) {  // fixed by the caller
+    d->spmv_var = d->res_var = c->opt.spmv_variant;
+    return FE_OK;
+  }
   const bool fp32 = c->opt.precision == FE_MIXED;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   FE_CUDA_TRY(cudaEventCreate(&e0));
@@ -1019,15 +1029,25 @@ void launch_update_p(const fe_ctx *c, const DeviceState *d, bool fp32, const voi
 }
 
 void launch_init_solve(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const double *rhs,
-                       double tol, bool outer, cudaStream_t s) {
+                       double tol, bool outer, cudaStream_t s, bool keep_x) {
   d->launches++;
   const int64_t n = c->n;
   if (fp32)
     init_solve_kernel<float><<<red_grid(n), kRedBlock, 0, s>>>(n, (float *)x, (float *)r, rhs, tol, outer,
-                                                               d->scal, d->partials, d->ticket);
+                                                               d->scal, d->partials, d->ticket, keep_x ? 1 : 0);
   else
     init_solve_kernel<double><<<red_grid(n), kRedBlock, 0, s>>>(n, (double *)x, (double *)r, rhs, tol, outer,
-                                                                d->scal, d->partials, d->ticket);
+                                                                d->scal, d->partials, d->ticket, keep_x ? 1 : 0);
+}
+
+__global__ void warm_fixup_kernel(double *scal) {
+  scal[S_RR] = scal[S_ORR];
+  scal[S_DONE] = (scal[S_BB] == 0.0 || scal[S_ODONE] != 0.0) ? 1.0 : 0.0;
+}
+
+void launch_warm_fixup(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
+  d->launches++;
+  warm_fixup_kernel<<<1, 1, 0, s>>>(d->scal);
 }
 
 void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
@@ -1037,12 +1057,12 @@ void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s)
 
 void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
   d->launches++;
-  integrate_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, c->h, d->x, d->v, d->q);
+  integrate_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, c->h, d->x, d->v, d->q, d->a_prev);
 }
 
 void launch_integrate_guarded(const fe_ctx *c, const DeviceState *d, bool fp32, cudaStream_t s) {
   d->launches++;
-  integrate_guard_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, c->h, d->x, d->v, d->q, d->scal, d->flags,
+  integrate_guard_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, c->h, d->x, d->v, d->q, d->a_prev, d->scal, d->flags,
                                                         c->nseg > 1 ? 2 : (fp32 ? 1 : 0));
 }
 

@@ -297,6 +297,17 @@ def test_contact_option_defaults(fe):
 def test_schedule_and_wait_option_defaults(fe):
     o = fe.options()
     assert o.factor_lag == 1 and o.dep_wait_s == 1.0 and o.element_fp64 == 0
+    assert o.warm_start == 0 and o.spmv_variant == -1
+
+
+def test_spmv_variant_is_checked_on_the_host(fe):
+    mesh = fi.tet_beam(1, 1, 2)
+    for v in (-1, 0, 3, 5):
+        _ctx(fe, mesh, spmv_variant=v).close()
+    for v in (-2, 6):
+        with pytest.raises(fe.FEError) as ei:
+            _ctx(fe, mesh, spmv_variant=v)
+        assert ei.value.status == 1
 
 
 def test_factor_lag_is_checked_on_the_host(fe):

@@ -61,7 +61,7 @@ def test_batch_graph_equals_host_driven_solve(gpu_lib, precision):
     for use_graph in (0, 1):
         b = gpu_lib.FEBatch([(m.mesh.elem_type, m.mesh.X, m.mesh.conn, m.mesh.fixed_nodes, m.model, m.params)
                              for m in mem], 0.01, 0.1, 0.01, 1000.0, precision=precision, refactor_every=3,
-                            use_graph=use_graph)
+                            use_graph=use_graph, spmv_variant=2)
         p = b.concat([m.load for m in mem])
         q, v = np.empty(b.n), np.empty(b.n)
         its = [b.step(p, q, v).iters for _ in range(5)]

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _rollout(fe, wl, steps, **kw):
-    ctx = fe.FEContext.from_workload(wl, **kw)
+    ctx = fe.FEContext.from_workload(wl, spmv_variant=4, **kw)
     q = np.empty(ctx.n)
     v = np.empty(ctx.n)
     its = []
@@ -59,7 +59,7 @@ def test_graph_step_dependency_timeout(gpu_lib, precision):
     wl = fi.workload("tet-mr", a=3, b=3, c=10)
     wl.precision = precision
     q_ref, v_ref, _ = _rollout(gpu_lib, wl, 3, refactor_every=1)
-    ctx = gpu_lib.FEContext.from_workload(wl, refactor_every=1, use_graph=1, dep_wait_s=0.02)
+    ctx = gpu_lib.FEContext.from_workload(wl, refactor_every=1, use_graph=1, dep_wait_s=0.02, spmv_variant=4)
     q = np.empty(ctx.n)
     ctx.step(wl.p(0).reshape(-1), q, None)
     order = ctx.ordering()

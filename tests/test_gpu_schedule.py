@@ -55,7 +55,7 @@ def test_factor_lag_schedule(gpu_lib, precision, lag):
 
 
 def test_expected_age_formula():
-    # R = 5, k = 1: the reading of round one (factor of A_s at s+1 .. s+5)
+    # R = 5, k = 1: the factor of A_s preconditions steps s+1 .. s+5
     assert [expected_age(t, 5, 1) for t in range(12)] == [0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 1]
     assert [expected_age(t, 5, 5) for t in range(16)] == list(range(10)) + [5, 6, 7, 8, 9, 5]
     assert [expected_age(t, 1, 1) for t in range(4)] == [0, 0, 0, 0]
@@ -75,7 +75,7 @@ def test_lagged_factor_deadline_runs_out_and_context_recovers(gpu_lib):
     uninterrupted one bit for bit."""
     import torch
     wl = fi.workload("tet-mr", a=20, b=20, c=80)
-    kw = dict(precision=0, refactor_every=3, factor_lag=1)
+    kw = dict(precision=0, refactor_every=3, factor_lag=1, spmv_variant=4)
     ref = gpu_lib.FEContext.from_workload(wl, **kw)
     ctx = gpu_lib.FEContext.from_workload(wl, factor_timeout_s=1e-6, **kw)
     q_ref = np.empty(ref.n)
@@ -109,7 +109,7 @@ def test_apply_dependency_wait_runs_out_and_context_recovers(gpu_lib, precision)
     returns FE_ERR_TIMEOUT with the state unchanged; the next calls run
     normally and equal an uninterrupted context's, bit for bit."""
     wl = fi.workload("tet-mr", a=3, b=4, c=9)
-    kw = dict(precision=precision, refactor_every=1, dep_wait_s=0.02)
+    kw = dict(precision=precision, refactor_every=1, dep_wait_s=0.02, spmv_variant=4)
     ref = gpu_lib.FEContext.from_workload(wl, **kw)
     ctx = gpu_lib.FEContext.from_workload(wl, **kw)
     q_ref, q = np.empty(ref.n), np.empty(ctx.n)

@@ -10,8 +10,9 @@ integration"), the material laws and the hex quadrature (Section 3.1), the
 consistent mass (Section 4.1), the co-rotational rotation (Eq. "eqmodel"), the
 pattern (Section 4.2), the contact stages (Section "Lagrangian
 multipliers": projection, offset scaling, correction sign), the filling-order
-test of Algorithm "add" (Section 4.2), Newton's corrections and the discrete
-adjoint (not in the paper: the chain of one step's residual).
+test of Algorithm "add" (Section 4.2), Newton's corrections, the discrete
+adjoint (not in the paper: the chain of one step's residual) and the Jacobi
+CG solve of the full-size reference (Section 6.2's stopping test).
 """
 import os
 import shutil
@@ -62,6 +63,10 @@ MUTANTS = [
      "            K = self.stiffness(q)\n"),
     ("filling-order test compares the rows only",
      "np.array_equal(prev[0], rows) and np.array_equal(prev[1], cols))", "np.array_equal(prev[0], rows))"),
+    ("CG without the Jacobi preconditioner's scaling of z", "        z = dinv * r\n        rz_new", "        z = r\n        rz_new"),
+    ("CG stops on the recursive residual alone",
+     "            r = b - A @ x                     # the recursion's residual drifts: confirm with the true one\n",
+     ""),
 ]
 
 

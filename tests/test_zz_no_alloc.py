@@ -80,7 +80,7 @@ def test_noalloc_then_steps_back_to_back(gpu_lib):
     fe = gpu_lib
     lib = fe.load()
     wl = fi.workload("tet-mr", a=3, b=4, c=9)
-    kw = dict(precision=1, refactor_every=2, factor_lag=1)
+    kw = dict(precision=1, refactor_every=2, factor_lag=1, spmv_variant=4)
     ref = fe.FEContext.from_workload(wl, **kw)
     ctx = fe.FEContext.from_workload(wl, **kw)
     q_ref, q = np.empty(ref.n), np.empty(ctx.n)
@@ -118,7 +118,7 @@ def test_noalloc_wait_timeout_is_reported_by_the_next_step(gpu_lib):
     fe = gpu_lib
     lib = fe.load()
     wl = fi.workload("tet-mr", a=3, b=4, c=9)
-    kw = dict(precision=1, refactor_every=1, dep_wait_s=0.02)
+    kw = dict(precision=1, refactor_every=1, dep_wait_s=0.02, spmv_variant=4)
     ref = fe.FEContext.from_workload(wl, **kw)
     ctx = fe.FEContext.from_workload(wl, **kw)
     q_ref, q = np.empty(ref.n), np.empty(ctx.n)
