@@ -409,12 +409,67 @@ def run_batch(args, world, rank, local, torch, dist):
 # --------------------------------------------------------------------- ours
 
 def _ctx_for(fe, wl, args, **kw):
-    kw.setdefault("use_graph", 1 if args.graph else 0)
-    return fe.FEContext.from_workload(wl, nd_leaf_nodes=args.nd_leaf,
-                                      factor_tf32=1 if args.factor_tf32 else 0,
-                                      precond_fp16=args.precond_fp16 if wl.precision else 0,
-                                      factor_lag=args.lag, element_fp64=1 if args.element_fp64 else 0,
-                                      warm_start=args.warm, **kw)
+    """The workload's context with the bench's options (kw overrides them)."""
+    opts = dict(nd_leaf_nodes=args.nd_leaf, use_graph=1 if args.graph else 0,
+                factor_tf32=1 if args.factor_tf32 else 0,
+                precond_fp16=args.precond_fp16 if wl.precision else 0,
+                factor_lag=args.lag, element_fp64=1 if args.element_fp64 else 0,
+                warm_start=args.warm, apply_sm_share=args.apply_share)
+    opts.update(kw)
+    return fe.FEContext.from_workload(wl, **opts)
+
+
+def oracle_position_error(fe, args, **kw):
+    """Positions after 10 steps from rest of the bench workload in the given
+    configuration against the FP64 oracle's rollout of the same steps
+    (tests/golden/tet30x30x120_mr_rollout.json, written by the oracle), on the
+    stored DOF sample, relative to the oracle's displacement there."""
+    import fe_inputs as fi
+    path = os.path.join(ROOT, "tests", "golden", "tet30x30x120_mr_rollout.json")
+    with open(path) as f:
+        g = json.load(f)
+    wl = fi.workload(g["workload"])
+    ctx = _ctx_for(fe, wl, args, use_graph=0, **kw)
+    q = np.empty(ctx.n)
+    for t in range(g["steps"]):
+        ctx.step(wl.p(t).reshape(-1), q, None)
+    ctx.close()
+    S = np.asarray(g["dofs"])
+    X = wl.mesh.X.reshape(-1)[S]
+    qo = np.asarray(g["q"])
+    return float(np.linalg.norm(q[S] - qo) / np.linalg.norm(qo - X))
+
+
+def measure_variant(fe, torch, wl_name, args, steps, warmup, **kw):
+    """steps/s of one more configuration (same timing as the headline: loads
+    in HBM, CUDA events around the steps on the caller's stream)."""
+    import fe_inputs as fi
+    wl = fi.workload(wl_name)
+    if "precision" in kw:
+        wl.precision = kw.pop("precision")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(priority=-1)
+    ctx = _ctx_for(fe, wl, args, device_ptrs=1, stream=stream.cuda_stream, **kw)
+    loads = torch.tensor(np.stack([wl.p(t).reshape(-1) for t in range(warmup + steps)]), dtype=torch.float64,
+                         device=dev)
+    q = torch.empty(ctx.n, dtype=torch.float64, device=dev)
+    its = []
+    with torch.cuda.stream(stream):
+        for t in range(warmup):
+            ctx.step(loads[t], q, None)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for t in range(warmup, warmup + steps):
+            its.append(ctx.step(loads[t], q, None).iters)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    ctx.close()
+    return {"value": steps / (ms / 1e3), "unit": "steps/s", "ms_per_step": ms / steps, "steps": steps,
+            "warmup": warmup, "mean_pcg_iters": float(np.mean(its)), "workload": wl_name,
+            "precision": "mixed" if wl.precision else "fp64",
+            "element_fp64": bool(kw.get("element_fp64", 0))}
 
 
 def _streaming_rooflines(wl, info, stage_ms, stage_calls, hbm, peak_kind, args, traffic):
@@ -473,6 +528,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP64-tangent and hex mixed-vs-FP64 measurements")
     ap.add_argument("--lag", type=int, default=1,
                     help="factor_lag k: the factor of A_s first preconditions step s+k")
     ap.add_argument("--element-fp64", action="store_true",
@@ -484,6 +541,8 @@ def main():
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: each step's solve and integration as one CUDA graph with device-side loops "
                          "(fe_options.use_graph); 0: host-driven PCG")
+    ap.add_argument("--apply-share", type=float, default=0.5,
+                    help="fraction of the application's CTA slots left to an in-flight factorisation")
     ap.add_argument("--warm", type=int, default=0, choices=[0, 1],
                     help="1: each step's PCG starts from the previous step's acceleration (fe_options.warm_start)")
     ap.add_argument("--nd-leaf", type=int, default=0,
@@ -658,6 +717,7 @@ def main():
                    "l2": "inputs larger than L2 (apply operators %.2f GB)" % (info["y_nnz"] * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single", "nd_leaf_nodes": args.nd_leaf or 64,
                    "pcg_graph": bool(args.graph), "warm_start": bool(args.warm),
+                   "apply_sm_share": args.apply_share,
                    "factor_tf32": bool(args.factor_tf32),
                    "precond_fp16": bool(wl.precision and args.precond_fp16),
                    "mean_pcg_iters": float(np.mean(iters)), "pcg_iters": iters, "factor_ages": ages,
@@ -672,6 +732,19 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
     }
+    if rank == 0 and not args.no_variants and args.workload == WORKLOAD and wl.precision and not args.element_fp64:
+        # the same workload with FP64 element tangents: the configuration whose
+        # positions follow the FP64 oracle to 1e-8; both configurations' error
+        # after 10 steps against the oracle's stored rollout is measured here
+        out["oracle_matching"] = measure_variant(fe, torch, WORKLOAD, args, K, W, element_fp64=1)
+        out["oracle_matching"]["position_error_10_steps"] = oracle_position_error(fe, args, element_fp64=1)
+        out["config"]["position_error_10_steps"] = oracle_position_error(fe, args)
+        # the hex beam (107,163 DOF, neo-Hookean): mixed with FP64 tangents vs
+        # FP64, both refined to 1e-8 on the FP64 system (equal accuracy)
+        mixed = measure_variant(fe, torch, "hex20x20x80-nh", args, 20, 5, precision=1, element_fp64=1)
+        fp64 = measure_variant(fe, torch, "hex20x20x80-nh", args, 10, 3, precision=0)
+        out["mixed_vs_fp64_hex20x20x80"] = {"mixed_fp64_tangents": mixed, "fp64": fp64,
+                                            "speedup": mixed["value"] / fp64["value"]}
     if rank == 0 and not args.no_adjoint and args.workload == WORKLOAD:
         out["adjoint"] = measure_adjoint(fe, torch)
     if rank == 0 and not args.no_batch and args.workload == WORKLOAD:

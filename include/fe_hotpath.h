@@ -174,13 +174,20 @@ typedef struct {
                              Single meshes; batches start from 0.            */
   int32_t spmv_variant;   /* -1 (default): the first solve times the SpMV
                              variants on the assembled matrix and keeps the
-                             fastest (batches: lanes per node for each size
-                             class).  0-3: the node-block kernel with 4, 8,
-                             16 or 32 lanes per node; 4, 5: CSR with 8 or 16
-                             threads per row (batches use 16 lanes for 4 and
-                             5).  Variants sum each row in a different order,
-                             so runs that must agree bit for bit across
-                             contexts fix one.                               */
+                             fastest (batches: one kernel per size class).
+                             0-3: the node-block kernel with 4, 8, 16 or 32
+                             lanes per node; 4, 5: CSR with 8 or 16 threads
+                             per row (for batches: every size class uses
+                             that kernel).  Variants sum each row in a
+                             different order, so runs that must agree bit
+                             for bit across contexts fix one.                */
+  double apply_sm_share;  /* 0 (default) to 0.9: while a lagged factorisation
+                             is in flight, the preconditioner application's
+                             persistent kernels launch this fraction fewer
+                             CTAs, leaving room on the SMs for the factor's
+                             kernels (the application is bound by its tree's
+                             dependency chains more than by its CTA count).
+                             The result does not depend on it.               */
 } fe_options;
 
 typedef struct {

@@ -31,7 +31,7 @@ class FeOptions(ct.Structure):
                 ("newton_tol", ct.c_double), ("factor_tf32", ct.c_int32),
                 ("precond_fp16", ct.c_int32), ("contact_sweeps", ct.c_int32), ("contact_tol", ct.c_double),
                 ("factor_lag", ct.c_int32), ("dep_wait_s", ct.c_double), ("element_fp64", ct.c_int32),
-                ("warm_start", ct.c_int32), ("spmv_variant", ct.c_int32)]
+                ("warm_start", ct.c_int32), ("spmv_variant", ct.c_int32), ("apply_sm_share", ct.c_double)]
 
 
 class FeStepInfo(ct.Structure):

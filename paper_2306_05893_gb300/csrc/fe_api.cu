@@ -725,7 +725,10 @@ static int solve_integrate_graph(fe_ctx *c, fe_step_info *info) {
   const bool batch = c->nseg > 1;
   if (batch) FE_TRY(tune_batch_spmv(c, d));
   else FE_TRY(tune_spmv(c, d));
-  DeviceState::StepGraph &sg = d->step_graph[d->cur];
+  // the application kernels' grids depend on whether a factorisation is in
+  // flight (apply_sm_share): one graph per (factor buffer, in flight)
+  const int gi = 2 * d->cur + ((d->factor_pending >= 0 && c->opt.apply_sm_share > 0.0) ? 1 : 0);
+  DeviceState::StepGraph &sg = d->step_graph[gi];
   if (!sg.exec || sg.cur != d->cur) FE_TRY(batch ? build_batch_graph(c, &sg) : build_step_graph(c, &sg));
   launch_pending_hold(d, d->stream);
   {

@@ -187,11 +187,42 @@ __global__ void __launch_bounds__(256) batch_bspmv_kernel(const int2 *__restrict
   }
 }
 
+// CSR SpMV over the same row blocks: the rows [3 n0, 3 n1) of each node
+// range, TPR threads per row (warp-uniform loop bound).
+template <typename TA, typename TV, int TPR, int MODE>
+__global__ void __launch_bounds__(256) batch_csr_kernel(const int2 *__restrict__ blocks,
+                                                        const int32_t *__restrict__ rowptr,
+                                                        const int32_t *__restrict__ colind, const TA *__restrict__ A,
+                                                        const TV *__restrict__ x, const double *__restrict__ b,
+                                                        TV *__restrict__ y) {
+  const int2 blk = blocks[blockIdx.x];
+  const int64_t rb = 3 * int64_t(blk.x), re = 3 * int64_t(blk.y);
+  const int sub = threadIdx.x % TPR;
+  for (int64_t r0 = rb + int64_t(threadIdx.x / 32) * (32 / TPR); r0 < re; r0 += 256 / TPR) {
+    const int64_t row = r0 + (threadIdx.x % 32) / TPR;
+    TV acc = TV(0);
+    if (row < re) {
+      const int32_t k1 = rowptr[row + 1];
+      for (int32_t k = rowptr[row] + sub; k < k1; k += TPR) acc += TV(A[k]) * x[colind[k]];
+    }
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
+    if (sub == 0 && row < re) y[row] = MODE == 0 ? acc : TV(b[row] - double(acc));
+  }
+}
+
 template <typename TA, typename TV, int MODE>
 void launch_class(const DeviceState::SpmvClass &k, const DeviceState *d, const TA *A, const TV *x, const double *b,
                   TV *y, cudaStream_t s) {
   if (!k.nblocks) return;
   const unsigned g = unsigned(k.nblocks);
+  if (k.lpn < 0) {  // CSR, -lpn threads per row
+    if (k.lpn == -16)
+      batch_csr_kernel<TA, TV, 16, MODE><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->colind, A, x, b, y);
+    else
+      batch_csr_kernel<TA, TV, 8, MODE><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->colind, A, x, b, y);
+    return;
+  }
   switch (k.lpn) {
     case 4:
       batch_bspmv_kernel<TA, TV, 4, MODE><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->bptr, d->bcol, d->fixed_row, A, x, b, y);
@@ -319,9 +350,10 @@ void launch_seg_cond(const fe_ctx *c, const DeviceState *d, cudaGraphConditional
   seg_cond_kernel<<<1, 256, 0, s>>>(h, d->bscal, d->scal, c->nseg, mode, double(c->opt.max_iters), d->flags);
 }
 
-// Size classes and row blocks of the batched SpMV, then each class's lanes
-// per node from {4, 8, 16, 32} by timing its own row blocks on the assembled
-// matrix (CUDA events, 3 runs each, the median).  Members are ordered by
+// Size classes and row blocks of the batched SpMV, then each class's kernel
+// by timing its own row blocks on the assembled matrix (CUDA events, one
+// untimed run then the median of five): the node-block kernel with 4, 8, 16
+// or 32 lanes per node, or CSR with 8 or 16 threads per row.  Members are ordered by
 // their mean blocks per free node and cut into at most three classes of
 // about equal node counts: longer rows want more lanes per node.
 int tune_batch_spmv(fe_ctx *c, DeviceState *d) {
@@ -373,16 +405,16 @@ int tune_batch_spmv(fe_ctx *c, DeviceState *d) {
   const int fixed = c->opt.spmv_variant;
   for (auto &cl : d->spmv_classes) {
     if (fixed >= 0) {  // fixed by the caller: no timing
-      cl.lpn = fixed <= 3 ? (4 << fixed) : 16;
+      cl.lpn = fixed <= 3 ? (4 << fixed) : (fixed == 4 ? -8 : -16);
       continue;
     }
     if (er != cudaSuccess || !cl.nblocks) continue;
     float best = 1e30f;
     int best_lpn = 16;
-    for (int lpn : {4, 8, 16, 32}) {
+    for (int lpn : {4, 8, 16, 32, -8, -16}) {  // node-block lanes per node, or CSR threads per row
       cl.lpn = lpn;
-      float t[3] = {0.f, 0.f, 0.f};
-      for (int rep = 0; rep < 3 && er == cudaSuccess; ++rep) {
+      float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int rep = 0; rep < 6 && er == cudaSuccess; ++rep) {  // one untimed run, five timed
         er = cudaEventRecord(e0, d->stream);
         if (er == cudaSuccess) run_class(c, d, cl, fp32, d->vp, d->vq, nullptr, d->stream);
         if (er == cudaSuccess) er = cudaGetLastError();
@@ -390,9 +422,9 @@ int tune_batch_spmv(fe_ctx *c, DeviceState *d) {
         if (er == cudaSuccess) er = cudaEventSynchronize(e1);
         if (er == cudaSuccess) er = cudaEventElapsedTime(&t[rep], e0, e1);
       }
-      std::sort(t, t + 3);
-      if (er == cudaSuccess && t[1] < best) {
-        best = t[1];
+      std::sort(t + 1, t + 6);
+      if (er == cudaSuccess && t[3] < best) {
+        best = t[3];
         best_lpn = lpn;
       }
     }

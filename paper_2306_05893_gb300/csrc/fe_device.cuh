@@ -142,7 +142,7 @@ struct DeviceState {
     cudaGraphExec_t exec = nullptr;
     int64_t k_pro = 0, k_inner = 0, k_outer = 0;
   };
-  StepGraph step_graph[2];
+  StepGraph step_graph[4];         // [2 * cur + (a factorisation in flight)]
   void *part_f = nullptr, *part_b = nullptr;                // partial sums of split apply tasks
   int *tick_f = nullptr, *tick_b = nullptr;                 // their tickets (zero between launches)
   // dataflow application: task lists, per-front counters (forward: children
@@ -189,9 +189,10 @@ struct DeviceState {
   // batched SpMV schedule (fe_batch.cu): members grouped into size classes
   // by their mean 3x3 blocks per node; each class is a table of row blocks
   // (node ranges of at most kBatchBlockNodes nodes inside one member) and
-  // has its own lanes per node, chosen by timing the candidates
+  // has its own kernel (node-block lanes per node or CSR threads per row),
+  // chosen by timing the candidates
   struct SpmvClass {
-    int lpn = 16;
+    int lpn = 16;                  // node-block lanes per node, or -(CSR threads per row)
     int2 *blocks = nullptr;
     int64_t nblocks = 0;
     std::vector<int32_t> members;

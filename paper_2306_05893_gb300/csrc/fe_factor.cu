@@ -1736,8 +1736,14 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device);
-  const unsigned gf = unsigned(std::max<int64_t>(1, std::min<int64_t>(d->n_apply_fwd, int64_t(sms) * std::max(1, per_sm[0]))));
-  const unsigned gb = unsigned(std::max<int64_t>(1, std::min<int64_t>(d->n_apply_bwd, int64_t(sms) * std::max(1, per_sm[1]))));
+  // while a lagged factorisation is in flight, leave apply_sm_share of the
+  // CTA slots to its kernels (tasks are taken from a queue in topological
+  // order, so any grid size gives the same result)
+  const double keep = d->factor_pending >= 0 ? 1.0 - c->opt.apply_sm_share : 1.0;
+  const int64_t slots_f = std::max<int64_t>(1, int64_t(double(int64_t(sms) * std::max(1, per_sm[0])) * keep));
+  const int64_t slots_b = std::max<int64_t>(1, int64_t(double(int64_t(sms) * std::max(1, per_sm[1])) * keep));
+  const unsigned gf = unsigned(std::max<int64_t>(1, std::min<int64_t>(d->n_apply_fwd, slots_f)));
+  const unsigned gb = unsigned(std::max<int64_t>(1, std::min<int64_t>(d->n_apply_bwd, slots_b)));
   {
     // a pending test hold applies to the next application that runs, never
     // to one captured into a graph (the whole-step graph applies it before

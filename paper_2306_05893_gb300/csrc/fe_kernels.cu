@@ -940,9 +940,9 @@ void launch_residual(const fe_ctx *c, const DeviceState *d, bool, cudaStream_t s
   launch_spmv_variant<double, double, 1>(c, d, d->res_var, d->A64, d->x, d->r, d->b, d->scal, d->flags, s);
 }
 
-// Times every variant of both products (CUDA events on the main stream, 3
-// runs each, the median) on the assembled matrix; the timing runs write
-// their scalars and flags to scratch words, not the solve's.
+// Times every variant of both products (CUDA events on the main stream, one
+// untimed run then the median of five) on the assembled matrix; the timing
+// runs write their scalars and flags to scratch words, not the solve's.
 int tune_spmv(fe_ctx *c, DeviceState *d) {
   if (d->spmv_var >= 0) return FE_OK;
   if (c->opt.spmv_variant >= 0) {  // fixed by the caller
@@ -959,8 +959,9 @@ int tune_spmv(fe_ctx *c, DeviceState *d) {
   for (int prod = 0; prod < 2 && er == cudaSuccess; ++prod) {
     float bt = 1e30f;
     for (int var = 0; var < kSpmvVariants && er == cudaSuccess; ++var) {
-      float t[3] = {0.f, 0.f, 0.f};
-      for (int rep = 0; rep < 3 && er == cudaSuccess; ++rep) {
+      // one untimed run (caches, first-launch costs), then five timed ones
+      float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int rep = 0; rep < 6 && er == cudaSuccess; ++rep) {
         er = cudaMemsetAsync(ts, 0, S_COUNT * sizeof(double) + 4 * sizeof(int), d->stream);
         if (er == cudaSuccess) er = cudaEventRecord(e0, d->stream);
         if (er == cudaSuccess) {
@@ -974,9 +975,9 @@ int tune_spmv(fe_ctx *c, DeviceState *d) {
         if (er == cudaSuccess) er = cudaEventSynchronize(e1);
         if (er == cudaSuccess) er = cudaEventElapsedTime(&t[rep], e0, e1);
       }
-      std::sort(t, t + 3);
-      if (er == cudaSuccess && t[1] < bt) {
-        bt = t[1];
+      std::sort(t + 1, t + 6);
+      if (er == cudaSuccess && t[3] < bt) {  // the median of the timed runs
+        bt = t[3];
         best[prod] = var;
       }
     }

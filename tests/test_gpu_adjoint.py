@@ -96,8 +96,9 @@ def test_adjoint_mixed_precision(gpu_lib):
     m = O.Model(mesh.elem_type, mesh.X, mesh.conn, mesh.fixed_nodes, fi.NEOHOOKE,
                 E[:, None] * base[None, :], 1000.0, 0.01, 0.1, 0.01)
     _, so, po = O.adjoint_rollout(m, q0, np.zeros_like(q0), lambda t: loads[t], loads.shape[0], qt)
-    assert np.linalg.norm(ds - so) <= 1e-3 * np.linalg.norm(so)
-    assert np.linalg.norm(dp - po) <= 1e-3 * np.linalg.norm(po)
+    es, ep = np.linalg.norm(ds - so) / np.linalg.norm(so), np.linalg.norm(dp - po) / np.linalg.norm(po)
+    print(f"mixed adjoint: dL/ds error {es:.2e}, dL/dp error {ep:.2e}")
+    assert es <= 1e-3 and ep <= 1e-3
     ctx.close()
 
 

@@ -37,20 +37,24 @@ def test_contact_rollout_matches_oracle(gpu_lib, precision, tol):
     ctx.set_contacts(nodes, normals, offsets)
     qg, vg = np.empty_like(q), np.empty_like(q)
     active = 0
+    worst = [0.0, 0.0]
     for t in range(5):
         ctx.step(p, qg, vg)
         lam_g = ctx.contact_forces()
         q, v, _, lam, _ = m.contact_step(q, v, p, nodes, normals, offsets)
         active = max(active, int((lam > 0).sum()))
         scale = max(np.abs(lam).max(), 1e-30)
+        worst[0] = max(worst[0], np.abs(lam_g - lam).max() / scale)
         assert np.abs(lam_g - lam).max() <= tol * scale, (t, np.abs(lam_g - lam).max(), scale)
         disp = np.abs(q - mesh.X.reshape(-1)).max()
+        worst[1] = max(worst[1], np.abs(qg - q).max() / disp)
         assert np.abs(qg - q).max() <= tol * disp
         if precision == 0:
             gap = qg.reshape(-1, 3)[nodes, 2] - offsets
             assert gap.min() >= -1e-9 * 0.002
             assert lam_g.min() >= 0.0
     assert active >= 1
+    print(f"contact precision={precision}: worst multiplier error {worst[0]:.2e}, position error {worst[1]:.2e}")
     ctx.close()
 
 

@@ -37,13 +37,16 @@ def test_newton_steps_match_oracle(gpu_lib, beta, precision, tol):
     q = mesh.X.reshape(-1).copy()
     v = np.zeros_like(q)
     qg, vg = np.empty_like(q), np.empty_like(q)
+    worst = 0.0
     for t in range(3):
         info = ctx.step(p, qg, vg)
         q, v, a, corr = m.newton_step(q, v, p, iters)
         assert info.newton == iters
         disp = np.abs(q - mesh.X.reshape(-1)).max()
+        worst = max(worst, np.abs(qg - q).max() / disp)
         assert np.abs(qg - q).max() <= tol * disp
         assert np.abs(vg - v).max() <= tol * np.abs(v).max()
+    print(f"Newton beta={beta} precision={precision}: worst position error {worst:.2e}")
     if beta == 0.0 and precision == 0:
         assert info.newton_correction <= 1e-9
     ctx.close()
