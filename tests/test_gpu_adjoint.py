@@ -2,7 +2,7 @@
 against central finite differences of the GPU rollout (reading C-13:
 eps = 1e-6 relative, solves at tol 1e-13, so FD noise stays < 1e-5).
 Tolerances: FP64 gradients <= 1e-8 relative to the oracle's (norm); mixed
-path <= 1e-3 (FP32 tangent and dual-number pass)."""
+path <= 1e-5 (FP32 tangent and dual-number pass; measured 1.6e-6)."""
 import numpy as np
 import pytest
 
@@ -98,7 +98,7 @@ def test_adjoint_mixed_precision(gpu_lib):
     _, so, po = O.adjoint_rollout(m, q0, np.zeros_like(q0), lambda t: loads[t], loads.shape[0], qt)
     es, ep = np.linalg.norm(ds - so) / np.linalg.norm(so), np.linalg.norm(dp - po) / np.linalg.norm(po)
     print(f"mixed adjoint: dL/ds error {es:.2e}, dL/dp error {ep:.2e}")
-    assert es <= 1e-3 and ep <= 1e-3
+    assert es <= 1e-5 and ep <= 1e-5
     ctx.close()
 
 

@@ -2,7 +2,8 @@
 newton_step (direct solves), through the C ABI (fe_options.newton_iters).
 
 Tolerances relative to the displacement: FP64 path 1e-8 (PCG to 1e-12 with
-the exact factor), mixed path 1e-4 (FP32 tangent and factor, FP64 residual).
+the exact factor), mixed path 2e-6 (FP32 tangent and factor, FP64 forces and
+residual; measured 3e-7 with stiffness damping, 2e-11 without).
 """
 import numpy as np
 import pytest
@@ -24,7 +25,7 @@ def _case(beta, g_scale=5.0):
 
 
 @pytest.mark.parametrize("beta", [0.0, 0.01])
-@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-4)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 2e-6)])
 def test_newton_steps_match_oracle(gpu_lib, beta, precision, tol):
     # with stiffness damping the iteration leaves out dK in the damping term;
     # at 5 g its iterates oscillate through indefinite tangents (the oracle's

@@ -233,7 +233,8 @@ def test_rollout_with_tf32_factor(gpu_lib):
     assert all(i.rel_residual <= wl.tol for i in infos)
 
 
-def test_indefinite_matrix_is_reported(gpu_lib):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_indefinite_matrix_is_reported(gpu_lib, precision):
     """A random 5%-of-spacing jitter makes the neo-Hookean tangent indefinite
     (the oracle's A has a negative eigenvalue there): the factor reports a
     non-positive pivot as FE_ERR_BREAKDOWN (reading C-6)."""
@@ -243,7 +244,7 @@ def test_indefinite_matrix_is_reported(gpu_lib):
                 LAWS[fi.NEOHOOKE], 1000., .01, .1, .01)
     Ao, _ = m.system(q, v, p)
     assert np.linalg.eigvalsh(Ao.toarray()).min() < 0
-    ctx = _ctx(gpu_lib, mesh, fi.NEOHOOKE, 0)
+    ctx = _ctx(gpu_lib, mesh, fi.NEOHOOKE, precision)
     ctx.set_state(q, v)
     ctx.assemble(p)
     with pytest.raises(gpu_lib.FEError) as ei:
