@@ -268,29 +268,46 @@ __device__ __forceinline__ double pivot_inverse(double d, int *flags, bool repor
   return 1.0 / d;
 }
 
-// Task (front, k0, kb): LDL^T of the kb x kb diagonal block.  The eliminations
-// run in the factor's type TF with the pivots of the running Schur
-// complement in TF; the pivots D are accumulated beside them from the final
-// (unscaled) columns in FP64 (FP64 factor) or double-float (FP32 factor),
-// d_i = a_ii - sum_j F_ij^2 / d_j, by a ninth warp (lane l: rows l and
-// l + 32), and stored in FP64 with their inverses, which also scale the
-// stored L.  The same row operations applied to the identity give L_KK^{-1}
-// (Gauss-Jordan), written into Y[K, K]; L goes back into F.
-//
-// Warps 0-7 hold the block in registers: thread (tr, tc) = (tid / 16,
-// tid % 16) owns rows tr + 16a and columns tc + 16b (a, b < 4).  An entry
-// (i, c) holds L_ic until its column is final (after step c - 1), is then
-// saved and restarts as the Gauss-Jordan entry Xi_ic, so one register and one
-// FMA per entry and step serve both.  At step j the pivot column F_:j, its
-// pivot's reciprocal and the Gauss-Jordan row Xi_j: come from
-// double-buffered shared vectors written by their owners at step j - 1: one
-// barrier per pivot among warps 0-7 (named barrier 1), and no FP64 or
-// double-float work gates the next step (GB300's FP64 pipe issues a warp
-// instruction only every ~64 cycles per SM sub-partition).  The ninth warp
-// does not join that barrier: it follows the final columns as they land in
-// Ls through a progress word (release after the barrier, acquire before the
-// read), so its pivot chain overlaps the elimination.
+// Task (front, k0, kb): LDL^T of the kb x kb diagonal block (kb <= 64),
+// blocked in 16-pivot sub-blocks so that the serial chain of a sub-block runs
+// inside one warp and the eight elimination warps meet at three barriers per
+// sub-block instead of one per pivot.  For sub-block b (columns
+// B = [16b, 16b + 16)):
+//  A. one warp factors the 16 x 16 diagonal sub-block (lane l keeps row 16b + l
+//     in registers; each pivot and column reaches the lanes by shuffles);
+//  B. one thread per row below solves the sub-block's columns,
+//     W[i, B] = S[i, B] L_BB^{-T} (forward substitution);
+//  C. all eight warps apply the rank-16 update S[I, J] -= L[I, B] W[J, B]^T
+//     to the sub-blocks below and right of b (thread (tr, tc): rows
+//     tr + 16a, columns tc + 16c).
+// The eliminations run in TF with the pivots of the running Schur complement
+// in TF; S ends holding the final unscaled columns W = L d and Lsc the
+// scaled L.  The pivots D are accumulated beside them from the final columns
+// in FP64 (FP64 factor) or double-float (FP32 factor),
+// d_i = a_ii - sum_j W_ij^2 / d_j, by a ninth warp that follows the
+// sub-blocks as they are published (thread 0 releases a progress word after
+// the barrier that ends step B, the warp acquires it): per sub-block the
+// squares of its 16 columns are formed up front, then 16 steps each take a
+// pivot's inverse and fold its column into every later row at once (lane l:
+// rows l and l + 32), so only the pivots' recurrence is serial.  The FP32
+// elimination takes the fast reciprocal of its own pivots; the stored L is
+// W times the inverses of the pivot warp's pivots.  L_KK^{-1} (written into
+// Y[K, K]) is formed after the elimination by blocked inversion of the unit
+// lower L: the diagonal
+// 16 x 16 inverses by one warp each, then, one block diagonal at a time,
+// X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj.  GB300's FP64 pipe issues a warp
+// instruction only every ~64 cycles per SM sub-partition, so no FP64 or
+// double-float work sits on the elimination's chain.
 constexpr int kDiagThreads = 288;
+constexpr int kDP = 65;  // row pitch of the 64 x 64 shared arrays (conflict-free columns)
+
+// S, Lsc, X (64 x kDP each), T (3 x 16 x 17), the TF pivot inverses (64),
+// then the FP64 / double-float pivots and their inverses (64 doubles each)
+template <typename TF>
+constexpr size_t diag_smem() {
+  return size_t(3 * 64 * kDP + 3 * 16 * 17 + 64) * sizeof(TF) + 2 * 64 * sizeof(double);
+}
+static_assert((3 * 64 * kDP + 3 * 16 * 17 + 64) % 2 == 0, "the pivot arrays stay 8-byte aligned");
 
 // block-scope acquire / release on a shared word (the pivot warp follows the
 // elimination's progress without joining its barriers)
@@ -307,6 +324,7 @@ __device__ __forceinline__ void st_release_cta_shared(int *p, int v) {
                "r"(v)
                : "memory");
 }
+__device__ __forceinline__ void elim_barrier() { asm volatile("bar.sync 1, 256;\n" ::: "memory"); }
 
 template <typename TF>
 __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t *__restrict__ tasks,
@@ -315,19 +333,23 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
                                                                   double *__restrict__ D,
                                                                   double *__restrict__ Dinv, int *flags) {
   constexpr bool kDF = sizeof(TF) == 4;
+  constexpr unsigned kAll = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char dsm_raw[];
-  double *dg = reinterpret_cast<double *>(dsm_raw);  // [64] FP64 pivots, or [64] DF pivots
-  DF *dgf = reinterpret_cast<DF *>(dsm_raw);
-  TF(*Ls)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double));  // input, then final L (unscaled)
-  TF(*Xs)[65] = reinterpret_cast<TF(*)[65]>(dsm_raw + 64 * sizeof(double) + 64 * 65 * sizeof(TF));
-  __shared__ TF colb[2][64], xrow[2][64], pinv[2];
-  __shared__ double s_inv[64];  // FP64 inverses, or DF inverses in the same bytes
-  __shared__ int s_done;        // columns [0, s_done] of Ls hold their final values
+  TF(*S)[kDP] = reinterpret_cast<TF(*)[kDP]>(dsm_raw);  // input, then W (lower) and the TF pivots
+  TF(*Lsc)[kDP] = S + 64;                               // L = W / d (TF pivots), strictly lower
+  TF(*X)[kDP] = S + 128;                                // L^{-1}, lower blocks
+  TF(*T)[16][17] = reinterpret_cast<TF(*)[16][17]>(S + 192);
+  TF *pinv = reinterpret_cast<TF *>(T + 3);
+  double *dg = reinterpret_cast<double *>(pinv + 64);  // [64] FP64 pivots, or DF pivots
+  double *s_inv = dg + 64;                             // [64] FP64 inverses, or DF inverses
+  DF *dgf = reinterpret_cast<DF *>(dg);
   DF *s_invf = reinterpret_cast<DF *>(s_inv);
+  __shared__ int s_done;  // columns [0, s_done) of S hold their final values
   pdl_launch_dependents();
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int32_t k0 = t.y & 0xffffff, kb = t.z;
+  const int nsb = (kb + 15) >> 4, n16 = 16 * nsb;
   TF *Ff = F + fr.f_off;
   pdl_wait();
   {  // all of a thread's loads of the block in flight before its stores
@@ -341,53 +363,41 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const int idx = threadIdx.x + k * kDiagThreads;
-      if (idx < 64 * 64) Ls[idx % 64][idx / 64] = v[k];
+      if (idx < 64 * 64) S[idx % 64][idx / 64] = v[k];
+      if (idx < 64 * 64 && idx % 64 == idx / 64) dg[idx % 64] = double(v[k]);  // the pivot warp's start
     }
   }
+  if (threadIdx.x == 0) s_done = 0;
   __syncthreads();
-  auto safe_inv = [](TF d) { return d > TF(0) ? TF(1) / d : TF(1); };
-  const bool pivot_warp = threadIdx.x >= 256;
-  const int lane = threadIdx.x & 31;
-  const int tr = (threadIdx.x & 255) >> 4, tc = threadIdx.x & 15;
-  TF R[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = tr + 16 * a, c = tc + 16 * b;
-      // column 0 is final from the start: it restarts as Xi at once
-      R[a][b] = (c == 0 && i > 0) ? TF(0) : Ls[i][c];
-    }
-  if (threadIdx.x < 64) {
-    colb[0][threadIdx.x] = Ls[threadIdx.x][0];
-    xrow[0][threadIdx.x] = threadIdx.x == 0 ? TF(1) : TF(0);
-  }
-  if (threadIdx.x == 0) {
-    pinv[0] = safe_inv(Ls[0][0]);
-    s_done = 0;
-  }
-  // pivot warp: lane l keeps rows l and l + 32 in FP64 / double-float
-  DF p0 = {1.f, 0.f}, p1 = {1.f, 0.f};
-  double q0 = 1.0, q1 = 1.0;
-  if (pivot_warp) {
+  // the elimination's own pivots (the stored D comes from the pivot warp):
+  // the fast reciprocal for FP32
+  auto safe_inv = [](TF d) {
+    if constexpr (sizeof(TF) == 4)
+      return d > TF(0) ? __fdividef(1.f, d) : TF(1);
+    else
+      return d > TF(0) ? TF(1) / d : TF(1);
+  };
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the pivot warp is warp 1, so that it shares no SM sub-partition with
+  // warp 0, which runs the elimination's serial step A
+  if (warp == 1) {
+    // ------------------------------------------------------- pivot warp
+    // lane l keeps rows l and l + 32 in double-float (FP32 factor) or FP64
+    DF p0 = {1.f, 0.f}, p1 = {1.f, 0.f};
+    double q0 = 1.0, q1 = 1.0;
+    // (from the copy of the input diagonal: the elimination overwrites S's)
     if constexpr (kDF) {
-      p0 = {lane < kb ? float(Ls[lane][lane]) : 1.f, 0.f};
-      p1 = {lane + 32 < kb ? float(Ls[lane + 32][lane + 32]) : 1.f, 0.f};
+      if (lane < kb) p0 = {float(dg[lane]), 0.f};
+      if (lane + 32 < kb) p1 = {float(dg[lane + 32]), 0.f};
     } else {
-      q0 = lane < kb ? double(Ls[lane][lane]) : 1.0;
-      q1 = lane + 32 < kb ? double(Ls[lane + 32][lane + 32]) : 1.0;
+      if (lane < kb) q0 = dg[lane];
+      if (lane + 32 < kb) q1 = dg[lane + 32];
     }
-  }
-  __syncthreads();
-  if (pivot_warp) {
-    // fold column j (final, unscaled) into the pivots of rows > j.  The
-    // elimination uses the FP32 pivots, so this chain runs beside it without
-    // joining its barriers: lane 0 waits (bounded) until column j is final
-    // in Ls, published by a release of s_done after the elimination's barrier.
-    for (int j = 0; j < kb; ++j) {
+    for (int sb = 0; sb < nsb; ++sb) {
+      const int b0 = 16 * sb, b1 = b0 + 16;
       int late = 0;
       if (lane == 0) {
-        for (int spins = 0; ld_acquire_cta_shared(&s_done) < j; ++spins)
+        for (int spins = 0; ld_acquire_cta_shared(&s_done) < b1; ++spins)
           if (spins > (1 << 24)) {
             atomicOr(flags, FLAG_WAIT_TIMEOUT);
             late = 1;
@@ -395,95 +405,183 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
           }
       }
       __syncwarp();
-      if (__shfl_sync(0xffffffffu, late, 0)) break;
+      if (__shfl_sync(kAll, late, 0)) break;
+      // the squares of the sub-block's final columns in both of the lane's
+      // rows, formed before the chain (only the pivots' own recurrence is
+      // serial: every row's update of a step is one SIMD instruction stream)
       const int i0 = lane, i1 = lane + 32;
-      const TF f0 = Ls[i0][j], f1 = Ls[i1][j];
       if constexpr (kDF) {
-        const float djh = __shfl_sync(0xffffffffu, j < 32 ? p0.hi : p1.hi, j & 31);
-        const float djl = __shfl_sync(0xffffffffu, j < 32 ? p0.lo : p1.lo, j & 31);
-        const DF inv = df_pivot_inverse({djh, djl}, flags, lane == (j & 31));
-        if (lane == (j & 31)) s_invf[j] = inv;
-        if (i0 > j && i0 < kb) p0 = df_sub(p0, df_mul(df_two_prod(float(f0), float(f0)), inv));
-        if (i1 > j && i1 < kb) p1 = df_sub(p1, df_mul(df_two_prod(float(f1), float(f1)), inv));
+        DF sq0[16], sq1[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const float w0 = float(S[i0][b0 + jj]), w1 = float(S[i1][b0 + jj]);
+          sq0[jj] = df_two_prod(w0, w0);
+          sq1[jj] = df_two_prod(w1, w1);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int j = b0 + jj;
+          if (j >= kb) break;
+          const float djh = __shfl_sync(kAll, j < 32 ? p0.hi : p1.hi, j & 31);
+          const float djl = __shfl_sync(kAll, j < 32 ? p0.lo : p1.lo, j & 31);
+          const DF inv = df_pivot_inverse({djh, djl}, flags, lane == 0);
+          if (lane == 0) s_invf[j] = inv;
+          const DF n0 = df_sub(p0, df_mul(sq0[jj], inv)), n1 = df_sub(p1, df_mul(sq1[jj], inv));
+          if (i0 > j && i0 < kb) p0 = n0;
+          if (i1 > j && i1 < kb) p1 = n1;
+        }
       } else {
-        const double dj = __shfl_sync(0xffffffffu, j < 32 ? q0 : q1, j & 31);
-        const double inv = pivot_inverse(dj, flags, lane == (j & 31));
-        if (lane == (j & 31)) s_inv[j] = inv;
-        if (i0 > j && i0 < kb) q0 -= double(f0) * double(f0) * inv;
-        if (i1 > j && i1 < kb) q1 -= double(f1) * double(f1) * inv;
-      }
-    }
-  } else {
-    for (int j = 0; j < kb; ++j) {
-      const int cur = j & 1, nxt = cur ^ 1;
-      const TF tinv = pinv[cur];
-      TF lij[4], val[4];
+        double sq0[16], sq1[16];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = tr + 16 * a;
-        lij[a] = i > j ? colb[cur][i] * tinv : TF(0);
-      }
+        for (int jj = 0; jj < 16; ++jj) {
+          const double w0 = double(S[i0][b0 + jj]), w1 = double(S[i1][b0 + jj]);
+          sq0[jj] = w0 * w0;
+          sq1[jj] = w1 * w1;
+        }
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int c = tc + 16 * b;
-        val[b] = c > j ? colb[cur][c] : xrow[cur][c];  // L update right of j, Gauss-Jordan at or left of j
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) R[a][b] -= lij[a] * val[b];
-      // publish column j+1 (final now), its pivot's reciprocal, and row j+1 of Xi
-      const int jn = j + 1;
-      if (tc == (jn & 15)) {
-        const int bs = jn >> 4;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          if (b != bs) continue;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const int i = tr + 16 * a;
-            colb[nxt][i] = R[a][b];
-            if (i == jn) pinv[nxt] = safe_inv(R[a][b]);
-            if (i > jn) {
-              Ls[i][jn] = R[a][b];
-              R[a][b] = TF(0);  // restarts as Xi_{i, j+1}
-            }
-          }
+        for (int jj = 0; jj < 16; ++jj) {
+          const int j = b0 + jj;
+          if (j >= kb) break;
+          const double dj = __shfl_sync(kAll, j < 32 ? q0 : q1, j & 31);
+          const double inv = pivot_inverse(dj, flags, lane == 0);
+          if (lane == 0) s_inv[j] = inv;
+          if (i0 > j && i0 < kb) q0 -= sq0[jj] * inv;
+          if (i1 > j && i1 < kb) q1 -= sq1[jj] * inv;
         }
       }
-      if (tr == (jn & 15)) {
-        const int as = jn >> 4;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          if (a != as) continue;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int c = tc + 16 * b;
-            xrow[nxt][c] = c < jn ? R[a][b] : (c == jn ? TF(1) : TF(0));
-          }
-        }
-      }
-      // the eight elimination warps only (named barrier 1)
-      asm volatile("bar.sync 1, 256;\n" ::: "memory");
-      if (threadIdx.x == 0) st_release_cta_shared(&s_done, jn);  // column j+1 is in Ls
     }
-  }
-  __syncthreads();
-  if (!pivot_warp) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = tr + 16 * a, c = tc + 16 * b;
-        Xs[i][c] = i > c ? R[a][b] : (i == c ? TF(1) : TF(0));
-      }
-  } else {
     if constexpr (kDF) {
       dgf[lane] = p0;
       dgf[lane + 32] = p1;
     } else {
       dg[lane] = q0;
       dg[lane + 32] = q1;
+    }
+  } else {
+    // ------------------------------------------------ elimination warps
+    const int ew = warp == 0 ? 0 : warp - 1;  // 0-7
+    const int tid = 32 * ew + lane;
+    for (int sb = 0; sb < nsb; ++sb) {
+      const int b0 = 16 * sb, b1 = b0 + 16;
+      if (ew == 0) {
+        // A: the 16 x 16 diagonal sub-block (lanes 16-31 mirror 0-15)
+        const int l = lane & 15, row = b0 + l;
+        const bool own = lane < 16;
+        TF r[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) r[c] = S[row][b0 + c];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          // column j reaches the lanes first (its entries are final), then
+          // the pivot's reciprocal, the row's L entry and the updates
+          TF wc[16];
+#pragma unroll
+          for (int c = 1; c < 16; ++c)  // (constant bounds: r stays in registers)
+            if (c > j) wc[c] = __shfl_sync(kAll, r[j], c);  // W[b0 + c, b0 + j]
+          const TF inv = safe_inv(__shfl_sync(kAll, r[j], j));
+          const TF lj = r[j] * inv;  // row's L entry (its W entry r[j] is final)
+#pragma unroll
+          for (int c = 1; c < 16; ++c)
+            if (c > j && l >= c) r[c] -= lj * wc[c];
+          if (own && l > j) {
+            S[row][b0 + j] = r[j];
+            Lsc[row][b0 + j] = lj;
+          }
+          if (own && l == j) {
+            S[row][row] = r[j];
+            pinv[row] = inv;
+          }
+        }
+      }
+      elim_barrier();
+      // B: the rows below, one thread per row
+      if (tid < n16 - b1) {
+        const int i = b1 + tid;
+        TF s[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) s[c] = S[i][b0 + c];
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+#pragma unroll
+          for (int c2 = 1; c2 < 16; ++c2)
+            if (c2 > c) s[c2] -= s[c] * Lsc[b0 + c2][b0 + c];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          S[i][b0 + c] = s[c];
+          Lsc[i][b0 + c] = s[c] * pinv[b0 + c];
+        }
+      }
+      elim_barrier();
+      if (tid == 0) st_release_cta_shared(&s_done, b1);  // columns < b1 are final in S
+      // C: rank-16 update of the sub-blocks below and right of sb
+      if (b1 < n16) {
+        const int tr = tid >> 4, tc = tid & 15;
+        TF acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            acc[a][c] = (c > sb && a >= c && a < nsb) ? S[tr + 16 * a][tc + 16 * c] : TF(0);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          TF li[4], wc[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            li[a] = (a > sb && a < nsb) ? Lsc[tr + 16 * a][b0 + j] : TF(0);
+            wc[a] = (a > sb && a < nsb) ? S[tc + 16 * a][b0 + j] : TF(0);
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (c <= a) acc[a][c] -= li[a] * wc[c];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (c > sb && a >= c && a < nsb) S[tr + 16 * a][tc + 16 * c] = acc[a][c];
+      }
+      elim_barrier();
+    }
+    // L^{-1}: the diagonal 16 x 16 inverses (warp w: block w, lane c: column c)
+    if (ew < nsb) {
+      const int w0 = 16 * ew, c = lane & 15;
+      TF x[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        TF acc = i == c ? TF(1) : TF(0);
+#pragma unroll
+        for (int k = 0; k < 15; ++k)
+          if (k < i) acc -= Lsc[w0 + i][w0 + k] * x[k];
+        x[i] = acc;
+      }
+      if (lane < 16) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) X[w0 + i][w0 + c] = x[i];
+      }
+    }
+    elim_barrier();
+    // then the blocks below the diagonal, one block diagonal o at a time
+    const int r = tid >> 4, c = tid & 15;
+    for (int o = 1; o < nsb; ++o) {
+      for (int bj = 0; bj + o < nsb; ++bj) {
+        const int bi = bj + o;
+        TF acc = TF(0);
+        for (int k = bj; k < bi; ++k)
+#pragma unroll
+          for (int m = 0; m < 16; ++m) acc += Lsc[16 * bi + r][16 * k + m] * X[16 * k + m][16 * bj + c];
+        T[bj][r][c] = acc;
+      }
+      elim_barrier();
+      for (int bj = 0; bj + o < nsb; ++bj) {
+        const int bi = bj + o;
+        TF acc = TF(0);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) acc += X[16 * bi + r][16 * bi + m] * T[bj][m][c];
+        X[16 * bi + r][16 * bj + c] = -acc;
+      }
+      elim_barrier();
     }
   }
   __syncthreads();
@@ -501,15 +599,16 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     Dinv[fr.first + k0 + threadIdx.x] = dinv;
   }
   TF *Yf = Y + fr.y_off;
-  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-    const int i = idx % kb, j = idx / kb;
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
+    const int i = idx & 63, j = idx >> 6;
+    if (i >= kb || j >= kb) continue;
     TF sc;
     if constexpr (kDF)
       sc = s_invf[j].hi;
     else
       sc = TF(s_inv[j]);
-    if (i > j) Ff[(k0 + i) + int64_t(k0 + j) * fr.ldf] = Ls[i][j] * sc;
-    Yf[(k0 + i) + int64_t(k0 + j) * fr.ldy] = Xs[i][j];
+    if (i > j) Ff[(k0 + i) + int64_t(k0 + j) * fr.ldf] = S[i][j] * sc;
+    Yf[(k0 + i) + int64_t(k0 + j) * fr.ldy] = i > j ? X[i][j] : (i == j ? TF(1) : TF(0));
   }
 }
 
@@ -1641,7 +1740,7 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
   const CUtensorMap *ymaps = fmaps ? fmaps + (1 + buf) * nf : nullptr;
   const CUtensorMap *ycmaps = fmaps ? fmaps + (3 + buf) * nf : nullptr;
   const size_t tsm = 2 * 64 * 65 * sizeof(TF);
-  const size_t dsm = 64 * sizeof(double) + 2 * 64 * 65 * sizeof(TF);
+  const size_t dsm = diag_smem<TF>();
   cudaFuncSetAttribute(front_diag_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dsm));
   cudaFuncSetAttribute(front_panel_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
   cudaFuncSetAttribute(front_update_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
