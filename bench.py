@@ -43,6 +43,18 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _bf16_peak():
+    """Dense BF16 tensor peak: the measured sustained bf16 GEMM rate (the
+    factor runs inside a long step)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["bf16_tflops_sustained"]), \
+            "measured bf16 sustained %.1f TFLOP/s" % float(pk["bf16_tflops_sustained"])
+    except Exception:
+        return 1700.0, "fallback bf16 sustained 1700 TFLOP/s"
+
+
 def _tf32_peak():
     """Dense TF32 tensor peak: the measured sustained bf16 GEMM rate (the factor
     runs inside a long step) times the nominal TF32/bf16 ratio 1.1/2.25."""
@@ -414,7 +426,8 @@ def _ctx_for(fe, wl, args, **kw):
                 factor_tf32=1 if args.factor_tf32 else 0,
                 precond_fp16=args.precond_fp16 if wl.precision else 0,
                 factor_lag=args.lag, element_fp64=1 if args.element_fp64 else 0,
-                warm_start=args.warm, apply_sm_share=args.apply_share)
+                warm_start=args.warm, apply_sm_share=args.apply_share,
+                update_bf16=args.update_bf16 if wl.precision else 0)
     opts.update(kw)
     return fe.FEContext.from_workload(wl, **opts)
 
@@ -541,6 +554,9 @@ def main():
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: each step's solve and integration as one CUDA graph with device-side loops "
                          "(fe_options.use_graph); 0: host-driven PCG")
+    ap.add_argument("--update-bf16", type=int, choices=[0, 1], default=1,
+                    help="mixed precision: the superpanels' deferred factor updates with BF16 "
+                         "operands on the tensor cores (fe_options.update_bf16)")
     ap.add_argument("--apply-share", type=float, default=0.5,
                     help="fraction of the application's CTA slots left to an in-flight factorisation")
     ap.add_argument("--warm", type=int, default=0, choices=[0, 1],
@@ -614,6 +630,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     stage_ms, stage_calls, launches = ctx.stage_times()
     update_flops = ctx.update_flops()
+    update_bf16_flops = ctx.update_bf16_flops()
     main_sum = sum(stage_ms[k] for k in ("element", "assembly", "apply", "spmv", "vector", "residual",
                                          "integrate", "pcg_graph")) / K
     timed_stages = {k: v / K for k, v in stage_ms.items()}
@@ -665,17 +682,41 @@ def main():
     upd_flops = update_flops / upd_calls
     upd_tflops = upd_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
     tr = traffic.get("front_update_tc_kernel")
-    if wl.precision:
+    tc_roof = {"bound": "tensor",
+               "kernel": "front_update_tc_kernel (factor trailing updates, tcgen05 kind::tf32, "
+                         + ("TF32" if args.factor_tf32 else "3xTF32") + ")",
+               "achieved": upd_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": upd_tflops / tf32_peak,
+               "traffic": tr["bytes_per_launch"] if tr else None,
+               "traffic_source": f"{tr['profile']} ({tr['date']})" if tr else None,
+               "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
+               "peak_source": tf32_src,
+               "note": "achieved counts algorithmic flops; 3xTF32 issues 3 TF32 MMAs per product, "
+                       "so frac <= 1/3; the update launches run on the low-priority factor stream"}
+    if wl.precision and args.update_bf16:
+        # the superpanels' deferred updates (the bulk of the factor's flops) in
+        # the BF16 kernel; the remaining (eager, in-superpanel) updates above
+        bf_peak, bf_src = _bf16_peak()
+        bcalls = max(1, stage_calls["factor_update_bf16"])
+        bms = stage_ms["factor_update_bf16"] / bcalls
+        bflops = update_bf16_flops / bcalls
+        btf = bflops / (bms / 1e3) / 1e12 if bms > 0 else 0.0
+        tb = traffic.get("front_update_bf16_kernel")
+        tc_roof["kernel"] = "front_update_tc_kernel (eager in-superpanel updates, tcgen05 kind::tf32, " + \
+            ("TF32" if args.factor_tf32 else "3xTF32") + ")"
         roofline = {"bound": "tensor",
-                    "kernel": "front_update_tc_kernel (factor trailing updates, tcgen05 kind::tf32, "
-                              + ("TF32" if args.factor_tf32 else "3xTF32") + ")",
-                    "achieved": upd_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": upd_tflops / tf32_peak,
-                    "traffic": tr["bytes_per_launch"] if tr else None,
-                    "traffic_source": f"{tr['profile']} ({tr['date']})" if tr else None,
-                    "flops_per_launch": upd_flops, "avg_ms": upd_ms, "launches": upd_calls,
-                    "peak_source": tf32_src,
-                    "note": "achieved counts algorithmic flops; 3xTF32 issues 3 TF32 MMAs per product, "
-                            "so frac <= 1/3; the update launches run on the low-priority factor stream"}
+                    "kernel": "front_update_bf16_kernel (superpanel trailing updates, TMA + tcgen05 kind::f16, "
+                              "BF16 operands, FP32 accumulation)",
+                    "achieved": btf, "peak": bf_peak, "unit": "TFLOP/s", "frac": btf / bf_peak,
+                    "traffic": tb["bytes_per_launch"] if tb else None,
+                    "traffic_source": f"{tb['profile']} ({tb['date']})" if tb else None,
+                    "flops_per_launch": bflops, "avg_ms": bms, "launches": bcalls,
+                    "peak_source": bf_src,
+                    "note": "achieved counts algorithmic flops (lower triangle of the Schur updates plus the "
+                            "apply-operator updates); launched on the low-priority factor stream, timed live "
+                            "with CUDA events there",
+                    "eager_updates": tc_roof}
+    elif wl.precision:
+        roofline = tc_roof
     else:
         roofline = {"bound": "alu", "kernel": "front_update_kernel<double> (factor trailing updates, FP64)",
                     "achieved": upd_tflops, "peak": 1.25, "unit": "TFLOP/s", "frac": upd_tflops / 1.25,
@@ -718,6 +759,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single", "nd_leaf_nodes": args.nd_leaf or 64,
                    "pcg_graph": bool(args.graph), "warm_start": bool(args.warm),
                    "apply_sm_share": args.apply_share,
+                   "update_bf16": bool(args.update_bf16),
                    "factor_tf32": bool(args.factor_tf32),
                    "precond_fp16": bool(wl.precision and args.precond_fp16),
                    "mean_pcg_iters": float(np.mean(iters)), "pcg_iters": iters, "factor_ages": ages,

@@ -188,6 +188,20 @@ typedef struct {
                              kernels (the application is bound by its tree's
                              dependency chains more than by its CTA count).
                              The result does not depend on it.               */
+  int32_t update_bf16;    /* FE_MIXED: 1 (default) applies each superpanel's
+                             deferred trailing update (the rank-256 updates
+                             of the rest of a front, the bulk of the factor's
+                             flops) on the tensor cores with BF16 operands and
+                             FP32 accumulation (tcgen05 kind::f16), read by
+                             TMA from K-major BF16 copies of W = L D, L and
+                             the pivot rows of Y that the panel and diagonal
+                             kernels write beside their FP32 results; 0 keeps
+                             them in the TF32 kernel (factor_tf32).  The
+                             factor is a preconditioner: operands rounded to
+                             BF16 (relative 2^-9) leave the PCG iteration
+                             counts of the bench mesh unchanged, and the solve
+                             is refined to tol in FP64 either way.  Ignored
+                             for FE_FP64.                                    */
 } fe_options;
 
 typedef struct {
@@ -382,12 +396,17 @@ enum {
   FE_STAGE_FACTOR_UPDATE, /* the factor's trailing-update launches only */
   FE_STAGE_PCG_GRAPH,     /* PCG iterations replayed as CUDA graphs (use_graph) */
   FE_STAGE_CONTACT,       /* constraint resolution and motion correction      */
+  FE_STAGE_FACTOR_UPDATE_BF16, /* the superpanels' BF16 trailing-update launches
+                                  (update_bf16); FE_STAGE_FACTOR_UPDATE then
+                                  times the other update launches        */
   FE_STAGE_COUNT
 };
 int fe_get_stage_times(fe_ctx *ctx, double *ms, int64_t *calls, int64_t *kernel_launches);
 /* Algorithmic flops of the trailing-update launches timed so far (lower
  * triangle of the Schur updates plus the apply-operator updates). */
 int fe_get_update_flops(fe_ctx *ctx, double *flops);
+/* The same for the launches timed as FE_STAGE_FACTOR_UPDATE_BF16. */
+int fe_get_update_bf16_flops(fe_ctx *ctx, double *flops);
 int fe_reset_stage_times(fe_ctx *ctx);
 
 /* Replaces the material parameters ([n_elems * 3], element-major, the layout

@@ -263,6 +263,12 @@ def fe_get_update_flops(ctx):
     return f.value
 
 
+def fe_get_update_bf16_flops(ctx):
+    f = ct.c_double()
+    _check(ctx, load().fe_get_update_bf16_flops(ctx, ct.byref(f)))
+    return f.value
+
+
 def fe_reset_stage_times(ctx):
     _check(ctx, load().fe_reset_stage_times(ctx))
 
@@ -431,6 +437,9 @@ class FEContext:
 
     def update_flops(self):
         return fe_get_update_flops(self.ctx)
+
+    def update_bf16_flops(self):
+        return fe_get_update_bf16_flops(self.ctx)
 
     def reset_stage_times(self):
         fe_reset_stage_times(self.ctx)

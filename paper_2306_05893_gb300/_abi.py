@@ -31,7 +31,8 @@ class FeOptions(ct.Structure):
                 ("newton_tol", ct.c_double), ("factor_tf32", ct.c_int32),
                 ("precond_fp16", ct.c_int32), ("contact_sweeps", ct.c_int32), ("contact_tol", ct.c_double),
                 ("factor_lag", ct.c_int32), ("dep_wait_s", ct.c_double), ("element_fp64", ct.c_int32),
-                ("warm_start", ct.c_int32), ("spmv_variant", ct.c_int32), ("apply_sm_share", ct.c_double)]
+                ("warm_start", ct.c_int32), ("spmv_variant", ct.c_int32), ("apply_sm_share", ct.c_double),
+                ("update_bf16", ct.c_int32)]
 
 
 class FeStepInfo(ct.Structure):
@@ -47,7 +48,7 @@ class FeInfo(ct.Structure):
 
 
 STAGES = ["element", "assembly", "factor", "apply", "spmv", "vector", "residual", "integrate",
-          "factor_update", "pcg_graph", "contact"]
+          "factor_update", "pcg_graph", "contact", "factor_update_bf16"]
 
 P = ct.POINTER
 CTX = ct.c_void_p
@@ -85,6 +86,7 @@ SIGNATURES = {
     "fe_get_stage_times": (ct.c_int, [CTX, DP, P(ct.c_int64), P(ct.c_int64)]),
     "fe_reset_stage_times": (ct.c_int, [CTX]),
     "fe_get_update_flops": (ct.c_int, [CTX, DP]),
+    "fe_get_update_bf16_flops": (ct.c_int, [CTX, DP]),
     "fe_set_params": (ct.c_int, [CTX, ct.c_void_p]),
     "fe_adjoint": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "fe_clear_checkpoints": (ct.c_int, [CTX]),

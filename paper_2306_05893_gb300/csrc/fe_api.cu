@@ -157,7 +157,34 @@ int encode_tensor_maps(fe_ctx *c, DeviceState *d) {
         return set_error(c, FE_ERR_CUDA, "tensor map of front " + std::to_string(f) + " (Y rows) rejected");
     }
   }
-  return upload(c, d, reinterpret_cast<CUtensorMap **>(&d->tmaps), maps);
+  int st = upload(c, d, reinterpret_cast<CUtensorMap **>(&d->tmaps), maps);
+  if (st || !c->opt.update_bf16) return st;
+  // update_bf16: the K-major BF16 copies of a superpanel ([rows][256], rows
+  // of 512 bytes) and one map each, 128 rows x 64 columns per box (128 bytes:
+  // one 128-byte swizzle span, the MMA operand layout); zeroed once, so that
+  // rows a copy never receives read as finite values
+  const int64_t rows_wl = std::max<int64_t>(c->w_total, 1), rows_y = std::max<int64_t>(c->n_free, 1);
+  st = dallocv(c, d, &d->bt_w, size_t(rows_wl) * 256 * 2);
+  if (!st) st = dallocv(c, d, &d->bt_l, size_t(rows_wl) * 256 * 2);
+  if (!st) st = dallocv(c, d, &d->bt_y, size_t(rows_y) * 256 * 2);
+  if (st) return st;
+  FE_CUDA_TRY(cudaMemset(d->bt_w, 0, size_t(rows_wl) * 512));
+  FE_CUDA_TRY(cudaMemset(d->bt_l, 0, size_t(rows_wl) * 512));
+  FE_CUDA_TRY(cudaMemset(d->bt_y, 0, size_t(rows_y) * 512));
+  std::vector<CUtensorMap> bm(3);
+  void *bases[3] = {d->bt_w, d->bt_l, d->bt_y};
+  const int64_t rows[3] = {rows_wl, rows_wl, rows_y};
+  for (int k = 0; k < 3; ++k) {
+    const cuuint32_t es[2] = {1, 1};
+    const cuuint64_t dim[2] = {256, cuuint64_t(rows[k])};
+    const cuuint64_t stride[1] = {512};
+    const cuuint32_t box[2] = {64, 128};
+    if (encode(&bm[size_t(k)], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bases[k], dim, stride, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return set_error(c, FE_ERR_CUDA, "tensor map of the BF16 superpanel copies rejected");
+  }
+  return upload(c, d, reinterpret_cast<CUtensorMap **>(&d->bmaps), bm);
 }
 
 #define FE_TRY(x)      \
@@ -321,6 +348,9 @@ int ensure_device(fe_ctx *c) {
       T.trail_off.push_back(int64_t(all.size())); T.trail_n.push_back(int64_t(L.trail[s].size() / 4));
       T.trail_flops.push_back(L.trail_flops[s]);
       all.insert(all.end(), L.trail[s].begin(), L.trail[s].end());
+      T.tend_off.push_back(int64_t(all.size())); T.tend_n.push_back(int64_t(L.tend[s].size() / 4));
+      T.tend_flops.push_back(L.tend_flops[s]);
+      all.insert(all.end(), L.tend[s].begin(), L.tend[s].end());
     }
     pad4();
     T.fwd_off = int64_t(all.size()); T.fwd_n = int64_t(L.fwd_tasks.size() / 4);
@@ -1418,6 +1448,12 @@ int fe_get_update_flops(fe_ctx *c, double *flops) {
   return FE_OK;
 }
 
+int fe_get_update_bf16_flops(fe_ctx *c, double *flops) {
+  if (!c || !flops) return FE_ERR_ARG;
+  *flops = c->dev ? c->dev->update_bf16_flops : 0.0;
+  return FE_OK;
+}
+
 int fe_reset_stage_times(fe_ctx *c) {
   if (!c) return FE_ERR_ARG;
   DeviceState *d = c->dev;
@@ -1431,6 +1467,7 @@ int fe_reset_stage_times(fe_ctx *c) {
   }
   d->launches = 0;
   d->update_flops = 0.0;
+  d->update_bf16_flops = 0.0;
   return FE_OK;
 }
 

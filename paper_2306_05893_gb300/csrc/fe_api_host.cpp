@@ -35,6 +35,7 @@ int fe_options_default(fe_options *o) {
   o->warm_start = 0;
   o->spmv_variant = -1;
   o->apply_sm_share = 0.0;
+  o->update_bf16 = 1;
   return FE_OK;
 }
 
@@ -98,6 +99,7 @@ int fe_create(const fe_mesh *mesh, const fe_material *mat, double h, double alph
     if (!(c->opt.dep_wait_s > 0) || !std::isfinite(c->opt.dep_wait_s)) c->opt.dep_wait_s = 1.0;
     c->opt.element_fp64 = (c->opt.precision == FE_MIXED && c->opt.element_fp64) ? 1 : 0;
     c->opt.warm_start = c->opt.warm_start ? 1 : 0;
+    c->opt.update_bf16 = (c->opt.precision == FE_MIXED && c->opt.update_bf16) ? 1 : 0;
     if (!(c->opt.apply_sm_share >= 0.0 && c->opt.apply_sm_share <= 0.9)) {
       delete c;
       return FE_ERR_ARG;

@@ -51,6 +51,10 @@ struct Level {
   std::vector<int32_t> asm_tasks;     // (front, c0, c1) triples
   std::vector<std::vector<int32_t>> diag, panel, trail;  // int4 per task
   std::vector<double> trail_flops;    // algorithmic flops of each step's update launch
+  // superpanel ends in the BF16 kernel (FE_MIXED with update_bf16): the
+  // deferred rank-K updates of the rest of the fronts, split off trail
+  std::vector<std::vector<int32_t>> tend;
+  std::vector<double> tend_flops;
   // apply task lists
   // (front, r0, j0, slot): rows [r0, r0 + fwd_rows) x pivot columns [j0, j0 + kFwdCols)
   std::vector<int32_t> fwd_tasks;

@@ -113,6 +113,11 @@ struct DeviceState {
   // front over all rows of Y[0] then Y[1] (128 x 16 boxes); null for the
   // FP64 factor
   void *tmaps = nullptr;
+  // update_bf16: K-major BF16 copies of the current superpanel, [rows][256]
+  // (Wt, Lt: W = L D and L, row w_off + r of a front; Yk: the pivot rows of
+  // Y, row first + c for column c), and their three tensor maps
+  void *bt_w = nullptr, *bt_l = nullptr, *bt_y = nullptr;
+  void *bmaps = nullptr;
   // contacts (fe_contact.cu): constraint data, forward solves G, compliance
   // W (m x m), PGS right-hand side and multipliers
   int32_t *c_node = nullptr;
@@ -162,8 +167,8 @@ struct DeviceState {
   // task list offsets: per level {asm, per step: diag, panel, trail}, fwd, bwd
   struct LevelTasks {
     int64_t asm_off = 0, asm_n = 0;
-    std::vector<int64_t> diag_off, diag_n, panel_off, panel_n, trail_off, trail_n;
-    std::vector<double> trail_flops;
+    std::vector<int64_t> diag_off, diag_n, panel_off, panel_n, trail_off, trail_n, tend_off, tend_n;
+    std::vector<double> trail_flops, tend_flops;
     int64_t fwd_off = 0, fwd_n = 0, bwd_off = 0, bwd_n = 0;
     int64_t nfronts = 0, fronts_off = 0;
   };
@@ -181,6 +186,7 @@ struct DeviceState {
   int64_t stage_calls[FE_STAGE_COUNT] = {0};
   mutable int64_t launches = 0;
   double update_flops = 0.0;            // algorithmic flops of the timed update launches
+  double update_bf16_flops = 0.0;       // the same for the BF16 superpanel-end launches
 
   // batched solve: member DOF ranges, row -> member, per-member scalars
   int64_t *seg_dof = nullptr;

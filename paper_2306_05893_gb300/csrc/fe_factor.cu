@@ -15,6 +15,7 @@
 // a level: the only serial dependency left is the level order
 // (leaves up for L, root down for L^T), as in the paper's level schedule.
 #include <cuda.h>  // CUtensorMap
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -331,7 +332,8 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
                                                                   const DFront *__restrict__ fronts,
                                                                   TF *__restrict__ F, TF *__restrict__ Y,
                                                                   double *__restrict__ D,
-                                                                  double *__restrict__ Dinv, int *flags) {
+                                                                  double *__restrict__ Dinv, int *flags,
+                                                                  __nv_bfloat16 *__restrict__ by) {
   constexpr bool kDF = sizeof(TF) == 4;
   constexpr unsigned kAll = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char dsm_raw[];
@@ -599,8 +601,23 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     Dinv[fr.first + k0 + threadIdx.x] = dinv;
   }
   TF *Yf = Y + fr.y_off;
+  if (by) {
+    // the BF16 copy's chunk of this panel is zero in the columns of the
+    // superpanel's later panels (Y's upper triangle there): the copy is
+    // reused by every superpanel and factorisation, and those positions may
+    // hold another superpanel's values
+    const int32_t s1 = min((k0 / kSuper + 1) * kSuper, fr.npiv);
+    const int ncol = s1 - (k0 + kb);
+    for (int idx = threadIdx.x; idx < 64 * ncol; idx += blockDim.x)
+      by[(int64_t(fr.first) + k0 + kb + idx / 64) * kSuper + (k0 % kSuper) + (idx & 63)] = __float2bfloat16_rn(0.f);
+  }
   for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
     const int i = idx & 63, j = idx >> 6;
+    // the BF16 copy of the pivot rows of Y (update_bf16): column k0 + j,
+    // all 64 rows of the chunk (zeros past kb)
+    if (by && j < kb)
+      by[(int64_t(fr.first) + k0 + j) * kSuper + (k0 % kSuper) + i] =
+          __float2bfloat16_rn(i >= kb ? 0.f : float(i > j ? X[i][j] : (i == j ? TF(1) : TF(0))));
     if (i >= kb || j >= kb) continue;
     TF sc;
     if constexpr (kDF)
@@ -615,11 +632,20 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
 // ------------------------------------------------------- panel and X_K
 // PANEL (front, k0, r0): rows [r0, r0+64) of the panel: L = F L_KK^{-T} D^{-1}.
 // XK    (front, k0, c0): Y[K, c0:c0+64] <- L_KK^{-1} Y[K, c0:c0+64].
+// With the BF16 superpanel ends (bw non-null), both also write their results
+// into the K-major BF16 copies of the superpanel, at column k0 - s0 of the
+// 256: PANEL the rows of W = F L_KK^{-T} (bw) and of L (bl), XK the pivot rows
+// of Y as row first + c of by; the 64 columns of a panel's chunk are written
+// whole (zeros past the panel's kb pivots), so the last, partial chunk of a
+// superpanel adds nothing.
 template <typename TF>
 __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restrict__ tasks,
                                                           const DFront *__restrict__ fronts,
                                                           TF *__restrict__ F, TF *__restrict__ Y,
-                                                          const double *__restrict__ Dinv) {
+                                                          const double *__restrict__ Dinv,
+                                                          __nv_bfloat16 *__restrict__ bw,
+                                                          __nv_bfloat16 *__restrict__ bl,
+                                                          __nv_bfloat16 *__restrict__ by) {
   extern __shared__ unsigned char psm[];
   TF(*Ls)[65] = reinterpret_cast<TF(*)[65]>(psm);
   TF(*Bs)[65] = reinterpret_cast<TF(*)[65]>(psm + 64 * 65 * sizeof(TF));
@@ -659,12 +685,17 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       const int c = tc + 16 * s;
-      if (c >= kb) continue;
-      const TF di = TF(Dinv[fr.first + k0 + c]);
+      const TF di = c < kb ? TF(Dinv[fr.first + k0 + c]) : TF(0);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int32_t r = a0 + tr * 4 + u;
-        if (r < m) Ff[r + int64_t(k0 + c) * fr.ldf] = acc[u][s] * di;
+        if (r >= m) continue;
+        if (c < kb) Ff[r + int64_t(k0 + c) * fr.ldf] = acc[u][s] * di;
+        if (bw) {
+          const int64_t o = (fr.w_off + r) * int64_t(kSuper) + (k0 % kSuper) + c;
+          bw[o] = __float2bfloat16_rn(float(acc[u][s]));
+          bl[o] = __float2bfloat16_rn(float(acc[u][s] * di));
+        }
       }
     }
   } else {  // T_XK
@@ -688,11 +719,12 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int i = tr * 4 + u;
-      if (i >= kb) continue;
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const int32_t c = a0 + tc + 16 * s;
-        if (c < k0) Yf[(k0 + i) + int64_t(c) * fr.ldy] = acc[u][s];
+        if (c >= k0) continue;
+        if (i < kb) Yf[(k0 + i) + int64_t(c) * fr.ldy] = acc[u][s];
+        if (by) by[(int64_t(fr.first) + c) * kSuper + (k0 % kSuper) + i] = __float2bfloat16_rn(float(acc[u][s]));
       }
     }
   }
@@ -1237,6 +1269,210 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kUTmemCols) : "memory");
 }
 
+// ------------------------------------------ superpanel ends in BF16
+// update_bf16: the deferred update of a superpanel (columns [s0, s1),
+// K = s1 - s0 <= kSuper) applied to the rest of the front, task
+// (front, kind | chunks, i0, j0) as for front_update_tc_kernel:
+//   TRAIL  F[i, j] -= sum_l W[i, l] L[j, l]   (i >= j >= s1, lower part)
+//   RUPD   Y[i, c] -= sum_l L[i, l] Y[l, c]   (i >= s1, c < s1)
+// with W = L D.  The operands are the K-major BF16 copies of the superpanel
+// that the panel and diagonal kernels wrote (Wt, Lt: row w_off + r of the
+// front; Yk: row first + c; 256 BF16 per row), loaded by TMA as 128-row x
+// 64-column boxes in the 128-byte-swizzled layout that tcgen05.mma reads
+// directly, so no thread touches an operand:
+//  * warp 0 (one lane): streams the K chunks (A and B box of 16 KB each)
+//    through a two-stage ring, a stage refilled once the MMAs that read it
+//    have completed;
+//  * warp 1: allocates the tensor memory; one lane issues four
+//    tcgen05.mma.kind::f16 (BF16 x BF16, M = N = 128, K = 16) per chunk into
+//    a 128 x 128 FP32 accumulator and commits each chunk to its stage's
+//    empty mbarrier and the last to the accumulator's;
+//  * warps 2-5: read the accumulator (warp w: lanes 32 (w % 4) ..), stage
+//    its negative in the freed ring (0 outside the task's rows and columns:
+//    rows below s1 or past the front, columns past the superpanel for RUPD,
+//    the upper part for TRAIL) and one lane adds it to F or Y with eight TMA
+//    reduce-add boxes (each entry receives exactly one addition per launch:
+//    deterministic).
+// The two stages (64 KB) hold the staged FP32 tile afterwards, so three CTAs
+// fit an SM.  Every mbarrier wait is bounded as in front_update_tc_kernel.
+constexpr int kBfThreads = 192;
+constexpr int kBfBox = 128 * 64 * 2;  // bytes of one operand box
+constexpr int kBfStages = 2;
+constexpr size_t bf16_update_smem() { return size_t(kBfStages) * 2 * kBfBox + 1024; }  // + alignment slack
+static_assert(kBfStages * 2 * kBfBox == 128 * 128 * 4, "the staged output tile fills the ring");
+
+// tcgen05 instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B
+// BF16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kT128 >> 3) << 17) |
+                                (uint32_t(kT128 >> 4) << 24);
+
+// shared-memory descriptor of a K-major operand in the 128-byte swizzle
+// layout (8-row groups of 128-byte rows, 1024 bytes apart): start address
+// >> 4 (bits 0-13), leading offset unused (1), stride 1024 >> 4 (bits
+// 32-45), fixed 0b001 at bits 46-48, swizzle mode 2 (128 bytes) at bits
+// 61-63.  The box is 1024-byte aligned; a K step of 16 BF16 (32 bytes)
+// inside the 128-byte row advances the start address by 2.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
+         (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+
+__global__ void __launch_bounds__(kBfThreads) front_update_bf16_kernel(
+    const int32_t *__restrict__ tasks, const DFront *__restrict__ fronts, const CUtensorMap *__restrict__ bmaps,
+    const CUtensorMap *__restrict__ fmaps, const CUtensorMap *__restrict__ ycmaps, int *flags) {
+  extern __shared__ __align__(1024) unsigned char bsm_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * kBfStages + 1];  // full[2], empty[2], accumulator
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+  const volatile int *abort_word = &s_abort;
+  pdl_launch_dependents();
+  const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
+  const DFront fr = fronts[t.x];
+  const int kind = (t.y >> 24) & 7;
+  const int32_t s0 = t.y & 0xffffff, i0 = t.z, j0 = t.w, m = fr.m, p = fr.npiv;
+  const int32_t s1 = min(s0 + kSuper, p);
+  const int nq = (s1 - s0 + 63) / 64;  // 64-column chunks (a partial last one reads zeros)
+  const bool trail = kind == T_TRAIL;
+  const CUtensorMap *mapA = trail ? bmaps : bmaps + 1;      // Wt or Lt
+  const CUtensorMap *mapB = trail ? bmaps + 1 : bmaps + 2;  // Lt or Yk
+  const CUtensorMap *mapC = trail ? fmaps + t.x : ycmaps + t.x;
+  const int32_t rowA = int32_t(fr.w_off) + i0;
+  const int32_t rowB = trail ? int32_t(fr.w_off) + j0 : fr.first + j0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ring = (smem_u32(bsm_raw) + 1023u) & ~1023u;  // 1024-byte aligned stages
+  float *ring_f = reinterpret_cast<float *>(bsm_raw + (ring - smem_u32(bsm_raw)));
+  const uint32_t bar_full = smem_u32(bars), bar_empty = bar_full + 8 * kBfStages, bar_acc = bar_empty + 8 * kBfStages;
+  // the copies and F / Y come from the preceding launches; waiting for them
+  // before the tensor-memory allocation also keeps a CTA from holding tensor
+  // memory while an earlier update launch still needs some
+  pdl_wait();
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int b = 0; b < kBfStages; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_full + 8 * b) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_empty + 8 * b) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_acc) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  bool ok = true;
+  int issued = 0, mma_chunks = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int q = 0; q < nq && ok; ++q) {
+        const int s = q % kBfStages;
+        if (q >= kBfStages) ok = mbar_wait(bar_empty + 8 * s, uint32_t((q - kBfStages) / kBfStages) & 1u, abort_word);
+        if (!ok) break;
+        const uint32_t bar = bar_full + 8 * s, dA = ring + uint32_t(s) * 2 * kBfBox, dB = dA + kBfBox;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(2 * kBfBox)
+                     : "memory");
+        tma_load_2d(dA, mapA, 64 * q, rowA, bar);
+        tma_load_2d(dB, mapB, 64 * q, rowB, bar);
+        issued = q + 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int q = 0; q < nq && ok; ++q) {
+        const int s = q % kBfStages;
+        ok = mbar_wait(bar_full + 8 * s, uint32_t(q / kBfStages) & 1u, abort_word);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t a = ring + uint32_t(s) * 2 * kBfBox, b = a + kBfBox;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t da = umma_desc_sw128(a) + uint64_t(2 * kk), db = umma_desc_sw128(b) + uint64_t(2 * kk);
+          const uint32_t acc = (q > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(kIdescBf16), "r"(acc)
+              : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         bar_empty + 8 * s)
+                     : "memory");
+        mma_chunks = q + 1;
+      }
+      if (ok)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_acc)
+                     : "memory");
+    }
+    __syncwarp();
+  } else {
+    // epilogue warps 2-5: TMEM lane quarter g = warp % 4
+    const int g = warp & 3;
+    if (lane == 0) ok = mbar_wait(bar_acc, 0u, abort_word);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+      const int rl = 32 * g + lane;
+      const int32_t r = i0 + rl;
+      const bool rin = r >= s1 && r < m;
+      const int32_t chi_g = trail ? min(m, r + 1) : s1;
+      const int clo = trail ? max(0, s1 - j0) : 0;
+      const int chi = rin ? max(0, min(kT128, chi_g - j0)) : 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {  // 64 columns per round
+        uint32_t v[4][16];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const uint32_t ta = tmem + (uint32_t(32 * g) << 16) + uint32_t(64 * h + 16 * x);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];\n"
+              : "=r"(v[x][0]), "=r"(v[x][1]), "=r"(v[x][2]), "=r"(v[x][3]), "=r"(v[x][4]), "=r"(v[x][5]),
+                "=r"(v[x][6]), "=r"(v[x][7]), "=r"(v[x][8]), "=r"(v[x][9]), "=r"(v[x][10]), "=r"(v[x][11]),
+                "=r"(v[x][12]), "=r"(v[x][13]), "=r"(v[x][14]), "=r"(v[x][15])
+              : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int cl = 64 * h + 16 * x + e;
+            ring_f[cl * kT128 + rl] = (cl >= clo && cl < chi) ? -__uint_as_float(v[x][e]) : 0.f;
+          }
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic-proxy stores -> TMA
+    }
+  }
+  if (!ok) s_abort = 1;
+  ok = __syncthreads_and(ok) != 0;
+  if (ok && threadIdx.x == 64) {
+    for (int b = 0; b < 8; ++b) tma_reduce_add_2d(mapC, i0, j0 + 16 * b, ring + uint32_t(b) * kT128 * 16 * 4);
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+  }
+  // on a timeout: the loads (warp 0) and MMAs (warp 1) still in flight finish
+  // before the shared and tensor memory are given up (each wait bounded)
+  if (!ok && warp == 0 && lane == 0) {
+    atomicOr(flags, FLAG_WAIT_TIMEOUT);
+    for (int q = max(0, issued - kBfStages); q < issued; ++q)
+      mbar_wait(bar_full + 8 * (q % kBfStages), uint32_t(q / kBfStages) & 1u);
+  }
+  if (!ok && warp == 1 && lane == 0 && mma_chunks > 0) {
+    const int q = mma_chunks - 1;
+    mbar_wait(bar_empty + 8 * (q % kBfStages), uint32_t(q / kBfStages) & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128) : "memory");
+}
+
 // ------------------------------------------------------------------ apply
 
 // Deterministic combination of a block split over several CTAs: each CTA
@@ -1746,6 +1982,17 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
   cudaFuncSetAttribute(front_update_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsm));
   cudaFuncSetAttribute(front_update_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(update_smem<3>()));
   cudaFuncSetAttribute(front_update_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(update_smem<1>()));
+  cudaFuncSetAttribute(front_update_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bf16_update_smem()));
+  // BF16 copies of the superpanels (FP32 factor with update_bf16)
+  __nv_bfloat16 *bw = nullptr, *bl = nullptr, *by = nullptr;
+  if constexpr (sizeof(TF) == 4) {
+    if (c->opt.update_bf16 && d->bt_w) {
+      bw = reinterpret_cast<__nv_bfloat16 *>(d->bt_w);
+      bl = reinterpret_cast<__nv_bfloat16 *>(d->bt_l);
+      by = reinterpret_cast<__nv_bfloat16 *>(d->bt_y);
+    }
+  }
+  const CUtensorMap *bmaps = reinterpret_cast<const CUtensorMap *>(d->bmaps);
   for (size_t lv = 0; lv < d->lt.size(); ++lv) {
     const auto &L = d->lt[lv];
     if (L.asm_n) d->launches++;
@@ -1756,10 +2003,10 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
       d->launches += (L.diag_n[st] > 0) + (L.panel_n[st] > 0) + (L.trail_n[st] > 0);
       if (L.diag_n[st])
         launch_pdl(front_diag_kernel<TF>, unsigned(L.diag_n[st]), kDiagThreads, dsm, s, d->tasks + L.diag_off[st],
-                   d->fronts, F, Y, d->D[buf], d->D[buf] + c->n_free, d->flags);
+                   d->fronts, F, Y, d->D[buf], d->D[buf] + c->n_free, d->flags, by);
       if (L.panel_n[st])
         launch_pdl(front_panel_kernel<TF>, unsigned(L.panel_n[st]), 256, tsm, s, d->tasks + L.panel_off[st],
-                   d->fronts, F, Y, d->D[buf] + c->n_free);
+                   d->fronts, F, Y, d->D[buf] + c->n_free, bw, bl, by);
       if (L.trail_n[st]) {
         const int ev = stage_begin(c, FE_STAGE_FACTOR_UPDATE, s);
         if (ev >= 0) d->update_flops += L.trail_flops[st];
@@ -1773,6 +2020,14 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
         else
           launch_pdl(front_update_kernel<TF>, unsigned(L.trail_n[st]), 256, tsm, s, d->tasks + L.trail_off[st],
                      d->fronts, F, Y, d->D[buf]);
+        stage_end(c, ev, s);
+      }
+      if (L.tend_n[st] && bw) {
+        d->launches++;
+        const int ev = stage_begin(c, FE_STAGE_FACTOR_UPDATE_BF16, s);
+        if (ev >= 0) d->update_bf16_flops += L.tend_flops[st];
+        launch_pdl(front_update_bf16_kernel, unsigned(L.tend_n[st]), kBfThreads, bf16_update_smem(), s,
+                   d->tasks + L.tend_off[st], d->fronts, bmaps, fmaps, ycmaps, d->flags);
         stage_end(c, ev, s);
       }
     }

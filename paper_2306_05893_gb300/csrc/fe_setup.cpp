@@ -620,6 +620,8 @@ int build_ordering(fe_ctx *c) {
   // trailing-update tile: 128 x 128 for the FP32 factor, 64 x 64 for FP64
   const int32_t ut = c->opt.precision == FE_MIXED ? 128 : kTile;
   const int32_t sp = c->opt.precision == FE_MIXED ? kSuper : kNB;
+  // the superpanels' deferred updates go to the BF16 kernel's lists
+  const bool bf16_end = c->opt.precision == FE_MIXED && c->opt.update_bf16;
   const int32_t fr_rows = fwd_rows(c->opt);
   const int32_t vw = y_vec(c->opt);  // rows per 16-byte vector of Y
   const int32_t br = bwd_rows(c->opt);
@@ -632,6 +634,8 @@ int build_ordering(fe_ctx *c) {
     L.panel.assign(steps, {});
     L.trail.assign(steps, {});
     L.trail_flops.assign(steps, 0.0);
+    L.tend.assign(steps, {});
+    L.tend_flops.assign(steps, 0.0);
     // assembly tasks: narrower column ranges for larger fronts (a task's
     // work grows with the front's rows; the top levels hold few fronts), the
     // largest fronts first so that the level's last wave is short
@@ -697,15 +701,27 @@ int build_ordering(fe_ctx *c) {
           // start 16-byte aligned); the rows and columns of the tile below
           // s1 belong to the superpanel and are left alone by the kernel
           const int32_t t1 = c->opt.precision == FE_MIXED ? (s1 & ~3) : s1;
+          auto &dst = bf16_end ? L.tend[s] : L.trail[s];
           for (int32_t j0 = t1; j0 < m; j0 += ut)
-            for (int32_t i0 = j0; i0 < m; i0 += ut) push(L.trail[s], f, code, i0, j0);
+            for (int32_t i0 = j0; i0 < m; i0 += ut) push(dst, f, code, i0, j0);
           for (int32_t i0 = t1; i0 < m; i0 += ut)
-            for (int32_t c0 = 0; c0 < s1; c0 += ut) push(L.trail[s], f, codeu, i0, c0);
+            for (int32_t c0 = 0; c0 < s1; c0 += ut) push(dst, f, codeu, i0, c0);
         }
         // algorithmic flops of this panel's updates (the zero products of the
-        // superpanel's upper triangle in Y are not counted)
+        // superpanel's upper triangle in Y are not counted); with the BF16
+        // superpanel ends, the part applied there (rows and columns from the
+        // superpanel's end s1 on) is booked to the end step
         const double rem = double(m - k1);
-        L.trail_flops[s] += rem * (rem + 1.0) * kb + 2.0 * rem * double(k1) * kb;
+        const double all_flops = rem * (rem + 1.0) * kb + 2.0 * rem * double(k1) * kb;
+        if (bf16_end) {
+          const double re = double(m - s1);
+          const double end_flops = re * (re + 1.0) * kb + 2.0 * re * double(k1) * kb;
+          const int s_end_step = (s1 - 1) / kNB;
+          L.trail_flops[s] += all_flops - end_flops;
+          L.tend_flops[s_end_step] += end_flops;
+        } else {
+          L.trail_flops[s] += all_flops;
+        }
         flops += double(kb) * kb * kb / 3.0 * 2.0            // diag LDL^T + inverse
                  + 2.0 * rem * kb * kb                        // panel
                  + 2.0 * double(kb) * kb * k0                 // X_K

@@ -298,6 +298,7 @@ def test_schedule_and_wait_option_defaults(fe):
     o = fe.options()
     assert o.factor_lag == 1 and o.dep_wait_s == 1.0 and o.element_fp64 == 0
     assert o.warm_start == 0 and o.spmv_variant == -1
+    assert o.apply_sm_share == 0.0 and o.update_bf16 == 1
 
 
 def test_spmv_variant_is_checked_on_the_host(fe):
