@@ -746,6 +746,24 @@ def main():
         breakdown_note = ("element, assembly and factor stages from the timed (graph) run; apply, spmv, vector, "
                           "residual and integrate from a host-driven run of the same steps")
     streaming = _streaming_rooflines(wl, info, stage_ms, stage_calls, hbm, peak_kind, args, traffic)
+    # the dominant kernel by share of the serialised launch list: with the BF16
+    # factor updates the preconditioner application (one forward and one
+    # backward launch per PCG iteration), HBM-bound; the factor's tensor-core
+    # kernel follows as roofline_tensor
+    roofline_tensor = roofline
+    if wl.precision and args.update_bf16 and "apply" in streaming:
+        a = streaming["apply"]
+        roofline = {"bound": "hbm", "kernel": "fwd_kernel + bwd_kernel (one preconditioner application)",
+                    "achieved": a["achieved"], "peak": a["peak"], "unit": "GB/s", "frac": a["frac"],
+                    "traffic": a["traffic"], "traffic_source": a["traffic_source"],
+                    "bytes_per_launch": a["bytes_per_launch"], "avg_ms": a["avg_ms"],
+                    "launches": stage_calls.get("apply", 0),
+                    "peak_source": "measured copy bandwidth (%s)" % peak_kind,
+                    "dominant_by": "share of the serialised launch list (profiles/launches_tet30x30x120-mr.md)",
+                    "note": "algorithmic bytes: both sweeps read every stored entry of the binary16 apply "
+                            "operators once, plus the vectors; timed with CUDA events on the main stream in a "
+                            "host-driven run of the same steps (inside the step graph the application runs in "
+                            "device-side loops)"}
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -765,6 +783,7 @@ def main():
                    "mean_pcg_iters": float(np.mean(iters)), "pcg_iters": iters, "factor_ages": ages,
                    "refinements": refs, "max_displacement_m": disp},
         "roofline": roofline,
+        "roofline_tensor": roofline_tensor,
         "roofline_streaming": streaming,
         "stage_breakdown": breakdown_note,
         "stages_ms_per_step": timed_stages,
