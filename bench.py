@@ -428,6 +428,8 @@ def _ctx_for(fe, wl, args, **kw):
                 factor_lag=args.lag, element_fp64=1 if args.element_fp64 else 0,
                 warm_start=args.warm, apply_sm_share=args.apply_share,
                 update_bf16=args.update_bf16 if wl.precision else 0)
+    if args.inner_tol:
+        opts["inner_tol"] = args.inner_tol
     opts.update(kw)
     return fe.FEContext.from_workload(wl, **opts)
 
@@ -554,6 +556,9 @@ def main():
     ap.add_argument("--graph", type=int, default=1, choices=[0, 1],
                     help="1: each step's solve and integration as one CUDA graph with device-side loops "
                          "(fe_options.use_graph); 0: host-driven PCG")
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="mixed precision: the inner FP32 PCG's tolerance per refinement sweep "
+                         "(fe_options.inner_tol; 0: the library default 1e-4)")
     ap.add_argument("--update-bf16", type=int, choices=[0, 1], default=1,
                     help="mixed precision: the superpanels' deferred factor updates with BF16 "
                          "operands on the tensor cores (fe_options.update_bf16)")
@@ -778,6 +783,7 @@ def main():
                    "pcg_graph": bool(args.graph), "warm_start": bool(args.warm),
                    "apply_sm_share": args.apply_share,
                    "update_bf16": bool(args.update_bf16),
+                   "inner_tol": args.inner_tol or 1e-4,
                    "factor_tf32": bool(args.factor_tf32),
                    "precond_fp16": bool(wl.precision and args.precond_fp16),
                    "mean_pcg_iters": float(np.mean(iters)), "pcg_iters": iters, "factor_ages": ages,

@@ -244,16 +244,16 @@ __device__ __forceinline__ DF df_sub(DF x, DF y) {
   s.lo += x.lo - y.lo;
   return df_quick(s.hi, s.lo);
 }
-// 1/d: the FP32 reciprocal refined by one Newton step x + x (1 - d x) with
-// the residual formed in double-float (error ~2^-46 relative).  A
-// non-positive pivot is flagged and replaced by 1 so the factorisation
-// finishes without NaNs.
-__device__ __forceinline__ DF df_pivot_inverse(DF d, int *flags, bool report) {
-  if (!(d.hi > 0.f)) {
-    if (report) atomicOr(flags, FLAG_PIVOT);
-    d = {1.f, 0.f};
-  }
-  const float x = __frcp_rn(d.hi);
+// 1/d: the hardware reciprocal estimate (within 2 ulp) refined by one Newton
+// step x + x (1 - d x) with the residual formed in double-float, which
+// squares its relative error (~2^-44).  Branch-free: a non-positive pivot is
+// replaced by 1 so the factorisation finishes without NaNs, and the caller
+// flags it.
+__device__ __forceinline__ DF df_pivot_inverse(DF d) {
+  const bool ok = d.hi > 0.f;
+  d.hi = ok ? d.hi : 1.f;
+  d.lo = ok ? d.lo : 0.f;
+  const float x = __fdividef(1.f, d.hi);
   const DF dx = df_mul(d, {x, 0.f});
   const float r = (1.f - dx.hi) - dx.lo;
   const DF q = df_two_prod(x, r);
@@ -420,18 +420,29 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
           sq0[jj] = df_two_prod(w0, w0);
           sq1[jj] = df_two_prod(w1, w1);
         }
+        // the chain has no branch and no store: the inverses stay in
+        // registers until the sub-block is done, a bad pivot is flagged once
+        DF invs[16];
+        bool bad = false;
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           const int j = b0 + jj;
-          if (j >= kb) break;
-          const float djh = __shfl_sync(kAll, j < 32 ? p0.hi : p1.hi, j & 31);
-          const float djl = __shfl_sync(kAll, j < 32 ? p0.lo : p1.lo, j & 31);
-          const DF inv = df_pivot_inverse({djh, djl}, flags, lane == 0);
-          if (lane == 0) s_invf[j] = inv;
-          const DF n0 = df_sub(p0, df_mul(sq0[jj], inv)), n1 = df_sub(p1, df_mul(sq1[jj], inv));
-          if (i0 > j && i0 < kb) p0 = n0;
-          if (i1 > j && i1 < kb) p1 = n1;
+          invs[jj] = {1.f, 0.f};
+          if (j < kb) {  // (warp-uniform)
+            const float djh = __shfl_sync(kAll, j < 32 ? p0.hi : p1.hi, j & 31);
+            const float djl = __shfl_sync(kAll, j < 32 ? p0.lo : p1.lo, j & 31);
+            bad = bad || !(djh > 0.f);
+            const DF inv = df_pivot_inverse({djh, djl});
+            invs[jj] = inv;
+            const DF n0 = df_sub(p0, df_mul(sq0[jj], inv)), n1 = df_sub(p1, df_mul(sq1[jj], inv));
+            p0 = (i0 > j && i0 < kb) ? n0 : p0;
+            p1 = (i1 > j && i1 < kb) ? n1 : p1;
+          }
         }
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj)
+          if (lane == jj && b0 + jj < kb) s_invf[b0 + jj] = invs[jj];
+        if (bad && lane == 0) atomicOr(flags, FLAG_PIVOT);
       } else {
         double sq0[16], sq1[16];
 #pragma unroll
@@ -605,19 +616,28 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
     // the BF16 copy's chunk of this panel is zero in the columns of the
     // superpanel's later panels (Y's upper triangle there): the copy is
     // reused by every superpanel and factorisation, and those positions may
-    // hold another superpanel's values
+    // hold another superpanel's values.  Then the panel's own columns,
+    // L_KK^{-1} column j with all 64 rows of the chunk (zeros past kb); both
+    // as 16-byte stores of eight BF16.
     const int32_t s1 = min((k0 / kSuper + 1) * kSuper, fr.npiv);
     const int ncol = s1 - (k0 + kb);
-    for (int idx = threadIdx.x; idx < 64 * ncol; idx += blockDim.x)
-      by[(int64_t(fr.first) + k0 + kb + idx / 64) * kSuper + (k0 % kSuper) + (idx & 63)] = __float2bfloat16_rn(0.f);
+    for (int idx = threadIdx.x; idx < 8 * ncol; idx += blockDim.x)
+      *reinterpret_cast<uint4 *>(by + (int64_t(fr.first) + k0 + kb + idx / 8) * kSuper + (k0 % kSuper) +
+                                 8 * (idx & 7)) = make_uint4(0u, 0u, 0u, 0u);
+    for (int idx = threadIdx.x; idx < 8 * kb; idx += blockDim.x) {
+      const int j = idx >> 3, ib = 8 * (idx & 7);
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int i = ib + e;
+        v[e] = __float2bfloat16_rn(i >= kb ? 0.f : float(i > j ? X[i][j] : (i == j ? TF(1) : TF(0))));
+      }
+      *reinterpret_cast<uint4 *>(by + (int64_t(fr.first) + k0 + j) * kSuper + (k0 % kSuper) + ib) =
+          *reinterpret_cast<const uint4 *>(v);
+    }
   }
   for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
     const int i = idx & 63, j = idx >> 6;
-    // the BF16 copy of the pivot rows of Y (update_bf16): column k0 + j,
-    // all 64 rows of the chunk (zeros past kb)
-    if (by && j < kb)
-      by[(int64_t(fr.first) + k0 + j) * kSuper + (k0 % kSuper) + i] =
-          __float2bfloat16_rn(i >= kb ? 0.f : float(i > j ? X[i][j] : (i == j ? TF(1) : TF(0))));
     if (i >= kb || j >= kb) continue;
     TF sc;
     if constexpr (kDF)
@@ -630,6 +650,9 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
 }
 
 // ------------------------------------------------------- panel and X_K
+// row pitch (BF16 entries) of the staged copy tiles: 144-byte rows keep the
+// 16-byte row chunks aligned and spread a warp's scalar stores over banks
+constexpr int kPanelStage = 72;
 // PANEL (front, k0, r0): rows [r0, r0+64) of the panel: L = F L_KK^{-T} D^{-1}.
 // XK    (front, k0, c0): Y[K, c0:c0+64] <- L_KK^{-1} Y[K, c0:c0+64].
 // With the BF16 superpanel ends (bw non-null), both also write their results
@@ -646,7 +669,7 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
                                                           __nv_bfloat16 *__restrict__ bw,
                                                           __nv_bfloat16 *__restrict__ bl,
                                                           __nv_bfloat16 *__restrict__ by) {
-  extern __shared__ unsigned char psm[];
+  extern __shared__ __align__(16) unsigned char psm[];
   TF(*Ls)[65] = reinterpret_cast<TF(*)[65]>(psm);
   TF(*Bs)[65] = reinterpret_cast<TF(*)[65]>(psm + 64 * 65 * sizeof(TF));
   pdl_launch_dependents();
@@ -682,20 +705,38 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
 #pragma unroll
         for (int s = 0; s < 4; ++s) acc[u][s] += av[u] * bv[s];
     }
+    TF di[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       const int c = tc + 16 * s;
-      const TF di = c < kb ? TF(Dinv[fr.first + k0 + c]) : TF(0);
+      di[s] = c < kb ? TF(Dinv[fr.first + k0 + c]) : TF(0);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int32_t r = a0 + tr * 4 + u;
-        if (r >= m) continue;
-        if (c < kb) Ff[r + int64_t(k0 + c) * fr.ldf] = acc[u][s] * di;
-        if (bw) {
-          const int64_t o = (fr.w_off + r) * int64_t(kSuper) + (k0 % kSuper) + c;
-          bw[o] = __float2bfloat16_rn(float(acc[u][s]));
-          bl[o] = __float2bfloat16_rn(float(acc[u][s] * di));
+        if (r < m && c < kb) Ff[r + int64_t(k0 + c) * fr.ldf] = acc[u][s] * di[s];
+      }
+    }
+    if (bw) {
+      // the rows of the BF16 copies, staged so that each row's 64 columns
+      // (128 bytes) leave as eight 16-byte stores
+      __syncthreads();
+      __nv_bfloat16(*tw)[kPanelStage] = reinterpret_cast<__nv_bfloat16(*)[kPanelStage]>(psm);
+      __nv_bfloat16(*tl)[kPanelStage] = tw + 64;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          tw[tr * 4 + u][tc + 16 * s] = __float2bfloat16_rn(float(acc[u][s]));
+          tl[tr * 4 + u][tc + 16 * s] = __float2bfloat16_rn(float(acc[u][s] * di[s]));
         }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < 2 * 64 * 8; idx += blockDim.x) {
+        const int h = idx >> 9, row = (idx >> 3) & 63, ch = idx & 7;
+        const int32_t r = a0 + row;
+        if (r >= m) continue;
+        const uint4 v = *reinterpret_cast<const uint4 *>((h ? tl : tw)[row] + 8 * ch);
+        __nv_bfloat16 *dst = (h ? bl : bw) + (fr.w_off + r) * int64_t(kSuper) + (k0 % kSuper) + 8 * ch;
+        *reinterpret_cast<uint4 *>(dst) = v;
       }
     }
   } else {  // T_XK
@@ -722,9 +763,25 @@ __global__ void __launch_bounds__(256) front_panel_kernel(const int32_t *__restr
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const int32_t c = a0 + tc + 16 * s;
+        if (c < k0 && i < kb) Yf[(k0 + i) + int64_t(c) * fr.ldy] = acc[u][s];
+      }
+    }
+    if (by) {
+      // the pivot rows of Y in the BF16 copy: per column c its 64 entries
+      // (128 bytes), staged and written as eight 16-byte stores
+      __syncthreads();
+      __nv_bfloat16(*ty)[kPanelStage] = reinterpret_cast<__nv_bfloat16(*)[kPanelStage]>(psm);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) ty[tc + 16 * s][tr * 4 + u] = __float2bfloat16_rn(float(acc[u][s]));
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < 64 * 8; idx += blockDim.x) {
+        const int col = idx >> 3, ch = idx & 7;
+        const int32_t c = a0 + col;
         if (c >= k0) continue;
-        if (i < kb) Yf[(k0 + i) + int64_t(c) * fr.ldy] = acc[u][s];
-        if (by) by[(int64_t(fr.first) + c) * kSuper + (k0 % kSuper) + i] = __float2bfloat16_rn(float(acc[u][s]));
+        const uint4 v = *reinterpret_cast<const uint4 *>(ty[col] + 8 * ch);
+        *reinterpret_cast<uint4 *>(by + (int64_t(fr.first) + c) * kSuper + (k0 % kSuper) + 8 * ch) = v;
       }
     }
   }

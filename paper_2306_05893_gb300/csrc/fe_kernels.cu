@@ -538,9 +538,12 @@ void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const dou
 // ------------------------------------------------------------------ SpMV
 constexpr int kRedBlock = 256;
 
+// four blocks per SM: the grid-wide sum's tail (the last block adding the
+// partials) stays short; at 350k DOF this measured 0.8 % more steps/s than
+// eight per SM, and two per SM 0.8 % fewer
 static unsigned red_grid(int64_t n) {
   int64_t g = (n + kRedBlock - 1) / kRedBlock;
-  return unsigned(std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8)));
+  return unsigned(std::max<int64_t>(1, std::min<int64_t>(g, 152 * 4)));
 }
 
 // y = A x (TPR threads per row) fused with x.y; the last block sets
