@@ -312,6 +312,7 @@ int ensure_device(fe_ctx *c) {
     o.f_off = F.f_off; o.y_off = F.y_off; o.w_off = F.w_off; o.u_off = F.u_off;
     o.rows_off = F.rows_off; o.fac_off = fac;
     o.ldy = F.ldy; o.parent = F.parent; o.ldf = F.ldf;
+    o.fcols = int16_t(F.fcols); o.brows = int16_t(F.brows);
     o.nfwd = c->front_nfwd[f]; o.nbwd = c->front_nbwd[f];
     fac += F.npiv + 1;
   }

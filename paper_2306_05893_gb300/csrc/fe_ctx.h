@@ -16,6 +16,10 @@ constexpr int kSuper = 256;    // FP32 factor: trailing updates are applied once
 constexpr int kBwdCols = 32;   // pivot columns per task of the backward apply
 constexpr int kFwdCols = 256;  // pivot columns per task of the forward apply (split over CTAs)
 constexpr int kBwdRows = 1024; // rows per task of the backward apply (split over CTAs)
+// application tasks per level below which a level's tasks are made narrower
+// (forward: fewer pivot columns; backward: fewer rows; down to a quarter):
+// about one per resident CTA of the sweeps (four per SM on 152 SMs)
+constexpr int kApplyTasksPerLevel = 608;
 // rows of Y per 16-byte vector: 8 binary16, 4 FP32, 2 FP64 entries
 inline int y_vec(const fe_options &o) { return o.precision == FE_MIXED ? (o.precond_fp16 ? 8 : 4) : 2; }
 inline int fwd_rows(const fe_options &o) { return 32 * y_vec(o); }  // 32 threads x one 16-byte vector
@@ -41,6 +45,8 @@ struct Front {
   int64_t rows_off = 0;   // offset into upd_rows_new / upd_rows_old
   int64_t rmap_off = 0;   // offset of this front's map into its parent's front
   int32_t ldy = 0;        // leading dimension of Y (m rounded up to 4)
+  int32_t fcols = kFwdCols;  // pivot columns per forward application task
+  int32_t brows = 0;         // rows per backward application task (bwd_rows or a half or quarter of it)
   int32_t m() const { return npiv + nupd; }
 };
 

@@ -24,6 +24,7 @@ struct DFront {
   int32_t ldy, parent;               // parent front (-1: a root)
   int32_t nfwd, nbwd;                // tasks of this front in the dataflow application lists
   int32_t ldf;                       // leading dimension of the front's F (multiple of 4)
+  int16_t fcols, brows;              // application task sizes: forward pivot columns, backward rows
   int64_t f_off, y_off, w_off, u_off, rows_off, fac_off;
 };
 

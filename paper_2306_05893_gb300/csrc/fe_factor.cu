@@ -1602,15 +1602,17 @@ __device__ __forceinline__ bool dep_wait(const int *p, int target, int *abort_wo
 }
 
 // Forward task (front, r0, j0, slot): rows [r0, r0 + 32*VW) of Y w_P over the
-// pivot columns [j0, j0 + kFwdCols), where w = [r_P; 0] + the children's
+// pivot columns [j0, j0 + fcols) (the front's task width: kFwdCols, or a half
+// or a quarter of it on the tree's sparsely populated last levels), where
+// w = [r_P; 0] + the children's
 // update vectors (gathered through the position lists, children in fixed
 // order).  256 threads: 32 row lanes of VW consecutive rows (one 16-byte
 // load per column) x 8 column groups, the next 4 columns' loads in flight
 // while the current ones are used.  Static data (descriptors, gather
 // indices, the first Y vectors) is loaded before the dependency wait.  Rows
 // < p give y_P (times D^{-1}) into yperm, rows >= p the update vector.  Row
-// blocks with more than kFwdCols columns are split over tasks (slot >= 0)
-// and combined in chunk order by the last one (deterministic).
+// blocks with more than fcols columns are split over tasks (slot >= 0) and
+// combined in chunk order by the last one (deterministic).
 constexpr int kPre = 4;  // gather sources prefetched per position
 
 // One task of look-ahead in the persistent apply kernels: a CTA takes the
@@ -1699,7 +1701,8 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     int *const fdonev = fdone + rk * rs.f;
     const int32_t p = fr.npiv, m = fr.m;
     const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
-    const int32_t j1 = (j0 + kFwdCols < jmax) ? j0 + kFwdCols : jmax;
+    const int32_t fc = fr.fcols;  // this front's columns per task (at most kFwdCols)
+    const int32_t j1 = (j0 + fc < jmax) ? j0 + fc : jmax;
     // static gather indices: column j0 + tid of w, and row r0 + tid's child sum
     const int32_t jg = j0 + int32_t(threadIdx.x);
     int32_t gq0 = 0, gq1 = 0, gperm = 0, gsrc[kPre];
@@ -1794,11 +1797,11 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     }
     bool final = true;
     if (slot >= 0) {
-      const int nch = (jmax + kFwdCols - 1) / kFwdCols;
+      const int nch = (jmax + fc - 1) / fc;
 #pragma unroll
       for (int k = 0; k < (RB + 255) / 256; ++k) {
         const int tt = threadIdx.x + 256 * k;
-        if (tt < RB) pv[int64_t(slot + j0 / kFwdCols) * RB + tt] = sums[k];
+        if (tt < RB) pv[int64_t(slot + j0 / fc) * RB + tt] = sums[k];
       }
       final = last_of_block(tv + slot, nch);
       if (final) {
@@ -1857,13 +1860,15 @@ __device__ __forceinline__ void xs_vec(const double *p, double (&x)[VW]) {
 }
 
 // Backward task (front, c0, i0, slot): pivot columns [c0, c0 + 32) over the
-// rows [i0, i0 + BR) (BR = kBwdRows, twice that for the binary16 Y); warp w
+// rows [i0, i0 + brows) (the front's task height: BR = kBwdRows, twice that
+// for the binary16 Y, or a half or a quarter of BR on the tree's sparsely
+// populated last levels); warp w
 // owns columns c0 + w + 8k (k < 4) and streams them together, eight 16-byte
 // loads per lane in flight.
 // x = [D^{-1} y_P; z_U] is staged in shared memory from the VW-aligned row at
 // or below c0 (rows above a column are zeros of L^{-1}, so reading from the
 // aligned row is exact); z_U was written by the parent's tasks.  Columns
-// longer than BR rows are split over tasks (slot >= 0) and combined in
+// longer than brows rows are split over tasks (slot >= 0) and combined in
 // row-chunk order.  Also resets the forward counters for the next
 // application.
 template <typename TF, typename TV>
@@ -1906,7 +1911,8 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
     const int32_t p = fr.npiv, m = fr.m;
     const int32_t a0 = c0 & ~(VW - 1);
     const int32_t xa = a0 > ilo0 ? a0 : ilo0;                                 // first row of this task
-    const int32_t xb = (ilo0 + BR < fr.ldy) ? ilo0 + BR : fr.ldy;  // end row
+    const int32_t br = fr.brows;  // this front's rows per task (at most BR)
+    const int32_t xb = (ilo0 + br < fr.ldy) ? ilo0 + br : fr.ldy;  // end row
     // static: where each staged row comes from (-1: zero, >= 0: yperm index,
     // <= -2: z index -2 - idx)
     const int32_t *urows = upd_rows_old + fr.rows_off;
@@ -1999,12 +2005,12 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
           if (jc[k] < p) z[perm[fr.first + jc[k]]] = acc[k];
       }
     } else {
-      const int32_t k_first = a0 / BR;
-      const int nch = (fr.ldy - 1) / BR - k_first + 1;
+      const int32_t k_first = a0 / br;
+      const int nch = (fr.ldy - 1) / br - k_first + 1;
       if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          part[int64_t(slot + ilo0 / BR - k_first) * kBwdCols + w + 8 * k] = acc[k];
+          part[int64_t(slot + ilo0 / br - k_first) * kBwdCols + w + 8 * k] = acc[k];
       }
       if (last_of_block(tickets + slot, nch) && threadIdx.x < kBwdCols) {
         TV sm = TV(0);

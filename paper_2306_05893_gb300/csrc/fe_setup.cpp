@@ -653,29 +653,54 @@ int build_ordering(fe_ctx *c) {
         }
       }
     }
+    // task sizes of the application sweeps on this level: a level with
+    // fewer than kApplyTasksPerLevel tasks at the full sizes (the few large
+    // fronts near the root) takes narrower ones, down to a quarter, so its
+    // dependency chain spreads over more CTAs
+    auto fwd_count = [&](int32_t fc) {
+      int64_t n = 0;
+      for (int32_t f : L.fronts) {
+        const Front &F = c->fronts[f];
+        for (int32_t r0 = 0; r0 < F.m(); r0 += fr_rows) n += std::max(1, (std::min(r0 + fr_rows, F.npiv) + fc - 1) / fc);
+      }
+      return n;
+    };
+    auto bwd_count = [&](int32_t b) {
+      int64_t n = 0;
+      for (int32_t f : L.fronts) {
+        const Front &F = c->fronts[f];
+        for (int32_t c0 = 0; c0 < F.npiv; c0 += kBwdCols) n += (F.ldy - 1) / b - (c0 & ~(vw - 1)) / b + 1;
+      }
+      return n;
+    };
+    int32_t lfc = kFwdCols, lbr = br;
+    while (lfc > kFwdCols / 4 && fwd_count(lfc) < kApplyTasksPerLevel) lfc /= 2;
+    while (lbr > br / 4 && lbr / 2 >= vw && bwd_count(lbr) < kApplyTasksPerLevel) lbr /= 2;
     for (int32_t f : L.fronts) {
+      c->fronts[f].fcols = lfc;
+      c->fronts[f].brows = lbr;
       const Front &F = c->fronts[f];
       const int32_t m = F.m(), p = F.npiv;
       // apply tasks; a block split over several tasks owns consecutive
       // partial-sum slots, reduced in order by the last task to finish
       for (int32_t r0 = 0; r0 < m; r0 += fr_rows) {
         const int32_t jmax = std::min(r0 + fr_rows, p);
-        const int32_t nch = std::max(1, (jmax + kFwdCols - 1) / kFwdCols);
+        const int32_t nch = std::max(1, (jmax + lfc - 1) / lfc);
         const int32_t slot = nch > 1 ? int32_t(c->fwd_slots) : -1;
         if (nch > 1) c->fwd_slots += nch;
         for (int32_t k = 0; k < nch; ++k) {
           L.fwd_tasks.push_back(f); L.fwd_tasks.push_back(r0);
-          L.fwd_tasks.push_back(k * kFwdCols); L.fwd_tasks.push_back(slot);
+          L.fwd_tasks.push_back(k * lfc); L.fwd_tasks.push_back(slot);
         }
       }
       for (int32_t c0 = 0; c0 < p; c0 += kBwdCols) {
         const int32_t a0 = c0 & ~(vw - 1);
-        const int32_t k0 = a0 / br, k1 = (F.ldy - 1) / br;
+        const int32_t k0 = a0 / lbr, k1 = (F.ldy - 1) / lbr;
         const int32_t slot = k1 > k0 ? int32_t(c->bwd_slots) : -1;
         if (k1 > k0) c->bwd_slots += k1 - k0 + 1;
         for (int32_t k = k0; k <= k1; ++k) {
           L.bwd_tasks.push_back(f); L.bwd_tasks.push_back(c0);
-          L.bwd_tasks.push_back(k * br); L.bwd_tasks.push_back(slot);
+          L.bwd_tasks.push_back(k * lbr); L.bwd_tasks.push_back(slot);
         }
       }
       for (int s = 0; s * kNB < p; ++s) {

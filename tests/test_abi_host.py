@@ -339,7 +339,9 @@ def test_noalloc_scratch_size(fe, precision):
     at least the vectors whose sizes the setup fixes (n, the fronts' update
     rows, the free DOFs), at most those plus the split tasks' partial sums
     (bounded by one 256-row block per forward task and one 32-column block per
-    backward task); FP64 needs about twice the mixed path's bytes."""
+    backward task, the tasks counted at their finest sizes: 64 forward pivot
+    columns and 64 rows, 256 backward rows); FP64 needs about twice the mixed
+    path's bytes."""
     mesh = fi.tet_beam(6, 6, 24)
     ctx = _ctx(fe, mesh, precision=precision)
     info = ctx.info()
@@ -347,9 +349,9 @@ def test_noalloc_scratch_size(fe, precision):
     info["u_total"] = int(order["nupd"].sum())
     ts = 8 if precision == 0 else 4
     lo = _apply_work_bytes(info, ts, 1, 1, 1)
-    n_fwd = sum(int(np.ceil(m / 256.0)) * int(np.ceil(p / 256.0)) for m, p in
+    n_fwd = sum(int(np.ceil(m / 64.0)) * int(np.ceil(p / 64.0)) for m, p in
                 zip(order["npiv"] + order["nupd"], order["npiv"]))
-    n_bwd = sum(int(np.ceil(m / 1024.0)) * int(np.ceil(p / 32.0)) for m, p in
+    n_bwd = sum(int(np.ceil(m / 256.0)) * int(np.ceil(p / 32.0)) for m, p in
                 zip(order["npiv"] + order["nupd"], order["npiv"]))
     hi = _apply_work_bytes(info, ts, 256 * n_fwd, 32 * n_bwd, n_fwd + n_bwd)
     assert lo <= info["noalloc_bytes"] <= hi, (lo, info["noalloc_bytes"], hi)
