@@ -636,6 +636,7 @@ def main():
     stage_ms, stage_calls, launches = ctx.stage_times()
     update_flops = ctx.update_flops()
     update_bf16_flops = ctx.update_bf16_flops()
+    update_bf16_tiles = ctx.update_bf16_tiles()
     main_sum = sum(stage_ms[k] for k in ("element", "assembly", "apply", "spmv", "vector", "residual",
                                          "integrate", "pcg_graph")) / K
     timed_stages = {k: v / K for k, v in stage_ms.items()}
@@ -720,6 +721,13 @@ def main():
                             "apply-operator updates); launched on the low-priority factor stream, timed live "
                             "with CUDA events there",
                     "eager_updates": tc_roof}
+        # the same launches against HBM: each output tile of F or Y is read
+        # and written once by its reduce-add (the BF16 operands come from L2)
+        tbytes = update_bf16_tiles / bcalls * 128 * 128 * 4 * 2
+        tgbs = tbytes / (bms / 1e3) / 1e9 if bms > 0 else 0.0
+        roofline["hbm_view"] = {"bytes_per_launch": int(tbytes), "achieved": tgbs, "peak": hbm, "unit": "GB/s",
+                                "frac": tgbs / hbm,
+                                "note": "output-tile read-modify-write only (128 KB per 128x128 FP32 tile)"}
     elif wl.precision:
         roofline = tc_roof
     else:

@@ -407,6 +407,9 @@ int fe_get_stage_times(fe_ctx *ctx, double *ms, int64_t *calls, int64_t *kernel_
 int fe_get_update_flops(fe_ctx *ctx, double *flops);
 /* The same for the launches timed as FE_STAGE_FACTOR_UPDATE_BF16. */
 int fe_get_update_bf16_flops(fe_ctx *ctx, double *flops);
+/* The 128 x 128 output tiles of those launches (each read and written once
+ * by a TMA reduce-add: 128 KB of DRAM traffic for F or Y per tile). */
+int fe_get_update_bf16_tiles(fe_ctx *ctx, int64_t *tiles);
 int fe_reset_stage_times(fe_ctx *ctx);
 
 /* Replaces the material parameters ([n_elems * 3], element-major, the layout

@@ -269,6 +269,12 @@ def fe_get_update_bf16_flops(ctx):
     return f.value
 
 
+def fe_get_update_bf16_tiles(ctx):
+    t = ct.c_int64()
+    _check(ctx, load().fe_get_update_bf16_tiles(ctx, ct.byref(t)))
+    return t.value
+
+
 def fe_reset_stage_times(ctx):
     _check(ctx, load().fe_reset_stage_times(ctx))
 
@@ -440,6 +446,9 @@ class FEContext:
 
     def update_bf16_flops(self):
         return fe_get_update_bf16_flops(self.ctx)
+
+    def update_bf16_tiles(self):
+        return fe_get_update_bf16_tiles(self.ctx)
 
     def reset_stage_times(self):
         fe_reset_stage_times(self.ctx)

@@ -87,6 +87,7 @@ SIGNATURES = {
     "fe_reset_stage_times": (ct.c_int, [CTX]),
     "fe_get_update_flops": (ct.c_int, [CTX, DP]),
     "fe_get_update_bf16_flops": (ct.c_int, [CTX, DP]),
+    "fe_get_update_bf16_tiles": (ct.c_int, [CTX, P(ct.c_int64)]),
     "fe_set_params": (ct.c_int, [CTX, ct.c_void_p]),
     "fe_adjoint": (ct.c_int, [CTX, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "fe_clear_checkpoints": (ct.c_int, [CTX]),

@@ -1455,6 +1455,12 @@ int fe_get_update_bf16_flops(fe_ctx *c, double *flops) {
   return FE_OK;
 }
 
+int fe_get_update_bf16_tiles(fe_ctx *c, int64_t *tiles) {
+  if (!c || !tiles) return FE_ERR_ARG;
+  *tiles = c->dev ? c->dev->update_bf16_tiles : 0;
+  return FE_OK;
+}
+
 int fe_reset_stage_times(fe_ctx *c) {
   if (!c) return FE_ERR_ARG;
   DeviceState *d = c->dev;
@@ -1469,6 +1475,7 @@ int fe_reset_stage_times(fe_ctx *c) {
   d->launches = 0;
   d->update_flops = 0.0;
   d->update_bf16_flops = 0.0;
+  d->update_bf16_tiles = 0;
   return FE_OK;
 }
 

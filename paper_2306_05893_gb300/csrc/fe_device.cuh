@@ -188,6 +188,7 @@ struct DeviceState {
   mutable int64_t launches = 0;
   double update_flops = 0.0;            // algorithmic flops of the timed update launches
   double update_bf16_flops = 0.0;       // the same for the BF16 superpanel-end launches
+  int64_t update_bf16_tiles = 0;        // and their 128 x 128 output tiles
 
   // batched solve: member DOF ranges, row -> member, per-member scalars
   int64_t *seg_dof = nullptr;

@@ -2088,7 +2088,10 @@ static void factor_levels(fe_ctx *c, DeviceState *d, int buf, const TF *Afac, cu
       if (L.tend_n[st] && bw) {
         d->launches++;
         const int ev = stage_begin(c, FE_STAGE_FACTOR_UPDATE_BF16, s);
-        if (ev >= 0) d->update_bf16_flops += L.tend_flops[st];
+        if (ev >= 0) {
+          d->update_bf16_flops += L.tend_flops[st];
+          d->update_bf16_tiles += L.tend_n[st];
+        }
         launch_pdl(front_update_bf16_kernel, unsigned(L.tend_n[st]), kBfThreads, bf16_update_smem(), s,
                    d->tasks + L.tend_off[st], d->fronts, bmaps, fmaps, ycmaps, d->flags);
         stage_end(c, ev, s);
