@@ -280,8 +280,19 @@ int ensure_device(fe_ctx *c) {
   FE_TRY(dalloc(c, d, &d->fe, size_t(E) * 3 * npe));
   FE_TRY(dallocv(c, d, &d->Ke, size_t(E) * ke * (c->opt.element_fp64 ? sizeof(double) : ts)));
   FE_TRY(dallocv(c, d, &d->A, size_t(c->nnz) * ts));
-  if (fp32) FE_TRY(dalloc(c, d, &d->A64, size_t(c->nnz)));
-  else d->A64 = static_cast<double *>(d->A);
+  if (fp32) {
+    FE_TRY(dalloc(c, d, &d->A2, size_t(c->nnz)));
+    FE_TRY(dalloc(c, d, &d->x2, n));
+    FE_CUDA_TRY(cudaMemset(d->x2, 0, n * sizeof(float2)));
+    std::vector<float2> bm2(c->bmass.size());
+    for (size_t k = 0; k < bm2.size(); ++k) {
+      const float h = float(c->bmass[k]);
+      bm2[k] = make_float2(h, float(c->bmass[k] - double(h)));
+    }
+    FE_TRY(upload(c, d, &d->bmass2, bm2));
+  } else {
+    d->A64 = static_cast<double *>(d->A);
+  }
   FE_TRY(dallocv(c, d, &d->Afac, size_t(c->nnz) * ts));
   FE_TRY(dallocv(c, d, &d->vz, n * ts));
   FE_TRY(dallocv(c, d, &d->vp, n * ts));
@@ -579,7 +590,7 @@ static cudaError_t capture_pcg(fe_ctx *c, bool fp32, void *X, void *R, cudaStrea
 // Captures the solve and the guarded integration of a step for the current
 // factor buffer.  FP64: init (x = 0, r = b), PCG.  Mixed: init; WHILE
 // (S_ODONE == 0, S_ITERS < max_iters) { inner init (d = 0, r32 = r); inner
-// PCG to inner_tol; x += d; r = b - A64 x }.
+// PCG to inner_tol; x += d; r = b - A x (FP64-accurate: A2, x2 in double-float) }.
 static int build_step_graph(fe_ctx *c, DeviceState::StepGraph *sg) {
   DeviceState *d = c->dev;
   const bool fp32 = mixed(c);
@@ -604,7 +615,7 @@ static int build_step_graph(fe_ctx *c, DeviceState::StepGraph *sg) {
       e = capture_pcg(c, false, d->x, d->r, s, s2, sg);
     } else if (e == cudaSuccess) {
       launch_init_solve(c, d, false, d->x, d->r, d->b, c->opt.tol, true, s, warm);  // x = 0 (or kept), r = b
-      if (warm) launch_residual(c, d, true, s);  // r = b - A64 x
+      if (warm) launch_residual(c, d, true, s);  // r = b - A x
       cudaGraphConditionalHandle ho;
       e = cudaGraphConditionalHandleCreate(&ho, capturing_graph(s), 0, 0);
       if (e == cudaSuccess) {
@@ -716,7 +727,7 @@ static int build_batch_graph(fe_ctx *c, DeviceState::StepGraph *sg) {
           DeviceState::StepGraph inner{};
           e = capture_pcg_batch(c, true, d->vd, d->vr, s2, s3, &inner);
           launch_refine_update(c, d, s2);
-          launch_batch_spmv(c, d, true, d->x, d->r, d->b, s2);  // r = b - A64 x (FP64)
+          launch_batch_spmv(c, d, true, d->x, d->r, d->b, s2);  // r = b - A x (FP64-accurate)
           launch_seg_dot64(c, d, d->r, d->r, SEG_ORR, 0.0, s2);
           launch_seg_cond(c, d, ho, 1, s2);
           sg->k_outer = d->launches - l0 - inner.k_inner;
@@ -920,7 +931,7 @@ int solve_batch(fe_ctx *c, fe_step_info *info) {
     for (;;) {
       if (sweeps > 0) {
         Stage st(c, FE_STAGE_RESIDUAL, s);
-        launch_batch_spmv(c, d, true, d->x, d->r, d->b, s);  // r = b - A64 x (FP64)
+        launch_batch_spmv(c, d, true, d->x, d->r, d->b, s);  // r = b - A x (FP64-accurate)
         launch_seg_dot64(c, d, d->r, d->r, SEG_ORR, 0.0, s);
       }
       FE_TRY(read_batch_scalars(c));
@@ -1111,7 +1122,8 @@ int fe_assemble(fe_ctx *c, const double *p_ext, double *A_vals, double *b) {
   if (A_vals) {
     double *tmp = nullptr;
     FE_CUDA_TRY(cudaMalloc(&tmp, c->nnz * sizeof(double)));
-    launch_convert(d->A64, false, tmp, false, c->nnz, d->stream);  // the FP64 copy of A
+    if (d->A2) launch_pair_to_double(d->A2, tmp, c->nnz, d->stream);  // the float-pair A, as doubles
+    else launch_convert(d->A64, false, tmp, false, c->nnz, d->stream);
     cudaError_t e = cudaMemcpyAsync(A_vals, tmp, c->nnz * sizeof(double),
                                     c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                     d->stream);

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "fe_device.cuh"
+#include "fe_df.cuh"
 
 namespace fe {
 
@@ -41,9 +42,9 @@ __global__ void __launch_bounds__(256) seg_dot_kernel(const TV *__restrict__ x, 
   const int b = blockIdx.x;
   double *s = bs + int64_t(b) * B_COUNT;
   const int64_t d0 = seg_dof[b], d1 = seg_dof[b + 1];
-  double acc = 0.0;
-  for (int64_t i = d0 + threadIdx.x; i < d1; i += 256) acc += double(x[i]) * double(y[i]);
-  const double tot = cta_sum<256>(acc, sh);
+  DotAcc<TV> acc;
+  for (int64_t i = d0 + threadIdx.x; i < d1; i += 256) acc.add(x[i], y[i]);
+  const double tot = cta_sum<256>(acc.value(), sh);
   if (threadIdx.x != 0) return;
   switch (mode) {
     case SEG_PQ:
@@ -98,9 +99,11 @@ __global__ void __launch_bounds__(256) seg_dot_kernel(const TV *__restrict__ x, 
 // x = 0, r = rhs (cast); members already converged keep r = 0 so they stay put
 template <typename TV>
 __global__ void seg_init_kernel(int64_t n, TV *__restrict__ x, TV *__restrict__ r, const double *__restrict__ rhs,
-                                const int32_t *__restrict__ row_seg, const double *__restrict__ bs, int inner) {
+                                const int32_t *__restrict__ row_seg, const double *__restrict__ bs, int inner,
+                                float2 *__restrict__ x2) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     x[i] = TV(0);
+    if (x2) x2[i] = make_float2(0.f, 0.f);  // the outer x's float-pair mirror (mixed path)
     const bool frozen = inner && bs[int64_t(row_seg[i]) * B_COUNT + B_ODONE] != 0.0;
     r[i] = frozen ? TV(0) : TV(rhs[i]);
   }
@@ -211,6 +214,111 @@ __global__ void __launch_bounds__(256) batch_csr_kernel(const int2 *__restrict__
   }
 }
 
+// y = b - A x in the mixed path (A2 and x2 as float pairs, double-float
+// products and sums, y in FP64): the node-block and CSR forms of the two
+// kernels above.
+template <int LPN>
+__global__ void __launch_bounds__(256) batch_bres_df_kernel(const int2 *__restrict__ blocks,
+                                                            const int32_t *__restrict__ rowptr,
+                                                            const int32_t *__restrict__ bptr,
+                                                            const int32_t *__restrict__ bcol,
+                                                            const int8_t *__restrict__ fixed_row,
+                                                            const float2 *__restrict__ A, const float2 *__restrict__ x,
+                                                            const double *__restrict__ b, double *__restrict__ y) {
+  const int2 blk = blocks[blockIdx.x];
+  const int sub = threadIdx.x % LPN;
+  for (int64_t n0 = blk.x + int64_t(threadIdx.x / 32) * (32 / LPN); n0 < blk.y; n0 += 256 / LPN) {
+    const int64_t nd = n0 + (threadIdx.x % 32) / LPN;  // the loop bound is warp-uniform
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+    bool fixed = true;
+    if (nd < blk.y) {
+      fixed = fixed_row[3 * nd] != 0;
+      if (!fixed) {
+        const int32_t k0 = bptr[nd], k1 = bptr[nd + 1];
+        const int32_t r0 = rowptr[3 * nd], r1 = rowptr[3 * nd + 1], r2 = rowptr[3 * nd + 2];
+        for (int32_t k = k0 + sub; k < k1; k += LPN) {
+          const int64_t cc = 3 * int64_t(bcol[k]);
+          const float2 x0 = x[cc], x1 = x[cc + 1], x2 = x[cc + 2];
+          const int32_t o = 3 * (k - k0);
+          df_fma_to(h0, l0, A[r0 + o], x0);
+          df_fma_to(h0, l0, A[r0 + o + 1], x1);
+          df_fma_to(h0, l0, A[r0 + o + 2], x2);
+          df_fma_to(h1, l1, A[r1 + o], x0);
+          df_fma_to(h1, l1, A[r1 + o + 1], x1);
+          df_fma_to(h1, l1, A[r1 + o + 2], x2);
+          df_fma_to(h2, l2, A[r2 + o], x0);
+          df_fma_to(h2, l2, A[r2 + o + 1], x1);
+          df_fma_to(h2, l2, A[r2 + o + 2], x2);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = LPN / 2; o > 0; o >>= 1) {
+      df_shfl_add<LPN>(h0, l0, o);
+      df_shfl_add<LPN>(h1, l1, o);
+      df_shfl_add<LPN>(h2, l2, o);
+    }
+    if (sub < 3 && nd < blk.y) {
+      const int64_t rw = 3 * nd + sub;
+      float hi = sub == 0 ? h0 : (sub == 1 ? h1 : h2), lo = sub == 0 ? l0 : (sub == 1 ? l1 : l2);
+      if (fixed) {
+        hi = lo = 0.f;
+        df_fma_to(hi, lo, A[rowptr[rw]], x[rw]);
+      }
+      y[rw] = b[rw] - df_value(hi, lo);
+    }
+  }
+}
+
+template <int TPR>
+__global__ void __launch_bounds__(256) batch_csr_res_df_kernel(const int2 *__restrict__ blocks,
+                                                               const int32_t *__restrict__ rowptr,
+                                                               const int32_t *__restrict__ colind,
+                                                               const float2 *__restrict__ A,
+                                                               const float2 *__restrict__ x,
+                                                               const double *__restrict__ b, double *__restrict__ y) {
+  const int2 blk = blocks[blockIdx.x];
+  const int64_t rb = 3 * int64_t(blk.x), re = 3 * int64_t(blk.y);
+  const int sub = threadIdx.x % TPR;
+  for (int64_t r0 = rb + int64_t(threadIdx.x / 32) * (32 / TPR); r0 < re; r0 += 256 / TPR) {
+    const int64_t row = r0 + (threadIdx.x % 32) / TPR;
+    float hi = 0.f, lo = 0.f;
+    if (row < re) {
+      const int32_t k1 = rowptr[row + 1];
+      for (int32_t k = rowptr[row] + sub; k < k1; k += TPR) df_fma_to(hi, lo, A[k], x[colind[k]]);
+    }
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) df_shfl_add<TPR>(hi, lo, o);
+    if (sub == 0 && row < re) y[row] = b[row] - df_value(hi, lo);
+  }
+}
+
+void launch_class_res_df(const DeviceState::SpmvClass &k, const DeviceState *d, const double *b, double *y,
+                         cudaStream_t s) {
+  if (!k.nblocks) return;
+  const unsigned g = unsigned(k.nblocks);
+  if (k.lpn < 0) {  // CSR, -lpn threads per row
+    if (k.lpn == -16)
+      batch_csr_res_df_kernel<16><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->colind, d->A2, d->x2, b, y);
+    else
+      batch_csr_res_df_kernel<8><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->colind, d->A2, d->x2, b, y);
+    return;
+  }
+  switch (k.lpn) {
+    case 4:
+      batch_bres_df_kernel<4><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->bptr, d->bcol, d->fixed_row, d->A2, d->x2, b, y);
+      break;
+    case 8:
+      batch_bres_df_kernel<8><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->bptr, d->bcol, d->fixed_row, d->A2, d->x2, b, y);
+      break;
+    case 32:
+      batch_bres_df_kernel<32><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->bptr, d->bcol, d->fixed_row, d->A2, d->x2, b, y);
+      break;
+    default:
+      batch_bres_df_kernel<16><<<g, 256, 0, s>>>(k.blocks, d->rowptr, d->bptr, d->bcol, d->fixed_row, d->A2, d->x2, b, y);
+  }
+}
+
 template <typename TA, typename TV, int MODE>
 void launch_class(const DeviceState::SpmvClass &k, const DeviceState *d, const TA *A, const TV *x, const double *b,
                   TV *y, cudaStream_t s) {
@@ -240,7 +348,9 @@ void launch_class(const DeviceState::SpmvClass &k, const DeviceState *d, const T
 
 void run_class(const fe_ctx *c, const DeviceState *d, const DeviceState::SpmvClass &k, bool fp32, const void *x,
                void *y, const double *b, cudaStream_t s) {
-  if (b)
+  if (b && d->A2)  // the mixed path's residual: A2 and the mirror x2 of x (= d->x)
+    launch_class_res_df(k, d, b, static_cast<double *>(y), s);
+  else if (b)
     launch_class<double, double, 1>(k, d, d->A64, static_cast<const double *>(x), b, static_cast<double *>(y), s);
   else if (fp32)
     launch_class<float, float, 0>(k, d, static_cast<const float *>(d->A), static_cast<const float *>(x), nullptr,
@@ -306,10 +416,10 @@ void launch_seg_init(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, 
   d->launches++;
   if (fp32)
     seg_init_kernel<float><<<grid_for(c->n), 256, 0, s>>>(c->n, (float *)x, (float *)r, rhs, d->row_seg, d->bscal,
-                                                          inner);
+                                                          inner, nullptr);
   else
     seg_init_kernel<double><<<grid_for(c->n), 256, 0, s>>>(c->n, (double *)x, (double *)r, rhs, d->row_seg,
-                                                           d->bscal, inner);
+                                                           d->bscal, inner, x == d->x ? d->x2 : nullptr);
 }
 
 void launch_seg_axpy(const fe_ctx *c, const DeviceState *d, bool fp32, void *x, void *r, const void *p,

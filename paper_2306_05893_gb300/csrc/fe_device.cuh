@@ -69,6 +69,7 @@ struct DeviceState {
   int32_t *node_ptr = nullptr, *node_src = nullptr;
   int32_t *bptr = nullptr, *bcol = nullptr, *bsrc_ptr = nullptr, *bsrc = nullptr;
   double *bmass = nullptr;
+  float2 *bmass2 = nullptr;        // mixed path: bmass as float pairs (the assembly's double-float mass)
 
   // state
   double *q = nullptr, *v = nullptr, *pext = nullptr, *acc = nullptr;
@@ -81,15 +82,21 @@ struct DeviceState {
   double *fe = nullptr;
   void *Ke = nullptr;
   // system: A in the matrix type (FP64, or FP32 in the mixed path: the inner
-  // SpMV and the snapshot the factor reads), its FP64 copy A64 in the mixed
-  // path (the refinement residual; equal to A in the FP64 path), b in FP64
+  // SpMV and the snapshot the factor reads), b in FP64.  The refinement
+  // residual's FP64-accurate A: A64 = A in the FP64 path; in the mixed path
+  // A2, the values as float pairs (hi, lo; fe_df.cuh), read by double-float
+  // residual kernels, and A64 null
   void *A = nullptr;
   double *A64 = nullptr;
+  float2 *A2 = nullptr;
   void *Afac = nullptr;
   double *b = nullptr;
 
   // PCG vectors (FP64 outer) and inner vectors (matrix type)
   double *x = nullptr, *r = nullptr;
+  // mixed path: the refinement iterate x as float pairs, written with x by
+  // the outer init and every refinement update, read by the residual
+  float2 *x2 = nullptr;
   void *vz = nullptr, *vp = nullptr, *vq = nullptr, *vr = nullptr, *vd = nullptr;
   double *scal = nullptr;          // [S_COUNT] device scalars
   double *partials = nullptr;      // [kMaxBlocks]
@@ -262,6 +269,7 @@ void launch_integrate_guarded(const fe_ctx *c, const DeviceState *d, bool fp32, 
 void launch_graph_cond(const fe_ctx *c, const DeviceState *d, cudaGraphConditionalHandle h, int mode,
                        cudaStream_t s);
 void launch_convert(const void *src, bool src32, void *dst, bool dst32, int64_t n, cudaStream_t s);
+void launch_pair_to_double(const float2 *src, double *dst, int64_t n, cudaStream_t s);  // dst = hi + lo
 
 // (fe_batch.cu)
 void launch_seg_dot(const fe_ctx *c, const DeviceState *d, bool fp32, const void *x, const void *y, int mode,

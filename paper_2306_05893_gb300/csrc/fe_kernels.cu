@@ -10,6 +10,7 @@
 #include <string>
 
 #include "fe_device.cuh"
+#include "fe_df.cuh"
 #include "fe_material.cuh"
 
 namespace fe {
@@ -383,15 +384,17 @@ void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool
 // incidence list.  Fixed nodes keep the lone unit diagonal and b = 0.
 //
 // FP64 path: every sum in FP64.  Mixed path (FP32 tangents): GB300's FP64
-// pipe issues at a small fraction of the FP32 rate, and a conversion plus an
-// FP64 add per gathered value made this kernel ALU-bound, so the block sums
-// are kept as double-float pairs (hi + lo, Knuth's TwoSum: the exact sum of
-// the FP32 values to about 2^-46), and A = cM M + cK K is formed in
-// double-float (Dekker's product through FMA for cK K); A is written rounded
-// to FP32 (the inner solve and the factor) and as double(hi) + double(lo)
-// (the FP64 copy the refinement residual uses).  The damping part of b is
-// summed in FP32 per lane (its terms carry the FP32 tangent's rounding
-// already) and reduced across the warp in FP64 with the forces.
+// pipe issues at a small fraction of the FP32 rate, so the kernel keeps FP64
+// work out of the per-block code: the block sums are double-float pairs
+// (hi + lo, Knuth's TwoSum: the exact sum of the FP32 values to about
+// 2^-46), A = cM M + cK K is formed in double-float (Dekker's product through
+// FMA for cK K and cM M, the block mass read as a float pair), and A is
+// written rounded to FP32 (the inner solve and the factor) and as the pair
+// itself (A2, the FP64-accurate copy the refinement residual reads in
+// double-float).  The damping part of b is summed in FP32 (its terms carry
+// the FP32 tangent's rounding already), the element forces in FP64; the
+// three rows' sums are reduced across the warp in one transposed reduction
+// (warp_sum3) instead of three.
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
   const float s = hi + x;
   const float bb = s - hi;
@@ -399,26 +402,49 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
   hi = s;
 }
 
+// Warp sum of three values at once: after exchanging halves (lane ^ 16:
+// lanes below 16 keep v0, v1, the others v2 and a zero) and quarters (lane ^
+// 8), each lane sums one value over its group of eight.  Lane l ends with the
+// total of v[(l >> 3) & 3] (v[3] = 0): lanes 0, 8 and 16 hold v0, v1, v2.
+// Six additions instead of fifteen; a fixed order, so deterministic.
+template <typename T>
+__device__ __forceinline__ T warp_sum3(T v0, T v1, T v2) {
+  const int lane = threadIdx.x & 31;
+  const bool up = (lane & 16) != 0;
+  T k0 = up ? v2 : v0, k1 = up ? T(0) : v1;
+  const T s0 = up ? v0 : v2, s1 = up ? v1 : T(0);
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  const bool hi8 = (lane & 8) != 0;
+  T k = hi8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  return k;
+}
+
 template <typename TK, typename TA>
 __global__ void __launch_bounds__(256) assemble_block_kernel(
     int64_t n_nodes, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ bptr,
     const int32_t *__restrict__ bcol, const int32_t *__restrict__ bsrc_ptr, const int32_t *__restrict__ bsrc,
-    const double *__restrict__ bmass, const TK *__restrict__ Ke, const double *__restrict__ fe,
-    const int32_t *__restrict__ node_ptr, const int32_t *__restrict__ node_src,
+    const double *__restrict__ bmass, const float2 *__restrict__ bmass2, const TK *__restrict__ Ke,
+    const double *__restrict__ fe, const int32_t *__restrict__ node_ptr, const int32_t *__restrict__ node_src,
     const int8_t *__restrict__ fixed_row, const double *__restrict__ v, const double *__restrict__ w,
     const double *__restrict__ p, double cM, double cK, double al, double bh, TA *__restrict__ A,
-    double *__restrict__ A64, double *__restrict__ b) {
+    float2 *__restrict__ A2, double *__restrict__ b) {
   constexpr bool DF = sizeof(TK) == 4;  // FP32 tangents: double-float sums
   const int lane = threadIdx.x & 31;
   const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
-  // cK as a float pair (cK = ckh + ckl to 2^-48)
+  // cK and cM as float pairs (c = ch + cl to 2^-48)
   const float ckh = float(cK), ckl = float(cK - double(ckh));
+  const float cmh = float(cM), cml = float(cM - double(cmh));
+  const float alf = float(al), bhf = float(bh);
   for (int64_t nd = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); nd < n_nodes; nd += warps) {
     const int64_t r0 = 3 * nd;
     if (fixed_row[r0]) {
       if (lane < 3) {
         A[rowptr[r0 + lane]] = TA(1);
-        if (A64) A64[rowptr[r0 + lane]] = 1.0;
+        if (A2) A2[rowptr[r0 + lane]] = make_float2(1.f, 0.f);
         b[r0 + lane] = 0.0;
       }
       continue;
@@ -428,7 +454,6 @@ __global__ void __launch_bounds__(256) assemble_block_kernel(
     float accf[3] = {0.f, 0.f, 0.f};
     for (int32_t k = bptr[nd] + lane; k < bptr[nd + 1]; k += 32) {
       const int32_t j1 = bsrc_ptr[k + 1];
-      const double mb = bmass[k];
       const int32_t bp = 3 * (k - bptr[nd]);
       const int64_t cn = 3 * int64_t(bcol[k]);
       if constexpr (DF) {
@@ -440,12 +465,13 @@ __global__ void __launch_bounds__(256) assemble_block_kernel(
 #pragma unroll
           for (int q = 0; q < 9; ++q) two_sum_acc(hi[q], lo[q], float(src[q]));
         }
-        // cM * mb once per block in FP64, as a float pair
-        const double m64 = cM * mb;
-        const float mh = float(m64), ml = float(m64 - double(mh));
-        const float alm = float(al * mb);
+        // cM mb in double-float: (cmh + cml)(mb.x + mb.y), the cml mb.y term
+        // (~2^-48 of the product) dropped
+        const float2 mb = bmass2[k];
+        const float mh = mb.x * cmh;
+        const float ml = fmaf(mb.x, cmh, -mh) + fmaf(mb.y, cmh, mb.x * cml);
+        const float alm = alf * mb.x;
         const float vv[3] = {float(v[cn]), float(v[cn + 1]), float(v[cn + 2])};
-        const float bhf = float(bh);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
 #pragma unroll
@@ -459,15 +485,16 @@ __global__ void __launch_bounds__(256) assemble_block_kernel(
               pl += ((ph - (s - bb)) + (mh - bb)) + ml;
               ph = s;
             }
-            const float sh = ph + pl;              // renormalise: sh = fl(ph + pl)
+            const float sh = ph + pl;  // renormalise: sh = fl(ph + pl)
             const float sl = pl - (sh - ph);
             A[rps[i] + bp + kk] = TA(sh);
-            A64[rps[i] + bp + kk] = double(sh) + double(sl);
+            A2[rps[i] + bp + kk] = make_float2(sh, sl);
             accf[i] += ((i == kk ? alm : 0.f) + bhf * hi[q]) * vv[kk];
           }
-          if (w) acc[i] += mb * w[cn + i];  // the M w term of a Newton correction
+          if (w) acc[i] += bmass[k] * w[cn + i];  // the M w term of a Newton correction
         }
       } else {
+        const double mb = bmass[k];
         double blk[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) blk[q] = 0.0;
@@ -485,31 +512,26 @@ __global__ void __launch_bounds__(256) assemble_block_kernel(
             const double Ks = blk[3 * i + kk];
             const double a = cM * Ms + cK * Ks;
             A[rps[i] + bp + kk] = TA(a);
-            if (A64) A64[rps[i] + bp + kk] = a;
+            if (A2) A2[rps[i] + bp + kk] = df_split(a);
             acc[i] += (al * Ms + bh * Ks) * vv[kk];
           }
           if (w) acc[i] += mb * w[cn + i];  // the M w term of a Newton correction
         }
       }
     }
-    double fs[3] = {0.0, 0.0, 0.0};
+    double fs[3] = {acc[0], acc[1], acc[2]};
     for (int32_t j = node_ptr[nd] + lane; j < node_ptr[nd + 1]; j += 32) {
       const double *f = fe + int64_t(node_src[j]) * 3;
       fs[0] += f[0];
       fs[1] += f[1];
       fs[2] += f[2];
     }
-    double a0 = acc[0] + double(accf[0]) + fs[0], a1 = acc[1] + double(accf[1]) + fs[1],
-           a2 = acc[2] + double(accf[2]) + fs[2];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-    }
-    if (lane < 3) {
-      const double tot = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
-      b[r0 + lane] = (p ? p[r0 + lane] : 0.0) - tot;
+    const double tot = warp_sum3<double>(fs[0], fs[1], fs[2]);
+    double totf = 0.0;
+    if constexpr (DF) totf = double(warp_sum3<float>(accf[0], accf[1], accf[2]));
+    if ((lane & 7) == 0 && lane < 24) {
+      const int i = lane >> 3;
+      b[r0 + i] = (p ? p[r0 + i] : 0.0) - (tot + totf);
     }
   }
 }
@@ -523,15 +545,15 @@ void launch_assemble(const fe_ctx *c, const DeviceState *d, bool fp32, const dou
   const unsigned grid = unsigned(std::min<int64_t>((nn + 7) / 8, 152 * 64));
   if (fp32 && !c->opt.element_fp64)
     assemble_block_kernel<float, float><<<grid, 256, 0, s>>>(
-        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const float *)d->Ke, d->fe, d->node_ptr,
-        d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh, (float *)d->A, d->A64, d->b);
+        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, d->bmass2, (const float *)d->Ke, d->fe,
+        d->node_ptr, d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh, (float *)d->A, d->A2, d->b);
   else if (fp32)
     assemble_block_kernel<double, float><<<grid, 256, 0, s>>>(
-        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const double *)d->Ke, d->fe,
-        d->node_ptr, d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh, (float *)d->A, d->A64, d->b);
+        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, d->bmass2, (const double *)d->Ke, d->fe,
+        d->node_ptr, d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh, (float *)d->A, d->A2, d->b);
   else
     assemble_block_kernel<double, double><<<grid, 256, 0, s>>>(
-        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, (const double *)d->Ke, d->fe,
+        nn, d->rowptr, d->bptr, d->bcol, d->bsrc_ptr, d->bsrc, d->bmass, nullptr, (const double *)d->Ke, d->fe,
         d->node_ptr, d->node_src, d->fixed_row, v, w, pext, cM, cK, al, bh, (double *)d->A, nullptr, d->b);
 }
 
@@ -565,7 +587,7 @@ __global__ void __launch_bounds__(kRedBlock) spmv_dot_kernel(
   const int64_t groups = int64_t(gridDim.x) * (kRedBlock / TPR);
   // the loop bound is warp-uniform so every lane reaches every shuffle
   const int64_t warp_row0 = int64_t(blockIdx.x) * (kRedBlock / TPR) + (threadIdx.x / 32) * (32 / TPR);
-  double dot = 0.0;
+  DotAcc<TV> dot;
   for (int64_t r0 = warp_row0; r0 < n; r0 += groups) {
     const int64_t row = r0 + (threadIdx.x % 32) / TPR;
     TV acc = TV(0);
@@ -577,11 +599,11 @@ __global__ void __launch_bounds__(kRedBlock) spmv_dot_kernel(
     for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
     if (sub == 0 && row < n) {
       y[row] = acc;
-      dot += double(x[row]) * double(acc);
+      dot.add(x[row], acc);
     }
   }
   double tot;
-  if (grid_sum<kRedBlock>(dot, partials, ticket, &tot) && threadIdx.x == 0) {
+  if (grid_sum<kRedBlock>(dot.value(), partials, ticket, &tot) && threadIdx.x == 0) {
     scal[S_PQ] = tot;
     if (!(tot > 0.0)) {
       atomicOr(flags, FLAG_BREAKDOWN);
@@ -615,7 +637,7 @@ __global__ void __launch_bounds__(kRedBlock) bspmv_kernel(
   const int64_t groups = int64_t(gridDim.x) * (kRedBlock / LPN);
   // the loop bound is warp-uniform so every lane reaches every shuffle
   const int64_t warp_node0 = int64_t(blockIdx.x) * (kRedBlock / LPN) + (threadIdx.x / 32) * GPW;
-  double red = 0.0;
+  DotAcc<TV> red;  // MODE 0: x.y; MODE 1: ||r||^2 (FP64)
   for (int64_t n0 = warp_node0; n0 < n_nodes; n0 += groups) {
     const int64_t nd = n0 + (threadIdx.x % 32) / LPN;
     TV a0 = TV(0), a1 = TV(0), a2 = TV(0);
@@ -641,25 +663,22 @@ __global__ void __launch_bounds__(kRedBlock) bspmv_kernel(
       a1 += __shfl_xor_sync(0xffffffffu, a1, o, LPN);
       a2 += __shfl_xor_sync(0xffffffffu, a2, o, LPN);
     }
-    if (sub == 0 && nd < n_nodes) {
-      const TV acc[3] = {a0, a1, a2};
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int64_t r = 3 * nd + i;
-        const TV yi = fixed ? TV(A[rowptr[r]]) * x[r] : acc[i];
-        if constexpr (MODE == 0) {
-          y[r] = yi;
-          red += double(x[r]) * double(yi);
-        } else {
-          const double ri = b[r] - double(yi);
-          y[r] = TV(ri);
-          red += ri * ri;
-        }
+    // every lane of the group holds the three sums: lane i < 3 finishes row 3 nd + i
+    if (sub < 3 && nd < n_nodes) {
+      const int64_t r = 3 * nd + sub;
+      const TV yi = fixed ? TV(A[rowptr[r]]) * x[r] : (sub == 0 ? a0 : (sub == 1 ? a1 : a2));
+      if constexpr (MODE == 0) {
+        y[r] = yi;
+        red.add(x[r], yi);
+      } else {
+        const double ri = b[r] - double(yi);
+        y[r] = TV(ri);
+        red.s += ri * ri;
       }
     }
   }
   double tot;
-  if (grid_sum<kRedBlock>(red, partials, ticket, &tot) && threadIdx.x == 0) {
+  if (grid_sum<kRedBlock>(red.value(), partials, ticket, &tot) && threadIdx.x == 0) {
     if constexpr (MODE == 0) {
       scal[S_PQ] = tot;
       if (!(tot > 0.0)) {
@@ -708,6 +727,108 @@ __global__ void __launch_bounds__(kRedBlock) residual_kernel(
   }
 }
 
+// r = b - A x in the mixed path: A and x as float pairs (A2, the assembly's
+// FP64-accurate copy of A, and x2, the refinement iterate's mirror), every
+// product and sum in double-float on the FP32 pipe; r and ||r||^2 in FP64
+// (one conversion per row) -> S_ORR, S_ODONE.  The same 8 bytes per value as
+// the FP64 kernels, about a dozen FP32 instructions per product instead of
+// one FP64 multiply-add (fe_df.cuh).  Node-block form as bspmv_kernel (LPN
+// lanes per node); after the group's reduction every lane holds the three
+// row sums and lane i < 3 finishes row 3 nd + i.
+template <int LPN>
+__global__ void __launch_bounds__(kRedBlock) bres_df_kernel(
+    int64_t n_nodes, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ bptr,
+    const int32_t *__restrict__ bcol, const int8_t *__restrict__ fixed_row, const float2 *__restrict__ A,
+    const float2 *__restrict__ x, double *__restrict__ r, const double *__restrict__ b, double *scal,
+    double *partials, unsigned int *ticket) {
+  constexpr int GPW = 32 / LPN;  // nodes per warp
+  const int sub = threadIdx.x % LPN;
+  const int64_t groups = int64_t(gridDim.x) * (kRedBlock / LPN);
+  // the loop bound is warp-uniform so every lane reaches every shuffle
+  const int64_t warp_node0 = int64_t(blockIdx.x) * (kRedBlock / LPN) + (threadIdx.x / 32) * GPW;
+  double red = 0.0;
+  for (int64_t n0 = warp_node0; n0 < n_nodes; n0 += groups) {
+    const int64_t nd = n0 + (threadIdx.x % 32) / LPN;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+    bool fixed = true;
+    if (nd < n_nodes) {
+      fixed = fixed_row[3 * nd] != 0;
+      if (!fixed) {
+        const int32_t k0 = bptr[nd], k1 = bptr[nd + 1];
+        const int32_t r0 = rowptr[3 * nd], r1 = rowptr[3 * nd + 1], r2 = rowptr[3 * nd + 2];
+        for (int32_t k = k0 + sub; k < k1; k += LPN) {
+          const int64_t cc = 3 * int64_t(bcol[k]);
+          const float2 x0 = x[cc], x1 = x[cc + 1], x2 = x[cc + 2];
+          const int32_t o = 3 * (k - k0);
+          df_fma_to(h0, l0, A[r0 + o], x0);
+          df_fma_to(h0, l0, A[r0 + o + 1], x1);
+          df_fma_to(h0, l0, A[r0 + o + 2], x2);
+          df_fma_to(h1, l1, A[r1 + o], x0);
+          df_fma_to(h1, l1, A[r1 + o + 1], x1);
+          df_fma_to(h1, l1, A[r1 + o + 2], x2);
+          df_fma_to(h2, l2, A[r2 + o], x0);
+          df_fma_to(h2, l2, A[r2 + o + 1], x1);
+          df_fma_to(h2, l2, A[r2 + o + 2], x2);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = LPN / 2; o > 0; o >>= 1) {
+      df_shfl_add<LPN>(h0, l0, o);
+      df_shfl_add<LPN>(h1, l1, o);
+      df_shfl_add<LPN>(h2, l2, o);
+    }
+    if (sub < 3 && nd < n_nodes) {
+      const int64_t rw = 3 * nd + sub;
+      float hi = sub == 0 ? h0 : (sub == 1 ? h1 : h2), lo = sub == 0 ? l0 : (sub == 1 ? l1 : l2);
+      if (fixed) {  // the lone diagonal entry
+        hi = lo = 0.f;
+        df_fma_to(hi, lo, A[rowptr[rw]], x[rw]);
+      }
+      const double ri = b[rw] - df_value(hi, lo);
+      r[rw] = ri;
+      red += ri * ri;
+    }
+  }
+  double tot;
+  if (grid_sum<kRedBlock>(red, partials, ticket, &tot) && threadIdx.x == 0) {
+    scal[S_ORR] = tot;
+    scal[S_ODONE] = (tot <= scal[S_OTOL2]) ? 1.0 : 0.0;
+  }
+}
+
+// The CSR form of bres_df_kernel (TPR threads per row).
+template <int TPR>
+__global__ void __launch_bounds__(kRedBlock) residual_df_kernel(
+    int64_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colind, const float2 *__restrict__ A,
+    const float2 *__restrict__ x, const double *__restrict__ b, double *__restrict__ r, double *scal,
+    double *partials, unsigned int *ticket) {
+  const int sub = threadIdx.x % TPR;
+  const int64_t groups = int64_t(gridDim.x) * (kRedBlock / TPR);
+  const int64_t warp_row0 = int64_t(blockIdx.x) * (kRedBlock / TPR) + (threadIdx.x / 32) * (32 / TPR);
+  double rr = 0.0;
+  for (int64_t r0 = warp_row0; r0 < n; r0 += groups) {
+    const int64_t row = r0 + (threadIdx.x % 32) / TPR;
+    float hi = 0.f, lo = 0.f;
+    if (row < n) {
+      const int32_t k1 = rowptr[row + 1];
+      for (int32_t k = rowptr[row] + sub; k < k1; k += TPR) df_fma_to(hi, lo, A[k], x[colind[k]]);
+    }
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) df_shfl_add<TPR>(hi, lo, o);
+    if (sub == 0 && row < n) {
+      const double ri = b[row] - df_value(hi, lo);
+      r[row] = ri;
+      rr += ri * ri;
+    }
+  }
+  double tot;
+  if (grid_sum<kRedBlock>(rr, partials, ticket, &tot) && threadIdx.x == 0) {
+    scal[S_ORR] = tot;
+    scal[S_ODONE] = (tot <= scal[S_OTOL2]) ? 1.0 : 0.0;
+  }
+}
+
 // x += alpha p; r -= alpha q; ||r||^2 -> S_RR; S_DONE when below S_TOL2.
 template <typename TV>
 __global__ void __launch_bounds__(kRedBlock) axpy_norm_kernel(int64_t n, TV *__restrict__ x,
@@ -718,15 +839,15 @@ __global__ void __launch_bounds__(kRedBlock) axpy_norm_kernel(int64_t n, TV *__r
                                                               double max_iters) {
   if (solve_done(scal)) return;
   const TV al = TV(scal[S_ALPHA]);
-  double rr = 0.0;
+  DotAcc<TV> rr;
   for (int64_t i = int64_t(blockIdx.x) * kRedBlock + threadIdx.x; i < n; i += int64_t(gridDim.x) * kRedBlock) {
     x[i] += al * p[i];
     const TV ri = r[i] - al * q[i];
     r[i] = ri;
-    rr += double(ri) * double(ri);
+    rr.add(ri, ri);
   }
   double tot;
-  if (grid_sum<kRedBlock>(rr, partials, ticket, &tot) && threadIdx.x == 0) {
+  if (grid_sum<kRedBlock>(rr.value(), partials, ticket, &tot) && threadIdx.x == 0) {
     scal[S_RR] = tot;
     scal[S_ITERS] += 1.0;
     if (tot <= scal[S_TOL2])
@@ -743,11 +864,11 @@ __global__ void __launch_bounds__(kRedBlock) dot_rz_kernel(int64_t n, const TV *
                                                            double *scal, double *partials,
                                                            unsigned int *ticket, int *flags) {
   if (solve_done(scal)) return;
-  double s = 0.0;
+  DotAcc<TV> s;
   for (int64_t i = int64_t(blockIdx.x) * kRedBlock + threadIdx.x; i < n; i += int64_t(gridDim.x) * kRedBlock)
-    s += double(r[i]) * double(z[i]);
+    s.add(r[i], z[i]);
   double tot;
-  if (grid_sum<kRedBlock>(s, partials, ticket, &tot) && threadIdx.x == 0) {
+  if (grid_sum<kRedBlock>(s.value(), partials, ticket, &tot) && threadIdx.x == 0) {
     if (!(tot > 0.0) && scal[S_RR] > 0.0) {  // P^{-1} lost definiteness
       atomicOr(flags, FLAG_BREAKDOWN);
       scal[S_DONE] = 1.0;
@@ -773,17 +894,19 @@ __global__ void update_p_kernel(int64_t n, const TV *__restrict__ z, TV *__restr
 // Start of a (sub)solve: x = 0, r = rhs (cast), ||rhs||^2 -> tolerance.
 // outer = 1: S_BB, S_OTOL2 = tol^2 * bb, S_ORR, S_ODONE.  outer = 0: inner
 // solve with S_TOL2 = tol^2 * ||rhs||^2, S_DONE.
+// x2 (mixed path's outer solve, else null): x as float pairs, for the residual.
 template <typename TV>
 __global__ void __launch_bounds__(kRedBlock) init_solve_kernel(int64_t n, TV *__restrict__ x,
                                                                TV *__restrict__ r,
                                                                const double *__restrict__ rhs,
                                                                double tol, int outer, double *scal,
                                                                double *partials, unsigned int *ticket,
-                                                               int keep_x) {
+                                                               int keep_x, float2 *__restrict__ x2) {
   double s = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * kRedBlock + threadIdx.x; i < n; i += int64_t(gridDim.x) * kRedBlock) {
     const double v = rhs[i];
     if (!keep_x) x[i] = TV(0);  // a warm start keeps x (its residual follows)
+    if (x2) x2[i] = keep_x ? df_split(double(x[i])) : make_float2(0.f, 0.f);
     r[i] = TV(v);
     s += v * v;
   }
@@ -803,9 +926,14 @@ __global__ void __launch_bounds__(kRedBlock) init_solve_kernel(int64_t n, TV *__
   }
 }
 
-__global__ void refine_update_kernel(int64_t n, double *__restrict__ x, const float *__restrict__ d) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    x[i] += double(d[i]);
+// x += d, and its float-pair mirror x2 (read by the double-float residual)
+__global__ void refine_update_kernel(int64_t n, double *__restrict__ x, const float *__restrict__ d,
+                                     float2 *__restrict__ x2) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double xi = x[i] + double(d[i]);
+    x[i] = xi;
+    if (x2) x2[i] = df_split(xi);
+  }
 }
 
 __global__ void integrate_kernel(int64_t n, double h, const double *__restrict__ a, double *__restrict__ v,
@@ -886,8 +1014,8 @@ static unsigned ew_grid(int64_t n) {
 // SpMV variants: 0-3 the node-block kernel with 4, 8, 16 or 32 lanes per
 // node, 4-5 the CSR kernel with 8 or 16 threads per row.  The first solve
 // of a context times them (tune_spmv) and keeps the fastest for each of the
-// two products: y = A x with x.y in the inner solve's type, and the FP64
-// residual r = b - A64 x.
+// two products: y = A x with x.y in the inner solve's type, and the
+// refinement residual r = b - A x (FP64, or double-float on float pairs).
 constexpr int kSpmvVariants = 6;
 
 template <typename TA, typename TV, int MODE>
@@ -944,10 +1072,44 @@ void launch_spmv_dot(const fe_ctx *c, const DeviceState *d, bool fp32, const voi
   spmv_dot_var(c, d, d->spmv_var, fp32, x, y, d->scal, d->flags, s);
 }
 
+// r = b - A x for the refinement: A itself in the FP64 path; in the mixed
+// path A2 and x2 (float pairs) in double-float, the variant numbering as
+// launch_spmv_variant's.
+static void res_var_launch(const fe_ctx *c, const DeviceState *d, int var, double *scal, int *flags,
+                           cudaStream_t s) {
+  if (!d->A2) {
+    launch_spmv_variant<double, double, 1>(c, d, var, d->A64, d->x, d->r, d->b, scal, flags, s);
+    return;
+  }
+  const int64_t nn = c->n_nodes, n = c->n;
+  switch (var) {
+#define FE_BRES(V, L)                                                                                         \
+  case V:                                                                                                     \
+    bres_df_kernel<L><<<spmv_grid(nn * L), kRedBlock, 0, s>>>(nn, d->rowptr, d->bptr, d->bcol, d->fixed_row,   \
+                                                             d->A2, d->x2, d->r, d->b, scal, d->partials,    \
+                                                             d->ticket);                                     \
+    break;
+    FE_BRES(0, 4)
+    FE_BRES(1, 8)
+    FE_BRES(2, 16)
+    FE_BRES(3, 32)
+#undef FE_BRES
+    default: {
+      const bool t16 = var == 5;
+      const unsigned g = spmv_grid(n * (t16 ? 16 : 8) / 4);
+      if (t16)
+        residual_df_kernel<16><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, d->A2, d->x2, d->b, d->r, scal,
+                                                       d->partials, d->ticket);
+      else
+        residual_df_kernel<8><<<g, kRedBlock, 0, s>>>(n, d->rowptr, d->colind, d->A2, d->x2, d->b, d->r, scal,
+                                                      d->partials, d->ticket);
+    }
+  }
+}
+
 void launch_residual(const fe_ctx *c, const DeviceState *d, bool, cudaStream_t s) {
-  // r = b - A64 x: the FP64 copy of A (A itself in the FP64 path)
   d->launches++;
-  launch_spmv_variant<double, double, 1>(c, d, d->res_var, d->A64, d->x, d->r, d->b, d->scal, d->flags, s);
+  res_var_launch(c, d, d->res_var, d->scal, d->flags, s);
 }
 
 // Times every variant of both products (CUDA events on the main stream, one
@@ -978,7 +1140,7 @@ int tune_spmv(fe_ctx *c, DeviceState *d) {
           if (prod == 0)
             spmv_dot_var(c, d, var, fp32, d->vp, d->vq, ts, tf, d->stream);
           else
-            launch_spmv_variant<double, double, 1>(c, d, var, d->A64, d->x, d->r, d->b, ts, tf, d->stream);
+            res_var_launch(c, d, var, ts, tf, d->stream);
           er = cudaGetLastError();
         }
         if (er == cudaSuccess) er = cudaEventRecord(e1, d->stream);
@@ -1045,10 +1207,12 @@ void launch_init_solve(const fe_ctx *c, const DeviceState *d, bool fp32, void *x
   const int64_t n = c->n;
   if (fp32)
     init_solve_kernel<float><<<red_grid(n), kRedBlock, 0, s>>>(n, (float *)x, (float *)r, rhs, tol, outer,
-                                                               d->scal, d->partials, d->ticket, keep_x ? 1 : 0);
-  else
+                                                               d->scal, d->partials, d->ticket, keep_x ? 1 : 0,
+                                                               nullptr);
+  else  // the outer solve's x: its float-pair mirror too (mixed path)
     init_solve_kernel<double><<<red_grid(n), kRedBlock, 0, s>>>(n, (double *)x, (double *)r, rhs, tol, outer,
-                                                                d->scal, d->partials, d->ticket, keep_x ? 1 : 0);
+                                                                d->scal, d->partials, d->ticket, keep_x ? 1 : 0,
+                                                                x == d->x ? d->x2 : nullptr);
 }
 
 __global__ void warm_fixup_kernel(double *scal) {
@@ -1063,7 +1227,7 @@ void launch_warm_fixup(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
 
 void launch_refine_update(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
   d->launches++;
-  refine_update_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, d->x, (const float *)d->vd);
+  refine_update_kernel<<<ew_grid(c->n), 256, 0, s>>>(c->n, d->x, (const float *)d->vd, d->x2);
 }
 
 void launch_integrate(const fe_ctx *c, const DeviceState *d, cudaStream_t s) {
@@ -1104,6 +1268,15 @@ void launch_convert(const void *src, bool src32, void *dst, bool dst32, int64_t 
     convert_kernel<double, float><<<g, 256, 0, s>>>((const double *)src, (float *)dst, n);
   else
     convert_kernel<double, double><<<g, 256, 0, s>>>((const double *)src, (double *)dst, n);
+}
+
+__global__ void pair_to_double_kernel(const float2 *__restrict__ src, double *__restrict__ dst, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    dst[i] = df_value(src[i]);
+}
+
+void launch_pair_to_double(const float2 *src, double *dst, int64_t n, cudaStream_t s) {
+  pair_to_double_kernel<<<ew_grid(n), 256, 0, s>>>(src, dst, n);
 }
 
 }  // namespace fe
