@@ -104,6 +104,17 @@ int upload(fe_ctx *c, DeviceState *d, T **p, const std::vector<T> &h) {
   return FE_OK;
 }
 
+// v as float pairs (hi = fl32(v), lo = fl32(v - hi)), the layout the
+// double-float kernels read
+std::vector<float2> float_pairs(const std::vector<double> &v) {
+  std::vector<float2> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    const float h = float(v[i]);
+    out[i] = make_float2(h, float(v[i] - double(h)));
+  }
+  return out;
+}
+
 // Tensor maps for the TMA loads of the FP32 factor's trailing updates.
 // Per front: F as a 2-D array (rows contiguous, leading dimension ldf),
 // 128 x 16 boxes (a 128-row tile of 16 columns); Y as a 2-D array (the
@@ -235,6 +246,11 @@ int ensure_device(fe_ctx *c) {
     for (int64_t e = 0; e < E; ++e)
       for (int k = 0; k < 3; ++k) pt[k * E + e] = c->params[3 * e + k];
     FE_TRY(upload(c, d, &d->params, pt));
+    if (fp32 && !c->opt.element_fp64) {  // the double-float force's inputs
+      FE_TRY(upload(c, d, &d->rest2, float_pairs(c->rest)));
+      FE_TRY(upload(c, d, &d->params2, float_pairs(pt)));
+      FE_TRY(dalloc(c, d, &d->u2, size_t(n)));
+    }
   }
   FE_TRY(upload(c, d, &d->X, c->X));
   FE_TRY(upload(c, d, &d->rowptr, c->rowptr));
@@ -284,12 +300,7 @@ int ensure_device(fe_ctx *c) {
     FE_TRY(dalloc(c, d, &d->A2, size_t(c->nnz)));
     FE_TRY(dalloc(c, d, &d->x2, n));
     FE_CUDA_TRY(cudaMemset(d->x2, 0, n * sizeof(float2)));
-    std::vector<float2> bm2(c->bmass.size());
-    for (size_t k = 0; k < bm2.size(); ++k) {
-      const float h = float(c->bmass[k]);
-      bm2[k] = make_float2(h, float(c->bmass[k] - double(h)));
-    }
-    FE_TRY(upload(c, d, &d->bmass2, bm2));
+    FE_TRY(upload(c, d, &d->bmass2, float_pairs(c->bmass)));
   } else {
     d->A64 = static_cast<double *>(d->A);
   }
@@ -1098,7 +1109,14 @@ int fe_element_eval(fe_ctx *c, const double *q, double *f_e, double *K_e) {
     return FE_OK;
   };
   int st = FE_OK;
-  if (f_e) st = out(f_e, d->fe, false, nf);
+  if (f_e && d->u2) {  // the double-float force path stores f_e as float pairs
+    launch_pair_to_double(reinterpret_cast<const float2 *>(d->fe), tmp, nf, d->stream);
+    FE_CUDA_TRY(cudaMemcpyAsync(f_e, tmp, nf * sizeof(double),
+                                c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d->stream));
+    FE_CUDA_TRY(cudaStreamSynchronize(d->stream));
+  } else if (f_e) {
+    st = out(f_e, d->fe, false, nf);
+  }
   if (!st && K_e) st = out(K_e, d->Ke, mixed(c) && !c->opt.element_fp64, nk);
   cudaFree(tmp);
   if (st) return st;
@@ -1304,6 +1322,10 @@ int fe_set_params(fe_ctx *c, const double *params) {
     FE_CUDA_TRY(cudaStreamSynchronize(c->dev->stream));
     FE_CUDA_TRY(cudaStreamSynchronize(c->dev->fstream));
     FE_CUDA_TRY(cudaMemcpy(c->dev->params, pt.data(), pt.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (c->dev->params2) {
+      const std::vector<float2> p2 = float_pairs(pt);
+      FE_CUDA_TRY(cudaMemcpy(c->dev->params2, p2.data(), p2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    }
   }
   return FE_OK;
 }

@@ -77,9 +77,13 @@ struct DeviceState {
   double *stage_in = nullptr, *stage_out = nullptr;  // pinned host staging [n]
   double *stage_big = nullptr; size_t stage_big_bytes = 0;
 
-  // element outputs: forces f_e in FP64; tangents K_e in FP64, or FP32 in
+  // element outputs: forces f_e in FP64, or as float pairs (double-float)
+  // in the mixed path with FP32 tangents; tangents K_e in FP64, or FP32 in
   // the mixed path (unless element_fp64)
   double *fe = nullptr;
+  // that path's inputs as float pairs: rest data and parameters (made at
+  // setup and by fe_set_params), the displacement q - X (per launch)
+  float2 *rest2 = nullptr, *params2 = nullptr, *u2 = nullptr;
   void *Ke = nullptr;
   // system: A in the matrix type (FP64, or FP32 in the mixed path: the inner
   // SpMV and the snapshot the factor reads), b in FP64.  The refinement

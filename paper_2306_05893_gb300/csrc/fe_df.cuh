@@ -74,4 +74,53 @@ struct DotAcc {
   __device__ __forceinline__ double value() const { return s; }
 };
 
+// A double-float number for the element kernels' force path (the material
+// laws are templates on their number type).  Sums and products follow the
+// error-free transformations above with one renormalisation each: relative
+// error about 2^-46 per operation (2^-53 in FP64), exponent range that of
+// FP32.  Division: the FP32 quotient corrected by one remainder step.
+// Constants convert from double at compile time (constexpr); conversions
+// from run-time doubles (three FP64-pipe instructions) belong outside the
+// hot loops.
+struct dfloat {
+  float hi, lo;
+  dfloat() = default;
+  __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr dfloat(double v) : hi(float(v)), lo(float(v - double(float(v)))) {}
+  __host__ __device__ constexpr dfloat(int v) : dfloat(double(v)) {}
+  __device__ __forceinline__ explicit dfloat(float2 p) : hi(p.x), lo(p.y) {}
+  __device__ __forceinline__ explicit operator float() const { return hi + lo; }
+  __device__ __forceinline__ explicit operator double() const { return double(hi) + double(lo); }
+  __device__ __forceinline__ float2 pair() const { return make_float2(hi, lo); }
+};
+
+__device__ __forceinline__ dfloat df_renorm(float s, float e) {
+  const float h = s + e;
+  return dfloat(h, e - (h - s));
+}
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+  const float s = a.hi + b.hi, bb = s - a.hi;
+  const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+  return df_renorm(s, e);
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
+  return df_renorm(p, e);
+}
+__device__ __forceinline__ dfloat operator/(dfloat a, dfloat b) {
+  const float q1 = a.hi / b.hi;
+  const dfloat r = a - b * dfloat(q1, 0.f);  // the remainder, in double-float
+  const float q2 = r.hi / b.hi;
+  return df_renorm(q1, q2);
+}
+__device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
+__device__ __forceinline__ dfloat &operator-=(dfloat &a, dfloat b) { return a = a - b; }
+__device__ __forceinline__ dfloat &operator*=(dfloat &a, dfloat b) { return a = a * b; }
+__device__ __forceinline__ dfloat &operator/=(dfloat &a, dfloat b) { return a = a / b; }
+__device__ __forceinline__ bool operator>(dfloat a, dfloat b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ bool operator<(dfloat a, dfloat b) { return b > a; }
+
 }  // namespace fe

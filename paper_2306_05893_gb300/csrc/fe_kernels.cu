@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <string>
+#include <type_traits>
 
 #include "fe_device.cuh"
 #include "fe_df.cuh"
@@ -63,8 +64,36 @@ __device__ __forceinline__ bool solve_done(const double *scal) { return scal[S_D
 
 // ---------------------------------------------------------- element kernels
 
-template <typename T>
-__device__ __forceinline__ T ld_cast(const double *p) { return T(__ldg(p)); }
+// An element kernel's inputs in its force type TF.  FP64: read from the
+// stored doubles.  Double-float (the mixed path with FP32 tangents): read
+// from float-pair copies (rest data and parameters made once, the
+// displacement q - X per launch by disp_pairs_kernel), so the force path
+// issues no FP64 conversion; f_e is stored as float pairs.
+template <typename TF>
+struct ElemSrc {
+  const double *rest, *params, *X, *q;
+  using fout = double;
+  __device__ __forceinline__ TF rest_at(int64_t i) const { return TF(__ldg(rest + i)); }
+  __device__ __forceinline__ TF param_at(int64_t i) const { return TF(__ldg(params + i)); }
+  __device__ __forceinline__ TF disp(int64_t dof) const { return TF(__ldg(q + dof) - __ldg(X + dof)); }
+  __device__ __forceinline__ static double out(TF v) { return double(v); }
+};
+template <>
+struct ElemSrc<dfloat> {
+  const float2 *rest, *params, *u;
+  using fout = float2;
+  __device__ __forceinline__ dfloat rest_at(int64_t i) const { return dfloat(__ldg(rest + i)); }
+  __device__ __forceinline__ dfloat param_at(int64_t i) const { return dfloat(__ldg(params + i)); }
+  __device__ __forceinline__ dfloat disp(int64_t dof) const { return dfloat(__ldg(u + dof)); }
+  __device__ __forceinline__ static float2 out(dfloat v) { return v.pair(); }
+};
+
+// u = q - X as float pairs (the double-float force's displacement)
+__global__ void disp_pairs_kernel(int64_t n, const double *__restrict__ q, const double *__restrict__ X,
+                                  float2 *__restrict__ u) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    u[i] = df_split(q[i] - X[i]);
+}
 
 // The tangent part of a tet: 144 entries of K_e = V grad N^T CC grad N in
 // fill order ((a*4 + b)*9 + 3i + k), into one shared-memory row.
@@ -94,18 +123,16 @@ __device__ __forceinline__ void tet_tangent(const L &law, const T g[4][3], T V, 
 }
 
 // One thread per tet.  Rest data SoA [10][E]: rows of Dm^{-1} (= grad N_1..3),
-// volume.  Outputs f_e [E][4][3] (force type TF) and K_e [E][144] (tangent
-// type T) in fill order, K_e staged through shared memory for coalesced
-// stores.  With TF = double and T = float (the mixed path) the kinematics,
-// stress and force are evaluated in FP64 and the tangent in FP32 from the
-// same displacement gradient.
+// volume.  Outputs f_e [E][4][3] (force type TF: FP64, or float pairs) and
+// K_e [E][144] (tangent type T) in fill order, K_e staged through shared
+// memory for coalesced stores.  With TF = dfloat and T = float (the mixed
+// path) the kinematics, stress and force are evaluated in double-float
+// (about 2^-46 per operation, on the FP32 pipe: GB300's FP64 pipe bound the
+// FP64 version) and the tangent in FP32 from the same displacement gradient.
 template <int MODEL, typename T, typename TF, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, int64_t e_begin, int64_t e_end,
-                                                    const int32_t *__restrict__ conn,
-                                                    const double *__restrict__ rest,
-                                                    const double *__restrict__ params,
-                                                    const double *__restrict__ X,
-                                                    const double *__restrict__ q, TF *__restrict__ f_out,
+                                                    const int32_t *__restrict__ conn, ElemSrc<TF> src,
+                                                    typename ElemSrc<TF>::fout *__restrict__ f_out,
                                                     T *__restrict__ K_out, int *flags) {
   extern __shared__ unsigned char smem_raw[];
   T *sk = reinterpret_cast<T *>(smem_raw);
@@ -119,11 +146,11 @@ __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, int64_t e_begin, 
 #pragma unroll
     for (int a = 1; a < 4; ++a)
 #pragma unroll
-      for (int J = 0; J < 3; ++J) g[a][J] = ld_cast<TF>(rest + (3 * (a - 1) + J) * E + e);
+      for (int J = 0; J < 3; ++J) g[a][J] = src.rest_at((3 * (a - 1) + J) * E + e);
 #pragma unroll
     for (int J = 0; J < 3; ++J) g[0][J] = -(g[1][J] + g[2][J] + g[3][J]);
-    const TF V = ld_cast<TF>(rest + 9 * E + e);
-    const TF p0 = ld_cast<TF>(params + e), p1 = ld_cast<TF>(params + E + e), p2 = ld_cast<TF>(params + 2 * E + e);
+    const TF V = src.rest_at(9 * E + e);
+    const TF p0 = src.param_at(e), p1 = src.param_at(E + e), p2 = src.param_at(2 * E + e);
     TF H[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -133,8 +160,8 @@ __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, int64_t e_begin, 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        // displacement in FP64, then the working type
-        const TF u = TF(__ldg(q + 3 * nd[a] + i) - __ldg(X + 3 * nd[a] + i));
+        // displacement in FP64 (or its float pair), then the working type
+        const TF u = src.disp(3 * nd[a] + i);
 #pragma unroll
         for (int J = 0; J < 3; ++J) H[i][J] += u * g[a][J];
       }
@@ -154,7 +181,7 @@ __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, int64_t e_begin, 
           TF s = TF(0);
 #pragma unroll
           for (int J = 0; J < 3; ++J) s += P[i][J] * g[a][J];
-          f_out[e * 12 + 3 * a + i] = V * s;
+          f_out[e * 12 + 3 * a + i] = ElemSrc<TF>::out(V * s);
         }
       if constexpr (sizeof(T) == sizeof(TF)) tet_tangent<T>(law, g, V, row);
     }
@@ -187,15 +214,12 @@ __global__ void __launch_bounds__(BLOCK) tet_kernel(int64_t E, int64_t e_begin, 
 // One thread per (hex, local node a); 8 Gauss points.  Rest data SoA
 // [8 * 25][E]: per Gauss point grad N (8 x 3) and w det J0.  Thread a owns
 // the block row a of K_e (72 values, tangent type T) and f_a (force type TF;
-// with TF = double and T = float the stress and force are evaluated in FP64
-// and the tangent in FP32 from the same displacement gradient).
+// with TF = dfloat and T = float the stress and force are evaluated in
+// double-float and the tangent in FP32 from the same displacement gradient).
 template <int MODEL, typename T, typename TF, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, int64_t e_end,
-                                                    const int32_t *__restrict__ conn,
-                                                    const double *__restrict__ rest,
-                                                    const double *__restrict__ params,
-                                                    const double *__restrict__ X,
-                                                    const double *__restrict__ q, TF *__restrict__ f_out,
+                                                    const int32_t *__restrict__ conn, ElemSrc<TF> src,
+                                                    typename ElemSrc<TF>::fout *__restrict__ f_out,
                                                     T *__restrict__ K_out, int *flags) {
   extern __shared__ unsigned char smem_raw[];
   T *sk = reinterpret_cast<T *>(smem_raw);
@@ -211,9 +235,9 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, 
     for (int b = 0; b < 8; ++b) {
       const int nb = __ldg(conn + e * 8 + b);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) u[b][i] = TF(__ldg(q + 3 * nb + i) - __ldg(X + 3 * nb + i));
+      for (int i = 0; i < 3; ++i) u[b][i] = src.disp(3 * nb + i);
     }
-    const TF p0 = ld_cast<TF>(params + e), p1 = ld_cast<TF>(params + E + e), p2 = ld_cast<TF>(params + 2 * E + e);
+    const TF p0 = src.param_at(e), p1 = src.param_at(E + e), p2 = src.param_at(2 * E + e);
     Law<MODEL, TF> law;
     Law<MODEL, T> lt;
     if constexpr (MODEL == FE_COROTATIONAL) {
@@ -225,13 +249,13 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, 
         for (int J = 0; J < 3; ++J) Hb[i][J] = TF(0);
 #pragma unroll 1
       for (int gp = 0; gp < 8; ++gp) {
-        const TF w = ld_cast<TF>(rest + (gp * 25 + 24) * E + e);
+        const TF w = src.rest_at((gp * 25 + 24) * E + e);
         vol += w;
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
           TF gb[3];
 #pragma unroll
-          for (int J = 0; J < 3; ++J) gb[J] = w * ld_cast<TF>(rest + (gp * 25 + 3 * b + J) * E + e);
+          for (int J = 0; J < 3; ++J) gb[J] = w * src.rest_at((gp * 25 + 3 * b + J) * E + e);
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -264,8 +288,8 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, 
 #pragma unroll
       for (int b = 0; b < 8; ++b)
 #pragma unroll
-        for (int J = 0; J < 3; ++J) g[b][J] = ld_cast<TF>(rest + (gp * 25 + 3 * b + J) * E + e);
-      const TF w = ld_cast<TF>(rest + (gp * 25 + 24) * E + e);
+        for (int J = 0; J < 3; ++J) g[b][J] = src.rest_at((gp * 25 + 3 * b + J) * E + e);
+      const TF w = src.rest_at((gp * 25 + 24) * E + e);
       TF H[3][3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
@@ -317,7 +341,7 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, 
         }
     }
 #pragma unroll
-    for (int i = 0; i < 3; ++i) f_out[e * 24 + 3 * a + i] = fa[i];
+    for (int i = 0; i < 3; ++i) f_out[e * 24 + 3 * a + i] = ElemSrc<TF>::out(fa[i]);
     T *row = sk + el * LD + a * 72;
 #pragma unroll
     for (int b = 0; b < 8; ++b)
@@ -331,33 +355,45 @@ __global__ void __launch_bounds__(BLOCK) hex_kernel(int64_t E, int64_t e_begin, 
     dst[idx] = sk[(idx / 576) * LD + idx % 576];
 }
 
+// T = float (FP32 tangents): the force in double-float from the float-pair
+// inputs; T = double: FP64 throughout.
 template <int MODEL, typename T>
 static void launch_element_t(const fe_ctx *c, const DeviceState *d, const double *q, cudaStream_t s) {
+  using TF = std::conditional_t<sizeof(T) == 4, dfloat, double>;
   const int64_t E = c->n_elems;
   const int64_t eb = c->model_range[MODEL][0], ee = c->model_range[MODEL][1];
   if (ee <= eb) return;
   const int64_t EN = ee - eb;
-  double *fo = d->fe;
+  ElemSrc<TF> src;
+  if constexpr (sizeof(T) == 4)
+    src = ElemSrc<TF>{d->rest2, d->params2, d->u2};
+  else
+    src = ElemSrc<TF>{d->rest, d->params, d->X, q};
+  auto *fo = reinterpret_cast<typename ElemSrc<TF>::fout *>(d->fe);
   T *Ko = reinterpret_cast<T *>(d->Ke);
   if (c->elem_type == FE_TET4) {
     constexpr int B = sizeof(T) == 8 ? 64 : 128;
     const size_t sm = size_t(B) * 145 * sizeof(T);
-    cudaFuncSetAttribute(tet_kernel<MODEL, T, double, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    tet_kernel<MODEL, T, double, B><<<unsigned((EN + B - 1) / B), B, sm, s>>>(E, eb, ee, d->conn, d->rest, d->params,
-                                                                              d->X, q, fo, Ko, d->flags);
+    cudaFuncSetAttribute(tet_kernel<MODEL, T, TF, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    tet_kernel<MODEL, T, TF, B><<<unsigned((EN + B - 1) / B), B, sm, s>>>(E, eb, ee, d->conn, src, fo, Ko, d->flags);
   } else {
     constexpr int B = 128, EPB = B / 8;
     const size_t sm = size_t(EPB) * 577 * sizeof(T);
-    cudaFuncSetAttribute(hex_kernel<MODEL, T, double, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    hex_kernel<MODEL, T, double, B><<<unsigned((EN + EPB - 1) / EPB), B, sm, s>>>(E, eb, ee, d->conn, d->rest,
-                                                                                 d->params, d->X, q, fo, Ko, d->flags);
+    cudaFuncSetAttribute(hex_kernel<MODEL, T, TF, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    hex_kernel<MODEL, T, TF, B><<<unsigned((EN + EPB - 1) / EPB), B, sm, s>>>(E, eb, ee, d->conn, src, fo, Ko,
+                                                                             d->flags);
   }
 }
 
-// Element forces always in FP64; tangents in FP32 when fp32 (the mixed path)
-// unless element_fp64.
+// Element forces in FP64, or in double-float (float pairs) with the FP32
+// tangents of the mixed path (unless element_fp64, which keeps both in FP64).
 void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool fp32, cudaStream_t s) {
   const bool k32 = fp32 && !c->opt.element_fp64;
+  if (k32) {  // the displacement as float pairs, once for every law's launch
+    d->launches++;
+    disp_pairs_kernel<<<unsigned(std::max<int64_t>(1, std::min<int64_t>((c->n + 255) / 256, 152 * 16))), 256, 0, s>>>(
+        c->n, q, d->X, d->u2);
+  }
   // one launch per material model present (a batch groups its members by model)
   for (int md = FE_SVK; md <= FE_COROTATIONAL; ++md) {
     if (c->model_range[md][1] <= c->model_range[md][0]) continue;
@@ -391,9 +427,10 @@ void launch_element(const fe_ctx *c, const DeviceState *d, const double *q, bool
 // FMA for cK K and cM M, the block mass read as a float pair), and A is
 // written rounded to FP32 (the inner solve and the factor) and as the pair
 // itself (A2, the FP64-accurate copy the refinement residual reads in
-// double-float).  The damping part of b is summed in FP32 (its terms carry
-// the FP32 tangent's rounding already), the element forces in FP64; the
-// three rows' sums are reduced across the warp in one transposed reduction
+// double-float).  The damping part of b is summed in FP32 per lane (its
+// terms carry the FP32 tangent's rounding already); with the element forces
+// (double-float pairs in this path) the lanes' sums are reduced across the
+// warp in double-float, the three rows in one transposed reduction
 // (warp_sum3) instead of three.
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
   const float s = hi + x;
@@ -408,18 +445,25 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
 // total of v[(l >> 3) & 3] (v[3] = 0): lanes 0, 8 and 16 hold v0, v1, v2.
 // Six additions instead of fifteen; a fixed order, so deterministic.
 template <typename T>
+__device__ __forceinline__ T shfl_xor_any(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+template <>
+__device__ __forceinline__ dfloat shfl_xor_any<dfloat>(dfloat v, int o) {
+  return dfloat(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+
+template <typename T>
 __device__ __forceinline__ T warp_sum3(T v0, T v1, T v2) {
   const int lane = threadIdx.x & 31;
   const bool up = (lane & 16) != 0;
   T k0 = up ? v2 : v0, k1 = up ? T(0) : v1;
   const T s0 = up ? v0 : v2, s1 = up ? v1 : T(0);
-  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  k0 += shfl_xor_any(s0, 16);
+  k1 += shfl_xor_any(s1, 16);
   const bool hi8 = (lane & 8) != 0;
   T k = hi8 ? k1 : k0;
-  k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+  k += shfl_xor_any(hi8 ? k0 : k1, 8);
 #pragma unroll
-  for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  for (int o = 4; o > 0; o >>= 1) k += shfl_xor_any(k, o);
   return k;
 }
 
@@ -428,7 +472,7 @@ __global__ void __launch_bounds__(256) assemble_block_kernel(
     int64_t n_nodes, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ bptr,
     const int32_t *__restrict__ bcol, const int32_t *__restrict__ bsrc_ptr, const int32_t *__restrict__ bsrc,
     const double *__restrict__ bmass, const float2 *__restrict__ bmass2, const TK *__restrict__ Ke,
-    const double *__restrict__ fe, const int32_t *__restrict__ node_ptr, const int32_t *__restrict__ node_src,
+    const void *__restrict__ fe, const int32_t *__restrict__ node_ptr, const int32_t *__restrict__ node_src,
     const int8_t *__restrict__ fixed_row, const double *__restrict__ v, const double *__restrict__ w,
     const double *__restrict__ p, double cM, double cK, double al, double bh, TA *__restrict__ A,
     float2 *__restrict__ A2, double *__restrict__ b) {
@@ -519,19 +563,34 @@ __global__ void __launch_bounds__(256) assemble_block_kernel(
         }
       }
     }
-    double fs[3] = {acc[0], acc[1], acc[2]};
-    for (int32_t j = node_ptr[nd] + lane; j < node_ptr[nd + 1]; j += 32) {
-      const double *f = fe + int64_t(node_src[j]) * 3;
-      fs[0] += f[0];
-      fs[1] += f[1];
-      fs[2] += f[2];
+    double tot;
+    if constexpr (DF) {
+      // the element forces as float pairs, summed in double-float with each
+      // lane's FP32 damping part; the M w term (Newton corrections) in FP64
+      dfloat fs[3] = {dfloat(accf[0], 0.f), dfloat(accf[1], 0.f), dfloat(accf[2], 0.f)};
+      const float2 *fe2 = static_cast<const float2 *>(fe);
+      for (int32_t j = node_ptr[nd] + lane; j < node_ptr[nd + 1]; j += 32) {
+        const float2 *f = fe2 + int64_t(node_src[j]) * 3;
+        fs[0] += dfloat(f[0]);
+        fs[1] += dfloat(f[1]);
+        fs[2] += dfloat(f[2]);
+      }
+      tot = double(warp_sum3<dfloat>(fs[0], fs[1], fs[2]));
+      if (w) tot += warp_sum3<double>(acc[0], acc[1], acc[2]);
+    } else {
+      double fs[3] = {acc[0], acc[1], acc[2]};
+      const double *fe64 = static_cast<const double *>(fe);
+      for (int32_t j = node_ptr[nd] + lane; j < node_ptr[nd + 1]; j += 32) {
+        const double *f = fe64 + int64_t(node_src[j]) * 3;
+        fs[0] += f[0];
+        fs[1] += f[1];
+        fs[2] += f[2];
+      }
+      tot = warp_sum3<double>(fs[0], fs[1], fs[2]);
     }
-    const double tot = warp_sum3<double>(fs[0], fs[1], fs[2]);
-    double totf = 0.0;
-    if constexpr (DF) totf = double(warp_sum3<float>(accf[0], accf[1], accf[2]));
     if ((lane & 7) == 0 && lane < 24) {
       const int i = lane >> 3;
-      b[r0 + i] = (p ? p[r0 + i] : 0.0) - (tot + totf);
+      b[r0 + i] = (p ? p[r0 + i] : 0.0) - tot;
     }
   }
 }

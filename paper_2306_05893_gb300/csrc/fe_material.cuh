@@ -8,6 +8,7 @@
 #pragma once
 
 #include "../../include/fe_hotpath.h"
+#include "fe_df.cuh"
 
 namespace fe {
 
@@ -38,6 +39,12 @@ template <>
 __device__ __forceinline__ double mexp<double>(double x) { return exp(x); }
 template <>
 __device__ __forceinline__ float mexp<float>(float x) { return expf(x); }
+// double-float: through FP64 (one transcendental per evaluation, outside the
+// laws' matrix arithmetic; the Mooney-Rivlin powers of J avoid it, mr_jpow)
+template <>
+__device__ __forceinline__ dfloat mlog1p<dfloat>(dfloat x) { return dfloat(log1p(double(x))); }
+template <>
+__device__ __forceinline__ dfloat mexp<dfloat>(dfloat x) { return dfloat(exp(double(x))); }
 
 // Kinematics common to every law.
 template <typename T>
@@ -154,6 +161,26 @@ struct Law<FE_NEOHOOKE, T> {
   }
 };
 
+// J^{-2/3} and J^{-4/3} of the Mooney-Rivlin law: exp(-(2/3) log1p(J - 1))
+// (accurate for J near 1); in double-float, J^{-1/3} from the FP32 reciprocal
+// cube root refined by one Newton step t <- t + t (1 - J t^3) / 3 with the
+// residual in double-float (quadratic convergence: about 1e-7 -> 1e-14),
+// no transcendental.
+template <typename T>
+__device__ __forceinline__ void mr_jpow(const Kin<T> &k, T &j23, T &j43) {
+  const T lnJ = mlog1p(k.Jm1);
+  j23 = mexp(T(-2.0 / 3.0) * lnJ);
+  j43 = mexp(T(-4.0 / 3.0) * lnJ);
+}
+template <>
+__device__ __forceinline__ void mr_jpow<dfloat>(const Kin<dfloat> &k, dfloat &j23, dfloat &j43) {
+  const dfloat t0(rcbrtf(k.J.hi), 0.f);
+  const dfloat e = dfloat(1) - k.J * (t0 * t0 * t0);
+  const dfloat t = t0 + t0 * e * dfloat(1.0 / 3.0);
+  j23 = t * t;
+  j43 = j23 * j23;
+}
+
 // Decoupled Mooney-Rivlin: psi = C10 (J^{-2/3} I1 - 3) + C01 (J^{-4/3} I2 - 3)
 // + kappa/2 (J - 1)^2, with I1 = tr C, I2 = ((tr C)^2 - tr C^2)/2.
 template <typename T>
@@ -161,9 +188,10 @@ struct Law<FE_MOONEY_RIVLIN, T> {
   T F[3][3], G[3][3], R[3][3], Cm[3][3], B[3][3];
   T cdd, gam, cff, cxg, cm;
   __device__ void init(const Kin<T> &k, const T H[3][3], T c10, T c01, T kap, T P[3][3]) {
-    T lnJ = mlog1p(k.Jm1);
-    T a = c10 * mexp(T(-2.0 / 3.0) * lnJ);
-    T b = c01 * mexp(T(-4.0 / 3.0) * lnJ);
+    T j23, j43;
+    mr_jpow(k, j23, j43);
+    T a = c10 * j23;
+    T b = c01 * j43;
     T J = k.J;
     // stress: P = G (4a devE + b Q) + kappa (J-1) J G,
     // Q = 4 devE + 8 trE devE - 8 dev(E^2)
