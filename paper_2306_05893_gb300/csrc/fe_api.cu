@@ -398,17 +398,19 @@ int ensure_device(fe_ctx *c) {
     FE_TRY(dalloc(c, d, &d->nv, size_t(c->n)));
   }
   // dataflow application: task lists and counters; the counters start in
-  // their reset state (forward: pending children; backward: 0 done) and
-  // every application leaves the other direction's counters reset
+  // their reset state (forward: the children's pending forward tasks, kept
+  // in df_pend0 for the resets; backward: 0 done) and every application
+  // leaves the other direction's counters reset
   FE_TRY(upload(c, d, &d->apply_fwd, c->apply_fwd));
   FE_TRY(upload(c, d, &d->apply_bwd, c->apply_bwd));
   d->n_apply_fwd = int64_t(c->apply_fwd.size() / 4);
   d->n_apply_bwd = int64_t(c->apply_bwd.size() / 4);
   {
-    std::vector<int> pend(nf), zero(nf, 0);
-    for (int64_t f = 0; f < nf; ++f) pend[f] = c->child_ptr[f + 1] - c->child_ptr[f];
+    std::vector<int> pend(nf, 0), zero(nf, 0);
+    for (int64_t f = 0; f < nf; ++f)
+      if (c->fronts[f].parent >= 0) pend[c->fronts[f].parent] += c->front_nfwd[f];
     FE_TRY(upload(c, d, &d->df_pend, pend));
-    FE_TRY(upload(c, d, &d->df_fdone, zero));
+    FE_TRY(upload(c, d, &d->df_pend0, pend));
     FE_TRY(upload(c, d, &d->df_bdone, zero));
     FE_TRY(upload(c, d, &d->df_ctl, std::vector<int>(4, 0)));
   }

@@ -216,9 +216,10 @@ static int contact_upload(fe_ctx *c, DeviceState *d) {
     std::vector<int32_t> sub;
     for (size_t t = 0; t + 3 < c->apply_fwd.size(); t += 4)
       if (on[c->apply_fwd[t]]) sub.insert(sub.end(), c->apply_fwd.begin() + t, c->apply_fwd.begin() + t + 4);
+    // each front's pending count: its children's forward tasks in the subset
     std::vector<int> pend(size_t(nf), 0);
     for (int64_t f = 0; f < nf; ++f)
-      if (on[f] && c->fronts[f].parent >= 0) pend[c->fronts[f].parent]++;
+      if (on[f] && c->fronts[f].parent >= 0) pend[c->fronts[f].parent] += c->front_nfwd[f];
     // the right-hand sides of one launch (at most kRhsPerLaunch; the task's
     // right-hand side rides in the front id's high byte), each subset task
     // repeated for them in order (the list stays topological)
@@ -242,9 +243,8 @@ static int contact_upload(fe_ctx *c, DeviceState *d) {
     if (!st) st = grow(c, d, &d->c_part, cb[4], size_t(nr) * slots * size_t(fwd_rows(c->opt)) * ts);
     if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_tick), cb[5], size_t(nr) * slots * sizeof(int));
     if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_pendm), cb[6], size_t(nr) * size_t(nf) * sizeof(int));
-    if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_fdm), cb[7], size_t(nr) * size_t(nf) * sizeof(int));
-    if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_bdm), cb[8], size_t(nf) * sizeof(int));
-    if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_ctl), cb[9], 4 * sizeof(int));
+    if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_bdm), cb[7], size_t(nf) * sizeof(int));
+    if (!st) st = grow(c, d, reinterpret_cast<void **>(&d->c_ctl), cb[8], 4 * sizeof(int));
     if (st) return st;
     if (!multi.empty())
       FE_CUDA_TRY(cudaMemcpy(d->c_tasks, multi.data(), multi.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -288,7 +288,7 @@ int contact_resolve(fe_ctx *c, DeviceState *d, bool fp32) {
                                                               d->c_normal, int(gi * nr), m, nr);
     apply_forward_multi_enqueue(c, d, d->cur, fp32, d->c_r,
                                 static_cast<unsigned char *>(d->c_G) + size_t(gi * nr) * size_t(nf) * ts, d->c_tasks,
-                                d->c_ntask, d->c_pend, d->c_pendm, d->c_fdm, d->c_bdm, d->c_ctl, d->c_u, d->c_part,
+                                d->c_ntask, d->c_pend, d->c_pendm, d->c_bdm, d->c_ctl, d->c_u, d->c_part,
                                 d->c_tick, nr, s);
     d->launches += 1;
   }

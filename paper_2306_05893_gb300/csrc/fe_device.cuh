@@ -137,14 +137,14 @@ struct DeviceState {
   void *c_G = nullptr;  // forward solves D^{-1} L^{-1} H^T e_i, [m][n_free] in the solve's precision
   // the fronts on the constraints' paths to the root: their forward tasks
   // (topological order, each repeated for the c_nrhs right-hand sides of a
-  // launch) and their numbers of children on the paths; per right-hand side
+  // launch) and their children's forward tasks on the paths; per right-hand side
   // of a launch: input vectors, update vectors, partial sums, tickets,
   // counters; the launch's control words
   int32_t *c_tasks = nullptr;
-  int *c_pend = nullptr, *c_pendm = nullptr, *c_fdm = nullptr, *c_bdm = nullptr, *c_ctl = nullptr, *c_tick = nullptr;
+  int *c_pend = nullptr, *c_pendm = nullptr, *c_bdm = nullptr, *c_ctl = nullptr, *c_tick = nullptr;
   void *c_r = nullptr, *c_u = nullptr, *c_part = nullptr;
   int64_t c_ntask = 0, c_nrhs = 0;
-  size_t c_bytes[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // capacities of the per-set buffers above
+  size_t c_bytes[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // capacities of the per-set buffers above
   int64_t c_cap = 0, c_m = 0;
   bool c_dirty = true;  // the context's constraint set changed since the last upload
   double *D[2] = {nullptr, nullptr};
@@ -166,7 +166,7 @@ struct DeviceState {
   // still pending; backward: tasks done), task queues and the abort flag
   int32_t *apply_fwd = nullptr, *apply_bwd = nullptr;
   int64_t n_apply_fwd = 0, n_apply_bwd = 0;
-  int *df_pend = nullptr, *df_fdone = nullptr, *df_bdone = nullptr, *df_ctl = nullptr;
+  int *df_pend = nullptr, *df_pend0 = nullptr, *df_bdone = nullptr, *df_ctl = nullptr;
   int df_grid = 0;                                          // resident CTAs of the application kernels
   mutable int df_hold = -1;        // fe_debug_hold_front: front held for the next application, or -1
   int df_hold_extra = 0;
@@ -323,7 +323,7 @@ int contact_resolve(fe_ctx *c, DeviceState *d, bool fp32);
 // forward solves of nrhs right-hand sides in one launch over a subset of
 // fronts closed under parents (fe_factor.cu)
 void apply_forward_multi_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *yp,
-                                 const int32_t *tasks, int64_t ntask, const int *pend_init, int *pend, int *fdone,
+                                 const int32_t *tasks, int64_t ntask, const int *pend_init, int *pend,
                                  int *bdone, int *ctl, void *u, void *part, int *tickets, int nrhs, cudaStream_t s);
 void apply_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *z,
                    cudaStream_t s, const double *done = nullptr);

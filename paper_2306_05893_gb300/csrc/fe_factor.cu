@@ -1615,6 +1615,19 @@ __device__ __forceinline__ bool dep_wait(const int *p, int target, int *abort_wo
 // combined in chunk order by the last one (deterministic).
 constexpr int kPre = 4;  // gather sources prefetched per position
 
+// Asynchronous 4- or 8-byte copy global -> shared (cp.async): a task starts
+// the copies of the inputs that no task of its launch writes before its
+// dependency wait, and waits for them (cp_async_wait_all, the issuing
+// thread's own copies) after it, so their latency overlaps the wait without
+// holding registers.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *smem, const void *gmem) {
+  static_assert(BYTES == 4 || BYTES == 8, "4- or 8-byte copies");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // One task of look-ahead in the persistent apply kernels: a CTA takes the
 // index of its next task while it starts the current one, and lanes 0-5 of
 // warp 0 load that task's descriptor (its int4 and the 96-byte DFront of its
@@ -1658,7 +1671,7 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
                                                   const int32_t *__restrict__ wsrc, const TV *__restrict__ r,
                                                   TV *__restrict__ ubuf, TV *__restrict__ yperm,
                                                   TV *__restrict__ part, int *__restrict__ tickets,
-                                                  int *pend, int *fdone, int *bdone, int *ctl, int nfronts,
+                                                  int *pend, int *bdone, int *ctl, int nfronts,
                                                   int *flags, uint64_t wait_ns, const double *__restrict__ done,
                                                   RhsStrides rs = RhsStrides{}) {
   static_assert(kFwdCols == 256, "one gathered column per thread");
@@ -1667,6 +1680,7 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
   constexpr int RB = 32 * VW;
   __shared__ TV gpart[8 * RB];
   __shared__ TV wp[kFwdCols];
+  __shared__ double s_dinv[RB];
   __shared__ int s_task, s_next, s_ok;
   __shared__ int4 s_t;
   __shared__ __align__(16) DFront s_fr;
@@ -1698,7 +1712,6 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     TV *const pv = part + rk * rs.p;
     int *const tv = tickets + rk * rs.t;
     int *const pendv = pend + rk * rs.f;
-    int *const fdonev = fdone + rk * rs.f;
     const int32_t p = fr.npiv, m = fr.m;
     const int32_t jmax = (r0 + RB < p) ? r0 + RB : p;
     const int32_t fc = fr.fcols;  // this front's columns per task (at most kFwdCols)
@@ -1713,6 +1726,15 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
     }
 #pragma unroll
     for (int k = 0; k < kPre; ++k) gsrc[k] = gq0 + k < gq1 ? wsrc[gq0 + k] : -1;
+    // inputs that no task of this launch writes are copied to shared memory
+    // asynchronously before the wait: this column's entry of r, and D^{-1}
+    // of this block's pivot rows
+    if (jg < j1) cp_async_small<sizeof(TV)>(wp + (jg - j0), rv + gperm);
+#pragma unroll
+    for (int k = 0; k < (RB + 255) / 256; ++k) {
+      const int32_t tt = int32_t(threadIdx.x) + 256 * k, i = r0 + tt;
+      if (tt < RB && i < p && i < m) cp_async_small<8>(s_dinv + tt, Dinv + fr.first + i);
+    }
     const int32_t ie = r0 + int32_t(threadIdx.x);
     int32_t eq0 = 0, eq1 = 0, esrc[kPre];
     if (threadIdx.x < RB && ie >= p && ie < m) {
@@ -1735,11 +1757,12 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
       cv[u] = (live && jq + 8 * u < j1) ? *reinterpret_cast<const V *>(yc + int64_t(jq + 8 * u) * fr.ldy) : V{};
     // the children's update vectors must be complete
     if (threadIdx.x == 0) s_ok = dep_wait(pendv + fid, 0, ctl + 2, flags, wait_ns);
+    cp_async_wait_all();
     __syncthreads();
     bool wnz = false;
     if (s_ok) {
       if (jg < j1) {
-        TV w = rv[gperm];
+        TV w = wp[jg - j0];
 #pragma unroll
         for (int k = 0; k < kPre; ++k)
           if (gsrc[k] >= 0) w += __ldcg(uv + gsrc[k]);
@@ -1809,8 +1832,11 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
         for (int k = 0; k < (RB + 255) / 256; ++k) {
           const int tt = threadIdx.x + 256 * k;
           TV sm = TV(0);
-          if (tt < RB)
+          if (tt < RB) {
+            // in chunk order; unrolled so that the loads overlap
+#pragma unroll 8
             for (int ch = 0; ch < nch; ++ch) sm += __ldcg(pv + int64_t(slot + ch) * RB + tt);
+          }
           sums[k] = sm;
         }
       }
@@ -1822,19 +1848,18 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
         const int32_t i = r0 + tt;
         if (tt >= RB || i >= m) continue;
         if (i < p)
-          yv[fr.first + i] = TV(double(sums[k]) * Dinv[fr.first + i]);
+          yv[fr.first + i] = TV(double(sums[k]) * s_dinv[tt]);
         else
           uv[fr.u_off + i - p] = csum + sums[k];
       }
     }
-    // completion: the front's last task releases the parent (ordered
-    // atomics by thread 0 after the barrier, as in last_of_block; the last
-    // task's acquire on fdone carries the front's other tasks' stores into
-    // its release of the parent's counter)
+    // completion: the parent's counter holds its children's pending tasks,
+    // so every task releases its share without waiting for an answer (a
+    // release reduction by thread 0 after the barrier, cumulative over the
+    // CTA's stores as in last_of_block)
     __syncthreads();
     if (threadIdx.x == 0) {
-      const int c = atom_add_acq_rel(fdonev + fid, 1);
-      if (c == fr.nfwd - 1 && fr.parent >= 0) red_add_release(pendv + fr.parent, -1);
+      if (fr.parent >= 0) red_add_release(pendv + fr.parent, -1);
       s_task = s_next;
     }
     if (threadIdx.x < 32) store_desc(nd, s_t, s_fr, threadIdx.x);
@@ -1878,21 +1903,22 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
                                                   const int32_t *__restrict__ upd_rows_old,
                                                   const TV *__restrict__ yperm, TV *__restrict__ z,
                                                   TV *__restrict__ part, int *__restrict__ tickets,
-                                                  int *pend, int *fdone, int *bdone, int *ctl, int nfronts,
-                                                  int *flags, uint64_t wait_ns, const double *__restrict__ done) {
+                                                  int *pend, const int *__restrict__ pend0, int *bdone, int *ctl,
+                                                  int nfronts, int *flags, uint64_t wait_ns,
+                                                  const double *__restrict__ done) {
   using V = typename Vec16<TF>::type;
   constexpr int VW = Vec16<TF>::n;
   constexpr int BR = sizeof(TF) == 2 ? 2 * kBwdRows : kBwdRows;  // rows per task
   constexpr int XS = BR / 256;                                   // staged rows per thread
   __shared__ __align__(16) TV xs[BR];
+  __shared__ int s_zpos[kBwdCols];
   __shared__ int s_task, s_next, s_ok;
   __shared__ int4 s_t;
   __shared__ __align__(16) DFront s_fr;
   if (done && *done != 0.0) return;
-  for (int i = blockIdx.x * 256 + threadIdx.x; i < nfronts; i += gridDim.x * 256) {
-    pend[i] = fronts[i].child_end - fronts[i].child_begin;
-    fdone[i] = 0;
-  }
+  // the forward counters for the next application: each front's children's
+  // forward tasks
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < nfronts; i += gridDim.x * 256) pend[i] = pend0[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl[0] = 0;
     ctl[2] = 0;
@@ -1949,16 +1975,31 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
         cv[h][k] = i < xb ? *reinterpret_cast<const V *>(yc[k] + i) : V{};
       }
     }
+    // copied to shared memory asynchronously before the wait: the pivot
+    // rows of x, which the forward launch wrote, and the output positions of
+    // the task's columns; the update rows of x come from the parent's tasks
+#pragma unroll
+    for (int k = 0; k < XS; ++k) {
+      const int32_t tt = int32_t(threadIdx.x) + 256 * k;
+      if (tt < xb - xa && xsrc[k] >= 0) cp_async_small<sizeof(TV)>(xs + tt, yperm + xsrc[k]);
+    }
+    if (threadIdx.x < kBwdCols) {
+      if (c0 + int32_t(threadIdx.x) < p)
+        cp_async_small<4>(s_zpos + threadIdx.x, perm + fr.first + c0 + int32_t(threadIdx.x));
+      else
+        s_zpos[threadIdx.x] = -1;
+    }
     // the parent's solution entries must be complete
     if (threadIdx.x == 0)
       s_ok = fr.parent < 0 ? 1 : dep_wait(bdone + fr.parent, fronts[fr.parent].nbwd, ctl + 3, flags, wait_ns);
+    cp_async_wait_all();
     __syncthreads();
     bool xnz = false;
 #pragma unroll
     for (int k = 0; k < XS; ++k) {
       const int32_t tt = int32_t(threadIdx.x) + 256 * k;
       if (tt < xb - xa) {
-        const TV xv = (xsrc[k] == -1 || !s_ok) ? TV(0) : (xsrc[k] >= 0 ? yperm[xsrc[k]] : __ldcg(z + (-2 - xsrc[k])));
+        const TV xv = (xsrc[k] == -1 || !s_ok) ? TV(0) : (xsrc[k] >= 0 ? xs[tt] : __ldcg(z + (-2 - xsrc[k])));
         xs[tt] = xv;
         xnz = xnz || xv != TV(0);
       }
@@ -2001,8 +2042,10 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
     if (slot < 0) {
       if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (jc[k] < p) z[perm[fr.first + jc[k]]] = acc[k];
+        for (int k = 0; k < 4; ++k) {
+          const int32_t zp = s_zpos[w + 8 * k];
+          if (zp >= 0) z[zp] = acc[k];
+        }
       }
     } else {
       const int32_t k_first = a0 / br;
@@ -2014,9 +2057,11 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
       }
       if (last_of_block(tickets + slot, nch) && threadIdx.x < kBwdCols) {
         TV sm = TV(0);
+        // in chunk order; unrolled so that the loads overlap
+#pragma unroll 8
         for (int ch = 0; ch < nch; ++ch) sm += __ldcg(part + int64_t(slot + ch) * kBwdCols + threadIdx.x);
-        const int32_t j = c0 + threadIdx.x;
-        if (j < p) z[perm[fr.first + j]] = sm;
+        const int32_t zp = s_zpos[threadIdx.x];
+        if (zp >= 0) z[zp] = sm;
       }
     }
     __syncthreads();
@@ -2119,20 +2164,18 @@ int factor_enqueue(fe_ctx *c, DeviceState *d, int buf, bool fp32, const void *Af
 // The per-right-hand-side forward counters of a multi-right-hand-side
 // launch set to the subset's own dependencies, and its control words cleared
 // (see apply_forward_multi_enqueue).
-__global__ void multi_reset_kernel(const int *__restrict__ pend_init, int *pend, int *fdone, int *ctl, int nfronts,
+__global__ void multi_reset_kernel(const int *__restrict__ pend_init, int *pend, int *ctl, int nfronts,
                                    int64_t total) {
-  for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < total; i += int64_t(gridDim.x) * 256) {
+  for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < total; i += int64_t(gridDim.x) * 256)
     pend[i] = pend_init[i % nfronts];
-    fdone[i] = 0;
-  }
   if (blockIdx.x == 0 && threadIdx.x < 4) ctl[threadIdx.x] = 0;
 }
 
 static uint64_t wait_ns_of(const fe_ctx *c) { return uint64_t(c->opt.dep_wait_s * 1e9); }
 
-// fe_debug_hold_front: one more pending child on a front for one application,
-// so its forward tasks wait on a count that nothing reaches (the backward
-// launch resets every counter afterwards)
+// fe_debug_hold_front: more pending child tasks on a front for one
+// application, so its forward tasks wait on a count that nothing reaches
+// (the backward launch resets every counter afterwards)
 __global__ void hold_front_kernel(int *pend, int front, int extra) { pend[front] += extra; }
 
 void launch_pending_hold(const DeviceState *d, cudaStream_t s) {
@@ -2175,9 +2218,9 @@ static void apply_levels_with(const fe_ctx *c, const DeviceState *d, int buf, co
   d->launches += 2;
   fwd_kernel<TF, TV><<<gf, 256, 0, s>>>(reinterpret_cast<const int4 *>(d->apply_fwd), d->n_apply_fwd, d->fronts, Y,
                                         Dinv, d->perm, d->wsrc_ptr, d->wsrc, r, u, yp, part_f, tick_f, d->df_pend,
-                                        d->df_fdone, d->df_bdone, d->df_ctl, nf, flags, wait_ns_of(c), done);
+                                        d->df_bdone, d->df_ctl, nf, flags, wait_ns_of(c), done);
   bwd_kernel<TF, TV><<<gb, 256, 0, s>>>(reinterpret_cast<const int4 *>(d->apply_bwd), d->n_apply_bwd, d->fronts, Y,
-                                        d->perm, d->upd_rows_old, yp, z, part_b, tick_b, d->df_pend, d->df_fdone,
+                                        d->perm, d->upd_rows_old, yp, z, part_b, tick_b, d->df_pend, d->df_pend0,
                                         d->df_bdone, d->df_ctl, nf, flags, wait_ns_of(c), done);
 }
 
@@ -2195,17 +2238,17 @@ static void apply_levels(const fe_ctx *c, const DeviceState *d, int buf, const T
 // repeated for the right-hand sides k < nrhs with k in the front id's high
 // byte; every right-hand side k has its own input r + k n, pivot output
 // yp + k n_free, update vectors u + k u_total, partial sums, tickets and
-// per-front counters (pend, fdone: nf each, pend set from pend_init, the
-// number of each front's children in the subset), and the launch has its
+// per-front counters (pend, nf each, set from pend_init: the forward tasks of
+// each front's children in the subset), and the launch has its
 // own control words, so the context's application state is not touched.  The
 // caller clears yp and u once (outside the subset they stay zero) and the
 // tickets once (the last CTA of a split block resets its ticket).
 void apply_forward_multi_enqueue(const fe_ctx *c, const DeviceState *d, int buf, bool fp32, const void *r, void *yp,
-                                 const int32_t *tasks, int64_t ntask, const int *pend_init, int *pend, int *fdone,
+                                 const int32_t *tasks, int64_t ntask, const int *pend_init, int *pend,
                                  int *bdone, int *ctl, void *u, void *part, int *tickets, int nrhs, cudaStream_t s) {
   const int nf = int(c->fronts.size());
   const int64_t total = int64_t(nf) * nrhs;
-  multi_reset_kernel<<<unsigned(std::min<int64_t>(1024, (total + 255) / 256)), 256, 0, s>>>(pend_init, pend, fdone,
+  multi_reset_kernel<<<unsigned(std::min<int64_t>(1024, (total + 255) / 256)), 256, 0, s>>>(pend_init, pend,
                                                                                            ctl, nf, total);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device);
@@ -2219,19 +2262,19 @@ void apply_forward_multi_enqueue(const fe_ctx *c, const DeviceState *d, int buf,
     fwd_kernel<__half, float><<<g, 256, 0, s>>>(tk, ntask, d->fronts, static_cast<const __half *>(d->Yh[buf]), Dinv,
                                                 d->perm, d->wsrc_ptr, d->wsrc, static_cast<const float *>(r),
                                                 static_cast<float *>(u), static_cast<float *>(yp),
-                                                static_cast<float *>(part), tickets, pend, fdone, bdone, ctl, nf,
+                                                static_cast<float *>(part), tickets, pend, bdone, ctl, nf,
                                                 d->flags, wait_ns_of(c), nullptr, rs);
   else if (fp32)
     fwd_kernel<float, float><<<g, 256, 0, s>>>(tk, ntask, d->fronts, static_cast<const float *>(d->Y[buf]), Dinv,
                                                d->perm, d->wsrc_ptr, d->wsrc, static_cast<const float *>(r),
                                                static_cast<float *>(u), static_cast<float *>(yp),
-                                               static_cast<float *>(part), tickets, pend, fdone, bdone, ctl, nf,
+                                               static_cast<float *>(part), tickets, pend, bdone, ctl, nf,
                                                d->flags, wait_ns_of(c), nullptr, rs);
   else
     fwd_kernel<double, double><<<g, 256, 0, s>>>(tk, ntask, d->fronts, static_cast<const double *>(d->Y[buf]), Dinv,
                                                  d->perm, d->wsrc_ptr, d->wsrc, static_cast<const double *>(r),
                                                  static_cast<double *>(u), static_cast<double *>(yp),
-                                                 static_cast<double *>(part), tickets, pend, fdone, bdone, ctl, nf,
+                                                 static_cast<double *>(part), tickets, pend, bdone, ctl, nf,
                                                  d->flags, wait_ns_of(c), nullptr, rs);
 }
 
