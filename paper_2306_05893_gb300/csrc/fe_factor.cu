@@ -1790,16 +1790,18 @@ __global__ void __launch_bounds__(256, 4) fwd_kernel(const int4 *__restrict__ ta
         TV wv[kFwdU];
 #pragma unroll
         for (int u = 0; u < kFwdU; ++u) wv[u] = jq + 8 * u < j1 ? wp[jq + 8 * u - j0] : TV(0);
+        // each column's registers are reloaded with the next round's column
+        // as soon as they are used, so the thread's loads stay in flight
+        // while it computes
+        const int32_t jn = jq + 8 * kFwdU;
 #pragma unroll
-        for (int e = 0; e < VW; ++e) {
+        for (int u = 0; u < kFwdU; ++u) {
 #pragma unroll
-          for (int u = 0; u < kFwdU; ++u) acc[e] += TV(vget(cv[u], e)) * wv[u];
+          for (int e = 0; e < VW; ++e) acc[e] += TV(vget(cv[u], e)) * wv[u];
+          cv[u] = jn + 8 * u < j1 ? *reinterpret_cast<const V *>(yc + int64_t(jn + 8 * u) * fr.ldy) : V{};
         }
-        jq += 8 * kFwdU;
+        jq = jn;
         if (jq >= j1) break;
-#pragma unroll
-        for (int u = 0; u < kFwdU; ++u)
-          cv[u] = jq + 8 * u < j1 ? *reinterpret_cast<const V *>(yc + int64_t(jq + 8 * u) * fr.ldy) : V{};
       }
     }
     NextDesc nd{};
@@ -2008,9 +2010,11 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
     const bool xany = __syncthreads_or(xnz) != 0;
     TV acc[4] = {TV(0), TV(0), TV(0), TV(0)};
     for (int32_t off = 0; xany;) {
+      // each row block's registers are reloaded with the next round's rows
+      // as soon as they are used (the thread's loads stay in flight)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int32_t i = ist + off + 32 * VW * h;
+        const int32_t i = ist + off + 32 * VW * h, inext = i + 64 * VW;
         if (i < xb) {
           TV xv[VW];
           xs_vec<VW>(xs + (i - xa), xv);
@@ -2020,17 +2024,11 @@ __global__ void __launch_bounds__(256, 4) bwd_kernel(const int4 *__restrict__ ta
             for (int q = 0; q < VW; ++q) acc[k] += TV(vget(cv[h][k], q)) * xv[q];
           }
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cv[h][k] = inext < xb ? *reinterpret_cast<const V *>(yc[k] + inext) : V{};
       }
       off += 64 * VW;
       if (xa + off >= xb) break;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int32_t i = ist + off + 32 * VW * h;
-          cv[h][k] = i < xb ? *reinterpret_cast<const V *>(yc[k] + i) : V{};
-        }
-      }
     }
     NextDesc nd{};
     if (threadIdx.x < 32) nd = load_desc(tasks, fronts, s_next, ntask, threadIdx.x);
