@@ -284,15 +284,20 @@ __device__ __forceinline__ double pivot_inverse(double d, int *flags, bool repor
 // The eliminations run in TF with the pivots of the running Schur complement
 // in TF; S ends holding the final unscaled columns W = L d and Lsc the
 // scaled L.  The pivots D are accumulated beside them from the final columns
-// in FP64 (FP64 factor) or double-float (FP32 factor),
-// d_i = a_ii - sum_j W_ij^2 / d_j, by a ninth warp that follows the
-// sub-blocks as they are published (thread 0 releases a progress word after
-// the barrier that ends step B, the warp acquires it): per sub-block the
-// squares of its 16 columns are formed up front, then 16 steps each take a
-// pivot's inverse and fold its column into every later row at once (lane l:
-// rows l and l + 32), so only the pivots' recurrence is serial.  The FP32
-// elimination takes the fast reciprocal of its own pivots; the stored L is
-// W times the inverses of the pivot warp's pivots.  L_KK^{-1} (written into
+// by a ninth warp that follows the sub-blocks as they are published (thread 0
+// releases a progress word after the barrier that ends step B, the warp
+// acquires it; lane l keeps rows l and l + 32).  FP32 factor: in
+// double-float, d_i = a_ii - sum_j W_ij L_ij, each term the exact product of
+// the elimination's final W and L entries, so no pivot waits for an earlier
+// one and the 64 inverses are taken at once at the end; the sum of the
+// squares of W over the pivot warp's own pivots (a serial recurrence of 64
+// double-float reciprocals) made this warp the block's critical path, and it
+// is no more accurate, since W and L carry the FP32 elimination's rounding
+// either way.  FP64 factor: d_i = a_ii - sum_j W_ij^2 / d_j in FP64, 16 steps
+// per sub-block each taking a pivot's inverse and folding its column into
+// every later row at once.  The FP32 elimination takes the fast reciprocal of
+// its own pivots; the stored L is W times the inverses of the pivot warp's
+// pivots.  L_KK^{-1} (written into
 // Y[K, K]) is formed after the elimination by blocked inversion of the unit
 // lower L: the diagonal
 // 16 x 16 inverses by one warp each, then, one block diagonal at a time,
@@ -408,41 +413,22 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
       }
       __syncwarp();
       if (__shfl_sync(kAll, late, 0)) break;
-      // the squares of the sub-block's final columns in both of the lane's
-      // rows, formed before the chain (only the pivots' own recurrence is
-      // serial: every row's update of a step is one SIMD instruction stream)
       const int i0 = lane, i1 = lane + 32;
       if constexpr (kDF) {
-        DF sq0[16], sq1[16];
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const float w0 = float(S[i0][b0 + jj]), w1 = float(S[i1][b0 + jj]);
-          sq0[jj] = df_two_prod(w0, w0);
-          sq1[jj] = df_two_prod(w1, w1);
-        }
-        // the chain has no branch and no store: the inverses stay in
-        // registers until the sub-block is done, a bad pivot is flagged once
-        DF invs[16];
-        bool bad = false;
+        // the sub-block's final columns folded into every later row as exact
+        // products W_ij L_ij with the elimination's own scaled column L (no
+        // pivot waits for an earlier pivot's inverse: only each row's sum is
+        // a chain, and the two rows of a lane interleave)
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           const int j = b0 + jj;
-          invs[jj] = {1.f, 0.f};
           if (j < kb) {  // (warp-uniform)
-            const float djh = __shfl_sync(kAll, j < 32 ? p0.hi : p1.hi, j & 31);
-            const float djl = __shfl_sync(kAll, j < 32 ? p0.lo : p1.lo, j & 31);
-            bad = bad || !(djh > 0.f);
-            const DF inv = df_pivot_inverse({djh, djl});
-            invs[jj] = inv;
-            const DF n0 = df_sub(p0, df_mul(sq0[jj], inv)), n1 = df_sub(p1, df_mul(sq1[jj], inv));
+            const DF n0 = df_sub(p0, df_two_prod(float(S[i0][j]), float(Lsc[i0][j])));
+            const DF n1 = df_sub(p1, df_two_prod(float(S[i1][j]), float(Lsc[i1][j])));
             p0 = (i0 > j && i0 < kb) ? n0 : p0;
             p1 = (i1 > j && i1 < kb) ? n1 : p1;
           }
         }
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj)
-          if (lane == jj && b0 + jj < kb) s_invf[b0 + jj] = invs[jj];
-        if (bad && lane == 0) atomicOr(flags, FLAG_PIVOT);
       } else {
         double sq0[16], sq1[16];
 #pragma unroll
@@ -464,6 +450,12 @@ __global__ void __launch_bounds__(kDiagThreads) front_diag_kernel(const int32_t 
       }
     }
     if constexpr (kDF) {
+      // the pivots are final: their inverses, all at once (a bad pivot is
+      // flagged once; the inverse of a non-positive one is taken of 1)
+      const bool bad = (lane < kb && !(p0.hi > 0.f)) || (lane + 32 < kb && !(p1.hi > 0.f));
+      if (__any_sync(kAll, bad) && lane == 0) atomicOr(flags, FLAG_PIVOT);
+      if (lane < kb) s_invf[lane] = df_pivot_inverse(p0);
+      if (lane + 32 < kb) s_invf[lane + 32] = df_pivot_inverse(p1);
       dgf[lane] = p0;
       dgf[lane + 32] = p1;
     } else {
