@@ -500,14 +500,16 @@ def _streaming_rooflines(wl, info, stage_ms, stage_calls, hbm, peak_kind, args, 
     kept, nblk = info["ntrip_kept"], info["n_blocks"]
     nodes = wl.mesh.n_nodes
     rest = (10 if npe == 4 else 200) * 8
+    df_force = mixed and not args.element_fp64
     bytes_ = {
-        # per element: K_e and f_e out, rest data + 3 parameters + connectivity in;
-        # per node: q and X in
-        "element": E * ((3 * npe) ** 2 * kb + 3 * npe * 8 + rest + 24 + 4 * npe) + nodes * 48,
+        # per element: K_e and f_e out (f_e as FP64 or as float pairs, 8 B
+        # either way), rest data + 3 parameters (doubles or float pairs) +
+        # connectivity in; per node: q and X, or the float pairs of q - X
+        "element": E * ((3 * npe) ** 2 * kb + 3 * npe * 8 + rest + 24 + 4 * npe) + nodes * (24 if df_force else 48),
         # per gathered triplet its K_e value; per block its source list entry
         # (kept / 9 of them), bsrc_ptr, column and mass; per slot A (and its
-        # FP64 copy in the mixed path); per element its forces and incidence;
-        # per row rowptr and v, p, b
+        # float-pair copy in the mixed path); per element its forces and
+        # incidence; per row rowptr and v, p, b
         "assembly": kept * kb + (kept // 9) * 4 + nblk * 16 + nnz * (ab + (8 if mixed else 0))
         + E * (3 * npe * 8 + 4 * npe) + n * (4 + 24) + nodes * 8,
         "spmv": nnz * (ab + 4) + (n + 1) * 4 + 2 * n * ab,
@@ -515,8 +517,12 @@ def _streaming_rooflines(wl, info, stage_ms, stage_calls, hbm, peak_kind, args, 
     }
     yb = 2 if (mixed and args.precond_fp16) else ab
     bytes_["apply"] = 2 * info["y_nnz"] * yb + 6 * info["n_free"] * ab + 2 * n * ab
+    # the SpMV and the residual run the variant the per-context autotuner
+    # chose (node-block or CSR); their bytes are the CSR product's
     kern = {"element": "tet_kernel" if npe == 4 else "hex_kernel", "assembly": "assemble_block_kernel",
-            "spmv": "spmv_dot_kernel", "residual": "residual_kernel", "apply": "fwd_kernel + bwd_kernel"}
+            "spmv": "bspmv_kernel / spmv_dot_kernel",
+            "residual": ("bres_df_kernel / residual_df_kernel" if mixed else "bspmv_kernel / residual_kernel"),
+            "apply": "fwd_kernel + bwd_kernel"}
     out = {}
     for k, b in bytes_.items():
         calls = stage_calls.get(k, 0)
