@@ -88,11 +88,13 @@ typedef struct {
 typedef struct {
   int32_t precision;      /* FE_FP64: all FP64.  FE_MIXED: FP32 element
                              tangents K_e, inner PCG (SpMV, vectors), factor
-                             and triangular solves; FP64 element forces f_e,
-                             FP64 sums in the assembly (A is kept in FP64 for
-                             the residual and in FP32 for the inner solves),
-                             FP64 right-hand side b, residual, dot products
-                             and pivots; iterative refinement to tol.       */
+                             and triangular solves; FP64-accurate element
+                             forces f_e, assembly sums and residual in
+                             double-float (pairs of floats, about 2^-46 per
+                             operation: A is kept as float pairs for the
+                             residual and in FP32 for the inner solves), FP64
+                             right-hand side b, dot products, and pivots summed
+                             in double-float; iterative refinement to tol.   */
   double tol;             /* stop when ||b - A a||_2 <= tol ||b||_2           */
   int32_t max_iters;      /* PCG iterations per step (all refinement sweeps)  */
   int32_t refactor_every; /* R: factor A_s at steps s = 0 mod R on the side
@@ -161,10 +163,11 @@ typedef struct {
                              (0: 1 s); a wait that runs out stops the
                              application and the call reports FE_ERR_TIMEOUT */
   int32_t element_fp64;   /* FE_MIXED only: 1 = the element kernel computes
-                             and stores the tangents K_e in FP64 too, so the
-                             FP64 copy of A equals the FP64 path's A and the
-                             refined solution reaches tol against the FP64
-                             system; the inner PCG, factor and solves stay
+                             and stores the tangents K_e and forces in FP64
+                             too, so the FP64-accurate copy of A carries the
+                             FP64 path's sums and the refined solution reaches
+                             tol against the FP64 system; the inner PCG,
+                             factor and solves stay
                              FP32 (0: FP32 tangents, see precision)          */
   int32_t warm_start;     /* 1: a step's PCG starts from the previous step's
                              acceleration instead of 0 (the stopping test
@@ -293,12 +296,14 @@ int fe_get_state(fe_ctx *ctx, double *q, double *v);
 
 /* Element kernel alone at positions q ([n], NULL: current state):
  * f_e [n_elems * 3npe] and K_e [n_elems * (3npe)^2] in fill order (FP64
- * outputs; FP32 tangents are widened).  Either output may be NULL. */
+ * outputs; FP32 tangents are widened, double-float forces summed to FP64).
+ * Either output may be NULL. */
 int fe_element_eval(fe_ctx *ctx, const double *q, double *f_e, double *K_e);
 
 /* Element kernel + fast assembly at the current state with external force
- * p_ext [n] (NULL = 0): A_vals [nnz] on the CSR pattern (the FP64 matrix the
- * residual uses: FP64 sums of the element tangents) and b [n]
+ * p_ext [n] (NULL = 0): A_vals [nnz] on the CSR pattern (the FP64-accurate
+ * matrix the residual uses: FP64, or double-float with FE_MIXED, sums of the
+ * element tangents) and b [n]
  * (Eq. "dynamic equation2"; fixed rows: A_ii = 1, b_i = 0).  Either output
  * may be NULL. */
 int fe_assemble(fe_ctx *ctx, const double *p_ext, double *A_vals, double *b);
