@@ -4,8 +4,9 @@ the C ABI, on seeded meshes that span several tiles and ragged tails.
 Tolerances (relative to the largest entry of the oracle quantity):
   FP64 path: element outputs and assembled A, b <= 1e-12 (same sums, other
   rounding order); positions after N steps <= 1e-8 of the displacement.
-  Mixed path (FP64 element forces, FP32 element tangents, FP64 assembly sums
-  and residual, FP32 inner solve and factor): forces <= 1e-12, tangents
+  Mixed path (FP64-accurate element forces, assembly sums and residual in
+  double-float, FP32 element tangents, FP32 inner solve and factor): forces
+  <= 1e-12, tangents
   <= 2e-5 (FP32 rounding of the contraction), A and b <= MIX_SYS (the FP32
   tangents' rounding, about 6e-8 of each entry, summed); positions after N
   steps <= MIX_POS of the displacement.  With element_fp64 the tangents, A
@@ -105,6 +106,33 @@ def test_exact_factor_inverts_A(gpu_lib, kind, leaf):
     zo = O.direct_solve(S, r)
     assert np.linalg.norm(z - zo) <= 1e-9 * np.linalg.norm(zo)
     assert np.all(z[fixed] == 0.0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind,law", [("tet", fi.MOONEY_RIVLIN), ("hex", fi.NEOHOOKE)])
+def test_mixed_refinement_residual_is_the_fp64_residual(gpu_lib, kind, law):
+    """The mixed path refines until its double-float residual b - A2 x2 (A
+    and the iterate as float pairs) is below tol; recomputed in FP64 on the
+    host from the same system (fe_assemble returns A2 summed to FP64, b is
+    FP64) and the step's acceleration (from rest, a = v+ / h), the residual
+    meets the tolerance too and agrees with the reported one to 1e-3 of
+    the tolerance (the pairs carry ~48 bits: their rounding is far below)."""
+    import scipy.sparse as sp
+    mesh = _mesh(kind)
+    q, _, p = _state(mesh, amp=0.01, seed=5)
+    v = np.zeros_like(q)
+    ctx = _ctx(gpu_lib, mesh, law, 1)
+    ctx.set_state(q, v)
+    A, b = ctx.assemble(p)
+    qo, vo = np.empty_like(q), np.empty_like(q)
+    info = ctx.step(p, qo, vo)
+    a = vo / 0.01
+    S = sp.csr_matrix((A, ctx.colind, ctx.rowptr), shape=(ctx.n, ctx.n))
+    rel = np.linalg.norm(b - S @ a) / np.linalg.norm(b)
+    print(f"{kind}: reported {info.rel_residual:.3e}, FP64 recomputed {rel:.3e}, {info.refinements} sweeps")
+    assert info.refinements >= 2
+    assert rel <= 1e-8
+    assert abs(rel - info.rel_residual) <= 1e-11
     ctx.close()
 
 
