@@ -24,18 +24,6 @@ __device__ __forceinline__ void df_add_to(float &hi, float &lo, float ph, float 
   hi = s;
 }
 
-// (hi, lo) += a b for floats a, b (the product exact through FMA)
-__device__ __forceinline__ void df_fma_to(float &hi, float &lo, float a, float b) {
-  const float p = a * b;
-  df_add_to(hi, lo, p, fmaf(a, b, -p));
-}
-
-// (hi, lo) += (a.x + a.y) b for a pair a and a float b
-__device__ __forceinline__ void df_fma_to(float &hi, float &lo, float2 a, float b) {
-  const float p = a.x * b;
-  df_add_to(hi, lo, p, fmaf(a.y, b, fmaf(a.x, b, -p)));
-}
-
 // (hi, lo) += (a.x + a.y)(b.x + b.y) (the lo * lo term, ~2^-48 of the product, dropped)
 __device__ __forceinline__ void df_fma_to(float &hi, float &lo, float2 a, float2 b) {
   const float p = a.x * b.x;
