@@ -192,7 +192,7 @@ typedef struct {
                              dependency chains more than by its CTA count).
                              The result does not depend on it.               */
   int32_t update_bf16;    /* FE_MIXED: 1 (default) applies each superpanel's
-                             deferred trailing update (the rank-256 updates
+                             deferred trailing update (the rank-512 updates
                              of the rest of a front, the bulk of the factor's
                              flops) on the tensor cores with BF16 operands and
                              FP32 accumulation (tcgen05 kind::f16), read by

@@ -170,25 +170,25 @@ int encode_tensor_maps(fe_ctx *c, DeviceState *d) {
   }
   int st = upload(c, d, reinterpret_cast<CUtensorMap **>(&d->tmaps), maps);
   if (st || !c->opt.update_bf16) return st;
-  // update_bf16: the K-major BF16 copies of a superpanel ([rows][256], rows
-  // of 512 bytes) and one map each, 128 rows x 64 columns per box (128 bytes:
+  // update_bf16: the K-major BF16 copies of a superpanel ([rows][kSuper],
+  // rows of 2 kSuper bytes) and one map each, 128 rows x 64 columns per box (128 bytes:
   // one 128-byte swizzle span, the MMA operand layout); zeroed once, so that
   // rows a copy never receives read as finite values
   const int64_t rows_wl = std::max<int64_t>(c->w_total, 1), rows_y = std::max<int64_t>(c->n_free, 1);
-  st = dallocv(c, d, &d->bt_w, size_t(rows_wl) * 256 * 2);
-  if (!st) st = dallocv(c, d, &d->bt_l, size_t(rows_wl) * 256 * 2);
-  if (!st) st = dallocv(c, d, &d->bt_y, size_t(rows_y) * 256 * 2);
+  st = dallocv(c, d, &d->bt_w, size_t(rows_wl) * kSuper * 2);
+  if (!st) st = dallocv(c, d, &d->bt_l, size_t(rows_wl) * kSuper * 2);
+  if (!st) st = dallocv(c, d, &d->bt_y, size_t(rows_y) * kSuper * 2);
   if (st) return st;
-  FE_CUDA_TRY(cudaMemset(d->bt_w, 0, size_t(rows_wl) * 512));
-  FE_CUDA_TRY(cudaMemset(d->bt_l, 0, size_t(rows_wl) * 512));
-  FE_CUDA_TRY(cudaMemset(d->bt_y, 0, size_t(rows_y) * 512));
+  FE_CUDA_TRY(cudaMemset(d->bt_w, 0, size_t(rows_wl) * kSuper * 2));
+  FE_CUDA_TRY(cudaMemset(d->bt_l, 0, size_t(rows_wl) * kSuper * 2));
+  FE_CUDA_TRY(cudaMemset(d->bt_y, 0, size_t(rows_y) * kSuper * 2));
   std::vector<CUtensorMap> bm(3);
   void *bases[3] = {d->bt_w, d->bt_l, d->bt_y};
   const int64_t rows[3] = {rows_wl, rows_wl, rows_y};
   for (int k = 0; k < 3; ++k) {
     const cuuint32_t es[2] = {1, 1};
-    const cuuint64_t dim[2] = {256, cuuint64_t(rows[k])};
-    const cuuint64_t stride[1] = {512};
+    const cuuint64_t dim[2] = {cuuint64_t(kSuper), cuuint64_t(rows[k])};
+    const cuuint64_t stride[1] = {cuuint64_t(kSuper) * 2};
     const cuuint32_t box[2] = {64, 128};
     if (encode(&bm[size_t(k)], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bases[k], dim, stride, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

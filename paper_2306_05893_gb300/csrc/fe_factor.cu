@@ -649,7 +649,7 @@ constexpr int kPanelStage = 72;
 // XK    (front, k0, c0): Y[K, c0:c0+64] <- L_KK^{-1} Y[K, c0:c0+64].
 // With the BF16 superpanel ends (bw non-null), both also write their results
 // into the K-major BF16 copies of the superpanel, at column k0 - s0 of the
-// 256: PANEL the rows of W = F L_KK^{-T} (bw) and of L (bl), XK the pivot rows
+// kSuper: PANEL the rows of W = F L_KK^{-T} (bw) and of L (bl), XK the pivot rows
 // of Y as row first + c of by; the 64 columns of a panel's chunk are written
 // whole (zeros past the panel's kb pivots), so the last, partial chunk of a
 // superpanel adds nothing.
@@ -1042,7 +1042,7 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
   const int4 t = reinterpret_cast<const int4 *>(tasks)[blockIdx.x];
   const DFront fr = fronts[t.x];
   const int kind = (t.y >> 24) & 7;
-  const int chunks = ((t.y >> 27) & 3) + 1;
+  const int chunks = ((t.y >> 27) & 7) + 1;
   const int32_t k0 = t.y & 0xffffff, i0 = t.z, j0 = t.w, m = fr.m, p = fr.npiv;
   const int32_t kend = min(k0 + 64 * chunks, p);
   const int32_t kw = kend - k0;
@@ -1326,7 +1326,7 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
 //   RUPD   Y[i, c] -= sum_l L[i, l] Y[l, c]   (i >= s1, c < s1)
 // with W = L D.  The operands are the K-major BF16 copies of the superpanel
 // that the panel and diagonal kernels wrote (Wt, Lt: row w_off + r of the
-// front; Yk: row first + c; 256 BF16 per row), loaded by TMA as 128-row x
+// front; Yk: row first + c; kSuper BF16 per row), loaded by TMA as 128-row x
 // 64-column boxes in the 128-byte-swizzled layout that tcgen05.mma reads
 // directly, so no thread touches an operand:
 //  * warp 0 (one lane): streams the K chunks (A and B box of 16 KB each)

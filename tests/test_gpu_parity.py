@@ -163,15 +163,15 @@ def test_mixed_factor_is_a_close_preconditioner(gpu_lib, bf16, tol):
                                                           (0, 1, 1, 3e-2, 2e-2)])
 @pytest.mark.parametrize("kind", ["tet", "hex"])
 def test_mixed_factor_with_superpanels(gpu_lib, kind, tf32, fp16, bf16, res_tol, sol_tol):
-    """FP32 factor of fronts wider than one superpanel (256 pivots, applied
+    """FP32 factor of fronts wider than one superpanel (512 pivots, applied
     to the rest of the front once per superpanel) with ragged tails: the
     preconditioned vector agrees with the FP64 direct solve to FP32 accuracy;
     a missed or doubled update would leave an O(1) error."""
-    mesh = fi.tet_beam(10, 10, 40) if kind == "tet" else fi.hex_beam(9, 9, 30, jitter=0.1, seed=4)
+    mesh = fi.tet_beam(14, 14, 40) if kind == "tet" else fi.hex_beam(13, 13, 30, jitter=0.1, seed=4)
     q, v, p = _state(mesh, amp=0.01, seed=6)
     ctx = _ctx(gpu_lib, mesh, fi.NEOHOOKE, 1, factor_tf32=tf32, precond_fp16=fp16, update_bf16=bf16)
     npiv = ctx.ordering()["npiv"]
-    assert npiv.max() > 256 and np.any(npiv % 64 != 0)
+    assert npiv.max() > 512 and np.any(npiv % 64 != 0)
     ctx.set_state(q, v)
     A, _ = ctx.assemble(p)
     ctx.factor_now()
