@@ -15,6 +15,10 @@ constexpr int kTile = 64;      // tile edge of the front update kernels
 constexpr int kSuper = 512;    // FP32 factor: trailing updates are applied once per kSuper pivots
                                // (512: a synchronous factorisation at 350k DOF takes 23.15 ms,
                                // against 24.05 at 256 and 23.55 at 1024)
+constexpr int kSub = 128;      // FP32 factor: inside a superpanel, the updates of its own columns
+                               // are applied once per kSub pivots (22.55 ms for the factorisation
+                               // above, against 23.15 with an update per 64-pivot panel)
+static_assert(kSuper % kSub == 0 && kSub % kNB == 0, "sub-blocks tile a superpanel in whole panels");
 constexpr int kBwdCols = 32;   // pivot columns per task of the backward apply
 constexpr int kFwdCols = 256;  // pivot columns per task of the forward apply (split over CTAs)
 constexpr int kBwdRows = 1024; // rows per task of the backward apply (split over CTAs)

@@ -863,10 +863,14 @@ __global__ void __launch_bounds__(256) front_update_kernel(const int32_t *__rest
 //   RUPD   Y[i, c] -= sum_l L[i, l] Y[l, c]         (c < k0 + K)
 // A task whose K range ends before the end of its superpanel (kSuper
 // columns) is an eager one: it updates only the columns (TRAIL) or rows
-// (RUPD) that are still inside the superpanel.  The superpanel's last panel
-// step then applies the whole superpanel at once (K up to kSuper) to the
-// rest of the front, so the trailing matrix is read and written once per
-// kSuper pivots instead of once per 64.
+// (RUPD) that are still inside the superpanel, and only those inside its
+// sub-block (kSub columns) when its K range also ends before the
+// sub-block's end.  A sub-block's last panel step applies the sub-block
+// (K = kSub) to the rest of the superpanel, and the superpanel's last panel
+// step applies the whole superpanel at once (K up to kSuper) to the rest of
+// the front, so the trailing matrix is read and written once per kSuper
+// pivots instead of once per 64, and the superpanel's own columns once per
+// kSub.
 //
 // Blackwell tensor cores (tcgen05, kind::tf32) with a 3xTF32 split
 // (a = a_hi + a_lo, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) so products keep
@@ -1047,7 +1051,17 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
   const int32_t kend = min(k0 + 64 * chunks, p);
   const int32_t kw = kend - k0;
   const int32_t s_end = min((k0 / kSuper + 1) * kSuper, p);
+  const int32_t b_end = min((k0 / kSub + 1) * kSub, s_end);
   const bool eager = kend < s_end;
+  const int32_t e_end = kend < b_end ? b_end : s_end;  // an eager task's column (row) bound
+  // TRAIL writes the lower part of columns < cmax (the sub-block's or the
+  // superpanel's end for an eager task), RUPD rows < rmax of columns < kend;
+  // a delayed task's tile may start below the superpanel's end (its origin is
+  // rounded down to a multiple of 4), and those rows and columns are not
+  // touched
+  const int32_t cmax = kind == T_TRAIL ? (eager ? e_end : m) : kend;
+  const int32_t rmax = (kind != T_TRAIL && eager) ? e_end : m;
+  const int32_t lo = eager ? 0 : s_end;
   const bool trail = kind == T_TRAIL;
   const CUtensorMap *mapA = fmaps + t.x;
   const CUtensorMap *mapB = trail ? fmaps + t.x : ymaps + t.x;
@@ -1250,14 +1264,6 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
     if (ok && nq > 0) ok = mbar_wait(bar_mma + 8 * ((nq - 1) % NOS), uint32_t((nq - 1) / NOS) & 1u, abort_word);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (ok) {
-      // TRAIL writes the lower part of columns < cmax (the superpanel's end
-      // for an eager task), RUPD rows < rmax of columns < kend; a delayed
-      // task's tile may start below the superpanel's end (its origin is
-      // rounded down to a multiple of 4), and those rows and columns are
-      // not touched
-      const int32_t cmax = trail ? (eager ? s_end : m) : kend;
-      const int32_t rmax = (!trail && eager) ? s_end : m;
-      const int32_t lo = eager ? 0 : s_end;
       const int g = warp & 3, h = warp >> 2;
       const int rl = 32 * g + lane;
       const int32_t r = i0 + rl;
@@ -1296,9 +1302,17 @@ __global__ void __launch_bounds__(kUThreads, 2) front_update_tc_kernel(
   if (!ok) s_abort = 1;
   ok = __syncthreads_and(ok) != 0;
   if (ok && threadIdx.x == 0) {
-    // F (or Y) += the staged tile: eight TMA reduce-add boxes, clipped to
-    // the front (entries outside the task's range add 0)
-    for (int b = 0; b < 8; ++b) tma_reduce_add_2d(mapC, i0, j0 + 16 * b, raw_u + uint32_t(b) * kT128 * 16 * 4);
+    // F (or Y) += the staged tile: TMA reduce-add boxes of 16 columns,
+    // clipped to the front (entries outside the task's range add 0); a box
+    // whose columns are all outside the range of every row of the tile
+    // (TRAIL: at or beyond min(cmax, the tile's last row + 1); RUPD: beyond
+    // kend; both: below lo for TRAIL) is left out
+    const int32_t c_hi = trail ? min(cmax, min(i0 + kT128, rmax)) : cmax;
+    const int32_t c_lo = trail ? lo : 0;
+    for (int b = 0; b < 8; ++b) {
+      const int32_t cb = j0 + 16 * b;
+      if (cb < c_hi && cb + 16 > c_lo) tma_reduce_add_2d(mapC, i0, cb, raw_u + uint32_t(b) * kT128 * 16 * 4);
+    }
     asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
     asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   }

@@ -711,13 +711,27 @@ int build_ordering(fe_ctx *c) {
         push(L.diag[s], f, (T_DIAG << 24) | k0, kb, 0);
         for (int32_t r0 = k1; r0 < m; r0 += kTile) push(L.panel[s], f, (T_PANEL << 24) | k0, r0, 0);
         for (int32_t c0 = 0; c0 < k0; c0 += kTile) push(L.panel[s], f, (T_XK << 24) | k0, c0, 0);
-        // trailing and Y updates: eager inside the superpanel [s0, s1), the
-        // rest of the front once per superpanel with K = s1 - s0 (FP32 path)
+        // trailing and Y updates (FP32 path): eager inside the sub-block
+        // [b0, b1) of the superpanel [s0, s1), the rest of the superpanel's
+        // columns (rows of Y) once per sub-block with K = b1 - b0, the rest
+        // of the front once per superpanel with K = s1 - s0
         const int32_t s0 = k0 / sp * sp, s1 = std::min(s0 + sp, p);
-        for (int32_t j0 = k1; j0 < s1; j0 += ut)
+        const int32_t sb = std::min(kSub, sp);
+        const int32_t b0 = k0 / sb * sb, b1 = std::min(b0 + sb, s1);
+        for (int32_t j0 = k1; j0 < b1; j0 += ut)
           for (int32_t i0 = j0; i0 < m; i0 += ut) push(L.trail[s], f, (T_TRAIL << 24) | k0, i0, j0);
-        for (int32_t i0 = k1; i0 < s1; i0 += ut)
+        for (int32_t i0 = k1; i0 < b1; i0 += ut)
           for (int32_t c0 = 0; c0 < k1; c0 += ut) push(L.trail[s], f, (T_RUPD << 24) | k0, i0, c0);
+        if (k1 == b1 && b1 < s1) {
+          // b1 is a multiple of kSub here, so the tiles start aligned
+          const int32_t chunks = (b1 - b0 + kNB - 1) / kNB;
+          const int32_t code = ((T_TRAIL | ((chunks - 1) << 3)) << 24) | b0;
+          const int32_t codeu = ((T_RUPD | ((chunks - 1) << 3)) << 24) | b0;
+          for (int32_t j0 = b1; j0 < s1; j0 += ut)
+            for (int32_t i0 = j0; i0 < m; i0 += ut) push(L.trail[s], f, code, i0, j0);
+          for (int32_t i0 = b1; i0 < s1; i0 += ut)
+            for (int32_t c0 = 0; c0 < b1; c0 += ut) push(L.trail[s], f, codeu, i0, c0);
+        }
         if (k1 == s1) {
           const int32_t chunks = (s1 - s0 + kNB - 1) / kNB;
           const int32_t code = ((T_TRAIL | ((chunks - 1) << 3)) << 24) | s0;
