@@ -325,8 +325,10 @@ int fe_apply_preconditioner(fe_ctx *ctx, const double *r, double *z);
  * The call is asynchronous on `stream` and allocates nothing: its work
  * vectors live in one file-scope device array of 64 MiB that every GPU
  * loading the library holds until exit.  A mesh needing more
- * (fe_info.noalloc_bytes: about (2 n + update rows + free DOFs) x 4 or 8
- * bytes) is rejected with FE_ERR_ARG before any GPU work.  The context must
+ * (fe_info.noalloc_bytes: (2 n + update rows + free DOFs) x 4 or 8 bytes
+ * plus the split application tasks' partial sums, two to three times the
+ * vectors alone; 16.9 MB mixed and 33.5 MB FP64 at 348,843 DOF) is
+ * rejected with FE_ERR_ARG before any GPU work.  The context must
  * already hold a factor (fe_factor_now or fe_step) and its device must be
  * current.  The first call on a device looks the array's address up
  * (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -376,3 +376,37 @@ def test_noalloc_rejects_oversize_mesh_on_the_host(fe):
     assert 0 < small.info()["noalloc_bytes"] <= 64 * 2 ** 20
     assert lib.fe_apply_preconditioner_noalloc(small.ctx, dummy, dummy, None) == 9
     small.close()
+
+
+def test_noalloc_scratch_size_and_over_size_refusal(fe):
+    """The allocation-free application's scratch (fe_info.noalloc_bytes) holds
+    at least the two work vectors of length n, the update vectors (the sum of
+    the fronts' update rows) and the permuted pivot vector, each 256-byte
+    aligned, at 8 bytes per value in FP64 and 4 in the mixed path.  A mesh
+    whose scratch exceeds the library's 64 MiB array is refused with
+    FE_ERR_ARG before any device work, so the call runs on a host without a
+    GPU (the pointers are never dereferenced)."""
+    mesh = fi.tet_beam(10, 10, 40)
+    sizes = {}
+    for prec, ts in ((0, 8), (1, 4)):
+        ctx = _ctx(fe, mesh, precision=prec)
+        o = ctx.ordering()
+        need = ctx.info()["noalloc_bytes"]
+        low = (2 * ctx.n + int(np.sum(o["nupd"])) + int(np.sum(o["npiv"]))) * ts
+        assert need % 256 == 0 and need >= low
+        sizes[prec] = need
+        ctx.close()
+    # the same layout at half the value size (the task tickets are 4-byte ints in both)
+    assert sizes[1] < sizes[0] <= 2 * sizes[1]
+
+    big = fi.tet_beam(40, 40, 160)  # 811,923 DOF: about 92 MiB of scratch in FP64
+    ctx = _ctx(fe, big, precision=0)
+    need = ctx.info()["noalloc_bytes"]
+    assert need > 64 << 20
+    dummy = (ct.c_double * 1)()
+    st = fe.load().fe_apply_preconditioner_noalloc(ctx.ctx, ct.cast(dummy, ct.c_void_p), ct.cast(dummy, ct.c_void_p),
+                                                   None)
+    assert st == 1  # FE_ERR_ARG
+    msg = fe.load().fe_last_error(ctx.ctx).decode()
+    assert str(need) in msg and str(64 << 20) in msg
+    ctx.close()
