@@ -164,9 +164,11 @@ def test_mixed_factor_is_a_close_preconditioner(gpu_lib, bf16, tol):
 @pytest.mark.parametrize("kind", ["tet", "hex"])
 def test_mixed_factor_with_superpanels(gpu_lib, kind, tf32, fp16, bf16, res_tol, sol_tol):
     """FP32 factor of fronts wider than one superpanel (512 pivots, applied
-    to the rest of the front once per superpanel) with ragged tails: the
-    preconditioned vector agrees with the FP64 direct solve to FP32 accuracy;
-    a missed or doubled update would leave an O(1) error."""
+    to the rest of the front once per superpanel; inside it, 128-pivot
+    sub-blocks applied to the rest of the superpanel once per sub-block)
+    with ragged tails: the preconditioned vector agrees with the FP64 direct
+    solve to FP32 accuracy; a missed or doubled update would leave an O(1)
+    error."""
     mesh = fi.tet_beam(14, 14, 40) if kind == "tet" else fi.hex_beam(13, 13, 30, jitter=0.1, seed=4)
     q, v, p = _state(mesh, amp=0.01, seed=6)
     ctx = _ctx(gpu_lib, mesh, fi.NEOHOOKE, 1, factor_tf32=tf32, precond_fp16=fp16, update_bf16=bf16)
